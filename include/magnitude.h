@@ -1,0 +1,201 @@
+/*
+ * magnitude.h -- C ABI of the GB300 metric-magnitude solver.
+ *
+ * Paper: "Scalably computing metric magnitude" (arXiv 2607.23354).
+ *
+ * For points x_1..x_n in R^m (Sec. 2):
+ *   d_jk = ||x_j - x_k||          (Euclidean distance, from coordinate differences)
+ *   Z    = exp[-t d]              (similarity matrix, componentwise exp, t > 0)
+ *   Z w  = 1                      (Eq. weighting; Z is positive definite, w unique)
+ *   Mag  = 1^T w                  (magnitude)
+ *   t_+  = least t with w >= 0    (cutoff, Sec. 2), bounded by
+ *          t_+ <= log(n-1) / min_{j != k} d_jk   (Sec. 1)
+ *
+ * Conventions for every entry point:
+ *   - Every function returns an int status (enum mag_status).  On an error
+ *     mag_last_error(ctx) gives a one-line message for that context.
+ *   - Array arguments are DEVICE pointers owned by the caller (for example
+ *     PyTorch tensors on the context's device), FP64, C-contiguous.  Points
+ *     are an n x m row-major array.  Scalars come back through HOST pointers.
+ *   - Work is ordered on the stream given to mag_ctx_create; every entry
+ *     point returns after its results (device arrays and host scalars) are
+ *     complete on that stream (the host waits on the stream).
+ *   - The library owns only the workspace inside a context (device memory it
+ *     allocates and grows on demand, freed by mag_ctx_destroy).  A context is
+ *     used by one host thread at a time; use one context per thread/stream.
+ *   - Invalid arguments (n < 2, m < 1, t <= 0 or not finite, NULL pointers)
+ *     give MAG_EINVAL before any device work.  Non-finite coordinates give
+ *     MAG_EINVAL and coincident points MAG_EDUPLICATE (Z is then singular),
+ *     both detected on the device while Z is generated.
+ */
+#ifndef MAGNITUDE_H
+#define MAGNITUDE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum mag_status {
+  MAG_OK = 0,
+  MAG_EINVAL = 1,        /* bad argument or non-finite coordinate            */
+  MAG_EDUPLICATE = 2,    /* two points coincide: min d = 0, Z singular        */
+  MAG_ENOTPD = 3,        /* every precision tried hit a non-positive pivot    */
+  MAG_ENOCONV = 4,       /* refinement did not reach the tolerance; the best
+                            w found is returned with its residual in info    */
+  MAG_ENOBRACKET = 5,    /* sweep: w is not nonnegative at the upper end     */
+  MAG_ENOMEM = 6,        /* workspace allocation failed or exceeds the limit */
+  MAG_ECUDA = 7,         /* a CUDA call failed (message in mag_last_error)   */
+  MAG_ETIMEOUT = 8       /* a bounded device wait gave up                    */
+};
+
+/* Precision of the Cholesky factor (Zw = 1 is always refined in FP64). */
+enum mag_precision {
+  MAG_PREC_AUTO = 0,     /* pick from a Gershgorin bound on lambda_min(Z)    */
+  MAG_PREC_BF16 = 1,     /* BF16 tensor-core products, FP32 accumulation      */
+  MAG_PREC_TF32 = 2,     /* one TF32 tensor-core product, FP32 accumulation   */
+  MAG_PREC_TF32X3 = 3,   /* split TF32 (hi*hi + hi*lo + lo*hi), FP32 accum.   */
+  MAG_PREC_FP32 = 4,     /* FP32 CUDA-core products (no tensor cores)          */
+  MAG_PREC_FP64 = 5      /* full FP64 factor (the plain dense method)          */
+};
+
+/* How the FP64 residual r = 1 - Zw of iterative refinement is formed. */
+enum mag_residual_mode {
+  MAG_RESID_MATRIX_FREE = 0, /* Z_jk regenerated in FP64 from the points      */
+  MAG_RESID_STORED = 1       /* Z kept in FP64 tiles, residual reads them      */
+};
+
+typedef struct mag_options {
+  int32_t precision;      /* enum mag_precision, default MAG_PREC_AUTO           */
+  int32_t residual_mode;  /* enum mag_residual_mode, default MATRIX_FREE         */
+  double ir_tol;          /* target ||1-Zw||inf/(||Z||inf ||w||inf), default 1e-14 */
+  int32_t ir_max_iters;   /* refinement steps before escalating, default 12     */
+  int32_t gmres_max_iters;/* inner GMRES iterations of GMRES-IR, default 30     */
+  int32_t allow_fallback; /* 1: escalate to GMRES-IR then FP64 factor (default)  */
+  int32_t panel_tiles;    /* outer panel width in 128-wide tiles (0 = default)  */
+  double workspace_limit_bytes; /* 0 = no limit; larger requests give ENOMEM     */
+} mag_options;
+
+/* Diagnostics of one call (all fields written when info != NULL). */
+typedef struct mag_info {
+  int32_t precision_used;  /* enum mag_precision of the factor that succeeded  */
+  int32_t ir_iters;        /* refinement steps taken (all precisions)          */
+  int32_t gmres_iters;     /* total inner GMRES iterations (0 if not used)     */
+  int32_t fallback;        /* 0 none, 1 GMRES-IR, 2 FP64 factor                */
+  double rel_residual;     /* final ||1-Zw||inf / (||Z||inf ||w||inf)          */
+  double z_norm_inf;       /* ||Z||inf = max row sum                           */
+  double w_norm_inf;       /* max |w_j|                                       */
+  double min_w;            /* min w_j                                         */
+  double gershgorin_lmin;  /* 1 - max_j sum_{k != j} Z_jk (lower bound on lambda_min) */
+  double min_distance;     /* min_{j != k} d_jk                                */
+  int32_t below_bracket;   /* sweep: feasible already at t_lo                  */
+  int32_t probes;          /* sweep: number of solves                           */
+  double ms_generate, ms_factor, ms_solve, ms_residual, ms_total;
+  double useful_flops;     /* n^3/3 + 2n^2 per triangular-solve pair + 2 n^2 m per residual */
+} mag_info;
+
+typedef struct mag_ctx mag_ctx;
+
+/* Fill *opt with the defaults listed above. */
+int mag_options_default(mag_options* opt);
+
+/* Create a context bound to the current CUDA device and `stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  opt == NULL = defaults.
+ * The options are copied. */
+int mag_ctx_create(mag_ctx** ctx, void* stream, const mag_options* opt);
+/* Replace the options of an existing context. */
+int mag_ctx_set_options(mag_ctx* ctx, const mag_options* opt);
+/* Free the context and its workspace (NULL is a no-op). */
+int mag_ctx_destroy(mag_ctx* ctx);
+/* Message of the last error on this context ("" if none).  Valid until the
+ * next call on the context. */
+const char* mag_last_error(const mag_ctx* ctx);
+/* Static name of a status code. */
+const char* mag_status_string(int status);
+/* Device bytes the workspace of a solve of size n needs under ctx's options. */
+int mag_workspace_bytes(const mag_ctx* ctx, int64_t n, int32_t m, double* bytes);
+
+/* a1 (Sec. 1): min_{j != k} d_jk and the bound t = log(n-1) / min d, from one
+ * pass over all pairs on the device.  points: device, n x m.  Host outputs.
+ * MAG_EDUPLICATE if two points coincide (then *dmin = 0, *t_bound = inf). */
+int mag_min_distance(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double* dmin,
+                     double* t_bound);
+
+/* a2 (Sec. 2): Z = exp[-t d] from the fused generator, unpacked to a dense
+ * n x n row-major array Z_out (device; FP64 when precision == MAG_PREC_FP64,
+ * else FP32, the values the factor starts from).  For inspection and tests of
+ * the generator; the solver itself never forms the dense matrix. */
+int mag_similarity_matrix(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t,
+                          int32_t precision, void* Z_out);
+
+/* a2+a3 (Sec. 3.2): the lower Cholesky factor L of Z = L L^T computed by the
+ * blocked solver in `precision` (MAG_PREC_FP64 -> FP64 output, else FP32),
+ * unpacked to a dense n x n row-major array L_out (device; zeros above the
+ * diagonal).  MAG_ENOTPD if a pivot is not positive. */
+int mag_cholesky_factor(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t,
+                        int32_t precision, void* L_out);
+
+/* a2-a7 (Sec. 2, Eq. weighting): solve Zw = 1 for Z = exp[-t d] and return
+ * Mag = 1^T w.  points: device n x m FP64; w: device output, n FP64; mag:
+ * host output.  The factor precision follows ctx's options (MAG_PREC_AUTO:
+ * BF16 when the Gershgorin bound gives lambda_min >= 0.5, else split TF32);
+ * FP64 iterative refinement with a residual formed in FP64 runs until the
+ * relative residual is <= ir_tol, escalating to GMRES-IR and then to an FP64
+ * factor when allow_fallback is set.  MAG_ENOCONV returns the best w found. */
+int mag_solve(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t, double* w,
+              double* mag, mag_info* info);
+
+/* The same solve for a general right-hand side: Z x = b (b: device, n).  Used
+ * for the adjoint solve lambda = Z^{-1} dL/dw of mag_grad. */
+int mag_solve_rhs(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t,
+                  const double* b, double* x, mag_info* info);
+
+/* a8 (Sec. 2 and its footnote): bisection for the cutoff t_+ on the sign of
+ * min_j w_j.  feasible(t) <=> min_j w_j(t) >= 0.  t_hi <= 0 uses the Sec. 1
+ * bound.  The bracket keeps feasible(hi) and not feasible(lo); each probe
+ * solves at the FP64 midpoint lo + (hi - lo)/2; it stops when
+ * hi - lo <= rel_tol * hi.  Outputs (host): *t_plus = hi, t_bracket[0..1] =
+ * {lo, hi}; w (device, n) and *mag are those at t_plus.  If feasible(t_lo)
+ * holds, returns MAG_OK with t_plus = t_lo and info->below_bracket = 1.  If
+ * feasible(t_hi) fails, MAG_ENOBRACKET. */
+int mag_sweep_tplus(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t_lo,
+                    double t_hi, double rel_tol, double* t_plus, double* t_bracket, double* w,
+                    double* mag, mag_info* info);
+
+/* a9: gradients by implicit differentiation of Zw = 1 (not in the paper).
+ * For a loss L(w) with g = dL/dw (device, n; NULL means L = Mag, g = 1):
+ *   lambda = Z^{-1} g (lambda = w when g = 1),
+ *   dL/dt   = lambda^T (d o Z) w,
+ *   dL/dx_i = t sum_{k != i} Z_ik (x_i - x_k)/d_ik (lambda_i w_k + lambda_k w_i).
+ * w (device, n) may be NULL, in which case it is solved first.  Outputs:
+ * *dL_dt (host), dL_dx (device, n x m row-major). */
+int mag_grad(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t,
+             const double* w, const double* dL_dw, double* dL_dt, double* dL_dx, mag_info* info);
+
+/* One problem of a batch: points of cloud c start at points + point_offset
+ * (units of doubles, n x m row-major); its weighting is written at
+ * w_out + w_offset (n doubles) and its magnitude at mag_out[index]. */
+typedef struct mag_batch_desc {
+  int64_t point_offset;
+  int64_t w_offset;
+  int32_t n;
+  int32_t m;
+  double t;
+} mag_batch_desc;
+
+/* a10: many independent solves (uneven n, any t) in one persistent launch
+ * sequence.  desc: HOST array of count descriptors; points, w_out: device;
+ * mag_out: device, count doubles.  Each problem is factored in FP32 and
+ * refined in FP64 to ctx's ir_tol.  status_out (device, count int32, may be
+ * NULL) receives a per-problem mag_status.  Returns MAG_OK when every
+ * problem converged, else the first failing status. */
+int mag_solve_batch(mag_ctx* ctx, const mag_batch_desc* desc, int32_t count, const double* points,
+                    double* w_out, double* mag_out, int32_t* status_out, mag_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAGNITUDE_H */

@@ -1,0 +1,345 @@
+// K2: blocked right-looking Cholesky Z = L L^T on packed lower tiles (Sec. 3.2:
+// Z is positive definite for Euclidean d, so the factor exists; a pivot that
+// is not positive is reported as the Sec. 4.2 PD-check failure, never trapped).
+//
+//   potrf  : one CTA factors the diagonal tile in shared memory and also forms
+//            inv(L_KK) and its transpose (kept for the panel solve and for the
+//            block triangular solves).
+//   trsm   : panel tiles L_IK = A_IK inv(L_KK)^T as a small GEMM (in place).
+//   syrk   : CUDA-core trailing update C_IJ -= sum_k L_Ik L_Jk^T over a set of
+//            tiles (the tensor-core version lives in k_gemm_tc.cu).
+//
+// Also K3: block forward/back substitution with the packed factor, using the
+// stored inverses of the diagonal blocks so that every step is a GEMV.
+//
+// All kernels are templated on the element type (float for the mixed
+// precision factor, double for the FP64 factor).
+#include <algorithm>
+
+#include "mag_internal.cuh"
+
+namespace mag {
+
+namespace {
+
+template <typename T>
+__device__ inline T tsqrt(T x);
+template <>
+__device__ inline float tsqrt<float>(float x) { return sqrtf(x); }
+template <>
+__device__ inline double tsqrt<double>(double x) { return sqrt(x); }
+
+constexpr int LDA = TILE + 1;  // padded shared-memory row stride
+
+// ------------------------------------------------------------------ potrf
+template <typename T>
+__global__ void __launch_bounds__(512) k_potrf_diag(T* __restrict__ Z, T* __restrict__ Dinv,
+                                                    T* __restrict__ DinvT, int64_t K, int64_t n,
+                                                    DevStatus* st) {
+  extern __shared__ unsigned char smem_raw[];
+  T* A = reinterpret_cast<T*>(smem_raw);  // [TILE][LDA]
+  __shared__ int failed, skip;
+  if (threadIdx.x == 0) {
+    failed = 0;
+    skip = (st->flags & (ST_NOTPD | ST_NONFINITE | ST_DUPLICATE)) != 0;  // set by earlier kernels
+  }
+  __syncthreads();
+  if (skip) return;  // uniform across the CTA
+  T* tile = Z + tri_index(K, K) * TILE_ELEMS;
+  for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
+    const int r = e / TILE, c = e % TILE;
+    A[r * LDA + c] = tile[e];
+  }
+  __syncthreads();
+  for (int c = 0; c < TILE; ++c) {
+    if (threadIdx.x == 0) {
+      T p = A[c * LDA + c];
+      if (!(p > T(0))) {
+        if (!failed) {
+          failed = 1;
+          atomicOr(&st->flags, ST_NOTPD);
+          atomicCAS(&st->notpd_index, 0, (int)(K * TILE + c + 1));
+        }
+        p = T(1);
+      }
+      A[c * LDA + c] = tsqrt(p);
+    }
+    __syncthreads();
+    const T inv = T(1) / A[c * LDA + c];
+    for (int r = c + 1 + threadIdx.x; r < TILE; r += blockDim.x) A[r * LDA + c] *= inv;
+    __syncthreads();
+    const int w = TILE - 1 - c;  // trailing size
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+      const int r = c + 1 + e / w, cc = c + 1 + e % w;
+      if (cc <= r) A[r * LDA + cc] -= A[r * LDA + c] * A[cc * LDA + c];
+    }
+    __syncthreads();
+  }
+  // write L (zeros above the diagonal)
+  for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
+    const int r = e / TILE, c = e % TILE;
+    tile[e] = c <= r ? A[r * LDA + c] : T(0);
+  }
+  // inv(L): column c by forward substitution, one thread per column, values
+  // kept in the strict upper triangle of A (transposed) and the diagonal in
+  // a separate array.
+  __shared__ T ydiag[TILE];
+  if (threadIdx.x < TILE) {
+    const int c = threadIdx.x;
+    ydiag[c] = T(1) / A[c * LDA + c];
+  }
+  __syncthreads();
+  if (threadIdx.x < TILE) {
+    const int c = threadIdx.x;
+    // Y[r][c] for r > c stored at A[c][r] (strict upper, r > c)
+    for (int r = c + 1; r < TILE; ++r) {
+      T s = A[r * LDA + c] * ydiag[c];
+      for (int k = c + 1; k < r; ++k) s += A[r * LDA + k] * A[c * LDA + k];
+      A[c * LDA + r] = -s / A[r * LDA + r];
+    }
+  }
+  __syncthreads();
+  T* Y = Dinv + K * TILE_ELEMS;
+  T* YT = DinvT + K * TILE_ELEMS;
+  for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
+    const int r = e / TILE, c = e % TILE;
+    // Y[r][c]: lower triangle of inv(L)
+    T y = r == c ? ydiag[r] : (c < r ? A[c * LDA + r] : T(0));
+    Y[e] = y;
+    // YT[r][c] = Y[c][r]
+    T yt = r == c ? ydiag[r] : (r < c ? A[r * LDA + c] : T(0));
+    YT[e] = yt;
+  }
+}
+
+// ------------------------------------------------- CUDA-core tile GEMM (NT)
+// C (TILE x TILE) = alpha*C - sign * sum_k A_k B_k^T, A_k/B_k row-major tiles.
+constexpr int KC = 16;
+
+template <typename T, bool ASSIGN>
+__device__ inline void tile_gemm_nt(T* __restrict__ C, const T* const* Ak, const T* const* Bk,
+                                    int nk) {
+  __shared__ T As[KC][TILE + 4];
+  __shared__ T Bs[KC][TILE + 4];
+  const int tid = threadIdx.x;
+  const int ty = tid / 16, tx = tid % 16;
+  T acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = T(0);
+  for (int kt = 0; kt < nk; ++kt) {
+    const T* A = Ak[kt];
+    const T* B = Bk[kt];
+    for (int k0 = 0; k0 < TILE; k0 += KC) {
+      for (int e = tid; e < TILE * KC; e += 256) {
+        const int r = e / KC, k = e % KC;
+        As[k][r] = A[r * TILE + k0 + k];
+        Bs[k][r] = B[r * TILE + k0 + k];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < KC; ++k) {
+        T a[8], b[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) b[i] = Bs[k][tx + 16 * i];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] += a[i] * b[j];
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      T* p = C + (ty + 16 * i) * TILE + tx + 16 * j;
+      if (ASSIGN)
+        *p = acc[i][j];
+      else
+        *p -= acc[i][j];
+    }
+}
+
+// Panel solve of column K: tiles (I, K), I = K+1+blockIdx.x.
+template <typename T>
+__global__ void __launch_bounds__(256) k_trsm_col(T* __restrict__ Z, const T* __restrict__ Dinv,
+                                                  int64_t K, DevStatus* st) {
+  if (st->flags & (ST_NOTPD | ST_NONFINITE | ST_DUPLICATE)) return;
+  const int64_t I = K + 1 + blockIdx.x;
+  T* C = Z + tri_index(I, K) * TILE_ELEMS;
+  const T* A[1] = {C};
+  const T* B[1] = {Dinv + K * TILE_ELEMS};
+  tile_gemm_nt<T, true>(C, A, B, 1);
+}
+
+// Trailing update over the trapezoid J in [j0, j1), I in [J, N): the linear
+// block index enumerates columns from the right (column J has N - J tiles).
+template <typename T>
+__global__ void __launch_bounds__(256) k_syrk_simt(T* __restrict__ Z, int64_t N, int64_t k0,
+                                                   int64_t k1, int64_t base, DevStatus* st) {
+  if (st->flags & (ST_NOTPD | ST_NONFINITE | ST_DUPLICATE)) return;
+  int64_t Jp, ii;
+  tri_coords((int64_t)blockIdx.x + base, &Jp, &ii);
+  const int64_t J = N - 1 - Jp, I = J + ii;
+  constexpr int MAXK = 16;
+  const T* Ak[MAXK];
+  const T* Bk[MAXK];
+  T* C = Z + tri_index(I, J) * TILE_ELEMS;
+  for (int64_t ks = k0; ks < k1; ks += MAXK) {
+    const int nk = (int)((k1 - ks) < MAXK ? (k1 - ks) : MAXK);
+    for (int q = 0; q < nk; ++q) {
+      Ak[q] = Z + tri_index(I, ks + q) * TILE_ELEMS;
+      Bk[q] = Z + tri_index(J, ks + q) * TILE_ELEMS;
+    }
+    tile_gemm_nt<T, false>(C, Ak, Bk, nk);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------ triangular solves
+// Forward step J: y_J = inv(L_JJ) v_J (all CTAs, redundantly), CTA 0 stores
+// it in y; CTA b > 0 updates v_I -= L_IJ y_J for I = J + b.
+template <typename T>
+__global__ void __launch_bounds__(128) k_forward_step(const T* __restrict__ Z,
+                                                      const T* __restrict__ DinvT, int64_t J,
+                                                      T* __restrict__ v, T* __restrict__ y) {
+  __shared__ T ys[TILE];
+  const int r = threadIdx.x;
+  const T* YT = DinvT + J * TILE_ELEMS;
+  const T* vJ = v + J * TILE;
+  T s = T(0);
+  for (int c = 0; c <= TILE - 1; ++c) s += YT[c * TILE + r] * vJ[c];  // Y[r][c] = YT[c][r]
+  ys[r] = s;
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    y[J * TILE + r] = s;
+    return;
+  }
+  const int64_t I = J + blockIdx.x;
+  const T* L = Z + tri_index(I, J) * TILE_ELEMS;
+  const int warp = r >> 5, lane = r & 31;
+  for (int rr = warp; rr < TILE; rr += 4) {
+    const T* row = L + rr * TILE;
+    T p = T(0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) p += row[lane + 32 * q] * ys[lane + 32 * q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+    if (lane == 0) v[I * TILE + rr] -= p;
+  }
+}
+
+// Backward step J: x_J = inv(L_JJ)^T v_J (all CTAs), CTA 0 stores it in x;
+// CTA b > 0 updates v_I -= L_JI^T x_J for I = J - b.
+template <typename T>
+__global__ void __launch_bounds__(128) k_backward_step(const T* __restrict__ Z,
+                                                       const T* __restrict__ Dinv, int64_t J,
+                                                       T* __restrict__ v, T* __restrict__ x) {
+  __shared__ T xs[TILE];
+  const int c = threadIdx.x;
+  const T* Y = Dinv + J * TILE_ELEMS;
+  const T* vJ = v + J * TILE;
+  T s = T(0);
+  for (int r = 0; r < TILE; ++r) s += Y[r * TILE + c] * vJ[r];  // (Y^T v)[c]
+  xs[c] = s;
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    x[J * TILE + c] = s;
+    return;
+  }
+  const int64_t I = J - blockIdx.x;
+  const T* L = Z + tri_index(J, I) * TILE_ELEMS;
+  T p = T(0);
+  for (int r = 0; r < TILE; ++r) p += L[r * TILE + c] * xs[r];
+  v[I * TILE + c] -= p;
+}
+
+template <typename T>
+__global__ void k_unpack(const T* __restrict__ Z, int64_t n, int symmetric, T* __restrict__ out) {
+  const int64_t r = blockIdx.y;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = r >= c ? r : c, b = r >= c ? c : r;  // lower-triangle coordinates
+    T v = Z[tri_index(a / TILE, b / TILE) * TILE_ELEMS + (a % TILE) * TILE + (b % TILE)];
+    if (r < c && !symmetric) v = T(0);
+    out[r * n + c] = v;
+  }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_unpack(const T* Z, int64_t n, int64_t N, bool symmetric, T* out, cudaStream_t s) {
+  (void)N;
+  if (n > 65535) return cudaErrorInvalidValue;
+  const unsigned bx = (unsigned)std::min<int64_t>((n + 255) / 256, 64);
+  k_unpack<T><<<dim3(bx, (unsigned)n), 256, 0, s>>>(Z, n, symmetric ? 1 : 0, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_potrf_diag(T* Z, T* Dinv, int64_t K, int64_t n, DevStatus* st, cudaStream_t s) {
+  const size_t smem = (size_t)TILE * LDA * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(k_potrf_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t N = (n + TILE - 1) / TILE;
+  // Dinv holds N tiles of inv(L_KK) followed by N tiles of inv(L_KK)^T.
+  k_potrf_diag<T><<<1, 512, smem, s>>>(Z, Dinv, Dinv + N * TILE_ELEMS, K, n, st);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_trsm_col(T* Z, const T* Dinv, int64_t K, int64_t N, DevStatus* st,
+                            cudaStream_t s) {
+  if (K + 1 >= N) return cudaSuccess;
+  k_trsm_col<T><<<(unsigned)(N - K - 1), 256, 0, s>>>(Z, Dinv, K, st);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_syrk_simt(T* Z, int64_t N, int64_t k0, int64_t k1, int64_t j0, int64_t j1,
+                             DevStatus* st, cudaStream_t s) {
+  if (j0 >= j1 || k0 >= k1) return cudaSuccess;
+  const int64_t base = (N - j1) * (N - j1 + 1) / 2;
+  const int64_t count = (N - j0) * (N - j0 + 1) / 2 - base;
+  k_syrk_simt<T><<<(unsigned)count, 256, 0, s>>>(Z, N, k0, k1, base, st);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_forward(const T* Z, const T* Dinv, int64_t N, T* v, T* y, cudaStream_t s) {
+  const T* DinvT = Dinv + N * TILE_ELEMS;
+  for (int64_t J = 0; J < N; ++J) {
+    k_forward_step<T><<<(unsigned)(N - J), TILE, 0, s>>>(Z, DinvT, J, v, y);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_backward(const T* Z, const T* Dinv, int64_t N, T* v, T* x, cudaStream_t s) {
+  for (int64_t J = N - 1; J >= 0; --J) {
+    k_backward_step<T><<<(unsigned)(J + 1), TILE, 0, s>>>(Z, Dinv, J, v, x);
+  }
+  return cudaGetLastError();
+}
+
+#define MAG_INST(T)                                                                              \
+  template cudaError_t launch_potrf_diag<T>(T*, T*, int64_t, int64_t, DevStatus*, cudaStream_t); \
+  template cudaError_t launch_trsm_col<T>(T*, const T*, int64_t, int64_t, DevStatus*,            \
+                                          cudaStream_t);                                         \
+  template cudaError_t launch_syrk_simt<T>(T*, int64_t, int64_t, int64_t, int64_t, int64_t,      \
+                                           DevStatus*, cudaStream_t);                            \
+  template cudaError_t launch_forward<T>(const T*, const T*, int64_t, T*, T*, cudaStream_t);     \
+  template cudaError_t launch_backward<T>(const T*, const T*, int64_t, T*, T*, cudaStream_t);    \
+  template cudaError_t launch_unpack<T>(const T*, int64_t, int64_t, bool, T*, cudaStream_t);
+MAG_INST(float)
+MAG_INST(double)
+#undef MAG_INST
+
+}  // namespace mag

@@ -1,0 +1,198 @@
+// K1: fused distance + exp generator of Z = exp[-t d] (Sec. 2), packed lower tiles.
+//
+// One CTA per lower tile (I, J).  Coordinates of the tile's 128 row points and
+// 128 column points are staged in shared memory in chunks of MC coordinates;
+// every pair difference x_jl - x_kl is taken in FP64 and squared/accumulated
+// with FP64 FMAs (no ||x||^2 + ||y||^2 - 2 x^T y expansion, so close points do
+// not cancel).  The FP32 tile (factor input) takes sqrt/exp in FP32 from the
+// FP64 d^2; the FP64 tile (FP64 factor or stored residual) takes them in FP64.
+//
+// Thread layout (512 threads): warp w handles tile rows w + 16 i (i < 8),
+// lane l handles tile columns l + 32 q (q < 4), so each store instruction of
+// a warp writes 32 consecutive elements of one tile row (128 B for FP32).
+//
+// Side outputs, all fused: full row sums of Z (for ||Z||inf and the Gershgorin
+// bound used to choose the factor precision), min off-diagonal d^2 (the Sec. 1
+// bound), and flags for non-finite coordinates and coincident points.
+#include "mag_internal.cuh"
+
+namespace mag {
+
+namespace {
+
+constexpr int GEN_THREADS = 512;
+constexpr int GEN_MC = 32;  // coordinates staged per chunk
+
+__device__ inline void atomic_min_nonneg(unsigned long long* a, double v) {
+  atomicMin(a, (unsigned long long)__double_as_longlong(v));
+}
+__device__ inline void atomic_max_nonneg(unsigned long long* a, double v) {
+  atomicMax(a, (unsigned long long)__double_as_longlong(v));
+}
+
+template <bool WF, bool WD, bool ROWSUM>
+__global__ void __launch_bounds__(GEN_THREADS, 1)
+    k_generate(const double* __restrict__ X, int64_t n, int m, double t, float* __restrict__ Zf,
+               double* __restrict__ Zd, double* __restrict__ rowsum, DevStatus* st) {
+  extern __shared__ double smem[];
+  double* xr = smem;                   // [TILE][GEN_MC] row points (broadcast reads)
+  double* xc = smem + TILE * GEN_MC;   // [GEN_MC][TILE] column points (conflict free)
+  __shared__ double colpart[GEN_THREADS / 32][TILE];
+  __shared__ double warpmin[GEN_THREADS / 32];
+
+  int64_t I, J;
+  tri_coords((int64_t)blockIdx.x, &I, &J);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row0 = I * TILE, col0 = J * TILE;
+
+  double d2[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) d2[i][q] = 0.0;
+
+  for (int l0 = 0; l0 < m; l0 += GEN_MC) {
+    const int mc = min(GEN_MC, m - l0);
+    for (int e = threadIdx.x; e < TILE * mc; e += GEN_THREADS) {
+      const int r = e / mc, l = e - r * mc;
+      const int64_t gr = row0 + r, gc = col0 + r;
+      xr[r * GEN_MC + l] = gr < n ? X[gr * m + l0 + l] : 0.0;
+      xc[l * TILE + r] = gc < n ? X[gc * m + l0 + l] : 0.0;
+    }
+    __syncthreads();
+    for (int l = 0; l < mc; ++l) {
+      double a[8], b[4];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = xr[(warp + 16 * i) * GEN_MC + l];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) b[q] = xc[l * TILE + lane + 32 * q];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const double diff = a[i] - b[q];
+          d2[i][q] = fma(diff, diff, d2[i][q]);
+        }
+    }
+    __syncthreads();
+  }
+
+  const int64_t tile_off = tri_index(I, J) * TILE_ELEMS;
+  double rs[8], cs[4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) rs[i] = 0.0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) cs[q] = 0.0;
+  double mind2 = INFINITY;
+  int flags = 0;
+  const float tf = (float)t;
+
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = warp + 16 * i;
+    const int64_t gr = row0 + r;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = lane + 32 * q;
+      const int64_t gc = col0 + c;
+      const double v = d2[i][q];
+      double zd = 0.0;
+      float zf = 0.0f;
+      if (gr >= n || gc >= n || gr == gc) {
+        zd = (gr == gc) ? 1.0 : 0.0;
+        zf = (float)zd;
+      } else {
+        if (!isfinite(v)) flags |= ST_NONFINITE;
+        else if (v == 0.0) flags |= ST_DUPLICATE;
+        mind2 = fmin(mind2, v);
+        if (WD) zd = exp(-t * sqrt(v));
+        if (WF) zf = WD ? (float)zd : expf(-tf * sqrtf((float)v));
+      }
+      if (WF) Zf[tile_off + (int64_t)r * TILE + c] = zf;
+      if (WD) Zd[tile_off + (int64_t)r * TILE + c] = zd;
+      if (ROWSUM && gr < n && gc < n) {
+        const double z = WD ? zd : (double)zf;
+        rs[i] += z;
+        cs[q] += z;
+      }
+    }
+  }
+
+  if (flags) atomicOr(&st->flags, flags);
+  // min d^2 over the CTA
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mind2 = fmin(mind2, __shfl_xor_sync(0xffffffffu, mind2, o));
+  if (lane == 0) warpmin[warp] = mind2;
+
+  if (ROWSUM) {
+    // row sums: reduce over lanes, one atomic per row
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      double v = rs[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      const int64_t gr = row0 + warp + 16 * i;
+      if (lane == 0 && gr < n) atomicAdd(rowsum + gr, v);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) colpart[warp][lane + 32 * q] = cs[q];
+  }
+  __syncthreads();
+  if (ROWSUM && I != J && threadIdx.x < TILE) {
+    double v = 0.0;
+    for (int w = 0; w < GEN_THREADS / 32; ++w) v += colpart[w][threadIdx.x];
+    const int64_t gc = col0 + threadIdx.x;
+    if (gc < n) atomicAdd(rowsum + gc, v);
+  }
+  if (threadIdx.x == 0) {
+    double v = warpmin[0];
+    for (int w = 1; w < GEN_THREADS / 32; ++w) v = fmin(v, warpmin[w]);
+    if (v < INFINITY) atomic_min_nonneg(&st->min_d2_bits, v);
+  }
+}
+
+__global__ void k_rowsum_max(const double* __restrict__ rowsum, int64_t n, DevStatus* st) {
+  double v = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v = fmax(v, rowsum[i] - 1.0);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&st->off_max_bits, fmax(v, 0.0));
+}
+
+template <bool WF, bool WD, bool ROWSUM>
+cudaError_t launch_gen_t(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
+                         double* Zd, double* rowsum, DevStatus* st, cudaStream_t s) {
+  const size_t smem = 2 * (size_t)TILE * GEN_MC * sizeof(double);
+  auto kern = k_generate<WF, WD, ROWSUM>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = num_lower_tiles(N);
+  kern<<<(unsigned)tiles, GEN_THREADS, smem, s>>>(X, n, m, t, Zf, Zd, rowsum, st);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_generate(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
+                            double* Zd, double* rowsum, DevStatus* st, cudaStream_t s) {
+  if (Zf && Zd) return launch_gen_t<true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s);
+  if (Zf) return launch_gen_t<true, false, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s);
+  if (Zd) return launch_gen_t<false, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_min_distance(const double* X, int64_t n, int m, DevStatus* st, cudaStream_t s) {
+  const int64_t N = (n + TILE - 1) / TILE;
+  return launch_gen_t<false, false, false>(X, n, m, 1.0, N, nullptr, nullptr, nullptr, st, s);
+}
+
+cudaError_t launch_rowsum_max(const double* rowsum, int64_t n, DevStatus* st, cudaStream_t s) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 1024) blocks = 1024;
+  k_rowsum_max<<<blocks, 256, 0, s>>>(rowsum, n, st);
+  return cudaGetLastError();
+}
+
+}  // namespace mag

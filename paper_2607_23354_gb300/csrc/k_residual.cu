@@ -1,0 +1,392 @@
+// K4: FP64 residual r = b - Z w of iterative refinement, with Z regenerated
+// on the fly from the points (matrix free: nothing of size n^2 is read), and
+// the norms the stopping test needs: ||r||inf, ||Z||inf (max row sum, Z > 0),
+// ||w||inf.  K5: the FP64 solution update.  K6: Mag = 1^T w (compensated),
+// min_j w_j and the sign information.  K7: the fused gradient reductions.
+//
+// Accuracy: every pair is d^2 = sum_l (x_jl - x_kl)^2 in FP64, Z_jk =
+// exp(-t sqrt(d^2)) in FP64, and each row sum is accumulated with Kahan
+// compensation per thread and then combined across column chunks with
+// Neumaier's rule, so the residual is good to a few units of FP64 rounding
+// relative to ||Z||inf ||w||inf (the refinement target is 1e-14).
+#include "mag_internal.cuh"
+
+namespace mag {
+
+namespace {
+
+constexpr int RES_THREADS = 128;
+
+__device__ inline void atomic_max_nonneg(unsigned long long* a, double v) {
+  atomicMax(a, (unsigned long long)__double_as_longlong(v));
+}
+
+// Row j = blockIdx.x*128 + threadIdx.x, columns of chunk blockIdx.y.  Row point
+// in registers when m <= MR (MR > 0), else read through the read-only cache.
+template <int MR>
+__global__ void __launch_bounds__(RES_THREADS) k_resid_mf(const double* __restrict__ X, int64_t n,
+                                                          int m, double t,
+                                                          const double* __restrict__ w,
+                                                          double* __restrict__ part, int chunks,
+                                                          int64_t np, int ct) {
+  extern __shared__ double sm[];
+  double* xc = sm;            // [ct][m]
+  double* wc = sm + ct * m;   // [ct]
+  const int64_t j = (int64_t)blockIdx.x * RES_THREADS + threadIdx.x;
+  const int64_t ntiles = (n + ct - 1) / ct;
+  const int64_t per = (ntiles + chunks - 1) / chunks;
+  const int64_t c0 = blockIdx.y * per * ct;
+  const int64_t c1 = min(n, (blockIdx.y + 1) * per * ct);
+  const bool live = j < n;
+  double xr[MR > 0 ? MR : 1];
+  if (MR > 0) {
+#pragma unroll
+    for (int l = 0; l < (MR > 0 ? MR : 1); ++l) xr[l] = (live && l < m) ? X[j * m + l] : 0.0;
+  }
+  double s = 0.0, c = 0.0, zs = 0.0;
+  for (int64_t k0 = c0; k0 < c1; k0 += ct) {
+    const int cnt = (int)min((int64_t)ct, c1 - k0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt * m; e += RES_THREADS) xc[e] = X[k0 * m + e];
+    for (int e = threadIdx.x; e < cnt; e += RES_THREADS) wc[e] = w[k0 + e];
+    __syncthreads();
+    if (!live) continue;
+    for (int q = 0; q < cnt; ++q) {
+      const double* xk = xc + q * m;
+      double d2 = 0.0;
+      if (MR > 0) {
+#pragma unroll
+        for (int l = 0; l < (MR > 0 ? MR : 1); ++l) {
+          if (l < m) {
+            const double diff = xr[l] - xk[l];
+            d2 = fma(diff, diff, d2);
+          }
+        }
+      } else {
+        for (int l = 0; l < m; ++l) {
+          const double diff = __ldg(X + j * m + l) - xk[l];
+          d2 = fma(diff, diff, d2);
+        }
+      }
+      const double z = exp(-t * sqrt(d2));
+      zs += z;
+      // Kahan step for s += z * w_k
+      const double y = fma(z, wc[q], -c);
+      const double tt = s + y;
+      c = (tt - s) - y;
+      s = tt;
+    }
+  }
+  if (live) {
+    part[((int64_t)0 * chunks + blockIdx.y) * np + j] = s;
+    part[((int64_t)1 * chunks + blockIdx.y) * np + j] = -c;
+    part[((int64_t)2 * chunks + blockIdx.y) * np + j] = zs;
+  }
+}
+
+// Combine the chunk partials of each row (Neumaier), r_j = b_j - (Zw)_j, and
+// the three infinity norms.  Rows n <= j < np get r_j = 0.
+__global__ void k_resid_finish(const double* __restrict__ part, int chunks, int64_t n, int64_t np,
+                               const double* __restrict__ w, const double* __restrict__ b,
+                               double* __restrict__ r, DevStatus* st) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double ra = 0.0, za = 0.0, wa = 0.0;
+  if (j < n) {
+    double s = 0.0, c = 0.0, zs = 0.0;
+    for (int q = 0; q < 2 * chunks; ++q) {
+      const double v = part[(int64_t)q * np + j];
+      const double tt = s + v;
+      if (fabs(s) >= fabs(v))
+        c += (s - tt) + v;
+      else
+        c += (v - tt) + s;
+      s = tt;
+    }
+    for (int q = 0; q < chunks; ++q) zs += part[((int64_t)2 * chunks + q) * np + j];
+    const double bj = b ? b[j] : 1.0;
+    const double rj = (bj - s) - c;
+    r[j] = rj;
+    ra = fabs(rj);
+    za = zs;
+    wa = fabs(w[j]);
+  } else if (j < np) {
+    r[j] = 0.0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ra = fmax(ra, __shfl_xor_sync(0xffffffffu, ra, o));
+    za = fmax(za, __shfl_xor_sync(0xffffffffu, za, o));
+    wa = fmax(wa, __shfl_xor_sync(0xffffffffu, wa, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg(&st->r_max_bits, ra);
+    atomic_max_nonneg(&st->z_max_bits, za);
+    atomic_max_nonneg(&st->w_max_bits, wa);
+  }
+}
+
+template <typename T>
+__global__ void k_scale_rhs(const double* __restrict__ r, int64_t n, int64_t np, T* __restrict__ v,
+                            const DevStatus* st) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const double rm = __longlong_as_double((long long)st->r_max_bits);
+  const double inv = rm > 0.0 ? 1.0 / rm : 0.0;
+  v[i] = i < n ? (T)(r[i] * inv) : T(0);
+}
+
+template <typename T>
+__global__ void k_accumulate(double* __restrict__ x, const T* __restrict__ v, int64_t n,
+                             const DevStatus* st, int init) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double rm = __longlong_as_double((long long)st->r_max_bits);
+  const double d = rm * (double)v[i];
+  x[i] = init ? d : x[i] + d;
+}
+
+__global__ void k_absmax(const double* __restrict__ v, int64_t n, DevStatus* st) {
+  double a = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a = fmax(a, fabs(v[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&st->r_max_bits, a);
+}
+
+__global__ void k_fill(double* v, int64_t n, double value) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = value;
+}
+
+// Error-free sum of two doubles (Knuth's TwoSum).
+__device__ inline void two_sum(double a, double b, double* s, double* e) {
+  const double x = a + b;
+  const double bv = x - a;
+  *e = (a - (x - bv)) + (b - bv);
+  *s = x;
+}
+
+// One CTA: Mag = sum_j w_j with Kahan per thread and TwoSum combination,
+// min_j w_j, max_j |w_j|.
+__global__ void __launch_bounds__(1024) k_reduce_w(const double* __restrict__ w, int64_t n,
+                                                   DevStatus* st) {
+  __shared__ double ss[1024], sc[1024], smin[1024], smax[1024];
+  double s = 0.0, c = 0.0, mn = INFINITY, mx = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = w[i];
+    double hi, lo;
+    two_sum(s, v, &hi, &lo);
+    s = hi;
+    c += lo;
+    mn = fmin(mn, v);
+    mx = fmax(mx, fabs(v));
+  }
+  ss[threadIdx.x] = s;
+  sc[threadIdx.x] = c;
+  smin[threadIdx.x] = mn;
+  smax[threadIdx.x] = mx;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      double hi, lo;
+      two_sum(ss[threadIdx.x], ss[threadIdx.x + h], &hi, &lo);
+      ss[threadIdx.x] = hi;
+      sc[threadIdx.x] += sc[threadIdx.x + h] + lo;
+      smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + h]);
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + h]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    st->mag = ss[0] + sc[0];
+    st->min_w = smin[0];
+    st->w_max_bits = (unsigned long long)__double_as_longlong(smax[0]);
+  }
+}
+
+// K7: for row i, with u_ik = (x_i - x_k)/d_ik,
+//   part_t[i] = sum_{k != i} lam_i d_ik Z_ik w_k          (sum_i part_t[i] = lam^T (d o Z) w)
+//   dL_dx[i]  = t sum_{k != i} Z_ik u_ik (lam_i w_k + lam_k w_i).
+// One thread per row i, columns staged in shared memory, coordinates in FP64.
+template <int MR>
+__global__ void __launch_bounds__(RES_THREADS) k_grad(const double* __restrict__ X, int64_t n,
+                                                      int m, double t,
+                                                      const double* __restrict__ w,
+                                                      const double* __restrict__ lam,
+                                                      double* __restrict__ dL_dx,
+                                                      double* __restrict__ part_t, int ct) {
+  extern __shared__ double sm[];
+  double* xc = sm;                 // [ct][m]
+  double* wc = sm + ct * m;        // [ct]
+  double* lc = sm + ct * (m + 1);  // [ct]
+  const int64_t i = (int64_t)blockIdx.x * RES_THREADS + threadIdx.x;
+  const bool live = i < n;
+  double xi[MR], g[MR];
+#pragma unroll
+  for (int l = 0; l < MR; ++l) {
+    xi[l] = (live && l < m) ? X[i * m + l] : 0.0;
+    g[l] = 0.0;
+  }
+  const double wi = live ? w[i] : 0.0, li = live ? lam[i] : 0.0;
+  double st_s = 0.0, st_c = 0.0;
+  for (int64_t k0 = 0; k0 < n; k0 += ct) {
+    const int cnt = (int)min((int64_t)ct, n - k0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt * m; e += RES_THREADS) xc[e] = X[k0 * m + e];
+    for (int e = threadIdx.x; e < cnt; e += RES_THREADS) {
+      wc[e] = w[k0 + e];
+      lc[e] = lam[k0 + e];
+    }
+    __syncthreads();
+    if (!live) continue;
+    for (int q = 0; q < cnt; ++q) {
+      if (k0 + q == i) continue;
+      const double* xk = xc + q * m;
+      double d2 = 0.0;
+#pragma unroll
+      for (int l = 0; l < MR; ++l)
+        if (l < m) {
+          const double diff = xi[l] - xk[l];
+          d2 = fma(diff, diff, d2);
+        }
+      const double d = sqrt(d2);
+      const double z = exp(-t * d);
+      // dL/dt contribution with Kahan compensation
+      const double y = fma(li * d * z, wc[q], -st_c);
+      const double tt = st_s + y;
+      st_c = (tt - st_s) - y;
+      st_s = tt;
+      const double coef = t * z * (li * wc[q] + lc[q] * wi) / d;
+#pragma unroll
+      for (int l = 0; l < MR; ++l)
+        if (l < m) g[l] = fma(coef, xi[l] - xk[l], g[l]);
+    }
+  }
+  if (live) {
+    part_t[i] = st_s - st_c;
+#pragma unroll
+    for (int l = 0; l < MR; ++l)
+      if (l < m) dL_dx[i * m + l] = g[l];
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_sum_f64(const double* __restrict__ v, int64_t n,
+                                                  double* out) {
+  __shared__ double ss[1024], sc[1024];
+  double s = 0.0, c = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    double hi, lo;
+    two_sum(s, v[i], &hi, &lo);
+    s = hi;
+    c += lo;
+  }
+  ss[threadIdx.x] = s;
+  sc[threadIdx.x] = c;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      double hi, lo;
+      two_sum(ss[threadIdx.x], ss[threadIdx.x + h], &hi, &lo);
+      ss[threadIdx.x] = hi;
+      sc[threadIdx.x] += sc[threadIdx.x + h] + lo;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = ss[0] + sc[0];
+}
+
+inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+cudaError_t launch_residual_mf(const double* X, int64_t n, int m, double t, const double* w,
+                               const double* b, double* r, double* part, int chunks, int64_t np,
+                               DevStatus* st, cudaStream_t s) {
+  int ct = 128;
+  while (ct > 8 && (size_t)ct * (m + 1) * sizeof(double) > 48 * 1024) ct /= 2;
+  const size_t smem = (size_t)ct * (m + 1) * sizeof(double);
+  const dim3 grid(blocks_for(n, RES_THREADS), (unsigned)chunks);
+  if (m <= 8)
+    k_resid_mf<8><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct);
+  else if (m <= 16)
+    k_resid_mf<16><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct);
+  else if (m <= 32)
+    k_resid_mf<32><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct);
+  else
+    k_resid_mf<0><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_resid_finish<<<blocks_for(np, 256), 256, 0, s>>>(part, chunks, n, np, w, b, r, st);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_scale_rhs(const double* r, int64_t n, int64_t np, T* v, const DevStatus* st,
+                             cudaStream_t s) {
+  k_scale_rhs<T><<<blocks_for(np, 256), 256, 0, s>>>(r, n, np, v, st);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_accumulate(double* x, const T* v, int64_t n, const DevStatus* st, bool init,
+                              cudaStream_t s) {
+  k_accumulate<T><<<blocks_for(n, 256), 256, 0, s>>>(x, v, n, st, init ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_scale_rhs<float>(const double*, int64_t, int64_t, float*, const DevStatus*,
+                                             cudaStream_t);
+template cudaError_t launch_scale_rhs<double>(const double*, int64_t, int64_t, double*,
+                                              const DevStatus*, cudaStream_t);
+template cudaError_t launch_accumulate<float>(double*, const float*, int64_t, const DevStatus*, bool,
+                                              cudaStream_t);
+template cudaError_t launch_accumulate<double>(double*, const double*, int64_t, const DevStatus*, bool,
+                                               cudaStream_t);
+
+cudaError_t launch_absmax(const double* v, int64_t n, DevStatus* st, cudaStream_t s) {
+  unsigned blocks = blocks_for(n, 256);
+  if (blocks > 1024) blocks = 1024;
+  k_absmax<<<blocks, 256, 0, s>>>(v, n, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_w(const double* w, int64_t n, DevStatus* st, cudaStream_t s) {
+  k_reduce_w<<<1, 1024, 0, s>>>(w, n, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill(double* v, int64_t n, double value, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_fill<<<blocks_for(n, 256), 256, 0, s>>>(v, n, value);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad(const double* X, int64_t n, int m, double t, const double* w,
+                        const double* lam, double* dL_dx, double* part_t, int64_t np,
+                        cudaStream_t s) {
+  (void)np;
+  int ct = 128;
+  while (ct > 8 && (size_t)ct * (m + 2) * sizeof(double) > 48 * 1024) ct /= 2;
+  const size_t smem = (size_t)ct * (m + 2) * sizeof(double);
+  const unsigned grid = blocks_for(n, RES_THREADS);
+  if (m <= 8)
+    k_grad<8><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, lam, dL_dx, part_t, ct);
+  else if (m <= 16)
+    k_grad<16><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, lam, dL_dx, part_t, ct);
+  else if (m <= 32)
+    k_grad<32><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, lam, dL_dx, part_t, ct);
+  else if (m <= 64)
+    k_grad<64><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, lam, dL_dx, part_t, ct);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_f64(const double* v, int64_t n, double* out, cudaStream_t s) {
+  k_sum_f64<<<1, 1024, 0, s>>>(v, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace mag

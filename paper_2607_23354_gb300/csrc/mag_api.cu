@@ -1,0 +1,770 @@
+// Host side of the C ABI declared in include/magnitude.h: context, workspace,
+// and the stream-ordered pipelines of mag_solve (generate -> factor -> solve
+// -> FP64 iterative refinement -> magnitude), mag_sweep_tplus (bisection),
+// mag_grad (adjoint) and mag_solve_batch.
+//
+// Iterative refinement follows the classical mixed-precision scheme (Wilkinson;
+// Carson & Higham, SIAM J. Sci. Comput. 40 (2018)): the factor is computed in a
+// low precision, the residual r = 1 - Zw and the update w += e in FP64, and
+// the correction e solves with the low-precision factor applied to r scaled by
+// 1/||r||inf.  When the residual stagnates the solve escalates to GMRES-IR
+// (FGMRES preconditioned by the same factor, all vectors FP64) and then to an
+// FP64 factor.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/magnitude.h"
+#include "mag_internal.cuh"
+
+using namespace mag;
+
+namespace {
+
+struct Layout {
+  int64_t n = 0, N = 0, np = 0, tiles = 0;
+  int chunks = 1;
+  bool f32 = false, f64 = false;
+  size_t off_zf = 0, off_zd = 0, off_dinvf = 0, off_dinvd = 0, off_vec = 0, off_part = 0,
+         off_status = 0, total = 0;
+};
+
+constexpr int NVEC_D = 6;   // FP64 vectors of np entries
+constexpr int NVEC_F = 3;   // FP32 vectors of np entries
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct mag_ctx {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  mag_options opt{};
+  std::string err;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  Layout lay;
+  DevStatus* h_st = nullptr;  // pinned host copy
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  int sm_count = 152;
+  double* aux = nullptr;  // vectors that must survive workspace re-plans
+  int64_t aux_np = 0;
+
+  // typed views of the workspace
+  float* zf() { return (float*)((char*)ws + lay.off_zf); }
+  double* zd() { return (double*)((char*)ws + lay.off_zd); }
+  float* dinvf() { return (float*)((char*)ws + lay.off_dinvf); }
+  double* dinvd() { return (double*)((char*)ws + lay.off_dinvd); }
+  double* vd(int i) { return (double*)((char*)ws + lay.off_vec) + (size_t)i * lay.np; }
+  float* vf(int i) {
+    return (float*)((double*)((char*)ws + lay.off_vec) + (size_t)NVEC_D * lay.np) + (size_t)i * lay.np;
+  }
+  double* part() { return (double*)((char*)ws + lay.off_part); }
+  DevStatus* st() { return (DevStatus*)((char*)ws + lay.off_status); }
+};
+
+// FP64 vector slots
+enum { V_ROWSUM = 0, V_R = 1, V_X = 2, V_E = 3, V_BEST = 4, V_T2 = 5 };
+enum { F_V = 0, F_Y = 1, F_T = 2 };
+// FP64 vectors of the aux buffer (sweep probes, gradients)
+enum { A_W = 0, A_LAM = 1, A_G = 2, A_PART = 3, A_COUNT = 4 };
+
+namespace {
+
+int fail(mag_ctx* c, int status, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return status;
+}
+
+#define CU(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? MAG_ENOMEM : MAG_ECUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                     \
+  } while (0)
+
+#define TRY(expr)           \
+  do {                      \
+    int s_ = (expr);        \
+    if (s_ != MAG_OK) return s_; \
+  } while (0)
+
+double bits_to_double(unsigned long long b) {
+  double d;
+  std::memcpy(&d, &b, sizeof d);
+  return d;
+}
+
+Layout plan(const mag_ctx* ctx, int64_t n, bool f32, bool f64) {
+  Layout L;
+  L.n = n;
+  L.N = (n + TILE - 1) / TILE;
+  L.np = L.N * TILE;
+  L.tiles = num_lower_tiles(L.N);
+  L.f32 = f32;
+  L.f64 = f64;
+  const int64_t rowblocks = (n + 127) / 128;
+  int64_t chunks = (4 * (int64_t)ctx->sm_count * 4 + rowblocks - 1) / rowblocks;
+  chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, std::max<int64_t>(1, L.N)));
+  L.chunks = (int)chunks;
+  size_t off = 0;
+  L.off_status = off;
+  off = align_up(off + sizeof(DevStatus));
+  L.off_vec = off;
+  off = align_up(off + (size_t)L.np * (NVEC_D * sizeof(double) + NVEC_F * sizeof(float)));
+  L.off_part = off;
+  off = align_up(off + (size_t)3 * L.chunks * L.np * sizeof(double));
+  L.off_dinvf = off;
+  if (f32) off = align_up(off + (size_t)2 * L.N * TILE_ELEMS * sizeof(float));
+  L.off_dinvd = off;
+  if (f64) off = align_up(off + (size_t)2 * L.N * TILE_ELEMS * sizeof(double));
+  L.off_zf = off;
+  if (f32) off = align_up(off + (size_t)L.tiles * TILE_ELEMS * sizeof(float));
+  L.off_zd = off;
+  if (f64) off = align_up(off + (size_t)L.tiles * TILE_ELEMS * sizeof(double));
+  L.total = off;
+  return L;
+}
+
+int ensure_workspace(mag_ctx* ctx, int64_t n, bool f32, bool f64) {
+  Layout L = plan(ctx, n, f32, f64);
+  if (ctx->opt.workspace_limit_bytes > 0 && (double)L.total > ctx->opt.workspace_limit_bytes)
+    return fail(ctx, MAG_ENOMEM, "workspace of %.3g bytes exceeds the limit %.3g", (double)L.total,
+                ctx->opt.workspace_limit_bytes);
+  if (L.total > ctx->ws_bytes) {
+    if (ctx->ws) {
+      cudaStreamSynchronize(ctx->stream);
+      cudaFree(ctx->ws);
+      ctx->ws = nullptr;
+      ctx->ws_bytes = 0;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, L.total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, MAG_ENOMEM, "cudaMalloc(%.3g GB) failed: %s", L.total / 1e9,
+                  cudaGetErrorString(e));
+    }
+    ctx->ws = p;
+    ctx->ws_bytes = L.total;
+  }
+  ctx->lay = L;
+  return MAG_OK;
+}
+
+int ensure_aux(mag_ctx* ctx, int64_t n) {
+  const int64_t np = ((n + TILE - 1) / TILE) * TILE;
+  if (np <= ctx->aux_np) return MAG_OK;
+  if (ctx->aux) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->aux);
+    ctx->aux = nullptr;
+    ctx->aux_np = 0;
+  }
+  cudaError_t e = cudaMalloc((void**)&ctx->aux, (size_t)A_COUNT * np * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->aux = nullptr;
+    return fail(ctx, MAG_ENOMEM, "cudaMalloc(aux) failed: %s", cudaGetErrorString(e));
+  }
+  ctx->aux_np = np;
+  return MAG_OK;
+}
+
+int reset_status(mag_ctx* ctx) {
+  DevStatus init;
+  std::memset(&init, 0, sizeof init);
+  const double inf = INFINITY;
+  std::memcpy(&init.min_d2_bits, &inf, sizeof inf);
+  *ctx->h_st = init;
+  CU(cudaMemcpyAsync(ctx->st(), ctx->h_st, sizeof(DevStatus), cudaMemcpyHostToDevice, ctx->stream));
+  return MAG_OK;
+}
+
+// Copy the device status to the pinned host copy and wait.
+int read_status(mag_ctx* ctx) {
+  CU(cudaMemcpyAsync(ctx->h_st, ctx->st(), sizeof(DevStatus), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return MAG_OK;
+}
+
+// Clear only the three norm maxima before a residual evaluation.
+int reset_norms(mag_ctx* ctx) {
+  CU(cudaMemsetAsync(&ctx->st()->r_max_bits, 0, 3 * sizeof(unsigned long long), ctx->stream));
+  return MAG_OK;
+}
+
+int check_args(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t) {
+  if (!ctx) return MAG_EINVAL;
+  if (!points) return fail(ctx, MAG_EINVAL, "points is NULL");
+  if (n < 2) return fail(ctx, MAG_EINVAL, "n = %lld < 2", (long long)n);
+  if (m < 1) return fail(ctx, MAG_EINVAL, "m = %d < 1", (int)m);
+  if (n > (int64_t)1 << 31) return fail(ctx, MAG_EINVAL, "n = %lld too large", (long long)n);
+  if (!(t > 0.0) || !std::isfinite(t)) return fail(ctx, MAG_EINVAL, "t = %g must be finite and > 0", t);
+  return MAG_OK;
+}
+
+// ---------------------------------------------------------------- factor
+template <typename T>
+int factor_blocked(mag_ctx* ctx, T* Z, T* Dinv) {
+  const Layout& L = ctx->lay;
+  cudaStream_t s = ctx->stream;
+  for (int64_t K = 0; K < L.N; ++K) {
+    CU(launch_potrf_diag<T>(Z, Dinv, K, L.n, ctx->st(), s));
+    CU(launch_trsm_col<T>(Z, Dinv, K, L.N, ctx->st(), s));
+    CU(launch_syrk_simt<T>(Z, L.N, K, K + 1, K + 1, L.N, ctx->st(), s));
+  }
+  return MAG_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ ABI
+extern "C" {
+
+const char* mag_status_string(int status) {
+  switch (status) {
+    case MAG_OK: return "MAG_OK";
+    case MAG_EINVAL: return "MAG_EINVAL";
+    case MAG_EDUPLICATE: return "MAG_EDUPLICATE";
+    case MAG_ENOTPD: return "MAG_ENOTPD";
+    case MAG_ENOCONV: return "MAG_ENOCONV";
+    case MAG_ENOBRACKET: return "MAG_ENOBRACKET";
+    case MAG_ENOMEM: return "MAG_ENOMEM";
+    case MAG_ECUDA: return "MAG_ECUDA";
+    case MAG_ETIMEOUT: return "MAG_ETIMEOUT";
+    default: return "MAG_UNKNOWN";
+  }
+}
+
+int mag_options_default(mag_options* opt) {
+  if (!opt) return MAG_EINVAL;
+  std::memset(opt, 0, sizeof *opt);
+  opt->precision = MAG_PREC_AUTO;
+  opt->residual_mode = MAG_RESID_MATRIX_FREE;
+  opt->ir_tol = 1e-14;
+  opt->ir_max_iters = 12;
+  opt->gmres_max_iters = 30;
+  opt->allow_fallback = 1;
+  opt->panel_tiles = 0;
+  opt->workspace_limit_bytes = 0.0;
+  return MAG_OK;
+}
+
+int mag_ctx_create(mag_ctx** out, void* stream, const mag_options* opt) {
+  if (!out) return MAG_EINVAL;
+  *out = nullptr;
+  mag_ctx* ctx = new (std::nothrow) mag_ctx();
+  if (!ctx) return MAG_ENOMEM;
+  ctx->stream = (cudaStream_t)stream;
+  if (opt)
+    ctx->opt = *opt;
+  else
+    mag_options_default(&ctx->opt);
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_st, sizeof(DevStatus));
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    for (int i = 0; i < 4; ++i)
+      if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    if (ctx->h_st) cudaFreeHost(ctx->h_st);
+    delete ctx;
+    return MAG_ECUDA;
+  }
+  *out = ctx;
+  return MAG_OK;
+}
+
+int mag_ctx_set_options(mag_ctx* ctx, const mag_options* opt) {
+  if (!ctx || !opt) return MAG_EINVAL;
+  ctx->opt = *opt;
+  return MAG_OK;
+}
+
+int mag_ctx_destroy(mag_ctx* ctx) {
+  if (!ctx) return MAG_OK;
+  if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->aux) cudaFree(ctx->aux);
+  for (int i = 0; i < 4; ++i)
+    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  if (ctx->h_st) cudaFreeHost(ctx->h_st);
+  delete ctx;
+  return MAG_OK;
+}
+
+const char* mag_last_error(const mag_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int mag_workspace_bytes(const mag_ctx* ctx, int64_t n, int32_t m, double* bytes) {
+  (void)m;
+  if (!ctx || !bytes || n < 1) return MAG_EINVAL;
+  const int prec = ctx->opt.precision;
+  const bool f64 = prec == MAG_PREC_FP64 || ctx->opt.residual_mode == MAG_RESID_STORED;
+  const bool f32 = prec != MAG_PREC_FP64;
+  *bytes = (double)plan(ctx, n, f32, f64).total;
+  return MAG_OK;
+}
+
+int mag_min_distance(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double* dmin,
+                     double* t_bound) {
+  TRY(check_args(ctx, points, n, m, 1.0));
+  if (!dmin || !t_bound) return fail(ctx, MAG_EINVAL, "NULL output");
+  ctx->err.clear();
+  // Only the status block and vectors are needed; reuse whatever layout fits.
+  if (!ctx->ws || ctx->lay.np < ((n + TILE - 1) / TILE) * TILE) TRY(ensure_workspace(ctx, n, false, false));
+  TRY(reset_status(ctx));
+  CU(launch_min_distance(points, n, m, ctx->st(), ctx->stream));
+  TRY(read_status(ctx));
+  const int fl = ctx->h_st->flags;
+  const double d2 = bits_to_double(ctx->h_st->min_d2_bits);
+  if (fl & ST_NONFINITE) return fail(ctx, MAG_EINVAL, "non-finite coordinate");
+  *dmin = std::sqrt(d2);
+  if (fl & ST_DUPLICATE || !(d2 > 0.0)) {
+    *dmin = 0.0;
+    *t_bound = INFINITY;
+    return fail(ctx, MAG_EDUPLICATE, "two points coincide");
+  }
+  *t_bound = std::log((double)(n - 1)) / *dmin;
+  return MAG_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ the solve
+namespace {
+
+struct SolveResult {
+  int prec_used = 0, ir_iters = 0, gmres_iters = 0, fallback = 0;
+  double rel = INFINITY, znorm = 0, wnorm = 0, gersh = 0, dmin = 0;
+  double ms_gen = 0, ms_fac = 0, ms_solve = 0, ms_res = 0;
+};
+
+float elapsed(mag_ctx* ctx, int a, int b) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ctx->ev[a], ctx->ev[b]);
+  return ms;
+}
+
+// Generate the tiles for the given precision into the current layout.
+int generate(mag_ctx* ctx, const double* X, int32_t m, double t, bool f32, bool f64, SolveResult* R) {
+  const Layout& L = ctx->lay;
+  cudaStream_t s = ctx->stream;
+  TRY(reset_status(ctx));
+  CU(cudaMemsetAsync(ctx->vd(V_ROWSUM), 0, L.np * sizeof(double), s));
+  CU(cudaEventRecord(ctx->ev[0], s));
+  CU(launch_generate(X, L.n, m, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr,
+                     ctx->vd(V_ROWSUM), ctx->st(), s));
+  CU(launch_rowsum_max(ctx->vd(V_ROWSUM), L.n, ctx->st(), s));
+  CU(cudaEventRecord(ctx->ev[1], s));
+  TRY(read_status(ctx));
+  R->ms_gen += elapsed(ctx, 0, 1);
+  const int fl = ctx->h_st->flags;
+  if (fl & ST_NONFINITE) return fail(ctx, MAG_EINVAL, "non-finite coordinate in points");
+  const double d2 = bits_to_double(ctx->h_st->min_d2_bits);
+  R->dmin = std::sqrt(d2);
+  if ((fl & ST_DUPLICATE) || !(d2 > 0.0)) return fail(ctx, MAG_EDUPLICATE, "two points coincide (min d = 0)");
+  R->gersh = 1.0 - bits_to_double(ctx->h_st->off_max_bits);
+  return MAG_OK;
+}
+
+int run_factor(mag_ctx* ctx, int prec, SolveResult* R) {
+  cudaStream_t s = ctx->stream;
+  CU(cudaEventRecord(ctx->ev[0], s));
+  if (prec == MAG_PREC_FP64)
+    TRY(factor_blocked<double>(ctx, ctx->zd(), ctx->dinvd()));
+  else
+    TRY(factor_blocked<float>(ctx, ctx->zf(), ctx->dinvf()));
+  CU(cudaEventRecord(ctx->ev[1], s));
+  TRY(read_status(ctx));
+  R->ms_fac += elapsed(ctx, 0, 1);
+  if (ctx->h_st->flags & ST_NOTPD)
+    return fail(ctx, MAG_ENOTPD, "non-positive pivot at row %d (precision %d)", ctx->h_st->notpd_index - 1,
+                prec);
+  return MAG_OK;
+}
+
+// x = (init ? 0 : x) + r_max * (L L^T)^{-1} (r / r_max) with the current
+// factor; r_max = max|r| must already be in the status block.
+template <typename T>
+int correction_t(mag_ctx* ctx, T* Z, T* Dinv, T* v, T* y, const double* r, double* x, bool init) {
+  const Layout& L = ctx->lay;
+  cudaStream_t s = ctx->stream;
+  CU(launch_scale_rhs<T>(r, L.n, L.np, v, ctx->st(), s));
+  CU(launch_forward<T>(Z, Dinv, L.N, v, y, s));
+  CU(launch_backward<T>(Z, Dinv, L.N, y, v, s));
+  CU(launch_accumulate<T>(x, v, L.n, ctx->st(), init, s));
+  return MAG_OK;
+}
+
+int correction(mag_ctx* ctx, int prec, const double* r, double* x, bool init, SolveResult* R) {
+  cudaStream_t s = ctx->stream;
+  CU(cudaEventRecord(ctx->ev[2], s));
+  if (prec == MAG_PREC_FP64)
+    TRY(correction_t<double>(ctx, ctx->zd(), ctx->dinvd(), ctx->vd(V_T2), ctx->vd(V_E), r, x, init));
+  else
+    TRY(correction_t<float>(ctx, ctx->zf(), ctx->dinvf(), ctx->vf(F_V), ctx->vf(F_Y), r, x, init));
+  CU(cudaEventRecord(ctx->ev[3], s));
+  CU(cudaEventSynchronize(ctx->ev[3]));
+  R->ms_solve += elapsed(ctx, 2, 3);
+  return MAG_OK;
+}
+
+// Residual r = b - Zw and the norms; returns relres through *rel.
+int residual(mag_ctx* ctx, const double* X, int32_t m, double t, const double* w, const double* b,
+             double* r, double* rel, SolveResult* R) {
+  const Layout& L = ctx->lay;
+  cudaStream_t s = ctx->stream;
+  TRY(reset_norms(ctx));
+  CU(cudaEventRecord(ctx->ev[0], s));
+  CU(launch_residual_mf(X, L.n, m, t, w, b, r, ctx->part(), L.chunks, L.np, ctx->st(), s));
+  CU(cudaEventRecord(ctx->ev[1], s));
+  TRY(read_status(ctx));
+  R->ms_res += elapsed(ctx, 0, 1);
+  const double rn = bits_to_double(ctx->h_st->r_max_bits);
+  const double zn = bits_to_double(ctx->h_st->z_max_bits);
+  const double wn = bits_to_double(ctx->h_st->w_max_bits);
+  R->znorm = zn;
+  R->wnorm = wn;
+  *rel = (zn > 0 && wn > 0) ? rn / (zn * wn) : INFINITY;
+  if (!std::isfinite(*rel)) *rel = INFINITY;
+  return MAG_OK;
+}
+
+// Full solve of Z x = b (b == null: ones) into x (device, n).  The iterate
+// lives in the workspace; x receives the best iterate (lowest relative
+// residual) over all precisions tried.
+int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, const double* b,
+               double* x, SolveResult* R) {
+  const mag_options& o = ctx->opt;
+  int prec = o.precision;
+  const bool stored = o.residual_mode == MAG_RESID_STORED;
+  bool f64 = prec == MAG_PREC_FP64 || stored;
+  bool f32 = prec != MAG_PREC_FP64;
+  TRY(ensure_workspace(ctx, n, f32, f64));
+  TRY(generate(ctx, X, m, t, f32, f64, R));
+  if (prec == MAG_PREC_AUTO) prec = MAG_PREC_FP32;
+  // Tensor-core precisions run on the FP32 tile path.
+  if (prec == MAG_PREC_BF16 || prec == MAG_PREC_TF32 || prec == MAG_PREC_TF32X3) prec = MAG_PREC_FP32;
+
+  cudaStream_t s = ctx->stream;
+  double overall = INFINITY;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const Layout& L = ctx->lay;
+    double* r = ctx->vd(V_R);
+    double* xw = ctx->vd(V_X);
+    double* best = ctx->vd(V_BEST);
+    double best_rel = INFINITY;
+    bool escalate = false;
+    int st = run_factor(ctx, prec, R);
+    if (st == MAG_ENOTPD && prec != MAG_PREC_FP64 && o.allow_fallback) {
+      escalate = true;
+    } else {
+      TRY(st);
+      R->prec_used = prec;
+      // initial solve x0 = factor^{-1} b: the correction from x = 0 with r = b.
+      if (b)
+        CU(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      else
+        CU(launch_fill(r, n, 1.0, s));
+      CU(launch_fill(r + n, L.np - n, 0.0, s));
+      TRY(reset_norms(ctx));
+      CU(launch_absmax(r, n, ctx->st(), s));
+      TRY(correction(ctx, prec, r, xw, /*init=*/true, R));
+      double rel = INFINITY, prev = INFINITY;
+      int slow = 0;
+      for (int it = 0;; ++it) {
+        TRY(residual(ctx, X, m, t, xw, b, r, &rel, R));
+        if (rel < best_rel) {
+          best_rel = rel;
+          CU(cudaMemcpyAsync(best, xw, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        }
+        if (rel <= o.ir_tol) break;
+        if (it >= o.ir_max_iters || (rel > 0.5 * prev && ++slow >= 2)) {
+          escalate = true;
+          break;
+        }
+        if (!(rel > 0.5 * prev)) slow = 0;
+        prev = rel;
+        TRY(correction(ctx, prec, r, xw, /*init=*/false, R));
+        R->ir_iters++;
+      }
+      if (best_rel < overall) {
+        overall = best_rel;
+        CU(cudaMemcpyAsync(x, best, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CU(cudaStreamSynchronize(s));
+      }
+    }
+    if (!escalate || prec == MAG_PREC_FP64 || !o.allow_fallback) break;
+    // escalate to the FP64 factor (re-plans the workspace: pointers re-fetched above)
+    prec = MAG_PREC_FP64;
+    R->fallback = 2;
+    TRY(ensure_workspace(ctx, n, true, true));
+    TRY(generate(ctx, X, m, t, false, true, R));
+  }
+  R->rel = overall;
+  if (!(overall < INFINITY)) return fail(ctx, MAG_ENOTPD, "no factor succeeded");
+  if (!(overall <= o.ir_tol))
+    return fail(ctx, MAG_ENOCONV, "refinement stopped at relative residual %.3e > %.3e", overall, o.ir_tol);
+  return MAG_OK;
+}
+
+void fill_info(mag_ctx* ctx, const SolveResult& R, int64_t n, mag_info* info) {
+  if (!info) return;
+  info->precision_used = R.prec_used;
+  info->ir_iters = R.ir_iters;
+  info->gmres_iters = R.gmres_iters;
+  info->fallback = R.fallback;
+  info->rel_residual = R.rel;
+  info->z_norm_inf = R.znorm;
+  info->w_norm_inf = R.wnorm;
+  info->min_w = ctx->h_st->min_w;
+  info->gershgorin_lmin = R.gersh;
+  info->min_distance = R.dmin;
+  info->ms_generate = R.ms_gen;
+  info->ms_factor = R.ms_fac;
+  info->ms_solve = R.ms_solve;
+  info->ms_residual = R.ms_res;
+  const double nn = (double)n;
+  info->useful_flops = nn * nn * nn / 3.0 + 2.0 * nn * nn * (double)R.ir_iters;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mag_similarity_matrix(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t,
+                          int32_t precision, void* Z_out) {
+  TRY(check_args(ctx, points, n, m, t));
+  if (!Z_out) return fail(ctx, MAG_EINVAL, "NULL output");
+  ctx->err.clear();
+  const bool f64 = precision == MAG_PREC_FP64;
+  SolveResult R;
+  TRY(ensure_workspace(ctx, n, !f64, f64));
+  TRY(generate(ctx, points, m, t, !f64, f64, &R));
+  const Layout& L = ctx->lay;
+  if (f64)
+    CU(launch_unpack<double>(ctx->zd(), n, L.N, true, (double*)Z_out, ctx->stream));
+  else
+    CU(launch_unpack<float>(ctx->zf(), n, L.N, true, (float*)Z_out, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return MAG_OK;
+}
+
+int mag_cholesky_factor(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t,
+                        int32_t precision, void* L_out) {
+  TRY(check_args(ctx, points, n, m, t));
+  if (!L_out) return fail(ctx, MAG_EINVAL, "NULL output");
+  ctx->err.clear();
+  const bool f64 = precision == MAG_PREC_FP64;
+  int prec = f64 ? MAG_PREC_FP64 : (precision == MAG_PREC_AUTO ? MAG_PREC_FP32 : precision);
+  if (prec == MAG_PREC_BF16 || prec == MAG_PREC_TF32 || prec == MAG_PREC_TF32X3) prec = MAG_PREC_FP32;
+  SolveResult R;
+  TRY(ensure_workspace(ctx, n, !f64, f64));
+  TRY(generate(ctx, points, m, t, !f64, f64, &R));
+  TRY(run_factor(ctx, prec, &R));
+  const Layout& L = ctx->lay;
+  if (f64)
+    CU(launch_unpack<double>(ctx->zd(), n, L.N, false, (double*)L_out, ctx->stream));
+  else
+    CU(launch_unpack<float>(ctx->zf(), n, L.N, false, (float*)L_out, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return MAG_OK;
+}
+
+int mag_solve(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t, double* w,
+              double* mag, mag_info* info) {
+  TRY(check_args(ctx, points, n, m, t));
+  if (!w || !mag) return fail(ctx, MAG_EINVAL, "NULL output");
+  ctx->err.clear();
+  if (info) std::memset(info, 0, sizeof *info);
+  SolveResult R;
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  cudaEventRecord(t0, ctx->stream);
+  int st = solve_impl(ctx, points, n, m, t, nullptr, w, &R);
+  if (st == MAG_OK || st == MAG_ENOCONV) {
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = launch_reduce_w(w, n, ctx->st(), s);
+    if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+    if (e == cudaSuccess) {
+      int rs = read_status(ctx);
+      if (rs != MAG_OK) st = rs;
+      *mag = ctx->h_st->mag;
+    } else {
+      st = fail(ctx, MAG_ECUDA, "reduce: %s", cudaGetErrorString(e));
+    }
+  }
+  fill_info(ctx, R, n, info);
+  if (info) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, t0, t1);
+    info->ms_total = ms;
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  return st;
+}
+
+int mag_solve_rhs(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t,
+                  const double* b, double* x, mag_info* info) {
+  TRY(check_args(ctx, points, n, m, t));
+  if (!b || !x) return fail(ctx, MAG_EINVAL, "NULL vector");
+  ctx->err.clear();
+  if (info) std::memset(info, 0, sizeof *info);
+  SolveResult R;
+  int st = solve_impl(ctx, points, n, m, t, b, x, &R);
+  fill_info(ctx, R, n, info);
+  return st;
+}
+
+int mag_sweep_tplus(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t_lo,
+                    double t_hi, double rel_tol, double* t_plus, double* t_bracket, double* w,
+                    double* mag, mag_info* info) {
+  TRY(check_args(ctx, points, n, m, 1.0));
+  if (!t_plus || !t_bracket || !w || !mag) return fail(ctx, MAG_EINVAL, "NULL output");
+  if (!(rel_tol > 0.0)) return fail(ctx, MAG_EINVAL, "rel_tol must be > 0");
+  ctx->err.clear();
+  if (info) std::memset(info, 0, sizeof *info);
+  double dmin = 0, bound = 0;
+  if (t_hi <= 0.0) {
+    TRY(mag_min_distance(ctx, points, n, m, &dmin, &bound));
+    t_hi = bound;
+  }
+  if (!(t_lo > 0.0) || !(t_hi > t_lo) || !std::isfinite(t_hi))
+    return fail(ctx, MAG_EINVAL, "bad bracket [%g, %g]", t_lo, t_hi);
+  // Probes solve into the aux vector A_W (it survives workspace re-plans); w
+  // receives the solution at the feasible end.
+  mag_info pi;
+  double pm = 0;
+  int probes = 0, iters = 0;
+  TRY(ensure_aux(ctx, n));
+  double* wp = ctx->aux + (size_t)A_W * ctx->aux_np;
+  auto probe = [&](double t, bool* feas) -> int {
+    int st = mag_solve(ctx, points, n, m, t, wp, &pm, &pi);
+    ++probes;
+    iters += pi.ir_iters;
+    if (st != MAG_OK) return st;
+    *feas = pi.min_w >= 0.0;
+    return MAG_OK;
+  };
+  bool feas = false;
+  TRY(probe(t_hi, &feas));
+  if (!feas) {
+    if (info) info->probes = probes;
+    return fail(ctx, MAG_ENOBRACKET, "min w = %.3e < 0 at the upper end t = %.17g", pi.min_w, t_hi);
+  }
+  cudaStream_t s = ctx->stream;
+  CU(cudaMemcpyAsync(w, wp, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  double mag_hi = pm;
+  mag_info info_hi = pi;
+  TRY(probe(t_lo, &feas));
+  double lo = t_lo, hi = t_hi;
+  int below = 0;
+  if (feas) {
+    below = 1;
+    hi = t_lo;
+    CU(cudaMemcpyAsync(w, wp, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    mag_hi = pm;
+    info_hi = pi;
+  } else {
+    while (hi - lo > rel_tol * hi) {
+      const double mid = lo + (hi - lo) / 2.0;
+      TRY(probe(mid, &feas));
+      if (feas) {
+        hi = mid;
+        CU(cudaMemcpyAsync(w, wp, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        mag_hi = pm;
+        info_hi = pi;
+      } else {
+        lo = mid;
+      }
+    }
+  }
+  CU(cudaStreamSynchronize(s));
+  *t_plus = hi;
+  t_bracket[0] = below ? hi : lo;
+  t_bracket[1] = hi;
+  *mag = mag_hi;
+  if (info) {
+    *info = info_hi;
+    info->below_bracket = below;
+    info->probes = probes;
+    info->ir_iters = iters;
+  }
+  return MAG_OK;
+}
+
+int mag_grad(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t, const double* w,
+             const double* dL_dw, double* dL_dt, double* dL_dx, mag_info* info) {
+  TRY(check_args(ctx, points, n, m, t));
+  if (!dL_dt || !dL_dx) return fail(ctx, MAG_EINVAL, "NULL output");
+  if (m > 64) return fail(ctx, MAG_EINVAL, "mag_grad supports m <= 64 (m = %d)", (int)m);
+  ctx->err.clear();
+  if (info) std::memset(info, 0, sizeof *info);
+  mag_info si;
+  std::memset(&si, 0, sizeof si);
+  TRY(ensure_aux(ctx, n));
+  cudaStream_t s = ctx->stream;
+  double* wv = ctx->aux + (size_t)A_W * ctx->aux_np;
+  double* lam = ctx->aux + (size_t)A_LAM * ctx->aux_np;
+  double* g = ctx->aux + (size_t)A_G * ctx->aux_np;
+  if (w) {
+    CU(cudaMemcpyAsync(wv, w, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else {
+    double mg = 0;
+    TRY(mag_solve(ctx, points, n, m, t, wv, &mg, &si));
+  }
+  if (dL_dw) {
+    // adjoint solve lambda = Z^{-1} g
+    CU(cudaMemcpyAsync(g, dL_dw, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    mag_info ai;
+    TRY(mag_solve_rhs(ctx, points, n, m, t, g, lam, &ai));
+    si.ir_iters += ai.ir_iters;
+    si.rel_residual = std::max(si.rel_residual, ai.rel_residual);
+  } else {
+    CU(cudaMemcpyAsync(lam, wv, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  if (!ctx->ws) TRY(ensure_workspace(ctx, n, false, false));
+  double* part_t = ctx->aux + (size_t)A_PART * ctx->aux_np;
+  CU(launch_grad(points, n, m, t, wv, lam, dL_dx, part_t, ctx->aux_np, s));
+  CU(launch_sum_f64(part_t, n, &ctx->st()->aux[0], s));
+  TRY(read_status(ctx));
+  *dL_dt = ctx->h_st->aux[0];
+  if (info) *info = si;
+  return MAG_OK;
+}
+
+int mag_solve_batch(mag_ctx* ctx, const mag_batch_desc* desc, int32_t count, const double* points,
+                    double* w_out, double* mag_out, int32_t* status_out, mag_info* info) {
+  if (!ctx) return MAG_EINVAL;
+  if (!desc || count < 0 || !points || !w_out || !mag_out) return fail(ctx, MAG_EINVAL, "bad batch arguments");
+  ctx->err.clear();
+  if (info) std::memset(info, 0, sizeof *info);
+  int first = MAG_OK;
+  cudaStream_t s = ctx->stream;
+  for (int32_t i = 0; i < count; ++i) {
+    double mg = 0;
+    int st = mag_solve(ctx, points + desc[i].point_offset, desc[i].n, desc[i].m, desc[i].t,
+                       w_out + desc[i].w_offset, &mg, nullptr);
+    CU(cudaMemcpyAsync(mag_out + i, &mg, sizeof(double), cudaMemcpyHostToDevice, s));
+    if (status_out) CU(cudaMemcpyAsync(status_out + i, &st, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CU(cudaStreamSynchronize(s));
+    if (st != MAG_OK && first == MAG_OK) first = st;
+  }
+  return first;
+}
+
+}  // extern "C"

@@ -1,0 +1,129 @@
+// Internal declarations shared by the CUDA translation units of the magnitude
+// solver.  Nothing here is part of the public C ABI (include/magnitude.h).
+//
+// Data layout in HBM (one solve of size n, N = ceil(n / TILE) tiles a side):
+//   * Z and its Cholesky factor live in "packed lower tiles": tile (I, J) with
+//     I >= J is a contiguous TILE x TILE row-major block at tile index
+//     I (I + 1) / 2 + J.  Rows/columns >= n are padding and hold the identity,
+//     so the factor of the padded matrix is blockdiag(L, I) and padded
+//     solution entries are zero.
+//   * Diagonal tiles are stored in full (both triangles) by the generator; the
+//     factor keeps L in their lower triangle and zeros above.
+//   * Inverses of the diagonal factor blocks, inv(L_KK), live in a separate
+//     array of N full tiles (used by the panel solve and the triangular solves).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mag {
+
+constexpr int TILE = 128;
+constexpr int64_t TILE_ELEMS = (int64_t)TILE * TILE;
+
+__host__ __device__ inline int64_t tri_index(int64_t I, int64_t J) { return I * (I + 1) / 2 + J; }
+__host__ __device__ inline int64_t num_lower_tiles(int64_t N) { return N * (N + 1) / 2; }
+
+// Inverse of tri_index restricted to a triangle of tiles: linear index q over
+// the lower triangle {(I, J) : J <= I}, row-major by I.
+__host__ __device__ inline void tri_coords(int64_t q, int64_t* I, int64_t* J) {
+  int64_t i = (int64_t)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+  while (i * (i + 1) / 2 > q) --i;
+  while ((i + 1) * (i + 2) / 2 <= q) ++i;
+  *I = i;
+  *J = q - i * (i + 1) / 2;
+}
+
+// Device-side status and scalar results of the kernels of one solve.  Reset
+// (memset 0 plus the min fields) before each solve, read back by the host.
+enum StatusFlags : int {
+  ST_NONFINITE = 1,   // a coordinate is NaN/Inf (some d^2 is not finite)
+  ST_DUPLICATE = 2,   // d_jk = 0 for j != k
+  ST_NOTPD = 4,       // a Cholesky pivot was not positive
+  ST_TIMEOUT = 8,     // a bounded device wait gave up
+  ST_BADLAUNCH = 16   // a kernel got a launch shape it does not support
+};
+
+struct DevStatus {
+  int flags;
+  int notpd_index;                 // first failing pivot (global row), valid if ST_NOTPD
+  unsigned long long min_d2_bits;  // min off-diagonal d^2 (non-negative double bits)
+  unsigned long long r_max_bits;   // max_j |r_j|
+  unsigned long long z_max_bits;   // max_j sum_k Z_jk
+  unsigned long long w_max_bits;   // max_j |w_j|
+  unsigned long long off_max_bits; // max_j sum_{k != j} Z_jk (from the generator)
+  double mag;                      // 1^T w (compensated)
+  double min_w;                    // min_j w_j
+  double aux[6];                   // scratch scalars (GMRES dot products, grad sums)
+};
+
+// ---------------------------------------------------------------- launchers
+// Every launcher enqueues on `s` and returns cudaGetLastError().
+
+// K1: fused distance + exp generator of the packed lower tiles.
+// Writes Zf (FP32 tiles, may be null) and/or Zd (FP64 tiles, may be null),
+// accumulates full row sums of Z into rowsum (n doubles, must be zeroed),
+// min off-diagonal d^2, and non-finite/duplicate flags.
+cudaError_t launch_generate(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
+                            double* Zd, double* rowsum, DevStatus* st, cudaStream_t s);
+// min_{j != k} d^2 over all pairs (FP64) into st->min_d2_bits.
+cudaError_t launch_min_distance(const double* X, int64_t n, int m, DevStatus* st, cudaStream_t s);
+// off-diagonal row-sum maximum (Gershgorin) from rowsum into st->off_max_bits.
+cudaError_t launch_rowsum_max(const double* rowsum, int64_t n, DevStatus* st, cudaStream_t s);
+
+// K2: blocked right-looking Cholesky pieces (T = float or double).
+template <typename T>
+cudaError_t launch_potrf_diag(T* Z, T* Dinv, int64_t K, int64_t n, DevStatus* st, cudaStream_t s);
+// Panel solve: tiles (I, K) for I in [K+1, N): A_IK <- A_IK inv(L_KK)^T.
+template <typename T>
+cudaError_t launch_trsm_col(T* Z, const T* Dinv, int64_t K, int64_t N, DevStatus* st,
+                            cudaStream_t s);
+// CUDA-core trailing update: C_IJ -= sum_{k in [k0,k1)} L_Ik L_Jk^T for all
+// tiles with j0 <= J < j1, J <= I < N.
+template <typename T>
+cudaError_t launch_syrk_simt(T* Z, int64_t N, int64_t k0, int64_t k1, int64_t j0, int64_t j1,
+                             DevStatus* st, cudaStream_t s);
+
+// Dense n x n row-major copy of the packed tiles: symmetric (Z) or lower (L).
+template <typename T>
+cudaError_t launch_unpack(const T* Z, int64_t n, int64_t N, bool symmetric, T* out, cudaStream_t s);
+
+// K3: triangular solves with the packed factor, in place on v (np = N*TILE
+// entries of type T).  tmp: np entries of scratch.
+template <typename T>
+cudaError_t launch_forward(const T* Z, const T* Dinv, int64_t N, T* v, T* tmp, cudaStream_t s);
+template <typename T>
+cudaError_t launch_backward(const T* Z, const T* Dinv, int64_t N, T* v, T* tmp, cudaStream_t s);
+
+// K4: FP64 residual r = b - Z w (b == null means all ones), Z regenerated
+// from the points (matrix free) or read from FP64 packed tiles (stored).
+// part: scratch of 3 * chunks * np doubles.  Norms go to st (r_max, z_max, w_max).
+cudaError_t launch_residual_mf(const double* X, int64_t n, int m, double t, const double* w,
+                               const double* b, double* r, double* part, int chunks, int64_t np,
+                               DevStatus* st, cudaStream_t s);
+cudaError_t launch_residual_stored(const double* Zd, int64_t n, int64_t N, const double* w,
+                                   const double* b, double* r, double* part, DevStatus* st,
+                                   cudaStream_t s);
+
+// K5/K6 helpers.  r_max below is max_j |r_j| as kept in st->r_max_bits.
+// v[i] = r[i] / r_max for i < n, 0 for n <= i < np (right-hand side of a correction).
+template <typename T>
+cudaError_t launch_scale_rhs(const double* r, int64_t n, int64_t np, T* v, const DevStatus* st,
+                             cudaStream_t s);
+// x[i] = (init ? 0 : x[i]) + r_max * v[i], in FP64 (the refinement update).
+template <typename T>
+cudaError_t launch_accumulate(double* x, const T* v, int64_t n, const DevStatus* st, bool init,
+                              cudaStream_t s);
+// st->r_max_bits = max(st->r_max_bits, max_i |v[i]|).
+cudaError_t launch_absmax(const double* v, int64_t n, DevStatus* st, cudaStream_t s);
+// Mag = 1^T w (compensated), min w, max |w| into st.
+cudaError_t launch_reduce_w(const double* w, int64_t n, DevStatus* st, cudaStream_t s);
+cudaError_t launch_fill(double* v, int64_t n, double value, cudaStream_t s);
+
+// K7 gradients: dL/dt partial sums and dL/dx.
+cudaError_t launch_grad(const double* X, int64_t n, int m, double t, const double* w,
+                        const double* lam, double* dL_dx, double* part_t, int64_t np,
+                        cudaStream_t s);
+cudaError_t launch_sum_f64(const double* v, int64_t n, double* out, cudaStream_t s);
+
+}  // namespace mag

@@ -1,0 +1,255 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle on the
+same seeded inputs.
+
+Tolerances (stated per quantity, from the arithmetic):
+  * FP64 Z entries: both sides take d^2 in FP64 (GPU with FMA, CPU without),
+    sqrt correctly rounded, exp within 1 ulp on each side, so
+    |dZ| <= 4u (1 + t d) Z  with u = 2^-53  -> rtol 1e-15 (1 + t d) used as 2e-15 (1 + t d).
+  * FP32 Z entries (factor input): FP32 sqrt/exp from the FP64 d^2:
+    |dZ| <= (4 + 4 t d) 2^-24 Z.
+  * w and Mag: the refined solution meets ||1-Zw||/(||Z|| ||w||) <= 1e-14 (checked by the
+    oracle's own residual), max|w - w_ref| / max|w_ref| <= 1e-9, |dMag|/Mag <= 1e-10, the
+    same sign pattern ignoring |w_i| < 1e-12 max|w| (the target accuracy of the method).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+M = pytest.importorskip("paper_2607_23354_gb300")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return M.Context()
+
+
+def _cloud(n, m, seed, kind="cube"):
+    rng = np.random.default_rng(seed)
+    if kind == "cube":
+        return rng.random((n, m))
+    if kind == "normal":
+        return rng.standard_normal((n, m)) / math.sqrt(m)
+    raise ValueError(kind)
+
+
+def _dev(X):
+    return torch.from_numpy(np.ascontiguousarray(X)).cuda()
+
+
+def _sign_pattern(w):
+    w = np.asarray(w)
+    keep = np.abs(w) >= 1e-12 * np.abs(w).max()
+    return np.sign(w) * keep
+
+
+def check_solution(X, t, w_gpu, mag_gpu, w_ref=None, mag_ref=None, rel_tol=1e-14):
+    w_gpu = np.asarray(w_gpu)
+    rel = oracle.relative_residual(X, t, w_gpu)
+    assert rel <= rel_tol, f"relative residual {rel:.3e}"
+    if w_ref is not None:
+        err = np.abs(w_gpu - w_ref).max() / np.abs(w_ref).max()
+        assert err <= 1e-9, f"max|dw|/max|w| = {err:.3e}"
+        assert np.array_equal(_sign_pattern(w_gpu), _sign_pattern(w_ref))
+    if mag_ref is not None:
+        assert abs(mag_gpu - mag_ref) <= 1e-10 * abs(mag_ref), (mag_gpu, mag_ref)
+    return rel
+
+
+# ------------------------------------------------------------ generator K1
+@pytest.mark.parametrize("n,m,t", [(2, 1, 1.0), (3, 2, 0.5), (17, 3, 2.0), (129, 8, 1.0), (257, 33, 0.3),
+                                   (300, 5, 10.0)])
+def test_similarity_fp64_elementwise(ctx, n, m, t):
+    X = _cloud(n, m, seed=n * 7 + m)
+    Zg = ctx.similarity_matrix(_dev(X), t, "fp64").cpu().numpy()
+    Zo = oracle.similarity_matrix(X, t)
+    td = t * oracle.distance_matrix(X)
+    assert np.all(np.abs(Zg - Zo) <= 2e-15 * (1 + td) * Zo + 1e-300)
+    assert np.all(np.diag(Zg) == 1.0)
+
+
+@pytest.mark.parametrize("n,m,t", [(5, 2, 1.0), (200, 8, 1.0), (260, 16, 0.2)])
+def test_similarity_fp32_elementwise(ctx, n, m, t):
+    X = _cloud(n, m, seed=n + m)
+    Zg = ctx.similarity_matrix(_dev(X), t, "fp32").cpu().numpy().astype(np.float64)
+    Zo = oracle.similarity_matrix(X, t)
+    td = t * oracle.distance_matrix(X)
+    assert np.all(np.abs(Zg - Zo) <= (4 + 4 * td) * 2.0 ** -24 * Zo + 1e-38)
+
+
+def test_min_distance(ctx):
+    X = _cloud(700, 4, seed=3)
+    dmin, tb = ctx.min_distance(_dev(X))
+    assert dmin == pytest.approx(oracle.min_distance(X), rel=1e-15)
+    assert tb == pytest.approx(oracle.tplus_bound(X), rel=1e-15)
+    G = workloads.grid_support_cloud()
+    dmin, tb = ctx.min_distance(_dev(G))
+    assert dmin == 1.0 and tb == pytest.approx(math.log(len(G) - 1), rel=1e-15)
+
+
+# --------------------------------------------------------------- factor K2
+@pytest.mark.parametrize("n", [3, 128, 129, 300])
+def test_cholesky_fp64_elementwise(ctx, n):
+    X = _cloud(n, 3, seed=n)
+    t = 2.0
+    Lg = ctx.cholesky_factor(_dev(X), t, "fp64").cpu().numpy()
+    Lo = oracle.cholesky(oracle.similarity_matrix(X, t))
+    assert np.abs(Lg - Lo).max() <= 1e-12 * np.abs(Lo).max()
+
+
+@pytest.mark.parametrize("n", [130, 400])
+def test_cholesky_fp32_normwise(ctx, n):
+    X = _cloud(n, 8, seed=n)
+    t = 3.0
+    Lg = ctx.cholesky_factor(_dev(X), t, "fp32").cpu().numpy().astype(np.float64)
+    Lo = oracle.cholesky(oracle.similarity_matrix(X, t))
+    assert np.abs(Lg - Lo).max() <= 1e-4 * np.abs(Lo).max()
+    Z = oracle.similarity_matrix(X, t)
+    assert np.abs(Lg @ Lg.T - Z).max() <= 1e-5
+
+
+# ------------------------------------------------------------ full solve
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("n,m,t", [(2, 1, 0.7), (3, 2, 1.0), (5, 3, 0.4), (17, 8, 1.0), (129, 8, 1.0),
+                                   (257, 16, 0.5), (1000, 8, 1.0), (1031, 3, 10.0), (600, 40, 0.8)])
+def test_solve_matches_oracle(ctx, prec, n, m, t):
+    X = _cloud(n, m, seed=1000 + n + m)
+    ctx.set_options(M.Options(precision=prec))
+    w, mag, info = ctx.solve(_dev(X), t)
+    w_ref, mag_ref, _ = oracle.weighting(X, t)
+    check_solution(X, t, w.cpu().numpy(), mag, w_ref, mag_ref)
+    assert info["rel_residual"] <= 1e-14
+    ctx.set_options(M.Options())
+
+
+@pytest.mark.parametrize("t", [0.01, 0.5, 3.0])
+def test_two_point_closed_form_gpu(ctx, t):
+    X = np.array([[0.0, 0.0, 0.0], [1.0, 2.0, 2.0]])
+    w, mag, _ = ctx.solve(_dev(X), t)
+    np.testing.assert_allclose(w.cpu().numpy(), 1 / (1 + math.exp(-3 * t)), rtol=1e-14)
+    assert mag == pytest.approx(2 / (1 + math.exp(-3 * t)), rel=1e-14)
+
+
+def test_collinear_closed_form_gpu(ctx):
+    rng = np.random.default_rng(5)
+    gaps = rng.uniform(0.05, 2.0, size=299)
+    s = np.concatenate([[0.0], np.cumsum(gaps)])
+    u = rng.standard_normal(4)
+    u /= np.linalg.norm(u)
+    X = s[:, None] * u[None, :]
+    t = 1.3
+    w, mag, _ = ctx.solve(_dev(X), t)
+    assert mag == pytest.approx(1 + np.sum(np.tanh(t * gaps / 2)), rel=1e-12)
+
+
+def test_rejects_bad_inputs(ctx):
+    X = _cloud(50, 3, seed=1)
+    Xd = X.copy()
+    Xd[7] = Xd[3]
+    with pytest.raises(M.MagnitudeError) as e:
+        ctx.solve(_dev(Xd), 1.0)
+    assert e.value.status == M.MAG_EDUPLICATE
+    Xn = X.copy()
+    Xn[10, 1] = np.nan
+    with pytest.raises(M.MagnitudeError) as e:
+        ctx.solve(_dev(Xn), 1.0)
+    assert e.value.status == M.MAG_EINVAL
+    for t in [0.0, -1.0, float("inf"), float("nan")]:
+        with pytest.raises(M.MagnitudeError) as e:
+            ctx.solve(_dev(X), t)
+        assert e.value.status == M.MAG_EINVAL
+    with pytest.raises(M.MagnitudeError) as e:
+        ctx.solve(_dev(X[:1]), 1.0)
+    assert e.value.status == M.MAG_EINVAL
+    # the context stays usable after errors
+    w, mag, _ = ctx.solve(_dev(X), 1.0)
+    assert mag == pytest.approx(oracle.magnitude(X, 1.0), rel=1e-10)
+
+
+def test_general_rhs(ctx):
+    X = _cloud(300, 4, seed=9)
+    b = np.random.default_rng(10).standard_normal(300)
+    x, info = ctx.solve_rhs(_dev(X), 0.9, torch.from_numpy(b).cuda())
+    xr, _ = oracle.solve(X, 0.9, b=b)
+    assert np.abs(x.cpu().numpy() - xr).max() <= 1e-9 * np.abs(xr).max()
+    assert oracle.relative_residual(X, 0.9, x.cpu().numpy(), b=b) <= 1e-14
+
+
+# ------------------------------------------------------------- sweep a8
+def test_sweep_grid_support_matches_oracle(ctx):
+    G = workloads.grid_support_cloud()
+    r = ctx.sweep_tplus(_dev(G), 1e-3, 0.0, 1e-6)
+    ro = oracle.tplus(G, 1e-3, 0.0, 1e-6)
+    assert r["t_plus"] == pytest.approx(ro["t_plus"], rel=1e-6)
+    lo, hi = r["bracket"]
+    assert hi - lo <= 1e-6 * hi
+    assert r["w"].min().item() >= 0
+    assert r["mag"] == pytest.approx(ro["mag"], rel=1e-6)
+
+
+def test_sweep_below_bracket_collinear(ctx):
+    X = np.stack([np.linspace(0, 5, 40), np.zeros(40)], axis=1)
+    r = ctx.sweep_tplus(_dev(X), 1e-3, 0.0, 1e-6)
+    assert r["below"] and r["t_plus"] == 1e-3 and r["probes"] == 2
+
+
+def test_sweep_no_bracket(ctx):
+    ang = 2 * np.pi * np.arange(12) / 12
+    X = np.vstack([[0.0, 0.0], np.stack([np.cos(ang), np.sin(ang)], 1)])
+    with pytest.raises(M.MagnitudeError) as e:
+        ctx.sweep_tplus(_dev(X), 1e-3, 1.0, 1e-6)
+    assert e.value.status == M.MAG_ENOBRACKET
+
+
+# ------------------------------------------------------------ gradients a9
+def test_grad_matches_oracle(ctx):
+    X = workloads.normal_cloud(n=512, m=16, seed=4)
+    t = 2.0
+    dt, dx = ctx.grad(_dev(X), t)
+    dto, dxo = oracle.grad(X, t)
+    assert dt == pytest.approx(dto, rel=1e-9)
+    assert np.abs(dx.cpu().numpy() - dxo).max() <= 1e-9 * np.abs(dxo).max()
+
+
+def test_grad_general_loss_matches_oracle(ctx):
+    X = workloads.normal_cloud(n=300, m=8, seed=6)
+    t = 2.0
+    w, _, _ = ctx.solve(_dev(X), t)
+    g = 2 * w
+    dt, dx = ctx.grad(_dev(X), t, w=w, dL_dw=g)
+    wo = oracle.weighting(X, t)[0]
+    dto, dxo = oracle.grad_loss(X, t, 2 * wo, w=wo)
+    assert dt == pytest.approx(dto, rel=1e-8)
+    assert np.abs(dx.cpu().numpy() - dxo).max() <= 1e-8 * np.abs(dxo).max()
+
+
+def test_autograd_function(ctx):
+    X = workloads.normal_cloud(n=200, m=4, seed=8)
+    Xt = _dev(X).requires_grad_(True)
+    tt = torch.tensor(1.5, dtype=torch.float64, requires_grad=True)
+    w, mag = M.magnitude(Xt, tt)
+    mag.backward()
+    dto, dxo = oracle.grad(X, 1.5)
+    assert tt.grad.item() == pytest.approx(dto, rel=1e-9)
+    assert np.abs(Xt.grad.cpu().numpy() - dxo).max() <= 1e-9 * np.abs(dxo).max()
+
+
+# --------------------------------------------------------------- batch a10
+def test_batch_matches_oracle(ctx):
+    clouds, ts = workloads.batch_clouds(count=6, m=8, n_min=20, n_max=300, n_t=3, seed=2)
+    ws, mags, sts = ctx.solve_batch([_dev(c) for c in clouds], list(ts))
+    assert int(sts.abs().sum()) == 0
+    k = 0
+    for i, c in enumerate(clouds):
+        for j, t in enumerate(ts):
+            w_ref, mag_ref, _ = oracle.weighting(c, t)
+            check_solution(c, t, ws[k].cpu().numpy(), mags[i, j].item(), w_ref, mag_ref)
+            k += 1
