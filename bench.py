@@ -1,0 +1,407 @@
+#!/usr/bin/env python3
+"""Benchmark of the metric-magnitude hot path on GB300.
+
+Workload (default): n = 100,000 points uniform in [0, 1]^8 (seeded), solved at
+t in {1, 10, log(n-1)/min d}; one step = those three solves of Zw = 1 to
+relative residual <= 1e-14 (generation, factor, triangular solves, FP64
+refinement, magnitude).  Metric unit: TFLOP/s of useful work
+(n^3/3 + 2 n^2 per refinement step, per solve) over device time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own replica (independent seeded
+problem) on its own GPU: weak scaling, no collective on the data path; the
+barrier and the max over ranks bracket the timed region.  `--impl reference`
+times the CPU FP64 oracle on the host cores on a bounded sample of the same
+workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "n=1e5 Zw=1 solve s & TFLOP/s, mixed+IR vs FP64 dense at 1e-14 resid; batch solve/s"
+UNIT = "TFLOP/s"
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=100_000)
+    p.add_argument("--m", type=int, default=8)
+    p.add_argument("--ts", default="1,10,bound", help="comma list of t values; 'bound' = log(n-1)/min d")
+    p.add_argument("--precision", default="auto")
+    p.add_argument("--resid", default="matrix_free", choices=["matrix_free", "stored"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--extras", action="store_true", help="also time sweep/grad/batch/FP64 comparators")
+    p.add_argument("--cpu-sample-n", type=int, default=6144)
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def source_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key):
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary,
+    or None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f).get(kernel_key)
+    except (OSError, ValueError):
+        return None
+    if not d:
+        return None
+    try:
+        if source_hash(d["sources"]) != d["source_hash"]:
+            return None
+    except (OSError, KeyError):
+        return None
+    return d.get("bytes_per_launch")
+
+
+def cpu_oracle_sample(X, t, n_s):
+    """Time the CPU oracle (as it stands) on a seeded n_s-point subset: one
+    weighting solve (Z, Cholesky, 2 refinement steps)."""
+    import oracle
+    import workloads
+    Xs = workloads.subsample(X, n_s, seed=11)
+    t0 = time.perf_counter()
+    w, mag, info = oracle.weighting(Xs, t, ir_steps=2)
+    el = time.perf_counter() - t0
+    flops = n_s ** 3 / 3 + 2 * n_s ** 2 * 2
+    return {"value": flops / el / 1e12, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n_s} of the {X.shape[0]} points (seeded subset), m={X.shape[1]}, t={t:g}: one oracle "
+                      f"solve (Z, Cholesky, forward/back substitution, 2 FP64 refinement steps) in {el:.2f} s",
+            "seconds": el, "rel_residual": info["rel_residual"]}
+
+
+# --------------------------------------------------------------- our arm
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    import paper_2607_23354_gb300 as M
+    import workloads
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    X = workloads.unit_cube_cloud(n=a.n, m=a.m, seed=workloads.SEEDS["cube"] + rank)
+    Xd = torch.from_numpy(X).to(dev)
+    opts = M.Options(precision=a.precision, residual_mode=a.resid, profile=True)
+    ctx = M.Context(opts)
+    dmin, bound = ctx.min_distance(Xd)
+    ts = [bound if s.strip() == "bound" else float(s) for s in a.ts.split(",")]
+    wbuf = torch.empty(a.n, dtype=torch.float64, device=dev)
+
+    def step(acc=None):
+        for t in ts:
+            _, mag, info = ctx.solve(Xd, t, w=wbuf)
+            if acc is not None:
+                acc.append((t, mag, info))
+
+    for _ in range(a.warmup):
+        step()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = str(getattr(props, "uuid", local))
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) > 8:
+        gpu_id = "GPU-" + gpu_id
+    sampler = ClockSampler(gpu_id)
+    stream = torch.cuda.current_stream(dev)
+    infos = []
+    barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step(infos)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = tt.item()
+    flops_step = sum(i["useful_flops"] for _, _, i in infos) / a.steps
+    value = world * flops_step * a.steps / (ms / 1e3) / 1e12
+
+    # e2e: host (pinned) points in, host w out, copies inside the timed region
+    e2e = None
+    if not a.no_e2e:
+        Xh = torch.from_numpy(X).pin_memory()
+        wh = torch.empty(a.n, dtype=torch.float64).pin_memory()
+        Xe = torch.empty_like(Xd)
+        h2d = Xh.numel() * 8
+        d2h = a.n * 8 * len(ts)
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        f2 = 0.0
+        for _ in range(a.steps):
+            Xe.copy_(Xh, non_blocking=True)
+            for t in ts:
+                _, mag, info = ctx.solve(Xe, t, w=wbuf)
+                wh.copy_(wbuf, non_blocking=True)
+                f2 += info["useful_flops"]
+            torch.cuda.synchronize(dev)
+        el = time.perf_counter() - t0
+        barrier()
+        if world > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([el], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            el = tt.item()
+        e2e = {"value": world * f2 / el / 1e12, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h + 8 * len(ts)}
+
+    out = None
+    if rank == 0:
+        peaks, peak_kind = measured_peaks()
+        last = infos[-len(ts):]
+        per_t = [{"t": t, "solve_s": i["ms_total"] / 1e3, "mag": mag, "rel_residual": i["rel_residual"],
+                  "ir_iters": i["ir_iters"], "precision_used": i["precision_used"], "fallback": i["fallback"],
+                  "ms_generate": i["ms_generate"], "ms_factor": i["ms_factor"], "ms_solve": i["ms_solve"],
+                  "ms_residual": i["ms_residual"], "residual_evals": i["residual_evals"]} for t, mag, i in last]
+        upd_ms = sum(i["ms_update"] for _, _, i in infos)
+        upd_launch = sum(i["update_launches"] for _, _, i in infos)
+        upd_flops = sum(i["update_flops"] for _, _, i in infos)
+        prec_used = {i["precision_used"] for _, _, i in infos}
+        tensor = any(p in (M.PREC_BF16, M.PREC_TF32, M.PREC_TF32X3) for p in prec_used)
+        smx = peaks.get("sm_max_mhz", 2070.0)
+        if tensor:
+            bf16 = peaks["bf16_tflops"]
+            peak = bf16 * (1.1 / 2.25)  # TF32 dense / BF16 dense, nominal ratio
+            bound, kname = "tensor", "trailing_update_tc"
+            peak_note = f"TF32 tensor peak = {peak_kind} BF16 {bf16} TF/s x nominal TF32/BF16 ratio 1.1/2.25"
+        else:
+            peak = 152 * 128 * 2 * smx * 1e6 / 1e12
+            bound, kname = "alu", "trailing_update_simt"
+            peak_note = f"FP32 FMA peak = 152 SMs x 128 lanes x 2 flops x {smx:.0f} MHz"
+        achieved = (upd_flops / upd_launch) / ((upd_ms / upd_launch) / 1e3) / 1e12 if upd_launch else None
+        traffic = ncu_traffic(kname)
+        roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                    "kernel": kname, "launches": upd_launch, "avg_launch_ms": upd_ms / max(upd_launch, 1),
+                    "flops_per_launch": upd_flops / max(upd_launch, 1), "peak_source": peak_note,
+                    "share_of_step": upd_ms / ms if ms else None}
+        launches = sum(i["kernel_launches"] for _, _, i in infos)
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+               "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": f"n={a.n} points uniform in [0,1]^{a.m} (seed {workloads.SEEDS['cube']}+rank), "
+                                      f"t in {{{', '.join(s.strip() for s in a.ts.split(','))}}}; one step = "
+                                      f"{len(ts)} solves to rel. residual <= 1e-14",
+                          "n": a.n, "m": a.m, "t": ts, "precision": a.precision, "residual_mode": a.resid,
+                          "parallelism": f"replicas x{world}",
+                          "l2": "inputs larger than L2 (packed factor tiles of several GB per solve)"},
+               "solve_s": sum(p["solve_s"] for p in per_t), "per_t": per_t,
+               "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+               "min_distance": dmin}
+    return out, (ctx, Xd, X, ts)
+
+
+def run_extras(ctx, a, out):
+    """Bounded side measurements: FP64 dense comparators, sweep, gradients, batch."""
+    import torch
+
+    import paper_2607_23354_gb300 as M
+    import workloads
+    ex = {}
+    # FP64 dense on the same GPU at the precision config's size (n = 16384)
+    Xm = torch.from_numpy(workloads.gaussian_mixture_cloud()).cuda()
+    for prec in ["fp64", "auto"]:
+        ctx.set_options(M.Options(precision=prec))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, mag, info = ctx.solve(Xm, 0.5)
+        torch.cuda.synchronize()
+        ex[f"mixture_n16384_t0.5_{prec}_s"] = time.perf_counter() - t0
+    ctx.set_options(M.Options(precision=a.precision, residual_mode=a.resid, profile=True))
+    try:
+        Zc = None
+        n2 = Xm.shape[0]
+        d = torch.cdist(Xm, Xm)
+        Zc = torch.exp(-0.5 * d)
+        del d
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L = torch.linalg.cholesky(Zc)
+        w = torch.cholesky_solve(torch.ones(n2, 1, dtype=torch.float64, device=Zc.device), L)
+        torch.cuda.synchronize()
+        ex["cusolver_fp64_n16384_s"] = time.perf_counter() - t0
+        del L, w, Zc
+    except Exception as e:  # noqa: BLE001
+        ex["cusolver_fp64_error"] = str(e)[:120]
+    # sweep on the grid-support cloud
+    G = torch.from_numpy(workloads.grid_support_cloud()).cuda()
+    t0 = time.perf_counter()
+    r = ctx.sweep_tplus(G, 1e-3, 0.0, 1e-6)
+    ex["sweep_grid_s"] = time.perf_counter() - t0
+    ex["sweep_grid_tplus"] = r["t_plus"]
+    ex["sweep_grid_probes"] = r["probes"]
+    # gradients
+    Xn = torch.from_numpy(workloads.normal_cloud()).cuda()
+    t0 = time.perf_counter()
+    ctx.grad(Xn, 2.0)
+    torch.cuda.synchronize()
+    ex["grad_n8192_m16_s"] = time.perf_counter() - t0
+    out["extras"] = ex
+
+
+# ---------------------------------------------------------- reference arm
+def run_reference(a):
+    import oracle
+    import workloads
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    X = workloads.unit_cube_cloud(n=a.n, m=a.m)
+    n_s = min(a.cpu_sample_n, a.n)
+    Xs = workloads.subsample(X, n_s, seed=11)
+    oracle.build()
+    times = []
+    for k in range(a.warmup + a.steps):
+        t0 = time.perf_counter()
+        oracle.weighting(Xs, 1.0, ir_steps=2)
+        el = time.perf_counter() - t0
+        if k >= a.warmup:
+            times.append(el)
+    tot = sum(times)
+    flops = n_s ** 3 / 3 + 2 * n_s ** 2 * 2
+    value = flops * len(times) / tot / 1e12
+    sample = (f"each step: one oracle solve of a seeded {n_s}-point subset of the n={a.n}, m={a.m} "
+              f"unit-cube workload at t=1 (Z, Cholesky, substitution, 2 FP64 refinement steps)")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": tot / len(times) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"n={a.n} points uniform in [0,1]^{a.m}; bounded CPU sample n={n_s}",
+                       "n": a.n, "m": a.m, "sample_n": n_s},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    a = parse_args()
+    if a.impl == "reference":
+        out = run_reference(a)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out, state = run_ours(a)
+    rank, world, _ = dist_env()
+    if rank == 0:
+        ctx, Xd, X, ts = state
+        if a.extras:
+            run_extras(ctx, a, out)
+        if not a.no_cpu:
+            out["cpu_baseline"] = cpu_oracle_sample(X, 1.0, min(a.cpu_sample_n, a.n))
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -76,6 +76,8 @@ typedef struct mag_options {
   int32_t allow_fallback; /* 1: escalate to GMRES-IR then FP64 factor (default)  */
   int32_t panel_tiles;    /* outer panel width in 128-wide tiles (0 = default)  */
   double workspace_limit_bytes; /* 0 = no limit; larger requests give ENOMEM     */
+  int32_t profile;        /* 1: time the trailing-update kernel with CUDA events */
+  int32_t reserved;
 } mag_options;
 
 /* Diagnostics of one call (all fields written when info != NULL). */
@@ -93,7 +95,13 @@ typedef struct mag_info {
   int32_t below_bracket;   /* sweep: feasible already at t_lo                  */
   int32_t probes;          /* sweep: number of solves                           */
   double ms_generate, ms_factor, ms_solve, ms_residual, ms_total;
-  double useful_flops;     /* n^3/3 + 2n^2 per triangular-solve pair + 2 n^2 m per residual */
+  double useful_flops;     /* n^3/3 + 2 n^2 ir_iters (factor + refinement steps)   */
+  int64_t kernel_launches; /* kernels this call launched                        */
+  int32_t residual_evals;  /* FP64 residual evaluations                         */
+  int32_t update_launches; /* trailing-update kernel launches                   */
+  double ms_update;        /* their total device time (profile = 1), else 0     */
+  double update_flops;     /* algorithmic flops of those launches: 2*128^3 per
+                              (output tile, panel tile) product                 */
 } mag_info;
 
 typedef struct mag_ctx mag_ctx;

@@ -38,7 +38,8 @@ class mag_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("residual_mode", ctypes.c_int32),
                 ("ir_tol", ctypes.c_double), ("ir_max_iters", ctypes.c_int32),
                 ("gmres_max_iters", ctypes.c_int32), ("allow_fallback", ctypes.c_int32),
-                ("panel_tiles", ctypes.c_int32), ("workspace_limit_bytes", ctypes.c_double)]
+                ("panel_tiles", ctypes.c_int32), ("workspace_limit_bytes", ctypes.c_double),
+                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class mag_info(ctypes.Structure):
@@ -50,7 +51,10 @@ class mag_info(ctypes.Structure):
                 ("below_bracket", ctypes.c_int32), ("probes", ctypes.c_int32),
                 ("ms_generate", ctypes.c_double), ("ms_factor", ctypes.c_double),
                 ("ms_solve", ctypes.c_double), ("ms_residual", ctypes.c_double),
-                ("ms_total", ctypes.c_double), ("useful_flops", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("useful_flops", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64), ("residual_evals", ctypes.c_int32),
+                ("update_launches", ctypes.c_int32), ("ms_update", ctypes.c_double),
+                ("update_flops", ctypes.c_double)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -128,6 +132,7 @@ class Options:
     allow_fallback: bool = True
     panel_tiles: int = 0
     workspace_limit_bytes: float = 0.0
+    profile: bool = False
 
     def to_c(self) -> mag_options:
         o = mag_options()
@@ -140,6 +145,7 @@ class Options:
         o.allow_fallback = int(self.allow_fallback)
         o.panel_tiles = self.panel_tiles
         o.workspace_limit_bytes = self.workspace_limit_bytes
+        o.profile = int(self.profile)
         return o
 
 

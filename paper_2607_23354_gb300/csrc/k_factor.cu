@@ -14,6 +14,8 @@
 //
 // All kernels are templated on the element type (float for the mixed
 // precision factor, double for the FP64 factor).
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "mag_internal.cuh"
@@ -271,7 +273,50 @@ __global__ void k_unpack(const T* __restrict__ Z, int64_t n, int symmetric, T* _
   }
 }
 
+// Panel copy of tile column K for the tensor-core update (one CTA per tile).
+__global__ void __launch_bounds__(256) k_split_col(const float* __restrict__ Z, int64_t K, int64_t k0,
+                                                   int64_t width, int mode, void* __restrict__ hi,
+                                                   void* __restrict__ lo) {
+  const int64_t I = K + 1 + blockIdx.x;
+  const float* src = Z + tri_index(I, K) * TILE_ELEMS;
+  const int64_t row0 = (I - k0) * TILE, col0 = (K - k0) * TILE;
+  for (int e = threadIdx.x; e < TILE * TILE / 4; e += blockDim.x) {
+    const int r = e / (TILE / 4), c = (e % (TILE / 4)) * 4;
+    const float4 x = reinterpret_cast<const float4*>(src)[e];
+    const int64_t off = (row0 + r) * width + col0 + c;
+    if (mode == UPD_BF16) {
+      __nv_bfloat162 a = __floats2bfloat162_rn(x.x, x.y), b = __floats2bfloat162_rn(x.z, x.w);
+      uint2 u;
+      u.x = *reinterpret_cast<uint32_t*>(&a);
+      u.y = *reinterpret_cast<uint32_t*>(&b);
+      *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(hi) + off) = u;
+    } else {
+      float xs[4] = {x.x, x.y, x.z, x.w}, h[4], l[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t hb, lb;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(xs[q]));
+        h[q] = __uint_as_float(hb);
+        const float rem = xs[q] - h[q];
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lb) : "f"(rem));
+        l[q] = __uint_as_float(lb);
+      }
+      *reinterpret_cast<float4*>(reinterpret_cast<float*>(hi) + off) = make_float4(h[0], h[1], h[2], h[3]);
+      if (mode == UPD_TF32X3)
+        *reinterpret_cast<float4*>(reinterpret_cast<float*>(lo) + off) = make_float4(l[0], l[1], l[2], l[3]);
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_split_col(const float* Z, int64_t K, int64_t N, int64_t k0, int64_t width, int mode,
+                             void* hi, void* lo, cudaStream_t s) {
+  if (K + 1 >= N) return cudaSuccess;
+  k_split_col<<<(unsigned)(N - K - 1), 256, 0, s>>>(Z, K, k0, width, mode, hi, lo);
+  note_launch();
+  return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_unpack(const T* Z, int64_t n, int64_t N, bool symmetric, T* out, cudaStream_t s) {
@@ -279,6 +324,7 @@ cudaError_t launch_unpack(const T* Z, int64_t n, int64_t N, bool symmetric, T* o
   if (n > 65535) return cudaErrorInvalidValue;
   const unsigned bx = (unsigned)std::min<int64_t>((n + 255) / 256, 64);
   k_unpack<T><<<dim3(bx, (unsigned)n), 256, 0, s>>>(Z, n, symmetric ? 1 : 0, out);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -291,6 +337,7 @@ cudaError_t launch_potrf_diag(T* Z, T* Dinv, int64_t K, int64_t n, DevStatus* st
   const int64_t N = (n + TILE - 1) / TILE;
   // Dinv holds N tiles of inv(L_KK) followed by N tiles of inv(L_KK)^T.
   k_potrf_diag<T><<<1, 512, smem, s>>>(Z, Dinv, Dinv + N * TILE_ELEMS, K, n, st);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -299,6 +346,7 @@ cudaError_t launch_trsm_col(T* Z, const T* Dinv, int64_t K, int64_t N, DevStatus
                             cudaStream_t s) {
   if (K + 1 >= N) return cudaSuccess;
   k_trsm_col<T><<<(unsigned)(N - K - 1), 256, 0, s>>>(Z, Dinv, K, st);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -309,6 +357,7 @@ cudaError_t launch_syrk_simt(T* Z, int64_t N, int64_t k0, int64_t k1, int64_t j0
   const int64_t base = (N - j1) * (N - j1 + 1) / 2;
   const int64_t count = (N - j0) * (N - j0 + 1) / 2 - base;
   k_syrk_simt<T><<<(unsigned)count, 256, 0, s>>>(Z, N, k0, k1, base, st);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -317,6 +366,7 @@ cudaError_t launch_forward(const T* Z, const T* Dinv, int64_t N, T* v, T* y, cud
   const T* DinvT = Dinv + N * TILE_ELEMS;
   for (int64_t J = 0; J < N; ++J) {
     k_forward_step<T><<<(unsigned)(N - J), TILE, 0, s>>>(Z, DinvT, J, v, y);
+    note_launch();
   }
   return cudaGetLastError();
 }
@@ -325,6 +375,7 @@ template <typename T>
 cudaError_t launch_backward(const T* Z, const T* Dinv, int64_t N, T* v, T* x, cudaStream_t s) {
   for (int64_t J = N - 1; J >= 0; --J) {
     k_backward_step<T><<<(unsigned)(J + 1), TILE, 0, s>>>(Z, Dinv, J, v, x);
+    note_launch();
   }
   return cudaGetLastError();
 }

@@ -170,6 +170,7 @@ cudaError_t launch_gen_t(const double* X, int64_t n, int m, double t, int64_t N,
   if (e != cudaSuccess) return e;
   const int64_t tiles = num_lower_tiles(N);
   kern<<<(unsigned)tiles, GEN_THREADS, smem, s>>>(X, n, m, t, Zf, Zd, rowsum, st);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -192,6 +193,7 @@ cudaError_t launch_rowsum_max(const double* rowsum, int64_t n, DevStatus* st, cu
   int blocks = (int)((n + 255) / 256);
   if (blocks > 1024) blocks = 1024;
   k_rowsum_max<<<blocks, 256, 0, s>>>(rowsum, n, st);
+  note_launch();
   return cudaGetLastError();
 }
 

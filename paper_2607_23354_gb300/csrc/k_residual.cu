@@ -316,9 +316,11 @@ cudaError_t launch_residual_mf(const double* X, int64_t n, int m, double t, cons
     k_resid_mf<32><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct);
   else
     k_resid_mf<0><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct);
+  note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_resid_finish<<<blocks_for(np, 256), 256, 0, s>>>(part, chunks, n, np, w, b, r, st);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -326,6 +328,7 @@ template <typename T>
 cudaError_t launch_scale_rhs(const double* r, int64_t n, int64_t np, T* v, const DevStatus* st,
                              cudaStream_t s) {
   k_scale_rhs<T><<<blocks_for(np, 256), 256, 0, s>>>(r, n, np, v, st);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -333,6 +336,7 @@ template <typename T>
 cudaError_t launch_accumulate(double* x, const T* v, int64_t n, const DevStatus* st, bool init,
                               cudaStream_t s) {
   k_accumulate<T><<<blocks_for(n, 256), 256, 0, s>>>(x, v, n, st, init ? 1 : 0);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -349,17 +353,20 @@ cudaError_t launch_absmax(const double* v, int64_t n, DevStatus* st, cudaStream_
   unsigned blocks = blocks_for(n, 256);
   if (blocks > 1024) blocks = 1024;
   k_absmax<<<blocks, 256, 0, s>>>(v, n, st);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_w(const double* w, int64_t n, DevStatus* st, cudaStream_t s) {
   k_reduce_w<<<1, 1024, 0, s>>>(w, n, st);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_fill(double* v, int64_t n, double value, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_fill<<<blocks_for(n, 256), 256, 0, s>>>(v, n, value);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -381,11 +388,13 @@ cudaError_t launch_grad(const double* X, int64_t n, int m, double t, const doubl
     k_grad<64><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, lam, dL_dx, part_t, ct);
   else
     return cudaErrorInvalidValue;
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_sum_f64(const double* v, int64_t n, double* out, cudaStream_t s) {
   k_sum_f64<<<1, 1024, 0, s>>>(v, n, out);
+  note_launch();
   return cudaGetLastError();
 }
 

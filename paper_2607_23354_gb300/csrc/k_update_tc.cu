@@ -1,0 +1,463 @@
+// K2c: the Cholesky trailing update on the 5th-generation tensor cores
+// (tcgen05.mma, accumulators in TMEM, operands staged by TMA).
+//
+//   C_IJ -= sum_{k in K-range} L_Ik L_Jk^T     for J in [j0, j1), I in [J, N)
+//
+// Operands come from the panel buffer P: a row-major matrix whose row block
+// (I - k0) holds [L_{I,k0} | L_{I,k0+1} | ...] for the current panel, already
+// split for the product kind (TF32 hi/lo pairs, TF32, or BF16).  Each CTA task
+// is a 128 x 256 output block: tile (I, J) and, when it is in the trapezoid,
+// tile (I, J+1) -- A = 128 rows of P (row block I), B = 256 rows of P (row
+// blocks J, J+1), both K-major with the 128-byte swizzle, so one
+// M=128 x N=256 MMA per K step covers both tiles.
+//
+// Products (FP32 accumulation in TMEM):
+//   TF32X3: A_hi B_hi + A_hi B_lo + A_lo B_hi with hi = rna_tf32(x),
+//           lo = rna_tf32(x - hi): about 2^-21 relative per product (the
+//           split-TF32 scheme of Markidis et al., IPDPSW 2018).
+//   TF32  : A_hi B_hi.        BF16: one product of BF16-rounded operands.
+//
+// Structure: persistent CTAs (one per SM, 6 warps), warp-specialized:
+//   warp 0     : TMA producer (one thread), S-stage shared-memory ring;
+//   warp 1     : TMEM owner and MMA issuer (one thread); two 128x256 FP32
+//                accumulators (all 512 TMEM columns) so the epilogue of one
+//                task overlaps the MMAs of the next;
+//   warps 2..5 : epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//                lanes 32*(w%4)..+31), C -= acc on the packed tiles.
+// Tasks are ordered in 16x16-tile super-blocks of the trapezoid so that the
+// CTAs running concurrently share panel rows through L2.
+//
+// Every mbarrier wait is bounded (wall-clock deadline via %globaltimer); on
+// expiry the CTA raises ST_TIMEOUT, stops issuing work, drains its own TMA
+// loads with a bounded wait, frees its TMEM and returns.
+#include <cuda.h>
+
+#include "mag_internal.cuh"
+
+namespace mag {
+
+namespace {
+
+constexpr int UPD_THREADS = 192;
+constexpr int A_ROWS = 128, B_ROWS = 256;
+constexpr int CHUNK_BYTES = 128;  // K bytes per stage row (one 128B swizzle row)
+constexpr int A_BYTES = A_ROWS * CHUNK_BYTES;  // 16 KB
+constexpr int B_BYTES = B_ROWS * CHUNK_BYTES;  // 32 KB
+constexpr uint32_t TMEM_COLS = 512;
+constexpr int SUPER = 16;  // super-block edge in tiles
+
+template <int MODE>
+struct ModeCfg;
+template <>
+struct ModeCfg<UPD_TF32X3> {  // hi/lo pairs, 3 MMAs per K step
+  static constexpr int STAGES = 2;
+  static constexpr int ELEM = 4;
+  static constexpr bool SPLIT = true;
+  static constexpr uint32_t FMT = 2;  // TF32
+};
+template <>
+struct ModeCfg<UPD_TF32> {
+  static constexpr int STAGES = 4;
+  static constexpr int ELEM = 4;
+  static constexpr bool SPLIT = false;
+  static constexpr uint32_t FMT = 2;
+};
+template <>
+struct ModeCfg<UPD_BF16> {
+  static constexpr int STAGES = 4;
+  static constexpr int ELEM = 2;
+  static constexpr bool SPLIT = false;
+  static constexpr uint32_t FMT = 1;  // BF16 (kind::f16)
+};
+
+// ------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with `parity` to complete.  Returns false if the
+// deadline passed (then raises the CTA abort flag) or another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          uint64_t deadline) {
+  uint32_t it = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if ((++it & 255u) == 0) {
+      if (*abort_flag) return false;
+      if (globaltimer() > deadline) {
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), version 1, base offset 0.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);         // start address
+  d |= (uint64_t)1 << 16;                           // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset
+  d |= (uint64_t)1 << 46;                           // descriptor version
+  d |= (uint64_t)2 << 61;                           // SWIZZLE_128B
+  return d;
+}
+// Instruction descriptor: D = F32, A/B format `fmt`, both K-major, M = 128, N = 256.
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(B_ROWS >> 3) << 17) |
+         ((uint32_t)(A_ROWS >> 4) << 24);
+}
+template <int MODE>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  constexpr uint32_t idesc = instr_desc(ModeCfg<MODE>::FMT);
+  if constexpr (MODE == UPD_BF16) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+      "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+      "[%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Task q -> output block (I, J) of the trapezoid; false if q falls outside it.
+__device__ __forceinline__ bool decode_task(int64_t q, const UpdParams& p, int64_t* I, int64_t* J) {
+  const int64_t sb = q / (SUPER * SUPER / 2);
+  const int loc = (int)(q % (SUPER * SUPER / 2));
+  const int64_t SC = p.super_cols;
+  const int64_t tri = SC * (SC + 1) / 2;
+  int64_t sr, sc;
+  if (sb < tri) {
+    tri_coords(sb, &sr, &sc);
+  } else {
+    const int64_t r = sb - tri;
+    sr = SC + r / SC;
+    sc = r % SC;
+  }
+  *I = p.j0 + sr * SUPER + (loc / (SUPER / 2));
+  *J = p.j0 + sc * SUPER + 2 * (loc % (SUPER / 2));
+  return *I < p.N && *J < p.j1 && *J <= *I;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(UPD_THREADS, 1)
+    k_update_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mB_hi,
+                const __grid_constant__ CUtensorMap mA_lo, const __grid_constant__ CUtensorMap mB_lo,
+                const UpdParams p) {
+  using Cfg = ModeCfg<MODE>;
+  constexpr int S = Cfg::STAGES;
+  constexpr int OPS = Cfg::SPLIT ? 2 : 1;                 // hi (+ lo) copies per operand
+  constexpr int STAGE_BYTES = OPS * (A_BYTES + B_BYTES);  // 96 KB or 48 KB
+  constexpr int KSTEP_BYTES = 32;                          // K per MMA: 8 tf32 / 16 bf16
+  constexpr int KSTEPS = CHUNK_BYTES / KSTEP_BYTES;        // 4
+  constexpr int ELEMS_PER_CHUNK = CHUNK_BYTES / Cfg::ELEM;
+
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], tfull_bar[2], tempty_bar[2];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull_bar[a], 1);
+      mbar_init(&tempty_bar[a], 4);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_sh)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = tmem_base_sh;
+  const uint64_t deadline = globaltimer() + p.timeout_ns;
+  const int64_t ntasks = p.n_super * (SUPER * SUPER / 2);
+  const int chunk_lo = p.kc_lo * (TILE * Cfg::ELEM / CHUNK_BYTES);
+  const int chunk_hi = p.kc_hi * (TILE * Cfg::ELEM / CHUNK_BYTES);
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t stage = 0, phase = 0;
+      uint32_t issued_parity[S];
+      bool issued[S];
+      for (int s = 0; s < S; ++s) issued[s] = false, issued_parity[s] = 0;
+      bool ok = true;
+      for (int64_t q = blockIdx.x; q < ntasks && ok; q += gridDim.x) {
+        int64_t I, J;
+        if (!decode_task(q, p, &I, &J)) continue;
+        const int ya = (int)((I - p.k0) * TILE), yb = (int)((J - p.k0) * TILE);
+        for (int c = chunk_lo; c < chunk_hi; ++c) {
+          if (!mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag, deadline)) {
+            ok = false;
+            break;
+          }
+          unsigned char* sbase = smem + stage * STAGE_BYTES;
+          mbar_expect_tx(&full_bar[stage], STAGE_BYTES);
+          const int x = c * ELEMS_PER_CHUNK;
+          tma_load_2d(sbase, &mA_hi, &full_bar[stage], x, ya);
+          tma_load_2d(sbase + A_BYTES, &mB_hi, &full_bar[stage], x, yb);
+          if (Cfg::SPLIT) {
+            tma_load_2d(sbase + A_BYTES + B_BYTES, &mA_lo, &full_bar[stage], x, ya);
+            tma_load_2d(sbase + 2 * A_BYTES + B_BYTES, &mB_lo, &full_bar[stage], x, yb);
+          }
+          issued[stage] = true;
+          issued_parity[stage] = phase;
+          if (++stage == S) stage = 0, phase ^= 1u;
+        }
+      }
+      if (!ok) {
+        // drain our own loads in flight (bounded), so no TMA lands after exit
+        const uint64_t dl = globaltimer() + 200000000ull;
+        for (int s = 0; s < S; ++s)
+          if (issued[s])
+            while (!mbar_try_wait(&full_bar[s], issued_parity[s]) && globaltimer() < dl) {
+            }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      uint32_t stage = 0, phase = 0, acc = 0, acc_phase = 0;
+      bool ok = true;
+      for (int64_t q = blockIdx.x; q < ntasks && ok; q += gridDim.x) {
+        int64_t I, J;
+        if (!decode_task(q, p, &I, &J)) continue;
+        if (!mbar_wait(&tempty_bar[acc], acc_phase ^ 1u, &abort_flag, deadline)) break;
+        tc_fence_after();
+        const uint32_t d = tmem_base + acc * (uint32_t)B_ROWS;
+        for (int c = chunk_lo; c < chunk_hi; ++c) {
+          if (!mbar_wait(&full_bar[stage], phase, &abort_flag, deadline)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sb = smem_u32(smem + stage * STAGE_BYTES);
+#pragma unroll
+          for (int k = 0; k < KSTEPS; ++k) {
+            const uint64_t ahi = smem_desc_sw128(sb + k * KSTEP_BYTES);
+            const uint64_t bhi = smem_desc_sw128(sb + A_BYTES + k * KSTEP_BYTES);
+            const uint32_t accum = (c > chunk_lo || k > 0) ? 1u : 0u;
+            mma<MODE>(d, ahi, bhi, accum);
+            if (Cfg::SPLIT) {
+              const uint64_t alo = smem_desc_sw128(sb + A_BYTES + B_BYTES + k * KSTEP_BYTES);
+              const uint64_t blo = smem_desc_sw128(sb + 2 * A_BYTES + B_BYTES + k * KSTEP_BYTES);
+              mma<MODE>(d, ahi, blo, 1u);
+              mma<MODE>(d, alo, bhi, 1u);
+            }
+          }
+          mma_commit(&empty_bar[stage]);  // stage free once these MMAs have read it
+          if (++stage == S) stage = 0, phase ^= 1u;
+        }
+        if (!ok) break;
+        mma_commit(&tfull_bar[acc]);  // accumulator ready once all MMAs finished
+        if (++acc == 2) acc = 0, acc_phase ^= 1u;
+      }
+    }
+  } else {
+    // --------------------------------------------------------------- epilogue
+    const int quad = warp & 3;  // TMEM lane quadrant this warp may access
+    const int row = quad * 32 + lane;
+    uint32_t acc = 0, acc_phase = 0;
+    for (int64_t q = blockIdx.x; q < ntasks; q += gridDim.x) {
+      int64_t I, J;
+      if (!decode_task(q, p, &I, &J)) continue;
+      if (!mbar_wait(&tfull_bar[acc], acc_phase, &abort_flag, deadline)) break;
+      tc_fence_after();
+      const bool second = (J + 1 < p.j1) && (J + 1 <= I);
+      const int nchunks = second ? 8 : 4;
+      for (int cc = 0; cc < nchunks; ++cc) {
+        float v[32];
+        tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + acc * (uint32_t)B_ROWS + cc * 32, v);
+        const int64_t Jx = J + (cc >> 2);
+        float4* cp = reinterpret_cast<float4*>(p.Z + tri_index(I, Jx) * TILE_ELEMS + (int64_t)row * TILE +
+                                               (cc & 3) * 32);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          float4 c4 = cp[i];
+          c4.x -= v[4 * i + 0];
+          c4.y -= v[4 * i + 1];
+          c4.z -= v[4 * i + 2];
+          c4.w -= v[4 * i + 3];
+          cp[i] = c4;
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty_bar[acc]);
+      if (++acc == 2) acc = 0, acc_phase ^= 1u;
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && abort_flag) atomicOr(&p.st->flags, ST_TIMEOUT);
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------ tensor maps
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)f;
+  }
+  return fn;
+}
+
+bool encode_2d(CUtensorMap* m, const void* base, bool bf16, int64_t cols, int64_t rows, int box_rows) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return false;
+  const int elem = bf16 ? 2 : 4;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(cols * elem)};
+  cuuint32_t box[2] = {(cuuint32_t)(CHUNK_BYTES / elem), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int MODE>
+cudaError_t launch_mode(const UpdMaps& maps, const UpdParams& p, int grid, cudaStream_t s) {
+  constexpr int S = ModeCfg<MODE>::STAGES;
+  constexpr int OPS = ModeCfg<MODE>::SPLIT ? 2 : 1;
+  const size_t smem = (size_t)S * OPS * (A_BYTES + B_BYTES) + 1024;
+  auto kern = k_update_tc<MODE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(maps.m);
+  kern<<<grid, UPD_THREADS, smem, s>>>(m[0], m[1], m[2], m[3], p);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+static_assert(sizeof(CUtensorMap) == 128, "CUtensorMap layout");
+
+bool make_update_maps(UpdMaps* maps, const void* hi, const void* lo, int mode, int64_t cols, int64_t rows) {
+  CUtensorMap* m = reinterpret_cast<CUtensorMap*>(maps->m);
+  const bool bf16 = mode == UPD_BF16;
+  if (!encode_2d(&m[0], hi, bf16, cols, rows, A_ROWS)) return false;
+  if (!encode_2d(&m[1], hi, bf16, cols, rows, B_ROWS)) return false;
+  const void* l = lo ? lo : hi;
+  if (!encode_2d(&m[2], l, bf16, cols, rows, A_ROWS)) return false;
+  if (!encode_2d(&m[3], l, bf16, cols, rows, B_ROWS)) return false;
+  return true;
+}
+
+int64_t update_num_super(int64_t N, int64_t j0, int64_t j1) {
+  const int64_t SR = (N - j0 + SUPER - 1) / SUPER;
+  const int64_t SC = (j1 - j0 + SUPER - 1) / SUPER;
+  if (SR <= 0 || SC <= 0) return 0;
+  if (SR <= SC) return SR * (SR + 1) / 2;
+  return SC * (SC + 1) / 2 + (SR - SC) * SC;
+}
+
+cudaError_t launch_update_tc(const UpdMaps& maps, UpdParams p, int mode, int grid, cudaStream_t s) {
+  p.super_cols = (p.j1 - p.j0 + SUPER - 1) / SUPER;
+  p.n_super = update_num_super(p.N, p.j0, p.j1);
+  if (p.n_super <= 0 || p.kc_hi <= p.kc_lo) return cudaSuccess;
+  const int64_t ntasks = p.n_super * (SUPER * SUPER / 2);
+  if ((int64_t)grid > ntasks) grid = (int)ntasks;
+  switch (mode) {
+    case UPD_TF32X3: return launch_mode<UPD_TF32X3>(maps, p, grid, s);
+    case UPD_TF32: return launch_mode<UPD_TF32>(maps, p, grid, s);
+    case UPD_BF16: return launch_mode<UPD_BF16>(maps, p, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace mag

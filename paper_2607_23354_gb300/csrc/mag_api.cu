@@ -23,6 +23,8 @@
 
 using namespace mag;
 
+std::atomic<long long> mag::g_kernel_launches{0};
+
 namespace {
 
 struct Layout {
@@ -30,7 +32,9 @@ struct Layout {
   int chunks = 1;
   bool f32 = false, f64 = false;
   size_t off_zf = 0, off_zd = 0, off_dinvf = 0, off_dinvd = 0, off_vec = 0, off_part = 0,
-         off_status = 0, total = 0;
+         off_status = 0, off_panel = 0, total = 0;
+  int nb = 8;          // panel width in tiles
+  int64_t W = 0;       // panel width in columns (nb * TILE)
 };
 
 constexpr int NVEC_D = 6;   // FP64 vectors of np entries
@@ -53,6 +57,12 @@ struct mag_ctx {
   int sm_count = 152;
   double* aux = nullptr;  // vectors that must survive workspace re-plans
   int64_t aux_np = 0;
+  std::vector<cudaEvent_t> prof_ev;  // event pairs around trailing-update launches
+  int prof_used = 0;
+  UpdMaps maps;                      // TMA descriptors of the panel buffer
+  const void* maps_base = nullptr;
+  int maps_mode = -1;
+  int64_t maps_W = 0, maps_np = 0;
 
   // typed views of the workspace
   float* zf() { return (float*)((char*)ws + lay.off_zf); }
@@ -64,6 +74,8 @@ struct mag_ctx {
     return (float*)((double*)((char*)ws + lay.off_vec) + (size_t)NVEC_D * lay.np) + (size_t)i * lay.np;
   }
   double* part() { return (double*)((char*)ws + lay.off_part); }
+  float* panel_hi() { return (float*)((char*)ws + lay.off_panel); }
+  float* panel_lo() { return panel_hi() + (size_t)lay.np * lay.W; }
   DevStatus* st() { return (DevStatus*)((char*)ws + lay.off_status); }
 };
 
@@ -124,6 +136,10 @@ Layout plan(const mag_ctx* ctx, int64_t n, bool f32, bool f64) {
   off = align_up(off + (size_t)L.np * (NVEC_D * sizeof(double) + NVEC_F * sizeof(float)));
   L.off_part = off;
   off = align_up(off + (size_t)3 * L.chunks * L.np * sizeof(double));
+  L.nb = ctx->opt.panel_tiles > 0 ? ctx->opt.panel_tiles : 8;
+  L.W = (int64_t)L.nb * TILE;
+  L.off_panel = off;
+  if (f32) off = align_up(off + (size_t)L.np * L.W * 2 * sizeof(float));  // hi + lo copies
   L.off_dinvf = off;
   if (f32) off = align_up(off + (size_t)2 * L.N * TILE_ELEMS * sizeof(float));
   L.off_dinvd = off;
@@ -215,14 +231,117 @@ int check_args(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double 
 }
 
 // ---------------------------------------------------------------- factor
+// Optional CUDA-event timing of the trailing-update launches (profile = 1).
+int prof_begin(mag_ctx* ctx) {
+  if (!ctx->opt.profile) return MAG_OK;
+  const size_t need = 2 * (size_t)(ctx->prof_used + 1);
+  while (ctx->prof_ev.size() < need) {
+    cudaEvent_t e;
+    CU(cudaEventCreate(&e));
+    ctx->prof_ev.push_back(e);
+  }
+  CU(cudaEventRecord(ctx->prof_ev[2 * ctx->prof_used], ctx->stream));
+  return MAG_OK;
+}
+int prof_end(mag_ctx* ctx) {
+  if (!ctx->opt.profile) return MAG_OK;
+  CU(cudaEventRecord(ctx->prof_ev[2 * ctx->prof_used + 1], ctx->stream));
+  ctx->prof_used++;
+  return MAG_OK;
+}
+// Sum of the recorded intervals (after the stream has been synchronized).
+double prof_collect(mag_ctx* ctx) {
+  double ms = 0;
+  for (int i = 0; i < ctx->prof_used; ++i) {
+    float v = 0;
+    if (cudaEventElapsedTime(&v, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]) == cudaSuccess) ms += v;
+  }
+  ctx->prof_used = 0;
+  return ms;
+}
+
+// Algorithmic flops of C_IJ -= sum_k L_Ik L_Jk^T over the tiles J in [j0, j1),
+// I in [J, N), k in [k0, k1): 2 * 128^3 per (output tile, k tile).
+double update_flops(int64_t N, int64_t k0, int64_t k1, int64_t j0, int64_t j1) {
+  const double tiles = (double)((N - j0) * (N - j0 + 1) / 2 - (N - j1) * (N - j1 + 1) / 2);
+  return tiles * (double)(k1 - k0) * 2.0 * TILE * TILE * TILE;
+}
+
 template <typename T>
-int factor_blocked(mag_ctx* ctx, T* Z, T* Dinv) {
+int factor_blocked(mag_ctx* ctx, T* Z, T* Dinv, int* launches, double* flops) {
   const Layout& L = ctx->lay;
   cudaStream_t s = ctx->stream;
   for (int64_t K = 0; K < L.N; ++K) {
     CU(launch_potrf_diag<T>(Z, Dinv, K, L.n, ctx->st(), s));
     CU(launch_trsm_col<T>(Z, Dinv, K, L.N, ctx->st(), s));
-    CU(launch_syrk_simt<T>(Z, L.N, K, K + 1, K + 1, L.N, ctx->st(), s));
+    if (K + 1 < L.N) {
+      TRY(prof_begin(ctx));
+      CU(launch_syrk_simt<T>(Z, L.N, K, K + 1, K + 1, L.N, ctx->st(), s));
+      TRY(prof_end(ctx));
+      ++*launches;
+      *flops += update_flops(L.N, K, K + 1, K + 1, L.N);
+    }
+  }
+  return MAG_OK;
+}
+
+// Two-level blocked Cholesky with the trailing update on tensor cores.  For
+// each panel of nb tile columns [k0, k1): potrf + panel solve per column,
+// the column's split copy into the panel buffer, a rank-128 tensor-core update
+// of the remaining panel columns; then one tensor-core update of the whole
+// trailing matrix with K = (k1 - k0) * 128.
+int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
+  const Layout& L = ctx->lay;
+  cudaStream_t s = ctx->stream;
+  float* Z = ctx->zf();
+  float* Dinv = ctx->dinvf();
+  void* hi = ctx->panel_hi();
+  void* lo = ctx->panel_lo();
+  if (ctx->maps_base != hi || ctx->maps_mode != mode || ctx->maps_W != L.W || ctx->maps_np != L.np) {
+    if (!make_update_maps(&ctx->maps, hi, lo, mode, L.W, L.np))
+      return fail(ctx, MAG_ECUDA, "cuTensorMapEncodeTiled failed for the panel buffer");
+    ctx->maps_base = hi;
+    ctx->maps_mode = mode;
+    ctx->maps_W = L.W;
+    ctx->maps_np = L.np;
+  }
+  UpdParams up;
+  std::memset(&up, 0, sizeof up);
+  up.Z = Z;
+  up.N = L.N;
+  up.st = ctx->st();
+  up.timeout_ns = 20000000000ull;
+  for (int64_t k0 = 0; k0 < L.N; k0 += L.nb) {
+    const int64_t k1 = std::min<int64_t>(L.N, k0 + L.nb);
+    up.k0 = k0;
+    for (int64_t K = k0; K < k1; ++K) {
+      CU(launch_potrf_diag<float>(Z, Dinv, K, L.n, ctx->st(), s));
+      CU(launch_trsm_col<float>(Z, Dinv, K, L.N, ctx->st(), s));
+      if (K + 1 >= L.N) continue;
+      CU(launch_split_col(Z, K, L.N, k0, L.W, mode, hi, lo, s));
+      if (K + 1 < k1) {
+        up.kc_lo = (int)(K - k0);
+        up.kc_hi = up.kc_lo + 1;
+        up.j0 = K + 1;
+        up.j1 = k1;
+        TRY(prof_begin(ctx));
+        CU(launch_update_tc(ctx->maps, up, mode, ctx->sm_count, s));
+        TRY(prof_end(ctx));
+        ++*launches;
+        *flops += update_flops(L.N, K, K + 1, K + 1, k1);
+      }
+    }
+    if (k1 < L.N) {
+      up.kc_lo = 0;
+      up.kc_hi = (int)(k1 - k0);
+      up.j0 = k1;
+      up.j1 = L.N;
+      TRY(prof_begin(ctx));
+      CU(launch_update_tc(ctx->maps, up, mode, ctx->sm_count, s));
+      TRY(prof_end(ctx));
+      ++*launches;
+      *flops += update_flops(L.N, k0, k1, k1, L.N);
+    }
   }
   return MAG_OK;
 }
@@ -298,6 +417,7 @@ int mag_ctx_destroy(mag_ctx* ctx) {
   if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->aux) cudaFree(ctx->aux);
+  for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
   for (int i = 0; i < 4; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   if (ctx->h_st) cudaFreeHost(ctx->h_st);
@@ -349,6 +469,8 @@ struct SolveResult {
   int prec_used = 0, ir_iters = 0, gmres_iters = 0, fallback = 0;
   double rel = INFINITY, znorm = 0, wnorm = 0, gersh = 0, dmin = 0;
   double ms_gen = 0, ms_fac = 0, ms_solve = 0, ms_res = 0;
+  int residual_evals = 0, update_launches = 0;
+  double ms_update = 0, update_flops = 0;
 };
 
 float elapsed(mag_ctx* ctx, int a, int b) {
@@ -382,13 +504,20 @@ int generate(mag_ctx* ctx, const double* X, int32_t m, double t, bool f32, bool 
 int run_factor(mag_ctx* ctx, int prec, SolveResult* R) {
   cudaStream_t s = ctx->stream;
   CU(cudaEventRecord(ctx->ev[0], s));
+  ctx->prof_used = 0;
   if (prec == MAG_PREC_FP64)
-    TRY(factor_blocked<double>(ctx, ctx->zd(), ctx->dinvd()));
+    TRY(factor_blocked<double>(ctx, ctx->zd(), ctx->dinvd(), &R->update_launches, &R->update_flops));
+  else if (prec == MAG_PREC_FP32)
+    TRY(factor_blocked<float>(ctx, ctx->zf(), ctx->dinvf(), &R->update_launches, &R->update_flops));
   else
-    TRY(factor_blocked<float>(ctx, ctx->zf(), ctx->dinvf()));
+    TRY(factor_tc(ctx, prec == MAG_PREC_BF16 ? UPD_BF16 : (prec == MAG_PREC_TF32 ? UPD_TF32 : UPD_TF32X3),
+                  &R->update_launches, &R->update_flops));
   CU(cudaEventRecord(ctx->ev[1], s));
   TRY(read_status(ctx));
   R->ms_fac += elapsed(ctx, 0, 1);
+  R->ms_update += prof_collect(ctx);
+  if (ctx->h_st->flags & ST_TIMEOUT)
+    return fail(ctx, MAG_ETIMEOUT, "a bounded device wait in the tensor-core update expired");
   if (ctx->h_st->flags & ST_NOTPD)
     return fail(ctx, MAG_ENOTPD, "non-positive pivot at row %d (precision %d)", ctx->h_st->notpd_index - 1,
                 prec);
@@ -432,6 +561,7 @@ int residual(mag_ctx* ctx, const double* X, int32_t m, double t, const double* w
   CU(cudaEventRecord(ctx->ev[1], s));
   TRY(read_status(ctx));
   R->ms_res += elapsed(ctx, 0, 1);
+  R->residual_evals++;
   const double rn = bits_to_double(ctx->h_st->r_max_bits);
   const double zn = bits_to_double(ctx->h_st->z_max_bits);
   const double wn = bits_to_double(ctx->h_st->w_max_bits);
@@ -454,9 +584,10 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
   bool f32 = prec != MAG_PREC_FP64;
   TRY(ensure_workspace(ctx, n, f32, f64));
   TRY(generate(ctx, X, m, t, f32, f64, R));
-  if (prec == MAG_PREC_AUTO) prec = MAG_PREC_FP32;
-  // Tensor-core precisions run on the FP32 tile path.
-  if (prec == MAG_PREC_BF16 || prec == MAG_PREC_TF32 || prec == MAG_PREC_TF32X3) prec = MAG_PREC_FP32;
+  // AUTO: BF16 products when the Gershgorin bound keeps lambda_min(Z) >= 1/2
+  // (then kappa(Z) <= 2 ||Z|| and a BF16 factor still contracts refinement),
+  // else split TF32.
+  if (prec == MAG_PREC_AUTO) prec = R->gersh >= 0.5 ? MAG_PREC_BF16 : MAG_PREC_TF32X3;
 
   cudaStream_t s = ctx->stream;
   double overall = INFINITY;
@@ -538,6 +669,10 @@ void fill_info(mag_ctx* ctx, const SolveResult& R, int64_t n, mag_info* info) {
   info->ms_residual = R.ms_res;
   const double nn = (double)n;
   info->useful_flops = nn * nn * nn / 3.0 + 2.0 * nn * nn * (double)R.ir_iters;
+  info->residual_evals = R.residual_evals;
+  info->update_launches = R.update_launches;
+  info->ms_update = R.ms_update;
+  info->update_flops = R.update_flops;
 }
 
 }  // namespace
@@ -568,8 +703,7 @@ int mag_cholesky_factor(mag_ctx* ctx, const double* points, int64_t n, int32_t m
   if (!L_out) return fail(ctx, MAG_EINVAL, "NULL output");
   ctx->err.clear();
   const bool f64 = precision == MAG_PREC_FP64;
-  int prec = f64 ? MAG_PREC_FP64 : (precision == MAG_PREC_AUTO ? MAG_PREC_FP32 : precision);
-  if (prec == MAG_PREC_BF16 || prec == MAG_PREC_TF32 || prec == MAG_PREC_TF32X3) prec = MAG_PREC_FP32;
+  int prec = f64 ? MAG_PREC_FP64 : (precision == MAG_PREC_AUTO ? MAG_PREC_TF32X3 : precision);
   SolveResult R;
   TRY(ensure_workspace(ctx, n, !f64, f64));
   TRY(generate(ctx, points, m, t, !f64, f64, &R));
@@ -590,6 +724,7 @@ int mag_solve(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t
   ctx->err.clear();
   if (info) std::memset(info, 0, sizeof *info);
   SolveResult R;
+  const long long l0 = g_kernel_launches.load();
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
@@ -612,6 +747,7 @@ int mag_solve(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t
     float ms = 0;
     cudaEventElapsedTime(&ms, t0, t1);
     info->ms_total = ms;
+    info->kernel_launches = g_kernel_launches.load() - l0;
   }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);

@@ -16,7 +16,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace mag {
+
+// Number of kernels enqueued by this library (all contexts), for the
+// per-call kernel_launches diagnostic.
+extern std::atomic<long long> g_kernel_launches;
+inline void note_launch(long long k = 1) { g_kernel_launches.fetch_add(k, std::memory_order_relaxed); }
 
 constexpr int TILE = 128;
 constexpr int64_t TILE_ELEMS = (int64_t)TILE * TILE;
@@ -87,6 +94,37 @@ cudaError_t launch_syrk_simt(T* Z, int64_t N, int64_t k0, int64_t k1, int64_t j0
 // Dense n x n row-major copy of the packed tiles: symmetric (Z) or lower (L).
 template <typename T>
 cudaError_t launch_unpack(const T* Z, int64_t n, int64_t N, bool symmetric, T* out, cudaStream_t s);
+
+// K2c on tensor cores (k_update_tc.cu).  Product kinds of the trailing update.
+enum UpdMode { UPD_TF32X3 = 0, UPD_TF32 = 1, UPD_BF16 = 2 };
+
+struct UpdParams {
+  float* Z;            // packed FP32 tiles (updated in place)
+  int64_t N;           // tiles per side
+  int64_t k0;          // first tile column of the panel = row block 0 of the panel buffer
+  int kc_lo, kc_hi;    // K range in panel-local tile columns [kc_lo, kc_hi)
+  int64_t j0, j1;      // output tile columns [j0, j1); rows I in [J, N)
+  int64_t n_super;     // filled by launch_update_tc
+  int64_t super_cols;  // filled by launch_update_tc
+  DevStatus* st;
+  uint64_t timeout_ns; // bound on every barrier wait inside the kernel
+};
+
+// Four TMA descriptors (A/B boxes of the hi and lo panel copies), 128 B each.
+struct alignas(64) UpdMaps {
+  unsigned char m[4][128];
+};
+
+bool make_update_maps(UpdMaps* maps, const void* hi, const void* lo, int mode, int64_t cols, int64_t rows);
+int64_t update_num_super(int64_t N, int64_t j0, int64_t j1);
+cudaError_t launch_update_tc(const UpdMaps& maps, UpdParams p, int mode, int grid, cudaStream_t s);
+
+// Panel copy of column K (tiles I in (K, N)) for the tensor-core update:
+// row (I - k0)*TILE + r, column (K - k0)*TILE + c of the row-major panel
+// buffer with `width` columns.  TF32X3: hi = rna_tf32(x), lo = rna_tf32(x - hi);
+// TF32: hi only; BF16: round-to-nearest BF16 into hi (as 16-bit words).
+cudaError_t launch_split_col(const float* Z, int64_t K, int64_t N, int64_t k0, int64_t width, int mode,
+                             void* hi, void* lo, cudaStream_t s);
 
 // K3: triangular solves with the packed factor, in place on v (np = N*TILE
 // entries of type T).  tmp: np entries of scratch.
