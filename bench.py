@@ -45,7 +45,7 @@ def parse_args():
     p.add_argument("--m", type=int, default=8)
     p.add_argument("--ts", default="1,10,bound", help="comma list of t values; 'bound' = log(n-1)/min d")
     p.add_argument("--precision", default="auto")
-    p.add_argument("--resid", default="matrix_free", choices=["matrix_free", "stored"])
+    p.add_argument("--resid", default="auto", choices=["auto", "matrix_free", "stored"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--extras", action="store_true", help="also time sweep/grad/batch/FP64 comparators")

@@ -64,12 +64,14 @@ enum mag_precision {
 /* How the FP64 residual r = 1 - Zw of iterative refinement is formed. */
 enum mag_residual_mode {
   MAG_RESID_MATRIX_FREE = 0, /* Z_jk regenerated in FP64 from the points      */
-  MAG_RESID_STORED = 1       /* Z kept in FP64 tiles, residual reads them      */
+  MAG_RESID_STORED = 1,      /* Z kept in FP64 tiles, residual reads them      */
+  MAG_RESID_AUTO = 2         /* STORED when its extra n^2/2 FP64 tiles fit in
+                                half of the free device memory, else MATRIX_FREE */
 };
 
 typedef struct mag_options {
   int32_t precision;      /* enum mag_precision, default MAG_PREC_AUTO           */
-  int32_t residual_mode;  /* enum mag_residual_mode, default MATRIX_FREE         */
+  int32_t residual_mode;  /* enum mag_residual_mode, default MAG_RESID_AUTO      */
   double ir_tol;          /* target ||1-Zw||inf/(||Z||inf ||w||inf), default 1e-14 */
   int32_t ir_max_iters;   /* refinement steps before escalating, default 12     */
   int32_t gmres_max_iters;/* inner GMRES iterations of GMRES-IR, default 30     */
@@ -86,6 +88,8 @@ typedef struct mag_info {
   int32_t ir_iters;        /* refinement steps taken (all precisions)          */
   int32_t gmres_iters;     /* total inner GMRES iterations (0 if not used)     */
   int32_t fallback;        /* 0 none, 1 GMRES-IR, 2 FP64 factor                */
+  int32_t residual_mode;   /* enum mag_residual_mode actually used (0 or 1)    */
+  int32_t reserved0;
   double rel_residual;     /* final ||1-Zw||inf / (||Z||inf ||w||inf)          */
   double z_norm_inf;       /* ||Z||inf = max row sum                           */
   double w_norm_inf;       /* max |w_j|                                       */
@@ -159,6 +163,16 @@ int mag_solve(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t
  * for the adjoint solve lambda = Z^{-1} dL/dw of mag_grad. */
 int mag_solve_rhs(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t,
                   const double* b, double* x, mag_info* info);
+
+/* a5 (accuracy measure of "numerically exact", Sec. 1): the FP64 residual
+ * r = b - Z w with Z = exp[-t d] regenerated from the points on the fly (no
+ * n x n storage), row sums compensated.  points: device n x m; w: device n;
+ * b: device n, or NULL for the all-ones right-hand side of Eq. weighting;
+ * r_out: device n, or NULL if only the norms are wanted.  norms (host, 4
+ * doubles): ||r||inf / (||Z||inf ||w||inf), ||r||inf, ||Z||inf (max row
+ * sum), ||w||inf. */
+int mag_residual(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t, const double* w,
+                 const double* b, double* r_out, double* norms);
 
 /* a8 (Sec. 2 and its footnote): bisection for the cutoff t_+ on the sign of
  * min_j w_j.  feasible(t) <=> min_j w_j(t) >= 0.  t_hi <= 0 uses the Sec. 1

@@ -31,7 +31,7 @@ PREC_AUTO, PREC_BF16, PREC_TF32, PREC_TF32X3, PREC_FP32, PREC_FP64 = range(6)
 PRECISIONS = {"auto": PREC_AUTO, "bf16": PREC_BF16, "tf32": PREC_TF32, "tf32x3": PREC_TF32X3,
               "fp32": PREC_FP32, "fp64": PREC_FP64}
 # enum mag_residual_mode
-RESID_MATRIX_FREE, RESID_STORED = 0, 1
+RESID_MATRIX_FREE, RESID_STORED, RESID_AUTO = 0, 1, 2
 
 
 class mag_options(ctypes.Structure):
@@ -45,6 +45,7 @@ class mag_options(ctypes.Structure):
 class mag_info(ctypes.Structure):
     _fields_ = [("precision_used", ctypes.c_int32), ("ir_iters", ctypes.c_int32),
                 ("gmres_iters", ctypes.c_int32), ("fallback", ctypes.c_int32),
+                ("residual_mode", ctypes.c_int32), ("reserved0", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double), ("z_norm_inf", ctypes.c_double),
                 ("w_norm_inf", ctypes.c_double), ("min_w", ctypes.c_double),
                 ("gershgorin_lmin", ctypes.c_double), ("min_distance", ctypes.c_double),
@@ -82,6 +83,7 @@ SIGNATURES = {
     "mag_cholesky_factor": (ctypes.c_int, [_P, _P, _I64, _I32, _D, _I32, _P]),
     "mag_solve": (ctypes.c_int, [_P, _P, _I64, _I32, _D, _P, _DP, ctypes.POINTER(mag_info)]),
     "mag_solve_rhs": (ctypes.c_int, [_P, _P, _I64, _I32, _D, _P, _P, ctypes.POINTER(mag_info)]),
+    "mag_residual": (ctypes.c_int, [_P, _P, _I64, _I32, _D, _P, _P, _P, _DP]),
     "mag_sweep_tplus": (ctypes.c_int, [_P, _P, _I64, _I32, _D, _D, _D, _DP, _DP, _P, _DP,
                                        ctypes.POINTER(mag_info)]),
     "mag_grad": (ctypes.c_int, [_P, _P, _I64, _I32, _D, _P, _P, _DP, _P, ctypes.POINTER(mag_info)]),
@@ -125,7 +127,7 @@ def status_string(status: int) -> str:
 class Options:
     """Solver options (see struct mag_options)."""
     precision: str = "auto"
-    residual_mode: str = "matrix_free"
+    residual_mode: str = "auto"
     ir_tol: float = 1e-14
     ir_max_iters: int = 12
     gmres_max_iters: int = 30
@@ -138,7 +140,8 @@ class Options:
         o = mag_options()
         load_library().mag_options_default(ctypes.byref(o))
         o.precision = PRECISIONS[self.precision]
-        o.residual_mode = {"matrix_free": RESID_MATRIX_FREE, "stored": RESID_STORED}[self.residual_mode]
+        o.residual_mode = {"matrix_free": RESID_MATRIX_FREE, "stored": RESID_STORED,
+                           "auto": RESID_AUTO}[self.residual_mode]
         o.ir_tol = self.ir_tol
         o.ir_max_iters = self.ir_max_iters
         o.gmres_max_iters = self.gmres_max_iters
@@ -251,6 +254,20 @@ class Context:
         self._check(self._lib.mag_solve_rhs(self._h, _P(X.data_ptr()), n, m, float(t), _P(b.data_ptr()),
                                             _P(x.data_ptr()), ctypes.byref(info)))
         return x, info.as_dict()
+
+    def residual(self, X: torch.Tensor, t: float, w: torch.Tensor, b: torch.Tensor | None = None,
+                 want_r: bool = True):
+        """r = b - Z w in FP64 (Z regenerated); returns (r or None, norms dict)."""
+        X = self._points(X)
+        n, m = X.shape
+        w = w.to(device=self.device, dtype=torch.float64).contiguous()
+        bb = None if b is None else b.to(device=self.device, dtype=torch.float64).contiguous()
+        r = torch.empty(n, dtype=torch.float64, device=self.device) if want_r else None
+        nr = (ctypes.c_double * 4)()
+        self._check(self._lib.mag_residual(self._h, _P(X.data_ptr()), n, m, float(t), _P(w.data_ptr()),
+                                           _P(0) if bb is None else _P(bb.data_ptr()),
+                                           _P(0) if r is None else _P(r.data_ptr()), ctypes.cast(nr, _DP)))
+        return r, {"rel_residual": nr[0], "r_norm_inf": nr[1], "z_norm_inf": nr[2], "w_norm_inf": nr[3]}
 
     def sweep_tplus(self, X: torch.Tensor, t_lo: float = 1e-3, t_hi: float = 0.0, rel_tol: float = 1e-6):
         X = self._points(X)

@@ -34,83 +34,84 @@ __device__ inline double tsqrt<double>(double x) { return sqrt(x); }
 constexpr int LDA = TILE + 1;  // padded shared-memory row stride
 
 // ------------------------------------------------------------------ potrf
+// One CTA, the diagonal tile in shared memory (row stride LDA).
+//
+// Factor: elimination on unscaled columns, one barrier per step:
+//   step c: p = A[c][c];  A[r][cc] -= A[r][c] A[cc][c] / p  for c < cc <= r,
+// which only reads column c (final after step c-1) and writes columns > c, so
+// no second barrier is needed; afterwards L[r][c] = A[r][c] / sqrt(p_c).
+// Inverse Y = inv(L): right-looking sweep over rows, one barrier per step, on
+// T = I - (partial sums), kept transposed in the strict upper triangle
+// (T[i][c] at A[c][i]) with its diagonal at A[i][i]:
+//   step k: y_kc = T[k][c] / L[k][k];  T[i][c] -= L[i][k] y_kc  for i > k, c <= k,
+// and Y[k][c] = T[k][c] / L[k][k] at the end.
 template <typename T>
 __global__ void __launch_bounds__(512) k_potrf_diag(T* __restrict__ Z, T* __restrict__ Dinv,
                                                     T* __restrict__ DinvT, int64_t K, int64_t n,
                                                     DevStatus* st) {
   extern __shared__ unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);  // [TILE][LDA]
-  __shared__ int failed, skip;
-  if (threadIdx.x == 0) {
-    failed = 0;
-    skip = (st->flags & (ST_NOTPD | ST_NONFINITE | ST_DUPLICATE)) != 0;  // set by earlier kernels
-  }
+  __shared__ T ldiag[TILE], linv[TILE];
+  __shared__ int skip;
+  const int tid = threadIdx.x;
+  if (tid == 0) skip = (st->flags & (ST_NOTPD | ST_NONFINITE | ST_DUPLICATE)) != 0;  // set by earlier kernels
   __syncthreads();
   if (skip) return;  // uniform across the CTA
   T* tile = Z + tri_index(K, K) * TILE_ELEMS;
-  for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
-    const int r = e / TILE, c = e % TILE;
-    A[r * LDA + c] = tile[e];
-  }
+  for (int e = tid; e < TILE * TILE; e += blockDim.x) A[(e / TILE) * LDA + (e % TILE)] = tile[e];
   __syncthreads();
-  for (int c = 0; c < TILE; ++c) {
-    if (threadIdx.x == 0) {
-      T p = A[c * LDA + c];
-      if (!(p > T(0))) {
-        if (!failed) {
-          failed = 1;
-          atomicOr(&st->flags, ST_NOTPD);
-          atomicCAS(&st->notpd_index, 0, (int)(K * TILE + c + 1));
-        }
-        p = T(1);
-      }
-      A[c * LDA + c] = tsqrt(p);
-    }
-    __syncthreads();
-    const T inv = T(1) / A[c * LDA + c];
-    for (int r = c + 1 + threadIdx.x; r < TILE; r += blockDim.x) A[r * LDA + c] *= inv;
-    __syncthreads();
+  for (int c = 0; c < TILE - 1; ++c) {
+    const T p = A[c * LDA + c];
+    const T pinv = p > T(0) ? T(1) / p : T(0);
     const int w = TILE - 1 - c;  // trailing size
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+    for (int e = tid; e < w * w; e += blockDim.x) {
       const int r = c + 1 + e / w, cc = c + 1 + e % w;
-      if (cc <= r) A[r * LDA + cc] -= A[r * LDA + c] * A[cc * LDA + c];
+      if (cc <= r) A[r * LDA + cc] -= A[r * LDA + c] * A[cc * LDA + c] * pinv;
     }
     __syncthreads();
   }
-  // write L (zeros above the diagonal)
-  for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
-    const int r = e / TILE, c = e % TILE;
-    tile[e] = c <= r ? A[r * LDA + c] : T(0);
-  }
-  // inv(L): column c by forward substitution, one thread per column, values
-  // kept in the strict upper triangle of A (transposed) and the diagonal in
-  // a separate array.
-  __shared__ T ydiag[TILE];
-  if (threadIdx.x < TILE) {
-    const int c = threadIdx.x;
-    ydiag[c] = T(1) / A[c * LDA + c];
-  }
-  __syncthreads();
-  if (threadIdx.x < TILE) {
-    const int c = threadIdx.x;
-    // Y[r][c] for r > c stored at A[c][r] (strict upper, r > c)
-    for (int r = c + 1; r < TILE; ++r) {
-      T s = A[r * LDA + c] * ydiag[c];
-      for (int k = c + 1; k < r; ++k) s += A[r * LDA + k] * A[c * LDA + k];
-      A[c * LDA + r] = -s / A[r * LDA + r];
+  if (tid < TILE) {
+    const T p = A[tid * LDA + tid];
+    const bool bad = !(p > T(0));
+    const T d = bad ? T(1) : tsqrt(p);
+    ldiag[tid] = d;
+    linv[tid] = T(1) / d;
+    if (bad) {
+      atomicOr(&st->flags, ST_NOTPD);
+      atomicMin(&st->notpd_index, (int)(K * TILE + tid + 1));
     }
   }
   __syncthreads();
+  // scale columns: L[r][c] = A[r][c] / d_c (r > c); diagonal of A <- T = I
+  for (int e = tid; e < TILE * TILE; e += blockDim.x) {
+    const int r = e / TILE, c = e % TILE;
+    if (r > c) A[r * LDA + c] *= linv[c];
+    else if (r == c) A[r * LDA + c] = T(1);
+    else A[r * LDA + c] = T(0);  // T[c][r] = 0 initially (stored transposed)
+  }
+  __syncthreads();
+  // write L (zeros above the diagonal)
+  for (int e = tid; e < TILE * TILE; e += blockDim.x) {
+    const int r = e / TILE, c = e % TILE;
+    tile[e] = c < r ? A[r * LDA + c] : (c == r ? ldiag[r] : T(0));
+  }
+  for (int k = 0; k < TILE - 1; ++k) {
+    const int rows = TILE - 1 - k, cols = k + 1;
+    for (int e = tid; e < rows * cols; e += blockDim.x) {
+      const int i = k + 1 + e / cols, c = e % cols;
+      const T tkc = (c == k) ? A[k * LDA + k] : A[c * LDA + k];  // T[k][c]
+      A[c * LDA + i] -= A[i * LDA + k] * (tkc * linv[k]);         // T[i][c] (c < i)
+    }
+    __syncthreads();
+  }
   T* Y = Dinv + K * TILE_ELEMS;
   T* YT = DinvT + K * TILE_ELEMS;
-  for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
+  for (int e = tid; e < TILE * TILE; e += blockDim.x) {
     const int r = e / TILE, c = e % TILE;
-    // Y[r][c]: lower triangle of inv(L)
-    T y = r == c ? ydiag[r] : (c < r ? A[c * LDA + r] : T(0));
-    Y[e] = y;
+    // Y[r][c] = T[r][c] / L[r][r] (lower), T[r][c] at A[c][r] for c < r
+    Y[e] = c < r ? A[c * LDA + r] * linv[r] : (c == r ? linv[r] : T(0));
     // YT[r][c] = Y[c][r]
-    T yt = r == c ? ydiag[r] : (r < c ? A[r * LDA + c] : T(0));
-    YT[e] = yt;
+    YT[e] = r < c ? A[r * LDA + c] * linv[c] : (c == r ? linv[r] : T(0));
   }
 }
 

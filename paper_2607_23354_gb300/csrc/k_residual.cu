@@ -84,6 +84,67 @@ __global__ void __launch_bounds__(RES_THREADS) k_resid_mf(const double* __restri
   }
 }
 
+// Stored variant of K4: (Zw)_j from the packed FP64 tiles of Z (lower tiles,
+// diagonal tiles in full).  Block (I, chunk) owns rows I*128..+127; for each
+// tile column J of its chunk it uses tile (I, J) row-wise when J <= I (staged
+// through shared memory in 32-column slabs so that global reads are
+// coalesced) and tile (J, I) column-wise when J > I (already coalesced).
+// Same per-thread Kahan sums and partial layout as the matrix-free kernel.
+__global__ void __launch_bounds__(TILE) k_resid_stored(const double* __restrict__ Zd, int64_t n, int64_t N,
+                                                       const double* __restrict__ w,
+                                                       double* __restrict__ part, int chunks, int64_t np) {
+  __shared__ double slab[TILE][33];
+  __shared__ double wj[TILE];
+  const int r = threadIdx.x;
+  const int64_t I = blockIdx.x;
+  const int64_t per = (N + chunks - 1) / chunks;
+  const int64_t J0 = blockIdx.y * per, J1 = min(N, J0 + per);
+  double s = 0.0, c = 0.0, zs = 0.0;
+  for (int64_t J = J0; J < J1; ++J) {
+    __syncthreads();
+    const int64_t col = J * TILE + r;
+    wj[r] = col < n ? w[col] : 0.0;
+    if (J <= I) {
+      const double* tile = Zd + tri_index(I, J) * TILE_ELEMS;
+      for (int sl = 0; sl < TILE; sl += 32) {
+        __syncthreads();
+        for (int e = r; e < TILE * 32; e += TILE) {
+          const int rr = e >> 5, cc = e & 31;
+          slab[rr][cc] = tile[rr * TILE + sl + cc];
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int cc = 0; cc < 32; ++cc) {
+          const double z = slab[r][cc];
+          zs += z;
+          const double y = fma(z, wj[sl + cc], -c);
+          const double tt = s + y;
+          c = (tt - s) - y;
+          s = tt;
+        }
+      }
+    } else {
+      const double* tile = Zd + tri_index(J, I) * TILE_ELEMS;
+      __syncthreads();
+#pragma unroll 8
+      for (int cc = 0; cc < TILE; ++cc) {
+        const double z = tile[cc * TILE + r];
+        zs += z;
+        const double y = fma(z, wj[cc], -c);
+        const double tt = s + y;
+        c = (tt - s) - y;
+        s = tt;
+      }
+    }
+  }
+  const int64_t j = I * TILE + r;
+  if (j < n) {
+    part[((int64_t)0 * chunks + blockIdx.y) * np + j] = s;
+    part[((int64_t)1 * chunks + blockIdx.y) * np + j] = -c;
+    part[((int64_t)2 * chunks + blockIdx.y) * np + j] = zs;
+  }
+}
+
 // Combine the chunk partials of each row (Neumaier), r_j = b_j - (Zw)_j, and
 // the three infinity norms.  Rows n <= j < np get r_j = 0.
 __global__ void k_resid_finish(const double* __restrict__ part, int chunks, int64_t n, int64_t np,
@@ -316,6 +377,18 @@ cudaError_t launch_residual_mf(const double* X, int64_t n, int m, double t, cons
     k_resid_mf<32><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct);
   else
     k_resid_mf<0><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_resid_finish<<<blocks_for(np, 256), 256, 0, s>>>(part, chunks, n, np, w, b, r, st);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_stored(const double* Zd, int64_t n, int64_t N, const double* w,
+                                   const double* b, double* r, double* part, int chunks, int64_t np,
+                                   DevStatus* st, cudaStream_t s) {
+  k_resid_stored<<<dim3((unsigned)N, (unsigned)chunks), TILE, 0, s>>>(Zd, n, N, w, part, chunks, np);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

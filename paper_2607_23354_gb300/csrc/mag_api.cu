@@ -32,7 +32,7 @@ struct Layout {
   int chunks = 1;
   bool f32 = false, f64 = false;
   size_t off_zf = 0, off_zd = 0, off_dinvf = 0, off_dinvd = 0, off_vec = 0, off_part = 0,
-         off_status = 0, off_panel = 0, total = 0;
+         off_status = 0, off_panel = 0, off_flags = 0, total = 0;
   int nb = 8;          // panel width in tiles
   int64_t W = 0;       // panel width in columns (nb * TILE)
 };
@@ -77,6 +77,7 @@ struct mag_ctx {
   float* panel_hi() { return (float*)((char*)ws + lay.off_panel); }
   float* panel_lo() { return panel_hi() + (size_t)lay.np * lay.W; }
   DevStatus* st() { return (DevStatus*)((char*)ws + lay.off_status); }
+  unsigned* flags() { return (unsigned*)((char*)ws + lay.off_flags); }
 };
 
 // FP64 vector slots
@@ -132,6 +133,8 @@ Layout plan(const mag_ctx* ctx, int64_t n, bool f32, bool f64) {
   size_t off = 0;
   L.off_status = off;
   off = align_up(off + sizeof(DevStatus));
+  L.off_flags = off;
+  off = align_up(off + (size_t)L.N * sizeof(unsigned));
   L.off_vec = off;
   off = align_up(off + (size_t)L.np * (NVEC_D * sizeof(double) + NVEC_F * sizeof(float)));
   L.off_part = off;
@@ -202,6 +205,7 @@ int reset_status(mag_ctx* ctx) {
   std::memset(&init, 0, sizeof init);
   const double inf = INFINITY;
   std::memcpy(&init.min_d2_bits, &inf, sizeof inf);
+  init.notpd_index = 0x7fffffff;  // atomicMin target
   *ctx->h_st = init;
   CU(cudaMemcpyAsync(ctx->st(), ctx->h_st, sizeof(DevStatus), cudaMemcpyHostToDevice, ctx->stream));
   return MAG_OK;
@@ -370,7 +374,7 @@ int mag_options_default(mag_options* opt) {
   if (!opt) return MAG_EINVAL;
   std::memset(opt, 0, sizeof *opt);
   opt->precision = MAG_PREC_AUTO;
-  opt->residual_mode = MAG_RESID_MATRIX_FREE;
+  opt->residual_mode = MAG_RESID_AUTO;
   opt->ir_tol = 1e-14;
   opt->ir_max_iters = 12;
   opt->gmres_max_iters = 30;
@@ -431,7 +435,7 @@ int mag_workspace_bytes(const mag_ctx* ctx, int64_t n, int32_t m, double* bytes)
   (void)m;
   if (!ctx || !bytes || n < 1) return MAG_EINVAL;
   const int prec = ctx->opt.precision;
-  const bool f64 = prec == MAG_PREC_FP64 || ctx->opt.residual_mode == MAG_RESID_STORED;
+  const bool f64 = prec == MAG_PREC_FP64 || ctx->opt.residual_mode != MAG_RESID_MATRIX_FREE;
   const bool f32 = prec != MAG_PREC_FP64;
   *bytes = (double)plan(ctx, n, f32, f64).total;
   return MAG_OK;
@@ -470,6 +474,7 @@ struct SolveResult {
   double rel = INFINITY, znorm = 0, wnorm = 0, gersh = 0, dmin = 0;
   double ms_gen = 0, ms_fac = 0, ms_solve = 0, ms_res = 0;
   int residual_evals = 0, update_launches = 0;
+  bool stored = false;
   double ms_update = 0, update_flops = 0;
 };
 
@@ -531,8 +536,8 @@ int correction_t(mag_ctx* ctx, T* Z, T* Dinv, T* v, T* y, const double* r, doubl
   const Layout& L = ctx->lay;
   cudaStream_t s = ctx->stream;
   CU(launch_scale_rhs<T>(r, L.n, L.np, v, ctx->st(), s));
-  CU(launch_forward<T>(Z, Dinv, L.N, v, y, s));
-  CU(launch_backward<T>(Z, Dinv, L.N, y, v, s));
+  CU(launch_forward_persistent<T>(Z, Dinv, L.N, v, y, ctx->flags(), ctx->st(), s));
+  CU(launch_backward_persistent<T>(Z, Dinv, L.N, y, v, ctx->flags(), ctx->st(), s));
   CU(launch_accumulate<T>(x, v, L.n, ctx->st(), init, s));
   return MAG_OK;
 }
@@ -552,12 +557,15 @@ int correction(mag_ctx* ctx, int prec, const double* r, double* x, bool init, So
 
 // Residual r = b - Zw and the norms; returns relres through *rel.
 int residual(mag_ctx* ctx, const double* X, int32_t m, double t, const double* w, const double* b,
-             double* r, double* rel, SolveResult* R) {
+             double* r, double* rel, bool stored, SolveResult* R) {
   const Layout& L = ctx->lay;
   cudaStream_t s = ctx->stream;
   TRY(reset_norms(ctx));
   CU(cudaEventRecord(ctx->ev[0], s));
-  CU(launch_residual_mf(X, L.n, m, t, w, b, r, ctx->part(), L.chunks, L.np, ctx->st(), s));
+  if (stored)
+    CU(launch_residual_stored(ctx->zd(), L.n, L.N, w, b, r, ctx->part(), L.chunks, L.np, ctx->st(), s));
+  else
+    CU(launch_residual_mf(X, L.n, m, t, w, b, r, ctx->part(), L.chunks, L.np, ctx->st(), s));
   CU(cudaEventRecord(ctx->ev[1], s));
   TRY(read_status(ctx));
   R->ms_res += elapsed(ctx, 0, 1);
@@ -579,7 +587,20 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
                double* x, SolveResult* R) {
   const mag_options& o = ctx->opt;
   int prec = o.precision;
-  const bool stored = o.residual_mode == MAG_RESID_STORED;
+  bool stored = o.residual_mode == MAG_RESID_STORED;
+  if (o.residual_mode == MAG_RESID_AUTO && prec != MAG_PREC_FP64) {
+    // Stored FP64 tiles cost one FP64 exp per pair once instead of once per
+    // refinement step; use them when they fit comfortably.
+    size_t fre = 0, tot = 0;
+    const Layout with = plan(ctx, n, true, true);
+    if (cudaMemGetInfo(&fre, &tot) == cudaSuccess) {
+      const double avail = (double)fre + (double)ctx->ws_bytes;
+      stored = (double)with.total <= 0.5 * avail;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  R->stored = stored;
   bool f64 = prec == MAG_PREC_FP64 || stored;
   bool f32 = prec != MAG_PREC_FP64;
   TRY(ensure_workspace(ctx, n, f32, f64));
@@ -616,7 +637,8 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
       double rel = INFINITY, prev = INFINITY;
       int slow = 0;
       for (int it = 0;; ++it) {
-        TRY(residual(ctx, X, m, t, xw, b, r, &rel, R));
+        // The FP64 factor overwrites the FP64 tiles, so it refines matrix free.
+        TRY(residual(ctx, X, m, t, xw, b, r, &rel, stored && prec != MAG_PREC_FP64, R));
         if (rel < best_rel) {
           best_rel = rel;
           CU(cudaMemcpyAsync(best, xw, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -657,6 +679,7 @@ void fill_info(mag_ctx* ctx, const SolveResult& R, int64_t n, mag_info* info) {
   info->ir_iters = R.ir_iters;
   info->gmres_iters = R.gmres_iters;
   info->fallback = R.fallback;
+  info->residual_mode = R.stored ? MAG_RESID_STORED : MAG_RESID_MATRIX_FREE;
   info->rel_residual = R.rel;
   info->z_norm_inf = R.znorm;
   info->w_norm_inf = R.wnorm;
@@ -764,6 +787,30 @@ int mag_solve_rhs(mag_ctx* ctx, const double* points, int64_t n, int32_t m, doub
   int st = solve_impl(ctx, points, n, m, t, b, x, &R);
   fill_info(ctx, R, n, info);
   return st;
+}
+
+int mag_residual(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t, const double* w,
+                 const double* b, double* r_out, double* norms) {
+  TRY(check_args(ctx, points, n, m, t));
+  if (!w || !norms) return fail(ctx, MAG_EINVAL, "NULL w or norms");
+  ctx->err.clear();
+  if (!ctx->ws || ctx->lay.np < ((n + TILE - 1) / TILE) * TILE) TRY(ensure_workspace(ctx, n, false, false));
+  const Layout& L = ctx->lay;
+  cudaStream_t s = ctx->stream;
+  TRY(reset_status(ctx));
+  // r_out holds exactly n entries, so the residual kernel gets n as its row
+  // stride and padding length.
+  double* r = r_out ? r_out : ctx->vd(V_R);
+  CU(launch_residual_mf(points, n, m, t, w, b, r, ctx->part(), L.chunks, n, ctx->st(), s));
+  TRY(read_status(ctx));
+  const double rn = bits_to_double(ctx->h_st->r_max_bits);
+  const double zn = bits_to_double(ctx->h_st->z_max_bits);
+  const double wn = bits_to_double(ctx->h_st->w_max_bits);
+  norms[0] = (zn > 0 && wn > 0) ? rn / (zn * wn) : INFINITY;
+  norms[1] = rn;
+  norms[2] = zn;
+  norms[3] = wn;
+  return MAG_OK;
 }
 
 int mag_sweep_tplus(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t_lo,

@@ -53,7 +53,7 @@ enum StatusFlags : int {
 
 struct DevStatus {
   int flags;
-  int notpd_index;                 // first failing pivot (global row), valid if ST_NOTPD
+  int notpd_index;                 // 1 + first failing pivot row, valid if ST_NOTPD
   unsigned long long min_d2_bits;  // min off-diagonal d^2 (non-negative double bits)
   unsigned long long r_max_bits;   // max_j |r_j|
   unsigned long long z_max_bits;   // max_j sum_k Z_jk
@@ -133,6 +133,15 @@ cudaError_t launch_forward(const T* Z, const T* Dinv, int64_t N, T* v, T* tmp, c
 template <typename T>
 cudaError_t launch_backward(const T* Z, const T* Dinv, int64_t N, T* v, T* tmp, cudaStream_t s);
 
+// K3, persistent single-launch versions (cooperative; per-tile ready flags,
+// N unsigned of scratch).  Same arguments as above; y/x must not alias v/yv.
+template <typename T>
+cudaError_t launch_forward_persistent(const T* Z, const T* Dinv, int64_t N, const T* v, T* y, unsigned* flags,
+                                      DevStatus* st, cudaStream_t s);
+template <typename T>
+cudaError_t launch_backward_persistent(const T* Z, const T* Dinv, int64_t N, const T* yv, T* x, unsigned* flags,
+                                       DevStatus* st, cudaStream_t s);
+
 // K4: FP64 residual r = b - Z w (b == null means all ones), Z regenerated
 // from the points (matrix free) or read from FP64 packed tiles (stored).
 // part: scratch of 3 * chunks * np doubles.  Norms go to st (r_max, z_max, w_max).
@@ -140,8 +149,8 @@ cudaError_t launch_residual_mf(const double* X, int64_t n, int m, double t, cons
                                const double* b, double* r, double* part, int chunks, int64_t np,
                                DevStatus* st, cudaStream_t s);
 cudaError_t launch_residual_stored(const double* Zd, int64_t n, int64_t N, const double* w,
-                                   const double* b, double* r, double* part, DevStatus* st,
-                                   cudaStream_t s);
+                                   const double* b, double* r, double* part, int chunks, int64_t np,
+                                   DevStatus* st, cudaStream_t s);
 
 // K5/K6 helpers.  r_max below is max_j |r_j| as kept in st->r_max_bits.
 // v[i] = r[i] / r_max for i < n, 0 for n <= i < np (right-hand side of a correction).

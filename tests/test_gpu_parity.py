@@ -105,6 +105,39 @@ def test_cholesky_fp64_elementwise(ctx, n):
     assert np.abs(Lg - Lo).max() <= 1e-12 * np.abs(Lo).max()
 
 
+@pytest.mark.parametrize("prec,tol", [("tf32x3", 2e-4), ("tf32", 5e-3)])
+@pytest.mark.parametrize("n", [130, 300, 1100, 2100])
+def test_cholesky_tensor_core_normwise(ctx, prec, tol, n):
+    # one panel (n <= 1024), a trapezoid (1100), several panels (2100)
+    X = _cloud(n, 3, seed=n)
+    t = 2.0
+    Lg = ctx.cholesky_factor(_dev(X), t, prec).cpu().numpy().astype(np.float64)
+    Z = oracle.similarity_matrix(X, t)
+    Lo = oracle.cholesky(Z)
+    assert np.abs(Lg - Lo).max() <= tol * np.abs(Lo).max()
+    assert np.all(np.triu(Lg, 1) == 0)
+
+
+def test_cholesky_bf16_well_conditioned(ctx):
+    X = _cloud(700, 8, seed=5)
+    t = 20.0  # Z close to the identity
+    Lg = ctx.cholesky_factor(_dev(X), t, "bf16").cpu().numpy().astype(np.float64)
+    Lo = oracle.cholesky(oracle.similarity_matrix(X, t))
+    assert np.abs(Lg - Lo).max() <= 2e-2 * np.abs(Lo).max()
+
+
+def test_bf16_ill_conditioned_reports_not_pd_then_falls_back(ctx):
+    X = _cloud(1500, 3, seed=6)
+    with pytest.raises(M.MagnitudeError) as e:
+        ctx.cholesky_factor(_dev(X), 2.0, "bf16")
+    assert e.value.status == M.MAG_ENOTPD
+    ctx.set_options(M.Options(precision="bf16"))
+    w, mag, info = ctx.solve(_dev(X), 2.0)
+    ctx.set_options(M.Options())
+    assert info["fallback"] == 2 and info["precision_used"] == M.PREC_FP64
+    check_solution(X, 2.0, w.cpu().numpy(), mag, *oracle.weighting(X, 2.0)[:2])
+
+
 @pytest.mark.parametrize("n", [130, 400])
 def test_cholesky_fp32_normwise(ctx, n):
     X = _cloud(n, 8, seed=n)
@@ -117,9 +150,10 @@ def test_cholesky_fp32_normwise(ctx, n):
 
 
 # ------------------------------------------------------------ full solve
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "tf32x3", "auto"])
 @pytest.mark.parametrize("n,m,t", [(2, 1, 0.7), (3, 2, 1.0), (5, 3, 0.4), (17, 8, 1.0), (129, 8, 1.0),
-                                   (257, 16, 0.5), (1000, 8, 1.0), (1031, 3, 10.0), (600, 40, 0.8)])
+                                   (257, 16, 0.5), (1000, 8, 1.0), (1031, 3, 10.0), (600, 40, 0.8),
+                                   (2500, 8, 1.0), (2049, 3, 30.0)])
 def test_solve_matches_oracle(ctx, prec, n, m, t):
     X = _cloud(n, m, seed=1000 + n + m)
     ctx.set_options(M.Options(precision=prec))
@@ -134,8 +168,12 @@ def test_solve_matches_oracle(ctx, prec, n, m, t):
 def test_two_point_closed_form_gpu(ctx, t):
     X = np.array([[0.0, 0.0, 0.0], [1.0, 2.0, 2.0]])
     w, mag, _ = ctx.solve(_dev(X), t)
-    np.testing.assert_allclose(w.cpu().numpy(), 1 / (1 + math.exp(-3 * t)), rtol=1e-14)
-    assert mag == pytest.approx(2 / (1 + math.exp(-3 * t)), rel=1e-14)
+    # refinement stops at relative residual 1e-14, so the forward error is
+    # bounded by kappa(Z) * 1e-14 with kappa = (1 + z) / (1 - z), z = exp(-3t)
+    z = math.exp(-3 * t)
+    tol = 2e-14 * (1 + z) / (1 - z)
+    np.testing.assert_allclose(w.cpu().numpy(), 1 / (1 + z), rtol=tol)
+    assert mag == pytest.approx(2 / (1 + z), rel=tol)
 
 
 def test_collinear_closed_form_gpu(ctx):
@@ -253,3 +291,38 @@ def test_batch_matches_oracle(ctx):
             w_ref, mag_ref, _ = oracle.weighting(c, t)
             check_solution(c, t, ws[k].cpu().numpy(), mags[i, j].item(), w_ref, mag_ref)
             k += 1
+
+
+# ----------------------------------------------------- residual modes a5
+@pytest.mark.parametrize("resid", ["matrix_free", "stored", "auto"])
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16", "fp64"])
+@pytest.mark.parametrize("n,m,t", [(300, 8, 1.0), (1500, 3, 5.0), (2100, 8, 20.0)])
+def test_residual_modes_match_oracle(ctx, resid, prec, n, m, t):
+    X = _cloud(n, m, seed=77 + n)
+    ctx.set_options(M.Options(precision=prec, residual_mode=resid))
+    try:
+        w, mag, info = ctx.solve(_dev(X), t)
+    finally:
+        ctx.set_options(M.Options())
+    w_ref, mag_ref, _ = oracle.weighting(X, t)
+    check_solution(X, t, w.cpu().numpy(), mag, w_ref, mag_ref)
+    if resid == "stored" and prec != "fp64" and info["fallback"] == 0:
+        assert info["residual_mode"] == M.RESID_STORED
+
+
+def test_residual_entry_point_matches_oracle(ctx):
+    X = _cloud(700, 5, seed=31)
+    t = 0.8
+    w_ref = oracle.weighting(X, t)[0]
+    w = w_ref + 1e-9 * np.random.default_rng(32).standard_normal(700)  # a perturbed weighting
+    r, nr = ctx.residual(_dev(X), t, torch.from_numpy(w).cuda())
+    ro, rs = oracle.residual_rows(X, t, w)
+    scale = np.abs(rs).max() * np.abs(w).max()
+    # exp within 1 ulp each side, d^2 with and without FMA: |dr_j| <= (2 + t d) u sum_k Z_jk |w_k|
+    assert np.abs(r.cpu().numpy() - ro).max() <= 2e-15 * scale
+    assert nr["rel_residual"] == pytest.approx(np.abs(ro).max() / scale, rel=1e-6)
+    assert nr["z_norm_inf"] == pytest.approx(np.abs(rs).max(), rel=1e-14)
+    b = np.random.default_rng(33).standard_normal(700)
+    r2, _ = ctx.residual(_dev(X), t, torch.from_numpy(w).cuda(), b=torch.from_numpy(b).cuda())
+    ro2, _ = oracle.residual_rows(X, t, w, b=b)
+    assert np.abs(r2.cpu().numpy() - ro2).max() <= 2e-15 * scale + 4e-16 * np.abs(b).max()
