@@ -174,6 +174,34 @@ int mag_solve_rhs(mag_ctx* ctx, const double* points, int64_t n, int32_t m, doub
 int mag_residual(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t, const double* w,
                  const double* b, double* r_out, double* norms);
 
+/* Largest n accepted by mag_residual_noalloc. */
+#define MAG_NOALLOC_MAX_N 262144
+
+/* The FP64 residual of mag_residual for callers that must not allocate device
+ * memory: code that runs under an external memory manager (a framework's
+ * caching allocator or a fixed memory budget) where a hidden cudaMalloc would
+ * fragment or exceed the budget, and latency-critical loops where cudaMalloc
+ * and cudaFree would synchronize the device.  (The paper has no counterpart;
+ * this is an interface convenience.)
+ *
+ * It needs no context and calls no allocating routine.  Its scratch (3 FP64
+ * partial sums per row and the norm maxima) is one static device array of
+ * 3 * MAG_NOALLOC_MAX_N + 32 doubles (about 6 MiB), which every GPU that loads
+ * this library holds until the process exits.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) with the
+ * caller's device current; make that first call before any stream capture.
+ * All calls share the array: the norm maxima are cleared at the start of
+ * each call, and calls that overlap on the GPU (other streams or threads)
+ * race on it, so serialize them.
+ *
+ * points: device n x m; w: device n; b: device n or NULL (all ones);
+ * r_out: device n (required); norms: host, 4 doubles as in mag_residual;
+ * stream: cudaStream_t (NULL = legacy default stream).  The call returns after
+ * the stream has completed the work.  MAG_EINVAL for bad arguments,
+ * MAG_ENOMEM when n > MAG_NOALLOC_MAX_N, MAG_ECUDA if a CUDA call fails. */
+int mag_residual_noalloc(const double* points, int64_t n, int32_t m, double t, const double* w,
+                         const double* b, double* r_out, double* norms, void* stream);
+
 /* a8 (Sec. 2 and its footnote): bisection for the cutoff t_+ on the sign of
  * min_j w_j.  feasible(t) <=> min_j w_j(t) >= 0.  t_hi <= 0 uses the Sec. 1
  * bound.  The bracket keeps feasible(hi) and not feasible(lo); each probe

@@ -30,6 +30,8 @@ MAG_OK, MAG_EINVAL, MAG_EDUPLICATE, MAG_ENOTPD, MAG_ENOCONV, MAG_ENOBRACKET, MAG
 PREC_AUTO, PREC_BF16, PREC_TF32, PREC_TF32X3, PREC_FP32, PREC_FP64 = range(6)
 PRECISIONS = {"auto": PREC_AUTO, "bf16": PREC_BF16, "tf32": PREC_TF32, "tf32x3": PREC_TF32X3,
               "fp32": PREC_FP32, "fp64": PREC_FP64}
+# #define MAG_NOALLOC_MAX_N
+NOALLOC_MAX_N = 262144
 # enum mag_residual_mode
 RESID_MATRIX_FREE, RESID_STORED, RESID_AUTO = 0, 1, 2
 
@@ -84,6 +86,7 @@ SIGNATURES = {
     "mag_solve": (ctypes.c_int, [_P, _P, _I64, _I32, _D, _P, _DP, ctypes.POINTER(mag_info)]),
     "mag_solve_rhs": (ctypes.c_int, [_P, _P, _I64, _I32, _D, _P, _P, ctypes.POINTER(mag_info)]),
     "mag_residual": (ctypes.c_int, [_P, _P, _I64, _I32, _D, _P, _P, _P, _DP]),
+    "mag_residual_noalloc": (ctypes.c_int, [_P, _I64, _I32, _D, _P, _P, _P, _DP, _P]),
     "mag_sweep_tplus": (ctypes.c_int, [_P, _P, _I64, _I32, _D, _D, _D, _DP, _DP, _P, _DP,
                                        ctypes.POINTER(mag_info)]),
     "mag_grad": (ctypes.c_int, [_P, _P, _I64, _I32, _D, _P, _P, _DP, _P, ctypes.POINTER(mag_info)]),
@@ -328,6 +331,28 @@ class Context:
         for d in descs:
             ws.append(W[d.w_offset:d.w_offset + d.n])
         return ws, M.reshape(len(flat), len(ts)), S.reshape(len(flat), len(ts))
+
+
+def residual_noalloc(X: torch.Tensor, t: float, w: torch.Tensor, b: torch.Tensor | None = None,
+                     stream: torch.cuda.Stream | None = None):
+    """mag_residual_noalloc: r = b - Z w with no device allocation inside the
+    library (static scratch; n <= NOALLOC_MAX_N).  Returns (r, norms dict);
+    r is allocated here by PyTorch, not by the library."""
+    lib = load_library()
+    X = X.to(torch.float64).contiguous()
+    n, m = X.shape
+    w = w.to(device=X.device, dtype=torch.float64).contiguous()
+    bb = None if b is None else b.to(device=X.device, dtype=torch.float64).contiguous()
+    r = torch.empty(n, dtype=torch.float64, device=X.device)
+    nr = (ctypes.c_double * 4)()
+    s = stream if stream is not None else torch.cuda.current_stream(X.device)
+    st = lib.mag_residual_noalloc(_P(X.data_ptr()), n, m, float(t), _P(w.data_ptr()),
+                                  _P(0) if bb is None else _P(bb.data_ptr()), _P(r.data_ptr()),
+                                  ctypes.cast(nr, _DP), _P(s.cuda_stream))
+    if st != MAG_OK:
+        raise MagnitudeError(st, "mag_residual_noalloc failed" +
+                             (f" (n = {n} > {NOALLOC_MAX_N})" if st == MAG_ENOMEM else ""))
+    return r, {"rel_residual": nr[0], "r_norm_inf": nr[1], "z_norm_inf": nr[2], "w_norm_inf": nr[3]}
 
 
 _ctx_cache: dict = {}

@@ -9,6 +9,11 @@
 // compensation per thread and then combined across column chunks with
 // Neumaier's rule, so the residual is good to a few units of FP64 rounding
 // relative to ||Z||inf ||w||inf (the refinement target is 1e-14).
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/magnitude.h"
 #include "mag_internal.cuh"
 
 namespace mag {
@@ -472,3 +477,79 @@ cudaError_t launch_sum_f64(const double* v, int64_t n, double* out, cudaStream_t
 }
 
 }  // namespace mag
+
+// ------------------------------------------------- allocation-free residual
+// Scratch of mag_residual_noalloc: 3 partial-sum rows of up to
+// MAG_NOALLOC_MAX_N doubles, then a DevStatus in the last 32 doubles.
+namespace mag {
+namespace {
+
+constexpr int64_t NOALLOC_STATUS_DOUBLES = 32;
+static_assert(sizeof(DevStatus) <= NOALLOC_STATUS_DOUBLES * sizeof(double), "status block fits");
+static __device__ __align__(256) double g_noalloc_scratch[3 * (int64_t)MAG_NOALLOC_MAX_N + NOALLOC_STATUS_DOUBLES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch on the current device (looked up once per device).
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+}  // namespace mag
+
+extern "C" int mag_residual_noalloc(const double* points, int64_t n, int32_t m, double t, const double* w,
+                                    const double* b, double* r_out, double* norms, void* stream) {
+  using namespace mag;
+  if (!points || !w || !r_out || !norms || n < 2 || m < 1 || !(t > 0.0) || !isfinite(t)) return MAG_EINVAL;
+  if (n > MAG_NOALLOC_MAX_N) return MAG_ENOMEM;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* scratch = nullptr;
+  if (noalloc_scratch(&scratch) != cudaSuccess) {
+    cudaGetLastError();
+    return MAG_ECUDA;
+  }
+  DevStatus* st = reinterpret_cast<DevStatus*>(scratch + 3 * (int64_t)MAG_NOALLOC_MAX_N);
+  // the partial sums are written in full; only the norm maxima start at zero
+  if (cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess) {
+    cudaGetLastError();
+    return MAG_ECUDA;
+  }
+  // as many column chunks as the scratch holds (at most 8): 3 * chunks * n <= 3 * MAX_N
+  int chunks = (int)std::min<int64_t>(8, MAG_NOALLOC_MAX_N / n);
+  if (chunks < 1) chunks = 1;
+  if (launch_residual_mf(points, n, m, t, w, b, r_out, scratch, chunks, n, st, s) != cudaSuccess) {
+    cudaGetLastError();
+    return MAG_ECUDA;
+  }
+  DevStatus h;
+  if (cudaMemcpyAsync(&h, st, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return MAG_ECUDA;
+  }
+  double rn, zn, wn;
+  std::memcpy(&rn, &h.r_max_bits, sizeof rn);
+  std::memcpy(&zn, &h.z_max_bits, sizeof zn);
+  std::memcpy(&wn, &h.w_max_bits, sizeof wn);
+  norms[0] = (zn > 0 && wn > 0) ? rn / (zn * wn) : INFINITY;
+  norms[1] = rn;
+  norms[2] = zn;
+  norms[3] = wn;
+  return MAG_OK;
+}
