@@ -265,9 +265,16 @@ def run_ours(a):
         upd_launch = sum(i["update_launches"] for _, _, i in infos)
         upd_flops = sum(i["update_flops"] for _, _, i in infos)
         prec_used = {i["precision_used"] for _, _, i in infos}
-        tensor = any(p in (M.PREC_BF16, M.PREC_TF32, M.PREC_TF32X3) for p in prec_used)
+        tensor = any(p in (M.PREC_BF16, M.PREC_TF32, M.PREC_TF32X3, M.PREC_FP16X3, M.PREC_FP16)
+                     for p in prec_used)
+        f16 = all(p in (M.PREC_BF16, M.PREC_FP16X3, M.PREC_FP16) for p in prec_used)
         smx = peaks.get("sm_max_mhz", 2070.0)
-        if tensor:
+        if tensor and f16:
+            bf16 = peaks["bf16_tflops"]
+            peak = bf16  # FP16 and BF16 dense tensor rates are equal (nominal 2.25 PF each)
+            bound, kname = "tensor", "trailing_update_tc"
+            peak_note = f"FP16 tensor peak = {peak_kind} BF16 {bf16} TF/s (equal nominal FP16/BF16 rates)"
+        elif tensor:
             bf16 = peaks["bf16_tflops"]
             peak = bf16 * (1.1 / 2.25)  # TF32 dense / BF16 dense, nominal ratio
             bound, kname = "tensor", "trailing_update_tc"

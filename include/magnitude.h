@@ -53,12 +53,17 @@ enum mag_status {
 
 /* Precision of the Cholesky factor (Zw = 1 is always refined in FP64). */
 enum mag_precision {
-  MAG_PREC_AUTO = 0,     /* pick from a Gershgorin bound on lambda_min(Z)    */
+  MAG_PREC_AUTO = 0,     /* FP16 if the Gershgorin bound gives lambda_min(Z) >= 1/2,
+                            else FP16X3                                       */
   MAG_PREC_BF16 = 1,     /* BF16 tensor-core products, FP32 accumulation      */
   MAG_PREC_TF32 = 2,     /* one TF32 tensor-core product, FP32 accumulation   */
   MAG_PREC_TF32X3 = 3,   /* split TF32 (hi*hi + hi*lo + lo*hi), FP32 accum.   */
   MAG_PREC_FP32 = 4,     /* FP32 CUDA-core products (no tensor cores)          */
-  MAG_PREC_FP64 = 5      /* full FP64 factor (the plain dense method)          */
+  MAG_PREC_FP64 = 5,     /* full FP64 factor (the plain dense method)          */
+  MAG_PREC_FP16X3 = 6,   /* split FP16 of the panel scaled by 2^12 (hi*hi +
+                            hi*lo + lo*hi), FP32 accumulation: split-TF32
+                            accuracy at the FP16 tensor rate                   */
+  MAG_PREC_FP16 = 7      /* one FP16 product of that scaled panel              */
 };
 
 /* How the FP64 residual r = 1 - Zw of iterative refinement is formed. */
@@ -152,7 +157,8 @@ int mag_cholesky_factor(mag_ctx* ctx, const double* points, int64_t n, int32_t m
 /* a2-a7 (Sec. 2, Eq. weighting): solve Zw = 1 for Z = exp[-t d] and return
  * Mag = 1^T w.  points: device n x m FP64; w: device output, n FP64; mag:
  * host output.  The factor precision follows ctx's options (MAG_PREC_AUTO:
- * BF16 when the Gershgorin bound gives lambda_min >= 0.5, else split TF32);
+ * one scaled-FP16 product when the Gershgorin bound gives lambda_min >= 0.5,
+ * else the scaled-FP16 split);
  * FP64 iterative refinement with a residual formed in FP64 runs until the
  * relative residual is <= ir_tol, escalating to GMRES-IR and then to an FP64
  * factor when allow_fallback is set.  MAG_ENOCONV returns the best w found. */

@@ -27,9 +27,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmagnitude.so")
 MAG_OK, MAG_EINVAL, MAG_EDUPLICATE, MAG_ENOTPD, MAG_ENOCONV, MAG_ENOBRACKET, MAG_ENOMEM, MAG_ECUDA, \
     MAG_ETIMEOUT = range(9)
 # enum mag_precision
-PREC_AUTO, PREC_BF16, PREC_TF32, PREC_TF32X3, PREC_FP32, PREC_FP64 = range(6)
+PREC_AUTO, PREC_BF16, PREC_TF32, PREC_TF32X3, PREC_FP32, PREC_FP64, PREC_FP16X3, PREC_FP16 = range(8)
 PRECISIONS = {"auto": PREC_AUTO, "bf16": PREC_BF16, "tf32": PREC_TF32, "tf32x3": PREC_TF32X3,
-              "fp32": PREC_FP32, "fp64": PREC_FP64}
+              "fp32": PREC_FP32, "fp64": PREC_FP64, "fp16x3": PREC_FP16X3, "fp16": PREC_FP16}
 # #define MAG_NOALLOC_MAX_N
 NOALLOC_MAX_N = 262144
 # enum mag_residual_mode

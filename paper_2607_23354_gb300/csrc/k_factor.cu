@@ -15,6 +15,7 @@
 // All kernels are templated on the element type (float for the mixed
 // precision factor, double for the FP64 factor).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -291,6 +292,24 @@ __global__ void __launch_bounds__(256) k_split_col(const float* __restrict__ Z, 
       u.x = *reinterpret_cast<uint32_t*>(&a);
       u.y = *reinterpret_cast<uint32_t*>(&b);
       *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(hi) + off) = u;
+    } else if (mode == UPD_FP16X3 || mode == UPD_FP16) {
+      const float sc = (float)(1 << FP16_SCALE_LOG2);
+      const float ys[4] = {x.x * sc, x.y * sc, x.z * sc, x.w * sc};
+      __half h[4], l[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        h[q] = __float2half_rn(ys[q]);
+        l[q] = __float2half_rn(ys[q] - __half2float(h[q]));
+      }
+      uint2 uh, ul;
+      __half2 h01 = __halves2half2(h[0], h[1]), h23 = __halves2half2(h[2], h[3]);
+      __half2 l01 = __halves2half2(l[0], l[1]), l23 = __halves2half2(l[2], l[3]);
+      uh.x = *reinterpret_cast<uint32_t*>(&h01);
+      uh.y = *reinterpret_cast<uint32_t*>(&h23);
+      ul.x = *reinterpret_cast<uint32_t*>(&l01);
+      ul.y = *reinterpret_cast<uint32_t*>(&l23);
+      *reinterpret_cast<uint2*>(reinterpret_cast<__half*>(hi) + off) = uh;
+      if (mode == UPD_FP16X3) *reinterpret_cast<uint2*>(reinterpret_cast<__half*>(lo) + off) = ul;
     } else {
       float xs[4] = {x.x, x.y, x.z, x.w}, h[4], l[4];
 #pragma unroll

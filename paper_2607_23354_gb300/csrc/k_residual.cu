@@ -90,63 +90,95 @@ __global__ void __launch_bounds__(RES_THREADS) k_resid_mf(const double* __restri
 }
 
 // Stored variant of K4: (Zw)_j from the packed FP64 tiles of Z (lower tiles,
-// diagonal tiles in full).  Block (I, chunk) owns rows I*128..+127; for each
-// tile column J of its chunk it uses tile (I, J) row-wise when J <= I (staged
-// through shared memory in 32-column slabs so that global reads are
-// coalesced) and tile (J, I) column-wise when J > I (already coalesced).
-// Same per-thread Kahan sums and partial layout as the matrix-free kernel.
-__global__ void __launch_bounds__(TILE) k_resid_stored(const double* __restrict__ Zd, int64_t n, int64_t N,
-                                                       const double* __restrict__ w,
-                                                       double* __restrict__ part, int chunks, int64_t np) {
-  __shared__ double slab[TILE][33];
-  __shared__ double wj[TILE];
-  const int r = threadIdx.x;
-  const int64_t I = blockIdx.x;
-  const int64_t per = (N + chunks - 1) / chunks;
-  const int64_t J0 = blockIdx.y * per, J1 = min(N, J0 + per);
-  double s = 0.0, c = 0.0, zs = 0.0;
-  for (int64_t J = J0; J < J1; ++J) {
-    __syncthreads();
-    const int64_t col = J * TILE + r;
-    wj[r] = col < n ? w[col] : 0.0;
-    if (J <= I) {
-      const double* tile = Zd + tri_index(I, J) * TILE_ELEMS;
-      for (int sl = 0; sl < TILE; sl += 32) {
-        __syncthreads();
-        for (int e = r; e < TILE * 32; e += TILE) {
-          const int rr = e >> 5, cc = e & 31;
-          slab[rr][cc] = tile[rr * TILE + sl + cc];
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int cc = 0; cc < 32; ++cc) {
-          const double z = slab[r][cc];
-          zs += z;
-          const double y = fma(z, wj[sl + cc], -c);
-          const double tt = s + y;
-          c = (tt - s) - y;
-          s = tt;
-        }
-      }
-    } else {
-      const double* tile = Zd + tri_index(J, I) * TILE_ELEMS;
-      __syncthreads();
-#pragma unroll 8
-      for (int cc = 0; cc < TILE; ++cc) {
-        const double z = tile[cc * TILE + r];
-        zs += z;
-        const double y = fma(z, wj[cc], -c);
-        const double tt = s + y;
-        c = (tt - s) - y;
-        s = tt;
-      }
-    }
+// diagonal tiles in full), each tile read once.  One CTA per lower tile
+// (I, J) computes the tile's row contributions Z_IJ w_J (rows of block I)
+// and, for I != J, its transposed contributions Z_IJ^T w_I (rows of block J),
+// and stores each as a partial P[row block][other block][r].  Within a tile
+// the sums are short trees (128 terms); across tiles k_resid_stored_finish
+// adds the N partials of a row with Neumaier compensation.
+// Thread layout (256 threads): warp wp covers tile rows 16 wp .. 16 wp + 15,
+// lane l covers columns 4l .. 4l+3 (each row read as one 1 KB coalesced line).
+__global__ void __launch_bounds__(256) k_resid_stored(const double* __restrict__ Zd, int64_t n, int64_t N,
+                                                      const double* __restrict__ w,
+                                                      double* __restrict__ P) {
+  __shared__ double colp[8][TILE];
+  int64_t I, J;
+  tri_coords((int64_t)blockIdx.x, &I, &J);
+  const int tid = threadIdx.x, wp = tid >> 5, l = tid & 31;
+  const double* tile = Zd + tri_index(I, J) * TILE_ELEMS;
+  double wj[4], c4[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t col = J * TILE + 4 * l + q;
+    wj[q] = col < n ? w[col] : 0.0;
   }
-  const int64_t j = I * TILE + r;
+#pragma unroll 4
+  for (int i = 0; i < 16; ++i) {
+    const int r = wp * 16 + i;
+    const int64_t row = I * TILE + r;
+    const double wi = row < n ? w[row] : 0.0;
+    const double2 a = *reinterpret_cast<const double2*>(tile + r * TILE + 4 * l);
+    const double2 bq = *reinterpret_cast<const double2*>(tile + r * TILE + 4 * l + 2);
+    double s = a.x * wj[0] + a.y * wj[1] + bq.x * wj[2] + bq.y * wj[3];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (l == 0) P[(I * N + J) * TILE + r] = s;
+    c4[0] = fma(a.x, wi, c4[0]);
+    c4[1] = fma(a.y, wi, c4[1]);
+    c4[2] = fma(bq.x, wi, c4[2]);
+    c4[3] = fma(bq.y, wi, c4[3]);
+  }
+  if (I == J) return;  // uniform: the diagonal tile is stored in full
+#pragma unroll
+  for (int q = 0; q < 4; ++q) colp[wp][4 * l + q] = c4[q];
+  __syncthreads();
+  if (tid < TILE) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += colp[k][tid];
+    P[(J * N + I) * TILE + tid] = s;
+  }
+}
+
+// r_j = b_j - sum_J P[I][J][r] (Neumaier over the N tile partials of the
+// row), with ||r||, ||Z|| (from the generator's row sums) and ||w|| maxima.
+__global__ void k_resid_stored_finish(const double* __restrict__ P, int64_t n, int64_t N, int64_t np,
+                                      const double* __restrict__ w, const double* __restrict__ b,
+                                      const double* __restrict__ rowsum, double* __restrict__ r,
+                                      DevStatus* st) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double ra = 0.0, za = 0.0, wa = 0.0;
   if (j < n) {
-    part[((int64_t)0 * chunks + blockIdx.y) * np + j] = s;
-    part[((int64_t)1 * chunks + blockIdx.y) * np + j] = -c;
-    part[((int64_t)2 * chunks + blockIdx.y) * np + j] = zs;
+    const int64_t I = j / TILE, rr = j % TILE;
+    double s = 0.0, c = 0.0;
+    for (int64_t J = 0; J < N; ++J) {
+      const double v = P[(I * N + J) * TILE + rr];
+      const double tt = s + v;
+      if (fabs(s) >= fabs(v))
+        c += (s - tt) + v;
+      else
+        c += (v - tt) + s;
+      s = tt;
+    }
+    const double bj = b ? b[j] : 1.0;
+    const double rj = (bj - s) - c;
+    r[j] = rj;
+    ra = fabs(rj);
+    za = rowsum[j];
+    wa = fabs(w[j]);
+  } else if (j < np) {
+    r[j] = 0.0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ra = fmax(ra, __shfl_xor_sync(0xffffffffu, ra, o));
+    za = fmax(za, __shfl_xor_sync(0xffffffffu, za, o));
+    wa = fmax(wa, __shfl_xor_sync(0xffffffffu, wa, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg(&st->r_max_bits, ra);
+    atomic_max_nonneg(&st->z_max_bits, za);
+    atomic_max_nonneg(&st->w_max_bits, wa);
   }
 }
 
@@ -391,13 +423,13 @@ cudaError_t launch_residual_mf(const double* X, int64_t n, int m, double t, cons
 }
 
 cudaError_t launch_residual_stored(const double* Zd, int64_t n, int64_t N, const double* w,
-                                   const double* b, double* r, double* part, int chunks, int64_t np,
+                                   const double* b, const double* rowsum, double* r, double* P, int64_t np,
                                    DevStatus* st, cudaStream_t s) {
-  k_resid_stored<<<dim3((unsigned)N, (unsigned)chunks), TILE, 0, s>>>(Zd, n, N, w, part, chunks, np);
+  k_resid_stored<<<(unsigned)num_lower_tiles(N), 256, 0, s>>>(Zd, n, N, w, P);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_resid_finish<<<blocks_for(np, 256), 256, 0, s>>>(part, chunks, n, np, w, b, r, st);
+  k_resid_stored_finish<<<blocks_for(np, 256), 256, 0, s>>>(P, n, N, np, w, b, rowsum, r, st);
   note_launch();
   return cudaGetLastError();
 }

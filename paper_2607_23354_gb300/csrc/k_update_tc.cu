@@ -16,6 +16,10 @@
 //           lo = rna_tf32(x - hi): about 2^-21 relative per product (the
 //           split-TF32 scheme of Markidis et al., IPDPSW 2018).
 //   TF32  : A_hi B_hi.        BF16: one product of BF16-rounded operands.
+//   FP16X3: the split with FP16 hi/lo of the panel scaled by 2^12 (FP16 has
+//           TF32's significand at twice the TF32 tensor rate; the scale keeps
+//           |L| <= 1 in range and small entries normal); the epilogue
+//           multiplies the accumulator by 2^-24.   FP16: A_hi B_hi of that.
 //
 // Structure: persistent CTAs (one per SM, 6 warps), warp-specialized:
 //   warp 0     : TMA producer (one thread), S-stage shared-memory ring;
@@ -68,6 +72,20 @@ struct ModeCfg<UPD_BF16> {
   static constexpr int ELEM = 2;
   static constexpr bool SPLIT = false;
   static constexpr uint32_t FMT = 1;  // BF16 (kind::f16)
+};
+template <>
+struct ModeCfg<UPD_FP16X3> {  // scaled FP16 hi/lo pairs, 3 MMAs per K step
+  static constexpr int STAGES = 2;
+  static constexpr int ELEM = 2;
+  static constexpr bool SPLIT = true;
+  static constexpr uint32_t FMT = 0;  // F16 (kind::f16)
+};
+template <>
+struct ModeCfg<UPD_FP16> {
+  static constexpr int STAGES = 4;
+  static constexpr int ELEM = 2;
+  static constexpr bool SPLIT = false;
+  static constexpr uint32_t FMT = 0;
 };
 
 // ------------------------------------------------------------ PTX wrappers
@@ -149,7 +167,7 @@ __host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt) {
 template <int MODE>
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
   constexpr uint32_t idesc = instr_desc(ModeCfg<MODE>::FMT);
-  if constexpr (MODE == UPD_BF16) {
+  if constexpr (ModeCfg<MODE>::ELEM == 2) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
@@ -343,6 +361,9 @@ __global__ void __launch_bounds__(UPD_THREADS, 1)
       tc_fence_after();
       const bool second = (J + 1 < p.j1) && (J + 1 <= I);
       const int nchunks = second ? 8 : 4;
+      // FP16 panels are stored scaled by 2^s, so products carry 2^(2s)
+      constexpr float acc_scale =
+          (MODE == UPD_FP16X3 || MODE == UPD_FP16) ? 1.0f / (float)(1u << (2 * FP16_SCALE_LOG2)) : 1.0f;
       for (int cc = 0; cc < nchunks; ++cc) {
         float v[32];
         tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + acc * (uint32_t)B_ROWS + cc * 32, v);
@@ -352,10 +373,10 @@ __global__ void __launch_bounds__(UPD_THREADS, 1)
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           float4 c4 = cp[i];
-          c4.x -= v[4 * i + 0];
-          c4.y -= v[4 * i + 1];
-          c4.z -= v[4 * i + 2];
-          c4.w -= v[4 * i + 3];
+          c4.x -= acc_scale * v[4 * i + 0];
+          c4.y -= acc_scale * v[4 * i + 1];
+          c4.z -= acc_scale * v[4 * i + 2];
+          c4.w -= acc_scale * v[4 * i + 3];
           cp[i] = c4;
         }
       }
@@ -394,15 +415,18 @@ EncodeTiledFn get_encode() {
   return fn;
 }
 
-bool encode_2d(CUtensorMap* m, const void* base, bool bf16, int64_t cols, int64_t rows, int box_rows) {
+bool encode_2d(CUtensorMap* m, const void* base, int mode, int64_t cols, int64_t rows, int box_rows) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return false;
-  const int elem = bf16 ? 2 : 4;
+  const bool bf16 = mode == UPD_BF16, f16 = mode == UPD_FP16X3 || mode == UPD_FP16;
+  const int elem = (bf16 || f16) ? 2 : 4;
+  const CUtensorMapDataType dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                      : (f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(cols * elem)};
   cuuint32_t box[2] = {(cuuint32_t)(CHUNK_BYTES / elem), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+  CUresult r = enc(m, dt, 2,
                    const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -429,12 +453,11 @@ static_assert(sizeof(CUtensorMap) == 128, "CUtensorMap layout");
 
 bool make_update_maps(UpdMaps* maps, const void* hi, const void* lo, int mode, int64_t cols, int64_t rows) {
   CUtensorMap* m = reinterpret_cast<CUtensorMap*>(maps->m);
-  const bool bf16 = mode == UPD_BF16;
-  if (!encode_2d(&m[0], hi, bf16, cols, rows, A_ROWS)) return false;
-  if (!encode_2d(&m[1], hi, bf16, cols, rows, B_ROWS)) return false;
+  if (!encode_2d(&m[0], hi, mode, cols, rows, A_ROWS)) return false;
+  if (!encode_2d(&m[1], hi, mode, cols, rows, B_ROWS)) return false;
   const void* l = lo ? lo : hi;
-  if (!encode_2d(&m[2], l, bf16, cols, rows, A_ROWS)) return false;
-  if (!encode_2d(&m[3], l, bf16, cols, rows, B_ROWS)) return false;
+  if (!encode_2d(&m[2], l, mode, cols, rows, A_ROWS)) return false;
+  if (!encode_2d(&m[3], l, mode, cols, rows, B_ROWS)) return false;
   return true;
 }
 
@@ -456,6 +479,8 @@ cudaError_t launch_update_tc(const UpdMaps& maps, UpdParams p, int mode, int gri
     case UPD_TF32X3: return launch_mode<UPD_TF32X3>(maps, p, grid, s);
     case UPD_TF32: return launch_mode<UPD_TF32>(maps, p, grid, s);
     case UPD_BF16: return launch_mode<UPD_BF16>(maps, p, grid, s);
+    case UPD_FP16X3: return launch_mode<UPD_FP16X3>(maps, p, grid, s);
+    case UPD_FP16: return launch_mode<UPD_FP16>(maps, p, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -32,7 +32,7 @@ struct Layout {
   int chunks = 1;
   bool f32 = false, f64 = false;
   size_t off_zf = 0, off_zd = 0, off_dinvf = 0, off_dinvd = 0, off_vec = 0, off_part = 0,
-         off_status = 0, off_panel = 0, off_flags = 0, total = 0;
+         off_status = 0, off_panel = 0, off_flags = 0, off_spart = 0, total = 0;
   int nb = 8;          // panel width in tiles
   int64_t W = 0;       // panel width in columns (nb * TILE)
 };
@@ -74,6 +74,7 @@ struct mag_ctx {
     return (float*)((double*)((char*)ws + lay.off_vec) + (size_t)NVEC_D * lay.np) + (size_t)i * lay.np;
   }
   double* part() { return (double*)((char*)ws + lay.off_part); }
+  double* spart() { return (double*)((char*)ws + lay.off_spart); }
   float* panel_hi() { return (float*)((char*)ws + lay.off_panel); }
   float* panel_lo() { return panel_hi() + (size_t)lay.np * lay.W; }
   DevStatus* st() { return (DevStatus*)((char*)ws + lay.off_status); }
@@ -151,6 +152,8 @@ Layout plan(const mag_ctx* ctx, int64_t n, bool f32, bool f64) {
   if (f32) off = align_up(off + (size_t)L.tiles * TILE_ELEMS * sizeof(float));
   L.off_zd = off;
   if (f64) off = align_up(off + (size_t)L.tiles * TILE_ELEMS * sizeof(double));
+  L.off_spart = off;  // partials of the stored residual: N * N * 128 doubles
+  if (f64) off = align_up(off + (size_t)L.N * L.N * TILE * sizeof(double));
   L.total = off;
   return L;
 }
@@ -287,6 +290,16 @@ int factor_blocked(mag_ctx* ctx, T* Z, T* Dinv, int* launches, double* flops) {
     }
   }
   return MAG_OK;
+}
+
+int upd_mode(int prec) {
+  switch (prec) {
+    case MAG_PREC_BF16: return UPD_BF16;
+    case MAG_PREC_TF32: return UPD_TF32;
+    case MAG_PREC_FP16X3: return UPD_FP16X3;
+    case MAG_PREC_FP16: return UPD_FP16;
+    default: return UPD_TF32X3;
+  }
 }
 
 // Two-level blocked Cholesky with the trailing update on tensor cores.  For
@@ -515,8 +528,7 @@ int run_factor(mag_ctx* ctx, int prec, SolveResult* R) {
   else if (prec == MAG_PREC_FP32)
     TRY(factor_blocked<float>(ctx, ctx->zf(), ctx->dinvf(), &R->update_launches, &R->update_flops));
   else
-    TRY(factor_tc(ctx, prec == MAG_PREC_BF16 ? UPD_BF16 : (prec == MAG_PREC_TF32 ? UPD_TF32 : UPD_TF32X3),
-                  &R->update_launches, &R->update_flops));
+    TRY(factor_tc(ctx, upd_mode(prec), &R->update_launches, &R->update_flops));
   CU(cudaEventRecord(ctx->ev[1], s));
   TRY(read_status(ctx));
   R->ms_fac += elapsed(ctx, 0, 1);
@@ -563,7 +575,8 @@ int residual(mag_ctx* ctx, const double* X, int32_t m, double t, const double* w
   TRY(reset_norms(ctx));
   CU(cudaEventRecord(ctx->ev[0], s));
   if (stored)
-    CU(launch_residual_stored(ctx->zd(), L.n, L.N, w, b, r, ctx->part(), L.chunks, L.np, ctx->st(), s));
+    CU(launch_residual_stored(ctx->zd(), L.n, L.N, w, b, ctx->vd(V_ROWSUM), r, ctx->spart(), L.np,
+                              ctx->st(), s));
   else
     CU(launch_residual_mf(X, L.n, m, t, w, b, r, ctx->part(), L.chunks, L.np, ctx->st(), s));
   CU(cudaEventRecord(ctx->ev[1], s));
@@ -605,10 +618,11 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
   bool f32 = prec != MAG_PREC_FP64;
   TRY(ensure_workspace(ctx, n, f32, f64));
   TRY(generate(ctx, X, m, t, f32, f64, R));
-  // AUTO: BF16 products when the Gershgorin bound keeps lambda_min(Z) >= 1/2
-  // (then kappa(Z) <= 2 ||Z|| and a BF16 factor still contracts refinement),
-  // else split TF32.
-  if (prec == MAG_PREC_AUTO) prec = R->gersh >= 0.5 ? MAG_PREC_BF16 : MAG_PREC_TF32X3;
+  // AUTO: one scaled-FP16 product when the Gershgorin bound keeps
+  // lambda_min(Z) >= 1/2 (then kappa(Z) <= 2 ||Z|| and an 11-bit factor still
+  // contracts refinement quickly), else the scaled-FP16 split (FP32-like
+  // factor accuracy at the FP16 tensor rate).
+  if (prec == MAG_PREC_AUTO) prec = R->gersh >= 0.5 ? MAG_PREC_FP16 : MAG_PREC_FP16X3;
 
   cudaStream_t s = ctx->stream;
   double overall = INFINITY;
@@ -726,7 +740,7 @@ int mag_cholesky_factor(mag_ctx* ctx, const double* points, int64_t n, int32_t m
   if (!L_out) return fail(ctx, MAG_EINVAL, "NULL output");
   ctx->err.clear();
   const bool f64 = precision == MAG_PREC_FP64;
-  int prec = f64 ? MAG_PREC_FP64 : (precision == MAG_PREC_AUTO ? MAG_PREC_TF32X3 : precision);
+  int prec = f64 ? MAG_PREC_FP64 : (precision == MAG_PREC_AUTO ? MAG_PREC_FP16X3 : precision);
   SolveResult R;
   TRY(ensure_workspace(ctx, n, !f64, f64));
   TRY(generate(ctx, points, m, t, !f64, f64, &R));

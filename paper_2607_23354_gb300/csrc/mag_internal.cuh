@@ -96,7 +96,11 @@ template <typename T>
 cudaError_t launch_unpack(const T* Z, int64_t n, int64_t N, bool symmetric, T* out, cudaStream_t s);
 
 // K2c on tensor cores (k_update_tc.cu).  Product kinds of the trailing update.
-enum UpdMode { UPD_TF32X3 = 0, UPD_TF32 = 1, UPD_BF16 = 2 };
+enum UpdMode { UPD_TF32X3 = 0, UPD_TF32 = 1, UPD_BF16 = 2, UPD_FP16X3 = 3, UPD_FP16 = 4 };
+// FP16 modes store the panel scaled by 2^FP16_SCALE_LOG2 (|L| <= 1 stays far
+// below the FP16 maximum; entries down to ~1e-8 stay normal); the update
+// multiplies the accumulator by 2^(-2 FP16_SCALE_LOG2), exactly.
+constexpr int FP16_SCALE_LOG2 = 12;
 
 struct UpdParams {
   float* Z;            // packed FP32 tiles (updated in place)
@@ -122,7 +126,8 @@ cudaError_t launch_update_tc(const UpdMaps& maps, UpdParams p, int mode, int gri
 // Panel copy of column K (tiles I in (K, N)) for the tensor-core update:
 // row (I - k0)*TILE + r, column (K - k0)*TILE + c of the row-major panel
 // buffer with `width` columns.  TF32X3: hi = rna_tf32(x), lo = rna_tf32(x - hi);
-// TF32: hi only; BF16: round-to-nearest BF16 into hi (as 16-bit words).
+// TF32: hi only; BF16: round-to-nearest BF16 into hi (as 16-bit words);
+// FP16X3: y = 2^12 x, hi = rn_fp16(y), lo = rn_fp16(y - hi); FP16: hi only.
 cudaError_t launch_split_col(const float* Z, int64_t K, int64_t N, int64_t k0, int64_t width, int mode,
                              void* hi, void* lo, cudaStream_t s);
 
@@ -148,8 +153,10 @@ cudaError_t launch_backward_persistent(const T* Z, const T* Dinv, int64_t N, con
 cudaError_t launch_residual_mf(const double* X, int64_t n, int m, double t, const double* w,
                                const double* b, double* r, double* part, int chunks, int64_t np,
                                DevStatus* st, cudaStream_t s);
+// Stored: P is scratch of N * N * 128 doubles (one partial per row block,
+// tile and row); rowsum holds the row sums of Z from the generator.
 cudaError_t launch_residual_stored(const double* Zd, int64_t n, int64_t N, const double* w,
-                                   const double* b, double* r, double* part, int chunks, int64_t np,
+                                   const double* b, const double* rowsum, double* r, double* P, int64_t np,
                                    DevStatus* st, cudaStream_t s);
 
 // K5/K6 helpers.  r_max below is max_j |r_j| as kept in st->r_max_bits.

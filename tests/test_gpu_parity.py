@@ -105,7 +105,7 @@ def test_cholesky_fp64_elementwise(ctx, n):
     assert np.abs(Lg - Lo).max() <= 1e-12 * np.abs(Lo).max()
 
 
-@pytest.mark.parametrize("prec,tol", [("tf32x3", 2e-4), ("tf32", 5e-3)])
+@pytest.mark.parametrize("prec,tol", [("tf32x3", 2e-4), ("tf32", 5e-3), ("fp16x3", 2e-4), ("fp16", 5e-3)])
 @pytest.mark.parametrize("n", [130, 300, 1100, 2100])
 def test_cholesky_tensor_core_normwise(ctx, prec, tol, n):
     # one panel (n <= 1024), a trapezoid (1100), several panels (2100)
@@ -150,7 +150,7 @@ def test_cholesky_fp32_normwise(ctx, n):
 
 
 # ------------------------------------------------------------ full solve
-@pytest.mark.parametrize("prec", ["fp32", "fp64", "tf32x3", "auto"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "tf32x3", "fp16x3", "auto"])
 @pytest.mark.parametrize("n,m,t", [(2, 1, 0.7), (3, 2, 1.0), (5, 3, 0.4), (17, 8, 1.0), (129, 8, 1.0),
                                    (257, 16, 0.5), (1000, 8, 1.0), (1031, 3, 10.0), (600, 40, 0.8),
                                    (2500, 8, 1.0), (2049, 3, 30.0)])
@@ -295,7 +295,7 @@ def test_batch_matches_oracle(ctx):
 
 # ----------------------------------------------------- residual modes a5
 @pytest.mark.parametrize("resid", ["matrix_free", "stored", "auto"])
-@pytest.mark.parametrize("prec", ["tf32x3", "bf16", "fp64"])
+@pytest.mark.parametrize("prec", ["tf32x3", "fp16x3", "bf16", "fp16", "fp64"])
 @pytest.mark.parametrize("n,m,t", [(300, 8, 1.0), (1500, 3, 5.0), (2100, 8, 20.0)])
 def test_residual_modes_match_oracle(ctx, resid, prec, n, m, t):
     X = _cloud(n, m, seed=77 + n)
