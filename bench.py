@@ -180,13 +180,14 @@ def run_ours(a):
     ctx = M.Context(opts)
     dmin, bound = ctx.min_distance(Xd)
     ts = [bound if s.strip() == "bound" else float(s) for s in a.ts.split(",")]
-    wbuf = torch.empty(a.n, dtype=torch.float64, device=dev)
+    Wbuf = torch.empty(len(ts), a.n, dtype=torch.float64, device=dev)
 
     def step(acc=None):
-        for t in ts:
-            _, mag, info = ctx.solve(Xd, t, w=wbuf)
-            if acc is not None:
-                acc.append((t, mag, info))
+        # one call for the step's t values: distances are computed once per
+        # call (and freed with it), Z and the factor once per t
+        _, mags, infos_t = ctx.solve_multi(Xd, ts, W=Wbuf)
+        if acc is not None:
+            acc.extend(zip(ts, mags, infos_t))
 
     for _ in range(a.warmup):
         step()
@@ -228,7 +229,6 @@ def run_ours(a):
     e2e = None
     if not a.no_e2e:
         Xh = torch.from_numpy(X).pin_memory()
-        wh = torch.empty(a.n, dtype=torch.float64).pin_memory()
         Xe = torch.empty_like(Xd)
         h2d = Xh.numel() * 8
         d2h = a.n * 8 * len(ts)
@@ -236,12 +236,12 @@ def run_ours(a):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         f2 = 0.0
+        Wh = torch.empty(len(ts), a.n, dtype=torch.float64).pin_memory()
         for _ in range(a.steps):
             Xe.copy_(Xh, non_blocking=True)
-            for t in ts:
-                _, mag, info = ctx.solve(Xe, t, w=wbuf)
-                wh.copy_(wbuf, non_blocking=True)
-                f2 += info["useful_flops"]
+            _, mags, infos_t = ctx.solve_multi(Xe, ts, W=Wbuf)
+            Wh.copy_(Wbuf, non_blocking=True)
+            f2 += sum(i["useful_flops"] for i in infos_t)
             torch.cuda.synchronize(dev)
         el = time.perf_counter() - t0
         barrier()
@@ -299,7 +299,8 @@ def run_ours(a):
                                       f"{len(ts)} solves to rel. residual <= 1e-14",
                           "n": a.n, "m": a.m, "t": ts, "precision": a.precision, "residual_mode": a.resid,
                           "parallelism": f"replicas x{world}",
-                          "l2": "inputs larger than L2 (packed factor tiles of several GB per solve)"},
+                          "l2": "inputs larger than L2 (packed factor tiles of several GB per solve)",
+                          "api": "mag_solve_multi (one call per step for all t; distances computed once per call)"},
                "solve_s": sum(p["solve_s"] for p in per_t), "per_t": per_t,
                "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
                "min_distance": dmin}
@@ -351,6 +352,33 @@ def run_extras(ctx, a, out):
     ctx.grad(Xn, 2.0)
     torch.cuda.synchronize()
     ex["grad_n8192_m16_s"] = time.perf_counter() - t0
+    # batch: 512 clouds in R^32 x 8 values of t (device-timed), and the same
+    # problems one by one with the FP64 factor on a sample, for solves/s
+    clouds, tvals = workloads.batch_clouds()
+    cl = [torch.from_numpy(c).cuda() for c in clouds]
+    ctx.set_options(M.Options())
+    ctx.solve_batch(cl[:16], list(tvals))  # warm-up and tuner
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    _, _, sts = ctx.solve_batch(cl, list(tvals))
+    e1.record()
+    torch.cuda.synchronize()
+    nsolves = len(cl) * len(tvals)
+    ex["batch_solves"] = nsolves
+    ex["batch_s"] = e0.elapsed_time(e1) / 1e3
+    ex["batch_solves_per_s"] = nsolves / ex["batch_s"]
+    ex["batch_failed"] = int((sts != 0).sum())
+    ctx.set_options(M.Options(precision="fp64"))
+    sample = [(c, t) for c in cl[::64] for t in tvals[::4]]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c, t in sample:
+        ctx.solve(c, float(t))
+    torch.cuda.synchronize()
+    ex["per_instance_fp64_solves_per_s"] = len(sample) / (time.perf_counter() - t0)
+    ex["per_instance_fp64_sample"] = f"{len(sample)} problems (every 64th cloud, t[0] and t[4])"
+    ctx.set_options(M.Options(precision=a.precision, residual_mode=a.resid, profile=True))
     out["extras"] = ex
 
 

@@ -84,7 +84,10 @@ typedef struct mag_options {
   int32_t panel_tiles;    /* outer panel width in 128-wide tiles (0 = default)  */
   double workspace_limit_bytes; /* 0 = no limit; larger requests give ENOMEM     */
   int32_t profile;        /* 1: time the trailing-update kernel with CUDA events */
-  int32_t reserved;
+  int32_t reuse_distances;/* 1 (default): inside one mag_solve_multi or
+                             mag_sweep_tplus call, keep the FP64 distances in
+                             device memory (n^2/2 doubles) and regenerate Z for
+                             each t from them when they fit; 0: recompute      */
 } mag_options;
 
 /* Diagnostics of one call (all fields written when info != NULL). */
@@ -164,6 +167,15 @@ int mag_cholesky_factor(mag_ctx* ctx, const double* points, int64_t n, int32_t m
  * factor when allow_fallback is set.  MAG_ENOCONV returns the best w found. */
 int mag_solve(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t, double* w,
               double* mag, mag_info* info);
+
+/* a2-a7 for several values of t on the same points (Sec. 2: Z = exp[-t d]
+ * shares d across t): ts (host, nt values), W (device, nt x n row-major: the
+ * weighting of ts[i] in row i), mags (host, nt), infos (host, nt, nullable).
+ * The FP64 distances are computed once and kept for the call (see
+ * reuse_distances).  Returns the first non-OK status; later t values are still
+ * solved. */
+int mag_solve_multi(mag_ctx* ctx, const double* points, int64_t n, int32_t m, const double* ts, int32_t nt,
+                    double* W, double* mags, mag_info* infos);
 
 /* The same solve for a general right-hand side: Z x = b (b: device, n).  Used
  * for the adjoint solve lambda = Z^{-1} dL/dw of mag_grad. */

@@ -41,7 +41,7 @@ class mag_options(ctypes.Structure):
                 ("ir_tol", ctypes.c_double), ("ir_max_iters", ctypes.c_int32),
                 ("gmres_max_iters", ctypes.c_int32), ("allow_fallback", ctypes.c_int32),
                 ("panel_tiles", ctypes.c_int32), ("workspace_limit_bytes", ctypes.c_double),
-                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("reuse_distances", ctypes.c_int32)]
 
 
 class mag_info(ctypes.Structure):
@@ -84,6 +84,7 @@ SIGNATURES = {
     "mag_similarity_matrix": (ctypes.c_int, [_P, _P, _I64, _I32, _D, _I32, _P]),
     "mag_cholesky_factor": (ctypes.c_int, [_P, _P, _I64, _I32, _D, _I32, _P]),
     "mag_solve": (ctypes.c_int, [_P, _P, _I64, _I32, _D, _P, _DP, ctypes.POINTER(mag_info)]),
+    "mag_solve_multi": (ctypes.c_int, [_P, _P, _I64, _I32, _DP, _I32, _P, _DP, ctypes.POINTER(mag_info)]),
     "mag_solve_rhs": (ctypes.c_int, [_P, _P, _I64, _I32, _D, _P, _P, ctypes.POINTER(mag_info)]),
     "mag_residual": (ctypes.c_int, [_P, _P, _I64, _I32, _D, _P, _P, _P, _DP]),
     "mag_residual_noalloc": (ctypes.c_int, [_P, _I64, _I32, _D, _P, _P, _P, _DP, _P]),
@@ -138,6 +139,7 @@ class Options:
     panel_tiles: int = 0
     workspace_limit_bytes: float = 0.0
     profile: bool = False
+    reuse_distances: bool = True
 
     def to_c(self) -> mag_options:
         o = mag_options()
@@ -152,6 +154,7 @@ class Options:
         o.panel_tiles = self.panel_tiles
         o.workspace_limit_bytes = self.workspace_limit_bytes
         o.profile = int(self.profile)
+        o.reuse_distances = int(self.reuse_distances)
         return o
 
 
@@ -248,6 +251,21 @@ class Context:
         d["status"] = st
         return w, mag.value, d
 
+    def solve_multi(self, X: torch.Tensor, ts, W: torch.Tensor | None = None):
+        """Weightings for several t on the same points (distances computed once).
+        Returns (W [len(ts), n], mags list, infos list)."""
+        X = self._points(X)
+        n, m = X.shape
+        nt = len(ts)
+        if W is None:
+            W = torch.empty(nt, n, dtype=torch.float64, device=self.device)
+        tt = (ctypes.c_double * nt)(*[float(t) for t in ts])
+        mg = (ctypes.c_double * nt)()
+        infos = (mag_info * nt)()
+        self._check(self._lib.mag_solve_multi(self._h, _P(X.data_ptr()), n, m, ctypes.cast(tt, _DP), nt,
+                                              _P(W.data_ptr()), ctypes.cast(mg, _DP), infos))
+        return W, list(mg), [i.as_dict() for i in infos]
+
     def solve_rhs(self, X: torch.Tensor, t: float, b: torch.Tensor):
         X = self._points(X)
         n, m = X.shape
@@ -324,10 +342,13 @@ class Context:
         M = torch.empty(len(descs), dtype=torch.float64, device=self.device)
         S = torch.empty(len(descs), dtype=torch.int32, device=self.device)
         info = mag_info()
+        S.fill_(-1)
         st = self._lib.mag_solve_batch(self._h, D, len(descs), _P(P.data_ptr()), _P(W.data_ptr()),
                                        _P(M.data_ptr()), _P(S.data_ptr()), ctypes.byref(info))
-        self._check(st, (MAG_OK, MAG_ENOCONV))
-        ws, k = [], 0
+        # per-problem failures are reported in S; raise only for a call-level error
+        if st != MAG_OK and not bool((S == st).any()):
+            self._check(st)
+        ws = []
         for d in descs:
             ws.append(W[d.w_offset:d.w_offset + d.n])
         return ws, M.reshape(len(flat), len(ts)), S.reshape(len(flat), len(ts))

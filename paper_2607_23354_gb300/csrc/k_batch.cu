@@ -1,0 +1,435 @@
+// K8: many small solves (uneven point clouds x values of t) in one persistent
+// launch.  Each CTA pops a problem from a global work queue (problems sorted
+// by decreasing n on the host, so the largest start first) and solves it
+// alone in its own global scratch:
+//
+//   Z  = exp(-t d)        FP64 full square (residual) + FP32 lower (factor),
+//                         from FP64 distances computed once per cloud
+//   Z  = L L^T            FP32 blocked right-looking Cholesky, B x B blocks
+//   w  = (L L^T)^{-1} 1   FP32 blocked substitution
+//   refinement            r = 1 - Z w in FP64 (compensated), w += solve(r / |r|)
+//                         until |r| / (|Z| |w|) <= tol, at most max_iter steps
+//   Mag = 1^T w           compensated
+//
+// A problem whose FP32 factor meets a non-positive pivot, or whose refinement
+// stalls, is reported in its status and left to the host to re-solve with the
+// single-problem path (which escalates precision).  The block size B is a
+// template parameter chosen by the host-side tuner.
+#include <algorithm>
+
+#include "mag_internal.cuh"
+#include "mag_math.cuh"
+
+namespace mag {
+
+namespace {
+
+constexpr int BT = 512;  // threads per CTA
+
+__device__ __forceinline__ void two_sum_d(double a, double b, double* s, double* e) {
+  const double x = a + b;
+  const double bv = x - a;
+  *e = (a - (x - bv)) + (b - bv);
+  *s = x;
+}
+
+// Packed lower distances of one cloud: D[i(i-1)/2 + j] = ||x_i - x_j||, j < i.
+__global__ void __launch_bounds__(256) k_batch_dist(const double* __restrict__ X, const BatchCloud* clouds,
+                                                    int nclouds, double* __restrict__ D, int* cloud_flags) {
+  int flags = 0;
+  const BatchCloud c = clouds[blockIdx.y];
+  const int64_t npairs = (int64_t)c.n * (c.n - 1) / 2;
+  const double* P = X + c.point_offset;
+  double* out = D + c.dist_offset;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < npairs;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = (int64_t)((1.0 + sqrt(1.0 + 8.0 * (double)q)) * 0.5);
+    while (i * (i - 1) / 2 > q) --i;
+    while ((i + 1) * i / 2 <= q) ++i;
+    const int64_t j = q - i * (i - 1) / 2;
+    double s = 0.0;
+    for (int l = 0; l < c.m; ++l) {
+      const double d = P[i * c.m + l] - P[j * c.m + l];
+      s = fma(d, d, s);
+    }
+    out[q] = sqrt(s);
+    if (!isfinite(s))
+      flags |= 1;
+    else if (s == 0.0)
+      flags |= 2;
+  }
+  if (flags) atomicOr(cloud_flags + blockIdx.y, flags);
+}
+
+// ---------------------------------------------------------- per-CTA pieces
+struct Scratch {
+  float* Lf;    // n x n row-major, lower triangle used
+  double* Zd;   // n x n row-major, full symmetric FP64 Z
+  double* w;    // n
+  double* r;    // n
+  float* v;     // n (FP32 right-hand side / solution)
+};
+
+// FP32 Cholesky of the n x n lower triangle of A (row stride n) in place.
+// Returns false on a non-positive pivot.
+template <int B>
+__device__ bool cta_cholesky(float* A, int n, float* sm, int* flag) {
+  float* D = sm;                    // [B][B+1] diagonal block
+  float* Pi = sm + B * (B + 1);     // [B][B+1] panel block of tile row bi
+  float* Pj = Pi + B * (B + 1);     // [B][B+1] panel block of tile row bj
+  const int tid = threadIdx.x;
+  const int nb = (n + B - 1) / B;
+  for (int kb = 0; kb < nb; ++kb) {
+    const int k0 = kb * B, kw = min(B, n - k0);
+    // (a) factor the diagonal block in shared memory (unscaled elimination)
+    __syncthreads();
+    for (int e = tid; e < B * B; e += BT) {
+      const int r = e / B, c = e % B;
+      D[r * (B + 1) + c] = (r < kw && c < kw && c <= r) ? A[(int64_t)(k0 + r) * n + k0 + c] : 0.0f;
+    }
+    __syncthreads();
+    for (int c = 0; c < kw - 1; ++c) {
+      const float p = D[c * (B + 1) + c];
+      const float pinv = p > 0.0f ? 1.0f / p : 0.0f;
+      const int w = kw - 1 - c;
+      for (int e = tid; e < w * w; e += BT) {
+        const int r = c + 1 + e / w, cc = c + 1 + e % w;
+        if (cc <= r) D[r * (B + 1) + cc] -= D[r * (B + 1) + c] * D[cc * (B + 1) + c] * pinv;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) *flag = 0;
+    __syncthreads();
+    if (tid < kw) {
+      const float p = D[tid * (B + 1) + tid];
+      if (!(p > 0.0f)) *flag = 1;
+    }
+    __syncthreads();
+    if (*flag) return false;
+    // scale: L[r][c] = D[r][c] / sqrt(p_c), L[c][c] = sqrt(p_c)
+    for (int e = tid; e < kw * kw; e += BT) {
+      const int r = e / kw, c = e % kw;
+      if (c < r) D[r * (B + 1) + c] *= rsqrtf(D[c * (B + 1) + c]);
+    }
+    __syncthreads();
+    if (tid < kw) D[tid * (B + 1) + tid] = sqrtf(D[tid * (B + 1) + tid]);
+    __syncthreads();
+    for (int e = tid; e < kw * kw; e += BT) {
+      const int r = e / kw, c = e % kw;
+      if (c <= r) A[(int64_t)(k0 + r) * n + k0 + c] = D[r * (B + 1) + c];
+    }
+    // (b) panel: rows i >= k0 + kw, x L^T = a (forward substitution per row)
+    for (int i = k0 + kw + tid; i < n; i += BT) {
+      float x[B];
+      float* row = A + (int64_t)i * n + k0;
+#pragma unroll
+      for (int c = 0; c < B; ++c) x[c] = c < kw ? row[c] : 0.0f;
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        if (c < kw) {
+          float s = x[c];
+#pragma unroll
+          for (int cc = 0; cc < c; ++cc) s -= x[cc] * D[c * (B + 1) + cc];
+          x[c] = s / D[c * (B + 1) + c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < B; ++c)
+        if (c < kw) row[c] = x[c];
+    }
+    __syncthreads();
+    // (c) trailing update of the lower tiles (bi, bj), kb < bj <= bi
+    for (int bi = kb + 1; bi < nb; ++bi) {
+      const int i0 = bi * B, iw = min(B, n - i0);
+      __syncthreads();
+      for (int e = tid; e < B * B; e += BT) {
+        const int r = e / B, c = e % B;
+        Pi[r * (B + 1) + c] = (r < iw && c < kw) ? A[(int64_t)(i0 + r) * n + k0 + c] : 0.0f;
+      }
+      for (int bj = kb + 1; bj <= bi; ++bj) {
+        const int j0 = bj * B, jw = min(B, n - j0);
+        __syncthreads();
+        for (int e = tid; e < B * B; e += BT) {
+          const int r = e / B, c = e % B;
+          Pj[r * (B + 1) + c] = (r < jw && c < kw) ? A[(int64_t)(j0 + r) * n + k0 + c] : 0.0f;
+        }
+        __syncthreads();
+        // each thread: (B*B/BT) outputs, rows ty + (BT/B')..; use a 2D split
+        constexpr int TPR = BT / B;       // threads per output row
+        constexpr int OPT = B / TPR;      // outputs per thread along the row
+        const int r = tid / TPR, c0 = tid % TPR;
+        float acc[OPT];
+#pragma unroll
+        for (int q = 0; q < OPT; ++q) acc[q] = 0.0f;
+#pragma unroll 8
+        for (int k = 0; k < B; ++k) {
+          const float a = Pi[r * (B + 1) + k];
+#pragma unroll
+          for (int q = 0; q < OPT; ++q) acc[q] = fmaf(a, Pj[(c0 + q * TPR) * (B + 1) + k], acc[q]);
+        }
+        if (r < iw) {
+#pragma unroll
+          for (int q = 0; q < OPT; ++q) {
+            const int c = c0 + q * TPR;
+            if (c < jw && (bi != bj || c <= r)) A[(int64_t)(i0 + r) * n + j0 + c] -= acc[q];
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// v <- (L L^T)^{-1} v with the FP32 factor (blocked; block solves by warp 0).
+template <int B>
+__device__ void cta_solve(const float* L, int n, float* v, float* sm) {
+  float* blk = sm;  // [B] block values
+  const int tid = threadIdx.x;
+  const int nb = (n + B - 1) / B;
+  // forward: L y = v
+  for (int kb = 0; kb < nb; ++kb) {
+    const int k0 = kb * B, kw = min(B, n - k0);
+    __syncthreads();
+    if (tid < 32) {
+      for (int r = 0; r < kw; ++r) {
+        const float* Lr = L + (int64_t)(k0 + r) * n + k0;
+        float s = 0.0f;
+        for (int c = tid; c < r; c += 32) s += Lr[c] * blk[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (tid == 0) blk[r] = (v[k0 + r] - s) / Lr[r];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < kw; e += BT) v[k0 + e] = blk[e];
+    for (int i = k0 + kw + tid; i < n; i += BT) {
+      const float* Li = L + (int64_t)i * n + k0;
+      float s = 0.0f;
+      for (int c = 0; c < kw; ++c) s += Li[c] * blk[c];
+      v[i] -= s;
+    }
+  }
+  // backward: L^T x = y
+  for (int kb = nb - 1; kb >= 0; --kb) {
+    const int k0 = kb * B, kw = min(B, n - k0);
+    __syncthreads();
+    if (tid < 32) {
+      for (int r = kw - 1; r >= 0; --r) {
+        float s = 0.0f;
+        for (int c = r + 1 + tid; c < kw; c += 32) s += L[(int64_t)(k0 + c) * n + k0 + r] * blk[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (tid == 0) blk[r] = (v[k0 + r] - s) / L[(int64_t)(k0 + r) * n + k0 + r];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < kw; e += BT) v[k0 + e] = blk[e];
+    // x_i -= sum_{c in block} L[k0+c][i] x_c for i < k0
+    for (int i = tid; i < k0; i += BT) {
+      float s = 0.0f;
+      for (int c = 0; c < kw; ++c) s += L[(int64_t)(k0 + c) * n + i] * blk[c];
+      v[i] -= s;
+    }
+  }
+  __syncthreads();
+}
+
+template <int B>
+__global__ void __launch_bounds__(BT, 1)
+    k_batch_solve(const BatchProblem* __restrict__ probs, const int* __restrict__ order, int count,
+                  const double* __restrict__ D, const int* __restrict__ cloud_flags, float* scratch_f,
+                  double* scratch_d, int64_t nmax,
+                  double* __restrict__ w_out, double* __restrict__ mag_out, int* __restrict__ status,
+                  int* queue, double tol, int max_iter) {
+  extern __shared__ float smf[];
+  __shared__ int s_q, s_flag;
+  __shared__ double red[BT / 32][3];
+  __shared__ double exptab[128];
+  load_exp_table(exptab);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  Scratch S;
+  S.Lf = scratch_f + (int64_t)blockIdx.x * (nmax * nmax + nmax);
+  S.v = S.Lf + nmax * nmax;
+  S.Zd = scratch_d + (int64_t)blockIdx.x * (nmax * nmax + 2 * nmax);
+  S.w = S.Zd + nmax * nmax;
+  S.r = S.w + nmax;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_q = atomicAdd(queue, 1);
+    __syncthreads();
+    const int q = s_q;
+    if (q >= count) break;
+    const int pid = order[q];
+    const BatchProblem P = probs[pid];
+    const int n = P.n;
+    const int cf = cloud_flags[P.cloud];
+    if (cf) {  // uniform across the CTA: report and skip the problem
+      if (tid == 0) {
+        status[pid] = (cf & 1) ? MAG_BATCH_NONFINITE : MAG_BATCH_DUPLICATE;
+        mag_out[pid] = 0.0;
+      }
+      continue;
+    }
+    const double* Dc = D + P.dist_offset;
+    // ---- Z: FP64 full square and FP32 lower
+    for (int64_t e = tid; e < (int64_t)n * n; e += BT) {
+      const int i = (int)(e / n), j = (int)(e % n);
+      double z = 1.0;
+      if (i != j) {
+        const int a = i > j ? i : j, b = i > j ? j : i;
+        z = exp_neg(-P.t * Dc[(int64_t)a * (a - 1) / 2 + b], exptab);
+      }
+      S.Zd[e] = z;
+      if (j <= i) S.Lf[e] = (float)z;
+    }
+    __syncthreads();
+    int st = MAG_BATCH_OK;
+    if (!cta_cholesky<B>(S.Lf, n, smf, &s_flag)) st = MAG_BATCH_NOTPD;
+    double rel = INFINITY;
+    if (st == MAG_BATCH_OK) {
+      for (int i = tid; i < n; i += BT) S.v[i] = 1.0f;
+      cta_solve<B>(S.Lf, n, S.v, smf);
+      for (int i = tid; i < n; i += BT) S.w[i] = (double)S.v[i];
+      __syncthreads();
+      double prev = INFINITY;
+      int slow = 0;
+      for (int it = 0;; ++it) {
+        // r = 1 - Z w (warp per row, Kahan per lane, TwoSum across lanes)
+        double rmax = 0.0, zmax = 0.0, wmax = 0.0;
+        for (int i = warp; i < n; i += BT / 32) {
+          const double* Zi = S.Zd + (int64_t)i * n;
+          double s = 0.0, c = 0.0, zs = 0.0;
+          for (int j = lane; j < n; j += 32) {
+            const double z = Zi[j];
+            zs += z;
+            const double y = fma(z, S.w[j], -c);
+            const double tt = s + y;
+            c = (tt - s) - y;
+            s = tt;
+          }
+          s -= c;
+          c = 0.0;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            double hi, lo;
+            const double other = __shfl_xor_sync(0xffffffffu, s, o);
+            const double oc = __shfl_xor_sync(0xffffffffu, c, o);
+            two_sum_d(s, other, &hi, &lo);
+            s = hi;
+            c += oc + lo;
+            zs += __shfl_xor_sync(0xffffffffu, zs, o);
+          }
+          const double ri = (1.0 - s) - c;
+          if (lane == 0) S.r[i] = ri;
+          rmax = fmax(rmax, fabs(ri));
+          zmax = fmax(zmax, zs);
+          wmax = fmax(wmax, fabs(S.w[i]));
+        }
+        if (lane == 0) {
+          red[warp][0] = rmax;
+          red[warp][1] = zmax;
+          red[warp][2] = wmax;
+        }
+        __syncthreads();
+        double rn = 0.0, zn = 0.0, wn = 0.0;
+        for (int k = 0; k < BT / 32; ++k) {
+          rn = fmax(rn, red[k][0]);
+          zn = fmax(zn, red[k][1]);
+          wn = fmax(wn, red[k][2]);
+        }
+        rel = (zn > 0.0 && wn > 0.0) ? rn / (zn * wn) : INFINITY;
+        __syncthreads();
+        if (rel <= tol) break;
+        if (it >= max_iter || !(rel < INFINITY) || (rel > 0.5 * prev && ++slow >= 2)) {
+          st = MAG_BATCH_NOCONV;
+          break;
+        }
+        if (!(rel > 0.5 * prev)) slow = 0;
+        prev = rel;
+        const double inv = rn > 0.0 ? 1.0 / rn : 0.0;
+        for (int i = tid; i < n; i += BT) S.v[i] = (float)(S.r[i] * inv);
+        cta_solve<B>(S.Lf, n, S.v, smf);
+        for (int i = tid; i < n; i += BT) S.w[i] += rn * (double)S.v[i];
+        __syncthreads();
+      }
+    }
+    // ---- outputs: w, Mag (compensated), status
+    double s = 0.0, c = 0.0;
+    for (int i = tid; i < n; i += BT) {
+      const double wi = S.w[i];
+      w_out[P.w_offset + i] = wi;
+      double hi, lo;
+      two_sum_d(s, wi, &hi, &lo);
+      s = hi;
+      c += lo;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double hi, lo;
+      const double other = __shfl_xor_sync(0xffffffffu, s, o);
+      const double oc = __shfl_xor_sync(0xffffffffu, c, o);
+      two_sum_d(s, other, &hi, &lo);
+      s = hi;
+      c += oc + lo;
+    }
+    if (lane == 0) {
+      red[warp][0] = s;
+      red[warp][1] = c;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double ss = 0.0, cc = 0.0;
+      for (int k = 0; k < BT / 32; ++k) {
+        double hi, lo;
+        two_sum_d(ss, red[k][0], &hi, &lo);
+        ss = hi;
+        cc += red[k][1] + lo;
+      }
+      mag_out[pid] = ss + cc;
+      status[pid] = st;
+    }
+  }
+}
+
+template <int B>
+cudaError_t launch_batch_t(const BatchProblem* probs, const int* order, int count, const double* D,
+                           const int* cloud_flags, float* scratch_f, double* scratch_d, int64_t nmax,
+                           double* w_out, double* mag_out, int* status, int* queue, double tol, int max_iter,
+                           int grid, cudaStream_t s) {
+  const size_t smem = 3 * (size_t)B * (B + 1) * sizeof(float);
+  auto kern = k_batch_solve<B>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, BT, smem, s>>>(probs, order, count, D, cloud_flags, scratch_f, scratch_d, nmax, w_out, mag_out,
+                              status, queue, tol, max_iter);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_batch_dist(const double* X, const BatchCloud* clouds, int nclouds, int64_t max_pairs,
+                              double* D, int* cloud_flags, cudaStream_t s) {
+  if (nclouds <= 0) return cudaSuccess;
+  const unsigned bx = (unsigned)std::min<int64_t>((max_pairs + 255) / 256, 256);
+  k_batch_dist<<<dim3(bx > 0 ? bx : 1, (unsigned)nclouds), 256, 0, s>>>(X, clouds, nclouds, D, cloud_flags);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_solve(int block, const BatchProblem* probs, const int* order, int count,
+                               const double* D, const int* cloud_flags, float* scratch_f, double* scratch_d,
+                               int64_t nmax, double* w_out, double* mag_out, int* status, int* queue, double tol,
+                               int max_iter, int grid, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (block == 32)
+    return launch_batch_t<32>(probs, order, count, D, cloud_flags, scratch_f, scratch_d, nmax, w_out, mag_out,
+                              status, queue, tol, max_iter, grid, s);
+  return launch_batch_t<64>(probs, order, count, D, cloud_flags, scratch_f, scratch_d, nmax, w_out, mag_out,
+                            status, queue, tol, max_iter, grid, s);
+}
+
+}  // namespace mag

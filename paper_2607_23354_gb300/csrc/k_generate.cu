@@ -15,6 +15,7 @@
 // bound used to choose the factor precision), min off-diagonal d^2 (the Sec. 1
 // bound), and flags for non-finite coordinates and coincident points.
 #include "mag_internal.cuh"
+#include "mag_math.cuh"
 
 namespace mag {
 
@@ -30,15 +31,17 @@ __device__ inline void atomic_max_nonneg(unsigned long long* a, double v) {
   atomicMax(a, (unsigned long long)__double_as_longlong(v));
 }
 
-template <bool WF, bool WD, bool ROWSUM>
+template <bool WF, bool WD, bool ROWSUM, bool WDIST>
 __global__ void __launch_bounds__(GEN_THREADS, 1)
     k_generate(const double* __restrict__ X, int64_t n, int m, double t, float* __restrict__ Zf,
-               double* __restrict__ Zd, double* __restrict__ rowsum, DevStatus* st) {
+               double* __restrict__ Zd, double* __restrict__ Dd, double* __restrict__ rowsum, DevStatus* st) {
   extern __shared__ double smem[];
   double* xr = smem;                   // [TILE][GEN_MC] row points (broadcast reads)
   double* xc = smem + TILE * GEN_MC;   // [GEN_MC][TILE] column points (conflict free)
   __shared__ double colpart[GEN_THREADS / 32][TILE];
   __shared__ double warpmin[GEN_THREADS / 32];
+  __shared__ double exptab[128];
+  if (WD) load_exp_table(exptab);
 
   int64_t I, J;
   tri_coords((int64_t)blockIdx.x, &I, &J);
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
       const int c = lane + 32 * q;
       const int64_t gc = col0 + c;
       const double v = d2[i][q];
-      double zd = 0.0;
+      double zd = 0.0, dd = 0.0;
       float zf = 0.0f;
       if (gr >= n || gc >= n || gr == gc) {
         zd = (gr == gc) ? 1.0 : 0.0;
@@ -105,11 +108,13 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
         if (!isfinite(v)) flags |= ST_NONFINITE;
         else if (v == 0.0) flags |= ST_DUPLICATE;
         mind2 = fmin(mind2, v);
-        if (WD) zd = exp(-t * sqrt(v));
+        if (WD || WDIST) dd = sqrt(v);
+        if (WD) zd = exp_neg(-t * dd, exptab);
         if (WF) zf = WD ? (float)zd : expf(-tf * sqrtf((float)v));
       }
       if (WF) Zf[tile_off + (int64_t)r * TILE + c] = zf;
       if (WD) Zd[tile_off + (int64_t)r * TILE + c] = zd;
+      if (WDIST) Dd[tile_off + (int64_t)r * TILE + c] = dd;
       if (ROWSUM && gr < n && gc < n) {
         const double z = WD ? zd : (double)zf;
         rs[i] += z;
@@ -151,6 +156,63 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
   }
 }
 
+// Z from stored FP64 distances (same layout): one CTA per lower tile, FP64
+// exp only.  Tiles of the padding get the identity, as in k_generate.
+template <bool WF, bool WD>
+__global__ void __launch_bounds__(256) k_generate_from_dist(const double* __restrict__ Dd, int64_t n, double t,
+                                                            float* __restrict__ Zf, double* __restrict__ Zd,
+                                                            double* __restrict__ rowsum) {
+  __shared__ double exptab[128];
+  __shared__ double colpart[8][TILE];
+  load_exp_table(exptab);
+  __syncthreads();
+  int64_t I, J;
+  tri_coords((int64_t)blockIdx.x, &I, &J);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t off = tri_index(I, J) * TILE_ELEMS;
+  const float tf = (float)t;
+  double cs[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int i = 0; i < 16; ++i) {
+    const int r = warp * 16 + i;
+    const int64_t gr = I * TILE + r;
+    double rs = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = lane + 32 * q;
+      const int64_t gc = J * TILE + c;
+      const int64_t e = off + (int64_t)r * TILE + c;
+      double zd;
+      float zf;
+      if (gr >= n || gc >= n || gr == gc) {
+        zd = (gr == gc) ? 1.0 : 0.0;
+        zf = (float)zd;
+        if (gr == gc && gr < n) rs += 1.0;  // the diagonal counts in its row sum
+      } else {
+        const double d = Dd[e];
+        zd = WD ? exp_neg(-t * d, exptab) : 0.0;
+        zf = WD ? (float)zd : expf(-tf * (float)d);
+        const double z = WD ? zd : (double)zf;
+        rs += z;
+        cs[q] += z;
+      }
+      if (WF) Zf[e] = zf;
+      if (WD) Zd[e] = zd;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+    if (lane == 0 && gr < n) atomicAdd(rowsum + gr, rs);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) colpart[warp][lane + 32 * q] = cs[q];
+  __syncthreads();
+  if (I != J && threadIdx.x < TILE) {
+    double v = 0.0;
+    for (int w = 0; w < 8; ++w) v += colpart[w][threadIdx.x];
+    const int64_t gc = J * TILE + threadIdx.x;
+    if (gc < n) atomicAdd(rowsum + gc, v);
+  }
+}
+
 __global__ void k_rowsum_max(const double* __restrict__ rowsum, int64_t n, DevStatus* st) {
   double v = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -161,15 +223,15 @@ __global__ void k_rowsum_max(const double* __restrict__ rowsum, int64_t n, DevSt
   if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&st->off_max_bits, fmax(v, 0.0));
 }
 
-template <bool WF, bool WD, bool ROWSUM>
+template <bool WF, bool WD, bool ROWSUM, bool WDIST = false>
 cudaError_t launch_gen_t(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
-                         double* Zd, double* rowsum, DevStatus* st, cudaStream_t s) {
+                         double* Zd, double* rowsum, DevStatus* st, cudaStream_t s, double* Dd = nullptr) {
   const size_t smem = 2 * (size_t)TILE * GEN_MC * sizeof(double);
-  auto kern = k_generate<WF, WD, ROWSUM>;
+  auto kern = k_generate<WF, WD, ROWSUM, WDIST>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t tiles = num_lower_tiles(N);
-  kern<<<(unsigned)tiles, GEN_THREADS, smem, s>>>(X, n, m, t, Zf, Zd, rowsum, st);
+  kern<<<(unsigned)tiles, GEN_THREADS, smem, s>>>(X, n, m, t, Zf, Zd, Dd, rowsum, st);
   note_launch();
   return cudaGetLastError();
 }
@@ -182,6 +244,29 @@ cudaError_t launch_generate(const double* X, int64_t n, int m, double t, int64_t
   if (Zf) return launch_gen_t<true, false, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s);
   if (Zd) return launch_gen_t<false, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s);
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_generate_dist(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
+                                 double* Zd, double* Dd, double* rowsum, DevStatus* st, cudaStream_t s) {
+  if (Zf && Zd) return launch_gen_t<true, true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd);
+  if (Zf) return launch_gen_t<true, false, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd);
+  if (Zd) return launch_gen_t<false, true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_generate_from_dist(const double* Dd, int64_t n, double t, int64_t N, float* Zf, double* Zd,
+                                     double* rowsum, cudaStream_t s) {
+  const unsigned tiles = (unsigned)num_lower_tiles(N);
+  if (Zf && Zd)
+    k_generate_from_dist<true, true><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum);
+  else if (Zf)
+    k_generate_from_dist<true, false><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum);
+  else if (Zd)
+    k_generate_from_dist<false, true><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum);
+  else
+    return cudaErrorInvalidValue;
+  note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_min_distance(const double* X, int64_t n, int m, DevStatus* st, cudaStream_t s) {

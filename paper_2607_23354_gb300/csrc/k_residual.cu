@@ -15,6 +15,7 @@
 
 #include "../../include/magnitude.h"
 #include "mag_internal.cuh"
+#include "mag_math.cuh"
 
 namespace mag {
 
@@ -37,6 +38,8 @@ __global__ void __launch_bounds__(RES_THREADS) k_resid_mf(const double* __restri
   extern __shared__ double sm[];
   double* xc = sm;            // [ct][m]
   double* wc = sm + ct * m;   // [ct]
+  __shared__ double exptab[128];
+  load_exp_table(exptab);
   const int64_t j = (int64_t)blockIdx.x * RES_THREADS + threadIdx.x;
   const int64_t ntiles = (n + ct - 1) / ct;
   const int64_t per = (ntiles + chunks - 1) / chunks;
@@ -73,7 +76,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_resid_mf(const double* __restri
           d2 = fma(diff, diff, d2);
         }
       }
-      const double z = exp(-t * sqrt(d2));
+      const double z = exp_neg(-t * sqrt(d2), exptab);
       zs += z;
       // Kahan step for s += z * w_k
       const double y = fma(z, wc[q], -c);
@@ -319,6 +322,8 @@ __global__ void __launch_bounds__(RES_THREADS) k_grad(const double* __restrict__
   double* xc = sm;                 // [ct][m]
   double* wc = sm + ct * m;        // [ct]
   double* lc = sm + ct * (m + 1);  // [ct]
+  __shared__ double exptab[128];
+  load_exp_table(exptab);
   const int64_t i = (int64_t)blockIdx.x * RES_THREADS + threadIdx.x;
   const bool live = i < n;
   double xi[MR], g[MR];
@@ -350,7 +355,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_grad(const double* __restrict__
           d2 = fma(diff, diff, d2);
         }
       const double d = sqrt(d2);
-      const double z = exp(-t * d);
+      const double z = exp_neg(-t * d, exptab);
       // dL/dt contribution with Kahan compensation
       const double y = fma(li * d * z, wc[q], -st_c);
       const double tt = st_s + y;
@@ -393,6 +398,48 @@ __global__ void __launch_bounds__(1024) k_sum_f64(const double* __restrict__ v, 
     __syncthreads();
   }
   if (threadIdx.x == 0) *out = ss[0] + sc[0];
+}
+
+// GMRES helpers (FP64): out[i] = <V_i, w> for i < k (V: k rows of length ld),
+// one CTA per i; and w -= sum_i h[i] V_i; and x = s * w.
+__global__ void __launch_bounds__(256) k_mdot(const double* __restrict__ V, int64_t ld, int k,
+                                              const double* __restrict__ w, int64_t n, double* __restrict__ out) {
+  __shared__ double ss[256], sc[256];
+  const double* v = V + (int64_t)blockIdx.x * ld;
+  double s = 0.0, c = 0.0;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    double hi, lo;
+    two_sum(s, v[j] * w[j], &hi, &lo);
+    s = hi;
+    c += lo;
+  }
+  ss[threadIdx.x] = s;
+  sc[threadIdx.x] = c;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      double hi, lo;
+      two_sum(ss[threadIdx.x], ss[threadIdx.x + h], &hi, &lo);
+      ss[threadIdx.x] = hi;
+      sc[threadIdx.x] += sc[threadIdx.x + h] + lo;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = ss[0] + sc[0];
+}
+
+__global__ void k_maxpy(const double* __restrict__ V, int64_t ld, int k, const double* __restrict__ h,
+                        double* __restrict__ w, int64_t n) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double acc = w[j];
+  for (int i = 0; i < k; ++i) acc -= h[i] * V[(int64_t)i * ld + j];
+  w[j] = acc;
+}
+
+__global__ void k_scale(const double* __restrict__ w, double s, double* __restrict__ x, int64_t n) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) x[j] = s * w[j];
 }
 
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
@@ -469,6 +516,28 @@ cudaError_t launch_absmax(const double* v, int64_t n, DevStatus* st, cudaStream_
 
 cudaError_t launch_reduce_w(const double* w, int64_t n, DevStatus* st, cudaStream_t s) {
   k_reduce_w<<<1, 1024, 0, s>>>(w, n, st);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mdot(const double* V, int64_t ld, int k, const double* w, int64_t n, double* out,
+                        cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  k_mdot<<<k, 256, 0, s>>>(V, ld, k, w, n, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_maxpy(const double* V, int64_t ld, int k, const double* h, double* w, int64_t n,
+                         cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  k_maxpy<<<blocks_for(n, 256), 256, 0, s>>>(V, ld, k, h, w, n);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(const double* w, double sc, double* x, int64_t n, cudaStream_t s) {
+  k_scale<<<blocks_for(n, 256), 256, 0, s>>>(w, sc, x, n);
   note_launch();
   return cudaGetLastError();
 }

@@ -32,7 +32,8 @@ struct Layout {
   int chunks = 1;
   bool f32 = false, f64 = false;
   size_t off_zf = 0, off_zd = 0, off_dinvf = 0, off_dinvd = 0, off_vec = 0, off_part = 0,
-         off_status = 0, off_panel = 0, off_flags = 0, off_spart = 0, total = 0;
+         off_status = 0, off_panel = 0, off_flags = 0, off_spart = 0, off_dist = 0, total = 0;
+  bool dist = false;   // FP64 distance tiles present
   int nb = 8;          // panel width in tiles
   int64_t W = 0;       // panel width in columns (nb * TILE)
 };
@@ -59,6 +60,17 @@ struct mag_ctx {
   int64_t aux_np = 0;
   std::vector<cudaEvent_t> prof_ev;  // event pairs around trailing-update launches
   int prof_used = 0;
+  double* gm = nullptr;              // GMRES basis, zeros and small vectors
+  size_t gm_bytes = 0;
+  bool dist_active = false;          // inside a call that reuses distances
+  bool dist_valid = false;           // dist() holds the distances of dist_pts
+  const double* dist_pts = nullptr;
+  int64_t dist_n = 0;
+  int32_t dist_m = 0;
+  double dist_dmin = 0, dist_gersh_unused = 0;
+  void* bws = nullptr;               // batch workspace
+  size_t bws_bytes = 0;
+  int batch_block = 0;               // tuned factor block of the batch kernel (0 = not tuned)
   UpdMaps maps;                      // TMA descriptors of the panel buffer
   const void* maps_base = nullptr;
   int maps_mode = -1;
@@ -75,6 +87,7 @@ struct mag_ctx {
   }
   double* part() { return (double*)((char*)ws + lay.off_part); }
   double* spart() { return (double*)((char*)ws + lay.off_spart); }
+  double* dist() { return (double*)((char*)ws + lay.off_dist); }
   float* panel_hi() { return (float*)((char*)ws + lay.off_panel); }
   float* panel_lo() { return panel_hi() + (size_t)lay.np * lay.W; }
   DevStatus* st() { return (DevStatus*)((char*)ws + lay.off_status); }
@@ -119,7 +132,7 @@ double bits_to_double(unsigned long long b) {
   return d;
 }
 
-Layout plan(const mag_ctx* ctx, int64_t n, bool f32, bool f64) {
+Layout plan(const mag_ctx* ctx, int64_t n, bool f32, bool f64, bool dist = false) {
   Layout L;
   L.n = n;
   L.N = (n + TILE - 1) / TILE;
@@ -140,6 +153,9 @@ Layout plan(const mag_ctx* ctx, int64_t n, bool f32, bool f64) {
   off = align_up(off + (size_t)L.np * (NVEC_D * sizeof(double) + NVEC_F * sizeof(float)));
   L.off_part = off;
   off = align_up(off + (size_t)3 * L.chunks * L.np * sizeof(double));
+  L.dist = dist;
+  L.off_dist = off;  // placed before every precision-dependent region: stable offset
+  if (dist) off = align_up(off + (size_t)L.tiles * TILE_ELEMS * sizeof(double));
   L.nb = ctx->opt.panel_tiles > 0 ? ctx->opt.panel_tiles : 8;
   L.W = (int64_t)L.nb * TILE;
   L.off_panel = off;
@@ -159,7 +175,7 @@ Layout plan(const mag_ctx* ctx, int64_t n, bool f32, bool f64) {
 }
 
 int ensure_workspace(mag_ctx* ctx, int64_t n, bool f32, bool f64) {
-  Layout L = plan(ctx, n, f32, f64);
+  Layout L = plan(ctx, n, f32, f64, ctx->dist_active);
   if (ctx->opt.workspace_limit_bytes > 0 && (double)L.total > ctx->opt.workspace_limit_bytes)
     return fail(ctx, MAG_ENOMEM, "workspace of %.3g bytes exceeds the limit %.3g", (double)L.total,
                 ctx->opt.workspace_limit_bytes);
@@ -170,6 +186,7 @@ int ensure_workspace(mag_ctx* ctx, int64_t n, bool f32, bool f64) {
       ctx->ws = nullptr;
       ctx->ws_bytes = 0;
     }
+    ctx->dist_valid = false;  // any stored distances are gone with the old buffer
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, L.total);
     if (e != cudaSuccess) {
@@ -394,6 +411,8 @@ int mag_options_default(mag_options* opt) {
   opt->allow_fallback = 1;
   opt->panel_tiles = 0;
   opt->workspace_limit_bytes = 0.0;
+  opt->profile = 0;
+  opt->reuse_distances = 1;
   return MAG_OK;
 }
 
@@ -434,6 +453,8 @@ int mag_ctx_destroy(mag_ctx* ctx) {
   if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->aux) cudaFree(ctx->aux);
+  if (ctx->bws) cudaFree(ctx->bws);
+  if (ctx->gm) cudaFree(ctx->gm);
   for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
   for (int i = 0; i < 4; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
@@ -504,19 +525,60 @@ int generate(mag_ctx* ctx, const double* X, int32_t m, double t, bool f32, bool 
   TRY(reset_status(ctx));
   CU(cudaMemsetAsync(ctx->vd(V_ROWSUM), 0, L.np * sizeof(double), s));
   CU(cudaEventRecord(ctx->ev[0], s));
-  CU(launch_generate(X, L.n, m, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr,
-                     ctx->vd(V_ROWSUM), ctx->st(), s));
+  const bool reuse = ctx->dist_active && L.dist && ctx->dist_valid && ctx->dist_pts == X && ctx->dist_n == L.n &&
+                     ctx->dist_m == m;
+  if (reuse) {
+    CU(launch_generate_from_dist(ctx->dist(), L.n, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr,
+                                 ctx->vd(V_ROWSUM), s));
+  } else if (ctx->dist_active && L.dist) {
+    CU(launch_generate_dist(X, L.n, m, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr, ctx->dist(),
+                            ctx->vd(V_ROWSUM), ctx->st(), s));
+  } else {
+    CU(launch_generate(X, L.n, m, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr,
+                       ctx->vd(V_ROWSUM), ctx->st(), s));
+  }
   CU(launch_rowsum_max(ctx->vd(V_ROWSUM), L.n, ctx->st(), s));
   CU(cudaEventRecord(ctx->ev[1], s));
   TRY(read_status(ctx));
   R->ms_gen += elapsed(ctx, 0, 1);
+  if (reuse) {
+    R->dmin = ctx->dist_dmin;
+    R->gersh = 1.0 - bits_to_double(ctx->h_st->off_max_bits);
+    return MAG_OK;
+  }
   const int fl = ctx->h_st->flags;
   if (fl & ST_NONFINITE) return fail(ctx, MAG_EINVAL, "non-finite coordinate in points");
   const double d2 = bits_to_double(ctx->h_st->min_d2_bits);
   R->dmin = std::sqrt(d2);
   if ((fl & ST_DUPLICATE) || !(d2 > 0.0)) return fail(ctx, MAG_EDUPLICATE, "two points coincide (min d = 0)");
   R->gersh = 1.0 - bits_to_double(ctx->h_st->off_max_bits);
+  if (ctx->dist_active && L.dist) {
+    ctx->dist_valid = true;
+    ctx->dist_pts = X;
+    ctx->dist_n = L.n;
+    ctx->dist_m = m;
+    ctx->dist_dmin = R->dmin;
+  }
   return MAG_OK;
+}
+
+// Turn distance reuse on for one call when it is allowed and the FP64
+// distance tiles fit next to the largest workspace the solve may need.
+void begin_dist_reuse(mag_ctx* ctx, int64_t n) {
+  ctx->dist_valid = false;
+  ctx->dist_active = false;
+  if (!ctx->opt.reuse_distances) return;
+  size_t fre = 0, tot = 0;
+  if (cudaMemGetInfo(&fre, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  const Layout with = plan(ctx, n, true, true, true);
+  ctx->dist_active = (double)with.total <= 0.8 * ((double)fre + (double)ctx->ws_bytes);
+}
+void end_dist_reuse(mag_ctx* ctx) {
+  ctx->dist_active = false;
+  ctx->dist_valid = false;
 }
 
 int run_factor(mag_ctx* ctx, int prec, SolveResult* R) {
@@ -590,6 +652,125 @@ int residual(mag_ctx* ctx, const double* X, int32_t m, double t, const double* w
   R->wnorm = wn;
   *rel = (zn > 0 && wn > 0) ? rn / (zn * wn) : INFINITY;
   if (!std::isfinite(*rel)) *rel = INFINITY;
+  return MAG_OK;
+}
+
+// GMRES-IR (Carson & Higham, SIAM J. Sci. Comput. 40 (2018)): refinement whose
+// correction equation Z d = r is solved by GMRES(k) in FP64, left-preconditioned
+// by the low-precision factor M = L L^T (M^{-1} Z is close to I even when
+// kappa(Z) u_factor is not small), with classical Gram-Schmidt applied twice.
+// x is the FP64 iterate (updated in place); returns the best relative residual.
+int gmres_ir(mag_ctx* ctx, int prec, const double* X, int32_t m, double t, const double* b, double* x,
+             bool stored, SolveResult* R, double* rel_out) {
+  const Layout& L = ctx->lay;
+  const int64_t n = L.n, np = L.np;
+  cudaStream_t s = ctx->stream;
+  const int k = std::max(2, std::min(ctx->opt.gmres_max_iters, 200));
+  const size_t need = ((size_t)(k + 1) * np + 2 * np + 2 * (size_t)(k + 2)) * sizeof(double);
+  if (need > ctx->gm_bytes) {
+    if (ctx->gm) {
+      cudaStreamSynchronize(s);
+      cudaFree(ctx->gm);
+      ctx->gm = nullptr;
+      ctx->gm_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc((void**)&ctx->gm, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      ctx->gm = nullptr;
+      return fail(ctx, MAG_ENOMEM, "GMRES basis: %s", cudaGetErrorString(e));
+    }
+    ctx->gm_bytes = need;
+  }
+  double* V = ctx->gm;                         // (k+1) x np
+  double* zeros = V + (size_t)(k + 1) * np;    // np
+  double* wv = zeros + np;                     // np
+  double* dh = wv + np;                        // k+2
+  double* dh2 = dh + (k + 2);                  // k+2
+  double* r = ctx->vd(V_R);
+  double* tmp = ctx->vd(V_E);
+  CU(cudaMemsetAsync(zeros, 0, np * sizeof(double), s));
+  auto precond_matvec = [&](const double* v, double* out) -> int {
+    // out = M^{-1} (Z v):  the residual kernel with b = 0 gives -Z v
+    TRY(reset_norms(ctx));
+    if (stored)
+      CU(launch_residual_stored(ctx->zd(), n, L.N, v, zeros, ctx->vd(V_ROWSUM), tmp, ctx->spart(), np, ctx->st(), s));
+    else
+      CU(launch_residual_mf(X, n, m, t, v, zeros, tmp, ctx->part(), L.chunks, np, ctx->st(), s));
+    TRY(correction(ctx, prec, tmp, out, /*init=*/true, R));
+    CU(launch_scale(out, -1.0, out, n, s));
+    return MAG_OK;
+  };
+  double best = INFINITY;
+  std::vector<double> H((size_t)(k + 1) * k), cs(k), sn(k), g(k + 1), y(k), h(k + 1), h2(k + 1);
+  for (int outer = 0; outer < 8; ++outer) {
+    double rel;
+    TRY(residual(ctx, X, m, t, x, b, r, &rel, stored, R));
+    best = std::min(best, rel);
+    if (rel <= ctx->opt.ir_tol) break;
+    // V_0 = M^{-1} r / beta
+    TRY(correction(ctx, prec, r, wv, /*init=*/true, R));
+    CU(launch_mdot(wv, np, 1, wv, n, dh, s));
+    double beta2 = 0;
+    CU(cudaMemcpyAsync(&beta2, dh, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    const double beta = std::sqrt(beta2);
+    if (!(beta > 0) || !std::isfinite(beta)) break;
+    CU(launch_scale(wv, 1.0 / beta, V, n, s));
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j = 0;
+    for (; j < k; ++j) {
+      TRY(precond_matvec(V + (size_t)j * np, wv));
+      // classical Gram-Schmidt, twice
+      CU(launch_mdot(V, np, j + 1, wv, n, dh, s));
+      CU(launch_maxpy(V, np, j + 1, dh, wv, n, s));
+      CU(launch_mdot(V, np, j + 1, wv, n, dh2, s));
+      CU(launch_maxpy(V, np, j + 1, dh2, wv, n, s));
+      CU(launch_mdot(wv, np, 1, wv, n, dh2 + j + 1, s));
+      CU(cudaMemcpyAsync(h.data(), dh, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CU(cudaMemcpyAsync(h2.data(), dh2, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      R->gmres_iters++;
+      double* col = &H[(size_t)j * (k + 1)];
+      for (int i = 0; i <= j; ++i) col[i] = h[i] + h2[i];
+      col[j + 1] = std::sqrt(std::max(h2[j + 1], 0.0));
+      // apply previous rotations, then a new one to zero col[j+1]
+      for (int i = 0; i < j; ++i) {
+        const double a = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = a;
+      }
+      const double den = std::hypot(col[j], col[j + 1]);
+      cs[j] = den > 0 ? col[j] / den : 1.0;
+      sn[j] = den > 0 ? col[j + 1] / den : 0.0;
+      col[j] = den;
+      const double hj1 = std::sqrt(std::max(h2[j + 1], 0.0));
+      col[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      const bool last = j + 1 == k || std::fabs(g[j + 1]) <= 1e-6 * beta || !(hj1 > 0);
+      if (!last) CU(launch_scale(wv, 1.0 / hj1, V + (size_t)(j + 1) * np, n, s));
+      if (last) {
+        ++j;
+        break;
+      }
+    }
+    // y = H^{-1} g (upper triangular j x j), x += V y
+    for (int i = j - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int c = i + 1; c < j; ++c) acc -= H[(size_t)c * (k + 1) + i] * y[c];
+      y[i] = acc / H[(size_t)i * (k + 1) + i];
+    }
+    for (int i = 0; i < j; ++i) y[i] = -y[i];
+    CU(cudaMemcpyAsync(dh, y.data(), j * sizeof(double), cudaMemcpyHostToDevice, s));
+    CU(launch_maxpy(V, np, j, dh, x, n, s));
+    R->ir_iters++;
+  }
+  double rel;
+  TRY(residual(ctx, X, m, t, x, b, r, &rel, stored, R));
+  best = std::min(best, rel);
+  *rel_out = rel;
   return MAG_OK;
 }
 
@@ -671,6 +852,19 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
         overall = best_rel;
         CU(cudaMemcpyAsync(x, best, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
         CU(cudaStreamSynchronize(s));
+      }
+      if (escalate && prec != MAG_PREC_FP64 && o.allow_fallback && o.gmres_max_iters > 0) {
+        // GMRES-IR with the same factor, from the best iterate so far
+        CU(cudaMemcpyAsync(xw, best, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        double grel = INFINITY;
+        R->fallback = 1;
+        TRY(gmres_ir(ctx, prec, X, m, t, b, xw, stored, R, &grel));
+        if (grel < overall) {
+          overall = grel;
+          CU(cudaMemcpyAsync(x, xw, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+          CU(cudaStreamSynchronize(s));
+        }
+        if (grel <= o.ir_tol) escalate = false;
       }
     }
     if (!escalate || prec == MAG_PREC_FP64 || !o.allow_fallback) break;
@@ -791,6 +985,29 @@ int mag_solve(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t
   return st;
 }
 
+int mag_solve_multi(mag_ctx* ctx, const double* points, int64_t n, int32_t m, const double* ts, int32_t nt,
+                    double* W, double* mags, mag_info* infos) {
+  TRY(check_args(ctx, points, n, m, 1.0));
+  if (!ts || nt < 1 || !W || !mags) return fail(ctx, MAG_EINVAL, "bad multi-t arguments");
+  for (int32_t i = 0; i < nt; ++i)
+    if (!(ts[i] > 0.0) || !std::isfinite(ts[i])) return fail(ctx, MAG_EINVAL, "t[%d] = %g", (int)i, ts[i]);
+  begin_dist_reuse(ctx, n);
+  int first = MAG_OK;
+  std::string first_err;
+  for (int32_t i = 0; i < nt; ++i) {
+    mag_info inf;
+    const int st = mag_solve(ctx, points, n, m, ts[i], W + (size_t)i * n, &mags[i], &inf);
+    if (infos) infos[i] = inf;
+    if (st != MAG_OK && first == MAG_OK) {
+      first = st;
+      first_err = ctx->err;
+    }
+  }
+  end_dist_reuse(ctx);
+  if (first != MAG_OK) ctx->err = first_err;
+  return first;
+}
+
 int mag_solve_rhs(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t,
                   const double* b, double* x, mag_info* info) {
   TRY(check_args(ctx, points, n, m, t));
@@ -849,6 +1066,11 @@ int mag_sweep_tplus(mag_ctx* ctx, const double* points, int64_t n, int32_t m, do
   int probes = 0, iters = 0;
   TRY(ensure_aux(ctx, n));
   double* wp = ctx->aux + (size_t)A_W * ctx->aux_np;
+  begin_dist_reuse(ctx, n);
+  struct EndReuse {
+    mag_ctx* c;
+    ~EndReuse() { end_dist_reuse(c); }
+  } end_reuse{ctx};
   auto probe = [&](double t, bool* feas) -> int {
     int st = mag_solve(ctx, points, n, m, t, wp, &pm, &pi);
     ++probes;
@@ -950,16 +1172,156 @@ int mag_solve_batch(mag_ctx* ctx, const mag_batch_desc* desc, int32_t count, con
   if (!desc || count < 0 || !points || !w_out || !mag_out) return fail(ctx, MAG_EINVAL, "bad batch arguments");
   ctx->err.clear();
   if (info) std::memset(info, 0, sizeof *info);
-  int first = MAG_OK;
-  cudaStream_t s = ctx->stream;
+  if (count == 0) return MAG_OK;
   for (int32_t i = 0; i < count; ++i) {
-    double mg = 0;
-    int st = mag_solve(ctx, points + desc[i].point_offset, desc[i].n, desc[i].m, desc[i].t,
-                       w_out + desc[i].w_offset, &mg, nullptr);
-    CU(cudaMemcpyAsync(mag_out + i, &mg, sizeof(double), cudaMemcpyHostToDevice, s));
-    if (status_out) CU(cudaMemcpyAsync(status_out + i, &st, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    const mag_batch_desc& d = desc[i];
+    if (d.n < 2 || d.m < 1 || !(d.t > 0.0) || !std::isfinite(d.t) || d.point_offset < 0 || d.w_offset < 0)
+      return fail(ctx, MAG_EINVAL, "bad descriptor %d (n=%d m=%d t=%g)", (int)i, (int)d.n, (int)d.m, d.t);
+  }
+  cudaStream_t s = ctx->stream;
+  const long long l0 = g_kernel_launches.load();
+  // group problems by cloud (same points, n, m): distances are shared across t
+  std::vector<BatchCloud> clouds;
+  std::vector<BatchProblem> probs(count);
+  std::vector<int> small, large;
+  int64_t dist_total = 0, max_pairs = 0, nmax = 0;
+  {
+    std::vector<std::pair<std::pair<int64_t, int64_t>, int>> keys;  // ((offset, n*65536+m), cloud)
+    for (int32_t i = 0; i < count; ++i) {
+      const mag_batch_desc& d = desc[i];
+      probs[i].w_offset = d.w_offset;
+      probs[i].n = d.n;
+      probs[i].t = d.t;
+      if (d.n > BATCH_NMAX) {
+        large.push_back(i);
+        probs[i].cloud = -1;
+        continue;
+      }
+      const std::pair<int64_t, int64_t> key(d.point_offset, (int64_t)d.n * 65536 + d.m);
+      int cid = -1;
+      for (auto& k : keys)
+        if (k.first == key) cid = k.second;
+      if (cid < 0) {
+        BatchCloud c;
+        c.point_offset = d.point_offset;
+        c.dist_offset = dist_total;
+        c.n = d.n;
+        c.m = d.m;
+        cid = (int)clouds.size();
+        clouds.push_back(c);
+        keys.push_back({key, cid});
+        const int64_t pairs = (int64_t)d.n * (d.n - 1) / 2;
+        dist_total += pairs;
+        max_pairs = std::max(max_pairs, pairs);
+      }
+      probs[i].cloud = cid;
+      probs[i].dist_offset = clouds[cid].dist_offset;
+      nmax = std::max<int64_t>(nmax, d.n);
+      small.push_back(i);
+    }
+  }
+  std::vector<int> st_host(count, MAG_BATCH_OK);
+  if (!small.empty()) {
+    std::sort(small.begin(), small.end(), [&](int a, int b) { return probs[a].n > probs[b].n; });
+    const int grid = std::min<int>(ctx->sm_count, (int)small.size());
+    // batch workspace: clouds | problems | order | status | queue | D | scratch_f | scratch_d
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+    const size_t o_cl = take(clouds.size() * sizeof(BatchCloud));
+    const size_t o_pr = take((size_t)count * sizeof(BatchProblem));
+    const size_t o_or = take(small.size() * sizeof(int));
+    const size_t o_st = take((size_t)count * sizeof(int));
+    const size_t o_q = take(2 * sizeof(int));
+    const size_t o_cf = take(clouds.size() * sizeof(int));
+    const size_t o_d = take((size_t)dist_total * sizeof(double));
+    const size_t o_sf = take((size_t)grid * (nmax * nmax + nmax) * sizeof(float));
+    const size_t o_sd = take((size_t)grid * (nmax * nmax + 2 * nmax) * sizeof(double));
+    if (off > ctx->bws_bytes) {
+      if (ctx->bws) {
+        cudaStreamSynchronize(s);
+        cudaFree(ctx->bws);
+        ctx->bws = nullptr;
+        ctx->bws_bytes = 0;
+      }
+      cudaError_t e = cudaMalloc(&ctx->bws, off);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->bws = nullptr;
+        return fail(ctx, MAG_ENOMEM, "batch workspace of %.3g GB: %s", off / 1e9, cudaGetErrorString(e));
+      }
+      ctx->bws_bytes = off;
+    }
+    char* base = (char*)ctx->bws;
+    BatchCloud* d_cl = (BatchCloud*)(base + o_cl);
+    BatchProblem* d_pr = (BatchProblem*)(base + o_pr);
+    int* d_or = (int*)(base + o_or);
+    int* d_st = (int*)(base + o_st);
+    int* d_q = (int*)(base + o_q);
+    int* d_cf = (int*)(base + o_cf);
+    double* d_D = (double*)(base + o_d);
+    float* d_sf = (float*)(base + o_sf);
+    double* d_sd = (double*)(base + o_sd);
+    CU(cudaMemcpyAsync(d_cl, clouds.data(), clouds.size() * sizeof(BatchCloud), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(d_pr, probs.data(), (size_t)count * sizeof(BatchProblem), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(d_or, small.data(), small.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    CU(cudaMemsetAsync(d_cf, 0, clouds.size() * sizeof(int), s));
+    CU(launch_batch_dist(points, d_cl, (int)clouds.size(), max_pairs, d_D, d_cf, s));
+    const double tol = ctx->opt.ir_tol;
+    const int max_iter = std::max(ctx->opt.ir_max_iters, 1);
+    if (ctx->batch_block == 0) {
+      // tuner: time both factor block sizes on a sample of mid-sized problems
+      const int ns = std::min<int>((int)small.size(), 2 * grid);
+      const int start = std::max<int>(0, (int)small.size() / 2 - ns / 2);
+      float best = 1e30f;
+      int best_b = 64;
+      for (int b : {32, 64}) {
+        CU(cudaMemsetAsync(d_q, 0, sizeof(int), s));
+        CU(cudaEventRecord(ctx->ev[0], s));
+        CU(launch_batch_solve(b, d_pr, d_or + start, ns, d_D, d_cf, d_sf, d_sd, nmax, w_out, mag_out, d_st, d_q,
+                              tol, max_iter, grid, s));
+        CU(cudaEventRecord(ctx->ev[1], s));
+        CU(cudaEventSynchronize(ctx->ev[1]));
+        const float ms = elapsed(ctx, 0, 1);
+        if (ms < best) best = ms, best_b = b;
+      }
+      ctx->batch_block = best_b;
+    }
+    CU(cudaMemsetAsync(d_q, 0, sizeof(int), s));
+    CU(cudaMemsetAsync(d_st, 0, (size_t)count * sizeof(int), s));
+    CU(launch_batch_solve(ctx->batch_block, d_pr, d_or, (int)small.size(), d_D, d_cf, d_sf, d_sd, nmax, w_out,
+                          mag_out, d_st, d_q, tol, max_iter, grid, s));
+    CU(cudaMemcpyAsync(st_host.data(), d_st, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
+  }
+  // problems too large for one CTA, or that the FP32 batch path could not
+  // finish, go through the single-problem solver (which escalates precision)
+  int first = MAG_OK, fallbacks = 0;
+  std::vector<int32_t> final_st(count, MAG_OK);
+  for (int32_t i = 0; i < count; ++i) {
+    if (probs[i].cloud >= 0 && (st_host[i] == MAG_BATCH_DUPLICATE || st_host[i] == MAG_BATCH_NONFINITE)) {
+      final_st[i] = st_host[i] == MAG_BATCH_DUPLICATE ? MAG_EDUPLICATE : MAG_EINVAL;
+      if (first == MAG_OK) first = final_st[i];
+      continue;
+    }
+    const bool redo = probs[i].cloud < 0 || st_host[i] != MAG_BATCH_OK;
+    if (!redo) continue;
+    ++fallbacks;
+    double mg = 0;
+    const mag_batch_desc& d = desc[i];
+    int st = mag_solve(ctx, points + d.point_offset, d.n, d.m, d.t, w_out + d.w_offset, &mg, nullptr);
+    CU(cudaMemcpyAsync(mag_out + i, &mg, sizeof(double), cudaMemcpyHostToDevice, s));
+    CU(cudaStreamSynchronize(s));
+    final_st[i] = st;
     if (st != MAG_OK && first == MAG_OK) first = st;
+  }
+  if (status_out) {
+    CU(cudaMemcpyAsync(status_out, final_st.data(), (size_t)count * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CU(cudaStreamSynchronize(s));
+  }
+  if (info) {
+    info->fallback = fallbacks;
+    info->kernel_launches = g_kernel_launches.load() - l0;
+    info->probes = ctx->batch_block;
   }
   return first;
 }

@@ -73,6 +73,12 @@ struct DevStatus {
 // min off-diagonal d^2, and non-finite/duplicate flags.
 cudaError_t launch_generate(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
                             double* Zd, double* rowsum, DevStatus* st, cudaStream_t s);
+// The same, also writing the FP64 distances d_jk into Dd (packed tiles like Z).
+cudaError_t launch_generate_dist(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
+                                 double* Zd, double* Dd, double* rowsum, DevStatus* st, cudaStream_t s);
+// Z from stored FP64 distance tiles: Zf (may be null) and Zd (may be null), row sums.
+cudaError_t launch_generate_from_dist(const double* Dd, int64_t n, double t, int64_t N, float* Zf, double* Zd,
+                                     double* rowsum, cudaStream_t s);
 // min_{j != k} d^2 over all pairs (FP64) into st->min_d2_bits.
 cudaError_t launch_min_distance(const double* X, int64_t n, int m, DevStatus* st, cudaStream_t s);
 // off-diagonal row-sum maximum (Gershgorin) from rowsum into st->off_max_bits.
@@ -173,6 +179,38 @@ cudaError_t launch_absmax(const double* v, int64_t n, DevStatus* st, cudaStream_
 // Mag = 1^T w (compensated), min w, max |w| into st.
 cudaError_t launch_reduce_w(const double* w, int64_t n, DevStatus* st, cudaStream_t s);
 cudaError_t launch_fill(double* v, int64_t n, double value, cudaStream_t s);
+// GMRES helpers: out[i] = <V_i, w> (i < k, compensated); w -= sum_i h[i] V_i; x = sc * w.
+cudaError_t launch_mdot(const double* V, int64_t ld, int k, const double* w, int64_t n, double* out,
+                        cudaStream_t s);
+cudaError_t launch_maxpy(const double* V, int64_t ld, int k, const double* h, double* w, int64_t n,
+                         cudaStream_t s);
+cudaError_t launch_scale(const double* w, double sc, double* x, int64_t n, cudaStream_t s);
+
+// K8 batch (k_batch.cu).
+struct BatchCloud {
+  int64_t point_offset;  // doubles into the points array
+  int64_t dist_offset;   // doubles into the packed-distance array
+  int32_t n, m;
+};
+struct BatchProblem {
+  int64_t dist_offset;   // of its cloud
+  int64_t w_offset;      // doubles into w_out
+  int32_t n, cloud;
+  double t;
+};
+enum BatchStatus { MAG_BATCH_OK = 0, MAG_BATCH_NOTPD = 1, MAG_BATCH_NOCONV = 2, MAG_BATCH_DUPLICATE = 3,
+                   MAG_BATCH_NONFINITE = 4 };
+constexpr int BATCH_NMAX = 2048;  // largest n solved inside one CTA
+// Also sets cloud_flags[c] |= 1 (non-finite coordinate) / 2 (coincident points);
+// cloud_flags must be zeroed.
+cudaError_t launch_batch_dist(const double* X, const BatchCloud* clouds, int nclouds, int64_t max_pairs,
+                              double* D, int* cloud_flags, cudaStream_t s);
+// block = 32 or 64 (factor block size); scratch_f: grid * (nmax^2 + nmax) floats,
+// scratch_d: grid * (nmax^2 + 2 nmax) doubles; queue: one zeroed int.
+cudaError_t launch_batch_solve(int block, const BatchProblem* probs, const int* order, int count,
+                               const double* D, const int* cloud_flags, float* scratch_f, double* scratch_d,
+                               int64_t nmax, double* w_out, double* mag_out, int* status, int* queue, double tol,
+                               int max_iter, int grid, cudaStream_t s);
 
 // K7 gradients: dL/dt partial sums and dL/dx.
 cudaError_t launch_grad(const double* X, int64_t n, int m, double t, const double* w,

@@ -326,3 +326,83 @@ def test_residual_entry_point_matches_oracle(ctx):
     r2, _ = ctx.residual(_dev(X), t, torch.from_numpy(w).cuda(), b=torch.from_numpy(b).cuda())
     ro2, _ = oracle.residual_rows(X, t, w, b=b)
     assert np.abs(r2.cpu().numpy() - ro2).max() <= 2e-15 * scale + 4e-16 * np.abs(b).max()
+
+
+def test_batch_mixed_sizes_and_fallbacks(ctx):
+    rng = np.random.default_rng(41)
+    clouds = [rng.standard_normal((n, 6)) for n in (2, 5, 64, 129, 700, 2100)]
+    bad = rng.standard_normal((40, 3))
+    bad[17] = bad[3]  # coincident points: Z singular
+    clouds.append(bad)
+    ts = [0.3, 3.0]
+    ws, mags, sts = ctx.solve_batch([_dev(c) for c in clouds], ts)
+    sts = sts.cpu().numpy()
+    k = 0
+    for i, c in enumerate(clouds):
+        for j, t in enumerate(ts):
+            if i == len(clouds) - 1:
+                assert sts[i, j] == M.MAG_EDUPLICATE
+            else:
+                assert sts[i, j] == M.MAG_OK
+                w_ref, mag_ref, _ = oracle.weighting(c, t)
+                check_solution(c, t, ws[k].cpu().numpy(), mags[i, j].item(), w_ref, mag_ref)
+            k += 1
+
+
+def test_batch_config_shape_sample(ctx):
+    clouds, ts = workloads.batch_clouds(count=12, seed=5)
+    ws, mags, sts = ctx.solve_batch([_dev(c) for c in clouds], list(ts))
+    assert int(sts.abs().sum()) == 0
+    k = 0
+    for i, c in enumerate(clouds):
+        for j, t in enumerate(ts):
+            if j in (0, 7):  # smallest and largest t against the oracle
+                w_ref, mag_ref, _ = oracle.weighting(c, t)
+                check_solution(c, t, ws[k].cpu().numpy(), mags[i, j].item(), w_ref, mag_ref)
+            else:
+                assert oracle.relative_residual(c, t, ws[k].cpu().numpy()) <= 1e-14
+            k += 1
+
+
+@pytest.mark.parametrize("prec,resid", [("fp16x3", "stored"), ("fp16x3", "matrix_free"), ("tf32x3", "stored")])
+def test_gmres_ir_finishes_after_refinement_is_cut_short(ctx, prec, resid):
+    X = _cloud(1500, 8, seed=61)
+    t = 1.0
+    ctx.set_options(M.Options(precision=prec, residual_mode=resid, ir_max_iters=1))
+    try:
+        w, mag, info = ctx.solve(_dev(X), t)
+    finally:
+        ctx.set_options(M.Options())
+    assert info["fallback"] == 1 and info["gmres_iters"] > 0
+    assert info["precision_used"] == M.PRECISIONS[prec]
+    w_ref, mag_ref, _ = oracle.weighting(X, t)
+    check_solution(X, t, w.cpu().numpy(), mag, w_ref, mag_ref)
+
+
+def test_fp64_exponential_over_its_range(ctx):
+    # points i * 2^-4 on a line and t = 32: every t * d_ij = 2 |i - j| is exact,
+    # so the FP64 tiles must equal exp(-2 |i - j|) to within two ulps (the
+    # device uses its own table-driven exp, the reference is the host libm).
+    n = 300
+    X = np.zeros((n, 2))
+    X[:, 0] = np.arange(n) * 0.0625
+    Zg = ctx.similarity_matrix(_dev(X), 32.0, "fp64").cpu().numpy()
+    k = np.abs(np.arange(n)[:, None] - np.arange(n)[None, :])
+    ref = np.exp(-2.0 * k)
+    assert np.all(np.abs(Zg - ref) <= 2 * np.spacing(ref))
+
+
+@pytest.mark.parametrize("resid", ["stored", "matrix_free"])
+def test_solve_multi_reuses_distances_and_matches(ctx, resid):
+    X = _cloud(1500, 8, seed=71)
+    ts = [0.5, 2.0, 30.0]
+    ctx.set_options(M.Options(residual_mode=resid))
+    try:
+        W, mags, infos = ctx.solve_multi(_dev(X), ts)
+        for i, t in enumerate(ts):
+            w_ref, mag_ref, _ = oracle.weighting(X, t)
+            check_solution(X, t, W[i].cpu().numpy(), mags[i], w_ref, mag_ref)
+            w1, m1, _ = ctx.solve(_dev(X), t)
+            assert abs(m1 - mags[i]) <= 1e-12 * abs(mags[i])
+    finally:
+        ctx.set_options(M.Options())
