@@ -49,16 +49,14 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--extras", action="store_true", help="also time sweep/grad/batch/FP64 comparators")
-    p.add_argument("--cpu-sample-n", type=int, default=6144)
+    p.add_argument("--cpu-sample-n", type=int, default=12288)
     return p.parse_args()
 
 
 # ----------------------------------------------------------------- helpers
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_2607_23354_gb300 import replicas
+    return replicas.rank_world()
 
 
 def measured_peaks():
@@ -216,12 +214,8 @@ def run_ours(a):
     torch.cuda.synchronize(dev)
     barrier()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = tt.item()
+    from paper_2607_23354_gb300 import replicas
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1), device=dev)
     flops_step = sum(i["useful_flops"] for _, _, i in infos) / a.steps
     value = world * flops_step * a.steps / (ms / 1e3) / 1e12
 
@@ -245,11 +239,7 @@ def run_ours(a):
             torch.cuda.synchronize(dev)
         el = time.perf_counter() - t0
         barrier()
-        if world > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([el], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            el = tt.item()
+        el = replicas.max_over_ranks(el, device=dev)
         e2e = {"value": world * f2 / el / 1e12, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h + 8 * len(ts)}
 
