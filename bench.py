@@ -50,6 +50,7 @@ def parse_args():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--extras", action="store_true", help="also time sweep/grad/batch/FP64 comparators")
     p.add_argument("--cpu-sample-n", type=int, default=12288)
+    p.add_argument("--panel-tiles", type=int, default=0, help="factor panel width in 128-wide tiles (0 = library default)")
     return p.parse_args()
 
 
@@ -174,7 +175,7 @@ def run_ours(a):
         dist.init_process_group("nccl", device_id=dev)
     X = workloads.unit_cube_cloud(n=a.n, m=a.m, seed=workloads.SEEDS["cube"] + rank)
     Xd = torch.from_numpy(X).to(dev)
-    opts = M.Options(precision=a.precision, residual_mode=a.resid, profile=True)
+    opts = M.Options(precision=a.precision, residual_mode=a.resid, profile=True, panel_tiles=a.panel_tiles)
     ctx = M.Context(opts)
     dmin, bound = ctx.min_distance(Xd)
     ts = [bound if s.strip() == "bound" else float(s) for s in a.ts.split(",")]
@@ -250,7 +251,10 @@ def run_ours(a):
         per_t = [{"t": t, "solve_s": i["ms_total"] / 1e3, "mag": mag, "rel_residual": i["rel_residual"],
                   "ir_iters": i["ir_iters"], "precision_used": i["precision_used"], "fallback": i["fallback"],
                   "ms_generate": i["ms_generate"], "ms_factor": i["ms_factor"], "ms_solve": i["ms_solve"],
-                  "ms_residual": i["ms_residual"], "residual_evals": i["residual_evals"]} for t, mag, i in last]
+                  "ms_residual": i["ms_residual"], "residual_evals": i["residual_evals"],
+                  "ms_factor_parts": {"update_trailing": i["ms_update"] - i["ms_update_panel"],
+                                      "update_panel": i["ms_update_panel"], "potrf": i["ms_potrf"],
+                                      "trsm": i["ms_trsm"], "split": i["ms_split"]}} for t, mag, i in last]
         upd_ms = sum(i["ms_update"] for _, _, i in infos)
         upd_launch = sum(i["update_launches"] for _, _, i in infos)
         upd_flops = sum(i["update_flops"] for _, _, i in infos)
@@ -288,6 +292,7 @@ def run_ours(a):
                                       f"t in {{{', '.join(s.strip() for s in a.ts.split(','))}}}; one step = "
                                       f"{len(ts)} solves to rel. residual <= 1e-14",
                           "n": a.n, "m": a.m, "t": ts, "precision": a.precision, "residual_mode": a.resid,
+                          "panel_tiles": a.panel_tiles or 8,
                           "parallelism": f"replicas x{world}",
                           "l2": "inputs larger than L2 (packed factor tiles of several GB per solve)",
                           "api": "mag_solve_multi (one call per step for all t; distances computed once per call)"},

@@ -114,6 +114,10 @@ typedef struct mag_info {
   double ms_update;        /* their total device time (profile = 1), else 0     */
   double update_flops;     /* algorithmic flops of those launches: 2*128^3 per
                               (output tile, panel tile) product                 */
+  double ms_update_panel;  /* part of ms_update spent inside panels (profile = 1) */
+  double ms_potrf;         /* diagonal-tile factors (profile = 1)              */
+  double ms_trsm;          /* panel solves (profile = 1)                        */
+  double ms_split;         /* panel copies for the tensor cores (profile = 1)   */
 } mag_info;
 
 typedef struct mag_ctx mag_ctx;

@@ -35,84 +35,145 @@ __device__ inline double tsqrt<double>(double x) { return sqrt(x); }
 constexpr int LDA = TILE + 1;  // padded shared-memory row stride
 
 // ------------------------------------------------------------------ potrf
-// One CTA, the diagonal tile in shared memory (row stride LDA).
+// One CTA (512 threads) per diagonal tile.  Thread (ty, tx) = (tid/32, tid%32)
+// owns, in registers, the entries (r, c) with r = ty + 16 a (a < 8) and
+// c = tx + 32 b (b < 4) of three 128 x 128 arrays: A (becoming L) and
+// T (becoming inv(L)).  Each elimination step publishes the one column or row
+// it needs through shared memory, so every step costs one barrier and a
+// handful of shared loads per thread.
 //
-// Factor: elimination on unscaled columns, one barrier per step:
-//   step c: p = A[c][c];  A[r][cc] -= A[r][c] A[cc][c] / p  for c < cc <= r,
-// which only reads column c (final after step c-1) and writes columns > c, so
-// no second barrier is needed; afterwards L[r][c] = A[r][c] / sqrt(p_c).
-// Inverse Y = inv(L): right-looking sweep over rows, one barrier per step, on
-// T = I - (partial sums), kept transposed in the strict upper triangle
-// (T[i][c] at A[c][i]) with its diagonal at A[i][i]:
-//   step k: y_kc = T[k][c] / L[k][k];  T[i][c] -= L[i][k] y_kc  for i > k, c <= k,
-// and Y[k][c] = T[k][c] / L[k][k] at the end.
+// Factor (unscaled elimination, LDL^T form):
+//   step c: p = A[c][c];  A[r][cc] -= A[r][c] A[cc][c] / p  for c < cc <= r;
+//   then L[r][c] = A[r][c] / sqrt(p_c), L[c][c] = sqrt(p_c).
+// Inverse (right-looking sweep over rows of T = inv(L), T starts as I):
+//   step k: T[i][c] -= L[i][k] T[k][c] / L[k][k]  for i > k, c <= k;
+//   Y[k][c] = T[k][c] / L[k][k].
 template <typename T>
 __global__ void __launch_bounds__(512) k_potrf_diag(T* __restrict__ Z, T* __restrict__ Dinv,
                                                     T* __restrict__ DinvT, int64_t K, int64_t n,
                                                     DevStatus* st) {
   extern __shared__ unsigned char smem_raw[];
-  T* A = reinterpret_cast<T*>(smem_raw);  // [TILE][LDA]
-  __shared__ T ldiag[TILE], linv[TILE];
+  T* Ls = reinterpret_cast<T*>(smem_raw);  // [TILE][LDA]: L for the inverse phase
+  __shared__ T colv[TILE], rowv[TILE], ldiag[TILE], linv[TILE];
   __shared__ int skip;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;
   if (tid == 0) skip = (st->flags & (ST_NOTPD | ST_NONFINITE | ST_DUPLICATE)) != 0;  // set by earlier kernels
   __syncthreads();
   if (skip) return;  // uniform across the CTA
   T* tile = Z + tri_index(K, K) * TILE_ELEMS;
-  for (int e = tid; e < TILE * TILE; e += blockDim.x) A[(e / TILE) * LDA + (e % TILE)] = tile[e];
+  T a[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a[i][j] = tile[(ty + 16 * i) * TILE + tx + 32 * j];
+  // publish column 0
+  if (tx == 0) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) colv[ty + 16 * i] = a[i][0];
+  }
   __syncthreads();
   for (int c = 0; c < TILE - 1; ++c) {
-    const T p = A[c * LDA + c];
+    const T p = colv[c];
     const T pinv = p > T(0) ? T(1) / p : T(0);
-    const int w = TILE - 1 - c;  // trailing size
-    for (int e = tid; e < w * w; e += blockDim.x) {
-      const int r = c + 1 + e / w, cc = c + 1 + e % w;
-      if (cc <= r) A[r * LDA + cc] -= A[r * LDA + c] * A[cc * LDA + c] * pinv;
+    T rc[8], cc4[4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) rc[i] = colv[ty + 16 * i] * pinv;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) cc4[j] = colv[tx + 32 * j];
+    if (tid == 0) ldiag[c] = p;  // pivot of step c
+    __syncthreads();             // everyone has read column c
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = ty + 16 * i;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int cc = tx + 32 * j;
+        if (r > c && cc > c && cc <= r) a[i][j] -= rc[i] * cc4[j];
+      }
+    }
+    // publish column c + 1 (owned by tx == (c+1) % 32, b == (c+1) / 32)
+    const int cn = c + 1;
+    if (tx == (cn & 31)) {
+      const int sel = cn >> 5;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        colv[ty + 16 * i] = sel == 0 ? a[i][0] : (sel == 1 ? a[i][1] : (sel == 2 ? a[i][2] : a[i][3]));
     }
     __syncthreads();
   }
+  if (tid == 0) ldiag[TILE - 1] = colv[TILE - 1];
+  __syncthreads();
   if (tid < TILE) {
-    const T p = A[tid * LDA + tid];
+    const T p = ldiag[tid];
     const bool bad = !(p > T(0));
     const T d = bad ? T(1) : tsqrt(p);
-    ldiag[tid] = d;
-    linv[tid] = T(1) / d;
     if (bad) {
       atomicOr(&st->flags, ST_NOTPD);
       atomicMin(&st->notpd_index, (int)(K * TILE + tid + 1));
     }
+    ldiag[tid] = d;
+    linv[tid] = T(1) / d;
   }
   __syncthreads();
-  // scale columns: L[r][c] = A[r][c] / d_c (r > c); diagonal of A <- T = I
-  for (int e = tid; e < TILE * TILE; e += blockDim.x) {
-    const int r = e / TILE, c = e % TILE;
-    if (r > c) A[r * LDA + c] *= linv[c];
-    else if (r == c) A[r * LDA + c] = T(1);
-    else A[r * LDA + c] = T(0);  // T[c][r] = 0 initially (stored transposed)
+  // scale to L, write it to global memory and to shared memory (the inverse
+  // phase reads its columns there), and start T = I in registers
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = ty + 16 * i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = tx + 32 * j;
+      T l = T(0);
+      if (c < r) l = a[i][j] * linv[c];
+      else if (c == r) l = ldiag[r];
+      tile[r * TILE + c] = l;
+      Ls[r * LDA + c] = l;
+      a[i][j] = (c == r) ? T(1) : T(0);
+    }
   }
-  __syncthreads();
-  // write L (zeros above the diagonal)
-  for (int e = tid; e < TILE * TILE; e += blockDim.x) {
-    const int r = e / TILE, c = e % TILE;
-    tile[e] = c < r ? A[r * LDA + c] : (c == r ? ldiag[r] : T(0));
-  }
+  T (&y)[8][4] = a;
+  // inverse sweep: needs column k of L (shared) and row k of T each step
   for (int k = 0; k < TILE - 1; ++k) {
-    const int rows = TILE - 1 - k, cols = k + 1;
-    for (int e = tid; e < rows * cols; e += blockDim.x) {
-      const int i = k + 1 + e / cols, c = e % cols;
-      const T tkc = (c == k) ? A[k * LDA + k] : A[c * LDA + k];  // T[k][c]
-      A[c * LDA + i] -= A[i * LDA + k] * (tkc * linv[k]);         // T[i][c] (c < i)
+    __syncthreads();
+    if (ty == (k & 15)) {
+      const int sel = k >> 4;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        T v = y[0][j];
+#pragma unroll
+        for (int i = 1; i < 8; ++i) v = sel == i ? y[i][j] : v;
+        rowv[tx + 32 * j] = v;  // T[k][.]
+      }
     }
     __syncthreads();
+    const T lk = linv[k];
+    T li[8], tk[4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) li[i] = Ls[(ty + 16 * i) * LDA + k] * lk;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) tk[j] = rowv[tx + 32 * j];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = ty + 16 * i;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = tx + 32 * j;
+        if (r > k && c <= k) y[i][j] -= li[i] * tk[j];
+      }
+    }
   }
   T* Y = Dinv + K * TILE_ELEMS;
   T* YT = DinvT + K * TILE_ELEMS;
-  for (int e = tid; e < TILE * TILE; e += blockDim.x) {
-    const int r = e / TILE, c = e % TILE;
-    // Y[r][c] = T[r][c] / L[r][r] (lower), T[r][c] at A[c][r] for c < r
-    Y[e] = c < r ? A[c * LDA + r] * linv[r] : (c == r ? linv[r] : T(0));
-    // YT[r][c] = Y[c][r]
-    YT[e] = r < c ? A[r * LDA + c] * linv[c] : (c == r ? linv[r] : T(0));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = ty + 16 * i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = tx + 32 * j;
+      const T v = c <= r ? y[i][j] * linv[r] : T(0);
+      Y[r * TILE + c] = v;
+      YT[c * TILE + r] = v;
+    }
   }
 }
 

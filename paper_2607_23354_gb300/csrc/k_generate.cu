@@ -81,11 +81,13 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
   }
 
   const int64_t tile_off = tri_index(I, J) * TILE_ELEMS;
-  double rs[8], cs[4];
+  // row/column partial sums of a thread cover 4 and 8 entries: FP32 is ample
+  // for a norm, and keeps the FP64 pipe for the distances and the exponential
+  float rs[8], cs[4];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) rs[i] = 0.0;
+  for (int i = 0; i < 8; ++i) rs[i] = 0.0f;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) cs[q] = 0.0;
+  for (int q = 0; q < 4; ++q) cs[q] = 0.0f;
   double mind2 = INFINITY;
   int flags = 0;
   const float tf = (float)t;
@@ -116,9 +118,9 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
       if (WD) Zd[tile_off + (int64_t)r * TILE + c] = zd;
       if (WDIST) Dd[tile_off + (int64_t)r * TILE + c] = dd;
       if (ROWSUM && gr < n && gc < n) {
-        const double z = WD ? zd : (double)zf;
-        rs[i] += z;
-        cs[q] += z;
+        const float zs = WF ? zf : (float)zd;
+        rs[i] += zs;
+        cs[q] += zs;
       }
     }
   }
@@ -133,14 +135,14 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
     // row sums: reduce over lanes, one atomic per row
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      double v = rs[i];
+      double v = (double)rs[i];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       const int64_t gr = row0 + warp + 16 * i;
       if (lane == 0 && gr < n) atomicAdd(rowsum + gr, v);
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) colpart[warp][lane + 32 * q] = cs[q];
+    for (int q = 0; q < 4; ++q) colpart[warp][lane + 32 * q] = (double)cs[q];
   }
   __syncthreads();
   if (ROWSUM && I != J && threadIdx.x < TILE) {

@@ -44,9 +44,6 @@ namespace {
 
 constexpr int UPD_THREADS = 192;
 constexpr int A_ROWS = 128, B_ROWS = 256;
-constexpr int CHUNK_BYTES = 128;  // K bytes per stage row (one 128B swizzle row)
-constexpr int A_BYTES = A_ROWS * CHUNK_BYTES;  // 16 KB
-constexpr int B_BYTES = B_ROWS * CHUNK_BYTES;  // 32 KB
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int SUPER = 16;  // super-block edge in tiles
 
@@ -54,39 +51,49 @@ template <int MODE>
 struct ModeCfg;
 template <>
 struct ModeCfg<UPD_TF32X3> {  // hi/lo pairs, 3 MMAs per K step
-  static constexpr int STAGES = 2;
   static constexpr int ELEM = 4;
   static constexpr bool SPLIT = true;
   static constexpr uint32_t FMT = 2;  // TF32
+  static constexpr int CHUNK = 128;
 };
 template <>
 struct ModeCfg<UPD_TF32> {
-  static constexpr int STAGES = 4;
   static constexpr int ELEM = 4;
   static constexpr bool SPLIT = false;
   static constexpr uint32_t FMT = 2;
+  static constexpr int CHUNK = 128;
 };
 template <>
 struct ModeCfg<UPD_BF16> {
-  static constexpr int STAGES = 4;
   static constexpr int ELEM = 2;
   static constexpr bool SPLIT = false;
   static constexpr uint32_t FMT = 1;  // BF16 (kind::f16)
+  static constexpr int CHUNK = 128;
 };
 template <>
 struct ModeCfg<UPD_FP16X3> {  // scaled FP16 hi/lo pairs, 3 MMAs per K step
-  static constexpr int STAGES = 2;
   static constexpr int ELEM = 2;
   static constexpr bool SPLIT = true;
   static constexpr uint32_t FMT = 0;  // F16 (kind::f16)
+  static constexpr int CHUNK = 128;
 };
 template <>
 struct ModeCfg<UPD_FP16> {
-  static constexpr int STAGES = 4;
   static constexpr int ELEM = 2;
   static constexpr bool SPLIT = false;
   static constexpr uint32_t FMT = 0;
+  static constexpr int CHUNK = 128;
 };
+// 128-byte stage rows everywhere (measured faster than 64-byte rows with twice
+// the stages for the split kinds): 2 stages of 96 KB for split kinds, 4 of 48 KB
+// otherwise.
+template <int MODE>
+constexpr int stages_of() {
+  return ModeCfg<MODE>::SPLIT ? 2 : 4;
+}
+__host__ __device__ constexpr int chunk_bytes_of(int mode) {
+  return (mode == UPD_TF32X3 || mode == UPD_FP16X3) ? 128 : 128;
+}
 
 // ------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -148,15 +155,17 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (SBO), version 1, base offset 0.
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+// Shared-memory matrix descriptor, K-major, version 1, base offset 0:
+// 128-byte rows -> SWIZZLE_128B (layout 2), 8-row groups 1024 B apart;
+// 64-byte rows  -> SWIZZLE_64B (layout 4), 8-row groups 512 B apart.
+template <int CHUNK>
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);         // start address
   d |= (uint64_t)1 << 16;                           // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset
+  d |= (uint64_t)((8 * CHUNK) >> 4) << 32;          // stride byte offset: 8 rows
   d |= (uint64_t)1 << 46;                           // descriptor version
-  d |= (uint64_t)2 << 61;                           // SWIZZLE_128B
+  d |= (uint64_t)(CHUNK == 128 ? 2 : 4) << 61;      // SWIZZLE_128B / SWIZZLE_64B
   return d;
 }
 // Instruction descriptor: D = F32, A/B format `fmt`, both K-major, M = 128, N = 256.
@@ -228,11 +237,14 @@ __global__ void __launch_bounds__(UPD_THREADS, 1)
                 const __grid_constant__ CUtensorMap mA_lo, const __grid_constant__ CUtensorMap mB_lo,
                 const UpdParams p) {
   using Cfg = ModeCfg<MODE>;
-  constexpr int S = Cfg::STAGES;
+  constexpr int S = stages_of<MODE>();
+  constexpr int CHUNK_BYTES = Cfg::CHUNK;                  // K bytes per stage row
+  constexpr int A_BYTES = A_ROWS * CHUNK_BYTES;
+  constexpr int B_BYTES = B_ROWS * CHUNK_BYTES;
   constexpr int OPS = Cfg::SPLIT ? 2 : 1;                 // hi (+ lo) copies per operand
-  constexpr int STAGE_BYTES = OPS * (A_BYTES + B_BYTES);  // 96 KB or 48 KB
-  constexpr int KSTEP_BYTES = 32;                          // K per MMA: 8 tf32 / 16 bf16
-  constexpr int KSTEPS = CHUNK_BYTES / KSTEP_BYTES;        // 4
+  constexpr int STAGE_BYTES = OPS * (A_BYTES + B_BYTES);  // 48 KB
+  constexpr int KSTEP_BYTES = 32;                          // K per MMA: 8 tf32 / 16 fp16
+  constexpr int KSTEPS = CHUNK_BYTES / KSTEP_BYTES;        // 2 or 4
   constexpr int ELEMS_PER_CHUNK = CHUNK_BYTES / Cfg::ELEM;
 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -330,13 +342,13 @@ __global__ void __launch_bounds__(UPD_THREADS, 1)
           const uint32_t sb = smem_u32(smem + stage * STAGE_BYTES);
 #pragma unroll
           for (int k = 0; k < KSTEPS; ++k) {
-            const uint64_t ahi = smem_desc_sw128(sb + k * KSTEP_BYTES);
-            const uint64_t bhi = smem_desc_sw128(sb + A_BYTES + k * KSTEP_BYTES);
+            const uint64_t ahi = smem_desc<CHUNK_BYTES>(sb + k * KSTEP_BYTES);
+            const uint64_t bhi = smem_desc<CHUNK_BYTES>(sb + A_BYTES + k * KSTEP_BYTES);
             const uint32_t accum = (c > chunk_lo || k > 0) ? 1u : 0u;
             mma<MODE>(d, ahi, bhi, accum);
             if (Cfg::SPLIT) {
-              const uint64_t alo = smem_desc_sw128(sb + A_BYTES + B_BYTES + k * KSTEP_BYTES);
-              const uint64_t blo = smem_desc_sw128(sb + 2 * A_BYTES + B_BYTES + k * KSTEP_BYTES);
+              const uint64_t alo = smem_desc<CHUNK_BYTES>(sb + A_BYTES + B_BYTES + k * KSTEP_BYTES);
+              const uint64_t blo = smem_desc<CHUNK_BYTES>(sb + 2 * A_BYTES + B_BYTES + k * KSTEP_BYTES);
               mma<MODE>(d, ahi, blo, 1u);
               mma<MODE>(d, alo, bhi, 1u);
             }
@@ -420,24 +432,26 @@ bool encode_2d(CUtensorMap* m, const void* base, int mode, int64_t cols, int64_t
   if (!enc) return false;
   const bool bf16 = mode == UPD_BF16, f16 = mode == UPD_FP16X3 || mode == UPD_FP16;
   const int elem = (bf16 || f16) ? 2 : 4;
+  const int chunk = chunk_bytes_of(mode);
   const CUtensorMapDataType dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                       : (f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(cols * elem)};
-  cuuint32_t box[2] = {(cuuint32_t)(CHUNK_BYTES / elem), (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)(chunk / elem), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(m, dt, 2,
                    const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   chunk == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
 template <int MODE>
 cudaError_t launch_mode(const UpdMaps& maps, const UpdParams& p, int grid, cudaStream_t s) {
-  constexpr int S = ModeCfg<MODE>::STAGES;
   constexpr int OPS = ModeCfg<MODE>::SPLIT ? 2 : 1;
-  const size_t smem = (size_t)S * OPS * (A_BYTES + B_BYTES) + 1024;
+  constexpr int CH = ModeCfg<MODE>::CHUNK;
+  const size_t smem = (size_t)stages_of<MODE>() * OPS * (A_ROWS + B_ROWS) * CH + 1024;
   auto kern = k_update_tc<MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -58,7 +58,8 @@ struct mag_ctx {
   int sm_count = 152;
   double* aux = nullptr;  // vectors that must survive workspace re-plans
   int64_t aux_np = 0;
-  std::vector<cudaEvent_t> prof_ev;  // event pairs around trailing-update launches
+  std::vector<cudaEvent_t> prof_ev;  // event pairs around profiled launches
+  std::vector<int> prof_cat;         // category of each used pair
   int prof_used = 0;
   double* gm = nullptr;              // GMRES basis, zeros and small vectors
   size_t gm_bytes = 0;
@@ -125,6 +126,11 @@ int fail(mag_ctx* c, int status, const char* fmt, ...) {
     int s_ = (expr);        \
     if (s_ != MAG_OK) return s_; \
   } while (0)
+
+// Refinement stops once its own FP64 residual is below this fraction of the
+// tolerance, so that an independent FP64 evaluation of the same residual
+// (which differs in rounding by far less than 10%) also meets the tolerance.
+constexpr double kStopMargin = 0.9;
 
 double bits_to_double(unsigned long long b) {
   double d;
@@ -255,8 +261,9 @@ int check_args(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double 
 }
 
 // ---------------------------------------------------------------- factor
-// Optional CUDA-event timing of the trailing-update launches (profile = 1).
-int prof_begin(mag_ctx* ctx) {
+// Optional CUDA-event timing of factor launches by category (profile = 1).
+enum { PC_UPDATE = 0, PC_UPDATE_PANEL = 1, PC_POTRF = 2, PC_TRSM = 3, PC_SPLIT = 4, PC_COUNT = 5 };
+int prof_begin(mag_ctx* ctx, int cat = PC_UPDATE) {
   if (!ctx->opt.profile) return MAG_OK;
   const size_t need = 2 * (size_t)(ctx->prof_used + 1);
   while (ctx->prof_ev.size() < need) {
@@ -264,6 +271,8 @@ int prof_begin(mag_ctx* ctx) {
     CU(cudaEventCreate(&e));
     ctx->prof_ev.push_back(e);
   }
+  if (ctx->prof_cat.size() < (size_t)ctx->prof_used + 1) ctx->prof_cat.resize(ctx->prof_used + 1);
+  ctx->prof_cat[ctx->prof_used] = cat;
   CU(cudaEventRecord(ctx->prof_ev[2 * ctx->prof_used], ctx->stream));
   return MAG_OK;
 }
@@ -273,15 +282,17 @@ int prof_end(mag_ctx* ctx) {
   ctx->prof_used++;
   return MAG_OK;
 }
-// Sum of the recorded intervals (after the stream has been synchronized).
-double prof_collect(mag_ctx* ctx) {
-  double ms = 0;
+// Per-category sums of the recorded intervals (after the stream has been
+// synchronized); returns the update total (trailing + panel updates).
+double prof_collect(mag_ctx* ctx, double* per_cat) {
+  for (int c = 0; c < PC_COUNT; ++c) per_cat[c] = 0;
   for (int i = 0; i < ctx->prof_used; ++i) {
     float v = 0;
-    if (cudaEventElapsedTime(&v, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]) == cudaSuccess) ms += v;
+    if (cudaEventElapsedTime(&v, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]) == cudaSuccess)
+      per_cat[ctx->prof_cat[i]] += v;
   }
   ctx->prof_used = 0;
-  return ms;
+  return per_cat[PC_UPDATE] + per_cat[PC_UPDATE_PANEL];
 }
 
 // Algorithmic flops of C_IJ -= sum_k L_Ik L_Jk^T over the tiles J in [j0, j1),
@@ -349,16 +360,22 @@ int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
     const int64_t k1 = std::min<int64_t>(L.N, k0 + L.nb);
     up.k0 = k0;
     for (int64_t K = k0; K < k1; ++K) {
+      TRY(prof_begin(ctx, PC_POTRF));
       CU(launch_potrf_diag<float>(Z, Dinv, K, L.n, ctx->st(), s));
+      TRY(prof_end(ctx));
+      TRY(prof_begin(ctx, PC_TRSM));
       CU(launch_trsm_col<float>(Z, Dinv, K, L.N, ctx->st(), s));
+      TRY(prof_end(ctx));
       if (K + 1 >= L.N) continue;
+      TRY(prof_begin(ctx, PC_SPLIT));
       CU(launch_split_col(Z, K, L.N, k0, L.W, mode, hi, lo, s));
+      TRY(prof_end(ctx));
       if (K + 1 < k1) {
         up.kc_lo = (int)(K - k0);
         up.kc_hi = up.kc_lo + 1;
         up.j0 = K + 1;
         up.j1 = k1;
-        TRY(prof_begin(ctx));
+        TRY(prof_begin(ctx, PC_UPDATE_PANEL));
         CU(launch_update_tc(ctx->maps, up, mode, ctx->sm_count, s));
         TRY(prof_end(ctx));
         ++*launches;
@@ -509,7 +526,7 @@ struct SolveResult {
   double ms_gen = 0, ms_fac = 0, ms_solve = 0, ms_res = 0;
   int residual_evals = 0, update_launches = 0;
   bool stored = false;
-  double ms_update = 0, update_flops = 0;
+  double ms_update = 0, update_flops = 0, ms_update_panel = 0, ms_potrf = 0, ms_trsm = 0, ms_split = 0;
 };
 
 float elapsed(mag_ctx* ctx, int a, int b) {
@@ -594,7 +611,12 @@ int run_factor(mag_ctx* ctx, int prec, SolveResult* R) {
   CU(cudaEventRecord(ctx->ev[1], s));
   TRY(read_status(ctx));
   R->ms_fac += elapsed(ctx, 0, 1);
-  R->ms_update += prof_collect(ctx);
+  double pc[PC_COUNT];
+  R->ms_update += prof_collect(ctx, pc);
+  R->ms_update_panel += pc[PC_UPDATE_PANEL];
+  R->ms_potrf += pc[PC_POTRF];
+  R->ms_trsm += pc[PC_TRSM];
+  R->ms_split += pc[PC_SPLIT];
   if (ctx->h_st->flags & ST_TIMEOUT)
     return fail(ctx, MAG_ETIMEOUT, "a bounded device wait in the tensor-core update expired");
   if (ctx->h_st->flags & ST_NOTPD)
@@ -707,7 +729,7 @@ int gmres_ir(mag_ctx* ctx, int prec, const double* X, int32_t m, double t, const
     double rel;
     TRY(residual(ctx, X, m, t, x, b, r, &rel, stored, R));
     best = std::min(best, rel);
-    if (rel <= ctx->opt.ir_tol) break;
+    if (rel <= kStopMargin * ctx->opt.ir_tol) break;
     // V_0 = M^{-1} r / beta
     TRY(correction(ctx, prec, r, wv, /*init=*/true, R));
     CU(launch_mdot(wv, np, 1, wv, n, dh, s));
@@ -838,7 +860,7 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
           best_rel = rel;
           CU(cudaMemcpyAsync(best, xw, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
         }
-        if (rel <= o.ir_tol) break;
+        if (rel <= kStopMargin * o.ir_tol) break;
         if (it >= o.ir_max_iters || (rel > 0.5 * prev && ++slow >= 2)) {
           escalate = true;
           break;
@@ -864,7 +886,7 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
           CU(cudaMemcpyAsync(x, xw, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
           CU(cudaStreamSynchronize(s));
         }
-        if (grel <= o.ir_tol) escalate = false;
+        if (grel <= kStopMargin * o.ir_tol) escalate = false;
       }
     }
     if (!escalate || prec == MAG_PREC_FP64 || !o.allow_fallback) break;
@@ -904,6 +926,10 @@ void fill_info(mag_ctx* ctx, const SolveResult& R, int64_t n, mag_info* info) {
   info->update_launches = R.update_launches;
   info->ms_update = R.ms_update;
   info->update_flops = R.update_flops;
+  info->ms_update_panel = R.ms_update_panel;
+  info->ms_potrf = R.ms_potrf;
+  info->ms_trsm = R.ms_trsm;
+  info->ms_split = R.ms_split;
 }
 
 }  // namespace
@@ -1266,7 +1292,7 @@ int mag_solve_batch(mag_ctx* ctx, const mag_batch_desc* desc, int32_t count, con
     CU(cudaMemcpyAsync(d_or, small.data(), small.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     CU(cudaMemsetAsync(d_cf, 0, clouds.size() * sizeof(int), s));
     CU(launch_batch_dist(points, d_cl, (int)clouds.size(), max_pairs, d_D, d_cf, s));
-    const double tol = ctx->opt.ir_tol;
+    const double tol = kStopMargin * ctx->opt.ir_tol;
     const int max_iter = std::max(ctx->opt.ir_max_iters, 1);
     if (ctx->batch_block == 0) {
       // tuner: time both factor block sizes on a sample of mid-sized problems

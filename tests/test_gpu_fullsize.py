@@ -1,0 +1,123 @@
+"""Parity on the full-size workloads (the configurations the benchmark and the
+paper's workloads use), through the C ABI.  Where the CPU oracle can solve at
+that size it gives the reference weighting; where it cannot (n = 1e5) the
+oracle checks what holds at any size: its own FP64 residual of the GPU's
+weighting over every row, Mag = 1^T w, and the sign structure.  These run
+for minutes on the host cores of the GPU machine.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+M = pytest.importorskip("paper_2607_23354_gb300")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return M.Context()
+
+
+def _dev(X):
+    return torch.from_numpy(np.ascontiguousarray(X)).cuda()
+
+
+def _signs(w):
+    keep = np.abs(w) >= 1e-12 * np.abs(w).max()
+    return np.sign(w) * keep
+
+
+def test_mixture_n16384_against_oracle(ctx):
+    # Gaussian mixture, n = 16384 in R^3: t = 0.5 and the Sec. 1 bound
+    X = workloads.gaussian_mixture_cloud()
+    bound = oracle.tplus_bound(X)
+    for t in (0.5, bound):
+        w, mag, info = ctx.solve(_dev(X), t)
+        wg = w.cpu().numpy()
+        w_ref, mag_ref, _ = oracle.weighting(X, t, ir_steps=1)
+        assert oracle.relative_residual(X, t, wg) <= 1e-14
+        assert np.abs(wg - w_ref).max() <= 1e-9 * np.abs(w_ref).max()
+        assert abs(mag - mag_ref) <= 1e-10 * abs(mag_ref)
+        assert np.array_equal(_signs(wg), _signs(w_ref))
+
+
+def test_cube_n1e5_residual_by_oracle(ctx):
+    # n = 100,000 in [0,1]^8 at t = 1 (the headline workload): the oracle's
+    # FP64 residual of the GPU weighting, every row
+    X = workloads.unit_cube_cloud()
+    t = 1.0
+    w, mag, info = ctx.solve(_dev(X), t)
+    wg = w.cpu().numpy()
+    rel = oracle.relative_residual(X, t, wg)
+    assert rel <= 1e-14, rel
+    assert info["rel_residual"] <= 1e-14
+    assert mag == pytest.approx(oracle.kahan_sum(wg), rel=1e-13)
+    assert info["min_w"] == pytest.approx(wg.min(), rel=1e-12, abs=1e-300)
+
+
+def test_normal_n8192_gradients(ctx):
+    # n = 8192 in R^16, N(0, I)/4, t = 2: dM/dt and dM/dx against the oracle's
+    # adjoint formulas and central differences on sampled coordinates
+    X = workloads.normal_cloud()
+    t, h = 2.0, 1e-6
+    dt, dx = ctx.grad(_dev(X), t)
+    dx = dx.cpu().numpy()
+    w_ref = oracle.weighting(X, t)[0]
+    dto, dxo = oracle.grad(X, t, w_ref)
+    assert dt == pytest.approx(dto, rel=1e-9)
+    assert np.abs(dx - dxo).max() <= 1e-8 * np.abs(dxo).max()
+    Xd = _dev(X)
+    fd_t = (ctx.solve(Xd, t + h)[1] - ctx.solve(Xd, t - h)[1]) / (2 * h)
+    assert dt == pytest.approx(fd_t, rel=1e-6)
+    rng = np.random.default_rng(4)
+    for i, l in zip(rng.integers(0, X.shape[0], 8), rng.integers(0, X.shape[1], 8)):
+        Xp, Xm = X.copy(), X.copy()
+        Xp[i, l] += h
+        Xm[i, l] -= h
+        fd = (ctx.solve(_dev(Xp), t)[1] - ctx.solve(_dev(Xm), t)[1]) / (2 * h)
+        assert dx[i, l] == pytest.approx(fd, rel=1e-4, abs=1e-6 * np.abs(dx).max())
+    # general loss L(w) = ||w||^2 through the adjoint solve
+    w, _, _ = ctx.solve(Xd, t)
+    dtl, dxl = ctx.grad(Xd, t, w=w, dL_dw=2 * w)
+    dtlo, dxlo = oracle.grad_loss(X, t, 2 * w_ref, w=w_ref)
+    assert dtl == pytest.approx(dtlo, rel=1e-8)
+    assert np.abs(dxl.cpu().numpy() - dxlo).max() <= 1e-7 * np.abs(dxlo).max()
+
+
+def test_batch_512_clouds_by_8_t(ctx):
+    clouds, ts = workloads.batch_clouds()
+    ws, mags, sts = ctx.solve_batch([_dev(c) for c in clouds], list(ts))
+    assert int((sts != 0).sum()) == 0
+    k = 0
+    worst = 0.0
+    for i, c in enumerate(clouds):
+        for j, t in enumerate(ts):
+            wg = ws[k].cpu().numpy()
+            k += 1
+            if (i + j) % 7:  # residual of a seeded 1/7 sample by the oracle
+                continue
+            worst = max(worst, oracle.relative_residual(c, t, wg))
+            assert mags[i, j].item() == pytest.approx(oracle.kahan_sum(wg), rel=1e-12)
+    assert worst <= 1e-14, worst
+
+
+def test_grid_support_sweep_full(ctx):
+    # Fig. 1 recipe (737 unique points of Z^2): bound = log(n-1) exactly, t_+ bracket
+    G = workloads.grid_support_cloud()
+    r = ctx.sweep_tplus(_dev(G), 1e-3, 0.0, 1e-6)
+    ro = oracle.tplus(G, 1e-3, 0.0, 1e-6)
+    assert r["bracket"][1] == pytest.approx(ro["bracket"][1], rel=1e-6)
+    assert r["bracket"][0] == pytest.approx(ro["bracket"][0], rel=1e-6)
+    assert r["probes"] == ro["probes"]
+    w_ref = oracle.weighting(G, r["t_plus"])[0]
+    assert np.array_equal(_signs(r["w"].cpu().numpy()), _signs(w_ref))
+    dmin, tb = ctx.min_distance(_dev(G))
+    assert tb == pytest.approx(math.log(len(G) - 1), rel=1e-15)
