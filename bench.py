@@ -51,6 +51,8 @@ def parse_args():
     p.add_argument("--extras", action="store_true", help="also time sweep/grad/batch/FP64 comparators")
     p.add_argument("--cpu-sample-n", type=int, default=12288)
     p.add_argument("--panel-tiles", type=int, default=0, help="factor panel width in 128-wide tiles (0 = library default)")
+    p.add_argument("--lookahead", type=int, default=1, help="1: factor the next panel on a second stream")
+    p.add_argument("--lookahead-sms", type=int, default=0, help="SMs kept for the panel stream (0 = library default)")
     return p.parse_args()
 
 
@@ -175,7 +177,8 @@ def run_ours(a):
         dist.init_process_group("nccl", device_id=dev)
     X = workloads.unit_cube_cloud(n=a.n, m=a.m, seed=workloads.SEEDS["cube"] + rank)
     Xd = torch.from_numpy(X).to(dev)
-    opts = M.Options(precision=a.precision, residual_mode=a.resid, profile=True, panel_tiles=a.panel_tiles)
+    opts = M.Options(precision=a.precision, residual_mode=a.resid, profile=True, panel_tiles=a.panel_tiles,
+                     lookahead=bool(a.lookahead), lookahead_sms=a.lookahead_sms)
     ctx = M.Context(opts)
     dmin, bound = ctx.min_distance(Xd)
     ts = [bound if s.strip() == "bound" else float(s) for s in a.ts.split(",")]

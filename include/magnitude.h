@@ -88,6 +88,13 @@ typedef struct mag_options {
                              mag_sweep_tplus call, keep the FP64 distances in
                              device memory (n^2/2 doubles) and regenerate Z for
                              each t from them when they fit; 0: recompute      */
+  int32_t lookahead;      /* 1 (default): the tensor-core factor runs the next
+                             panel (its update, diagonal factor, panel solve
+                             and copy) on a second stream alongside the
+                             trailing update of the current panel; 0: one
+                             stream, step after step (same arithmetic)        */
+  int32_t lookahead_sms;  /* SMs kept free of the trailing update for the
+                             panel stream (0 = default 16)                    */
 } mag_options;
 
 /* Diagnostics of one call (all fields written when info != NULL). */

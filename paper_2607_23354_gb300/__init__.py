@@ -41,7 +41,8 @@ class mag_options(ctypes.Structure):
                 ("ir_tol", ctypes.c_double), ("ir_max_iters", ctypes.c_int32),
                 ("gmres_max_iters", ctypes.c_int32), ("allow_fallback", ctypes.c_int32),
                 ("panel_tiles", ctypes.c_int32), ("workspace_limit_bytes", ctypes.c_double),
-                ("profile", ctypes.c_int32), ("reuse_distances", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("reuse_distances", ctypes.c_int32),
+                ("lookahead", ctypes.c_int32), ("lookahead_sms", ctypes.c_int32)]
 
 
 class mag_info(ctypes.Structure):
@@ -141,6 +142,8 @@ class Options:
     workspace_limit_bytes: float = 0.0
     profile: bool = False
     reuse_distances: bool = True
+    lookahead: bool = True
+    lookahead_sms: int = 0
 
     def to_c(self) -> mag_options:
         o = mag_options()
@@ -156,6 +159,8 @@ class Options:
         o.workspace_limit_bytes = self.workspace_limit_bytes
         o.profile = int(self.profile)
         o.reuse_distances = int(self.reuse_distances)
+        o.lookahead = int(self.lookahead)
+        o.lookahead_sms = int(self.lookahead_sms)
         return o
 
 

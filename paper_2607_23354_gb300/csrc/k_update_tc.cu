@@ -28,8 +28,12 @@
 //                task overlaps the MMAs of the next;
 //   warps 2..5 : epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
 //                lanes 32*(w%4)..+31), C -= acc on the packed tiles.
-// Tasks are ordered in 16x16-tile super-blocks of the trapezoid so that the
-// CTAs running concurrently share panel rows through L2.
+// Tasks come from a host-built table in 16x16-tile super-block order (so the
+// CTAs running concurrently share panel rows through L2); the producer thread
+// claims the next table entry with an atomic counter of the launch and hands
+// it to the MMA and epilogue roles through a small mbarrier ring.  CTAs that
+// start late (their SMs busy with other streams' kernels) find the queue
+// drained and exit, so a launch never waits for SMs it cannot get.
 //
 // Every mbarrier wait is bounded (wall-clock deadline via %globaltimer); on
 // expiry the CTA raises ST_TIMEOUT, stops issuing work, drains its own TMA
@@ -46,6 +50,7 @@ constexpr int UPD_THREADS = 192;
 constexpr int A_ROWS = 128, B_ROWS = 256;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int SUPER = 16;  // super-block edge in tiles
+constexpr int TQ = 4;      // depth of the task hand-off ring
 
 template <int MODE>
 struct ModeCfg;
@@ -212,23 +217,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Task q -> output block (I, J) of the trapezoid; false if q falls outside it.
-__device__ __forceinline__ bool decode_task(int64_t q, const UpdParams& p, int64_t* I, int64_t* J) {
-  const int64_t sb = q / (SUPER * SUPER / 2);
-  const int loc = (int)(q % (SUPER * SUPER / 2));
-  const int64_t SC = p.super_cols;
-  const int64_t tri = SC * (SC + 1) / 2;
-  int64_t sr, sc;
-  if (sb < tri) {
-    tri_coords(sb, &sr, &sc);
-  } else {
-    const int64_t r = sb - tri;
-    sr = SC + r / SC;
-    sc = r % SC;
-  }
-  *I = p.j0 + sr * SUPER + (loc / (SUPER / 2));
-  *J = p.j0 + sc * SUPER + 2 * (loc % (SUPER / 2));
-  return *I < p.N && *J < p.j1 && *J <= *I;
+// Task q -> output block (I, J) from the task table.
+__device__ __forceinline__ void decode_task(int64_t q, const UpdParams& p, int64_t* I, int64_t* J) {
+  const uint32_t v = __ldg(p.tasks + q);
+  *I = (int64_t)(v >> 16);
+  *J = (int64_t)(v & 0xFFFFu);
 }
 
 template <int MODE>
@@ -250,6 +243,8 @@ __global__ void __launch_bounds__(UPD_THREADS, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], tfull_bar[2], tempty_bar[2];
+  __shared__ __align__(8) uint64_t tq_full[TQ], tq_empty[TQ];
+  __shared__ int64_t tq_val[TQ];  // task index, or -1 once the queue is exhausted
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_flag;
 
@@ -262,6 +257,10 @@ __global__ void __launch_bounds__(UPD_THREADS, 1)
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull_bar[a], 1);
       mbar_init(&tempty_bar[a], 4);
+    }
+    for (int i = 0; i < TQ; ++i) {
+      mbar_init(&tq_full[i], 1);
+      mbar_init(&tq_empty[i], 5);  // the MMA thread + one thread per epilogue warp
     }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -278,7 +277,6 @@ __global__ void __launch_bounds__(UPD_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem_base = tmem_base_sh;
   const uint64_t deadline = globaltimer() + p.timeout_ns;
-  const int64_t ntasks = p.n_super * (SUPER * SUPER / 2);
   const int chunk_lo = p.kc_lo * (TILE * Cfg::ELEM / CHUNK_BYTES);
   const int chunk_hi = p.kc_hi * (TILE * Cfg::ELEM / CHUNK_BYTES);
 
@@ -290,9 +288,18 @@ __global__ void __launch_bounds__(UPD_THREADS, 1)
       bool issued[S];
       for (int s = 0; s < S; ++s) issued[s] = false, issued_parity[s] = 0;
       bool ok = true;
-      for (int64_t q = blockIdx.x; q < ntasks && ok; q += gridDim.x) {
+      uint32_t ts = 0, tph = 0;
+      while (ok) {
+        // claim the next task and hand it to the MMA and epilogue roles
+        if (!mbar_wait(&tq_empty[ts], tph ^ 1u, &abort_flag, deadline)) break;
+        const int64_t q = (int64_t)atomicAdd(p.counter, 1u);
+        const bool end = q >= p.ntasks;
+        tq_val[ts] = end ? -1 : q;
+        mbar_arrive(&tq_full[ts]);
+        if (++ts == TQ) ts = 0, tph ^= 1u;
+        if (end) break;
         int64_t I, J;
-        if (!decode_task(q, p, &I, &J)) continue;
+        decode_task(q, p, &I, &J);
         const int ya = (int)((I - p.k0) * TILE), yb = (int)((J - p.k0) * TILE);
         for (int c = chunk_lo; c < chunk_hi; ++c) {
           if (!mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag, deadline)) {
@@ -327,9 +334,13 @@ __global__ void __launch_bounds__(UPD_THREADS, 1)
     if (lane == 0) {
       uint32_t stage = 0, phase = 0, acc = 0, acc_phase = 0;
       bool ok = true;
-      for (int64_t q = blockIdx.x; q < ntasks && ok; q += gridDim.x) {
-        int64_t I, J;
-        if (!decode_task(q, p, &I, &J)) continue;
+      uint32_t ts = 0, tph = 0;
+      while (ok) {
+        if (!mbar_wait(&tq_full[ts], tph, &abort_flag, deadline)) break;
+        const int64_t q = tq_val[ts];
+        mbar_arrive(&tq_empty[ts]);
+        if (++ts == TQ) ts = 0, tph ^= 1u;
+        if (q < 0) break;
         if (!mbar_wait(&tempty_bar[acc], acc_phase ^ 1u, &abort_flag, deadline)) break;
         tc_fence_after();
         const uint32_t d = tmem_base + acc * (uint32_t)B_ROWS;
@@ -365,10 +376,16 @@ __global__ void __launch_bounds__(UPD_THREADS, 1)
     // --------------------------------------------------------------- epilogue
     const int quad = warp & 3;  // TMEM lane quadrant this warp may access
     const int row = quad * 32 + lane;
-    uint32_t acc = 0, acc_phase = 0;
-    for (int64_t q = blockIdx.x; q < ntasks; q += gridDim.x) {
+    uint32_t acc = 0, acc_phase = 0, ts = 0, tph = 0;
+    for (;;) {
+      if (!mbar_wait(&tq_full[ts], tph, &abort_flag, deadline)) break;
+      const int64_t q = tq_val[ts];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tq_empty[ts]);
+      if (++ts == TQ) ts = 0, tph ^= 1u;
+      if (q < 0) break;
       int64_t I, J;
-      if (!decode_task(q, p, &I, &J)) continue;
+      decode_task(q, p, &I, &J);
       if (!mbar_wait(&tfull_bar[acc], acc_phase, &abort_flag, deadline)) break;
       tc_fence_after();
       const bool second = (J + 1 < p.j1) && (J + 1 <= I);
@@ -475,20 +492,33 @@ bool make_update_maps(UpdMaps* maps, const void* hi, const void* lo, int mode, i
   return true;
 }
 
-int64_t update_num_super(int64_t N, int64_t j0, int64_t j1) {
-  const int64_t SR = (N - j0 + SUPER - 1) / SUPER;
-  const int64_t SC = (j1 - j0 + SUPER - 1) / SUPER;
-  if (SR <= 0 || SC <= 0) return 0;
-  if (SR <= SC) return SR * (SR + 1) / 2;
-  return SC * (SC + 1) / 2 + (SR - SC) * SC;
+int64_t update_tasks(int64_t N, int64_t j0, int64_t j1, std::vector<uint32_t>* out) {
+  if (j0 >= j1 || j0 >= N || N >= 65536) return 0;
+  const int64_t SR = (N - j0 + SUPER - 1) / SUPER;   // super-block rows
+  const int64_t SC = (j1 - j0 + SUPER - 1) / SUPER;  // super-block columns
+  const int64_t n_super = SR <= SC ? SR * (SR + 1) / 2 : SC * (SC + 1) / 2 + (SR - SC) * SC;
+  const size_t before = out->size();
+  for (int64_t sb = 0; sb < n_super; ++sb) {
+    int64_t sr, sc;
+    const int64_t tri = SC * (SC + 1) / 2;
+    if (sb < tri) {
+      tri_coords(sb, &sr, &sc);
+    } else {
+      sr = SC + (sb - tri) / SC;
+      sc = (sb - tri) % SC;
+    }
+    for (int r = 0; r < SUPER; ++r)
+      for (int c = 0; c < SUPER / 2; ++c) {
+        const int64_t I = j0 + sr * SUPER + r, J = j0 + sc * SUPER + 2 * c;
+        if (I < N && J < j1 && J <= I) out->push_back((uint32_t)(I << 16) | (uint32_t)J);
+      }
+  }
+  return (int64_t)(out->size() - before);
 }
 
 cudaError_t launch_update_tc(const UpdMaps& maps, UpdParams p, int mode, int grid, cudaStream_t s) {
-  p.super_cols = (p.j1 - p.j0 + SUPER - 1) / SUPER;
-  p.n_super = update_num_super(p.N, p.j0, p.j1);
-  if (p.n_super <= 0 || p.kc_hi <= p.kc_lo) return cudaSuccess;
-  const int64_t ntasks = p.n_super * (SUPER * SUPER / 2);
-  if ((int64_t)grid > ntasks) grid = (int)ntasks;
+  if (p.ntasks <= 0 || p.kc_hi <= p.kc_lo) return cudaSuccess;
+  if ((int64_t)grid > p.ntasks) grid = (int)p.ntasks;
   switch (mode) {
     case UPD_TF32X3: return launch_mode<UPD_TF32X3>(maps, p, grid, s);
     case UPD_TF32: return launch_mode<UPD_TF32>(maps, p, grid, s);

@@ -15,6 +15,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -32,10 +33,11 @@ struct Layout {
   int chunks = 1;
   bool f32 = false, f64 = false;
   size_t off_zf = 0, off_zd = 0, off_dinvf = 0, off_dinvd = 0, off_vec = 0, off_part = 0,
-         off_status = 0, off_panel = 0, off_flags = 0, off_spart = 0, off_dist = 0, total = 0;
+         off_status = 0, off_panel = 0, off_flags = 0, off_spart = 0, off_dist = 0, off_ctr = 0, total = 0;
   bool dist = false;   // FP64 distance tiles present
   int nb = 8;          // panel width in tiles
   int64_t W = 0;       // panel width in columns (nb * TILE)
+  int64_t nctr = 0;    // task counters of the tensor-core update launches of one factor
 };
 
 constexpr int NVEC_D = 6;   // FP64 vectors of np entries
@@ -72,10 +74,17 @@ struct mag_ctx {
   void* bws = nullptr;               // batch workspace
   size_t bws_bytes = 0;
   int batch_block = 0;               // tuned factor block of the batch kernel (0 = not tuned)
-  UpdMaps maps;                      // TMA descriptors of the panel buffer
-  const void* maps_base = nullptr;
-  int maps_mode = -1;
-  int64_t maps_W = 0, maps_np = 0;
+  UpdMaps maps[2];                   // TMA descriptors of the two panel buffers
+  const void* maps_base[2] = {nullptr, nullptr};
+  int maps_mode[2] = {-1, -1};
+  int64_t maps_W[2] = {0, 0}, maps_np[2] = {0, 0};
+  uint32_t* tasks_d = nullptr;       // task tables of the update launches of one factor
+  size_t tasks_cap = 0;
+  int64_t tasks_N = -1;
+  int tasks_nb = -1, tasks_la = -1;
+  std::map<std::pair<int64_t, int64_t>, std::pair<int64_t, int64_t>> task_rng;  // (j0, j1) -> (offset, count)
+  cudaStream_t side = nullptr;       // panel stream of the look-ahead factor
+  cudaEvent_t ev_la[3] = {nullptr, nullptr, nullptr};  // start, panel done, trailing done
 
   // typed views of the workspace
   float* zf() { return (float*)((char*)ws + lay.off_zf); }
@@ -89,8 +98,9 @@ struct mag_ctx {
   double* part() { return (double*)((char*)ws + lay.off_part); }
   double* spart() { return (double*)((char*)ws + lay.off_spart); }
   double* dist() { return (double*)((char*)ws + lay.off_dist); }
-  float* panel_hi() { return (float*)((char*)ws + lay.off_panel); }
-  float* panel_lo() { return panel_hi() + (size_t)lay.np * lay.W; }
+  float* panel_hi(int b) { return (float*)((char*)ws + lay.off_panel) + (size_t)b * 2 * lay.np * lay.W; }
+  float* panel_lo(int b) { return panel_hi(b) + (size_t)lay.np * lay.W; }
+  unsigned* counters() { return (unsigned*)((char*)ws + lay.off_ctr); }
   DevStatus* st() { return (DevStatus*)((char*)ws + lay.off_status); }
   unsigned* flags() { return (unsigned*)((char*)ws + lay.off_flags); }
 };
@@ -155,6 +165,9 @@ Layout plan(const mag_ctx* ctx, int64_t n, bool f32, bool f64, bool dist = false
   off = align_up(off + sizeof(DevStatus));
   L.off_flags = off;
   off = align_up(off + (size_t)L.N * sizeof(unsigned));
+  L.off_ctr = off;  // at most N - 1 in-panel + 2 per panel update launches
+  L.nctr = 2 * L.N + 16;
+  off = align_up(off + (size_t)L.nctr * sizeof(unsigned));
   L.off_vec = off;
   off = align_up(off + (size_t)L.np * (NVEC_D * sizeof(double) + NVEC_F * sizeof(float)));
   L.off_part = off;
@@ -165,7 +178,9 @@ Layout plan(const mag_ctx* ctx, int64_t n, bool f32, bool f64, bool dist = false
   L.nb = ctx->opt.panel_tiles > 0 ? ctx->opt.panel_tiles : 8;
   L.W = (int64_t)L.nb * TILE;
   L.off_panel = off;
-  if (f32) off = align_up(off + (size_t)L.np * L.W * 2 * sizeof(float));  // hi + lo copies
+  // two panel buffers (hi + lo copies each): the next panel is written while
+  // the trailing update still reads the current one
+  if (f32) off = align_up(off + (size_t)L.np * L.W * 4 * sizeof(float));
   L.off_dinvf = off;
   if (f32) off = align_up(off + (size_t)2 * L.N * TILE_ELEMS * sizeof(float));
   L.off_dinvd = off;
@@ -263,7 +278,7 @@ int check_args(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double 
 // ---------------------------------------------------------------- factor
 // Optional CUDA-event timing of factor launches by category (profile = 1).
 enum { PC_UPDATE = 0, PC_UPDATE_PANEL = 1, PC_POTRF = 2, PC_TRSM = 3, PC_SPLIT = 4, PC_COUNT = 5 };
-int prof_begin(mag_ctx* ctx, int cat = PC_UPDATE) {
+int prof_begin(mag_ctx* ctx, int cat = PC_UPDATE, cudaStream_t st = nullptr) {
   if (!ctx->opt.profile) return MAG_OK;
   const size_t need = 2 * (size_t)(ctx->prof_used + 1);
   while (ctx->prof_ev.size() < need) {
@@ -273,12 +288,12 @@ int prof_begin(mag_ctx* ctx, int cat = PC_UPDATE) {
   }
   if (ctx->prof_cat.size() < (size_t)ctx->prof_used + 1) ctx->prof_cat.resize(ctx->prof_used + 1);
   ctx->prof_cat[ctx->prof_used] = cat;
-  CU(cudaEventRecord(ctx->prof_ev[2 * ctx->prof_used], ctx->stream));
+  CU(cudaEventRecord(ctx->prof_ev[2 * ctx->prof_used], st ? st : ctx->stream));
   return MAG_OK;
 }
-int prof_end(mag_ctx* ctx) {
+int prof_end(mag_ctx* ctx, cudaStream_t st = nullptr) {
   if (!ctx->opt.profile) return MAG_OK;
-  CU(cudaEventRecord(ctx->prof_ev[2 * ctx->prof_used + 1], ctx->stream));
+  CU(cudaEventRecord(ctx->prof_ev[2 * ctx->prof_used + 1], st ? st : ctx->stream));
   ctx->prof_used++;
   return MAG_OK;
 }
@@ -335,65 +350,182 @@ int upd_mode(int prec) {
 // the column's split copy into the panel buffer, a rank-128 tensor-core update
 // of the remaining panel columns; then one tensor-core update of the whole
 // trailing matrix with K = (k1 - k0) * 128.
+// Task tables of every tensor-core update launch of one factor with the
+// current layout (built on the host once per (N, panel width, schedule)).
+int ensure_tasks(mag_ctx* ctx, bool la) {
+  const Layout& L = ctx->lay;
+  if (ctx->tasks_N == L.N && ctx->tasks_nb == L.nb && ctx->tasks_la == (int)la) return MAG_OK;
+  if (L.N >= 65536) return fail(ctx, MAG_EINVAL, "n = %lld too large for the tensor-core factor", (long long)L.n);
+  std::vector<uint32_t> t;
+  ctx->task_rng.clear();
+  auto add = [&](int64_t j0, int64_t j1) {
+    const auto key = std::make_pair(j0, j1);
+    if (j0 >= j1 || ctx->task_rng.count(key)) return;
+    const int64_t off = (int64_t)t.size();
+    const int64_t cnt = update_tasks(L.N, j0, j1, &t);
+    ctx->task_rng[key] = std::make_pair(off, cnt);
+  };
+  for (int64_t k0 = 0; k0 < L.N; k0 += L.nb) {
+    const int64_t k1 = std::min<int64_t>(L.N, k0 + L.nb), k2 = std::min<int64_t>(L.N, k1 + L.nb);
+    for (int64_t K = k0; K + 1 < k1; ++K) add(K + 1, k1);
+    if (la) {
+      add(k1, k2);
+      add(k2, L.N);
+    } else {
+      add(k1, L.N);
+    }
+  }
+  CU(cudaStreamSynchronize(ctx->stream));  // a previous factor may still read the old table
+  if (t.size() > ctx->tasks_cap) {
+    if (ctx->tasks_d) cudaFree(ctx->tasks_d);
+    ctx->tasks_d = nullptr;
+    ctx->tasks_cap = 0;
+    cudaError_t e = cudaMalloc((void**)&ctx->tasks_d, std::max<size_t>(1, t.size()) * sizeof(uint32_t));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      ctx->tasks_d = nullptr;
+      return fail(ctx, MAG_ENOMEM, "cudaMalloc(task table) failed: %s", cudaGetErrorString(e));
+    }
+    ctx->tasks_cap = std::max<size_t>(1, t.size());
+  }
+  if (!t.empty()) CU(cudaMemcpy(ctx->tasks_d, t.data(), t.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  ctx->tasks_N = L.N;
+  ctx->tasks_nb = L.nb;
+  ctx->tasks_la = (int)la;
+  return MAG_OK;
+}
+
+int ensure_maps(mag_ctx* ctx, int mode, int b) {
+  const Layout& L = ctx->lay;
+  void* hi = ctx->panel_hi(b);
+  if (ctx->maps_base[b] == hi && ctx->maps_mode[b] == mode && ctx->maps_W[b] == L.W && ctx->maps_np[b] == L.np)
+    return MAG_OK;
+  if (!make_update_maps(&ctx->maps[b], hi, ctx->panel_lo(b), mode, L.W, L.np))
+    return fail(ctx, MAG_ECUDA, "cuTensorMapEncodeTiled failed for the panel buffer");
+  ctx->maps_base[b] = hi;
+  ctx->maps_mode[b] = mode;
+  ctx->maps_W[b] = L.W;
+  ctx->maps_np[b] = L.np;
+  return MAG_OK;
+}
+
+// State of one tensor-core factorization: launch parameters and counters.
+struct TcFactor {
+  mag_ctx* ctx;
+  int mode;
+  int* launches;
+  double* flops;
+  int64_t next_ctr;
+};
+
+// C_IJ -= sum_{k in [kc_lo, kc_hi)} P_Ik P_Jk^T for J in [j0, j1) with the
+// panel of tile column k0 in buffer b, on stream st with at most `grid` CTAs.
+int tc_update(TcFactor& F, int b, int64_t k0, int kc_lo, int kc_hi, int64_t j0, int64_t j1, int grid,
+              cudaStream_t st, int cat) {
+  mag_ctx* ctx = F.ctx;
+  const Layout& L = ctx->lay;
+  auto it = ctx->task_rng.find(std::make_pair(j0, j1));
+  if (it == ctx->task_rng.end() || it->second.second == 0) return MAG_OK;
+  if (F.next_ctr >= L.nctr) return fail(ctx, MAG_ECUDA, "update launch counters exhausted");
+  UpdParams up;
+  std::memset(&up, 0, sizeof up);
+  up.Z = ctx->zf();
+  up.N = L.N;
+  up.k0 = k0;
+  up.kc_lo = kc_lo;
+  up.kc_hi = kc_hi;
+  up.j1 = j1;
+  up.tasks = ctx->tasks_d + it->second.first;
+  up.ntasks = it->second.second;
+  up.counter = ctx->counters() + F.next_ctr++;
+  up.st = ctx->st();
+  up.timeout_ns = 20000000000ull;
+  TRY(prof_begin(ctx, cat, st));
+  CU(launch_update_tc(ctx->maps[b], up, F.mode, grid, st));
+  TRY(prof_end(ctx, st));
+  ++*F.launches;
+  *F.flops += update_flops(L.N, k0 + kc_lo, k0 + kc_hi, j0, j1);
+  return MAG_OK;
+}
+
+// Diagonal factor + inverse, panel solve, panel copy into buffer b and the
+// in-panel updates of tile columns [k0, k1), on stream st.
+int tc_panel(TcFactor& F, int64_t k0, int b, cudaStream_t st) {
+  mag_ctx* ctx = F.ctx;
+  const Layout& L = ctx->lay;
+  float* Z = ctx->zf();
+  float* Dinv = ctx->dinvf();
+  const int64_t k1 = std::min<int64_t>(L.N, k0 + L.nb);
+  for (int64_t K = k0; K < k1; ++K) {
+    TRY(prof_begin(ctx, PC_POTRF, st));
+    CU(launch_potrf_diag<float>(Z, Dinv, K, L.n, ctx->st(), st));
+    TRY(prof_end(ctx, st));
+    TRY(prof_begin(ctx, PC_TRSM, st));
+    CU(launch_trsm_col<float>(Z, Dinv, K, L.N, ctx->st(), st));
+    TRY(prof_end(ctx, st));
+    if (K + 1 >= L.N) continue;
+    TRY(prof_begin(ctx, PC_SPLIT, st));
+    CU(launch_split_col(Z, K, L.N, k0, L.W, F.mode, ctx->panel_hi(b), ctx->panel_lo(b), st));
+    TRY(prof_end(ctx, st));
+    if (K + 1 < k1)
+      TRY(tc_update(F, b, k0, (int)(K - k0), (int)(K - k0) + 1, K + 1, k1, ctx->sm_count, st, PC_UPDATE_PANEL));
+  }
+  return MAG_OK;
+}
+
+// Two-level right-looking Cholesky with the tensor-core updates.  Without
+// look-ahead every step runs on the solver's stream.  With look-ahead the
+// panel stream updates the next panel's columns with the current panel and
+// factors it (into the other panel buffer) while the solver's stream applies
+// the current panel to the remaining columns; CTAs of the trailing update are
+// capped so that some SMs stay free for the panel stream.
 int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
   const Layout& L = ctx->lay;
   cudaStream_t s = ctx->stream;
-  float* Z = ctx->zf();
-  float* Dinv = ctx->dinvf();
-  void* hi = ctx->panel_hi();
-  void* lo = ctx->panel_lo();
-  if (ctx->maps_base != hi || ctx->maps_mode != mode || ctx->maps_W != L.W || ctx->maps_np != L.np) {
-    if (!make_update_maps(&ctx->maps, hi, lo, mode, L.W, L.np))
-      return fail(ctx, MAG_ECUDA, "cuTensorMapEncodeTiled failed for the panel buffer");
-    ctx->maps_base = hi;
-    ctx->maps_mode = mode;
-    ctx->maps_W = L.W;
-    ctx->maps_np = L.np;
+  const int64_t npanels = (L.N + L.nb - 1) / L.nb;
+  const bool la = ctx->opt.lookahead != 0 && npanels > 2;
+  TRY(ensure_tasks(ctx, la));
+  TRY(ensure_maps(ctx, mode, 0));
+  TRY(ensure_maps(ctx, mode, 1));
+  CU(cudaMemsetAsync(ctx->counters(), 0, (size_t)L.nctr * sizeof(unsigned), s));
+  TcFactor F{ctx, mode, launches, flops, 0};
+  if (!la) {
+    for (int64_t k0 = 0; k0 < L.N; k0 += L.nb) {
+      const int64_t k1 = std::min<int64_t>(L.N, k0 + L.nb);
+      TRY(tc_panel(F, k0, 0, s));
+      if (k1 < L.N) TRY(tc_update(F, 0, k0, 0, (int)(k1 - k0), k1, L.N, ctx->sm_count, s, PC_UPDATE));
+    }
+    return MAG_OK;
   }
-  UpdParams up;
-  std::memset(&up, 0, sizeof up);
-  up.Z = Z;
-  up.N = L.N;
-  up.st = ctx->st();
-  up.timeout_ns = 20000000000ull;
-  for (int64_t k0 = 0; k0 < L.N; k0 += L.nb) {
+  if (!ctx->side) {
+    CU(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+    for (int i = 0; i < 3; ++i) CU(cudaEventCreateWithFlags(&ctx->ev_la[i], cudaEventDisableTiming));
+  }
+  cudaStream_t side = ctx->side;
+  cudaEvent_t ev_start = ctx->ev_la[0], ev_panel = ctx->ev_la[1], ev_trail = ctx->ev_la[2];
+  const int reserve = ctx->opt.lookahead_sms > 0 ? ctx->opt.lookahead_sms : 16;
+  const int trail_grid = std::max(1, ctx->sm_count - reserve);
+  CU(cudaEventRecord(ev_start, s));
+  CU(cudaStreamWaitEvent(side, ev_start, 0));
+  TRY(tc_panel(F, 0, 0, side));
+  CU(cudaEventRecord(ev_panel, side));
+  int64_t p = 0;
+  for (int64_t k0 = 0;; k0 += L.nb, ++p) {
     const int64_t k1 = std::min<int64_t>(L.N, k0 + L.nb);
-    up.k0 = k0;
-    for (int64_t K = k0; K < k1; ++K) {
-      TRY(prof_begin(ctx, PC_POTRF));
-      CU(launch_potrf_diag<float>(Z, Dinv, K, L.n, ctx->st(), s));
-      TRY(prof_end(ctx));
-      TRY(prof_begin(ctx, PC_TRSM));
-      CU(launch_trsm_col<float>(Z, Dinv, K, L.N, ctx->st(), s));
-      TRY(prof_end(ctx));
-      if (K + 1 >= L.N) continue;
-      TRY(prof_begin(ctx, PC_SPLIT));
-      CU(launch_split_col(Z, K, L.N, k0, L.W, mode, hi, lo, s));
-      TRY(prof_end(ctx));
-      if (K + 1 < k1) {
-        up.kc_lo = (int)(K - k0);
-        up.kc_hi = up.kc_lo + 1;
-        up.j0 = K + 1;
-        up.j1 = k1;
-        TRY(prof_begin(ctx, PC_UPDATE_PANEL));
-        CU(launch_update_tc(ctx->maps, up, mode, ctx->sm_count, s));
-        TRY(prof_end(ctx));
-        ++*launches;
-        *flops += update_flops(L.N, K, K + 1, K + 1, k1);
-      }
-    }
-    if (k1 < L.N) {
-      up.kc_lo = 0;
-      up.kc_hi = (int)(k1 - k0);
-      up.j0 = k1;
-      up.j1 = L.N;
-      TRY(prof_begin(ctx));
-      CU(launch_update_tc(ctx->maps, up, mode, ctx->sm_count, s));
-      TRY(prof_end(ctx));
-      ++*launches;
-      *flops += update_flops(L.N, k0, k1, k1, L.N);
-    }
+    if (k1 >= L.N) break;
+    const int64_t k2 = std::min<int64_t>(L.N, k1 + L.nb);
+    const int b = (int)(p & 1);
+    CU(cudaStreamWaitEvent(s, ev_panel, 0));  // panel p factored and copied
+    // panel stream: next panel's columns, then the next panel itself
+    TRY(tc_update(F, b, k0, 0, (int)(k1 - k0), k1, k2, ctx->sm_count, side, PC_UPDATE));
+    TRY(tc_panel(F, k1, b ^ 1, side));
+    CU(cudaEventRecord(ev_panel, side));
+    // solver stream: the rest of the trailing matrix
+    if (k2 < L.N) TRY(tc_update(F, b, k0, 0, (int)(k1 - k0), k2, L.N, trail_grid, s, PC_UPDATE));
+    CU(cudaEventRecord(ev_trail, s));
+    CU(cudaStreamWaitEvent(side, ev_trail, 0));  // columns of panel p+2 and buffer b are free
   }
+  CU(cudaStreamWaitEvent(s, ev_panel, 0));
   return MAG_OK;
 }
 
@@ -430,6 +562,8 @@ int mag_options_default(mag_options* opt) {
   opt->workspace_limit_bytes = 0.0;
   opt->profile = 0;
   opt->reuse_distances = 1;
+  opt->lookahead = 1;
+  opt->lookahead_sms = 0;
   return MAG_OK;
 }
 
@@ -472,6 +606,13 @@ int mag_ctx_destroy(mag_ctx* ctx) {
   if (ctx->aux) cudaFree(ctx->aux);
   if (ctx->bws) cudaFree(ctx->bws);
   if (ctx->gm) cudaFree(ctx->gm);
+  if (ctx->tasks_d) cudaFree(ctx->tasks_d);
+  if (ctx->side) {
+    cudaStreamSynchronize(ctx->side);
+    cudaStreamDestroy(ctx->side);
+  }
+  for (int i = 0; i < 3; ++i)
+    if (ctx->ev_la[i]) cudaEventDestroy(ctx->ev_la[i]);
   for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
   for (int i = 0; i < 4; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);

@@ -17,6 +17,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <vector>
 
 namespace mag {
 
@@ -113,9 +114,10 @@ struct UpdParams {
   int64_t N;           // tiles per side
   int64_t k0;          // first tile column of the panel = row block 0 of the panel buffer
   int kc_lo, kc_hi;    // K range in panel-local tile columns [kc_lo, kc_hi)
-  int64_t j0, j1;      // output tile columns [j0, j1); rows I in [J, N)
-  int64_t n_super;     // filled by launch_update_tc
-  int64_t super_cols;  // filled by launch_update_tc
+  int64_t j1;          // output tile columns end before j1 (tile J+1 is skipped at j1)
+  const uint32_t* tasks;  // output blocks (I << 16) | J, in processing order
+  int64_t ntasks;
+  unsigned* counter;      // zero before the launch; CTAs claim tasks from it
   DevStatus* st;
   uint64_t timeout_ns; // bound on every barrier wait inside the kernel
 };
@@ -126,7 +128,12 @@ struct alignas(64) UpdMaps {
 };
 
 bool make_update_maps(UpdMaps* maps, const void* hi, const void* lo, int mode, int64_t cols, int64_t rows);
-int64_t update_num_super(int64_t N, int64_t j0, int64_t j1);
+// Appends the output blocks of one update (tile pairs (I, J), (I, J+1) for
+// J = j0, j0+2, ... < j1 and I in [J, N)) to `out` in 16-row x 8-pair
+// super-block order (rows of super-blocks top-down, lower triangle of the
+// super-block grid first), skipping blocks outside the trapezoid.  Returns
+// the number appended.  Requires N < 65536.
+int64_t update_tasks(int64_t N, int64_t j0, int64_t j1, std::vector<uint32_t>* out);
 cudaError_t launch_update_tc(const UpdMaps& maps, UpdParams p, int mode, int grid, cudaStream_t s);
 
 // Panel copy of column K (tiles I in (K, N)) for the tensor-core update:

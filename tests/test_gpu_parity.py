@@ -106,9 +106,10 @@ def test_cholesky_fp64_elementwise(ctx, n):
 
 
 @pytest.mark.parametrize("prec,tol", [("tf32x3", 2e-4), ("tf32", 5e-3), ("fp16x3", 2e-4), ("fp16", 5e-3)])
-@pytest.mark.parametrize("n", [130, 300, 1100, 2100])
+@pytest.mark.parametrize("n", [130, 300, 1100, 2100, 3300])
 def test_cholesky_tensor_core_normwise(ctx, prec, tol, n):
-    # one panel (n <= 1024), a trapezoid (1100), several panels (2100)
+    # one panel (n <= 1024), a trapezoid (1100), several panels (2100, 3300:
+    # the look-ahead schedule with a ragged last panel)
     X = _cloud(n, 3, seed=n)
     t = 2.0
     Lg = ctx.cholesky_factor(_dev(X), t, prec).cpu().numpy().astype(np.float64)
@@ -116,6 +117,21 @@ def test_cholesky_tensor_core_normwise(ctx, prec, tol, n):
     Lo = oracle.cholesky(Z)
     assert np.abs(Lg - Lo).max() <= tol * np.abs(Lo).max()
     assert np.all(np.triu(Lg, 1) == 0)
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "fp16x3", "fp16"])
+@pytest.mark.parametrize("n,panel,sms", [(3300, 8, 16), (3300, 2, 1), (5000, 4, 40), (2500, 3, 150)])
+def test_lookahead_factor_is_bitwise_the_serial_factor(prec, n, panel, sms):
+    # the look-ahead schedule applies the same products to every tile in the
+    # same order as the one-stream schedule, so the factors agree exactly
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    X = _dev(_cloud(n, 4, seed=n + panel))
+    base = dict(panel_tiles=panel, lookahead_sms=sms)
+    La = M.Context(M.Options(lookahead=True, **base)).cholesky_factor(X, 1.5, prec)
+    Ls = M.Context(M.Options(lookahead=False, **base)).cholesky_factor(X, 1.5, prec)
+    assert torch.equal(La, Ls)
+    assert torch.isfinite(La).all()
 
 
 def test_cholesky_bf16_well_conditioned(ctx):
