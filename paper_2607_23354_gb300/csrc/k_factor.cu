@@ -7,7 +7,7 @@
 //            block triangular solves).
 //   trsm   : panel tiles L_IK = A_IK inv(L_KK)^T as a small GEMM (in place).
 //   syrk   : CUDA-core trailing update C_IJ -= sum_k L_Ik L_Jk^T over a set of
-//            tiles (the tensor-core version lives in k_gemm_tc.cu).
+//            tiles (the tensor-core version lives in k_update_tc.cu).
 //
 // Also K3: block forward/back substitution with the packed factor, using the
 // stored inverses of the diagonal blocks so that every step is a GEMV.
@@ -174,6 +174,181 @@ __global__ void __launch_bounds__(512) k_potrf_diag(T* __restrict__ Z, T* __rest
       Y[r * TILE + c] = v;
       YT[c * TILE + r] = v;
     }
+  }
+}
+
+// ------------------------------------------------- blocked potrf (FP32)
+// The same factor and inverse for the FP32 factor, organised in 32 x 32
+// blocks of the tile held in shared memory (A: the tile becoming L; Y: inv(L)):
+//   for kb = 0..3 (o = 32 kb):
+//     warp 0 factors the diagonal block A[o:o+32, o:o+32] with lane l owning
+//       row l (pivots and column entries exchanged by shuffles, no barrier),
+//       then inverts it (lane l forward-substitutes column l of the identity)
+//       into the diagonal block of Y;
+//     all warps: blocks below it, A_ib,kb <- A_ib,kb Yd_kb^T (panel solve);
+//     all warps: trailing blocks A_ib,jb -= A_ib,kb A_jb,kb^T (kb < jb <= ib).
+//   Off-diagonal blocks of Y by block diagonals d = ib - jb = 1, 2, 3:
+//     Y_ib,jb = -Yd_ib (sum_{kb=jb}^{ib-1} L_ib,kb Y_kb,jb).
+// 32 + 14 barriers instead of four per column.  A non-positive pivot raises
+// ST_NOTPD with its row (1-based, smallest wins) and is replaced by 1 so the
+// kernel finishes without NaNs.
+constexpr int PB = 32;  // block edge
+
+__global__ void __launch_bounds__(512, 1) k_potrf_blk(float* __restrict__ Z, float* __restrict__ Dinv,
+                                                   float* __restrict__ DinvT, int64_t K, DevStatus* st) {
+  extern __shared__ float psm[];
+  float* A = psm;                // [TILE][LDA]
+  float* Y = psm + TILE * LDA;   // [TILE][LDA]
+  __shared__ float rdiag[TILE];  // 1 / L[i][i]
+  __shared__ int skip;
+  const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+  if (tid == 0) skip = (st->flags & (ST_NOTPD | ST_NONFINITE | ST_DUPLICATE)) != 0;  // set by earlier kernels
+  __syncthreads();
+  if (skip) return;  // uniform across the CTA
+  float* tile = Z + tri_index(K, K) * TILE_ELEMS;
+  for (int e = tid; e < TILE * TILE; e += 512) A[(e >> 7) * LDA + (e & 127)] = tile[e];
+  __syncthreads();
+
+  for (int kb = 0; kb < TILE / PB; ++kb) {
+    const int o = kb * PB;
+    if (w == 0) {
+      float d[PB];
+#pragma unroll
+      for (int j = 0; j < PB; ++j) d[j] = A[(o + l) * LDA + o + j];
+#pragma unroll
+      for (int c = 0; c < PB; ++c) {
+        const float piv = __shfl_sync(0xffffffffu, d[c], c);
+        const bool bad = !(piv > 0.f);
+        if (bad && l == 0) {
+          atomicOr(&st->flags, ST_NOTPD);
+          atomicMin(&st->notpd_index, (int)(K * TILE + o + c + 1));
+        }
+        const float sq = bad ? 1.f : sqrtf(piv);
+        const float rs = 1.f / sq;
+        const float lc = l > c ? d[c] * rs : (l == c ? sq : 0.f);
+        d[c] = lc;
+        if (l == c) rdiag[o + c] = rs;
+#pragma unroll
+        for (int j = c + 1; j < PB; ++j) d[j] -= lc * __shfl_sync(0xffffffffu, lc, j);
+      }
+#pragma unroll
+      for (int j = 0; j < PB; ++j) A[(o + l) * LDA + o + j] = j <= l ? d[j] : 0.f;
+      __syncwarp();
+      // column l of inv(L_D): y_i = (e_l[i] - sum_{k<i} L[i][k] y_k) / L[i][i]
+      float y[PB];
+#pragma unroll
+      for (int i = 0; i < PB; ++i) {
+        float acc = (i == l) ? 1.f : 0.f;
+#pragma unroll
+        for (int k = 0; k < i; ++k) acc -= A[(o + i) * LDA + o + k] * y[k];
+        y[i] = acc * rdiag[o + i];
+      }
+#pragma unroll
+      for (int i = 0; i < PB; ++i) Y[(o + i) * LDA + o + l] = y[i];
+    }
+    __syncthreads();
+    // panel solve of the blocks below: X[r][c] = sum_k A[r][k] Yd[c][k]
+    float xb[3][2];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int ro = o + PB * (b + 1);
+      if (ro < TILE) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int r = ro + w + 16 * q;
+          float acc = 0.f;
+#pragma unroll
+          for (int k = 0; k < PB; ++k) acc += A[r * LDA + o + k] * Y[(o + l) * LDA + o + k];
+          xb[b][q] = acc;
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int ro = o + PB * (b + 1);
+      if (ro < TILE) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) A[(ro + w + 16 * q) * LDA + o + l] = xb[b][q];
+      }
+    }
+    __syncthreads();
+    // trailing blocks
+    for (int ib = kb + 1; ib < TILE / PB; ++ib)
+      for (int jb = kb + 1; jb <= ib; ++jb) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int r = ib * PB + w + 16 * q, c = jb * PB + l;
+          float acc = 0.f;
+#pragma unroll
+          for (int k = 0; k < PB; ++k) acc += A[r * LDA + o + k] * A[c * LDA + o + k];
+          A[r * LDA + c] -= acc;
+        }
+      }
+    __syncthreads();
+  }
+
+  // off-diagonal blocks of Y = inv(L), one block diagonal at a time
+  for (int dd = 1; dd < TILE / PB; ++dd) {
+    float tv[3][2];
+#pragma unroll
+    for (int jb = 0; jb < 3; ++jb) {
+      const int ib = jb + dd;
+      if (ib < TILE / PB) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int r = ib * PB + w + 16 * q, c = jb * PB + l;
+          float acc = 0.f;
+          for (int kb = jb; kb < ib; ++kb) {
+#pragma unroll
+            for (int k = 0; k < PB; ++k) acc += A[r * LDA + kb * PB + k] * Y[(kb * PB + k) * LDA + c];
+          }
+          tv[jb][q] = acc;
+        }
+      }
+    }
+#pragma unroll
+    for (int jb = 0; jb < 3; ++jb) {
+      const int ib = jb + dd;
+      if (ib < TILE / PB) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) Y[(ib * PB + w + 16 * q) * LDA + jb * PB + l] = tv[jb][q];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int jb = 0; jb < 3; ++jb) {
+      const int ib = jb + dd;
+      if (ib < TILE / PB) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int r = ib * PB + w + 16 * q, c = jb * PB + l;
+          float acc = 0.f;
+#pragma unroll
+          for (int k = 0; k < PB; ++k) acc += Y[r * LDA + ib * PB + k] * Y[(ib * PB + k) * LDA + c];
+          tv[jb][q] = -acc;
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int jb = 0; jb < 3; ++jb) {
+      const int ib = jb + dd;
+      if (ib < TILE / PB) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) Y[(ib * PB + w + 16 * q) * LDA + jb * PB + l] = tv[jb][q];
+      }
+    }
+    __syncthreads();
+  }
+
+  float* Yg = Dinv + K * TILE_ELEMS;
+  float* YTg = DinvT + K * TILE_ELEMS;
+  for (int e = tid; e < TILE * TILE; e += 512) {
+    const int r = e >> 7, c = e & 127;
+    tile[e] = c <= r ? A[r * LDA + c] : 0.f;
+    Yg[e] = c <= r ? Y[r * LDA + c] : 0.f;
+    YTg[e] = r <= c ? Y[c * LDA + r] : 0.f;
   }
 }
 
@@ -411,13 +586,20 @@ cudaError_t launch_unpack(const T* Z, int64_t n, int64_t N, bool symmetric, T* o
 
 template <typename T>
 cudaError_t launch_potrf_diag(T* Z, T* Dinv, int64_t K, int64_t n, DevStatus* st, cudaStream_t s) {
-  const size_t smem = (size_t)TILE * LDA * sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(k_potrf_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
   const int64_t N = (n + TILE - 1) / TILE;
   // Dinv holds N tiles of inv(L_KK) followed by N tiles of inv(L_KK)^T.
-  k_potrf_diag<T><<<1, 512, smem, s>>>(Z, Dinv, Dinv + N * TILE_ELEMS, K, n, st);
+  if constexpr (sizeof(T) == 4) {
+    const size_t smem = (size_t)2 * TILE * LDA * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_potrf_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_potrf_blk<<<1, 512, smem, s>>>(Z, Dinv, Dinv + N * TILE_ELEMS, K, st);
+  } else {
+    const size_t smem = (size_t)TILE * LDA * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(k_potrf_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_potrf_diag<T><<<1, 512, smem, s>>>(Z, Dinv, Dinv + N * TILE_ELEMS, K, n, st);
+  }
   note_launch();
   return cudaGetLastError();
 }
