@@ -42,7 +42,8 @@ class mag_options(ctypes.Structure):
                 ("gmres_max_iters", ctypes.c_int32), ("allow_fallback", ctypes.c_int32),
                 ("panel_tiles", ctypes.c_int32), ("workspace_limit_bytes", ctypes.c_double),
                 ("profile", ctypes.c_int32), ("reuse_distances", ctypes.c_int32),
-                ("lookahead", ctypes.c_int32), ("lookahead_sms", ctypes.c_int32)]
+                ("lookahead", ctypes.c_int32), ("lookahead_sms", ctypes.c_int32),
+                ("cta_pairs", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
 
 class mag_info(ctypes.Structure):
@@ -144,6 +145,7 @@ class Options:
     reuse_distances: bool = True
     lookahead: bool = True
     lookahead_sms: int = 0
+    cta_pairs: bool = False
 
     def to_c(self) -> mag_options:
         o = mag_options()
@@ -161,6 +163,7 @@ class Options:
         o.reuse_distances = int(self.reuse_distances)
         o.lookahead = int(self.lookahead)
         o.lookahead_sms = int(self.lookahead_sms)
+        o.cta_pairs = int(self.cta_pairs)
         return o
 
 

@@ -92,59 +92,92 @@ __global__ void __launch_bounds__(RES_THREADS) k_resid_mf(const double* __restri
   }
 }
 
-// Stored variant of K4: (Zw)_j from the packed FP64 tiles of Z (lower tiles,
-// diagonal tiles in full), each tile read once.  One CTA per lower tile
-// (I, J) computes the tile's row contributions Z_IJ w_J (rows of block I)
-// and, for I != J, its transposed contributions Z_IJ^T w_I (rows of block J),
-// and stores each as a partial P[row block][other block][r].  Within a tile
-// the sums are short trees (128 terms); across tiles k_resid_stored_finish
-// adds the N partials of a row with Neumaier compensation.
-// Thread layout (256 threads): warp wp covers tile rows 16 wp .. 16 wp + 15,
-// lane l covers columns 4l .. 4l+3 (each row read as one 1 KB coalesced line).
+// Stored-tile residual: Zw from the FP64 lower tiles (Z_IJ for I >= J; the
+// diagonal tiles are stored in full).  CTA (t, J) works on column block J:
+// t = 0 takes the diagonal tile; t >= 1 the strip of RS_STRIP tiles (I, J),
+// I in [J+1+(t-1)S, J+1+tS).  For each tile it stores the row contributions
+// Z_IJ w_J (rows of block I) as partial P[I][J][r]; over the strip it
+// accumulates the transposed contributions Z_IJ^T w_I (rows of block J) in
+// registers and stores their sum once as P[J][J+t][c], so the cross-lane
+// reduction of the column sums is paid once per strip.  Every product is one
+// FP64 FMA; within a row the 128 terms are a short tree, across tiles
+// k_resid_stored_finish adds a row's partials with Neumaier compensation.
+// Thread layout (256 threads): lane = 8 * rs + cg; column group cg owns the
+// 16 columns 16k + 2cg, 16k + 2cg + 1 (k < 8); warp wp and row slot rs cover
+// tile rows 16 wp + 4 i + rs (i < 4).  Each load instruction reads four
+// 128-byte row segments.
+constexpr int RS_STRIP = 8;
+
 __global__ void __launch_bounds__(256) k_resid_stored(const double* __restrict__ Zd, int64_t n, int64_t N,
                                                       const double* __restrict__ w,
                                                       double* __restrict__ P) {
   __shared__ double colp[8][TILE];
-  int64_t I, J;
-  tri_coords((int64_t)blockIdx.x, &I, &J);
-  const int tid = threadIdx.x, wp = tid >> 5, l = tid & 31;
-  const double* tile = Zd + tri_index(I, J) * TILE_ELEMS;
-  double wj[4], c4[4] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t J = blockIdx.y;
+  const int64_t t = blockIdx.x;
+  const int64_t nstrips = (N - 1 - J + RS_STRIP - 1) / RS_STRIP;
+  if (t > nstrips) return;  // uniform
+  const int tid = threadIdx.x, wp = tid >> 5, l = tid & 31, cg = l & 7, rs = l >> 3;
+  double wc[16];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int64_t col = J * TILE + 4 * l + q;
-    wj[q] = col < n ? w[col] : 0.0;
+  for (int k = 0; k < 8; ++k) {
+    const int64_t col = J * TILE + 16 * k + 2 * cg;
+    wc[2 * k] = col < n ? w[col] : 0.0;
+    wc[2 * k + 1] = col + 1 < n ? w[col + 1] : 0.0;
   }
-#pragma unroll 4
-  for (int i = 0; i < 16; ++i) {
-    const int r = wp * 16 + i;
-    const int64_t row = I * TILE + r;
-    const double wi = row < n ? w[row] : 0.0;
-    const double2 a = *reinterpret_cast<const double2*>(tile + r * TILE + 4 * l);
-    const double2 bq = *reinterpret_cast<const double2*>(tile + r * TILE + 4 * l + 2);
-    double s = a.x * wj[0] + a.y * wj[1] + bq.x * wj[2] + bq.y * wj[3];
+  const int64_t I0 = t == 0 ? J : J + 1 + (t - 1) * RS_STRIP;
+  const int64_t I1 = t == 0 ? J + 1 : (I0 + RS_STRIP < N ? I0 + RS_STRIP : N);
+  double cs[16];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (l == 0) P[(I * N + J) * TILE + r] = s;
-    c4[0] = fma(a.x, wi, c4[0]);
-    c4[1] = fma(a.y, wi, c4[1]);
-    c4[2] = fma(bq.x, wi, c4[2]);
-    c4[3] = fma(bq.y, wi, c4[3]);
+  for (int k = 0; k < 16; ++k) cs[k] = 0.0;
+  for (int64_t I = I0; I < I1; ++I) {
+    const double* tile = Zd + tri_index(I, J) * TILE_ELEMS;
+#pragma unroll 2
+    for (int i = 0; i < 4; ++i) {
+      const int r = wp * 16 + 4 * i + rs;
+      const int64_t row = I * TILE + r;
+      const double wr = row < n ? w[row] : 0.0;
+      const double* rp = tile + r * TILE + 2 * cg;
+      double sr = 0.0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const double2 z = *reinterpret_cast<const double2*>(rp + 16 * k);
+        sr = fma(z.x, wc[2 * k], sr);
+        sr = fma(z.y, wc[2 * k + 1], sr);
+        cs[2 * k] = fma(z.x, wr, cs[2 * k]);
+        cs[2 * k + 1] = fma(z.y, wr, cs[2 * k + 1]);
+      }
+      sr += __shfl_xor_sync(0xffffffffu, sr, 1);
+      sr += __shfl_xor_sync(0xffffffffu, sr, 2);
+      sr += __shfl_xor_sync(0xffffffffu, sr, 4);
+      if (cg == 0) P[(I * N + J) * TILE + r] = sr;
+    }
   }
-  if (I == J) return;  // uniform: the diagonal tile is stored in full
+  if (t == 0) return;  // uniform: the diagonal tile's rows already cover both triangles
 #pragma unroll
-  for (int q = 0; q < 4; ++q) colp[wp][4 * l + q] = c4[q];
+  for (int k = 0; k < 16; ++k) {
+    cs[k] += __shfl_xor_sync(0xffffffffu, cs[k], 8);
+    cs[k] += __shfl_xor_sync(0xffffffffu, cs[k], 16);
+  }
+  if (rs == 0) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      colp[wp][16 * k + 2 * cg] = cs[2 * k];
+      colp[wp][16 * k + 2 * cg + 1] = cs[2 * k + 1];
+    }
+  }
   __syncthreads();
   if (tid < TILE) {
-    double s = 0.0;
+    double sc = 0.0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) s += colp[k][tid];
-    P[(J * N + I) * TILE + tid] = s;
+    for (int k = 0; k < 8; ++k) sc += colp[k][tid];
+    P[(J * N + J + t) * TILE + tid] = sc;
   }
 }
 
-// r_j = b_j - sum_J P[I][J][r] (Neumaier over the N tile partials of the
-// row), with ||r||, ||Z|| (from the generator's row sums) and ||w|| maxima.
+// r_j = b_j - (sum of the partials of row j) with Neumaier compensation: row
+// block X holds P[X][J] for J <= X (its tiles' row sums) followed by
+// P[X][X+t], t = 1..ceil((N-1-X)/S) (the strips' column sums); with ||r||,
+// ||Z|| (from the generator's row sums) and ||w|| maxima.
 __global__ void k_resid_stored_finish(const double* __restrict__ P, int64_t n, int64_t N, int64_t np,
                                       const double* __restrict__ w, const double* __restrict__ b,
                                       const double* __restrict__ rowsum, double* __restrict__ r,
@@ -153,8 +186,9 @@ __global__ void k_resid_stored_finish(const double* __restrict__ P, int64_t n, i
   double ra = 0.0, za = 0.0, wa = 0.0;
   if (j < n) {
     const int64_t I = j / TILE, rr = j % TILE;
+    const int64_t slots = I + 1 + (N - 1 - I + RS_STRIP - 1) / RS_STRIP;
     double s = 0.0, c = 0.0;
-    for (int64_t J = 0; J < N; ++J) {
+    for (int64_t J = 0; J < slots; ++J) {
       const double v = P[(I * N + J) * TILE + rr];
       const double tt = s + v;
       if (fabs(s) >= fabs(v))
@@ -472,7 +506,9 @@ cudaError_t launch_residual_mf(const double* X, int64_t n, int m, double t, cons
 cudaError_t launch_residual_stored(const double* Zd, int64_t n, int64_t N, const double* w,
                                    const double* b, const double* rowsum, double* r, double* P, int64_t np,
                                    DevStatus* st, cudaStream_t s) {
-  k_resid_stored<<<(unsigned)num_lower_tiles(N), 256, 0, s>>>(Zd, n, N, w, P);
+  if (N > 65535) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)((N - 1 + RS_STRIP - 1) / RS_STRIP + 1), (unsigned)N);
+  k_resid_stored<<<grid, 256, 0, s>>>(Zd, n, N, w, P);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -426,6 +426,377 @@ __global__ void __launch_bounds__(UPD_THREADS, 1)
   }
 }
 
+// ====================================================== CTA-pair version
+// The same update with tcgen05 MMAs of cta_group::2: a cluster of two CTAs on
+// two SMs computes a 256 x 256 block -- rows of tile I (CTA rank 0) and tile
+// I+1 (rank 1), columns of tiles J, J+1 -- as one M=256, N=256 MMA per K
+// step.  Each CTA stages only its own 128 rows of A and its 128-row half of
+// B (rank 0: tile J, rank 1: tile J+1); the MMA reads the peer's halves, so
+// per SM the L2 -> shared-memory traffic per flop is two thirds of the single-
+// CTA kernel's and the stage ring is 1.5x deeper.  Each CTA's TMEM receives
+// its own 128 rows x 256 columns of the accumulator.
+//
+// Roles (6 warps per CTA):
+//   warp 0 : TMA producer of this CTA's halves (local mbarrier); in rank 0 it
+//            also claims tasks and hands them to both CTAs (remote stores +
+//            remote mbarrier arrivals);
+//   warp 1 : TMEM allocation (both CTAs, cta_group::2); rank 0 issues the MMAs
+//            once both CTAs' stages are full; rank 1 forwards "stage full" of
+//            its own loads to rank 0's barrier (so each CTA can always wait
+//            for the loads it issued itself);
+//   warps 2..5 : epilogue on this CTA's rows.
+// MMA completion is committed to the barrier of both CTAs (multicast), the
+// epilogues of both CTAs report "accumulator drained" to rank 0.
+// Every wait is bounded as in the single-CTA kernel; both CTAs meet at a
+// cluster barrier before TMEM is released and before either exits.
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ void st_remote_s64(uint32_t cluster_addr, int64_t v) {
+  asm volatile("st.shared::cluster.s64 [%0], %1;" ::"r"(cluster_addr), "l"(v) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                                  uint64_t deadline) {
+  uint32_t it = 0;
+  while (!mbar_try_wait_cluster(bar, parity)) {
+    if ((++it & 255u) == 0) {
+      if (*abort_flag) return false;
+      if (globaltimer() > deadline) {
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Instruction descriptor for the pair: D = F32, M = 256, N = 256, K-major A/B.
+__host__ __device__ constexpr uint32_t instr_desc2(uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
+}
+template <int MODE>
+__device__ __forceinline__ void mma2(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  constexpr uint32_t idesc = instr_desc2(ModeCfg<MODE>::FMT);
+  if constexpr (ModeCfg<MODE>::ELEM == 2) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
+}
+// Arrive on the barrier at this offset in both CTAs once the MMAs issued so
+// far by this thread have completed.
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
+  const uint16_t mask = 3;
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
+template <int MODE>
+constexpr int stages2_of() {
+  return ModeCfg<MODE>::SPLIT ? 3 : 6;
+}
+constexpr uint32_t TMEM_COLS2 = 256;  // one 128 x 256 FP32 accumulator per CTA
+constexpr int NACC2 = (int)(TMEM_COLS2 / 256);
+
+template <int MODE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
+    k_update_tc2(const __grid_constant__ CUtensorMap m_hi, const __grid_constant__ CUtensorMap m_lo,
+                 const UpdParams p) {
+  using Cfg = ModeCfg<MODE>;
+  constexpr int S = stages2_of<MODE>();
+  constexpr int CHUNK_BYTES = Cfg::CHUNK;
+  constexpr int HALF_BYTES = 128 * CHUNK_BYTES;           // 128 rows of one operand copy
+  constexpr int OPS = Cfg::SPLIT ? 2 : 1;
+  constexpr int STAGE_BYTES = OPS * 2 * HALF_BYTES;        // A half + B half (x hi/lo)
+  constexpr int KSTEP_BYTES = 32;
+  constexpr int KSTEPS = CHUNK_BYTES / KSTEP_BYTES;
+  constexpr int ELEMS_PER_CHUNK = CHUNK_BYTES / Cfg::ELEM;
+  // stage layout: [A_hi | B_hi | A_lo | B_lo]
+  constexpr int OFF_BHI = HALF_BYTES, OFF_ALO = 2 * HALF_BYTES, OFF_BLO = 3 * HALF_BYTES;
+
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // full_bar: this CTA's own loads landed; peer_bar (rank 0): rank 1's loads landed
+  __shared__ __align__(8) uint64_t full_bar[S], peer_bar[S], empty_bar[S], tfull_bar[NACC2], tempty_bar[NACC2];
+  __shared__ __align__(8) uint64_t tq_full[TQ], tq_empty[TQ];
+  __shared__ int64_t tq_val[TQ];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&peer_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int a = 0; a < NACC2; ++a) {
+      mbar_init(&tfull_bar[a], 1);
+      mbar_init(&tempty_bar[a], 8);  // four epilogue warps of each CTA (rank 0's barrier is used)
+    }
+    for (int i = 0; i < TQ; ++i) {
+      mbar_init(&tq_full[i], 1);
+      // rank 0: its MMA thread + 4 epilogue warps + rank 1's producer, forwarder, 4 epilogue warps
+      mbar_init(&tq_empty[i], 11);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_sh)),
+                 "r"(TMEM_COLS2)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  cluster_sync_all();  // barriers of both CTAs initialised, TMEM allocated
+  tc_fence_after();
+  const uint32_t tmem_base = tmem_base_sh;
+  const uint64_t deadline = globaltimer() + p.timeout_ns;
+  // both CTAs must hold the accumulator at the same TMEM address
+  if (threadIdx.x == 0) {
+    const uint32_t peer = map_to_rank(smem_u32(&tmem_base_sh), rank ^ 1u);
+    uint32_t other;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(other) : "r"(peer) : "memory");
+    if (other != tmem_base) {
+      abort_flag = 1;
+      atomicOr(&p.st->flags, ST_TIMEOUT);
+    }
+  }
+  __syncthreads();
+  const bool run = abort_flag == 0;
+  const int chunk_lo = p.kc_lo * (TILE * Cfg::ELEM / CHUNK_BYTES);
+  const int chunk_hi = p.kc_hi * (TILE * Cfg::ELEM / CHUNK_BYTES);
+  // rank-0 addresses of the shared hand-off barriers, as seen from this CTA
+  const uint32_t r0_tq_empty = map_to_rank(smem_u32(&tq_empty[0]), 0);
+  const uint32_t r0_tempty = map_to_rank(smem_u32(&tempty_bar[0]), 0);
+  const uint32_t r0_peer = map_to_rank(smem_u32(&peer_bar[0]), 0);
+  const uint32_t r1_tq_full = map_to_rank(smem_u32(&tq_full[0]), 1);
+  const uint32_t r1_tq_val = map_to_rank(smem_u32(&tq_val[0]), 1);
+
+  if (run && warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t stage = 0, phase = 0, ts = 0, tph = 0;
+      uint32_t issued_parity[S];
+      bool issued[S];
+      for (int s = 0; s < S; ++s) issued[s] = false, issued_parity[s] = 0;
+      bool ok = true;
+      while (ok) {
+        int64_t q;
+        if (rank == 0) {
+          if (!mbar_wait_cluster(&tq_empty[ts], tph ^ 1u, &abort_flag, deadline)) break;
+          q = (int64_t)atomicAdd(p.counter, 1u);
+          if (q >= p.ntasks) q = -1;
+          tq_val[ts] = q;
+          st_remote_s64(r1_tq_val + ts * 8u, q);
+          mbar_arrive(&tq_full[ts]);
+          mbar_arrive_remote(r1_tq_full + ts * 8u);
+        } else {
+          if (!mbar_wait_cluster(&tq_full[ts], tph, &abort_flag, deadline)) break;
+          q = tq_val[ts];
+          mbar_arrive_remote(r0_tq_empty + ts * 8u);
+        }
+        if (++ts == TQ) ts = 0, tph ^= 1u;
+        if (q < 0) break;
+        int64_t I, J;
+        decode_task(q, p, &I, &J);
+        const int ya = (int)((I + rank - p.k0) * TILE), yb = (int)((J + rank - p.k0) * TILE);
+        for (int c = chunk_lo; c < chunk_hi; ++c) {
+          if (!mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag, deadline)) {
+            ok = false;
+            break;
+          }
+          unsigned char* sbase = smem + stage * STAGE_BYTES;
+          mbar_expect_tx(&full_bar[stage], STAGE_BYTES);
+          const int x = c * ELEMS_PER_CHUNK;
+          tma_load_2d(sbase, &m_hi, &full_bar[stage], x, ya);
+          tma_load_2d(sbase + OFF_BHI, &m_hi, &full_bar[stage], x, yb);
+          if (Cfg::SPLIT) {
+            tma_load_2d(sbase + OFF_ALO, &m_lo, &full_bar[stage], x, ya);
+            tma_load_2d(sbase + OFF_BLO, &m_lo, &full_bar[stage], x, yb);
+          }
+          issued[stage] = true;
+          issued_parity[stage] = phase;
+          if (++stage == S) stage = 0, phase ^= 1u;
+        }
+      }
+      if (!ok || abort_flag) {
+        // wait (bounded) for this CTA's own loads in flight
+        const uint64_t dl = globaltimer() + 200000000ull;
+        for (int s = 0; s < S; ++s)
+          if (issued[s])
+            while (!mbar_try_wait(&full_bar[s], issued_parity[s]) && globaltimer() < dl) {
+            }
+      }
+    }
+  } else if (run && warp == 1) {
+    if (lane == 0) {
+      uint32_t ts = 0, tph = 0, stage = 0, phase = 0;
+      if (rank == 0) {
+        // ------------------------------------------------------- MMA issuer
+        uint32_t acc = 0, acc_phase = 0;
+        bool ok = true;
+        while (ok) {
+          if (!mbar_wait_cluster(&tq_full[ts], tph, &abort_flag, deadline)) break;
+          const int64_t q = tq_val[ts];
+          mbar_arrive(&tq_empty[ts]);
+          if (++ts == TQ) ts = 0, tph ^= 1u;
+          if (q < 0) break;
+          if (!mbar_wait_cluster(&tempty_bar[acc], acc_phase ^ 1u, &abort_flag, deadline)) break;
+          tc_fence_after();
+          const uint32_t d = tmem_base + acc * 256u;
+          for (int c = chunk_lo; c < chunk_hi; ++c) {
+            if (!mbar_wait(&full_bar[stage], phase, &abort_flag, deadline) ||
+                !mbar_wait_cluster(&peer_bar[stage], phase, &abort_flag, deadline)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sb = smem_u32(smem + stage * STAGE_BYTES);
+#pragma unroll
+            for (int k = 0; k < KSTEPS; ++k) {
+              const uint64_t ahi = smem_desc<CHUNK_BYTES>(sb + k * KSTEP_BYTES);
+              const uint64_t bhi = smem_desc<CHUNK_BYTES>(sb + OFF_BHI + k * KSTEP_BYTES);
+              const uint32_t accum = (c > chunk_lo || k > 0) ? 1u : 0u;
+              mma2<MODE>(d, ahi, bhi, accum);
+              if (Cfg::SPLIT) {
+                const uint64_t alo = smem_desc<CHUNK_BYTES>(sb + OFF_ALO + k * KSTEP_BYTES);
+                const uint64_t blo = smem_desc<CHUNK_BYTES>(sb + OFF_BLO + k * KSTEP_BYTES);
+                mma2<MODE>(d, ahi, blo, 1u);
+                mma2<MODE>(d, alo, bhi, 1u);
+              }
+            }
+            mma_commit_pair(&empty_bar[stage]);  // stage of both CTAs free once read
+            if (++stage == S) stage = 0, phase ^= 1u;
+          }
+          if (!ok) break;
+          mma_commit_pair(&tfull_bar[acc]);  // both halves of the accumulator ready
+          if (++acc == NACC2) acc = 0, acc_phase ^= 1u;
+        }
+      } else {
+        // ------------------------------------------ forwarder (rank 1 only)
+        while (true) {
+          if (!mbar_wait_cluster(&tq_full[ts], tph, &abort_flag, deadline)) break;
+          const int64_t q = tq_val[ts];
+          mbar_arrive_remote(r0_tq_empty + ts * 8u);
+          if (++ts == TQ) ts = 0, tph ^= 1u;
+          if (q < 0) break;
+          bool ok = true;
+          for (int c = chunk_lo; c < chunk_hi; ++c) {
+            if (!mbar_wait(&full_bar[stage], phase, &abort_flag, deadline)) {
+              ok = false;
+              break;
+            }
+            mbar_arrive_remote(r0_peer + stage * 8u);
+            if (++stage == S) stage = 0, phase ^= 1u;
+          }
+          if (!ok) break;
+        }
+      }
+    }
+  } else if (run) {
+    // --------------------------------------------------------------- epilogue
+    const int quad = warp & 3;
+    const int row = quad * 32 + lane;
+    uint32_t acc = 0, acc_phase = 0, ts = 0, tph = 0;
+    constexpr float acc_scale =
+        (MODE == UPD_FP16X3 || MODE == UPD_FP16) ? 1.0f / (float)(1u << (2 * FP16_SCALE_LOG2)) : 1.0f;
+    for (;;) {
+      if (!mbar_wait_cluster(&tq_full[ts], tph, &abort_flag, deadline)) break;
+      const int64_t q = tq_val[ts];
+      __syncwarp();
+      if (lane == 0) {
+        if (rank == 0)
+          mbar_arrive(&tq_empty[ts]);
+        else
+          mbar_arrive_remote(r0_tq_empty + ts * 8u);
+      }
+      if (++ts == TQ) ts = 0, tph ^= 1u;
+      if (q < 0) break;
+      int64_t I, J;
+      decode_task(q, p, &I, &J);
+      const int64_t Ir = I + rank;  // this CTA's row tile
+      if (!mbar_wait_cluster(&tfull_bar[acc], acc_phase, &abort_flag, deadline)) break;
+      tc_fence_after();
+      if (Ir < p.N) {
+        for (int cc = 0; cc < 8; ++cc) {
+          const int64_t Jx = J + (cc >> 2);
+          if (Jx >= p.j1 || Jx > Ir) break;  // the second column tile is outside the trapezoid
+          float v[32];
+          tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + acc * 256u + cc * 32, v);
+          float4* cp = reinterpret_cast<float4*>(p.Z + tri_index(Ir, Jx) * TILE_ELEMS + (int64_t)row * TILE +
+                                                 (cc & 3) * 32);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            float4 c4 = cp[i];
+            c4.x -= acc_scale * v[4 * i + 0];
+            c4.y -= acc_scale * v[4 * i + 1];
+            c4.z -= acc_scale * v[4 * i + 2];
+            c4.w -= acc_scale * v[4 * i + 3];
+            cp[i] = c4;
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        if (rank == 0)
+          mbar_arrive(&tempty_bar[acc]);
+        else
+          mbar_arrive_remote(r0_tempty + acc * 8u);
+      }
+      if (++acc == NACC2) acc = 0, acc_phase ^= 1u;
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && abort_flag) atomicOr(&p.st->flags, ST_TIMEOUT);
+  cluster_sync_all();  // no CTA leaves while its peer may still signal it or read its stages
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS2)
+                 : "memory");
+  }
+}
+
 // ------------------------------------------------------------ tensor maps
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -478,6 +849,22 @@ cudaError_t launch_mode(const UpdMaps& maps, const UpdParams& p, int grid, cudaS
   return cudaGetLastError();
 }
 
+template <int MODE>
+cudaError_t launch_mode2(const UpdMaps& maps, const UpdParams& p, int grid, cudaStream_t s) {
+  constexpr int OPS = ModeCfg<MODE>::SPLIT ? 2 : 1;
+  constexpr int CH = ModeCfg<MODE>::CHUNK;
+  const size_t smem = (size_t)stages2_of<MODE>() * OPS * 2 * 128 * CH + 1024;
+  auto kern = k_update_tc2<MODE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(maps.m);
+  grid &= ~1;  // whole clusters
+  if (grid < 2) grid = 2;
+  kern<<<grid, UPD_THREADS, smem, s>>>(m[0], m[2], p);
+  note_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 static_assert(sizeof(CUtensorMap) == 128, "CUtensorMap layout");
@@ -492,8 +879,10 @@ bool make_update_maps(UpdMaps* maps, const void* hi, const void* lo, int mode, i
   return true;
 }
 
-int64_t update_tasks(int64_t N, int64_t j0, int64_t j1, std::vector<uint32_t>* out) {
+int64_t update_tasks(int64_t N, int64_t j0, int64_t j1, bool pairs, std::vector<uint32_t>* out) {
   if (j0 >= j1 || j0 >= N || N >= 65536) return 0;
+  const int rstep = pairs ? 2 : 1;                    // rows of tiles per task
+  const int SRB = SUPER / rstep;                      // tasks per super-block row
   const int64_t SR = (N - j0 + SUPER - 1) / SUPER;   // super-block rows
   const int64_t SC = (j1 - j0 + SUPER - 1) / SUPER;  // super-block columns
   const int64_t n_super = SR <= SC ? SR * (SR + 1) / 2 : SC * (SC + 1) / 2 + (SR - SC) * SC;
@@ -507,17 +896,28 @@ int64_t update_tasks(int64_t N, int64_t j0, int64_t j1, std::vector<uint32_t>* o
       sr = SC + (sb - tri) / SC;
       sc = (sb - tri) % SC;
     }
-    for (int r = 0; r < SUPER; ++r)
+    for (int r = 0; r < SRB; ++r)
       for (int c = 0; c < SUPER / 2; ++c) {
-        const int64_t I = j0 + sr * SUPER + r, J = j0 + sc * SUPER + 2 * c;
+        const int64_t I = j0 + sr * SUPER + rstep * r, J = j0 + sc * SUPER + 2 * c;
         if (I < N && J < j1 && J <= I) out->push_back((uint32_t)(I << 16) | (uint32_t)J);
       }
   }
   return (int64_t)(out->size() - before);
 }
 
-cudaError_t launch_update_tc(const UpdMaps& maps, UpdParams p, int mode, int grid, cudaStream_t s) {
+cudaError_t launch_update_tc(const UpdMaps& maps, UpdParams p, int mode, int grid, bool pairs, cudaStream_t s) {
   if (p.ntasks <= 0 || p.kc_hi <= p.kc_lo) return cudaSuccess;
+  if (pairs) {
+    if ((int64_t)grid > 2 * p.ntasks) grid = (int)(2 * p.ntasks);
+    switch (mode) {
+      case UPD_TF32X3: return launch_mode2<UPD_TF32X3>(maps, p, grid, s);
+      case UPD_TF32: return launch_mode2<UPD_TF32>(maps, p, grid, s);
+      case UPD_BF16: return launch_mode2<UPD_BF16>(maps, p, grid, s);
+      case UPD_FP16X3: return launch_mode2<UPD_FP16X3>(maps, p, grid, s);
+      case UPD_FP16: return launch_mode2<UPD_FP16>(maps, p, grid, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   if ((int64_t)grid > p.ntasks) grid = (int)p.ntasks;
   switch (mode) {
     case UPD_TF32X3: return launch_mode<UPD_TF32X3>(maps, p, grid, s);

@@ -81,7 +81,7 @@ struct mag_ctx {
   uint32_t* tasks_d = nullptr;       // task tables of the update launches of one factor
   size_t tasks_cap = 0;
   int64_t tasks_N = -1;
-  int tasks_nb = -1, tasks_la = -1;
+  int tasks_nb = -1, tasks_la = -1, tasks_pairs = -1;
   std::map<std::pair<int64_t, int64_t>, std::pair<int64_t, int64_t>> task_rng;  // (j0, j1) -> (offset, count)
   cudaStream_t side = nullptr;       // panel stream of the look-ahead factor
   cudaEvent_t ev_la[3] = {nullptr, nullptr, nullptr};  // start, panel done, trailing done
@@ -352,9 +352,10 @@ int upd_mode(int prec) {
 // trailing matrix with K = (k1 - k0) * 128.
 // Task tables of every tensor-core update launch of one factor with the
 // current layout (built on the host once per (N, panel width, schedule)).
-int ensure_tasks(mag_ctx* ctx, bool la) {
+int ensure_tasks(mag_ctx* ctx, bool la, bool pairs) {
   const Layout& L = ctx->lay;
-  if (ctx->tasks_N == L.N && ctx->tasks_nb == L.nb && ctx->tasks_la == (int)la) return MAG_OK;
+  if (ctx->tasks_N == L.N && ctx->tasks_nb == L.nb && ctx->tasks_la == (int)la && ctx->tasks_pairs == (int)pairs)
+    return MAG_OK;
   if (L.N >= 65536) return fail(ctx, MAG_EINVAL, "n = %lld too large for the tensor-core factor", (long long)L.n);
   std::vector<uint32_t> t;
   ctx->task_rng.clear();
@@ -362,7 +363,7 @@ int ensure_tasks(mag_ctx* ctx, bool la) {
     const auto key = std::make_pair(j0, j1);
     if (j0 >= j1 || ctx->task_rng.count(key)) return;
     const int64_t off = (int64_t)t.size();
-    const int64_t cnt = update_tasks(L.N, j0, j1, &t);
+    const int64_t cnt = update_tasks(L.N, j0, j1, pairs, &t);
     ctx->task_rng[key] = std::make_pair(off, cnt);
   };
   for (int64_t k0 = 0; k0 < L.N; k0 += L.nb) {
@@ -392,6 +393,7 @@ int ensure_tasks(mag_ctx* ctx, bool la) {
   ctx->tasks_N = L.N;
   ctx->tasks_nb = L.nb;
   ctx->tasks_la = (int)la;
+  ctx->tasks_pairs = (int)pairs;
   return MAG_OK;
 }
 
@@ -413,6 +415,7 @@ int ensure_maps(mag_ctx* ctx, int mode, int b) {
 struct TcFactor {
   mag_ctx* ctx;
   int mode;
+  bool pairs;
   int* launches;
   double* flops;
   int64_t next_ctr;
@@ -441,7 +444,7 @@ int tc_update(TcFactor& F, int b, int64_t k0, int kc_lo, int kc_hi, int64_t j0, 
   up.st = ctx->st();
   up.timeout_ns = 20000000000ull;
   TRY(prof_begin(ctx, cat, st));
-  CU(launch_update_tc(ctx->maps[b], up, F.mode, grid, st));
+  CU(launch_update_tc(ctx->maps[b], up, F.mode, grid, F.pairs, st));
   TRY(prof_end(ctx, st));
   ++*F.launches;
   *F.flops += update_flops(L.N, k0 + kc_lo, k0 + kc_hi, j0, j1);
@@ -484,11 +487,12 @@ int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
   cudaStream_t s = ctx->stream;
   const int64_t npanels = (L.N + L.nb - 1) / L.nb;
   const bool la = ctx->opt.lookahead != 0 && npanels > 2;
-  TRY(ensure_tasks(ctx, la));
+  const bool pairs = ctx->opt.cta_pairs != 0;
+  TRY(ensure_tasks(ctx, la, pairs));
   TRY(ensure_maps(ctx, mode, 0));
   TRY(ensure_maps(ctx, mode, 1));
   CU(cudaMemsetAsync(ctx->counters(), 0, (size_t)L.nctr * sizeof(unsigned), s));
-  TcFactor F{ctx, mode, launches, flops, 0};
+  TcFactor F{ctx, mode, pairs, launches, flops, 0};
   if (!la) {
     for (int64_t k0 = 0; k0 < L.N; k0 += L.nb) {
       const int64_t k1 = std::min<int64_t>(L.N, k0 + L.nb);
@@ -564,6 +568,8 @@ int mag_options_default(mag_options* opt) {
   opt->reuse_distances = 1;
   opt->lookahead = 1;
   opt->lookahead_sms = 0;
+  opt->cta_pairs = 0;
+  opt->reserved1 = 0;
   return MAG_OK;
 }
 

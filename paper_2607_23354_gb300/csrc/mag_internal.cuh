@@ -128,13 +128,16 @@ struct alignas(64) UpdMaps {
 };
 
 bool make_update_maps(UpdMaps* maps, const void* hi, const void* lo, int mode, int64_t cols, int64_t rows);
-// Appends the output blocks of one update (tile pairs (I, J), (I, J+1) for
-// J = j0, j0+2, ... < j1 and I in [J, N)) to `out` in 16-row x 8-pair
-// super-block order (rows of super-blocks top-down, lower triangle of the
-// super-block grid first), skipping blocks outside the trapezoid.  Returns
-// the number appended.  Requires N < 65536.
-int64_t update_tasks(int64_t N, int64_t j0, int64_t j1, std::vector<uint32_t>* out);
-cudaError_t launch_update_tc(const UpdMaps& maps, UpdParams p, int mode, int grid, cudaStream_t s);
+// Appends the output blocks of one update to `out`: tiles (I, J), (I, J+1)
+// for J = j0, j0+2, ... < j1 -- and, with `pairs` (the CTA-pair kernel),
+// also (I+1, J), (I+1, J+1) with I = j0, j0+2, ... -- for the rows I in
+// [J, N), in 16-row x 8-column-pair super-block order (rows of super-blocks
+// top-down, lower triangle of the super-block grid first), skipping blocks
+// outside the trapezoid.  Returns the number appended.  Requires N < 65536.
+int64_t update_tasks(int64_t N, int64_t j0, int64_t j1, bool pairs, std::vector<uint32_t>* out);
+// pairs: the CTA-pair (cta_group::2) kernel with a pair task table; grid is
+// rounded down to whole clusters of two CTAs.
+cudaError_t launch_update_tc(const UpdMaps& maps, UpdParams p, int mode, int grid, bool pairs, cudaStream_t s);
 
 // Panel copy of column K (tiles I in (K, N)) for the tensor-core update:
 // row (I - k0)*TILE + r, column (K - k0)*TILE + c of the row-major panel
