@@ -53,7 +53,8 @@ def parse_args():
     p.add_argument("--panel-tiles", type=int, default=0, help="factor panel width in 128-wide tiles (0 = library default)")
     p.add_argument("--lookahead", type=int, default=1, help="1: factor the next panel on a second stream")
     p.add_argument("--lookahead-sms", type=int, default=0, help="SMs kept for the panel stream (0 = library default)")
-    p.add_argument("--cta-pairs", type=int, default=0, help="1: CTA-pair (cta_group::2) tensor-core updates")
+    p.add_argument("--cta-pairs", type=int, default=2,
+                   help="CTA-pair (cta_group::2) tensor-core updates: 1 always, 0 never, 2 split precisions only")
     return p.parse_args()
 
 
@@ -179,7 +180,7 @@ def run_ours(a):
     X = workloads.unit_cube_cloud(n=a.n, m=a.m, seed=workloads.SEEDS["cube"] + rank)
     Xd = torch.from_numpy(X).to(dev)
     opts = M.Options(precision=a.precision, residual_mode=a.resid, profile=True, panel_tiles=a.panel_tiles,
-                     lookahead=bool(a.lookahead), lookahead_sms=a.lookahead_sms, cta_pairs=bool(a.cta_pairs))
+                     lookahead=bool(a.lookahead), lookahead_sms=a.lookahead_sms, cta_pairs=a.cta_pairs)
     ctx = M.Context(opts)
     dmin, bound = ctx.min_distance(Xd)
     ts = [bound if s.strip() == "bound" else float(s) for s in a.ts.split(",")]

@@ -95,10 +95,10 @@ typedef struct mag_options {
                              stream, step after step (same arithmetic)        */
   int32_t lookahead_sms;  /* SMs kept free of the trailing update for the
                              panel stream (0 = default 16)                    */
-  int32_t cta_pairs;      /* 1: tensor-core updates run on clusters
-                             of two CTAs sharing each 256 x 256 MMA
-                             (cta_group::2); 0 (default): one CTA per
-                             128 x 256 block                                  */
+  int32_t cta_pairs;      /* tensor-core updates on clusters of two CTAs
+                             sharing each 256 x 256 MMA (cta_group::2):
+                             1 always, 0 never, 2 (default) for the split
+                             precisions (FP16X3, TF32X3) only                 */
   int32_t reserved1;      /* set to 0                                          */
 } mag_options;
 

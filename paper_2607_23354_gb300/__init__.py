@@ -145,7 +145,7 @@ class Options:
     reuse_distances: bool = True
     lookahead: bool = True
     lookahead_sms: int = 0
-    cta_pairs: bool = False
+    cta_pairs: int = 2
 
     def to_c(self) -> mag_options:
         o = mag_options()

@@ -217,6 +217,55 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Bulk reduce-add of a 32 x 32 FP32 box from shared memory into global
+// memory (the L2 performs the read-modify-write), tracked by bulk groups.
+__device__ __forceinline__ void tma_reduce_add_3d(const CUtensorMap* map, uint32_t saddr, int x, int y, int z) {
+  asm volatile(
+      "cp.reduce.async.bulk.tensor.3d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+          (uint64_t)map),
+      "r"(x), "r"(y), "r"(z), "r"(saddr)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Epilogue of one accumulator for one warp: its 32 rows (TMEM lanes of the
+// warp's quadrant) of the 128 x 256 block, `nchunks` column chunks of 32
+// (4: tile J only, 8: tiles J and J+1).  Each chunk is read from TMEM,
+// scaled by -scale, written to a 4 KB staging box (row = lane, 16-byte chunks
+// XOR-swizzled by row as the 128-byte TMA swizzle expects: no bank
+// conflicts) and added to C_{Ir, J+cc/4} by the TMA; two boxes alternate.
+// Returns once the TMEM reads are done and the boxes may be reused.
+__device__ __forceinline__ void epilogue_reduce(const CUtensorMap* cmap, uint32_t tmem_addr, int64_t Ir, int64_t J,
+                                                int nchunks, int quad, int lane, float* stg, float scale) {
+  for (int cc = 0; cc < nchunks; ++cc) {
+    float* sb = stg + (cc & 1) * 1024;
+    if (cc >= 2) {
+      if (lane == 0) bulk_wait_read<1>();  // the box of chunk cc-2 has been read
+      __syncwarp();
+    }
+    float v[32];
+    tmem_ld32(tmem_addr + cc * 32, v);
+    float4* row = reinterpret_cast<float4*>(sb + lane * 32);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      row[j ^ (lane & 7)] =
+          make_float4(-scale * v[4 * j], -scale * v[4 * j + 1], -scale * v[4 * j + 2], -scale * v[4 * j + 3]);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) {
+      tma_reduce_add_3d(cmap, smem_u32(sb), (cc & 3) * 32, quad * 32, (int)tri_index(Ir, J + (cc >> 2)));
+      bulk_commit();
+    }
+  }
+  if (lane == 0) bulk_wait_read<0>();
+  __syncwarp();
+}
+
 // Task q -> output block (I, J) from the task table.
 __device__ __forceinline__ void decode_task(int64_t q, const UpdParams& p, int64_t* I, int64_t* J) {
   const uint32_t v = __ldg(p.tasks + q);
@@ -228,7 +277,7 @@ template <int MODE>
 __global__ void __launch_bounds__(UPD_THREADS, 1)
     k_update_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mB_hi,
                 const __grid_constant__ CUtensorMap mA_lo, const __grid_constant__ CUtensorMap mB_lo,
-                const UpdParams p) {
+                const __grid_constant__ CUtensorMap mC, const UpdParams p) {
   using Cfg = ModeCfg<MODE>;
   constexpr int S = stages_of<MODE>();
   constexpr int CHUNK_BYTES = Cfg::CHUNK;                  // K bytes per stage row
@@ -375,7 +424,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1)
   } else {
     // --------------------------------------------------------------- epilogue
     const int quad = warp & 3;  // TMEM lane quadrant this warp may access
-    const int row = quad * 32 + lane;
+    float* stg = reinterpret_cast<float*>(smem + S * STAGE_BYTES + (warp - 2) * 8192);
     uint32_t acc = 0, acc_phase = 0, ts = 0, tph = 0;
     for (;;) {
       if (!mbar_wait(&tq_full[ts], tph, &abort_flag, deadline)) break;
@@ -389,31 +438,18 @@ __global__ void __launch_bounds__(UPD_THREADS, 1)
       if (!mbar_wait(&tfull_bar[acc], acc_phase, &abort_flag, deadline)) break;
       tc_fence_after();
       const bool second = (J + 1 < p.j1) && (J + 1 <= I);
-      const int nchunks = second ? 8 : 4;
       // FP16 panels are stored scaled by 2^s, so products carry 2^(2s)
       constexpr float acc_scale =
           (MODE == UPD_FP16X3 || MODE == UPD_FP16) ? 1.0f / (float)(1u << (2 * FP16_SCALE_LOG2)) : 1.0f;
-      for (int cc = 0; cc < nchunks; ++cc) {
-        float v[32];
-        tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + acc * (uint32_t)B_ROWS + cc * 32, v);
-        const int64_t Jx = J + (cc >> 2);
-        float4* cp = reinterpret_cast<float4*>(p.Z + tri_index(I, Jx) * TILE_ELEMS + (int64_t)row * TILE +
-                                               (cc & 3) * 32);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          float4 c4 = cp[i];
-          c4.x -= acc_scale * v[4 * i + 0];
-          c4.y -= acc_scale * v[4 * i + 1];
-          c4.z -= acc_scale * v[4 * i + 2];
-          c4.w -= acc_scale * v[4 * i + 3];
-          cp[i] = c4;
-        }
-      }
+      epilogue_reduce(&mC, tmem_base + ((uint32_t)(quad * 32) << 16) + acc * (uint32_t)B_ROWS, I, J, second ? 8 : 4,
+                      quad, lane, stg, acc_scale);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty_bar[acc]);
       if (++acc == 2) acc = 0, acc_phase ^= 1u;
     }
+    if (lane == 0) bulk_wait_all();  // reduce-adds complete before the CTA ends
+    __syncwarp();
   }
 
   tc_fence_before();
@@ -529,13 +565,13 @@ template <int MODE>
 constexpr int stages2_of() {
   return ModeCfg<MODE>::SPLIT ? 3 : 6;
 }
-constexpr uint32_t TMEM_COLS2 = 256;  // one 128 x 256 FP32 accumulator per CTA
+constexpr uint32_t TMEM_COLS2 = 512;  // two 128 x 256 FP32 accumulators per CTA
 constexpr int NACC2 = (int)(TMEM_COLS2 / 256);
 
 template <int MODE>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
     k_update_tc2(const __grid_constant__ CUtensorMap m_hi, const __grid_constant__ CUtensorMap m_lo,
-                 const UpdParams p) {
+                 const __grid_constant__ CUtensorMap mC, const UpdParams p) {
   using Cfg = ModeCfg<MODE>;
   constexpr int S = stages2_of<MODE>();
   constexpr int CHUNK_BYTES = Cfg::CHUNK;
@@ -589,7 +625,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem_base = tmem_base_sh;
   const uint64_t deadline = globaltimer() + p.timeout_ns;
-  // both CTAs must hold the accumulator at the same TMEM address
+  // both CTAs must hold the accumulator at the same TMEM address; after an
+  // earlier launch gave up waiting, this one does no work either
   if (threadIdx.x == 0) {
     const uint32_t peer = map_to_rank(smem_u32(&tmem_base_sh), rank ^ 1u);
     uint32_t other;
@@ -598,8 +635,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
       abort_flag = 1;
       atomicOr(&p.st->flags, ST_TIMEOUT);
     }
+    if (*(volatile int*)&p.st->flags & ST_TIMEOUT) abort_flag = 1;
   }
-  __syncthreads();
+  cluster_sync_all();  // both decisions made; the pair works only if both CTAs will
+  if (threadIdx.x == 0) {
+    int other;
+    asm volatile("ld.shared::cluster.s32 %0, [%1];"
+                 : "=r"(other)
+                 : "r"(map_to_rank(smem_u32(&abort_flag), rank ^ 1u))
+                 : "memory");
+    if (other) abort_flag = 1;
+  }
+  cluster_sync_all();  // the peer has read this CTA's flag before it can change
   const bool run = abort_flag == 0;
   const int chunk_lo = p.kc_lo * (TILE * Cfg::ELEM / CHUNK_BYTES);
   const int chunk_hi = p.kc_hi * (TILE * Cfg::ELEM / CHUNK_BYTES);
@@ -734,7 +781,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
   } else if (run) {
     // --------------------------------------------------------------- epilogue
     const int quad = warp & 3;
-    const int row = quad * 32 + lane;
+    float* stg = reinterpret_cast<float*>(smem + S * STAGE_BYTES + (warp - 2) * 8192);
     uint32_t acc = 0, acc_phase = 0, ts = 0, tph = 0;
     constexpr float acc_scale =
         (MODE == UPD_FP16X3 || MODE == UPD_FP16) ? 1.0f / (float)(1u << (2 * FP16_SCALE_LOG2)) : 1.0f;
@@ -756,23 +803,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
       if (!mbar_wait_cluster(&tfull_bar[acc], acc_phase, &abort_flag, deadline)) break;
       tc_fence_after();
       if (Ir < p.N) {
-        for (int cc = 0; cc < 8; ++cc) {
-          const int64_t Jx = J + (cc >> 2);
-          if (Jx >= p.j1 || Jx > Ir) break;  // the second column tile is outside the trapezoid
-          float v[32];
-          tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + acc * 256u + cc * 32, v);
-          float4* cp = reinterpret_cast<float4*>(p.Z + tri_index(Ir, Jx) * TILE_ELEMS + (int64_t)row * TILE +
-                                                 (cc & 3) * 32);
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            float4 c4 = cp[i];
-            c4.x -= acc_scale * v[4 * i + 0];
-            c4.y -= acc_scale * v[4 * i + 1];
-            c4.z -= acc_scale * v[4 * i + 2];
-            c4.w -= acc_scale * v[4 * i + 3];
-            cp[i] = c4;
-          }
-        }
+        // tile (Ir, J) is always in the trapezoid; (Ir, J+1) only below j1 and the diagonal
+        const int nchunks = (J + 1 < p.j1 && J + 1 <= Ir) ? 8 : 4;
+        epilogue_reduce(&mC, tmem_base + ((uint32_t)(quad * 32) << 16) + acc * 256u, Ir, J, nchunks, quad, lane,
+                        stg, acc_scale);
       }
       tc_fence_before();
       __syncwarp();
@@ -784,6 +818,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
       }
       if (++acc == NACC2) acc = 0, acc_phase ^= 1u;
     }
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
   }
 
   tc_fence_before();
@@ -835,32 +871,36 @@ bool encode_2d(CUtensorMap* m, const void* base, int mode, int64_t cols, int64_t
   return r == CUDA_SUCCESS;
 }
 
+constexpr size_t EPI_STAGING = 4 * 8192;  // two 4 KB boxes per epilogue warp
+
 template <int MODE>
-cudaError_t launch_mode(const UpdMaps& maps, const UpdParams& p, int grid, cudaStream_t s) {
+cudaError_t launch_mode(const UpdMaps& maps, const CMap& cmap, const UpdParams& p, int grid, cudaStream_t s) {
   constexpr int OPS = ModeCfg<MODE>::SPLIT ? 2 : 1;
   constexpr int CH = ModeCfg<MODE>::CHUNK;
-  const size_t smem = (size_t)stages_of<MODE>() * OPS * (A_ROWS + B_ROWS) * CH + 1024;
+  const size_t smem = (size_t)stages_of<MODE>() * OPS * (A_ROWS + B_ROWS) * CH + EPI_STAGING + 1024;
   auto kern = k_update_tc<MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(maps.m);
-  kern<<<grid, UPD_THREADS, smem, s>>>(m[0], m[1], m[2], m[3], p);
+  const CUtensorMap* c = reinterpret_cast<const CUtensorMap*>(cmap.m);
+  kern<<<grid, UPD_THREADS, smem, s>>>(m[0], m[1], m[2], m[3], *c, p);
   note_launch();
   return cudaGetLastError();
 }
 
 template <int MODE>
-cudaError_t launch_mode2(const UpdMaps& maps, const UpdParams& p, int grid, cudaStream_t s) {
+cudaError_t launch_mode2(const UpdMaps& maps, const CMap& cmap, const UpdParams& p, int grid, cudaStream_t s) {
   constexpr int OPS = ModeCfg<MODE>::SPLIT ? 2 : 1;
   constexpr int CH = ModeCfg<MODE>::CHUNK;
-  const size_t smem = (size_t)stages2_of<MODE>() * OPS * 2 * 128 * CH + 1024;
+  const size_t smem = (size_t)stages2_of<MODE>() * OPS * 2 * 128 * CH + EPI_STAGING + 1024;
   auto kern = k_update_tc2<MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(maps.m);
   grid &= ~1;  // whole clusters
   if (grid < 2) grid = 2;
-  kern<<<grid, UPD_THREADS, smem, s>>>(m[0], m[2], p);
+  const CUtensorMap* c = reinterpret_cast<const CUtensorMap*>(cmap.m);
+  kern<<<grid, UPD_THREADS, smem, s>>>(m[0], m[2], *c, p);
   note_launch();
   return cudaGetLastError();
 }
@@ -877,6 +917,19 @@ bool make_update_maps(UpdMaps* maps, const void* hi, const void* lo, int mode, i
   if (!encode_2d(&m[2], l, mode, cols, rows, A_ROWS)) return false;
   if (!encode_2d(&m[3], l, mode, cols, rows, B_ROWS)) return false;
   return true;
+}
+
+bool make_c_map(CMap* map, float* Z, int64_t tiles) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc || tiles < 1 || tiles > 0x7fffffffLL) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)TILE, (cuuint64_t)TILE, (cuuint64_t)tiles};
+  cuuint64_t strides[2] = {(cuuint64_t)TILE * sizeof(float), (cuuint64_t)TILE_ELEMS * sizeof(float)};
+  cuuint32_t box[3] = {32, 32, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(reinterpret_cast<CUtensorMap*>(map->m), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, Z, dims, strides, box,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 int64_t update_tasks(int64_t N, int64_t j0, int64_t j1, bool pairs, std::vector<uint32_t>* out) {
@@ -905,26 +958,27 @@ int64_t update_tasks(int64_t N, int64_t j0, int64_t j1, bool pairs, std::vector<
   return (int64_t)(out->size() - before);
 }
 
-cudaError_t launch_update_tc(const UpdMaps& maps, UpdParams p, int mode, int grid, bool pairs, cudaStream_t s) {
+cudaError_t launch_update_tc(const UpdMaps& maps, const CMap& cmap, UpdParams p, int mode, int grid, bool pairs,
+                             cudaStream_t s) {
   if (p.ntasks <= 0 || p.kc_hi <= p.kc_lo) return cudaSuccess;
   if (pairs) {
     if ((int64_t)grid > 2 * p.ntasks) grid = (int)(2 * p.ntasks);
     switch (mode) {
-      case UPD_TF32X3: return launch_mode2<UPD_TF32X3>(maps, p, grid, s);
-      case UPD_TF32: return launch_mode2<UPD_TF32>(maps, p, grid, s);
-      case UPD_BF16: return launch_mode2<UPD_BF16>(maps, p, grid, s);
-      case UPD_FP16X3: return launch_mode2<UPD_FP16X3>(maps, p, grid, s);
-      case UPD_FP16: return launch_mode2<UPD_FP16>(maps, p, grid, s);
+      case UPD_TF32X3: return launch_mode2<UPD_TF32X3>(maps, cmap, p, grid, s);
+      case UPD_TF32: return launch_mode2<UPD_TF32>(maps, cmap, p, grid, s);
+      case UPD_BF16: return launch_mode2<UPD_BF16>(maps, cmap, p, grid, s);
+      case UPD_FP16X3: return launch_mode2<UPD_FP16X3>(maps, cmap, p, grid, s);
+      case UPD_FP16: return launch_mode2<UPD_FP16>(maps, cmap, p, grid, s);
       default: return cudaErrorInvalidValue;
     }
   }
   if ((int64_t)grid > p.ntasks) grid = (int)p.ntasks;
   switch (mode) {
-    case UPD_TF32X3: return launch_mode<UPD_TF32X3>(maps, p, grid, s);
-    case UPD_TF32: return launch_mode<UPD_TF32>(maps, p, grid, s);
-    case UPD_BF16: return launch_mode<UPD_BF16>(maps, p, grid, s);
-    case UPD_FP16X3: return launch_mode<UPD_FP16X3>(maps, p, grid, s);
-    case UPD_FP16: return launch_mode<UPD_FP16>(maps, p, grid, s);
+    case UPD_TF32X3: return launch_mode<UPD_TF32X3>(maps, cmap, p, grid, s);
+    case UPD_TF32: return launch_mode<UPD_TF32>(maps, cmap, p, grid, s);
+    case UPD_BF16: return launch_mode<UPD_BF16>(maps, cmap, p, grid, s);
+    case UPD_FP16X3: return launch_mode<UPD_FP16X3>(maps, cmap, p, grid, s);
+    case UPD_FP16: return launch_mode<UPD_FP16>(maps, cmap, p, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

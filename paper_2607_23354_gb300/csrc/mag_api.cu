@@ -78,6 +78,9 @@ struct mag_ctx {
   const void* maps_base[2] = {nullptr, nullptr};
   int maps_mode[2] = {-1, -1};
   int64_t maps_W[2] = {0, 0}, maps_np[2] = {0, 0};
+  CMap cmap;                         // TMA descriptor of the FP32 tiles (update epilogue)
+  const void* cmap_base = nullptr;
+  int64_t cmap_tiles = 0;
   uint32_t* tasks_d = nullptr;       // task tables of the update launches of one factor
   size_t tasks_cap = 0;
   int64_t tasks_N = -1;
@@ -444,7 +447,7 @@ int tc_update(TcFactor& F, int b, int64_t k0, int kc_lo, int kc_hi, int64_t j0, 
   up.st = ctx->st();
   up.timeout_ns = 20000000000ull;
   TRY(prof_begin(ctx, cat, st));
-  CU(launch_update_tc(ctx->maps[b], up, F.mode, grid, F.pairs, st));
+  CU(launch_update_tc(ctx->maps[b], ctx->cmap, up, F.mode, grid, F.pairs, st));
   TRY(prof_end(ctx, st));
   ++*F.launches;
   *F.flops += update_flops(L.N, k0 + kc_lo, k0 + kc_hi, j0, j1);
@@ -487,10 +490,17 @@ int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
   cudaStream_t s = ctx->stream;
   const int64_t npanels = (L.N + L.nb - 1) / L.nb;
   const bool la = ctx->opt.lookahead != 0 && npanels > 2;
-  const bool pairs = ctx->opt.cta_pairs != 0;
+  const bool split = mode == UPD_FP16X3 || mode == UPD_TF32X3;
+  const bool pairs = ctx->opt.cta_pairs == 1 || (ctx->opt.cta_pairs == 2 && split);
   TRY(ensure_tasks(ctx, la, pairs));
   TRY(ensure_maps(ctx, mode, 0));
   TRY(ensure_maps(ctx, mode, 1));
+  if (ctx->cmap_base != ctx->zf() || ctx->cmap_tiles != L.tiles) {
+    if (!make_c_map(&ctx->cmap, ctx->zf(), L.tiles))
+      return fail(ctx, MAG_ECUDA, "cuTensorMapEncodeTiled failed for the factor tiles");
+    ctx->cmap_base = ctx->zf();
+    ctx->cmap_tiles = L.tiles;
+  }
   CU(cudaMemsetAsync(ctx->counters(), 0, (size_t)L.nctr * sizeof(unsigned), s));
   TcFactor F{ctx, mode, pairs, launches, flops, 0};
   if (!la) {
@@ -568,7 +578,7 @@ int mag_options_default(mag_options* opt) {
   opt->reuse_distances = 1;
   opt->lookahead = 1;
   opt->lookahead_sms = 0;
-  opt->cta_pairs = 0;
+  opt->cta_pairs = 2;
   opt->reserved1 = 0;
   return MAG_OK;
 }

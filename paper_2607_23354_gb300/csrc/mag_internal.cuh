@@ -128,6 +128,14 @@ struct alignas(64) UpdMaps {
 };
 
 bool make_update_maps(UpdMaps* maps, const void* hi, const void* lo, int mode, int64_t cols, int64_t rows);
+
+// TMA descriptor of the packed FP32 tiles Z seen as [tiles][128][128] with
+// 32 x 32 boxes and the 128-byte swizzle: the target of the update
+// epilogue's bulk reduce-add C += (-acc).
+struct alignas(64) CMap {
+  unsigned char m[128];
+};
+bool make_c_map(CMap* map, float* Z, int64_t tiles);
 // Appends the output blocks of one update to `out`: tiles (I, J), (I, J+1)
 // for J = j0, j0+2, ... < j1 -- and, with `pairs` (the CTA-pair kernel),
 // also (I+1, J), (I+1, J+1) with I = j0, j0+2, ... -- for the rows I in
@@ -137,7 +145,8 @@ bool make_update_maps(UpdMaps* maps, const void* hi, const void* lo, int mode, i
 int64_t update_tasks(int64_t N, int64_t j0, int64_t j1, bool pairs, std::vector<uint32_t>* out);
 // pairs: the CTA-pair (cta_group::2) kernel with a pair task table; grid is
 // rounded down to whole clusters of two CTAs.
-cudaError_t launch_update_tc(const UpdMaps& maps, UpdParams p, int mode, int grid, bool pairs, cudaStream_t s);
+cudaError_t launch_update_tc(const UpdMaps& maps, const CMap& cmap, UpdParams p, int mode, int grid, bool pairs,
+                             cudaStream_t s);
 
 // Panel copy of column K (tiles I in (K, N)) for the tensor-core update:
 // row (I - k0)*TILE + r, column (K - k0)*TILE + c of the row-major panel

@@ -121,7 +121,7 @@ def test_cholesky_tensor_core_normwise(ctx, prec, tol, n):
 
 @pytest.mark.parametrize("prec", ["tf32x3", "fp16x3", "fp16"])
 @pytest.mark.parametrize("n,panel,sms", [(3300, 8, 16), (3300, 2, 1), (5000, 4, 40), (2500, 3, 150)])
-def test_lookahead_factor_is_bitwise_the_serial_factor(prec, n, panel, sms):
+def test_lookahead_and_cta_pairs_give_bitwise_the_serial_factor(prec, n, panel, sms):
     # the look-ahead schedule applies the same products to every tile in the
     # same order as the one-stream schedule, so the factors agree exactly
     if not torch.cuda.is_available():
@@ -132,6 +132,12 @@ def test_lookahead_factor_is_bitwise_the_serial_factor(prec, n, panel, sms):
     Ls = M.Context(M.Options(lookahead=False, **base)).cholesky_factor(X, 1.5, prec)
     assert torch.equal(La, Ls)
     assert torch.isfinite(La).all()
+    # the CTA-pair kernel (one M=256 MMA per K step over two SMs) forms the
+    # same products per output tile in the same order
+    for la in (True, False):
+        Lp = M.Context(M.Options(lookahead=la, cta_pairs=True, **base)).cholesky_factor(X, 1.5, prec)
+        Lq = M.Context(M.Options(lookahead=la, cta_pairs=False, **base)).cholesky_factor(X, 1.5, prec)
+        assert torch.equal(Lp, Lq)
 
 
 def test_cholesky_bf16_well_conditioned(ctx):
