@@ -53,7 +53,7 @@ def parse_args():
     p.add_argument("--panel-tiles", type=int, default=0, help="factor panel width in 128-wide tiles (0 = library default)")
     p.add_argument("--lookahead", type=int, default=1, help="1: factor the next panel on a second stream")
     p.add_argument("--lookahead-sms", type=int, default=0, help="SMs kept for the panel stream (0 = library default)")
-    p.add_argument("--cta-pairs", type=int, default=2,
+    p.add_argument("--cta-pairs", type=int, default=1,
                    help="CTA-pair (cta_group::2) tensor-core updates: 1 always, 0 never, 2 split precisions only")
     return p.parse_args()
 

@@ -81,7 +81,7 @@ typedef struct mag_options {
   int32_t ir_max_iters;   /* refinement steps before escalating, default 12     */
   int32_t gmres_max_iters;/* inner GMRES iterations of GMRES-IR, default 30     */
   int32_t allow_fallback; /* 1: escalate to GMRES-IR then FP64 factor (default)  */
-  int32_t panel_tiles;    /* outer panel width in 128-wide tiles (0 = default)  */
+  int32_t panel_tiles;    /* outer panel width in 128-wide tiles (0 = 16)       */
   double workspace_limit_bytes; /* 0 = no limit; larger requests give ENOMEM     */
   int32_t profile;        /* 1: time the trailing-update kernel with CUDA events */
   int32_t reuse_distances;/* 1 (default): inside one mag_solve_multi or
@@ -97,7 +97,7 @@ typedef struct mag_options {
                              panel stream (0 = default 16)                    */
   int32_t cta_pairs;      /* tensor-core updates on clusters of two CTAs
                              sharing each 256 x 256 MMA (cta_group::2):
-                             1 always, 0 never, 2 (default) for the split
+                             1 (default) always, 0 never, 2 for the split
                              precisions (FP16X3, TF32X3) only                 */
   int32_t reserved1;      /* set to 0                                          */
 } mag_options;

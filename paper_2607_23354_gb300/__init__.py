@@ -145,7 +145,7 @@ class Options:
     reuse_distances: bool = True
     lookahead: bool = True
     lookahead_sms: int = 0
-    cta_pairs: int = 2
+    cta_pairs: int = 1
 
     def to_c(self) -> mag_options:
         o = mag_options()

@@ -154,6 +154,17 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+// The same load into this CTA's shared memory, completing on an mbarrier of
+// the peer CTA of a CTA pair (cluster address), as the pair's MMA issuer waits
+// on its own barrier for both CTAs' operands.
+__device__ __forceinline__ void tma_load_2d_peer_bar(void* dst, const CUtensorMap* map, uint32_t bar_cluster, int x,
+                                                     int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%2, "
+      "%3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar_cluster)
+      : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -586,8 +597,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  // full_bar: this CTA's own loads landed; peer_bar (rank 0): rank 1's loads landed
-  __shared__ __align__(8) uint64_t full_bar[S], peer_bar[S], empty_bar[S], tfull_bar[NACC2], tempty_bar[NACC2];
+  // full_bar (rank 0's is used): both CTAs' loads of a stage landed
+  __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], tfull_bar[NACC2], tempty_bar[NACC2];
   __shared__ __align__(8) uint64_t tq_full[TQ], tq_empty[TQ];
   __shared__ int64_t tq_val[TQ];
   __shared__ uint32_t tmem_base_sh;
@@ -598,7 +609,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full_bar[s], 1);
-      mbar_init(&peer_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
     for (int a = 0; a < NACC2; ++a) {
@@ -607,8 +617,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
     }
     for (int i = 0; i < TQ; ++i) {
       mbar_init(&tq_full[i], 1);
-      // rank 0: its MMA thread + 4 epilogue warps + rank 1's producer, forwarder, 4 epilogue warps
-      mbar_init(&tq_empty[i], 11);
+      // rank 0: its MMA thread + 4 epilogue warps + rank 1's producer and 4 epilogue warps
+      mbar_init(&tq_empty[i], 10);
     }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -653,7 +663,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
   // rank-0 addresses of the shared hand-off barriers, as seen from this CTA
   const uint32_t r0_tq_empty = map_to_rank(smem_u32(&tq_empty[0]), 0);
   const uint32_t r0_tempty = map_to_rank(smem_u32(&tempty_bar[0]), 0);
-  const uint32_t r0_peer = map_to_rank(smem_u32(&peer_bar[0]), 0);
+  const uint32_t r0_full = map_to_rank(smem_u32(&full_bar[0]), 0);
   const uint32_t r1_tq_full = map_to_rank(smem_u32(&tq_full[0]), 1);
   const uint32_t r1_tq_val = map_to_rank(smem_u32(&tq_val[0]), 1);
 
@@ -691,13 +701,24 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
             break;
           }
           unsigned char* sbase = smem + stage * STAGE_BYTES;
-          mbar_expect_tx(&full_bar[stage], STAGE_BYTES);
           const int x = c * ELEMS_PER_CHUNK;
-          tma_load_2d(sbase, &m_hi, &full_bar[stage], x, ya);
-          tma_load_2d(sbase + OFF_BHI, &m_hi, &full_bar[stage], x, yb);
-          if (Cfg::SPLIT) {
-            tma_load_2d(sbase + OFF_ALO, &m_lo, &full_bar[stage], x, ya);
-            tma_load_2d(sbase + OFF_BLO, &m_lo, &full_bar[stage], x, yb);
+          if (rank == 0) {
+            // rank 0's barrier counts the bytes of both CTAs' loads of this stage
+            mbar_expect_tx(&full_bar[stage], 2 * STAGE_BYTES);
+            tma_load_2d(sbase, &m_hi, &full_bar[stage], x, ya);
+            tma_load_2d(sbase + OFF_BHI, &m_hi, &full_bar[stage], x, yb);
+            if (Cfg::SPLIT) {
+              tma_load_2d(sbase + OFF_ALO, &m_lo, &full_bar[stage], x, ya);
+              tma_load_2d(sbase + OFF_BLO, &m_lo, &full_bar[stage], x, yb);
+            }
+          } else {
+            const uint32_t bar = r0_full + stage * 8u;
+            tma_load_2d_peer_bar(sbase, &m_hi, bar, x, ya);
+            tma_load_2d_peer_bar(sbase + OFF_BHI, &m_hi, bar, x, yb);
+            if (Cfg::SPLIT) {
+              tma_load_2d_peer_bar(sbase + OFF_ALO, &m_lo, bar, x, ya);
+              tma_load_2d_peer_bar(sbase + OFF_BLO, &m_lo, bar, x, yb);
+            }
           }
           issued[stage] = true;
           issued_parity[stage] = phase;
@@ -705,12 +726,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
         }
       }
       if (!ok || abort_flag) {
-        // wait (bounded) for this CTA's own loads in flight
+        // wait (bounded) for this CTA's loads in flight: rank 0 on its
+        // barriers; rank 1, whose loads complete on rank 0's barriers, for
+        // the same bound
         const uint64_t dl = globaltimer() + 200000000ull;
-        for (int s = 0; s < S; ++s)
-          if (issued[s])
-            while (!mbar_try_wait(&full_bar[s], issued_parity[s]) && globaltimer() < dl) {
-            }
+        bool any = false;
+        for (int s = 0; s < S; ++s) any = any || issued[s];
+        if (rank == 0) {
+          for (int s = 0; s < S; ++s)
+            if (issued[s])
+              while (!mbar_try_wait(&full_bar[s], issued_parity[s]) && globaltimer() < dl) {
+              }
+        } else if (any) {
+          while (globaltimer() < dl) {
+          }
+        }
       }
     }
   } else if (run && warp == 1) {
@@ -730,8 +760,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
           tc_fence_after();
           const uint32_t d = tmem_base + acc * 256u;
           for (int c = chunk_lo; c < chunk_hi; ++c) {
-            if (!mbar_wait(&full_bar[stage], phase, &abort_flag, deadline) ||
-                !mbar_wait_cluster(&peer_bar[stage], phase, &abort_flag, deadline)) {
+            if (!mbar_wait_cluster(&full_bar[stage], phase, &abort_flag, deadline)) {
               ok = false;
               break;
             }
@@ -756,25 +785,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
           if (!ok) break;
           mma_commit_pair(&tfull_bar[acc]);  // both halves of the accumulator ready
           if (++acc == NACC2) acc = 0, acc_phase ^= 1u;
-        }
-      } else {
-        // ------------------------------------------ forwarder (rank 1 only)
-        while (true) {
-          if (!mbar_wait_cluster(&tq_full[ts], tph, &abort_flag, deadline)) break;
-          const int64_t q = tq_val[ts];
-          mbar_arrive_remote(r0_tq_empty + ts * 8u);
-          if (++ts == TQ) ts = 0, tph ^= 1u;
-          if (q < 0) break;
-          bool ok = true;
-          for (int c = chunk_lo; c < chunk_hi; ++c) {
-            if (!mbar_wait(&full_bar[stage], phase, &abort_flag, deadline)) {
-              ok = false;
-              break;
-            }
-            mbar_arrive_remote(r0_peer + stage * 8u);
-            if (++stage == S) stage = 0, phase ^= 1u;
-          }
-          if (!ok) break;
         }
       }
     }

@@ -15,6 +15,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -178,7 +179,7 @@ Layout plan(const mag_ctx* ctx, int64_t n, bool f32, bool f64, bool dist = false
   L.dist = dist;
   L.off_dist = off;  // placed before every precision-dependent region: stable offset
   if (dist) off = align_up(off + (size_t)L.tiles * TILE_ELEMS * sizeof(double));
-  L.nb = ctx->opt.panel_tiles > 0 ? ctx->opt.panel_tiles : 8;
+  L.nb = ctx->opt.panel_tiles > 0 ? ctx->opt.panel_tiles : 16;
   L.W = (int64_t)L.nb * TILE;
   L.off_panel = off;
   // two panel buffers (hi + lo copies each): the next panel is written while
@@ -369,9 +370,17 @@ int ensure_tasks(mag_ctx* ctx, bool la, bool pairs) {
     const int64_t cnt = update_tasks(L.N, j0, j1, pairs, &t);
     ctx->task_rng[key] = std::make_pair(off, cnt);
   };
+  // the in-panel updates of the recursive panel factor (tc_panel_range)
+  std::function<void(int64_t, int64_t)> panel = [&](int64_t a, int64_t b) {
+    if (b - a <= 1) return;
+    const int64_t mid = a + (b - a) / 2;
+    panel(a, mid);
+    add(mid, b);
+    panel(mid, b);
+  };
   for (int64_t k0 = 0; k0 < L.N; k0 += L.nb) {
     const int64_t k1 = std::min<int64_t>(L.N, k0 + L.nb), k2 = std::min<int64_t>(L.N, k1 + L.nb);
-    for (int64_t K = k0; K + 1 < k1; ++K) add(K + 1, k1);
+    panel(k0, k1);
     if (la) {
       add(k1, k2);
       add(k2, L.N);
@@ -454,29 +463,41 @@ int tc_update(TcFactor& F, int b, int64_t k0, int kc_lo, int kc_hi, int64_t j0, 
   return MAG_OK;
 }
 
-// Diagonal factor + inverse, panel solve, panel copy into buffer b and the
-// in-panel updates of tile columns [k0, k1), on stream st.
-int tc_panel(TcFactor& F, int64_t k0, int b, cudaStream_t st) {
+// Tile columns [a, b) of the panel that starts at k0 (copies go to panel
+// buffer `buf`), factored recursively: the left half, then one update of the
+// right half with all columns of the left half (K = 128 (mid - a)), then the
+// right half; a single column is its diagonal factor + inverse, its panel
+// solve and its copy.  Every output tile of the panel is read and written
+// once per recursion level instead of once per earlier column.
+int tc_panel_range(TcFactor& F, int64_t k0, int64_t a, int64_t b, int buf, cudaStream_t st) {
   mag_ctx* ctx = F.ctx;
   const Layout& L = ctx->lay;
   float* Z = ctx->zf();
   float* Dinv = ctx->dinvf();
-  const int64_t k1 = std::min<int64_t>(L.N, k0 + L.nb);
-  for (int64_t K = k0; K < k1; ++K) {
+  if (b - a == 1) {
     TRY(prof_begin(ctx, PC_POTRF, st));
-    CU(launch_potrf_diag<float>(Z, Dinv, K, L.n, ctx->st(), st));
+    CU(launch_potrf_diag<float>(Z, Dinv, a, L.n, ctx->st(), st));
     TRY(prof_end(ctx, st));
     TRY(prof_begin(ctx, PC_TRSM, st));
-    CU(launch_trsm_col<float>(Z, Dinv, K, L.N, ctx->st(), st));
+    CU(launch_trsm_col<float>(Z, Dinv, a, L.N, ctx->st(), st));
     TRY(prof_end(ctx, st));
-    if (K + 1 >= L.N) continue;
-    TRY(prof_begin(ctx, PC_SPLIT, st));
-    CU(launch_split_col(Z, K, L.N, k0, L.W, F.mode, ctx->panel_hi(b), ctx->panel_lo(b), st));
-    TRY(prof_end(ctx, st));
-    if (K + 1 < k1)
-      TRY(tc_update(F, b, k0, (int)(K - k0), (int)(K - k0) + 1, K + 1, k1, ctx->sm_count, st, PC_UPDATE_PANEL));
+    if (a + 1 < L.N) {
+      TRY(prof_begin(ctx, PC_SPLIT, st));
+      CU(launch_split_col(Z, a, L.N, k0, L.W, F.mode, ctx->panel_hi(buf), ctx->panel_lo(buf), st));
+      TRY(prof_end(ctx, st));
+    }
+    return MAG_OK;
   }
-  return MAG_OK;
+  const int64_t mid = a + (b - a) / 2;
+  TRY(tc_panel_range(F, k0, a, mid, buf, st));
+  TRY(tc_update(F, buf, k0, (int)(a - k0), (int)(mid - k0), mid, b, ctx->sm_count, st, PC_UPDATE_PANEL));
+  return tc_panel_range(F, k0, mid, b, buf, st);
+}
+
+// The panel of tile columns [k0, min(N, k0 + nb)) into panel buffer b.
+int tc_panel(TcFactor& F, int64_t k0, int b, cudaStream_t st) {
+  const int64_t k1 = std::min<int64_t>(F.ctx->lay.N, k0 + F.ctx->lay.nb);
+  return tc_panel_range(F, k0, k0, k1, b, st);
 }
 
 // Two-level right-looking Cholesky with the tensor-core updates.  Without
@@ -578,7 +599,7 @@ int mag_options_default(mag_options* opt) {
   opt->reuse_distances = 1;
   opt->lookahead = 1;
   opt->lookahead_sms = 0;
-  opt->cta_pairs = 2;
+  opt->cta_pairs = 1;
   opt->reserved1 = 0;
   return MAG_OK;
 }
