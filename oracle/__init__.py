@@ -68,6 +68,7 @@ def _load():
                 "orc_solve": (i32, [P, i64, i64, d, P, i32, P, P]),
                 "orc_weighting": (i32, [P, i64, i64, d, i32, P, P]),
                 "orc_tplus": (i32, [P, i64, i64, d, d, d, i32, P, P, P, P, P]),
+                "orc_tplus_ridders": (i32, [P, i64, i64, d, d, d, i32, P, P, P, P, P]),
                 "orc_grad": (None, [P, i64, i64, d, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
@@ -203,9 +204,10 @@ def magnitude(X, t, ir_steps=2) -> float:
     return weighting(X, t, ir_steps)[1]
 
 
-def tplus(X, t_lo=1e-3, t_hi=0.0, rel_tol=1e-6, ir_steps=2):
-    """Sec. 2 cutoff by bisection.  Returns dict with t_plus, bracket, below,
-    probes, w, mag.  t_hi <= 0 uses the Sec. 1 bound."""
+def tplus(X, t_lo=1e-3, t_hi=0.0, rel_tol=1e-6, ir_steps=2, method="bisection"):
+    """Sec. 2 cutoff by bisection (default) or Ridders' method on min_j w_j(t).
+    Returns dict with t_plus, bracket, below, probes, w, mag.  t_hi <= 0 uses
+    the Sec. 1 bound."""
     X = _c(X)
     n, m = X.shape
     out = np.zeros(3)
@@ -213,9 +215,9 @@ def tplus(X, t_lo=1e-3, t_hi=0.0, rel_tol=1e-6, ir_steps=2):
     probes = ctypes.c_int(0)
     w = np.empty(n)
     mag = ctypes.c_double(0.0)
-    st = _load().orc_tplus(_p(X), n, m, float(t_lo), float(t_hi), float(rel_tol), int(ir_steps),
-                           _p(out), ctypes.byref(below), ctypes.byref(probes), _p(w),
-                           ctypes.byref(mag))
+    fn = {"bisection": _load().orc_tplus, "ridders": _load().orc_tplus_ridders}[method]
+    st = fn(_p(X), n, m, float(t_lo), float(t_hi), float(rel_tol), int(ir_steps),
+            _p(out), ctypes.byref(below), ctypes.byref(probes), _p(w), ctypes.byref(mag))
     if st:
         raise OracleError(st, "tplus")
     return {"t_plus": out[0], "bracket": (out[1], out[2]), "below": bool(below.value),

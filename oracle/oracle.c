@@ -312,6 +312,97 @@ int orc_tplus(const double* X, int64_t n, int64_t m, double t_lo, double t_hi, d
   return ORC_OK;
 }
 
+/* ---- Sec. 2 cutoff t_+ by Ridders' method (the root-finder the paper
+ * prefers for its fewer evaluations; Ridders, IEEE Trans. Circuits Syst. 26
+ * (1979)) on f(t) = min_j w_j(t), with the bracket kept on feasibility as in
+ * orc_tplus: feasible(hi) (f >= 0), not feasible(lo) (f < 0), stop when
+ * hi - lo <= rel_tol * hi, t_+ = hi.  One iteration, with f1 = f(lo),
+ * f2 = f(hi) at its start:
+ *   1. x3 = lo + (hi - lo)/2, f3 = f(x3); the bracket end of x3's class
+ *      moves to x3;
+ *   2. Ridders' point x4 = x3 + (x3 - x1) sign(f1 - f2) f3 / sqrt(f3^2 - f1 f2)
+ *      (x1 = the old lo); if it lies strictly inside the current bracket,
+ *      f4 = f(x4) and the end of x4's class moves to x4;
+ *   3. once two successive x4 agree to within delta = rel_tol * hi / 2, one
+ *      more evaluation at x4 -/+ delta (toward the other end) closes the
+ *      bracket around the converged estimate.
+ * Same outputs and errors as orc_tplus. */
+int orc_tplus_ridders(const double* X, int64_t n, int64_t m, double t_lo, double t_hi, double rel_tol,
+                      int ir_steps, double* out3, int* below, int* probes, double* w, double* mag) {
+  if (n < 2) return ORC_EINVAL;
+  double dmin = orc_min_distance(X, n, m);
+  if (!(dmin > 0.0)) return ORC_EDUPLICATE;
+  if (t_hi <= 0.0) t_hi = log((double)(n - 1)) / dmin;
+  if (!(t_lo > 0.0) || !(t_hi > t_lo)) return ORC_EINVAL;
+  double* wt = (double*)malloc((size_t)n * sizeof(double));
+  if (!wt) return ORC_ENOMEM;
+  double o[4];
+  int np = 0, st;
+  *below = 0;
+  st = orc_weighting(X, n, m, t_hi, ir_steps, w, o);
+  ++np;
+  if (st) { free(wt); return st; }
+  if (!(o[2] >= 0.0)) { free(wt); *probes = np; return ORC_ENOBRACKET; }
+  *mag = o[0];
+  double fhi = o[2];
+  st = orc_weighting(X, n, m, t_lo, ir_steps, wt, o);
+  ++np;
+  if (st) { free(wt); return st; }
+  double lo = t_lo, hi = t_hi, flo = o[2];
+  /* evaluate f at t and move the bracket end of t's class there */
+#define ORC_PROBE(tt, fout)                                     \
+  do {                                                          \
+    st = orc_weighting(X, n, m, (tt), ir_steps, wt, o);         \
+    ++np;                                                       \
+    if (st) { free(wt); return st; }                            \
+    (fout) = o[2];                                              \
+    if (o[2] >= 0.0) {                                          \
+      hi = (tt); fhi = o[2];                                    \
+      memcpy(w, wt, (size_t)n * sizeof(double));                \
+      *mag = o[0];                                              \
+    } else {                                                    \
+      lo = (tt); flo = o[2];                                    \
+    }                                                           \
+  } while (0)
+  if (flo >= 0.0) {
+    *below = 1;
+    hi = t_lo;
+    memcpy(w, wt, (size_t)n * sizeof(double));
+    *mag = o[0];
+  } else {
+    double prev_x4 = NAN;
+    while (hi - lo > rel_tol * hi) {
+      const double x1 = lo, f1 = flo, f2 = fhi;
+      const double x3 = lo + (hi - lo) / 2.0;
+      double f3, f4;
+      ORC_PROBE(x3, f3);
+      if (hi - lo <= rel_tol * hi) break;
+      const double sq = sqrt(f3 * f3 - f1 * f2);
+      if (!(sq > 0.0)) continue;
+      const double x4 = x3 + (x3 - x1) * (f1 >= f2 ? 1.0 : -1.0) * f3 / sq;
+      if (!(x4 > lo && x4 < hi)) { prev_x4 = NAN; continue; }
+      ORC_PROBE(x4, f4);
+      (void)f4;
+      if (hi - lo <= rel_tol * hi) break;
+      const double delta = 0.5 * rel_tol * hi;
+      if (fabs(x4 - prev_x4) <= delta) {
+        const double xc = (hi == x4) ? x4 - delta : x4 + delta;
+        if (xc > lo && xc < hi) {
+          double fc;
+          ORC_PROBE(xc, fc);
+          (void)fc;
+        }
+      }
+      prev_x4 = x4;
+    }
+  }
+#undef ORC_PROBE
+  if (out3) { out3[0] = hi; out3[1] = lo; out3[2] = hi; }
+  *probes = np;
+  free(wt);
+  return ORC_OK;
+}
+
 /* ---- gradients by implicit differentiation of Zw = 1 ----
  * For a loss L(w) with g = dL/dw and lambda = Z^{-1} g:
  *   dL = -lambda^T (dZ) w,

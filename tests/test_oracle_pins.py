@@ -312,6 +312,49 @@ def test_tplus_no_bracket():
     assert e.value.status == oracle.ENOBRACKET
 
 
+def test_tplus_ridders_regular_polygon_root():
+    # Ridders' method (the paper's preferred root-finder) on min_j w_j(t):
+    # the same bracket invariant and width, fewer solves than bisection
+    k = 12
+    X = _kgon(k)
+    root = brentq(lambda t: _kgon_S(t, k) - k * math.exp(-t), 0.2, 20.0, xtol=1e-15, rtol=1e-15)
+    r = oracle.tplus(X, 1e-3, 0.0, 1e-6, method="ridders")
+    lo, hi = r["bracket"]
+    assert lo <= root + 1e-12 and root - 1e-12 <= hi
+    assert hi - lo <= 1e-6 * hi
+    assert not r["below"] and r["w"].min() >= 0
+    assert r["probes"] < oracle.tplus(X, 1e-3, 0.0, 1e-6)["probes"]
+
+
+def test_tplus_ridders_exact_scaling_law():
+    # t and d enter only as t d, and every step of the protocol scales exactly by 2
+    X = np.random.default_rng(19).standard_normal((90, 3))
+    r1 = oracle.tplus(X, 1e-3, 0.0, 1e-6, method="ridders")
+    r2 = oracle.tplus(2.0 * X, 0.5e-3, oracle.tplus_bound(X) / 2, 1e-6, method="ridders")
+    assert r2["t_plus"] == r1["t_plus"] / 2
+    assert r2["probes"] == r1["probes"]
+
+
+@pytest.mark.parametrize("seed", [31, 32, 33])
+def test_tplus_ridders_agrees_with_bisection(seed):
+    X = np.random.default_rng(seed).standard_normal((120, 4))
+    rb = oracle.tplus(X, 1e-3, 0.0, 1e-6)
+    rr = oracle.tplus(X, 1e-3, 0.0, 1e-6, method="ridders")
+    # both brackets hold the sign change and are at most 1e-6 wide
+    assert abs(rr["t_plus"] - rb["t_plus"]) <= 1e-6 * rb["t_plus"]
+    assert max(rr["bracket"][0], rb["bracket"][0]) <= min(rr["bracket"][1], rb["bracket"][1])
+    assert rr["probes"] <= rb["probes"]
+
+
+def test_tplus_ridders_edge_cases():
+    X, _, _ = _collinear(30, 3, seed=20)
+    r = oracle.tplus(X, 1e-3, 0.0, 1e-6, method="ridders")
+    assert r["below"] and r["t_plus"] == 1e-3 and r["probes"] == 2
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.tplus(_kgon(12), 1e-3, 1.0, 1e-6, method="ridders")
+    assert e.value.status == oracle.ENOBRACKET
+
+
 def test_tplus_rejects_duplicates():
     X = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 0.0]])
     with pytest.raises(oracle.OracleError) as e:
