@@ -53,6 +53,9 @@ def parse_args():
     p.add_argument("--panel-tiles", type=int, default=0, help="factor panel width in 128-wide tiles (0 = library default)")
     p.add_argument("--lookahead", type=int, default=1, help="1: factor the next panel on a second stream")
     p.add_argument("--lookahead-sms", type=int, default=0, help="SMs kept for the panel stream (0 = library default)")
+    p.add_argument("--paper-sweep", action="store_true",
+                   help="instead of the headline step: the paper's runtime workload (t_+ and w(t_+) for "
+                        "n in 1e3..3e4, m in 3..100, two covariances, 3 runs) with bisection and Ridders")
     p.add_argument("--cta-pairs", type=int, default=1,
                    help="CTA-pair (cta_group::2) tensor-core updates: 1 always, 0 never, 2 split precisions only")
     return p.parse_args()
@@ -433,8 +436,49 @@ def run_reference(a):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_paper_sweep(a):
+    """The paper's runtime workload: for every (n, m, covariance, run) the
+    cutoff t_+ on [1e-3, bound] (rel. width 1e-6) and the weighting there, by
+    bisection and by Ridders' method; wall time per sweep on one GPU."""
+    import torch
+
+    import paper_2607_23354_gb300 as M
+    import workloads
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    ctx = M.Context(M.Options(precision=a.precision, residual_mode=a.resid))
+    # warm-up: library load, workspace, task tables
+    ctx.sweep_tplus(torch.from_numpy(workloads.paper_runtime_cloud(1000, 3)).cuda(), 1e-3, 0.0, 1e-6)
+    rows = []
+    units = [(n, m, c, r) for n in workloads.PAPER_RUNTIME_NS for m in workloads.PAPER_RUNTIME_MS
+             for c in workloads.PAPER_RUNTIME_COVS for r in range(3)]
+    for i, (n, m, c, r) in enumerate(units):
+        if i % world != rank:
+            continue
+        Xd = torch.from_numpy(workloads.paper_runtime_cloud(n, m, c, r)).cuda()
+        for method in ("bisection", "ridders"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            try:
+                res = ctx.sweep_tplus(Xd, 1e-3, 0.0, 1e-6, method=method)
+                torch.cuda.synchronize()
+                rows.append({"n": n, "m": m, "cov": c, "run": r, "method": method,
+                             "seconds": time.perf_counter() - t0, "t_plus": res["t_plus"],
+                             "bracket": list(res["bracket"]), "below": res["below"],
+                             "probes": res["probes"], "mag": res["mag"],
+                             "rel_residual": res["info"]["rel_residual"]})
+            except M.MagnitudeError as e:
+                rows.append({"n": n, "m": m, "cov": c, "run": r, "method": method, "status": e.status,
+                             "error": str(e)[:160]})
+    return {"metric": "paper runtime workload: t_+ and w(t_+) per point cloud", "unit": "s",
+            "n_gpus": world, "rank": rank, "data": "synthetic", "rows": rows}
+
+
 def main():
     a = parse_args()
+    if a.paper_sweep:
+        print(json.dumps(run_paper_sweep(a)), flush=True)
+        return
     if a.impl == "reference":
         out = run_reference(a)
         if out is not None:

@@ -99,7 +99,8 @@ typedef struct mag_options {
                              sharing each 256 x 256 MMA (cta_group::2):
                              1 (default) always, 0 never, 2 for the split
                              precisions (FP16X3, TF32X3) only                 */
-  int32_t reserved1;      /* set to 0                                          */
+  int32_t tplus_method;   /* mag_sweep_tplus root-finder on min_j w_j(t):
+                             0 (default) bisection, 1 Ridders' method        */
 } mag_options;
 
 /* Diagnostics of one call (all fields written when info != NULL). */

@@ -14,6 +14,7 @@ the magnitude is 1^T w, and the cutoff t_+ is the least t with w >= 0.
 from __future__ import annotations
 
 import ctypes
+import dataclasses
 import os
 import threading
 from dataclasses import dataclass, fields
@@ -43,7 +44,7 @@ class mag_options(ctypes.Structure):
                 ("panel_tiles", ctypes.c_int32), ("workspace_limit_bytes", ctypes.c_double),
                 ("profile", ctypes.c_int32), ("reuse_distances", ctypes.c_int32),
                 ("lookahead", ctypes.c_int32), ("lookahead_sms", ctypes.c_int32),
-                ("cta_pairs", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+                ("cta_pairs", ctypes.c_int32), ("tplus_method", ctypes.c_int32)]
 
 
 class mag_info(ctypes.Structure):
@@ -146,6 +147,7 @@ class Options:
     lookahead: bool = True
     lookahead_sms: int = 0
     cta_pairs: int = 1
+    tplus_method: str = "bisection"
 
     def to_c(self) -> mag_options:
         o = mag_options()
@@ -164,6 +166,7 @@ class Options:
         o.lookahead = int(self.lookahead)
         o.lookahead_sms = int(self.lookahead_sms)
         o.cta_pairs = int(self.cta_pairs)
+        o.tplus_method = {"bisection": 0, "ridders": 1}[self.tplus_method]
         return o
 
 
@@ -299,17 +302,27 @@ class Context:
                                            _P(0) if r is None else _P(r.data_ptr()), ctypes.cast(nr, _DP)))
         return r, {"rel_residual": nr[0], "r_norm_inf": nr[1], "z_norm_inf": nr[2], "w_norm_inf": nr[3]}
 
-    def sweep_tplus(self, X: torch.Tensor, t_lo: float = 1e-3, t_hi: float = 0.0, rel_tol: float = 1e-6):
+    def sweep_tplus(self, X: torch.Tensor, t_lo: float = 1e-3, t_hi: float = 0.0, rel_tol: float = 1e-6,
+                    method: str | None = None):
+        """Sec. 2 cutoff t_+ (feasible end of a bracket at most rel_tol wide).
+        method: "bisection" or "ridders" (default: the context's options)."""
         X = self._points(X)
         n, m = X.shape
         w = torch.empty(n, dtype=torch.float64, device=self.device)
         tp, mag = ctypes.c_double(0.0), ctypes.c_double(0.0)
         br = (ctypes.c_double * 2)()
         info = mag_info()
-        self._check(self._lib.mag_sweep_tplus(self._h, _P(X.data_ptr()), n, m, float(t_lo), float(t_hi),
-                                              float(rel_tol), ctypes.byref(tp),
-                                              ctypes.cast(br, _DP), _P(w.data_ptr()),
-                                              ctypes.byref(mag), ctypes.byref(info)))
+        saved = self.options
+        if method is not None and method != saved.tplus_method:
+            self.set_options(dataclasses.replace(saved, tplus_method=method))
+        try:
+            self._check(self._lib.mag_sweep_tplus(self._h, _P(X.data_ptr()), n, m, float(t_lo), float(t_hi),
+                                                  float(rel_tol), ctypes.byref(tp),
+                                                  ctypes.cast(br, _DP), _P(w.data_ptr()),
+                                                  ctypes.byref(mag), ctypes.byref(info)))
+        finally:
+            if self.options is not saved:
+                self.set_options(saved)
         d = info.as_dict()
         return {"t_plus": tp.value, "bracket": (br[0], br[1]), "w": w, "mag": mag.value,
                 "below": bool(d["below_bracket"]), "probes": d["probes"], "info": d}
@@ -407,8 +420,9 @@ def solve(X, t, options: Options | None = None):
     return w, mag
 
 
-def sweep_tplus(X, t_lo=1e-3, t_hi=0.0, rel_tol=1e-6, options: Options | None = None):
-    return default_context(options).sweep_tplus(X, t_lo, t_hi, rel_tol)
+def sweep_tplus(X, t_lo=1e-3, t_hi=0.0, rel_tol=1e-6, options: Options | None = None,
+                method: str | None = None):
+    return default_context(options).sweep_tplus(X, t_lo, t_hi, rel_tol, method=method)
 
 
 class MagnitudeFn(torch.autograd.Function):

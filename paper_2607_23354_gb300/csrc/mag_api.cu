@@ -600,7 +600,7 @@ int mag_options_default(mag_options* opt) {
   opt->lookahead = 1;
   opt->lookahead_sms = 0;
   opt->cta_pairs = 1;
-  opt->reserved1 = 0;
+  opt->tplus_method = 0;
   return MAG_OK;
 }
 
@@ -1283,6 +1283,7 @@ int mag_sweep_tplus(mag_ctx* ctx, const double* points, int64_t n, int32_t m, do
     *feas = pi.min_w >= 0.0;
     return MAG_OK;
   };
+  const bool ridders = ctx->opt.tplus_method == 1;
   bool feas = false;
   TRY(probe(t_hi, &feas));
   if (!feas) {
@@ -1302,7 +1303,7 @@ int mag_sweep_tplus(mag_ctx* ctx, const double* points, int64_t n, int32_t m, do
     CU(cudaMemcpyAsync(w, wp, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     mag_hi = pm;
     info_hi = pi;
-  } else {
+  } else if (!ridders) {
     while (hi - lo > rel_tol * hi) {
       const double mid = lo + (hi - lo) / 2.0;
       TRY(probe(mid, &feas));
@@ -1314,6 +1315,54 @@ int mag_sweep_tplus(mag_ctx* ctx, const double* points, int64_t n, int32_t m, do
       } else {
         lo = mid;
       }
+    }
+  } else {
+    // Ridders' method (Ridders, IEEE Trans. Circuits Syst. 26 (1979)) on
+    // f(t) = min_j w_j(t) with the bracket kept on feasibility: each
+    // iteration evaluates the midpoint x3, then Ridders' point
+    // x4 = x3 + (x3 - x1) sign(f1 - f2) f3 / sqrt(f3^2 - f1 f2) when it lies
+    // inside the bracket; once two successive x4 agree to within
+    // delta = rel_tol hi / 2, one evaluation at x4 -/+ delta closes the
+    // bracket.  Every evaluation moves the bracket end of its class.
+    double flo = pi.min_w, fhi = info_hi.min_w;
+    auto eval = [&](double t, double* f) -> int {
+      TRY(probe(t, &feas));
+      *f = pi.min_w;
+      if (feas) {
+        hi = t;
+        fhi = pi.min_w;
+        CU(cudaMemcpyAsync(w, wp, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        mag_hi = pm;
+        info_hi = pi;
+      } else {
+        lo = t;
+        flo = pi.min_w;
+      }
+      return MAG_OK;
+    };
+    double prev_x4 = NAN;
+    while (hi - lo > rel_tol * hi) {
+      const double x1 = lo, f1 = flo, f2 = fhi;
+      const double x3 = lo + (hi - lo) / 2.0;
+      double f3 = 0, f4 = 0;
+      TRY(eval(x3, &f3));
+      if (hi - lo <= rel_tol * hi) break;
+      const double sq = std::sqrt(f3 * f3 - f1 * f2);
+      if (!(sq > 0.0)) continue;
+      const double x4 = x3 + (x3 - x1) * (f1 >= f2 ? 1.0 : -1.0) * f3 / sq;
+      if (!(x4 > lo && x4 < hi)) {
+        prev_x4 = NAN;
+        continue;
+      }
+      TRY(eval(x4, &f4));
+      if (hi - lo <= rel_tol * hi) break;
+      const double delta = 0.5 * rel_tol * hi;
+      if (std::fabs(x4 - prev_x4) <= delta) {
+        const double xc = (hi == x4) ? x4 - delta : x4 + delta;
+        double fc = 0;
+        if (xc > lo && xc < hi) TRY(eval(xc, &fc));
+      }
+      prev_x4 = x4;
     }
   }
   CU(cudaStreamSynchronize(s));

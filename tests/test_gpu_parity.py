@@ -255,6 +255,29 @@ def test_sweep_grid_support_matches_oracle(ctx):
     assert r["mag"] == pytest.approx(ro["mag"], rel=1e-6)
 
 
+@pytest.mark.parametrize("cloud", ["grid", "normal120", "kgon12"])
+def test_sweep_ridders_matches_oracle(ctx, cloud):
+    # Ridders' method on min_j w_j(t), the same bracketed protocol on both sides
+    if cloud == "grid":
+        X = workloads.grid_support_cloud()
+    elif cloud == "normal120":
+        X = np.random.default_rng(32).standard_normal((120, 4))
+    else:
+        k = 12
+        X = np.array([[0.0, 0.0]] + [[math.cos(2 * math.pi * j / k), math.sin(2 * math.pi * j / k)]
+                                     for j in range(k)])
+    r = ctx.sweep_tplus(_dev(X), 1e-3, 0.0, 1e-6, method="ridders")
+    ro = oracle.tplus(X, 1e-3, 0.0, 1e-6, method="ridders")
+    rb = oracle.tplus(X, 1e-3, 0.0, 1e-6)
+    lo, hi = r["bracket"]
+    assert hi - lo <= 1e-6 * hi
+    assert r["t_plus"] == pytest.approx(ro["t_plus"], rel=1e-6)
+    assert r["t_plus"] == pytest.approx(rb["t_plus"], rel=1e-6)
+    assert r["w"].min().item() >= 0
+    assert r["probes"] < rb["probes"]
+    assert ctx.options.tplus_method == "bisection"  # the per-call method did not stick
+
+
 def test_sweep_below_bracket_collinear(ctx):
     X = np.stack([np.linspace(0, 5, 40), np.zeros(40)], axis=1)
     r = ctx.sweep_tplus(_dev(X), 1e-3, 0.0, 1e-6)

@@ -13,7 +13,7 @@ import math
 
 import numpy as np
 
-SEEDS = {"grid": 1005, "mixture": 1002, "cube": 1003, "normal": 1004, "batch": 1006}
+SEEDS = {"grid": 1005, "mixture": 1002, "cube": 1003, "normal": 1004, "batch": 1006, "runtime": 1007}
 
 
 def grid_support_cloud(seed: int = SEEDS["grid"], samples: int = 1000, grid: int = 64):
@@ -80,6 +80,23 @@ def batch_clouds(count: int = 512, m: int = 32, n_min: int = 64, n_max: int = 20
     clouds = [np.ascontiguousarray(rng.standard_normal((int(s), m)), dtype=np.float64) for s in sizes]
     ts = np.geomspace(t_min, t_max, n_t)
     return clouds, ts
+
+
+PAPER_RUNTIME_NS = (1000, 3000, 10000, 30000)
+PAPER_RUNTIME_MS = (3, 10, 30, 100)
+PAPER_RUNTIME_COVS = ("identity", "halving")
+
+
+def paper_runtime_cloud(n: int, m: int, cov: str = "identity", run: int = 0, seed: int = SEEDS["runtime"]):
+    """The paper's runtime workload (Sec. 4, experimental results): n points
+    from N(0, I_m) ("identity") or from N(0, Sigma) with Sigma_jj = 2^-(j-1)
+    ("halving"), for n in PAPER_RUNTIME_NS and m in PAPER_RUNTIME_MS, three
+    runs per configuration; the task is t_+ and the weighting at t_+.  Each
+    (n, m, cov, run) has its own seeded stream."""
+    ci = PAPER_RUNTIME_COVS.index(cov)
+    rng = np.random.default_rng([seed, n, m, ci, run])
+    sd = np.ones(m) if cov == "identity" else np.sqrt(2.0 ** -np.arange(m))
+    return np.ascontiguousarray(rng.standard_normal((n, m)) * sd, dtype=np.float64)
 
 
 def subsample(X, n: int, seed: int = 0):
