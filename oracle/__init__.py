@@ -69,6 +69,7 @@ def _load():
                 "orc_weighting": (i32, [P, i64, i64, d, i32, P, P]),
                 "orc_tplus": (i32, [P, i64, i64, d, d, d, i32, P, P, P, P, P]),
                 "orc_tplus_ridders": (i32, [P, i64, i64, d, d, d, i32, P, P, P, P, P]),
+                "orc_scale_zero": (i32, [P, i64, i64, i32, P, P]),
                 "orc_grad": (None, [P, i64, i64, d, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
@@ -222,6 +223,20 @@ def tplus(X, t_lo=1e-3, t_hi=0.0, rel_tol=1e-6, ir_steps=2, method="bisection"):
         raise OracleError(st, "tplus")
     return {"t_plus": out[0], "bracket": (out[1], out[2]), "below": bool(below.value),
             "probes": probes.value, "w": w, "mag": mag.value}
+
+
+def scale_zero(X, ir_steps=2):
+    """App. C, Eq. scaleZero: w0 = d^{-1} 1 / (1^T d^{-1} 1) by a pivoted LU of
+    the distance matrix and FP64 refinement.  Returns (w0, s = 1^T d^{-1} 1,
+    info with the relative residual of d v = 1 and ||d||_inf)."""
+    X = _c(X)
+    n, m = X.shape
+    w0 = np.empty(n)
+    out = np.zeros(3)
+    st = _load().orc_scale_zero(_p(X), n, m, int(ir_steps), _p(w0), _p(out))
+    if st:
+        raise OracleError(st, "scale_zero")
+    return w0, float(out[0]), {"rel_residual": float(out[1]), "d_norm_inf": float(out[2])}
 
 
 def grad(X, t, w=None, lam=None):

@@ -258,6 +258,111 @@ int orc_weighting(const double* X, int64_t n, int64_t m, double t, int ir_steps,
   return ORC_OK;
 }
 
+/* ---- App. C, Eq. scaleZero: the weighting at scale zero ----
+ * lim_{t -> 0} Z(t)^{-1} 1 = d^{-1} 1 / (1^T d^{-1} 1).  d (zero diagonal,
+ * conditionally negative definite for Euclidean points) is indefinite, so the
+ * plain definition is a general solve: d built in full, Gaussian elimination
+ * with partial pivoting, `ir_steps` FP64 refinement steps (r = 1 - d v with
+ * compensated row sums), then s = 1^T v (compensated) and w0 = v / s.
+ * out (nullable, 3 doubles): s = 1^T d^{-1} 1, relative residual
+ * ||1 - d v||_inf / (||d||_inf ||v||_inf), ||d||_inf. */
+static void orc_dist_residual(const double* X, int64_t n, int64_t m, const double* v, double* r,
+                              double* rowsum) {
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t j = 0; j < n; ++j) {
+    orc_acc dv = {0.0, 0.0}, ds = {0.0, 0.0};
+    for (int64_t k = 0; k < n; ++k) {
+      const double d = orc_distance(X, m, j, k);
+      acc_add(&dv, d * v[k]);
+      acc_add(&ds, d);
+    }
+    r[j] = (1.0 - dv.s) - dv.c;
+    if (rowsum) rowsum[j] = acc_value(&ds);
+  }
+}
+
+/* LU with partial pivoting of the n x n row-major A in place; piv[k] = row
+ * swapped with k.  Returns 1 + the first zero pivot, or 0. */
+static int64_t orc_lu(double* A, int64_t n, int64_t* piv) {
+  for (int64_t k = 0; k < n; ++k) {
+    int64_t p = k;
+    for (int64_t i = k + 1; i < n; ++i)
+      if (fabs(A[i * n + k]) > fabs(A[p * n + k])) p = i;
+    piv[k] = p;
+    if (A[p * n + k] == 0.0) return k + 1;
+    if (p != k)
+      for (int64_t j = 0; j < n; ++j) {
+        double tmp = A[k * n + j];
+        A[k * n + j] = A[p * n + j];
+        A[p * n + j] = tmp;
+      }
+#pragma omp parallel for schedule(static)
+    for (int64_t i = k + 1; i < n; ++i) {
+      const double l = A[i * n + k] / A[k * n + k];
+      A[i * n + k] = l;
+      for (int64_t j = k + 1; j < n; ++j) A[i * n + j] -= l * A[k * n + j];
+    }
+  }
+  return 0;
+}
+
+static void orc_lu_solve(const double* A, int64_t n, const int64_t* piv, double* x) {
+  for (int64_t k = 0; k < n; ++k) {
+    double tmp = x[k];
+    x[k] = x[piv[k]];
+    x[piv[k]] = tmp;
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = 0; k < i; ++k) x[i] -= A[i * n + k] * x[k];
+  for (int64_t i = n - 1; i >= 0; --i) {
+    for (int64_t k = i + 1; k < n; ++k) x[i] -= A[i * n + k] * x[k];
+    x[i] /= A[i * n + i];
+  }
+}
+
+int orc_scale_zero(const double* X, int64_t n, int64_t m, int ir_steps, double* w0, double* out3) {
+  if (n < 2 || m < 1) return ORC_EINVAL;
+  double* A = (double*)malloc((size_t)n * n * sizeof(double));
+  int64_t* piv = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+  double* v = (double*)malloc((size_t)n * sizeof(double));
+  double* r = (double*)malloc((size_t)n * sizeof(double));
+  double* rs = (double*)malloc((size_t)n * sizeof(double));
+  if (!A || !piv || !v || !r || !rs) {
+    free(A); free(piv); free(v); free(r); free(rs);
+    return ORC_ENOMEM;
+  }
+  orc_distance_matrix(X, n, m, A);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t k = 0; k < n; ++k)
+      if (j != k && A[j * n + k] == 0.0) {
+        free(A); free(piv); free(v); free(r); free(rs);
+        return ORC_EDUPLICATE;
+      }
+  if (orc_lu(A, n, piv)) {
+    free(A); free(piv); free(v); free(r); free(rs);
+    return ORC_ENOTPD;
+  }
+  for (int64_t j = 0; j < n; ++j) v[j] = 1.0;
+  orc_lu_solve(A, n, piv, v);
+  for (int step = 0; step < ir_steps; ++step) {
+    orc_dist_residual(X, n, m, v, r, NULL);
+    orc_lu_solve(A, n, piv, r);
+    for (int64_t j = 0; j < n; ++j) v[j] += r[j];
+  }
+  orc_dist_residual(X, n, m, v, r, rs);
+  orc_acc sum = {0.0, 0.0};
+  for (int64_t j = 0; j < n; ++j) acc_add(&sum, v[j]);
+  const double sv = acc_value(&sum);
+  for (int64_t j = 0; j < n; ++j) w0[j] = v[j] / sv;
+  if (out3) {
+    out3[0] = sv;
+    out3[1] = max_abs(r, n) / (max_abs(rs, n) * max_abs(v, n));
+    out3[2] = max_abs(rs, n);
+  }
+  free(A); free(piv); free(v); free(r); free(rs);
+  return ORC_OK;
+}
+
 /* ---- Sec. 2 cutoff t_+ by bisection on the sign of min_j w_j ----
  * feasible(t) <=> min_j w_j(t) >= 0.  t_hi <= 0 means the Sec. 1 bound.
  * Invariant: feasible(hi) and not feasible(lo); midpoint lo + (hi - lo)/2;

@@ -447,3 +447,78 @@ def test_grad_general_loss_adjoint_central_differences():
         Xp[i, l] += h
         Xm[i, l] -= h
         assert dx[i, l] == pytest.approx((L(Xp, t) - L(Xm, t)) / (2 * h), rel=1e-5, abs=1e-8)
+
+
+# --------------------------------------------------------- scale zero (App. C)
+
+def test_scale_zero_two_points():
+    a = 2.5
+    X = np.array([[0.0, 0.0], [a, 0.0]])
+    w0, s, info = oracle.scale_zero(X)
+    np.testing.assert_allclose(w0, [0.5, 0.5], rtol=1e-15)
+    assert s == pytest.approx(2.0 / a, rel=1e-15)
+
+
+def test_scale_zero_collinear_closed_form():
+    # d v = 1 on a line: v = (1, 0, ..., 0, 1) / L, so w0 is 1/2 at the two
+    # ends and 0 inside, and 1^T d^{-1} 1 = 2 / L
+    X, gaps, _ = _collinear(40, 3, seed=41)
+    L = gaps.sum()
+    w0, s, info = oracle.scale_zero(X)
+    expect = np.zeros(40)
+    expect[0] = expect[-1] = 0.5
+    np.testing.assert_allclose(w0, expect, atol=1e-12)
+    assert s == pytest.approx(2.0 / L, rel=1e-12)
+
+
+def test_scale_zero_centred_polygon_closed_form():
+    # centre + regular k-gon of radius 1: v = (alpha, 1/k, ..., 1/k) with
+    # alpha = 1 - (2/k) cot(pi / 2k) (the centre row gives k beta = 1, a
+    # vertex row alpha + beta sum_j 2 sin(pi j / k) = 1)
+    k = 12
+    alpha = 1.0 - (2.0 / k) / math.tan(math.pi / (2 * k))
+    v = np.concatenate([[alpha], np.full(k, 1.0 / k)])
+    w0, s, _ = oracle.scale_zero(_kgon(k))
+    assert alpha < 0  # the centre carries a negative weight at scale zero
+    np.testing.assert_allclose(w0, v / v.sum(), rtol=1e-12, atol=1e-14)
+    assert s == pytest.approx(v.sum(), rel=1e-12)
+
+
+def test_scale_zero_is_the_small_t_limit():
+    # Eq. scaleZero: Z(t)^{-1} 1 -> d^{-1} 1 / 1^T d^{-1} 1 as t -> 0, with O(t)
+    # error; the weighting side is the Cholesky path of Z, the limit side the
+    # pivoted LU of d
+    X = np.random.default_rng(42).standard_normal((60, 3))
+    w0, _, _ = oracle.scale_zero(X)
+    errs = []
+    for t in (1e-3, 1e-4):
+        w, _, _ = oracle.weighting(X, t)
+        errs.append(np.abs(w - w0).max() / np.abs(w0).max())
+    assert errs[1] < 2e-3
+    assert errs[0] / errs[1] == pytest.approx(10.0, rel=0.2)
+
+
+def test_scale_zero_matches_scipy_and_invariances():
+    rng = np.random.default_rng(43)
+    X = rng.standard_normal((150, 6))
+    w0, s, info = oracle.scale_zero(X)
+    D = scipy.spatial.distance.cdist(X, X)
+    v = scipy.linalg.solve(D, np.ones(150))
+    np.testing.assert_allclose(w0, v / v.sum(), rtol=1e-9, atol=1e-12)
+    assert info["rel_residual"] < 1e-15
+    assert w0.sum() == pytest.approx(1.0, rel=1e-14)
+    # permutation, translation + rotation, scaling (w0 is scale-free, s scales as 1/lambda)
+    perm = rng.permutation(150)
+    np.testing.assert_allclose(oracle.scale_zero(X[perm])[0], w0[perm], rtol=1e-10, atol=1e-13)
+    Q, _ = np.linalg.qr(rng.standard_normal((6, 6)))
+    np.testing.assert_allclose(oracle.scale_zero(X @ Q + 3.0)[0], w0, rtol=1e-9, atol=1e-12)
+    w2, s2, _ = oracle.scale_zero(2.0 * X)
+    np.testing.assert_allclose(w2, w0, rtol=1e-12, atol=1e-14)
+    assert s2 == pytest.approx(s / 2.0, rel=1e-12)
+
+
+def test_scale_zero_rejects_duplicates():
+    X = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 0.0]])
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.scale_zero(X)
+    assert e.value.status == oracle.EDUPLICATE
