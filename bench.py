@@ -327,7 +327,7 @@ def run_ours(a):
     return out, (ctx, Xd, X, ts)
 
 
-def run_extras(ctx, a, out):
+def run_extras(ctx, a, out, Xd):
     """Bounded side measurements: FP64 dense comparators, sweep, gradients, batch."""
     import torch
 
@@ -398,6 +398,18 @@ def run_extras(ctx, a, out):
     torch.cuda.synchronize()
     ex["per_instance_fp64_solves_per_s"] = len(sample) / (time.perf_counter() - t0)
     ex["per_instance_fp64_sample"] = f"{len(sample)} problems (every 64th cloud, t[0] and t[4])"
+    # scale-zero weighting (App. C, Eq. scaleZero) on the precision config's
+    # cloud (n = 16384) and on the headline cloud
+    ctx.set_options(M.Options(precision=a.precision, residual_mode=a.resid))
+    for name, Xs in (("mixture_n16384", Xm), ("cube_n%d" % Xd.shape[0], Xd)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, s0, i0 = ctx.scale_zero(Xs)
+        torch.cuda.synchronize()
+        ex[f"scale_zero_{name}_s"] = time.perf_counter() - t0
+        ex[f"scale_zero_{name}_rel_residual"] = i0["rel_residual"]
+        ex[f"scale_zero_{name}_ir_iters"] = i0["ir_iters"]
+        ex[f"scale_zero_{name}_precision"] = i0["precision_used"]
     ctx.set_options(M.Options(precision=a.precision, residual_mode=a.resid, profile=True))
     out["extras"] = ex
 
@@ -489,7 +501,7 @@ def main():
     if rank == 0:
         ctx, Xd, X, ts = state
         if a.extras:
-            run_extras(ctx, a, out)
+            run_extras(ctx, a, out, Xd)
         if not a.no_cpu:
             out["cpu_baseline"] = cpu_oracle_sample(X, 1.0, min(a.cpu_sample_n, a.n))
         print(json.dumps(out), flush=True)

@@ -237,10 +237,16 @@ int mag_residual(mag_ctx* ctx, const double* points, int64_t n, int32_t m, doubl
 int mag_residual_noalloc(const double* points, int64_t n, int32_t m, double t, const double* w,
                          const double* b, double* r_out, double* norms, void* stream);
 
-/* a8 (Sec. 2 and its footnote): bisection for the cutoff t_+ on the sign of
- * min_j w_j.  feasible(t) <=> min_j w_j(t) >= 0.  t_hi <= 0 uses the Sec. 1
- * bound.  The bracket keeps feasible(hi) and not feasible(lo); each probe
- * solves at the FP64 midpoint lo + (hi - lo)/2; it stops when
+/* a8 (Sec. 2 and its footnote): the cutoff t_+ on the sign of min_j w_j by
+ * bisection (default) or Ridders' method (options.tplus_method = 1, the
+ * root-finder Sec. 2 prefers).  feasible(t) <=> min_j w_j(t) >= 0.
+ * t_hi <= 0 uses the Sec. 1 bound.  The bracket keeps feasible(hi) and not
+ * feasible(lo).  Bisection solves at the FP64 midpoint lo + (hi - lo)/2.
+ * Ridders evaluates the midpoint x3, then x4 = x3 + (x3 - lo) sign(f(lo) -
+ * f(hi)) f(x3) / sqrt(f(x3)^2 - f(lo) f(hi)) with f = min_j w_j when x4 lies
+ * inside the bracket, and once two successive x4 agree to rel_tol hi / 2 one
+ * more point x4 -/+ rel_tol hi / 2 toward the other end; every evaluation
+ * moves the bracket end of its feasibility class.  Both stop when
  * hi - lo <= rel_tol * hi.  Outputs (host): *t_plus = hi, t_bracket[0..1] =
  * {lo, hi}; w (device, n) and *mag are those at t_plus.  If feasible(t_lo)
  * holds, returns MAG_OK with t_plus = t_lo and info->below_bracket = 1.  If
@@ -248,6 +254,21 @@ int mag_residual_noalloc(const double* points, int64_t n, int32_t m, double t, c
 int mag_sweep_tplus(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t_lo,
                     double t_hi, double rel_tol, double* t_plus, double* t_bracket, double* w,
                     double* mag, mag_info* info);
+
+/* The weighting at scale zero (App. C, Eq. scaleZero):
+ *   w0 = lim_{t -> 0} Z(t)^{-1} 1 = d^{-1} 1 / (1^T d^{-1} 1).
+ * d (zero diagonal) is indefinite; the library solves instead
+ * M z = 1 with M = 1 1^T - d / c, positive definite for c large enough and
+ * with d^{-1} 1 proportional to M^{-1} 1 (Sherman-Morrison), so that
+ * w0 = z / 1^T z and 1^T d^{-1} 1 = 1^T z / (c (1^T z - 1)).  c starts at
+ * 4 max_j ||x_j - x_0|| (>= 2 max d) and doubles on a non-positive pivot.
+ * M has the structure of Z (unit diagonal, entries in [0, 1]), so the same
+ * tensor-core factor, FP64 refinement (to options.ir_tol on M z = 1) and
+ * fallbacks apply.  Outputs: w0 (device, n, sums to 1), *s = 1^T d^{-1} 1
+ * (host); info as for mag_solve on M (min_w is min_j w0_j).  Errors as
+ * mag_solve; MAG_EDUPLICATE if two points coincide. */
+int mag_scale_zero(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double* w0, double* s,
+                   mag_info* info);
 
 /* a9: gradients by implicit differentiation of Zw = 1 (not in the paper).
  * For a loss L(w) with g = dL/dw (device, n; NULL means L = Mag, g = 1):

@@ -95,6 +95,7 @@ SIGNATURES = {
     "mag_sweep_tplus": (ctypes.c_int, [_P, _P, _I64, _I32, _D, _D, _D, _DP, _DP, _P, _DP,
                                        ctypes.POINTER(mag_info)]),
     "mag_grad": (ctypes.c_int, [_P, _P, _I64, _I32, _D, _P, _P, _DP, _P, ctypes.POINTER(mag_info)]),
+    "mag_scale_zero": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _DP, ctypes.POINTER(mag_info)]),
     "mag_solve_batch": (ctypes.c_int, [_P, ctypes.POINTER(mag_batch_desc), _I32, _P, _P, _P, _P,
                                        ctypes.POINTER(mag_info)]),
 }
@@ -327,6 +328,20 @@ class Context:
         return {"t_plus": tp.value, "bracket": (br[0], br[1]), "w": w, "mag": mag.value,
                 "below": bool(d["below_bracket"]), "probes": d["probes"], "info": d}
 
+    def scale_zero(self, X: torch.Tensor):
+        """App. C, Eq. scaleZero: w0 = d^{-1} 1 / 1^T d^{-1} 1.  Returns
+        (w0 [n], s = 1^T d^{-1} 1, info)."""
+        X = self._points(X)
+        n, m = X.shape
+        w0 = torch.empty(n, dtype=torch.float64, device=self.device)
+        sv = ctypes.c_double(0.0)
+        info = mag_info()
+        st = self._check(self._lib.mag_scale_zero(self._h, _P(X.data_ptr()), n, m, _P(w0.data_ptr()),
+                                                  ctypes.byref(sv), ctypes.byref(info)))
+        d = info.as_dict()
+        d["status"] = st
+        return w0, sv.value, d
+
     def grad(self, X: torch.Tensor, t: float, w: torch.Tensor | None = None,
              dL_dw: torch.Tensor | None = None):
         X = self._points(X)
@@ -423,6 +438,10 @@ def solve(X, t, options: Options | None = None):
 def sweep_tplus(X, t_lo=1e-3, t_hi=0.0, rel_tol=1e-6, options: Options | None = None,
                 method: str | None = None):
     return default_context(options).sweep_tplus(X, t_lo, t_hi, rel_tol, method=method)
+
+
+def scale_zero(X, options: Options | None = None):
+    return default_context(options).scale_zero(X)
 
 
 class MagnitudeFn(torch.autograd.Function):

@@ -34,7 +34,8 @@ __device__ inline void atomic_max_nonneg(unsigned long long* a, double v) {
 template <bool WF, bool WD, bool ROWSUM, bool WDIST>
 __global__ void __launch_bounds__(GEN_THREADS, 1)
     k_generate(const double* __restrict__ X, int64_t n, int m, double t, float* __restrict__ Zf,
-               double* __restrict__ Zd, double* __restrict__ Dd, double* __restrict__ rowsum, DevStatus* st) {
+               double* __restrict__ Zd, double* __restrict__ Dd, double* __restrict__ rowsum, DevStatus* st,
+               int kind) {
   extern __shared__ double smem[];
   double* xr = smem;                   // [TILE][GEN_MC] row points (broadcast reads)
   double* xc = smem + TILE * GEN_MC;   // [GEN_MC][TILE] column points (conflict free)
@@ -111,8 +112,8 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
         else if (v == 0.0) flags |= ST_DUPLICATE;
         mind2 = fmin(mind2, v);
         if (WD || WDIST) dd = sqrt(v);
-        if (WD) zd = exp_neg(-t * dd, exptab);
-        if (WF) zf = WD ? (float)zd : expf(-tf * sqrtf((float)v));
+        if (WD) zd = kind ? fma(-t, dd, 1.0) : exp_neg(-t * dd, exptab);
+        if (WF) zf = WD ? (float)zd : (kind ? 1.0f - tf * sqrtf((float)v) : expf(-tf * sqrtf((float)v)));
       }
       if (WF) Zf[tile_off + (int64_t)r * TILE + c] = zf;
       if (WD) Zd[tile_off + (int64_t)r * TILE + c] = zd;
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
 template <bool WF, bool WD>
 __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __restrict__ Dd, int64_t n, double t,
                                                             float* __restrict__ Zf, double* __restrict__ Zd,
-                                                            double* __restrict__ rowsum) {
+                                                            double* __restrict__ rowsum, int kind) {
   __shared__ double exptab[128];
   __shared__ double colpart[8][TILE];
   load_exp_table(exptab);
@@ -191,8 +192,8 @@ __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __rest
         if (gr == gc && gr < n) rs += 1.0;  // the diagonal counts in its row sum
       } else {
         const double d = Dd[e];
-        zd = WD ? exp_neg(-t * d, exptab) : 0.0;
-        zf = WD ? (float)zd : expf(-tf * (float)d);
+        zd = WD ? (kind ? fma(-t, d, 1.0) : exp_neg(-t * d, exptab)) : 0.0;
+        zf = WD ? (float)zd : (kind ? 1.0f - tf * (float)d : expf(-tf * (float)d));
         const double z = WD ? zd : (double)zf;
         rs += z;
         cs[q] += z;
@@ -215,6 +216,24 @@ __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __rest
   }
 }
 
+// max_j ||x_j - x_0||^2 (FP64 differences) into aux_bits: 2 max_j ||x_j - x_0||
+// bounds every pairwise distance (triangle inequality through x_0).
+__global__ void k_far_from_first(const double* __restrict__ X, int64_t n, int m, DevStatus* st) {
+  double v = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s2 = 0.0;
+    for (int l = 0; l < m; ++l) {
+      const double diff = X[i * m + l] - X[l];
+      s2 = fma(diff, diff, s2);
+    }
+    v = fmax(v, s2);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&st->far_d2_bits, v);
+}
+
 __global__ void k_rowsum_max(const double* __restrict__ rowsum, int64_t n, DevStatus* st) {
   double v = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -227,13 +246,14 @@ __global__ void k_rowsum_max(const double* __restrict__ rowsum, int64_t n, DevSt
 
 template <bool WF, bool WD, bool ROWSUM, bool WDIST = false>
 cudaError_t launch_gen_t(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
-                         double* Zd, double* rowsum, DevStatus* st, cudaStream_t s, double* Dd = nullptr) {
+                         double* Zd, double* rowsum, DevStatus* st, cudaStream_t s, double* Dd = nullptr,
+                         int kind = 0) {
   const size_t smem = 2 * (size_t)TILE * GEN_MC * sizeof(double);
   auto kern = k_generate<WF, WD, ROWSUM, WDIST>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t tiles = num_lower_tiles(N);
-  kern<<<(unsigned)tiles, GEN_THREADS, smem, s>>>(X, n, m, t, Zf, Zd, Dd, rowsum, st);
+  kern<<<(unsigned)tiles, GEN_THREADS, smem, s>>>(X, n, m, t, Zf, Zd, Dd, rowsum, st, kind);
   note_launch();
   return cudaGetLastError();
 }
@@ -241,30 +261,31 @@ cudaError_t launch_gen_t(const double* X, int64_t n, int m, double t, int64_t N,
 }  // namespace
 
 cudaError_t launch_generate(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
-                            double* Zd, double* rowsum, DevStatus* st, cudaStream_t s) {
-  if (Zf && Zd) return launch_gen_t<true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s);
-  if (Zf) return launch_gen_t<true, false, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s);
-  if (Zd) return launch_gen_t<false, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s);
+                            double* Zd, double* rowsum, DevStatus* st, cudaStream_t s, int kind) {
+  if (Zf && Zd) return launch_gen_t<true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, nullptr, kind);
+  if (Zf) return launch_gen_t<true, false, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, nullptr, kind);
+  if (Zd) return launch_gen_t<false, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, nullptr, kind);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_generate_dist(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
-                                 double* Zd, double* Dd, double* rowsum, DevStatus* st, cudaStream_t s) {
-  if (Zf && Zd) return launch_gen_t<true, true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd);
-  if (Zf) return launch_gen_t<true, false, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd);
-  if (Zd) return launch_gen_t<false, true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd);
+                                 double* Zd, double* Dd, double* rowsum, DevStatus* st, cudaStream_t s,
+                                 int kind) {
+  if (Zf && Zd) return launch_gen_t<true, true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd, kind);
+  if (Zf) return launch_gen_t<true, false, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd, kind);
+  if (Zd) return launch_gen_t<false, true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd, kind);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_generate_from_dist(const double* Dd, int64_t n, double t, int64_t N, float* Zf, double* Zd,
-                                     double* rowsum, cudaStream_t s) {
+                                     double* rowsum, cudaStream_t s, int kind) {
   const unsigned tiles = (unsigned)num_lower_tiles(N);
   if (Zf && Zd)
-    k_generate_from_dist<true, true><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum);
+    k_generate_from_dist<true, true><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum, kind);
   else if (Zf)
-    k_generate_from_dist<true, false><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum);
+    k_generate_from_dist<true, false><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum, kind);
   else if (Zd)
-    k_generate_from_dist<false, true><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum);
+    k_generate_from_dist<false, true><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum, kind);
   else
     return cudaErrorInvalidValue;
   note_launch();
@@ -274,6 +295,14 @@ cudaError_t launch_generate_from_dist(const double* Dd, int64_t n, double t, int
 cudaError_t launch_min_distance(const double* X, int64_t n, int m, DevStatus* st, cudaStream_t s) {
   const int64_t N = (n + TILE - 1) / TILE;
   return launch_gen_t<false, false, false>(X, n, m, 1.0, N, nullptr, nullptr, nullptr, st, s);
+}
+
+cudaError_t launch_far_from_first(const double* X, int64_t n, int m, DevStatus* st, cudaStream_t s) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  k_far_from_first<<<blocks, 256, 0, s>>>(X, n, m, st);
+  note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_rowsum_max(const double* rowsum, int64_t n, DevStatus* st, cudaStream_t s) {

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_resid_mf(const double* __restri
                                                           int m, double t,
                                                           const double* __restrict__ w,
                                                           double* __restrict__ part, int chunks,
-                                                          int64_t np, int ct) {
+                                                          int64_t np, int ct, int kind) {
   extern __shared__ double sm[];
   double* xc = sm;            // [ct][m]
   double* wc = sm + ct * m;   // [ct]
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_resid_mf(const double* __restri
           d2 = fma(diff, diff, d2);
         }
       }
-      const double z = exp_neg(-t * sqrt(d2), exptab);
+      const double z = kind ? fma(-t, sqrt(d2), 1.0) : exp_neg(-t * sqrt(d2), exptab);
       zs += z;
       // Kahan step for s += z * w_k
       const double y = fma(z, wc[q], -c);
@@ -482,19 +482,19 @@ inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + thre
 
 cudaError_t launch_residual_mf(const double* X, int64_t n, int m, double t, const double* w,
                                const double* b, double* r, double* part, int chunks, int64_t np,
-                               DevStatus* st, cudaStream_t s) {
+                               DevStatus* st, cudaStream_t s, int kind) {
   int ct = 128;
   while (ct > 8 && (size_t)ct * (m + 1) * sizeof(double) > 48 * 1024) ct /= 2;
   const size_t smem = (size_t)ct * (m + 1) * sizeof(double);
   const dim3 grid(blocks_for(n, RES_THREADS), (unsigned)chunks);
   if (m <= 8)
-    k_resid_mf<8><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct);
+    k_resid_mf<8><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct, kind);
   else if (m <= 16)
-    k_resid_mf<16><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct);
+    k_resid_mf<16><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct, kind);
   else if (m <= 32)
-    k_resid_mf<32><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct);
+    k_resid_mf<32><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct, kind);
   else
-    k_resid_mf<0><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct);
+    k_resid_mf<0><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct, kind);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

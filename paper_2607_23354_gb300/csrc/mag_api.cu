@@ -88,6 +88,7 @@ struct mag_ctx {
   int tasks_nb = -1, tasks_la = -1, tasks_pairs = -1;
   std::map<std::pair<int64_t, int64_t>, std::pair<int64_t, int64_t>> task_rng;  // (j0, j1) -> (offset, count)
   cudaStream_t side = nullptr;       // panel stream of the look-ahead factor
+  int kind = MAT_EXP;                // matrix the solve path generates (MatKind)
   cudaEvent_t ev_la[3] = {nullptr, nullptr, nullptr};  // start, panel done, trailing done
 
   // typed views of the workspace
@@ -309,6 +310,8 @@ double prof_collect(mag_ctx* ctx, double* per_cat) {
     float v = 0;
     if (cudaEventElapsedTime(&v, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]) == cudaSuccess)
       per_cat[ctx->prof_cat[i]] += v;
+    else
+      cudaGetLastError();  // an interval cut short by an error: drop it, leave no pending error
   }
   ctx->prof_used = 0;
   return per_cat[PC_UPDATE] + per_cat[PC_UPDATE_PANEL];
@@ -693,6 +696,43 @@ int mag_min_distance(mag_ctx* ctx, const double* points, int64_t n, int32_t m, d
   return MAG_OK;
 }
 
+int mag_scale_zero(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double* w0, double* s,
+                   mag_info* info) {
+  TRY(check_args(ctx, points, n, m, 1.0));
+  if (!w0 || !s) return fail(ctx, MAG_EINVAL, "NULL output");
+  ctx->err.clear();
+  if (info) std::memset(info, 0, sizeof *info);
+  // c >= 2 max d from 2 max_j ||x_j - x_0|| (triangle inequality through x_0)
+  if (!ctx->ws || ctx->lay.np < ((n + TILE - 1) / TILE) * TILE) TRY(ensure_workspace(ctx, n, false, false));
+  TRY(reset_status(ctx));
+  CU(launch_far_from_first(points, n, m, ctx->st(), ctx->stream));
+  TRY(read_status(ctx));
+  const double far = std::sqrt(bits_to_double(ctx->h_st->far_d2_bits));
+  if (!std::isfinite(far)) return fail(ctx, MAG_EINVAL, "non-finite coordinate");
+  if (!(far > 0.0)) return fail(ctx, MAG_EDUPLICATE, "all points coincide");
+  double c = 4.0 * far;
+  // M = 1 1^T - d / c is positive definite for c large enough; d^{-1} 1 is
+  // proportional to M^{-1} 1 (Sherman-Morrison), so w0 = z / 1^T z with M z = 1
+  double sz = 0.0;
+  mag_info zi;
+  int st = MAG_ENOTPD;
+  for (int attempt = 0; attempt < 8 && st == MAG_ENOTPD; ++attempt) {
+    ctx->kind = MAT_SHIFTED_DIST;
+    st = mag_solve(ctx, points, n, m, 1.0 / c, w0, &sz, &zi);
+    ctx->kind = MAT_EXP;
+    if (st == MAG_ENOTPD) c *= 2.0;
+  }
+  if (info) *info = zi;
+  if (st != MAG_OK && st != MAG_ENOCONV) return st;
+  if (!(sz > 0.0) || !std::isfinite(sz)) return fail(ctx, MAG_ENOCONV, "1^T z = %g is not positive", sz);
+  CU(launch_scale(w0, 1.0 / sz, w0, n, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  // M z = 1  =>  d z = c (1^T z - 1) 1  =>  1^T d^{-1} 1 = 1^T z / (c (1^T z - 1))
+  *s = sz / (c * (sz - 1.0));
+  if (info) info->min_w = zi.min_w / sz;
+  return st;
+}
+
 }  // extern "C"
 
 // ------------------------------------------------------------ the solve
@@ -709,7 +749,10 @@ struct SolveResult {
 
 float elapsed(mag_ctx* ctx, int a, int b) {
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, ctx->ev[a], ctx->ev[b]);
+  if (cudaEventElapsedTime(&ms, ctx->ev[a], ctx->ev[b]) != cudaSuccess) {
+    cudaGetLastError();  // an event not recorded on this path: no time, no pending error
+    ms = 0.f;
+  }
   return ms;
 }
 
@@ -724,13 +767,13 @@ int generate(mag_ctx* ctx, const double* X, int32_t m, double t, bool f32, bool 
                      ctx->dist_m == m;
   if (reuse) {
     CU(launch_generate_from_dist(ctx->dist(), L.n, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr,
-                                 ctx->vd(V_ROWSUM), s));
+                                 ctx->vd(V_ROWSUM), s, ctx->kind));
   } else if (ctx->dist_active && L.dist) {
     CU(launch_generate_dist(X, L.n, m, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr, ctx->dist(),
-                            ctx->vd(V_ROWSUM), ctx->st(), s));
+                            ctx->vd(V_ROWSUM), ctx->st(), s, ctx->kind));
   } else {
     CU(launch_generate(X, L.n, m, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr,
-                       ctx->vd(V_ROWSUM), ctx->st(), s));
+                       ctx->vd(V_ROWSUM), ctx->st(), s, ctx->kind));
   }
   CU(launch_rowsum_max(ctx->vd(V_ROWSUM), L.n, ctx->st(), s));
   CU(cudaEventRecord(ctx->ev[1], s));
@@ -840,7 +883,7 @@ int residual(mag_ctx* ctx, const double* X, int32_t m, double t, const double* w
     CU(launch_residual_stored(ctx->zd(), L.n, L.N, w, b, ctx->vd(V_ROWSUM), r, ctx->spart(), L.np,
                               ctx->st(), s));
   else
-    CU(launch_residual_mf(X, L.n, m, t, w, b, r, ctx->part(), L.chunks, L.np, ctx->st(), s));
+    CU(launch_residual_mf(X, L.n, m, t, w, b, r, ctx->part(), L.chunks, L.np, ctx->st(), s, ctx->kind));
   CU(cudaEventRecord(ctx->ev[1], s));
   TRY(read_status(ctx));
   R->ms_res += elapsed(ctx, 0, 1);
@@ -896,7 +939,7 @@ int gmres_ir(mag_ctx* ctx, int prec, const double* X, int32_t m, double t, const
     if (stored)
       CU(launch_residual_stored(ctx->zd(), n, L.N, v, zeros, ctx->vd(V_ROWSUM), tmp, ctx->spart(), np, ctx->st(), s));
     else
-      CU(launch_residual_mf(X, n, m, t, v, zeros, tmp, ctx->part(), L.chunks, np, ctx->st(), s));
+      CU(launch_residual_mf(X, n, m, t, v, zeros, tmp, ctx->part(), L.chunks, np, ctx->st(), s, ctx->kind));
     TRY(correction(ctx, prec, tmp, out, /*init=*/true, R));
     CU(launch_scale(out, -1.0, out, n, s));
     return MAG_OK;
@@ -1165,10 +1208,12 @@ int mag_solve(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t
   cudaEventCreate(&t1);
   cudaEventRecord(t0, ctx->stream);
   int st = solve_impl(ctx, points, n, m, t, nullptr, w, &R);
+  bool timed = false;
   if (st == MAG_OK || st == MAG_ENOCONV) {
     cudaStream_t s = ctx->stream;
     cudaError_t e = launch_reduce_w(w, n, ctx->st(), s);
     if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+    timed = e == cudaSuccess;
     if (e == cudaSuccess) {
       int rs = read_status(ctx);
       if (rs != MAG_OK) st = rs;
@@ -1180,7 +1225,10 @@ int mag_solve(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t
   fill_info(ctx, R, n, info);
   if (info) {
     float ms = 0;
-    cudaEventElapsedTime(&ms, t0, t1);
+    if (!timed || cudaEventElapsedTime(&ms, t0, t1) != cudaSuccess) {
+      cudaGetLastError();  // the end event was not recorded (failed solve): no total time
+      ms = 0;
+    }
     info->ms_total = ms;
     info->kernel_launches = g_kernel_launches.load() - l0;
   }

@@ -60,6 +60,7 @@ struct DevStatus {
   unsigned long long z_max_bits;   // max_j sum_k Z_jk
   unsigned long long w_max_bits;   // max_j |w_j|
   unsigned long long off_max_bits; // max_j sum_{k != j} Z_jk (from the generator)
+  unsigned long long far_d2_bits;  // max_j ||x_j - x_0||^2 (k_far_from_first)
   double mag;                      // 1^T w (compensated)
   double min_w;                    // min_j w_j
   double aux[6];                   // scratch scalars (GMRES dot products, grad sums)
@@ -71,15 +72,21 @@ struct DevStatus {
 // K1: fused distance + exp generator of the packed lower tiles.
 // Writes Zf (FP32 tiles, may be null) and/or Zd (FP64 tiles, may be null),
 // accumulates full row sums of Z into rowsum (n doubles, must be zeroed),
-// min off-diagonal d^2, and non-finite/duplicate flags.
+// min off-diagonal d^2, and non-finite/duplicate flags.  kind selects the
+// matrix: MAT_EXP, Z_jk = exp(-t d_jk) (Eq. weighting); MAT_SHIFTED_DIST,
+// Z_jk = 1 - t d_jk (the scale-zero system with t = 1/c).
+enum MatKind : int { MAT_EXP = 0, MAT_SHIFTED_DIST = 1 };
 cudaError_t launch_generate(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
-                            double* Zd, double* rowsum, DevStatus* st, cudaStream_t s);
+                            double* Zd, double* rowsum, DevStatus* st, cudaStream_t s, int kind = MAT_EXP);
 // The same, also writing the FP64 distances d_jk into Dd (packed tiles like Z).
 cudaError_t launch_generate_dist(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
-                                 double* Zd, double* Dd, double* rowsum, DevStatus* st, cudaStream_t s);
+                                 double* Zd, double* Dd, double* rowsum, DevStatus* st, cudaStream_t s,
+                                 int kind = MAT_EXP);
 // Z from stored FP64 distance tiles: Zf (may be null) and Zd (may be null), row sums.
 cudaError_t launch_generate_from_dist(const double* Dd, int64_t n, double t, int64_t N, float* Zf, double* Zd,
-                                     double* rowsum, cudaStream_t s);
+                                     double* rowsum, cudaStream_t s, int kind = MAT_EXP);
+// max_j ||x_j - x_0||^2 into st->far_d2_bits (st->far_d2_bits must start at 0).
+cudaError_t launch_far_from_first(const double* X, int64_t n, int m, DevStatus* st, cudaStream_t s);
 // min_{j != k} d^2 over all pairs (FP64) into st->min_d2_bits.
 cudaError_t launch_min_distance(const double* X, int64_t n, int m, DevStatus* st, cudaStream_t s);
 // off-diagonal row-sum maximum (Gershgorin) from rowsum into st->off_max_bits.
@@ -177,7 +184,7 @@ cudaError_t launch_backward_persistent(const T* Z, const T* Dinv, int64_t N, con
 // part: scratch of 3 * chunks * np doubles.  Norms go to st (r_max, z_max, w_max).
 cudaError_t launch_residual_mf(const double* X, int64_t n, int m, double t, const double* w,
                                const double* b, double* r, double* part, int chunks, int64_t np,
-                               DevStatus* st, cudaStream_t s);
+                               DevStatus* st, cudaStream_t s, int kind = MAT_EXP);
 // Stored: P is scratch of N * N * 128 doubles (one partial per row block,
 // tile and row); rowsum holds the row sums of Z from the generator.
 cudaError_t launch_residual_stored(const double* Zd, int64_t n, int64_t N, const double* w,

@@ -451,3 +451,86 @@ def test_solve_multi_reuses_distances_and_matches(ctx, resid):
             assert abs(m1 - mags[i]) <= 1e-12 * abs(mags[i])
     finally:
         ctx.set_options(M.Options())
+
+
+# ------------------------------------------------- scale zero (App. C, Eq. scaleZero)
+
+SCALE_ZERO_CASES = ["two", "three", "normal300x5", "ragged129x10", "cube1000x8", "normal2500x3", "grid",
+                    "normal700x100"]
+
+
+@pytest.mark.parametrize("case", SCALE_ZERO_CASES)
+def test_scale_zero_matches_oracle(ctx, case):
+    rng = np.random.default_rng(1000 + SCALE_ZERO_CASES.index(case))
+    if case == "two":
+        X = np.array([[0.0, 0.0], [1.5, 0.5]])
+    elif case == "three":
+        X = np.array([[0.0, 0.0], [3.0, 0.0], [3.0, 0.1]])
+    elif case == "grid":
+        X = workloads.grid_support_cloud()
+    else:
+        kind, dims = case[:-len(case.lstrip("abcdefghijklmnopqrstuvwxyz"))], case.lstrip("abcdefghijklmnopqrstuvwxyz")
+        n, m = (int(v) for v in dims.split("x"))
+        X = rng.random((n, m)) if kind == "cube" else rng.standard_normal((n, m))
+    w0, s, info = ctx.scale_zero(_dev(X))
+    w0r, sr, ir = oracle.scale_zero(X)
+    w0 = w0.cpu().numpy()
+    assert info["rel_residual"] <= 1e-14  # of M z = 1, refined in FP64
+    assert abs(w0.sum() - 1.0) <= 1e-12
+    # backward stability on the paper's system d v = 1 with v = s w0 (FP64 check)
+    D = np.sqrt(np.maximum(((X[:, None, :] - X[None, :, :]) ** 2).sum(-1), 0.0))
+    v = s * w0
+    rel_d = np.abs(1.0 - D @ v).max() / (np.abs(D).sum(1).max() * np.abs(v).max())
+    assert rel_d <= 1e-13, rel_d
+    # forward error: the refinement leaves ||1 - M z|| <= 1e-14 ||M|| ||z||, so w0
+    # agrees with the oracle to kappa(M) 1e-14 (1e-9 when that is smaller), M
+    # = 1 1^T - d / c with the library's first c = 4 max_j ||x_j - x_0||
+    c = 4.0 * np.sqrt(((X - X[0]) ** 2).sum(1)).max()
+    kappa = np.linalg.cond(1.0 - D / c)
+    tol = max(1e-9, 2e-14 * kappa)
+    assert np.abs(w0 - w0r).max() <= tol * np.abs(w0r).max()
+    assert s == pytest.approx(sr, rel=tol)
+
+
+def test_scale_zero_closed_forms(ctx):
+    # points on a line: w0 = 1/2 at the ends, 0 inside, 1^T d^{-1} 1 = 2 / L
+    rng = np.random.default_rng(44)
+    gaps = rng.uniform(0.05, 2.0, size=299)
+    pos = np.concatenate([[0.0], np.cumsum(gaps)])
+    u = rng.standard_normal(4)
+    u /= np.linalg.norm(u)
+    X = pos[:, None] * u[None, :]
+    w0, s, _ = ctx.scale_zero(_dev(X))
+    expect = np.zeros(300)
+    expect[0] = expect[-1] = 0.5
+    # d on a line is ill-conditioned (kappa(M) ~ 1e6 here): the forward error
+    # is bounded by kappa(M) times the 1e-14 residual of M z = 1
+    D = np.abs(pos[:, None] - pos[None, :])
+    kappa = np.linalg.cond(1.0 - D / (4.0 * pos[-1]))
+    tol = max(1e-11, 2e-14 * kappa)
+    np.testing.assert_allclose(w0.cpu().numpy(), expect, atol=0.5 * tol)
+    assert s == pytest.approx(2.0 / gaps.sum(), rel=tol)
+    # centre + regular 12-gon: v = (1 - (2/k) cot(pi/2k), 1/k, ...)
+    k = 12
+    ang = 2 * np.pi * np.arange(k) / k
+    X = np.vstack([[0.0, 0.0], np.stack([np.cos(ang), np.sin(ang)], axis=1)])
+    alpha = 1.0 - (2.0 / k) / math.tan(math.pi / (2 * k))
+    v = np.concatenate([[alpha], np.full(k, 1.0 / k)])
+    w0, s, _ = ctx.scale_zero(_dev(X))
+    np.testing.assert_allclose(w0.cpu().numpy(), v / v.sum(), rtol=1e-12, atol=1e-14)
+    assert s == pytest.approx(v.sum(), rel=1e-12)
+
+
+def test_scale_zero_is_the_small_t_limit_of_the_solver(ctx):
+    X = np.random.default_rng(45).standard_normal((500, 3))
+    w0, _, _ = ctx.scale_zero(_dev(X))
+    w, _, _ = ctx.solve(_dev(X), 1e-4)
+    w0 = w0.cpu().numpy()
+    assert np.abs(w.cpu().numpy() - w0).max() <= 2e-3 * np.abs(w0).max()
+
+
+def test_scale_zero_rejects_duplicates(ctx):
+    X = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 0.0], [2.0, 3.0]])
+    with pytest.raises(M.MagnitudeError) as e:
+        ctx.scale_zero(_dev(X))
+    assert e.value.status == M.MAG_EDUPLICATE
