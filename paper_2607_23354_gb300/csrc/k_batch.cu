@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(BT, 1)
   extern __shared__ float smf[];
   __shared__ int s_q, s_flag;
   __shared__ double red[BT / 32][3];
-  __shared__ double exptab[128];
+  __shared__ double exptab[2 * EXPT_SIZE];
   load_exp_table(exptab);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   Scratch S;

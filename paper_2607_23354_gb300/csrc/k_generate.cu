@@ -40,8 +40,8 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
   double* xr = smem;                   // [TILE][GEN_MC] row points (broadcast reads)
   double* xc = smem + TILE * GEN_MC;   // [GEN_MC][TILE] column points (conflict free)
   __shared__ double colpart[GEN_THREADS / 32][TILE];
-  __shared__ double warpmin[GEN_THREADS / 32];
-  __shared__ double exptab[128];
+  __shared__ unsigned long long warpmin[GEN_THREADS / 32];
+  __shared__ double exptab[2 * EXPT_SIZE];
   if (WD) load_exp_table(exptab);
 
   int64_t I, J;
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
   for (int i = 0; i < 8; ++i) rs[i] = 0.0f;
 #pragma unroll
   for (int q = 0; q < 4; ++q) cs[q] = 0.0f;
-  double mind2 = INFINITY;
+  unsigned long long mind2b = 0x7ff0000000000000ull;  // +inf
   int flags = 0;
   const float tf = (float)t;
 
@@ -108,9 +108,12 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
         zd = (gr == gc) ? 1.0 : 0.0;
         zf = (float)zd;
       } else {
-        if (!isfinite(v)) flags |= ST_NONFINITE;
-        else if (v == 0.0) flags |= ST_DUPLICATE;
-        mind2 = fmin(mind2, v);
+        // v >= 0 or NaN: the checks and the minimum on the bit pattern (integer
+        // pipe; non-negative doubles order like their bits)
+        const unsigned long long vb = (unsigned long long)__double_as_longlong(v);
+        if ((vb >> 52) >= 0x7ffull) flags |= ST_NONFINITE;
+        else if (vb == 0ull) flags |= ST_DUPLICATE;
+        else mind2b = vb < mind2b ? vb : mind2b;
         if (WD || WDIST) dd = sqrt(v);
         if (WD) zd = kind ? fma(-t, dd, 1.0) : exp_neg(-t * dd, exptab);
         if (WF) zf = WD ? (float)zd : (kind ? 1.0f - tf * sqrtf((float)v) : expf(-tf * sqrtf((float)v)));
@@ -129,8 +132,11 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
   if (flags) atomicOr(&st->flags, flags);
   // min d^2 over the CTA
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mind2 = fmin(mind2, __shfl_xor_sync(0xffffffffu, mind2, o));
-  if (lane == 0) warpmin[warp] = mind2;
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_xor_sync(0xffffffffu, mind2b, o);
+    mind2b = other < mind2b ? other : mind2b;
+  }
+  if (lane == 0) warpmin[warp] = mind2b;
 
   if (ROWSUM) {
     // row sums: reduce over lanes, one atomic per row
@@ -153,9 +159,9 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
     if (gc < n) atomicAdd(rowsum + gc, v);
   }
   if (threadIdx.x == 0) {
-    double v = warpmin[0];
-    for (int w = 1; w < GEN_THREADS / 32; ++w) v = fmin(v, warpmin[w]);
-    if (v < INFINITY) atomic_min_nonneg(&st->min_d2_bits, v);
+    unsigned long long v = warpmin[0];
+    for (int w = 1; w < GEN_THREADS / 32; ++w) v = warpmin[w] < v ? warpmin[w] : v;
+    if (v < 0x7ff0000000000000ull) atomicMin(&st->min_d2_bits, v);
   }
 }
 
@@ -165,7 +171,7 @@ template <bool WF, bool WD>
 __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __restrict__ Dd, int64_t n, double t,
                                                             float* __restrict__ Zf, double* __restrict__ Zd,
                                                             double* __restrict__ rowsum, int kind) {
-  __shared__ double exptab[128];
+  __shared__ double exptab[2 * EXPT_SIZE];
   __shared__ double colpart[8][TILE];
   load_exp_table(exptab);
   __syncthreads();

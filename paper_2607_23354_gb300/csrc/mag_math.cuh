@@ -3,14 +3,16 @@
 // floating-point arithmetic", ACM TOMS 15(2), 1989), used wherever the solver
 // needs Z_jk = exp(-t d_jk) in FP64.
 //
-//   x = (64 k + j) ln2/64 + r,  |r| <= ln2/128  (N = 64k + j = round(64 x / ln 2),
-//                                                r with the two-part ln2/64)
-//   exp(x) = 2^k 2^(j/64) exp(r),  exp(r) - 1 = r + r^2/2 + ... + r^5/120
-//   (Taylor, truncation below 3.4e-17 relative), 2^(j/64) = T_hi + T_lo.
+//   x = (256 k + j) ln2/256 + r, |r| <= ln2/512 (N = 256k + j = round(256 x / ln 2),
+//                                               r with the two-part ln2/256)
+//   exp(x) = 2^k 2^(j/256) exp(r),  exp(r) - 1 = r + r^2/2 + r^3/6 + r^4/24
+//   (Taylor, truncation below 4e-17 relative), 2^(j/256) = T_hi + T_lo.
 //
-// About 12 FP64 operations; at most about one unit in the last place from the
-// exact value (the tests compare it with the host libm exp).  Results below
-// 2^-1021 (x < -708) are returned as 0, NaN propagates.  The 128-double table
+// Ten FP64 operations; the range test and the final 2^k scaling are integer
+// operations on the bit patterns (the FP64 pipe is the generator's limit).
+// At most about one unit in the last place from the exact value (the tests
+// compare it with the host libm exp).  Results below 2^-1021 (x below about
+// -707.7) are returned as 0, NaN propagates.  The 2 * EXPT_SIZE-double table
 // (T_hi, T_lo pairs) must be staged by the caller, usually in shared memory:
 // load_exp_table().
 #pragma once
@@ -22,26 +24,27 @@ namespace mag {
 #include "exp_table.inc"
 
 __device__ __forceinline__ void load_exp_table(double* tab) {
-  for (int i = threadIdx.x; i < 128; i += blockDim.x) tab[i] = kExpTable[i];
+  for (int i = threadIdx.x; i < 2 * EXPT_SIZE; i += blockDim.x) tab[i] = kExpTable[i];
 }
 
 __device__ __forceinline__ double exp_neg(double x, const double* tab) {
-  if (!(x > -708.0)) return x != x ? x : 0.0;
+  if ((__double2hiint(x) & 0x7ff00000) == 0x7ff00000) return x != x ? x : 0.0;  // NaN, -inf
   const double shift = 0x1.8p52;
   double kd = fma(x, EXPT_INV_L, shift);
-  const int N = __double2loint(kd);
+  const int N = __double2loint(kd);        // round(x 256 / ln 2)
+  if (N < -1021 * EXPT_SIZE) return 0.0;   // 2^k with k < -1021
   kd -= shift;
   double r = fma(-kd, EXPT_L1, x);
   r = fma(-kd, EXPT_L2, r);
-  double a = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-  a = fma(a, r, 1.0 / 6.0);
+  double a = fma(r, 1.0 / 24.0, 1.0 / 6.0);
   a = fma(a, r, 0.5);
   a = fma(a, r, 1.0);
   const double p = a * r;
-  const int j = N & 63, k = N >> 6;
+  static_assert(EXPT_SIZE == 256, "k = N >> 8 below");
+  const int j = N & (EXPT_SIZE - 1), k = N >> 8;
   const double th = tab[2 * j], tl = tab[2 * j + 1];
-  const double s = th + fma(th, p, tl);
-  return s * __hiloint2double((k + 1023) << 20, 0);
+  const double s = th + fma(th, p, tl);  // in [0.998, 2.003): 2^k s stays normal for k >= -1021
+  return __hiloint2double(__double2hiint(s) + k * (1 << 20), __double2loint(s));
 }
 
 }  // namespace mag
