@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
         else mind2b = vb < mind2b ? vb : mind2b;
         if (WD || WDIST) dd = sqrt(v);
         if (WD) zd = kind ? fma(-t, dd, 1.0) : exp_neg(-t * dd, exptab);
-        if (WF) zf = WD ? (float)zd : (kind ? 1.0f - tf * sqrtf((float)v) : expf(-tf * sqrtf((float)v)));
+        if (WF) zf = WD ? f64_to_f32_nonneg(zd) : (kind ? 1.0f - tf * sqrtf((float)v) : expf(-tf * sqrtf((float)v)));
       }
       if (WF) Zf[tile_off + (int64_t)r * TILE + c] = zf;
       if (WD) Zd[tile_off + (int64_t)r * TILE + c] = zd;
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __rest
                                                             float* __restrict__ Zf, double* __restrict__ Zd,
                                                             double* __restrict__ rowsum, int kind) {
   __shared__ double exptab[2 * EXPT_SIZE];
-  __shared__ double colpart[8][TILE];
+  __shared__ float colpart[8][TILE];
   load_exp_table(exptab);
   __syncthreads();
   int64_t I, J;
@@ -180,11 +180,12 @@ __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __rest
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t off = tri_index(I, J) * TILE_ELEMS;
   const float tf = (float)t;
-  double cs[4] = {0.0, 0.0, 0.0, 0.0};
+  // row/column partial sums in FP32 (a norm; the FP64 pipe is the limit)
+  float cs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   for (int i = 0; i < 16; ++i) {
     const int r = warp * 16 + i;
     const int64_t gr = I * TILE + r;
-    double rs = 0.0;
+    float rs = 0.0f;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int c = lane + 32 * q;
@@ -195,28 +196,27 @@ __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __rest
       if (gr >= n || gc >= n || gr == gc) {
         zd = (gr == gc) ? 1.0 : 0.0;
         zf = (float)zd;
-        if (gr == gc && gr < n) rs += 1.0;  // the diagonal counts in its row sum
+        if (gr == gc && gr < n) rs += 1.0f;  // the diagonal counts in its row sum
       } else {
         const double d = Dd[e];
         zd = WD ? (kind ? fma(-t, d, 1.0) : exp_neg(-t * d, exptab)) : 0.0;
-        zf = WD ? (float)zd : (kind ? 1.0f - tf * (float)d : expf(-tf * (float)d));
-        const double z = WD ? zd : (double)zf;
-        rs += z;
-        cs[q] += z;
+        zf = WD ? f64_to_f32_nonneg(zd) : (kind ? 1.0f - tf * (float)d : expf(-tf * (float)d));
+        rs += zf;
+        cs[q] += zf;
       }
       if (WF) Zf[e] = zf;
       if (WD) Zd[e] = zd;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
-    if (lane == 0 && gr < n) atomicAdd(rowsum + gr, rs);
+    if (lane == 0 && gr < n) atomicAdd(rowsum + gr, (double)rs);
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) colpart[warp][lane + 32 * q] = cs[q];
   __syncthreads();
   if (I != J && threadIdx.x < TILE) {
     double v = 0.0;
-    for (int w = 0; w < 8; ++w) v += colpart[w][threadIdx.x];
+    for (int w = 0; w < 8; ++w) v += (double)colpart[w][threadIdx.x];
     const int64_t gc = J * TILE + threadIdx.x;
     if (gc < n) atomicAdd(rowsum + gc, v);
   }

@@ -47,4 +47,14 @@ __device__ __forceinline__ double exp_neg(double x, const double* tab) {
   return __hiloint2double(__double2hiint(s) + k * (1 << 20), __double2loint(s));
 }
 
+// x in [0, 2^128) to FP32, round to nearest even, on the integer pipe; values
+// below 2^-126 (FP32 subnormals) become 0.  Used for the FP32 copy of a Z
+// entry, whose role is the factor's input.
+__device__ __forceinline__ float f64_to_f32_nonneg(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  if ((b >> 52) < 1023 - 126) return 0.0f;
+  b += 0x0FFFFFFFull + ((b >> 29) & 1ull);  // round the 29 dropped bits, ties to even
+  return __uint_as_float((unsigned)(b >> 29) - ((1023u - 127u) << 23));
+}
+
 }  // namespace mag
