@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) k_batch_dist(const double* __restrict__ X
       const double d = P[i * c.m + l] - P[j * c.m + l];
       s = fma(d, d, s);
     }
-    out[q] = sqrt(s);
+    out[q] = sqrt_pos(s);
     if (!isfinite(s))
       flags |= 1;
     else if (s == 0.0)

@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
         if ((vb >> 52) >= 0x7ffull) flags |= ST_NONFINITE;
         else if (vb == 0ull) flags |= ST_DUPLICATE;
         else mind2b = vb < mind2b ? vb : mind2b;
-        if (WD || WDIST) dd = sqrt(v);
+        if (WD || WDIST) dd = sqrt_pos(v);
         if (WD) zd = kind ? fma(-t, dd, 1.0) : exp_neg(-t * dd, exptab);
         if (WF) zf = WD ? f64_to_f32_nonneg(zd) : (kind ? 1.0f - tf * sqrtf((float)v) : expf(-tf * sqrtf((float)v)));
       }

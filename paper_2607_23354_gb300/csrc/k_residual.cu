@@ -76,7 +76,8 @@ __global__ void __launch_bounds__(RES_THREADS) k_resid_mf(const double* __restri
           d2 = fma(diff, diff, d2);
         }
       }
-      const double z = kind ? fma(-t, sqrt(d2), 1.0) : exp_neg(-t * sqrt(d2), exptab);
+      const double dd = sqrt_pos(d2);
+      const double z = kind ? fma(-t, dd, 1.0) : exp_neg(-t * dd, exptab);
       zs += z;
       // Kahan step for s += z * w_k
       const double y = fma(z, wc[q], -c);
@@ -388,7 +389,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_grad(const double* __restrict__
           const double diff = xi[l] - xk[l];
           d2 = fma(diff, diff, d2);
         }
-      const double d = sqrt(d2);
+      const double d = sqrt_pos(d2);
       const double z = exp_neg(-t * d, exptab);
       // dL/dt contribution with Kahan compensation
       const double y = fma(li * d * z, wc[q], -st_c);

@@ -57,4 +57,33 @@ __device__ __forceinline__ float f64_to_f32_nonneg(double x) {
   return __uint_as_float((unsigned)(b >> 29) - ((1023u - 127u) << 23));
 }
 
+// sqrt(v) for v >= 0 by Markstein's method (P. Markstein, "Computation of
+// elementary functions on the IBM RISC System/6000 processor", IBM J. Res.
+// Dev. 34(1), 1990): y ~ 1/sqrt(v) from the FP32 reciprocal square root of
+// v's leading bits (|y sqrt(v) - 1| < 2^-20), s = v y, then two corrections
+// s += (y/2)(v - s^2) whose residual is exact with an FMA; each multiplies
+// the relative error by about that of y, leaving < 2^-60 before the final
+// rounding (within one unit in the last place).  Five FP64 operations; the
+// seed and its widening to FP64 run on the FP32 and integer pipes.  Outside
+// [2^-120, 2^120] (and for 0, inf, NaN) it defers to the library sqrt.
+__device__ __forceinline__ double sqrt_pos(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned e = (unsigned)(b >> 52);
+  if (e < 1023 - 120 || e > 1023 + 120) return sqrt(v);
+  // v's top 24 significand bits as an FP32 (truncated: a seed needs no rounding)
+  const float vf = __uint_as_float((unsigned)(b >> 29) - ((1023u - 127u) << 23));
+  const float yf = rsqrtf(vf);
+  const unsigned yb = __float_as_uint(yf);
+  // FP32 -> FP64 of a normal positive float on the integer pipe
+  const unsigned long long ywide =
+      ((unsigned long long)((yb >> 23) + (1023u - 127u)) << 52) | ((unsigned long long)(yb & 0x7fffffu) << 29);
+  const double y = __longlong_as_double((long long)ywide);
+  const double h = 0.5 * y;  // exact
+  double s = v * y;
+  double r = fma(-s, s, v);
+  s = fma(h, r, s);
+  r = fma(-s, s, v);
+  return fma(h, r, s);
+}
+
 }  // namespace mag
