@@ -56,6 +56,8 @@ def parse_args():
     p.add_argument("--paper-sweep", action="store_true",
                    help="instead of the headline step: the paper's runtime workload (t_+ and w(t_+) for "
                         "n in 1e3..3e4, m in 3..100, two covariances, 3 runs) with bisection and Ridders")
+    p.add_argument("--batch-only", action="store_true",
+                   help="instead of the headline step: time the batched solver (512 clouds in R^32 x 8 t)")
     p.add_argument("--cta-pairs", type=int, default=1,
                    help="CTA-pair (cta_group::2) tensor-core updates: 1 always, 0 never, 2 split precisions only")
     return p.parse_args()
@@ -448,6 +450,36 @@ def run_reference(a):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_batch_only(a):
+    """The batched solver alone: 512 clouds in R^32 (sizes log-uniform in
+    [64, 2048]) x 8 values of t, one persistent launch; warm-up, then a
+    device-timed run per step."""
+    import torch
+
+    import paper_2607_23354_gb300 as M
+    import workloads
+    torch.cuda.set_device(0)
+    ctx = M.Context(M.Options())
+    clouds, tvals = workloads.batch_clouds()
+    cl = [torch.from_numpy(c).cuda() for c in clouds]
+    for _ in range(max(1, a.warmup)):
+        ctx.solve_batch(cl, list(tvals))
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(a.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, _, sts = ctx.solve_batch(cl, list(tvals))
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    nsolves = len(cl) * len(tvals)
+    best = min(times)
+    return {"metric": "batch solves per second (512 clouds in R^32 x 8 t, rel. residual <= 1e-14)",
+            "value": nsolves / best, "unit": "solves/s", "seconds": times, "solves": nsolves,
+            "failed": int((sts != 0).sum()), "data": "synthetic"}
+
+
 def run_paper_sweep(a):
     """The paper's runtime workload: for every (n, m, covariance, run) the
     cutoff t_+ on [1e-3, bound] (rel. width 1e-6) and the weighting there, by
@@ -490,6 +522,9 @@ def main():
     a = parse_args()
     if a.paper_sweep:
         print(json.dumps(run_paper_sweep(a)), flush=True)
+        return
+    if a.batch_only:
+        print(json.dumps(run_batch_only(a)), flush=True)
         return
     if a.impl == "reference":
         out = run_reference(a)

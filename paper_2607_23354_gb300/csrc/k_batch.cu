@@ -274,16 +274,22 @@ __global__ void __launch_bounds__(BT, 1)
       continue;
     }
     const double* Dc = D + P.dist_offset;
-    // ---- Z: FP64 full square and FP32 lower
-    for (int64_t e = tid; e < (int64_t)n * n; e += BT) {
-      const int i = (int)(e / n), j = (int)(e % n);
-      double z = 1.0;
-      if (i != j) {
-        const int a = i > j ? i : j, b = i > j ? j : i;
-        z = exp_neg(-P.t * Dc[(int64_t)a * (a - 1) / 2 + b], exptab);
+    // ---- Z: FP64 full square and FP32 lower, one exp per pair j < i (warp
+    // per row, lanes along the row), mirrored into the upper triangle; the
+    // row sums of Z (for ||Z||inf) come with the first residual
+    double zmax_p = 0.0;
+    for (int i = warp; i < n; i += BT / 32) {
+      const double* Di = Dc + (int64_t)i * (i - 1) / 2;
+      for (int j = lane; j < i; j += 32) {
+        const double z = exp_neg(-P.t * Di[j], exptab);
+        S.Zd[(int64_t)i * n + j] = z;
+        S.Zd[(int64_t)j * n + i] = z;
+        S.Lf[(int64_t)i * n + j] = f64_to_f32_nonneg(z);
       }
-      S.Zd[e] = z;
-      if (j <= i) S.Lf[e] = (float)z;
+      if (lane == 0) {
+        S.Zd[(int64_t)i * n + i] = 1.0;
+        S.Lf[(int64_t)i * n + i] = 1.0f;
+      }
     }
     __syncthreads();
     int st = MAG_BATCH_OK;
@@ -297,21 +303,28 @@ __global__ void __launch_bounds__(BT, 1)
       double prev = INFINITY;
       int slow = 0;
       for (int it = 0;; ++it) {
-        // r = 1 - Z w (warp per row, Kahan per lane, TwoSum across lanes)
-        double rmax = 0.0, zmax = 0.0, wmax = 0.0;
+        // r = 1 - Z w (warp per row; per lane FMA chains of 16 terms whose
+        // sums are combined with Neumaier compensation, TwoSum across lanes)
+        double rmax = 0.0, wmax = 0.0;
         for (int i = warp; i < n; i += BT / 32) {
           const double* Zi = S.Zd + (int64_t)i * n;
-          double s = 0.0, c = 0.0, zs = 0.0;
-          for (int j = lane; j < n; j += 32) {
-            const double z = Zi[j];
-            zs += z;
-            const double y = fma(z, S.w[j], -c);
-            const double tt = s + y;
-            c = (tt - s) - y;
+          double s = 0.0, c = 0.0;
+          float zs = 0.0f;  // row sum of Z, first pass only (a norm: FP32 is ample)
+          for (int j0 = lane; j0 < n; j0 += 32 * 16) {
+            double part = 0.0;
+#pragma unroll 4
+            for (int q = 0; q < 16; ++q) {
+              const int j = j0 + 32 * q;
+              if (j < n) {
+                const double z = Zi[j];
+                part = fma(z, S.w[j], part);
+                if (it == 0) zs += (float)z;
+              }
+            }
+            const double tt = s + part;
+            c += fabs(s) >= fabs(part) ? (s - tt) + part : (part - tt) + s;
             s = tt;
           }
-          s -= c;
-          c = 0.0;
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) {
             double hi, lo;
@@ -320,17 +333,20 @@ __global__ void __launch_bounds__(BT, 1)
             two_sum_d(s, other, &hi, &lo);
             s = hi;
             c += oc + lo;
-            zs += __shfl_xor_sync(0xffffffffu, zs, o);
           }
           const double ri = (1.0 - s) - c;
           if (lane == 0) S.r[i] = ri;
           rmax = fmax(rmax, fabs(ri));
-          zmax = fmax(zmax, zs);
           wmax = fmax(wmax, fabs(S.w[i]));
+          if (it == 0) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) zs += __shfl_xor_sync(0xffffffffu, zs, o);
+            zmax_p = fmax(zmax_p, (double)zs);
+          }
         }
         if (lane == 0) {
           red[warp][0] = rmax;
-          red[warp][1] = zmax;
+          red[warp][1] = zmax_p;
           red[warp][2] = wmax;
         }
         __syncthreads();
