@@ -572,9 +572,15 @@ __device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
       : "memory");
 }
 
+// K chunks (128-byte rows) per stage: the one-product kinds take two, so that
+// every stage hand-off carries as much MMA work as a split stage.
+template <int MODE>
+constexpr int chunks2_of() {
+  return ModeCfg<MODE>::SPLIT ? 1 : 2;
+}
 template <int MODE>
 constexpr int stages2_of() {
-  return ModeCfg<MODE>::SPLIT ? 3 : 6;
+  return 3;  // x 64 KB
 }
 constexpr uint32_t TMEM_COLS2 = 512;  // two 128 x 256 FP32 accumulators per CTA
 constexpr int NACC2 = (int)(TMEM_COLS2 / 256);
@@ -588,12 +594,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
   constexpr int CHUNK_BYTES = Cfg::CHUNK;
   constexpr int HALF_BYTES = 128 * CHUNK_BYTES;           // 128 rows of one operand copy
   constexpr int OPS = Cfg::SPLIT ? 2 : 1;
-  constexpr int STAGE_BYTES = OPS * 2 * HALF_BYTES;        // A half + B half (x hi/lo)
+  constexpr int CPS = chunks2_of<MODE>();
+  constexpr int STAGE_BYTES = OPS * CPS * 2 * HALF_BYTES;  // A half + B half (x hi/lo or x chunks)
   constexpr int KSTEP_BYTES = 32;
   constexpr int KSTEPS = CHUNK_BYTES / KSTEP_BYTES;
   constexpr int ELEMS_PER_CHUNK = CHUNK_BYTES / Cfg::ELEM;
-  // stage layout: [A_hi | B_hi | A_lo | B_lo]
+  // stage layout: [A_hi | B_hi | A_lo | B_lo] for the split kinds,
+  // [A_c | B_c | A_c+1 | B_c+1] (two K chunks) for the one-product kinds
   constexpr int OFF_BHI = HALF_BYTES, OFF_ALO = 2 * HALF_BYTES, OFF_BLO = 3 * HALF_BYTES;
+  static_assert(OPS * CPS == 2, "64 KB stages");
 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -695,30 +704,29 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
         int64_t I, J;
         decode_task(q, p, &I, &J);
         const int ya = (int)((I + rank - p.k0) * TILE), yb = (int)((J + rank - p.k0) * TILE);
-        for (int c = chunk_lo; c < chunk_hi; ++c) {
+        for (int c = chunk_lo; c < chunk_hi; c += CPS) {
           if (!mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag, deadline)) {
             ok = false;
             break;
           }
           unsigned char* sbase = smem + stage * STAGE_BYTES;
           const int x = c * ELEMS_PER_CHUNK;
+          // second copy: the lo operands (split kinds) or the next K chunk
+          const CUtensorMap* m2 = Cfg::SPLIT ? &m_lo : &m_hi;
+          const int x2 = Cfg::SPLIT ? x : x + ELEMS_PER_CHUNK;
           if (rank == 0) {
             // rank 0's barrier counts the bytes of both CTAs' loads of this stage
             mbar_expect_tx(&full_bar[stage], 2 * STAGE_BYTES);
             tma_load_2d(sbase, &m_hi, &full_bar[stage], x, ya);
             tma_load_2d(sbase + OFF_BHI, &m_hi, &full_bar[stage], x, yb);
-            if (Cfg::SPLIT) {
-              tma_load_2d(sbase + OFF_ALO, &m_lo, &full_bar[stage], x, ya);
-              tma_load_2d(sbase + OFF_BLO, &m_lo, &full_bar[stage], x, yb);
-            }
+            tma_load_2d(sbase + OFF_ALO, m2, &full_bar[stage], x2, ya);
+            tma_load_2d(sbase + OFF_BLO, m2, &full_bar[stage], x2, yb);
           } else {
             const uint32_t bar = r0_full + stage * 8u;
             tma_load_2d_peer_bar(sbase, &m_hi, bar, x, ya);
             tma_load_2d_peer_bar(sbase + OFF_BHI, &m_hi, bar, x, yb);
-            if (Cfg::SPLIT) {
-              tma_load_2d_peer_bar(sbase + OFF_ALO, &m_lo, bar, x, ya);
-              tma_load_2d_peer_bar(sbase + OFF_BLO, &m_lo, bar, x, yb);
-            }
+            tma_load_2d_peer_bar(sbase + OFF_ALO, m2, bar, x2, ya);
+            tma_load_2d_peer_bar(sbase + OFF_BLO, m2, bar, x2, yb);
           }
           issued[stage] = true;
           issued_parity[stage] = phase;
@@ -759,7 +767,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
           if (!mbar_wait_cluster(&tempty_bar[acc], acc_phase ^ 1u, &abort_flag, deadline)) break;
           tc_fence_after();
           const uint32_t d = tmem_base + acc * 256u;
-          for (int c = chunk_lo; c < chunk_hi; ++c) {
+          for (int c = chunk_lo; c < chunk_hi; c += CPS) {
             if (!mbar_wait_cluster(&full_bar[stage], phase, &abort_flag, deadline)) {
               ok = false;
               break;
@@ -778,6 +786,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
                 mma2<MODE>(d, ahi, blo, 1u);
                 mma2<MODE>(d, alo, bhi, 1u);
               }
+            }
+            if (!Cfg::SPLIT) {
+#pragma unroll
+              for (int k = 0; k < KSTEPS; ++k)
+                mma2<MODE>(d, smem_desc<CHUNK_BYTES>(sb + OFF_ALO + k * KSTEP_BYTES),
+                           smem_desc<CHUNK_BYTES>(sb + OFF_BLO + k * KSTEP_BYTES), 1u);
             }
             mma_commit_pair(&empty_bar[stage]);  // stage of both CTAs free once read
             if (++stage == S) stage = 0, phase ^= 1u;
@@ -902,7 +916,7 @@ template <int MODE>
 cudaError_t launch_mode2(const UpdMaps& maps, const CMap& cmap, const UpdParams& p, int grid, cudaStream_t s) {
   constexpr int OPS = ModeCfg<MODE>::SPLIT ? 2 : 1;
   constexpr int CH = ModeCfg<MODE>::CHUNK;
-  const size_t smem = (size_t)stages2_of<MODE>() * OPS * 2 * 128 * CH + EPI_STAGING + 1024;
+  const size_t smem = (size_t)stages2_of<MODE>() * OPS * chunks2_of<MODE>() * 2 * 128 * CH + EPI_STAGING + 1024;
   auto kern = k_update_tc2<MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
