@@ -179,26 +179,37 @@ __global__ void __launch_bounds__(512) k_potrf_diag(T* __restrict__ Z, T* __rest
 
 // ------------------------------------------------- blocked potrf (FP32)
 // The same factor and inverse for the FP32 factor, organised in 32 x 32
-// blocks of the tile held in shared memory (A: the tile becoming L; Y: inv(L)):
+// blocks of the tile held in shared memory (A: the tile becoming L; Y: inv(L);
+// row stride LDB = 132 floats so that rows are 16-byte aligned for float4
+// loads):
 //   for kb = 0..3 (o = 32 kb):
 //     warp 0 factors the diagonal block A[o:o+32, o:o+32] with lane l owning
-//       row l (pivots and column entries exchanged by shuffles, no barrier),
-//       then inverts it (lane l forward-substitutes column l of the identity)
-//       into the diagonal block of Y;
+//       row l (pivots and column entries exchanged by shuffles, no barrier;
+//       1/sqrt of the pivot from rsqrtf), then inverts it (lane l forward-
+//       substitutes column l of the identity) into the diagonal block of Y;
 //     all warps: blocks below it, A_ib,kb <- A_ib,kb Yd_kb^T (panel solve);
 //     all warps: trailing blocks A_ib,jb -= A_ib,kb A_jb,kb^T (kb < jb <= ib).
 //   Off-diagonal blocks of Y by block diagonals d = ib - jb = 1, 2, 3:
 //     Y_ib,jb = -Yd_ib (sum_{kb=jb}^{ib-1} L_ib,kb Y_kb,jb).
-// 32 + 14 barriers instead of four per column.  A non-positive pivot raises
-// ST_NOTPD with its row (1-based, smallest wins) and is replaced by 1 so the
-// kernel finishes without NaNs.
-constexpr int PB = 32;  // block edge
+// The block products read four consecutive k per float4 (one shared-memory
+// wavefront serves the warp's broadcast operand).  A non-positive pivot
+// raises ST_NOTPD with its row (1-based, smallest wins) and is replaced by 1
+// so the kernel finishes without NaNs.
+constexpr int PB = 32;   // block edge
+constexpr int LDB = 132; // shared-memory row stride (floats), 16-byte aligned rows
+
+__device__ __forceinline__ float dot4(float4 a, float4 b, float acc) {
+  acc = fmaf(a.x, b.x, acc);
+  acc = fmaf(a.y, b.y, acc);
+  acc = fmaf(a.z, b.z, acc);
+  return fmaf(a.w, b.w, acc);
+}
 
 __global__ void __launch_bounds__(512, 1) k_potrf_blk(float* __restrict__ Z, float* __restrict__ Dinv,
-                                                   float* __restrict__ DinvT, int64_t K, DevStatus* st) {
-  extern __shared__ float psm[];
-  float* A = psm;                // [TILE][LDA]
-  float* Y = psm + TILE * LDA;   // [TILE][LDA]
+                                                      float* __restrict__ DinvT, int64_t K, DevStatus* st) {
+  extern __shared__ __align__(16) float psm[];
+  float* A = psm;                // [TILE][LDB]
+  float* Y = psm + TILE * LDB;   // [TILE][LDB]
   __shared__ float rdiag[TILE];  // 1 / L[i][i]
   __shared__ int skip;
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
@@ -206,7 +217,10 @@ __global__ void __launch_bounds__(512, 1) k_potrf_blk(float* __restrict__ Z, flo
   __syncthreads();
   if (skip) return;  // uniform across the CTA
   float* tile = Z + tri_index(K, K) * TILE_ELEMS;
-  for (int e = tid; e < TILE * TILE; e += 512) A[(e >> 7) * LDA + (e & 127)] = tile[e];
+  for (int e = tid; e < TILE * TILE / 4; e += 512) {
+    const int r = e >> 5, c = (e & 31) * 4;
+    *reinterpret_cast<float4*>(A + r * LDB + c) = reinterpret_cast<const float4*>(tile)[e];
+  }
   __syncthreads();
 
   for (int kb = 0; kb < TILE / PB; ++kb) {
@@ -214,7 +228,10 @@ __global__ void __launch_bounds__(512, 1) k_potrf_blk(float* __restrict__ Z, flo
     if (w == 0) {
       float d[PB];
 #pragma unroll
-      for (int j = 0; j < PB; ++j) d[j] = A[(o + l) * LDA + o + j];
+      for (int j = 0; j < PB; j += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(A + (o + l) * LDB + o + j);
+        d[j] = v.x, d[j + 1] = v.y, d[j + 2] = v.z, d[j + 3] = v.w;
+      }
 #pragma unroll
       for (int c = 0; c < PB; ++c) {
         const float piv = __shfl_sync(0xffffffffu, d[c], c);
@@ -223,31 +240,39 @@ __global__ void __launch_bounds__(512, 1) k_potrf_blk(float* __restrict__ Z, flo
           atomicOr(&st->flags, ST_NOTPD);
           atomicMin(&st->notpd_index, (int)(K * TILE + o + c + 1));
         }
-        const float sq = bad ? 1.f : sqrtf(piv);
-        const float rs = 1.f / sq;
-        const float lc = l > c ? d[c] * rs : (l == c ? sq : 0.f);
+        const float rs = bad ? 1.f : rsqrtf(piv);
+        const float lc = l > c ? d[c] * rs : (l == c ? (bad ? 1.f : piv * rs) : 0.f);
         d[c] = lc;
-        if (l == c) rdiag[o + c] = rs;
+        if (l == c) rdiag[o + c] = 1.f / lc;
 #pragma unroll
         for (int j = c + 1; j < PB; ++j) d[j] -= lc * __shfl_sync(0xffffffffu, lc, j);
       }
 #pragma unroll
-      for (int j = 0; j < PB; ++j) A[(o + l) * LDA + o + j] = j <= l ? d[j] : 0.f;
+      for (int j = 0; j < PB; j += 4)
+        *reinterpret_cast<float4*>(A + (o + l) * LDB + o + j) =
+            make_float4(j <= l ? d[j] : 0.f, j + 1 <= l ? d[j + 1] : 0.f, j + 2 <= l ? d[j + 2] : 0.f,
+                        j + 3 <= l ? d[j + 3] : 0.f);
       __syncwarp();
       // column l of inv(L_D): y_i = (e_l[i] - sum_{k<i} L[i][k] y_k) / L[i][i]
+      // (two partial sums per row for a shorter dependence chain)
       float y[PB];
 #pragma unroll
       for (int i = 0; i < PB; ++i) {
-        float acc = (i == l) ? 1.f : 0.f;
+        float a0 = (i == l) ? 1.f : 0.f, a1 = 0.f;
 #pragma unroll
-        for (int k = 0; k < i; ++k) acc -= A[(o + i) * LDA + o + k] * y[k];
-        y[i] = acc * rdiag[o + i];
+        for (int k = 0; k + 1 < i; k += 2) {
+          const float2 lk = *reinterpret_cast<const float2*>(A + (o + i) * LDB + o + k);
+          a0 -= lk.x * y[k];
+          a1 -= lk.y * y[k + 1];
+        }
+        if (i & 1) a0 -= A[(o + i) * LDB + o + i - 1] * y[i - 1];
+        y[i] = (a0 + a1) * rdiag[o + i];
       }
 #pragma unroll
-      for (int i = 0; i < PB; ++i) Y[(o + i) * LDA + o + l] = y[i];
+      for (int i = 0; i < PB; ++i) Y[(o + i) * LDB + o + l] = y[i];
     }
     __syncthreads();
-    // panel solve of the blocks below: X[r][c] = sum_k A[r][k] Yd[c][k]
+    // panel solve of the blocks below: X[r][c] = sum_k A[r][o+k] Yd[c][k]
     float xb[3][2];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
@@ -258,7 +283,9 @@ __global__ void __launch_bounds__(512, 1) k_potrf_blk(float* __restrict__ Z, flo
           const int r = ro + w + 16 * q;
           float acc = 0.f;
 #pragma unroll
-          for (int k = 0; k < PB; ++k) acc += A[r * LDA + o + k] * Y[(o + l) * LDA + o + k];
+          for (int k = 0; k < PB; k += 4)
+            acc = dot4(*reinterpret_cast<const float4*>(A + r * LDB + o + k),
+                       *reinterpret_cast<const float4*>(Y + (o + l) * LDB + o + k), acc);
           xb[b][q] = acc;
         }
       }
@@ -269,7 +296,7 @@ __global__ void __launch_bounds__(512, 1) k_potrf_blk(float* __restrict__ Z, flo
       const int ro = o + PB * (b + 1);
       if (ro < TILE) {
 #pragma unroll
-        for (int q = 0; q < 2; ++q) A[(ro + w + 16 * q) * LDA + o + l] = xb[b][q];
+        for (int q = 0; q < 2; ++q) A[(ro + w + 16 * q) * LDB + o + l] = xb[b][q];
       }
     }
     __syncthreads();
@@ -281,8 +308,10 @@ __global__ void __launch_bounds__(512, 1) k_potrf_blk(float* __restrict__ Z, flo
           const int r = ib * PB + w + 16 * q, c = jb * PB + l;
           float acc = 0.f;
 #pragma unroll
-          for (int k = 0; k < PB; ++k) acc += A[r * LDA + o + k] * A[c * LDA + o + k];
-          A[r * LDA + c] -= acc;
+          for (int k = 0; k < PB; k += 4)
+            acc = dot4(*reinterpret_cast<const float4*>(A + r * LDB + o + k),
+                       *reinterpret_cast<const float4*>(A + c * LDB + o + k), acc);
+          A[r * LDB + c] -= acc;
         }
       }
     __syncthreads();
@@ -301,7 +330,14 @@ __global__ void __launch_bounds__(512, 1) k_potrf_blk(float* __restrict__ Z, flo
           float acc = 0.f;
           for (int kb = jb; kb < ib; ++kb) {
 #pragma unroll
-            for (int k = 0; k < PB; ++k) acc += A[r * LDA + kb * PB + k] * Y[(kb * PB + k) * LDA + c];
+            for (int k = 0; k < PB; k += 4) {
+              const float4 lr = *reinterpret_cast<const float4*>(A + r * LDB + kb * PB + k);
+              const float* yc = Y + (kb * PB + k) * LDB + c;
+              acc = fmaf(lr.x, yc[0], acc);
+              acc = fmaf(lr.y, yc[LDB], acc);
+              acc = fmaf(lr.z, yc[2 * LDB], acc);
+              acc = fmaf(lr.w, yc[3 * LDB], acc);
+            }
           }
           tv[jb][q] = acc;
         }
@@ -312,7 +348,7 @@ __global__ void __launch_bounds__(512, 1) k_potrf_blk(float* __restrict__ Z, flo
       const int ib = jb + dd;
       if (ib < TILE / PB) {
 #pragma unroll
-        for (int q = 0; q < 2; ++q) Y[(ib * PB + w + 16 * q) * LDA + jb * PB + l] = tv[jb][q];
+        for (int q = 0; q < 2; ++q) Y[(ib * PB + w + 16 * q) * LDB + jb * PB + l] = tv[jb][q];
       }
     }
     __syncthreads();
@@ -325,7 +361,14 @@ __global__ void __launch_bounds__(512, 1) k_potrf_blk(float* __restrict__ Z, flo
           const int r = ib * PB + w + 16 * q, c = jb * PB + l;
           float acc = 0.f;
 #pragma unroll
-          for (int k = 0; k < PB; ++k) acc += Y[r * LDA + ib * PB + k] * Y[(ib * PB + k) * LDA + c];
+          for (int k = 0; k < PB; k += 4) {
+            const float4 yr = *reinterpret_cast<const float4*>(Y + r * LDB + ib * PB + k);
+            const float* tc = Y + (ib * PB + k) * LDB + c;
+            acc = fmaf(yr.x, tc[0], acc);
+            acc = fmaf(yr.y, tc[LDB], acc);
+            acc = fmaf(yr.z, tc[2 * LDB], acc);
+            acc = fmaf(yr.w, tc[3 * LDB], acc);
+          }
           tv[jb][q] = -acc;
         }
       }
@@ -336,7 +379,7 @@ __global__ void __launch_bounds__(512, 1) k_potrf_blk(float* __restrict__ Z, flo
       const int ib = jb + dd;
       if (ib < TILE / PB) {
 #pragma unroll
-        for (int q = 0; q < 2; ++q) Y[(ib * PB + w + 16 * q) * LDA + jb * PB + l] = tv[jb][q];
+        for (int q = 0; q < 2; ++q) Y[(ib * PB + w + 16 * q) * LDB + jb * PB + l] = tv[jb][q];
       }
     }
     __syncthreads();
@@ -346,9 +389,9 @@ __global__ void __launch_bounds__(512, 1) k_potrf_blk(float* __restrict__ Z, flo
   float* YTg = DinvT + K * TILE_ELEMS;
   for (int e = tid; e < TILE * TILE; e += 512) {
     const int r = e >> 7, c = e & 127;
-    tile[e] = c <= r ? A[r * LDA + c] : 0.f;
-    Yg[e] = c <= r ? Y[r * LDA + c] : 0.f;
-    YTg[e] = r <= c ? Y[c * LDA + r] : 0.f;
+    tile[e] = c <= r ? A[r * LDB + c] : 0.f;
+    Yg[e] = c <= r ? Y[r * LDB + c] : 0.f;
+    YTg[e] = r <= c ? Y[c * LDB + r] : 0.f;
   }
 }
 
@@ -589,7 +632,7 @@ cudaError_t launch_potrf_diag(T* Z, T* Dinv, int64_t K, int64_t n, DevStatus* st
   const int64_t N = (n + TILE - 1) / TILE;
   // Dinv holds N tiles of inv(L_KK) followed by N tiles of inv(L_KK)^T.
   if constexpr (sizeof(T) == 4) {
-    const size_t smem = (size_t)2 * TILE * LDA * sizeof(float);
+    const size_t smem = (size_t)2 * TILE * LDB * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_potrf_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_potrf_blk<<<1, 512, smem, s>>>(Z, Dinv, Dinv + N * TILE_ELEMS, K, st);
