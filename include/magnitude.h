@@ -81,7 +81,8 @@ typedef struct mag_options {
   int32_t ir_max_iters;   /* refinement steps before escalating, default 12     */
   int32_t gmres_max_iters;/* inner GMRES iterations of GMRES-IR, default 30     */
   int32_t allow_fallback; /* 1: escalate to GMRES-IR then FP64 factor (default)  */
-  int32_t panel_tiles;    /* outer panel width in 128-wide tiles (0 = 16)       */
+  int32_t panel_tiles;    /* outer panel width in 128-wide tiles (0: 16 for the
+                             split precisions, 24 for one-product factors)     */
   double workspace_limit_bytes; /* 0 = no limit; larger requests give ENOMEM     */
   int32_t profile;        /* 1: time the trailing-update kernel with CUDA events */
   int32_t reuse_distances;/* 1 (default): inside one mag_solve_multi or
@@ -94,7 +95,8 @@ typedef struct mag_options {
                              trailing update of the current panel; 0: one
                              stream, step after step (same arithmetic)        */
   int32_t lookahead_sms;  /* SMs kept free of the trailing update for the
-                             panel stream (0 = default 16)                    */
+                             panel stream (0: 16 for the split precisions,
+                             32 for one-product factors)                      */
   int32_t cta_pairs;      /* tensor-core updates on clusters of two CTAs
                              sharing each 256 x 256 MMA (cta_group::2):
                              1 (default) always, 0 never, 2 for the split

@@ -53,7 +53,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))
         for cmd, res in zip(jobs, results):
-            if verbose or res.returncode != 0:
+            if verbose or res.returncode != 0 or "warning" in res.stderr.lower():
                 print(" ".join(cmd))
                 print(res.stdout + res.stderr)
             if res.returncode != 0:

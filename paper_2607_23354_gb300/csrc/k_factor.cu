@@ -28,8 +28,6 @@ namespace {
 template <typename T>
 __device__ inline T tsqrt(T x);
 template <>
-__device__ inline float tsqrt<float>(float x) { return sqrtf(x); }
-template <>
 __device__ inline double tsqrt<double>(double x) { return sqrt(x); }
 
 constexpr int LDA = TILE + 1;  // padded shared-memory row stride

@@ -24,9 +24,6 @@ namespace {
 constexpr int GEN_THREADS = 512;
 constexpr int GEN_MC = 32;  // coordinates staged per chunk
 
-__device__ inline void atomic_min_nonneg(unsigned long long* a, double v) {
-  atomicMin(a, (unsigned long long)__double_as_longlong(v));
-}
 __device__ inline void atomic_max_nonneg(unsigned long long* a, double v) {
   atomicMax(a, (unsigned long long)__double_as_longlong(v));
 }

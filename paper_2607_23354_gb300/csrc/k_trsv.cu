@@ -90,7 +90,7 @@ struct Vec4<float> {
 };
 template <>
 struct Vec4<double> {
-  using type = double4;
+  using type = double4_16a;
 };
 
 template <typename T>
@@ -104,10 +104,10 @@ __device__ __forceinline__ float4 ldv_cg<float>(const float* p) {
   return __ldcg(reinterpret_cast<const float4*>(p));
 }
 template <>
-__device__ __forceinline__ double4 ldv_cg<double>(const double* p) {
+__device__ __forceinline__ double4_16a ldv_cg<double>(const double* p) {
   const double2 a = __ldcg(reinterpret_cast<const double2*>(p));
   const double2 b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
-  return make_double4(a.x, a.y, b.x, b.y);
+  return make_double4_16a(a.x, a.y, b.x, b.y);
 }
 
 // Forward: thread (warp w, lane l) covers tile rows w*32 + i, columns 4l..4l+3.

@@ -17,6 +17,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -36,8 +37,8 @@ struct Layout {
   size_t off_zf = 0, off_zd = 0, off_dinvf = 0, off_dinvd = 0, off_vec = 0, off_part = 0,
          off_status = 0, off_panel = 0, off_flags = 0, off_spart = 0, off_dist = 0, off_ctr = 0, total = 0;
   bool dist = false;   // FP64 distance tiles present
-  int nb = 8;          // panel width in tiles
-  int64_t W = 0;       // panel width in columns (nb * TILE)
+  int nb = 24;         // panel buffer capacity in tiles (the widest panel a factor may use)
+  int64_t W = 0;       // panel buffer row length in columns (nb * TILE)
   int64_t nctr = 0;    // task counters of the tensor-core update launches of one factor
 };
 
@@ -82,11 +83,14 @@ struct mag_ctx {
   CMap cmap;                         // TMA descriptor of the FP32 tiles (update epilogue)
   const void* cmap_base = nullptr;
   int64_t cmap_tiles = 0;
-  uint32_t* tasks_d = nullptr;       // task tables of the update launches of one factor
-  size_t tasks_cap = 0;
-  int64_t tasks_N = -1;
-  int tasks_nb = -1, tasks_la = -1, tasks_pairs = -1;
-  std::map<std::pair<int64_t, int64_t>, std::pair<int64_t, int64_t>> task_rng;  // (j0, j1) -> (offset, count)
+  // task tables of the update launches of one factor, per (N, panel width,
+  // look-ahead, CTA pairs): device table and (j0, j1) -> (offset, count)
+  struct TaskTable {
+    uint32_t* d = nullptr;
+    std::map<std::pair<int64_t, int64_t>, std::pair<int64_t, int64_t>> rng;
+  };
+  std::map<std::tuple<int64_t, int, int, int>, TaskTable> task_tables;
+  TaskTable* tasks = nullptr;        // the table of the factor in progress
   cudaStream_t side = nullptr;       // panel stream of the look-ahead factor
   int kind = MAT_EXP;                // matrix the solve path generates (MatKind)
   cudaEvent_t ev_la[3] = {nullptr, nullptr, nullptr};  // start, panel done, trailing done
@@ -180,7 +184,9 @@ Layout plan(const mag_ctx* ctx, int64_t n, bool f32, bool f64, bool dist = false
   L.dist = dist;
   L.off_dist = off;  // placed before every precision-dependent region: stable offset
   if (dist) off = align_up(off + (size_t)L.tiles * TILE_ELEMS * sizeof(double));
-  L.nb = ctx->opt.panel_tiles > 0 ? ctx->opt.panel_tiles : 16;
+  // panel buffers sized for the widest default panel, so that factors of
+  // different precisions in one call share the workspace
+  L.nb = ctx->opt.panel_tiles > 0 ? ctx->opt.panel_tiles : 24;
   L.W = (int64_t)L.nb * TILE;
   L.off_panel = off;
   // two panel buffers (hi + lo copies each): the next panel is written while
@@ -358,20 +364,24 @@ int upd_mode(int prec) {
 // of the remaining panel columns; then one tensor-core update of the whole
 // trailing matrix with K = (k1 - k0) * 128.
 // Task tables of every tensor-core update launch of one factor with the
-// current layout (built on the host once per (N, panel width, schedule)).
-int ensure_tasks(mag_ctx* ctx, bool la, bool pairs) {
+// current N, panel width nb and schedule (built on the host once and kept).
+int ensure_tasks(mag_ctx* ctx, int nb, bool la, bool pairs) {
   const Layout& L = ctx->lay;
-  if (ctx->tasks_N == L.N && ctx->tasks_nb == L.nb && ctx->tasks_la == (int)la && ctx->tasks_pairs == (int)pairs)
+  const auto key = std::make_tuple(L.N, nb, (int)la, (int)pairs);
+  auto found = ctx->task_tables.find(key);
+  if (found != ctx->task_tables.end()) {
+    ctx->tasks = &found->second;
     return MAG_OK;
+  }
   if (L.N >= 65536) return fail(ctx, MAG_EINVAL, "n = %lld too large for the tensor-core factor", (long long)L.n);
   std::vector<uint32_t> t;
-  ctx->task_rng.clear();
+  mag_ctx::TaskTable tab;
   auto add = [&](int64_t j0, int64_t j1) {
-    const auto key = std::make_pair(j0, j1);
-    if (j0 >= j1 || ctx->task_rng.count(key)) return;
+    const auto k = std::make_pair(j0, j1);
+    if (j0 >= j1 || tab.rng.count(k)) return;
     const int64_t off = (int64_t)t.size();
     const int64_t cnt = update_tasks(L.N, j0, j1, pairs, &t);
-    ctx->task_rng[key] = std::make_pair(off, cnt);
+    tab.rng[k] = std::make_pair(off, cnt);
   };
   // the in-panel updates of the recursive panel factor (tc_panel_range)
   std::function<void(int64_t, int64_t)> panel = [&](int64_t a, int64_t b) {
@@ -381,8 +391,8 @@ int ensure_tasks(mag_ctx* ctx, bool la, bool pairs) {
     add(mid, b);
     panel(mid, b);
   };
-  for (int64_t k0 = 0; k0 < L.N; k0 += L.nb) {
-    const int64_t k1 = std::min<int64_t>(L.N, k0 + L.nb), k2 = std::min<int64_t>(L.N, k1 + L.nb);
+  for (int64_t k0 = 0; k0 < L.N; k0 += nb) {
+    const int64_t k1 = std::min<int64_t>(L.N, k0 + nb), k2 = std::min<int64_t>(L.N, k1 + nb);
     panel(k0, k1);
     if (la) {
       add(k1, k2);
@@ -391,24 +401,20 @@ int ensure_tasks(mag_ctx* ctx, bool la, bool pairs) {
       add(k1, L.N);
     }
   }
-  CU(cudaStreamSynchronize(ctx->stream));  // a previous factor may still read the old table
-  if (t.size() > ctx->tasks_cap) {
-    if (ctx->tasks_d) cudaFree(ctx->tasks_d);
-    ctx->tasks_d = nullptr;
-    ctx->tasks_cap = 0;
-    cudaError_t e = cudaMalloc((void**)&ctx->tasks_d, std::max<size_t>(1, t.size()) * sizeof(uint32_t));
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      ctx->tasks_d = nullptr;
-      return fail(ctx, MAG_ENOMEM, "cudaMalloc(task table) failed: %s", cudaGetErrorString(e));
-    }
-    ctx->tasks_cap = std::max<size_t>(1, t.size());
+  cudaError_t e = cudaMalloc((void**)&tab.d, std::max<size_t>(1, t.size()) * sizeof(uint32_t));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, MAG_ENOMEM, "cudaMalloc(task table) failed: %s", cudaGetErrorString(e));
   }
-  if (!t.empty()) CU(cudaMemcpy(ctx->tasks_d, t.data(), t.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
-  ctx->tasks_N = L.N;
-  ctx->tasks_nb = L.nb;
-  ctx->tasks_la = (int)la;
-  ctx->tasks_pairs = (int)pairs;
+  if (!t.empty()) {
+    e = cudaMemcpy(tab.d, t.data(), t.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(tab.d);
+      return fail(ctx, MAG_ECUDA, "task table upload: %s", cudaGetErrorString(e));
+    }
+  }
+  auto ins = ctx->task_tables.emplace(key, std::move(tab));
+  ctx->tasks = &ins.first->second;
   return MAG_OK;
 }
 
@@ -431,6 +437,7 @@ struct TcFactor {
   mag_ctx* ctx;
   int mode;
   bool pairs;
+  int nb;  // panel width in tiles of this factor
   int* launches;
   double* flops;
   int64_t next_ctr;
@@ -442,8 +449,8 @@ int tc_update(TcFactor& F, int b, int64_t k0, int kc_lo, int kc_hi, int64_t j0, 
               cudaStream_t st, int cat) {
   mag_ctx* ctx = F.ctx;
   const Layout& L = ctx->lay;
-  auto it = ctx->task_rng.find(std::make_pair(j0, j1));
-  if (it == ctx->task_rng.end() || it->second.second == 0) return MAG_OK;
+  auto it = ctx->tasks->rng.find(std::make_pair(j0, j1));
+  if (it == ctx->tasks->rng.end() || it->second.second == 0) return MAG_OK;
   if (F.next_ctr >= L.nctr) return fail(ctx, MAG_ECUDA, "update launch counters exhausted");
   UpdParams up;
   std::memset(&up, 0, sizeof up);
@@ -453,7 +460,7 @@ int tc_update(TcFactor& F, int b, int64_t k0, int kc_lo, int kc_hi, int64_t j0, 
   up.kc_lo = kc_lo;
   up.kc_hi = kc_hi;
   up.j1 = j1;
-  up.tasks = ctx->tasks_d + it->second.first;
+  up.tasks = ctx->tasks->d + it->second.first;
   up.ntasks = it->second.second;
   up.counter = ctx->counters() + F.next_ctr++;
   up.st = ctx->st();
@@ -499,7 +506,7 @@ int tc_panel_range(TcFactor& F, int64_t k0, int64_t a, int64_t b, int buf, cudaS
 
 // The panel of tile columns [k0, min(N, k0 + nb)) into panel buffer b.
 int tc_panel(TcFactor& F, int64_t k0, int b, cudaStream_t st) {
-  const int64_t k1 = std::min<int64_t>(F.ctx->lay.N, k0 + F.ctx->lay.nb);
+  const int64_t k1 = std::min<int64_t>(F.ctx->lay.N, k0 + F.nb);
   return tc_panel_range(F, k0, k0, k1, b, st);
 }
 
@@ -512,11 +519,14 @@ int tc_panel(TcFactor& F, int64_t k0, int b, cudaStream_t st) {
 int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
   const Layout& L = ctx->lay;
   cudaStream_t s = ctx->stream;
-  const int64_t npanels = (L.N + L.nb - 1) / L.nb;
-  const bool la = ctx->opt.lookahead != 0 && npanels > 2;
   const bool split = mode == UPD_FP16X3 || mode == UPD_TF32X3;
+  // panel width and panel-stream SMs by product count (measured at n = 1e5):
+  // one-product updates are short, so wider panels and a larger panel share
+  const int nb = std::max(1, std::min(L.nb, ctx->opt.panel_tiles > 0 ? ctx->opt.panel_tiles : (split ? 16 : 24)));
+  const int64_t npanels = (L.N + nb - 1) / nb;
+  const bool la = ctx->opt.lookahead != 0 && npanels > 2;
   const bool pairs = ctx->opt.cta_pairs == 1 || (ctx->opt.cta_pairs == 2 && split);
-  TRY(ensure_tasks(ctx, la, pairs));
+  TRY(ensure_tasks(ctx, nb, la, pairs));
   TRY(ensure_maps(ctx, mode, 0));
   TRY(ensure_maps(ctx, mode, 1));
   if (ctx->cmap_base != ctx->zf() || ctx->cmap_tiles != L.tiles) {
@@ -526,10 +536,10 @@ int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
     ctx->cmap_tiles = L.tiles;
   }
   CU(cudaMemsetAsync(ctx->counters(), 0, (size_t)L.nctr * sizeof(unsigned), s));
-  TcFactor F{ctx, mode, pairs, launches, flops, 0};
+  TcFactor F{ctx, mode, pairs, nb, launches, flops, 0};
   if (!la) {
-    for (int64_t k0 = 0; k0 < L.N; k0 += L.nb) {
-      const int64_t k1 = std::min<int64_t>(L.N, k0 + L.nb);
+    for (int64_t k0 = 0; k0 < L.N; k0 += nb) {
+      const int64_t k1 = std::min<int64_t>(L.N, k0 + nb);
       TRY(tc_panel(F, k0, 0, s));
       if (k1 < L.N) TRY(tc_update(F, 0, k0, 0, (int)(k1 - k0), k1, L.N, ctx->sm_count, s, PC_UPDATE));
     }
@@ -541,17 +551,17 @@ int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
   }
   cudaStream_t side = ctx->side;
   cudaEvent_t ev_start = ctx->ev_la[0], ev_panel = ctx->ev_la[1], ev_trail = ctx->ev_la[2];
-  const int reserve = ctx->opt.lookahead_sms > 0 ? ctx->opt.lookahead_sms : 16;
+  const int reserve = ctx->opt.lookahead_sms > 0 ? ctx->opt.lookahead_sms : (split ? 16 : 32);
   const int trail_grid = std::max(1, ctx->sm_count - reserve);
   CU(cudaEventRecord(ev_start, s));
   CU(cudaStreamWaitEvent(side, ev_start, 0));
   TRY(tc_panel(F, 0, 0, side));
   CU(cudaEventRecord(ev_panel, side));
   int64_t p = 0;
-  for (int64_t k0 = 0;; k0 += L.nb, ++p) {
-    const int64_t k1 = std::min<int64_t>(L.N, k0 + L.nb);
+  for (int64_t k0 = 0;; k0 += nb, ++p) {
+    const int64_t k1 = std::min<int64_t>(L.N, k0 + nb);
     if (k1 >= L.N) break;
-    const int64_t k2 = std::min<int64_t>(L.N, k1 + L.nb);
+    const int64_t k2 = std::min<int64_t>(L.N, k1 + nb);
     const int b = (int)(p & 1);
     CU(cudaStreamWaitEvent(s, ev_panel, 0));  // panel p factored and copied
     // panel stream: next panel's columns, then the next panel itself
@@ -646,7 +656,8 @@ int mag_ctx_destroy(mag_ctx* ctx) {
   if (ctx->aux) cudaFree(ctx->aux);
   if (ctx->bws) cudaFree(ctx->bws);
   if (ctx->gm) cudaFree(ctx->gm);
-  if (ctx->tasks_d) cudaFree(ctx->tasks_d);
+  for (auto& kv : ctx->task_tables)
+    if (kv.second.d) cudaFree(kv.second.d);
   if (ctx->side) {
     cudaStreamSynchronize(ctx->side);
     cudaStreamDestroy(ctx->side);
