@@ -1580,24 +1580,7 @@ int mag_solve_batch(mag_ctx* ctx, const mag_batch_desc* desc, int32_t count, con
     CU(launch_batch_dist(points, d_cl, (int)clouds.size(), max_pairs, d_D, d_cf, s));
     const double tol = kStopMargin * ctx->opt.ir_tol;
     const int max_iter = std::max(ctx->opt.ir_max_iters, 1);
-    if (ctx->batch_block == 0) {
-      // tuner: time both factor block sizes on a sample of mid-sized problems
-      const int ns = std::min<int>((int)small.size(), 2 * grid);
-      const int start = std::max<int>(0, (int)small.size() / 2 - ns / 2);
-      float best = 1e30f;
-      int best_b = 64;
-      for (int b : {32, 64}) {
-        CU(cudaMemsetAsync(d_q, 0, sizeof(int), s));
-        CU(cudaEventRecord(ctx->ev[0], s));
-        CU(launch_batch_solve(b, d_pr, d_or + start, ns, d_D, d_cf, d_sf, d_sd, nmax, w_out, mag_out, d_st, d_q,
-                              tol, max_iter, grid, s));
-        CU(cudaEventRecord(ctx->ev[1], s));
-        CU(cudaEventSynchronize(ctx->ev[1]));
-        const float ms = elapsed(ctx, 0, 1);
-        if (ms < best) best = ms, best_b = b;
-      }
-      ctx->batch_block = best_b;
-    }
+    ctx->batch_block = 64;  // factor block of the batched Cholesky
     CU(cudaMemsetAsync(d_q, 0, sizeof(int), s));
     CU(cudaMemsetAsync(d_st, 0, (size_t)count * sizeof(int), s));
     CU(launch_batch_solve(ctx->batch_block, d_pr, d_or, (int)small.size(), d_D, d_cf, d_sf, d_sd, nmax, w_out,
