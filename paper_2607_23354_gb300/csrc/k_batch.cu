@@ -198,9 +198,13 @@ __device__ bool cta_cholesky(float* A, int n, float* sm, int* flag) {
   return true;
 }
 
-// v <- (L L^T)^{-1} v with the FP32 factor (blocked; block solves by warp 0).
+// v <- (L L^T)^{-1} v with the FP32 factor (blocked).  The diagonal block
+// solves run in warp 0 column by column: lane l holds rows l and l + 32 of the
+// block's right-hand side; each step divides the pivot row, broadcasts the
+// solved unknown by a shuffle and updates the lanes' remaining rows.
 template <int B>
 __device__ void cta_solve(const float* L, int n, float* v, float* sm) {
+  static_assert(B == 64, "two rows per lane");
   float* blk = sm;  // [B] block values
   const int tid = threadIdx.x;
   const int nb = (n + B - 1) / B;
@@ -209,15 +213,22 @@ __device__ void cta_solve(const float* L, int n, float* v, float* sm) {
     const int k0 = kb * B, kw = min(B, n - k0);
     __syncthreads();
     if (tid < 32) {
-      for (int r = 0; r < kw; ++r) {
-        const float* Lr = L + (int64_t)(k0 + r) * n + k0;
-        float s = 0.0f;
-        for (int c = tid; c < r; c += 32) s += Lr[c] * blk[c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (tid == 0) blk[r] = (v[k0 + r] - s) / Lr[r];
-        __syncwarp();
+      const int r0 = tid, r1 = tid + 32;
+      float y0 = r0 < kw ? v[k0 + r0] : 0.0f, y1 = r1 < kw ? v[k0 + r1] : 0.0f;
+      const float* L0 = L + (int64_t)(k0 + r0) * n + k0;
+      const float* L1 = L + (int64_t)(k0 + r1) * n + k0;
+      for (int c = 0; c < kw; ++c) {
+        // the owner of row c finishes it, then every lane eliminates it
+        const float own = c < 32 ? y0 : y1;
+        float xc = __shfl_sync(0xffffffffu, own, c & 31);
+        xc /= L[(int64_t)(k0 + c) * n + k0 + c];
+        if (r0 == c) y0 = xc;
+        if (r1 == c) y1 = xc;
+        if (r0 > c && r0 < kw) y0 -= L0[c] * xc;
+        if (r1 > c && r1 < kw) y1 -= L1[c] * xc;
       }
+      if (r0 < kw) blk[r0] = y0;
+      if (r1 < kw) blk[r1] = y1;
     }
     __syncthreads();
     for (int e = tid; e < kw; e += BT) v[k0 + e] = blk[e];
@@ -233,14 +244,20 @@ __device__ void cta_solve(const float* L, int n, float* v, float* sm) {
     const int k0 = kb * B, kw = min(B, n - k0);
     __syncthreads();
     if (tid < 32) {
-      for (int r = kw - 1; r >= 0; --r) {
-        float s = 0.0f;
-        for (int c = r + 1 + tid; c < kw; c += 32) s += L[(int64_t)(k0 + c) * n + k0 + r] * blk[c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (tid == 0) blk[r] = (v[k0 + r] - s) / L[(int64_t)(k0 + r) * n + k0 + r];
-        __syncwarp();
+      const int r0 = tid, r1 = tid + 32;
+      float x0 = r0 < kw ? v[k0 + r0] : 0.0f, x1 = r1 < kw ? v[k0 + r1] : 0.0f;
+      for (int c = kw - 1; c >= 0; --c) {
+        const float own = c < 32 ? x0 : x1;
+        float xc = __shfl_sync(0xffffffffu, own, c & 31);
+        const float* Lc = L + (int64_t)(k0 + c) * n + k0;  // row c: L[c][r] for r < c
+        xc /= Lc[c];
+        if (r0 == c) x0 = xc;
+        if (r1 == c) x1 = xc;
+        if (r0 < c) x0 -= Lc[r0] * xc;
+        if (r1 < c) x1 -= Lc[r1] * xc;
       }
+      if (r0 < kw) blk[r0] = x0;
+      if (r1 < kw) blk[r1] = x1;
     }
     __syncthreads();
     for (int e = tid; e < kw; e += BT) v[k0 + e] = blk[e];
