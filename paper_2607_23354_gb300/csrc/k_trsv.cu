@@ -203,11 +203,12 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_backward_persistent(const T* 
         known = warp_wait_progress(progress, need, deadline, &abort_flag);
         if (!known) break;
       }
-      const T* xj = x + J * TILE + w * 32;
+      // lane l holds x_J[32 w + l]; row i's value comes by shuffle
+      const T xl = __ldcg(x + J * TILE + w * 32 + l);
 #pragma unroll 8
       for (int i = 0; i < 32; ++i) {
         const auto a = ldv<T>(tile + (int64_t)i * TILE);
-        const T xi = __ldcg(xj + i);
+        const T xi = __shfl_sync(0xffffffffu, xl, i);
         p0 += a.x * xi;
         p1 += a.y * xi;
         p2 += a.z * xi;
