@@ -262,6 +262,7 @@ def run_ours(a):
                   "ir_iters": i["ir_iters"], "precision_used": i["precision_used"], "fallback": i["fallback"],
                   "ms_generate": i["ms_generate"], "ms_factor": i["ms_factor"], "ms_solve": i["ms_solve"],
                   "ms_residual": i["ms_residual"], "residual_evals": i["residual_evals"],
+                  "probe_rho": i["probe_rho"], "ms_probe": i["ms_probe"],
                   "ms_factor_parts": {"update_trailing": i["ms_update"] - i["ms_update_panel"],
                                       "update_panel": i["ms_update_panel"], "potrf": i["ms_potrf"],
                                       "trsm": i["ms_trsm"], "split": i["ms_split"]}} for t, mag, i in last]
@@ -296,11 +297,13 @@ def run_ours(a):
         split = (M.PREC_FP16X3, M.PREC_TF32X3)
         exec_flops = sum(i["update_flops"] * (3 if i["precision_used"] in split else 1) for _, _, i in infos)
         executed = exec_flops / (upd_ms / 1e3) / 1e12 if upd_ms else None
-        trec = ncu_traffic(kname)
+        # bytes per algorithmic flop of each precision's launches (ncu records of
+        # smaller captures) x this run's flops of that precision, per launch
+        trec = {M.PREC_FP16X3: ncu_traffic(kname), M.PREC_FP16: ncu_traffic(kname + "_fp16")}
         traffic = None
-        if trec and upd_launch:
-            # bytes per algorithmic flop from a smaller capture x this run's flops per launch
-            traffic = trec["bytes_per_flop"] * upd_flops / upd_launch
+        if upd_launch and all(trec.get(i["precision_used"]) for _, _, i in infos if i["update_flops"]):
+            traffic = sum(trec[i["precision_used"]]["bytes_per_flop"] * i["update_flops"]
+                          for _, _, i in infos if i["update_flops"]) / upd_launch
         roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                     "kernel": kname, "launches": upd_launch, "avg_launch_ms": upd_ms / max(upd_launch, 1),

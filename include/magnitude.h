@@ -53,8 +53,14 @@ enum mag_status {
 
 /* Precision of the Cholesky factor (Zw = 1 is always refined in FP64). */
 enum mag_precision {
-  MAG_PREC_AUTO = 0,     /* FP16 if the Gershgorin bound gives lambda_min(Z) >= 1/2,
-                            else FP16X3                                       */
+  MAG_PREC_AUTO = 0,     /* FP16 if the Gershgorin bound gives lambda_min(Z) >= 1/2;
+                            else (n >= 384 K, K = panel width in tiles) FP16
+                            when a probe (FP16 factor + two refinement steps
+                            on the leading 128 K points) predicts that its
+                            extra refinement steps cost less than the factor
+                            time saved; else FP16X3.  A mispredicted FP16
+                            factor that refines slowly is replaced by FP16X3
+                            (mag_info.fallback = 3).                        */
   MAG_PREC_BF16 = 1,     /* BF16 tensor-core products, FP32 accumulation      */
   MAG_PREC_TF32 = 2,     /* one TF32 tensor-core product, FP32 accumulation   */
   MAG_PREC_TF32X3 = 3,   /* split TF32 (hi*hi + hi*lo + lo*hi), FP32 accum.   */
@@ -110,7 +116,8 @@ typedef struct mag_info {
   int32_t precision_used;  /* enum mag_precision of the factor that succeeded  */
   int32_t ir_iters;        /* refinement steps taken (all precisions)          */
   int32_t gmres_iters;     /* total inner GMRES iterations (0 if not used)     */
-  int32_t fallback;        /* 0 none, 1 GMRES-IR, 2 FP64 factor                */
+  int32_t fallback;        /* 0 none, 1 GMRES-IR, 2 FP64 factor, 3 the probe's
+                              FP16 choice refined slowly: split factor       */
   int32_t residual_mode;   /* enum mag_residual_mode actually used (0 or 1)    */
   int32_t reserved0;
   double rel_residual;     /* final ||1-Zw||inf / (||Z||inf ||w||inf)          */
@@ -133,6 +140,10 @@ typedef struct mag_info {
   double ms_potrf;         /* diagonal-tile factors (profile = 1)              */
   double ms_trsm;          /* panel solves (profile = 1)                        */
   double ms_split;         /* panel copies for the tensor cores (profile = 1)   */
+  double probe_rho;        /* AUTO precision probe: predicted contraction per
+                              refinement step of the one-product FP16 factor
+                              (0 = no probe, +inf = its block factor broke down) */
+  double ms_probe;         /* device time of the probe                          */
 } mag_info;
 
 typedef struct mag_ctx mag_ctx;

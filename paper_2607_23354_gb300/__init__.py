@@ -61,7 +61,8 @@ class mag_info(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("residual_evals", ctypes.c_int32),
                 ("update_launches", ctypes.c_int32), ("ms_update", ctypes.c_double),
                 ("update_flops", ctypes.c_double), ("ms_update_panel", ctypes.c_double),
-                ("ms_potrf", ctypes.c_double), ("ms_trsm", ctypes.c_double), ("ms_split", ctypes.c_double)]
+                ("ms_potrf", ctypes.c_double), ("ms_trsm", ctypes.c_double), ("ms_split", ctypes.c_double),
+                ("probe_rho", ctypes.c_double), ("ms_probe", ctypes.c_double)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}

@@ -94,6 +94,11 @@ struct mag_ctx {
   cudaStream_t side = nullptr;       // panel stream of the look-ahead factor
   int kind = MAT_EXP;                // matrix the solve path generates (MatKind)
   cudaEvent_t ev_la[3] = {nullptr, nullptr, nullptr};  // start, panel done, trailing done
+  float* probe_z = nullptr;          // FP32 tiles of the leading block the precision probe factors
+  size_t probe_bytes = 0;
+  CMap probe_cmap;                   // TMA descriptor of those tiles (update epilogue)
+  const void* probe_cmap_base = nullptr;
+  int64_t probe_cmap_tiles = 0;
 
   // typed views of the workspace
   float* zf() { return (float*)((char*)ws + lay.off_zf); }
@@ -365,22 +370,21 @@ int upd_mode(int prec) {
 // trailing matrix with K = (k1 - k0) * 128.
 // Task tables of every tensor-core update launch of one factor with the
 // current N, panel width nb and schedule (built on the host once and kept).
-int ensure_tasks(mag_ctx* ctx, int nb, bool la, bool pairs) {
-  const Layout& L = ctx->lay;
-  const auto key = std::make_tuple(L.N, nb, (int)la, (int)pairs);
+int ensure_tasks(mag_ctx* ctx, int64_t N, int nb, bool la, bool pairs) {
+  const auto key = std::make_tuple(N, nb, (int)la, (int)pairs);
   auto found = ctx->task_tables.find(key);
   if (found != ctx->task_tables.end()) {
     ctx->tasks = &found->second;
     return MAG_OK;
   }
-  if (L.N >= 65536) return fail(ctx, MAG_EINVAL, "n = %lld too large for the tensor-core factor", (long long)L.n);
+  if (N >= 65536) return fail(ctx, MAG_EINVAL, "%lld tiles too many for the tensor-core factor", (long long)N);
   std::vector<uint32_t> t;
   mag_ctx::TaskTable tab;
   auto add = [&](int64_t j0, int64_t j1) {
     const auto k = std::make_pair(j0, j1);
     if (j0 >= j1 || tab.rng.count(k)) return;
     const int64_t off = (int64_t)t.size();
-    const int64_t cnt = update_tasks(L.N, j0, j1, pairs, &t);
+    const int64_t cnt = update_tasks(N, j0, j1, pairs, &t);
     tab.rng[k] = std::make_pair(off, cnt);
   };
   // the in-panel updates of the recursive panel factor (tc_panel_range)
@@ -391,14 +395,14 @@ int ensure_tasks(mag_ctx* ctx, int nb, bool la, bool pairs) {
     add(mid, b);
     panel(mid, b);
   };
-  for (int64_t k0 = 0; k0 < L.N; k0 += nb) {
-    const int64_t k1 = std::min<int64_t>(L.N, k0 + nb), k2 = std::min<int64_t>(L.N, k1 + nb);
+  for (int64_t k0 = 0; k0 < N; k0 += nb) {
+    const int64_t k1 = std::min<int64_t>(N, k0 + nb), k2 = std::min<int64_t>(N, k1 + nb);
     panel(k0, k1);
     if (la) {
       add(k1, k2);
-      add(k2, L.N);
+      add(k2, N);
     } else {
-      add(k1, L.N);
+      add(k1, N);
     }
   }
   cudaError_t e = cudaMalloc((void**)&tab.d, std::max<size_t>(1, t.size()) * sizeof(uint32_t));
@@ -432,7 +436,9 @@ int ensure_maps(mag_ctx* ctx, int mode, int b) {
   return MAG_OK;
 }
 
-// State of one tensor-core factorization: launch parameters and counters.
+// State of one tensor-core factorization: the matrix (packed FP32 tiles of
+// n rows = N tile rows, their diagonal inverses, the epilogue's descriptor of
+// the tiles), launch parameters and counters.
 struct TcFactor {
   mag_ctx* ctx;
   int mode;
@@ -441,6 +447,10 @@ struct TcFactor {
   int* launches;
   double* flops;
   int64_t next_ctr;
+  float* Z;
+  float* Dinv;
+  const CMap* cmap;
+  int64_t n, N;
 };
 
 // C_IJ -= sum_{k in [kc_lo, kc_hi)} P_Ik P_Jk^T for J in [j0, j1) with the
@@ -454,8 +464,8 @@ int tc_update(TcFactor& F, int b, int64_t k0, int kc_lo, int kc_hi, int64_t j0, 
   if (F.next_ctr >= L.nctr) return fail(ctx, MAG_ECUDA, "update launch counters exhausted");
   UpdParams up;
   std::memset(&up, 0, sizeof up);
-  up.Z = ctx->zf();
-  up.N = L.N;
+  up.Z = F.Z;
+  up.N = F.N;
   up.k0 = k0;
   up.kc_lo = kc_lo;
   up.kc_hi = kc_hi;
@@ -466,10 +476,10 @@ int tc_update(TcFactor& F, int b, int64_t k0, int kc_lo, int kc_hi, int64_t j0, 
   up.st = ctx->st();
   up.timeout_ns = 20000000000ull;
   TRY(prof_begin(ctx, cat, st));
-  CU(launch_update_tc(ctx->maps[b], ctx->cmap, up, F.mode, grid, F.pairs, st));
+  CU(launch_update_tc(ctx->maps[b], *F.cmap, up, F.mode, grid, F.pairs, st));
   TRY(prof_end(ctx, st));
   ++*F.launches;
-  *F.flops += update_flops(L.N, k0 + kc_lo, k0 + kc_hi, j0, j1);
+  *F.flops += update_flops(F.N, k0 + kc_lo, k0 + kc_hi, j0, j1);
   return MAG_OK;
 }
 
@@ -482,18 +492,18 @@ int tc_update(TcFactor& F, int b, int64_t k0, int kc_lo, int kc_hi, int64_t j0, 
 int tc_panel_range(TcFactor& F, int64_t k0, int64_t a, int64_t b, int buf, cudaStream_t st) {
   mag_ctx* ctx = F.ctx;
   const Layout& L = ctx->lay;
-  float* Z = ctx->zf();
-  float* Dinv = ctx->dinvf();
+  float* Z = F.Z;
+  float* Dinv = F.Dinv;
   if (b - a == 1) {
     TRY(prof_begin(ctx, PC_POTRF, st));
-    CU(launch_potrf_diag<float>(Z, Dinv, a, L.n, ctx->st(), st));
+    CU(launch_potrf_diag<float>(Z, Dinv, a, F.n, ctx->st(), st));
     TRY(prof_end(ctx, st));
     TRY(prof_begin(ctx, PC_TRSM, st));
-    CU(launch_trsm_col<float>(Z, Dinv, a, L.N, ctx->st(), st));
+    CU(launch_trsm_col<float>(Z, Dinv, a, F.N, ctx->st(), st));
     TRY(prof_end(ctx, st));
-    if (a + 1 < L.N) {
+    if (a + 1 < F.N) {
       TRY(prof_begin(ctx, PC_SPLIT, st));
-      CU(launch_split_col(Z, a, L.N, k0, L.W, F.mode, ctx->panel_hi(buf), ctx->panel_lo(buf), st));
+      CU(launch_split_col(Z, a, F.N, k0, L.W, F.mode, ctx->panel_hi(buf), ctx->panel_lo(buf), st));
       TRY(prof_end(ctx, st));
     }
     return MAG_OK;
@@ -506,7 +516,7 @@ int tc_panel_range(TcFactor& F, int64_t k0, int64_t a, int64_t b, int buf, cudaS
 
 // The panel of tile columns [k0, min(N, k0 + nb)) into panel buffer b.
 int tc_panel(TcFactor& F, int64_t k0, int b, cudaStream_t st) {
-  const int64_t k1 = std::min<int64_t>(F.ctx->lay.N, k0 + F.nb);
+  const int64_t k1 = std::min<int64_t>(F.N, k0 + F.nb);
   return tc_panel_range(F, k0, k0, k1, b, st);
 }
 
@@ -526,7 +536,7 @@ int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
   const int64_t npanels = (L.N + nb - 1) / nb;
   const bool la = ctx->opt.lookahead != 0 && npanels > 2;
   const bool pairs = ctx->opt.cta_pairs == 1 || (ctx->opt.cta_pairs == 2 && split);
-  TRY(ensure_tasks(ctx, nb, la, pairs));
+  TRY(ensure_tasks(ctx, L.N, nb, la, pairs));
   TRY(ensure_maps(ctx, mode, 0));
   TRY(ensure_maps(ctx, mode, 1));
   if (ctx->cmap_base != ctx->zf() || ctx->cmap_tiles != L.tiles) {
@@ -536,7 +546,7 @@ int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
     ctx->cmap_tiles = L.tiles;
   }
   CU(cudaMemsetAsync(ctx->counters(), 0, (size_t)L.nctr * sizeof(unsigned), s));
-  TcFactor F{ctx, mode, pairs, nb, launches, flops, 0};
+  TcFactor F{ctx, mode, pairs, nb, launches, flops, 0, ctx->zf(), ctx->dinvf(), &ctx->cmap, L.n, L.N};
   if (!la) {
     for (int64_t k0 = 0; k0 < L.N; k0 += nb) {
       const int64_t k1 = std::min<int64_t>(L.N, k0 + nb);
@@ -656,6 +666,7 @@ int mag_ctx_destroy(mag_ctx* ctx) {
   if (ctx->aux) cudaFree(ctx->aux);
   if (ctx->bws) cudaFree(ctx->bws);
   if (ctx->gm) cudaFree(ctx->gm);
+  if (ctx->probe_z) cudaFree(ctx->probe_z);
   for (auto& kv : ctx->task_tables)
     if (kv.second.d) cudaFree(kv.second.d);
   if (ctx->side) {
@@ -756,6 +767,7 @@ struct SolveResult {
   int residual_evals = 0, update_launches = 0;
   bool stored = false;
   double ms_update = 0, update_flops = 0, ms_update_panel = 0, ms_potrf = 0, ms_trsm = 0, ms_split = 0;
+  double probe_rho = 0, ms_probe = 0;
 };
 
 float elapsed(mag_ctx* ctx, int a, int b) {
@@ -859,24 +871,28 @@ int run_factor(mag_ctx* ctx, int prec, SolveResult* R) {
 
 // x = (init ? 0 : x) + r_max * (L L^T)^{-1} (r / r_max) with the current
 // factor; r_max = max|r| must already be in the status block.
+// The factor is that of the leading n rows (N tile rows, np = 128 N).
 template <typename T>
-int correction_t(mag_ctx* ctx, T* Z, T* Dinv, T* v, T* y, const double* r, double* x, bool init) {
-  const Layout& L = ctx->lay;
+int correction_t(mag_ctx* ctx, T* Z, T* Dinv, T* v, T* y, const double* r, double* x, bool init, int64_t n,
+                 int64_t np, int64_t N) {
   cudaStream_t s = ctx->stream;
-  CU(launch_scale_rhs<T>(r, L.n, L.np, v, ctx->st(), s));
-  CU(launch_forward_persistent<T>(Z, Dinv, L.N, v, y, ctx->flags(), ctx->st(), s));
-  CU(launch_backward_persistent<T>(Z, Dinv, L.N, y, v, ctx->flags(), ctx->st(), s));
-  CU(launch_accumulate<T>(x, v, L.n, ctx->st(), init, s));
+  CU(launch_scale_rhs<T>(r, n, np, v, ctx->st(), s));
+  CU(launch_forward_persistent<T>(Z, Dinv, N, v, y, ctx->flags(), ctx->st(), s));
+  CU(launch_backward_persistent<T>(Z, Dinv, N, y, v, ctx->flags(), ctx->st(), s));
+  CU(launch_accumulate<T>(x, v, n, ctx->st(), init, s));
   return MAG_OK;
 }
 
 int correction(mag_ctx* ctx, int prec, const double* r, double* x, bool init, SolveResult* R) {
   cudaStream_t s = ctx->stream;
   CU(cudaEventRecord(ctx->ev[2], s));
+  const Layout& L = ctx->lay;
   if (prec == MAG_PREC_FP64)
-    TRY(correction_t<double>(ctx, ctx->zd(), ctx->dinvd(), ctx->vd(V_T2), ctx->vd(V_E), r, x, init));
+    TRY(correction_t<double>(ctx, ctx->zd(), ctx->dinvd(), ctx->vd(V_T2), ctx->vd(V_E), r, x, init, L.n, L.np,
+                             L.N));
   else
-    TRY(correction_t<float>(ctx, ctx->zf(), ctx->dinvf(), ctx->vf(F_V), ctx->vf(F_Y), r, x, init));
+    TRY(correction_t<float>(ctx, ctx->zf(), ctx->dinvf(), ctx->vf(F_V), ctx->vf(F_Y), r, x, init, L.n, L.np,
+                            L.N));
   CU(cudaEventRecord(ctx->ev[3], s));
   CU(cudaEventSynchronize(ctx->ev[3]));
   R->ms_solve += elapsed(ctx, 2, 3);
@@ -906,6 +922,122 @@ int residual(mag_ctx* ctx, const double* X, int32_t m, double t, const double* w
   R->wnorm = wn;
   *rel = (zn > 0 && wn > 0) ? rn / (zn * wn) : INFINITY;
   if (!std::isfinite(*rel)) *rel = INFINITY;
+  return MAG_OK;
+}
+
+// Refinement steps after the first solve until a relative residual that
+// starts near rho and shrinks by rho per step is below tol.
+double ir_steps(double rho, double tol) {
+  if (!(rho < 1.0)) return INFINITY;
+  if (!(rho > 0.0)) return 0.0;
+  return std::max(0.0, std::ceil(std::log(tol) / std::log(rho)) - 1.0);
+}
+
+// Precision probe of the AUTO policy: the contraction of refinement with the
+// one-product FP16 factor, measured on the leading K x K tile block (K = the
+// panel buffer width).  The packed index of a tile does not depend on N, so
+// the first K(K+1)/2 tiles are the packed matrix of the first 128 K points:
+// a copy of their FP32 tiles is factored with FP16 updates (one panel of K
+// tiles), then x_0 = F^{-1} 1, r_0 = 1 - Z_K x_0, x_1 = x_0 + F^{-1} r_0,
+// r_1 = 1 - Z_K x_1 in FP64 give the block's contraction rho_K.  The
+// full system's contraction is predicted as rho_K n / (128 K): the error of
+// an FP16 operand grows with the row norms (about sqrt(n) for a flat kernel)
+// and lambda_min shrinks with the point density (about n^{-1/m} in m
+// dimensions), both bounded by that linear factor for m >= 2.  *rho =
+// +inf when the block's FP16 factor breaks down.  The full workspace's
+// vectors r and x, the FP32 diagonal inverses and panel buffer 0 are used as
+// scratch; the solve that follows rewrites them.
+int probe_fp16(mag_ctx* ctx, const double* X, int32_t m, double t, bool stored, SolveResult* R, double* rho) {
+  const Layout& L = ctx->lay;
+  cudaStream_t s = ctx->stream;
+  const int64_t K = L.nb, ns = K * TILE, tiles = K * (K + 1) / 2;
+  const size_t bytes = (size_t)tiles * TILE_ELEMS * sizeof(float);
+  if (bytes > ctx->probe_bytes) {
+    if (ctx->probe_z) {
+      cudaStreamSynchronize(s);
+      cudaFree(ctx->probe_z);
+      ctx->probe_z = nullptr;
+      ctx->probe_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc((void**)&ctx->probe_z, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      ctx->probe_z = nullptr;
+      return fail(ctx, MAG_ENOMEM, "precision probe tiles: %s", cudaGetErrorString(e));
+    }
+    ctx->probe_bytes = bytes;
+  }
+  if (ctx->probe_cmap_base != ctx->probe_z || ctx->probe_cmap_tiles != tiles) {
+    if (!make_c_map(&ctx->probe_cmap, ctx->probe_z, tiles))
+      return fail(ctx, MAG_ECUDA, "cuTensorMapEncodeTiled failed for the probe tiles");
+    ctx->probe_cmap_base = ctx->probe_z;
+    ctx->probe_cmap_tiles = tiles;
+  }
+  CU(cudaEventRecord(ctx->ev[0], s));
+  CU(cudaMemcpyAsync(ctx->probe_z, ctx->zf(), bytes, cudaMemcpyDeviceToDevice, s));
+  const bool pairs = ctx->opt.cta_pairs == 1;
+  TRY(ensure_tasks(ctx, K, (int)K, false, pairs));
+  TRY(ensure_maps(ctx, UPD_FP16, 0));
+  CU(cudaMemsetAsync(ctx->counters(), 0, (size_t)L.nctr * sizeof(unsigned), s));
+  int launches = 0;
+  double flops = 0;
+  TcFactor F{ctx, UPD_FP16, pairs, (int)K, &launches, &flops, 0, ctx->probe_z, ctx->dinvf(), &ctx->probe_cmap,
+             ns, K};
+  TRY(tc_panel_range(F, 0, 0, K, 0, s));
+  TRY(read_status(ctx));
+  const int fl = ctx->h_st->flags;
+  if (fl & ST_TIMEOUT) return fail(ctx, MAG_ETIMEOUT, "a bounded device wait in the precision probe expired");
+  if (fl & ST_NOTPD) {
+    // breakdown of the FP16 block factor: clear the flag for the real factor
+    ctx->h_st->flags = 0;
+    ctx->h_st->notpd_index = 0x7fffffff;
+    CU(cudaMemcpyAsync(ctx->st(), ctx->h_st, 2 * sizeof(int), cudaMemcpyHostToDevice, s));
+    CU(cudaStreamSynchronize(s));
+    *rho = INFINITY;
+    R->probe_rho = INFINITY;
+    return MAG_OK;
+  }
+  double* r = ctx->vd(V_R);
+  double* x = ctx->vd(V_X);
+  CU(launch_fill(r, ns, 1.0, s));
+  TRY(reset_norms(ctx));
+  CU(launch_absmax(r, ns, ctx->st(), s));
+  TRY(correction_t<float>(ctx, ctx->probe_z, ctx->dinvf(), ctx->vf(F_V), ctx->vf(F_Y), r, x, true, ns, ns, K));
+  // r_0 = (I - Z F^{-1}) 1 and r_1 = (I - Z F^{-1}) r_0: two samples of the
+  // operator that multiplies the residual in each refinement step
+  // (||r_0||inf / ||1||inf and ||r_1||inf / ||r_0||inf); rho_K is the larger.
+  // A residual at the FP64 rounding level of ||Z|| ||x|| cannot shrink
+  // further: r_0 there ends the probe (the FP16 factor solved the block to
+  // full accuracy), r_1 there is counted at that level.
+  const int chunks = (int)std::min<int64_t>(L.chunks, K);
+  auto block_residual = [&](double* rn, double* floor) -> int {
+    TRY(reset_norms(ctx));
+    if (stored)
+      CU(launch_residual_stored(ctx->zd(), ns, K, x, nullptr, ctx->vd(V_ROWSUM), r, ctx->spart(), ns, ctx->st(),
+                                s));
+    else
+      CU(launch_residual_mf(X, ns, m, t, x, nullptr, r, ctx->part(), chunks, ns, ctx->st(), s, ctx->kind));
+    TRY(read_status(ctx));
+    *rn = bits_to_double(ctx->h_st->r_max_bits);
+    *floor = 32.0 * 0x1p-52 * bits_to_double(ctx->h_st->z_max_bits) * bits_to_double(ctx->h_st->w_max_bits);
+    return MAG_OK;
+  };
+  double rn0 = 0.0, rn1 = 0.0, floor0 = 0.0, floor1 = 0.0, rk = 0.0;
+  TRY(block_residual(&rn0, &floor0));
+  if (!(rn0 <= floor0)) {
+    TRY(correction_t<float>(ctx, ctx->probe_z, ctx->dinvf(), ctx->vf(F_V), ctx->vf(F_Y), r, x, false, ns, ns, K));
+    TRY(block_residual(&rn1, &floor1));
+    rk = std::max(rn0, std::max(rn1, floor1) / rn0);
+  } else {
+    rk = rn0;
+  }
+  CU(cudaEventRecord(ctx->ev[1], s));
+  CU(cudaEventSynchronize(ctx->ev[1]));
+  R->ms_probe += elapsed(ctx, 0, 1);
+  if (ctx->h_st->flags & ST_TIMEOUT)
+    return fail(ctx, MAG_ETIMEOUT, "a bounded device wait in the precision probe expired");
+  *rho = std::isfinite(rk) ? rk * (double)L.n / (double)ns : INFINITY;
+  R->probe_rho = *rho;
   return MAG_OK;
 }
 
@@ -1055,13 +1187,35 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
   TRY(generate(ctx, X, m, t, f32, f64, R));
   // AUTO: one scaled-FP16 product when the Gershgorin bound keeps
   // lambda_min(Z) >= 1/2 (then kappa(Z) <= 2 ||Z|| and an 11-bit factor still
-  // contracts refinement quickly), else the scaled-FP16 split (FP32-like
-  // factor accuracy at the FP16 tensor rate).
-  if (prec == MAG_PREC_AUTO) prec = R->gersh >= 0.5 ? MAG_PREC_FP16 : MAG_PREC_FP16X3;
+  // contracts refinement quickly).  Otherwise the probe predicts the
+  // contraction rho of refinement with the FP16 factor; FP16 is taken when
+  // the extra refinement steps it needs over the split factor (whose error,
+  // and so its rho, is about 2^-12 times smaller) cost less than the half of
+  // the factor it saves.  With the FP64 tiles stored that half is worth about
+  // n / 9500 refinement steps at the GB300's rates (311 ms of factor against
+  // 29 ms per step at n = 1e5); a matrix-free residual step costs about four
+  // times more.  Else the scaled-FP16 split (FP32-like factor accuracy at the
+  // FP16 tensor rate).
+  bool probed16 = false;  // FP16 chosen on the probe's prediction
+  if (prec == MAG_PREC_AUTO) {
+    prec = MAG_PREC_FP16X3;
+    if (R->gersh >= 0.5) {
+      prec = MAG_PREC_FP16;
+    } else if (ctx->lay.N >= 3 * (int64_t)ctx->lay.nb) {
+      double rho = INFINITY;
+      TRY(probe_fp16(ctx, X, m, t, stored, R, &rho));
+      const double tol = kStopMargin * o.ir_tol;
+      const double saved = (double)n / 9500.0 * (stored ? 1.0 : 0.25);
+      if (rho < 1.0 && ir_steps(rho, tol) - ir_steps(rho * 0x1p-12, tol) <= saved) {
+        prec = MAG_PREC_FP16;
+        probed16 = true;
+      }
+    }
+  }
 
   cudaStream_t s = ctx->stream;
   double overall = INFINITY;
-  for (int attempt = 0; attempt < 2; ++attempt) {
+  for (int attempt = 0; attempt < 3; ++attempt) {
     const Layout& L = ctx->lay;
     double* r = ctx->vd(V_R);
     double* xw = ctx->vd(V_X);
@@ -1107,7 +1261,9 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
         CU(cudaMemcpyAsync(x, best, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
         CU(cudaStreamSynchronize(s));
       }
-      if (escalate && prec != MAG_PREC_FP64 && o.allow_fallback && o.gmres_max_iters > 0) {
+      // a mispredicted FP16 choice goes to the split factor instead of GMRES-IR
+      const bool to_split = escalate && probed16 && prec == MAG_PREC_FP16 && o.allow_fallback;
+      if (escalate && !to_split && prec != MAG_PREC_FP64 && o.allow_fallback && o.gmres_max_iters > 0) {
         // GMRES-IR with the same factor, from the best iterate so far
         CU(cudaMemcpyAsync(xw, best, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
         double grel = INFINITY;
@@ -1122,6 +1278,14 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
       }
     }
     if (!escalate || prec == MAG_PREC_FP64 || !o.allow_fallback) break;
+    if (probed16 && prec == MAG_PREC_FP16) {
+      // the FP16 factor overwrote the FP32 tiles: generate them again
+      prec = MAG_PREC_FP16X3;
+      probed16 = false;
+      R->fallback = 3;
+      TRY(generate(ctx, X, m, t, true, false, R));
+      continue;
+    }
     // escalate to the FP64 factor (re-plans the workspace: pointers re-fetched above)
     prec = MAG_PREC_FP64;
     R->fallback = 2;
@@ -1162,6 +1326,8 @@ void fill_info(mag_ctx* ctx, const SolveResult& R, int64_t n, mag_info* info) {
   info->ms_potrf = R.ms_potrf;
   info->ms_trsm = R.ms_trsm;
   info->ms_split = R.ms_split;
+  info->probe_rho = R.probe_rho;
+  info->ms_probe = R.ms_probe;
 }
 
 }  // namespace

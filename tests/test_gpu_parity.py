@@ -534,3 +534,47 @@ def test_scale_zero_rejects_duplicates(ctx):
     with pytest.raises(M.MagnitudeError) as e:
         ctx.scale_zero(_dev(X))
     assert e.value.status == M.MAG_EDUPLICATE
+
+
+# ------------------------------------------------- AUTO precision probe
+# Below the Gershgorin bound the AUTO policy factors the leading 3072 points
+# with the one-product FP16 factor, measures the contraction of two refinement
+# steps there and extrapolates it to n.  The three branches: FP16 taken,
+# FP16X3 taken, and a wrong FP16 prediction replaced by FP16X3.
+
+def test_auto_probe_takes_fp16_when_refinement_contracts_fast(ctx):
+    # [0,1]^8 at t = 10: rows of Z sum to several (no Gershgorin bound) while
+    # lambda_min(Z) stays near 0.6, so FP16 refines in a few steps
+    X = _cloud(32768, 8, 4242)
+    w, mag, info = ctx.solve(_dev(X), 10.0)
+    assert info["gershgorin_lmin"] < 0.5
+    assert 0.0 <= info["probe_rho"] < 1e-2, info["probe_rho"]
+    assert info["precision_used"] == M.PREC_FP16
+    assert info["fallback"] == 0
+    check_solution(X, 10.0, w.cpu().numpy(), mag)
+
+
+def test_auto_probe_keeps_the_split_factor_when_ill_conditioned(ctx):
+    # [0,1]^8 at t = 1: lambda_min(Z) near 0.08 against row sums in the
+    # thousands: FP16 refinement would barely contract
+    X = _cloud(16384, 8, 4243)
+    w, mag, info = ctx.solve(_dev(X), 1.0)
+    assert info["probe_rho"] > 1e-2, info["probe_rho"]
+    assert info["precision_used"] == M.PREC_FP16X3
+    assert info["fallback"] == 0
+    check_solution(X, 1.0, w.cpu().numpy(), mag)
+
+
+def test_auto_probe_misprediction_falls_back_to_the_split_factor(ctx):
+    # the leading 3072 points are far apart (their Z block is the identity, so
+    # the probe predicts no error at all) while the other 13312 form one dense
+    # cube at t = 0.3, where the FP16 factor cannot drive refinement
+    rng = np.random.default_rng(4244)
+    spread = rng.random((3072, 8)) * 1e4 + 10.0
+    cluster = rng.random((13312, 8))
+    X = np.vstack([spread, cluster])
+    w, mag, info = ctx.solve(_dev(X), 0.3)
+    assert info["probe_rho"] < 1e-6, info["probe_rho"]
+    assert info["fallback"] == 3
+    assert info["precision_used"] == M.PREC_FP16X3
+    check_solution(X, 0.3, w.cpu().numpy(), mag)
