@@ -101,8 +101,10 @@ typedef struct mag_options {
                              trailing update of the current panel; 0: one
                              stream, step after step (same arithmetic)        */
   int32_t lookahead_sms;  /* SMs kept free of the trailing update for the
-                             panel stream (0: 16 for the split precisions,
-                             32 for one-product factors)                      */
+                             panel stream (0: 24 for the split precisions,
+                             32 for one-product factors); the panel factor's
+                             launches beside the trailing update use that
+                             many CTAs                                         */
   int32_t cta_pairs;      /* tensor-core updates on clusters of two CTAs
                              sharing each 256 x 256 MMA (cta_group::2):
                              1 (default) always, 0 never, 2 for the split

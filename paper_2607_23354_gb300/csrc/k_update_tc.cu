@@ -40,6 +40,8 @@
 // loads with a bounded wait, frees its TMEM and returns.
 #include <cuda.h>
 
+#include <cuda_fp16.h>
+
 #include "mag_internal.cuh"
 
 namespace mag {
@@ -857,6 +859,216 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
   }
 }
 
+// ------------------------------------------------------------ panel solve
+// L_IK = Z_IK inv(L_KK)^T for the tiles I in (K, N) of column K on the
+// tensor cores, with the panel copies of the tensor-core update written from
+// the same result.  Both operands are split into FP16 hi + lo after a
+// power-of-two scale per row (so that no row overflows or sinks into FP16
+// subnormals whatever the size of inv(L_KK)); three products hi*hi + hi*lo +
+// lo*hi with FP32 accumulation give about 2^-22 per product, the accuracy of
+// the FP32 solve it replaces.  Row r of A scaled by 2^a_r and row c of B by
+// 2^b_c scale the result's (r, c) by 2^(a_r + b_c), removed exactly in the
+// epilogue.  Persistent CTAs (one per SM: 129 KB of shared memory) claim
+// tiles from a counter; the next tile's loads run during the current MMA.
+constexpr int TRSM_THREADS = 256;
+constexpr uint32_t TRSM_TMEM_COLS = 128;
+constexpr int TRSM_OP_BYTES = 2 * 128 * 128;  // one FP16 copy of a 128 x 128 operand: two 16 KB K chunks
+
+// A 128-row x 128-column FP16 operand in the layout the K-major SWIZZLE_128B
+// descriptors read: two chunks of 64 columns (16 KB each), row r at byte
+// 128 r of its chunk, 16-byte unit u (columns 8u .. 8u + 7 of the chunk) at
+// unit u ^ (r & 7).
+__device__ __forceinline__ uint32_t trsm_unit_offset(int r, int u16) {
+  const int chunk = u16 >> 3, u = u16 & 7;
+  return (uint32_t)(chunk * 16384 + r * 128 + ((u ^ (r & 7)) << 4));
+}
+
+__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
+
+// Power-of-two exponent e with max |x| * 2^e in [2^13, 2^14): 0 for a row of
+// zeros, subnormals or non-finite values.
+__device__ __forceinline__ int row_scale_exp(float m) {
+  const int ex = (int)((__float_as_uint(m) >> 23) & 0xffu);
+  if (ex == 0 || ex == 255) return 0;
+  const int e = 14 - (ex - 126);
+  return e < -100 ? -100 : (e > 100 ? 100 : e);
+}
+
+// 128 x 128 FP32 tile (row-major) in registers: warp w holds rows
+// 2 (w + 8 i) + (lane >> 4), i = 0..7, lane & 15 holds its columns
+// 8 (lane & 15) .. + 7.
+__device__ __forceinline__ void trsm_load(const float* __restrict__ src, float4 (&x)[16]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = 2 * (warp + 8 * i) + (lane >> 4);
+    const float4* p = reinterpret_cast<const float4*>(src + r * TILE + 8 * (lane & 15));
+    x[2 * i] = __ldcg(p);
+    x[2 * i + 1] = __ldcg(p + 1);
+  }
+}
+
+// Split the register tile into scaled FP16 hi / lo operands and the row
+// exponents.
+__device__ __forceinline__ void trsm_split(const float4 (&x)[16], unsigned char* hi, unsigned char* lo, int* rexp) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = 2 * (warp + 8 * i) + (lane >> 4);
+    const float4 a = x[2 * i], b = x[2 * i + 1];
+    float m = fmaxf(fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))),
+                    fmaxf(fmaxf(fabsf(b.x), fabsf(b.y)), fmaxf(fabsf(b.z), fabsf(b.w))));
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const int e = row_scale_exp(m);
+    const float sc = pow2f(e);
+    const float v[8] = {a.x * sc, a.y * sc, a.z * sc, a.w * sc, b.x * sc, b.y * sc, b.z * sc, b.w * sc};
+    __align__(16) __half h[8], l[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      h[q] = __float2half_rn(v[q]);
+      l[q] = __float2half_rn(v[q] - __half2float(h[q]));
+    }
+    const uint32_t off = trsm_unit_offset(r, lane & 15);
+    *reinterpret_cast<uint4*>(hi + off) = *reinterpret_cast<const uint4*>(h);
+    *reinterpret_cast<uint4*>(lo + off) = *reinterpret_cast<const uint4*>(l);
+    if ((lane & 15) == 0) rexp[r] = e;
+  }
+}
+
+__device__ __forceinline__ void mma_f16_128x128(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  // D = F32, A = B = F16, both K-major, M = 128, N = 128
+  constexpr uint32_t idesc = (1u << 4) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(TRSM_THREADS, 1)
+    k_trsm_tc(float* __restrict__ Z, const float* __restrict__ Dinv, int64_t K, int64_t N, int64_t k0,
+              int64_t width, int split, __half* __restrict__ phi, __half* __restrict__ plo,
+              unsigned* __restrict__ counter, DevStatus* st, uint64_t timeout_ns) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* b_hi = smem;
+  unsigned char* b_lo = smem + TRSM_OP_BYTES;
+  unsigned char* a_hi = smem + 2 * TRSM_OP_BYTES;
+  unsigned char* a_lo = smem + 3 * TRSM_OP_BYTES;
+  float* stage = reinterpret_cast<float*>(a_hi);  // the result, once the MMA has read A
+  __shared__ int aexp[TILE], bexp[TILE];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int s_next, s_skip, abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t ntiles = N - K - 1;
+  if (tid == 0) {
+    s_skip = (*(volatile int*)&st->flags & (ST_NOTPD | ST_NONFINITE | ST_DUPLICATE | ST_TIMEOUT)) != 0;
+    s_next = (int)atomicAdd(counter, 1u);
+    abort_flag = 0;
+    mbar_init(&done_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (s_skip || s_next >= ntiles) return;  // uniform: nothing claimed, nothing allocated
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(TRSM_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  float4 x[16];
+  trsm_load(Dinv + K * TILE_ELEMS, x);
+  trsm_split(x, b_hi, b_lo, bexp);
+  int64_t tile = s_next;
+  trsm_load(Z + tri_index(K + 1 + tile, K) * TILE_ELEMS, x);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  const uint64_t deadline = globaltimer() + timeout_ns;
+  uint32_t phase = 0;
+  const float pscale = (float)(1 << FP16_SCALE_LOG2);
+  while (tile < ntiles) {
+    const int64_t I = K + 1 + tile;
+    trsm_split(x, a_hi, a_lo, aexp);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (tid == 0) s_next = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t o = c * 16384 + k * 32;
+          const uint64_t ah = smem_desc<128>(smem_u32(a_hi + o)), al = smem_desc<128>(smem_u32(a_lo + o));
+          const uint64_t bh = smem_desc<128>(smem_u32(b_hi + o)), bl = smem_desc<128>(smem_u32(b_lo + o));
+          mma_f16_128x128(tmem, ah, bh, (c | k) != 0);
+          mma_f16_128x128(tmem, ah, bl, 1u);
+          mma_f16_128x128(tmem, al, bh, 1u);
+        }
+      }
+      mma_commit(&done_bar);
+    }
+    const int64_t next = s_next;
+    if (next < ntiles) trsm_load(Z + tri_index(K + 1 + next, K) * TILE_ELEMS, x);
+    const bool waited = mbar_wait(&done_bar, phase, &abort_flag, deadline);
+    phase ^= 1u;
+    const bool ok = __syncthreads_and(waited ? 1 : 0) != 0;  // one decision for the whole CTA
+    tc_fence_after();
+    if (ok) {
+      // TMEM lanes 32 (warp & 3) .. + 31 are the rows, warp >> 2 picks 64 columns
+      const int r = 32 * (warp & 3) + lane, c0 = 64 * (warp >> 2);
+      const float ra = pow2f(-aexp[r]);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + 32 * j), v);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int c = c0 + 32 * j + 4 * q;
+          const float4 o = make_float4(v[4 * q] * ra * pow2f(-bexp[c]), v[4 * q + 1] * ra * pow2f(-bexp[c + 1]),
+                                       v[4 * q + 2] * ra * pow2f(-bexp[c + 2]),
+                                       v[4 * q + 3] * ra * pow2f(-bexp[c + 3]));
+          reinterpret_cast<float4*>(stage + r * TILE)[(c >> 2) ^ (r & 31)] = o;
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (!ok) break;
+    // row-major write-out: warp w, rows w + 8 i; lane l, columns 4 l .. 4 l + 3
+    float* out = Z + tri_index(I, K) * TILE_ELEMS;
+    const int64_t prow = (I - k0) * TILE, pcol = (K - k0) * TILE + 4 * lane;
+    for (int i = 0; i < 16; ++i) {
+      const int r = warp + 8 * i;
+      const float4 o = reinterpret_cast<const float4*>(stage + r * TILE)[lane ^ (r & 31)];
+      reinterpret_cast<float4*>(out + r * TILE)[lane] = o;
+      const float y[4] = {o.x * pscale, o.y * pscale, o.z * pscale, o.w * pscale};
+      __align__(8) __half h[4], l[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        h[q] = __float2half_rn(y[q]);
+        l[q] = __float2half_rn(y[q] - __half2float(h[q]));
+      }
+      const int64_t off = (prow + r) * width + pcol;
+      *reinterpret_cast<uint2*>(phi + off) = *reinterpret_cast<const uint2*>(h);
+      if (split) *reinterpret_cast<uint2*>(plo + off) = *reinterpret_cast<const uint2*>(l);
+    }
+    __syncthreads();
+    tile = next;
+  }
+  if (tid == 0 && abort_flag) atomicOr(&st->flags, ST_TIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TRSM_TMEM_COLS)
+                 : "memory");
+}
+
 // ------------------------------------------------------------ tensor maps
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -1005,6 +1217,23 @@ cudaError_t launch_update_tc(const UpdMaps& maps, const CMap& cmap, UpdParams p,
     case UPD_FP16: return launch_mode<UPD_FP16>(maps, cmap, p, grid, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_trsm_tc(float* Z, const float* Dinv, int64_t K, int64_t N, int64_t k0, int64_t width, int mode,
+                           void* hi, void* lo, unsigned* counter, DevStatus* st, int grid, cudaStream_t s) {
+  const int64_t ntiles = N - K - 1;
+  if (ntiles <= 0) return cudaSuccess;
+  if (mode != UPD_FP16 && mode != UPD_FP16X3) return cudaErrorInvalidValue;
+  const size_t smem = 4 * (size_t)TRSM_OP_BYTES + 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_trsm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if ((int64_t)grid > ntiles) grid = (int)ntiles;
+  if (grid < 1) grid = 1;
+  k_trsm_tc<<<grid, TRSM_THREADS, smem, s>>>(Z, Dinv, K, N, k0, width, mode == UPD_FP16X3 ? 1 : 0,
+                                              static_cast<__half*>(hi), static_cast<__half*>(lo), counter, st,
+                                              10000000000ull);
+  note_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace mag

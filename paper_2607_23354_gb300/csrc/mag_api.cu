@@ -39,7 +39,8 @@ struct Layout {
   bool dist = false;   // FP64 distance tiles present
   int nb = 24;         // panel buffer capacity in tiles (the widest panel a factor may use)
   int64_t W = 0;       // panel buffer row length in columns (nb * TILE)
-  int64_t nctr = 0;    // task counters of the tensor-core update launches of one factor
+  int64_t nctr = 0;    // task counters of one factor: update launches, then one per panel solve
+  int64_t nctr_upd = 0;  // the update launches' share (at the front)
 };
 
 constexpr int NVEC_D = 6;   // FP64 vectors of np entries
@@ -179,8 +180,9 @@ Layout plan(const mag_ctx* ctx, int64_t n, bool f32, bool f64, bool dist = false
   off = align_up(off + sizeof(DevStatus));
   L.off_flags = off;
   off = align_up(off + (size_t)L.N * sizeof(unsigned));
-  L.off_ctr = off;  // at most N - 1 in-panel + 2 per panel update launches
-  L.nctr = 2 * L.N + 16;
+  L.off_ctr = off;  // at most N - 1 in-panel + 2 per panel update launches, one per column solve
+  L.nctr_upd = 2 * L.N + 16;
+  L.nctr = L.nctr_upd + L.N;
   off = align_up(off + (size_t)L.nctr * sizeof(unsigned));
   L.off_vec = off;
   off = align_up(off + (size_t)L.np * (NVEC_D * sizeof(double) + NVEC_F * sizeof(float)));
@@ -451,6 +453,10 @@ struct TcFactor {
   float* Dinv;
   const CMap* cmap;
   int64_t n, N;
+  // CTAs of the panel factor's launches: all SMs, or the SMs the trailing
+  // update leaves free while it runs beside them (a launch whose CTAs cannot
+  // all be resident ends only when the trailing update does)
+  int panel_grid;
 };
 
 // C_IJ -= sum_{k in [kc_lo, kc_hi)} P_Ik P_Jk^T for J in [j0, j1) with the
@@ -461,7 +467,7 @@ int tc_update(TcFactor& F, int b, int64_t k0, int kc_lo, int kc_hi, int64_t j0, 
   const Layout& L = ctx->lay;
   auto it = ctx->tasks->rng.find(std::make_pair(j0, j1));
   if (it == ctx->tasks->rng.end() || it->second.second == 0) return MAG_OK;
-  if (F.next_ctr >= L.nctr) return fail(ctx, MAG_ECUDA, "update launch counters exhausted");
+  if (F.next_ctr >= L.nctr_upd) return fail(ctx, MAG_ECUDA, "update launch counters exhausted");
   UpdParams up;
   std::memset(&up, 0, sizeof up);
   up.Z = F.Z;
@@ -498,6 +504,14 @@ int tc_panel_range(TcFactor& F, int64_t k0, int64_t a, int64_t b, int buf, cudaS
     TRY(prof_begin(ctx, PC_POTRF, st));
     CU(launch_potrf_diag<float>(Z, Dinv, a, F.n, ctx->st(), st));
     TRY(prof_end(ctx, st));
+    if (F.mode == UPD_FP16 || F.mode == UPD_FP16X3) {
+      // solve and panel copy in one tensor-core pass
+      TRY(prof_begin(ctx, PC_TRSM, st));
+      CU(launch_trsm_tc(Z, Dinv, a, F.N, k0, L.W, F.mode, ctx->panel_hi(buf), ctx->panel_lo(buf),
+                        ctx->counters() + L.nctr_upd + a, ctx->st(), F.panel_grid, st));
+      TRY(prof_end(ctx, st));
+      return MAG_OK;
+    }
     TRY(prof_begin(ctx, PC_TRSM, st));
     CU(launch_trsm_col<float>(Z, Dinv, a, F.N, ctx->st(), st));
     TRY(prof_end(ctx, st));
@@ -510,7 +524,7 @@ int tc_panel_range(TcFactor& F, int64_t k0, int64_t a, int64_t b, int buf, cudaS
   }
   const int64_t mid = a + (b - a) / 2;
   TRY(tc_panel_range(F, k0, a, mid, buf, st));
-  TRY(tc_update(F, buf, k0, (int)(a - k0), (int)(mid - k0), mid, b, ctx->sm_count, st, PC_UPDATE_PANEL));
+  TRY(tc_update(F, buf, k0, (int)(a - k0), (int)(mid - k0), mid, b, F.panel_grid, st, PC_UPDATE_PANEL));
   return tc_panel_range(F, k0, mid, b, buf, st);
 }
 
@@ -546,7 +560,8 @@ int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
     ctx->cmap_tiles = L.tiles;
   }
   CU(cudaMemsetAsync(ctx->counters(), 0, (size_t)L.nctr * sizeof(unsigned), s));
-  TcFactor F{ctx, mode, pairs, nb, launches, flops, 0, ctx->zf(), ctx->dinvf(), &ctx->cmap, L.n, L.N};
+  TcFactor F{ctx, mode, pairs, nb, launches, flops, 0, ctx->zf(), ctx->dinvf(), &ctx->cmap, L.n, L.N,
+             ctx->sm_count};
   if (!la) {
     for (int64_t k0 = 0; k0 < L.N; k0 += nb) {
       const int64_t k1 = std::min<int64_t>(L.N, k0 + nb);
@@ -561,12 +576,15 @@ int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
   }
   cudaStream_t side = ctx->side;
   cudaEvent_t ev_start = ctx->ev_la[0], ev_panel = ctx->ev_la[1], ev_trail = ctx->ev_la[2];
-  const int reserve = ctx->opt.lookahead_sms > 0 ? ctx->opt.lookahead_sms : (split ? 16 : 32);
+  // SMs for the panel stream, measured at n = 1e5 with the tensor-core panel
+  // solve: 24 for the split products, 32 for one-product factors
+  const int reserve = ctx->opt.lookahead_sms > 0 ? ctx->opt.lookahead_sms : (split ? 24 : 32);
   const int trail_grid = std::max(1, ctx->sm_count - reserve);
   CU(cudaEventRecord(ev_start, s));
   CU(cudaStreamWaitEvent(side, ev_start, 0));
-  TRY(tc_panel(F, 0, 0, side));
+  TRY(tc_panel(F, 0, 0, side));  // nothing runs beside the first panel: all SMs
   CU(cudaEventRecord(ev_panel, side));
+  const int beside = std::max(1, std::min(ctx->sm_count, reserve));
   int64_t p = 0;
   for (int64_t k0 = 0;; k0 += nb, ++p) {
     const int64_t k1 = std::min<int64_t>(L.N, k0 + nb);
@@ -576,6 +594,7 @@ int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
     CU(cudaStreamWaitEvent(s, ev_panel, 0));  // panel p factored and copied
     // panel stream: next panel's columns, then the next panel itself
     TRY(tc_update(F, b, k0, 0, (int)(k1 - k0), k1, k2, ctx->sm_count, side, PC_UPDATE));
+    F.panel_grid = k2 < L.N ? beside : ctx->sm_count;  // the last panel runs alone
     TRY(tc_panel(F, k1, b ^ 1, side));
     CU(cudaEventRecord(ev_panel, side));
     // solver stream: the rest of the trailing matrix
@@ -982,7 +1001,7 @@ int probe_fp16(mag_ctx* ctx, const double* X, int32_t m, double t, bool stored, 
   int launches = 0;
   double flops = 0;
   TcFactor F{ctx, UPD_FP16, pairs, (int)K, &launches, &flops, 0, ctx->probe_z, ctx->dinvf(), &ctx->probe_cmap,
-             ns, K};
+             ns, K, ctx->sm_count};
   TRY(tc_panel_range(F, 0, 0, K, 0, s));
   TRY(read_status(ctx));
   const int fl = ctx->h_st->flags;

@@ -162,6 +162,14 @@ cudaError_t launch_update_tc(const UpdMaps& maps, const CMap& cmap, UpdParams p,
 // FP16X3: y = 2^12 x, hi = rn_fp16(y), lo = rn_fp16(y - hi); FP16: hi only.
 cudaError_t launch_split_col(const float* Z, int64_t K, int64_t N, int64_t k0, int64_t width, int mode,
                              void* hi, void* lo, cudaStream_t s);
+// Panel solve + panel copy of column K on the tensor cores (FP16 and FP16X3
+// factors): L_IK = Z_IK inv(L_KK)^T from the split-FP16 products hi*hi +
+// hi*lo + lo*hi of row-scaled operands, written over Z_IK, then copied into
+// the panel buffer as launch_split_col does (lo only for FP16X3).  At most
+// `grid` persistent CTAs (129 KB of shared memory each) claim the N - K - 1
+// tiles from *counter, which must be zero before the launch.
+cudaError_t launch_trsm_tc(float* Z, const float* Dinv, int64_t K, int64_t N, int64_t k0, int64_t width, int mode,
+                           void* hi, void* lo, unsigned* counter, DevStatus* st, int grid, cudaStream_t s);
 
 // K3: triangular solves with the packed factor, in place on v (np = N*TILE
 // entries of type T).  tmp: np entries of scratch.
