@@ -32,7 +32,7 @@ template <bool WF, bool WD, bool ROWSUM, bool WDIST>
 __global__ void __launch_bounds__(GEN_THREADS, 1)
     k_generate(const double* __restrict__ X, int64_t n, int m, double t, float* __restrict__ Zf,
                double* __restrict__ Zd, double* __restrict__ Dd, double* __restrict__ rowsum, DevStatus* st,
-               int kind) {
+               int kind, double tiny_arg) {
   extern __shared__ double smem[];
   double* xr = smem;                   // [TILE][GEN_MC] row points (broadcast reads)
   double* xc = smem + TILE * GEN_MC;   // [GEN_MC][TILE] column points (conflict free)
@@ -89,6 +89,9 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
   unsigned long long mind2b = 0x7ff0000000000000ull;  // +inf
   int flags = 0;
   const float tf = (float)t;
+  // d > tiny_arg / t on the bit patterns (d >= 0): the FP64 pipe stays on
+  // the distances and the exponential
+  const unsigned long long tiny_bits = (unsigned long long)__double_as_longlong(tiny_arg / t);
 
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -112,8 +115,13 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
         else if (vb == 0ull) flags |= ST_DUPLICATE;
         else mind2b = vb < mind2b ? vb : mind2b;
         if (WD || WDIST) dd = sqrt_pos(v);
-        if (WD) zd = kind ? fma(-t, dd, 1.0) : exp_neg(-t * dd, exptab);
-        if (WF) zf = WD ? f64_to_f32_nonneg(zd) : (kind ? 1.0f - tf * sqrtf((float)v) : expf(-tf * sqrtf((float)v)));
+        if (WD && !kind && (unsigned long long)__double_as_longlong(dd) > tiny_bits) {
+          zf = exp_neg_tiny(t * dd);
+          zd = (double)zf;
+        } else {
+          if (WD) zd = kind ? fma(-t, dd, 1.0) : exp_neg(-t * dd, exptab);
+          if (WF) zf = WD ? f64_to_f32_nonneg(zd) : (kind ? 1.0f - tf * sqrtf((float)v) : expf(-tf * sqrtf((float)v)));
+        }
       }
       if (WF) Zf[tile_off + (int64_t)r * TILE + c] = zf;
       if (WD) Zd[tile_off + (int64_t)r * TILE + c] = zd;
@@ -167,7 +175,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
 template <bool WF, bool WD>
 __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __restrict__ Dd, int64_t n, double t,
                                                             float* __restrict__ Zf, double* __restrict__ Zd,
-                                                            double* __restrict__ rowsum, int kind) {
+                                                            double* __restrict__ rowsum, int kind, double tiny_arg) {
   __shared__ double exptab[2 * EXPT_SIZE];
   __shared__ float colpart[8][TILE];
   load_exp_table(exptab);
@@ -177,6 +185,7 @@ __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __rest
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t off = tri_index(I, J) * TILE_ELEMS;
   const float tf = (float)t;
+  const unsigned long long tiny_bits = (unsigned long long)__double_as_longlong(tiny_arg / t);
   // row/column partial sums in FP32 (a norm; the FP64 pipe is the limit)
   float cs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   for (int i = 0; i < 16; ++i) {
@@ -196,8 +205,13 @@ __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __rest
         if (gr == gc && gr < n) rs += 1.0f;  // the diagonal counts in its row sum
       } else {
         const double d = Dd[e];
-        zd = WD ? (kind ? fma(-t, d, 1.0) : exp_neg(-t * d, exptab)) : 0.0;
-        zf = WD ? f64_to_f32_nonneg(zd) : (kind ? 1.0f - tf * (float)d : expf(-tf * (float)d));
+        if (WD && !kind && (unsigned long long)__double_as_longlong(d) > tiny_bits) {
+          zf = exp_neg_tiny(t * d);
+          zd = (double)zf;
+        } else {
+          zd = WD ? (kind ? fma(-t, d, 1.0) : exp_neg(-t * d, exptab)) : 0.0;
+          zf = WD ? f64_to_f32_nonneg(zd) : (kind ? 1.0f - tf * (float)d : expf(-tf * (float)d));
+        }
         rs += zf;
         cs[q] += zf;
       }
@@ -250,13 +264,13 @@ __global__ void k_rowsum_max(const double* __restrict__ rowsum, int64_t n, DevSt
 template <bool WF, bool WD, bool ROWSUM, bool WDIST = false>
 cudaError_t launch_gen_t(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
                          double* Zd, double* rowsum, DevStatus* st, cudaStream_t s, double* Dd = nullptr,
-                         int kind = 0) {
+                         int kind = 0, double tiny_arg = INFINITY) {
   const size_t smem = 2 * (size_t)TILE * GEN_MC * sizeof(double);
   auto kern = k_generate<WF, WD, ROWSUM, WDIST>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t tiles = num_lower_tiles(N);
-  kern<<<(unsigned)tiles, GEN_THREADS, smem, s>>>(X, n, m, t, Zf, Zd, Dd, rowsum, st, kind);
+  kern<<<(unsigned)tiles, GEN_THREADS, smem, s>>>(X, n, m, t, Zf, Zd, Dd, rowsum, st, kind, tiny_arg);
   note_launch();
   return cudaGetLastError();
 }
@@ -264,31 +278,35 @@ cudaError_t launch_gen_t(const double* X, int64_t n, int m, double t, int64_t N,
 }  // namespace
 
 cudaError_t launch_generate(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
-                            double* Zd, double* rowsum, DevStatus* st, cudaStream_t s, int kind) {
-  if (Zf && Zd) return launch_gen_t<true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, nullptr, kind);
+                            double* Zd, double* rowsum, DevStatus* st, cudaStream_t s, int kind, double tiny_arg) {
+  if (Zf && Zd)
+    return launch_gen_t<true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, nullptr, kind, tiny_arg);
   if (Zf) return launch_gen_t<true, false, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, nullptr, kind);
-  if (Zd) return launch_gen_t<false, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, nullptr, kind);
+  if (Zd)
+    return launch_gen_t<false, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, nullptr, kind, tiny_arg);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_generate_dist(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
                                  double* Zd, double* Dd, double* rowsum, DevStatus* st, cudaStream_t s,
-                                 int kind) {
-  if (Zf && Zd) return launch_gen_t<true, true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd, kind);
+                                 int kind, double tiny_arg) {
+  if (Zf && Zd)
+    return launch_gen_t<true, true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd, kind, tiny_arg);
   if (Zf) return launch_gen_t<true, false, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd, kind);
-  if (Zd) return launch_gen_t<false, true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd, kind);
+  if (Zd)
+    return launch_gen_t<false, true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd, kind, tiny_arg);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_generate_from_dist(const double* Dd, int64_t n, double t, int64_t N, float* Zf, double* Zd,
-                                     double* rowsum, cudaStream_t s, int kind) {
+                                     double* rowsum, cudaStream_t s, int kind, double tiny_arg) {
   const unsigned tiles = (unsigned)num_lower_tiles(N);
   if (Zf && Zd)
-    k_generate_from_dist<true, true><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum, kind);
+    k_generate_from_dist<true, true><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum, kind, tiny_arg);
   else if (Zf)
-    k_generate_from_dist<true, false><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum, kind);
+    k_generate_from_dist<true, false><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum, kind, INFINITY);
   else if (Zd)
-    k_generate_from_dist<false, true><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum, kind);
+    k_generate_from_dist<false, true><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum, kind, tiny_arg);
   else
     return cudaErrorInvalidValue;
   note_launch();

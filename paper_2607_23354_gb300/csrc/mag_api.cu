@@ -799,7 +799,11 @@ float elapsed(mag_ctx* ctx, int a, int b) {
 }
 
 // Generate the tiles for the given precision into the current layout.
-int generate(mag_ctx* ctx, const double* X, int32_t m, double t, bool f32, bool f64, SolveResult* R) {
+// tiny_fp32: entries below e^-46 in FP32 (exp_neg_tiny), for the solve path;
+// the entry points that return Z or differentiate it keep FP64 everywhere.
+int generate(mag_ctx* ctx, const double* X, int32_t m, double t, bool f32, bool f64, SolveResult* R,
+             bool tiny_fp32 = false) {
+  const double tiny_arg = tiny_fp32 ? kTinyArg : INFINITY;
   const Layout& L = ctx->lay;
   cudaStream_t s = ctx->stream;
   TRY(reset_status(ctx));
@@ -809,13 +813,13 @@ int generate(mag_ctx* ctx, const double* X, int32_t m, double t, bool f32, bool 
                      ctx->dist_m == m;
   if (reuse) {
     CU(launch_generate_from_dist(ctx->dist(), L.n, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr,
-                                 ctx->vd(V_ROWSUM), s, ctx->kind));
+                                 ctx->vd(V_ROWSUM), s, ctx->kind, tiny_arg));
   } else if (ctx->dist_active && L.dist) {
     CU(launch_generate_dist(X, L.n, m, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr, ctx->dist(),
-                            ctx->vd(V_ROWSUM), ctx->st(), s, ctx->kind));
+                            ctx->vd(V_ROWSUM), ctx->st(), s, ctx->kind, tiny_arg));
   } else {
     CU(launch_generate(X, L.n, m, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr,
-                       ctx->vd(V_ROWSUM), ctx->st(), s, ctx->kind));
+                       ctx->vd(V_ROWSUM), ctx->st(), s, ctx->kind, tiny_arg));
   }
   CU(launch_rowsum_max(ctx->vd(V_ROWSUM), L.n, ctx->st(), s));
   CU(cudaEventRecord(ctx->ev[1], s));
@@ -1203,7 +1207,7 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
   bool f64 = prec == MAG_PREC_FP64 || stored;
   bool f32 = prec != MAG_PREC_FP64;
   TRY(ensure_workspace(ctx, n, f32, f64));
-  TRY(generate(ctx, X, m, t, f32, f64, R));
+  TRY(generate(ctx, X, m, t, f32, f64, R, true));
   // AUTO: one scaled-FP16 product when the Gershgorin bound keeps
   // lambda_min(Z) >= 1/2 (then kappa(Z) <= 2 ||Z|| and an 11-bit factor still
   // contracts refinement quickly).  Otherwise the probe predicts the
@@ -1302,14 +1306,14 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
       prec = MAG_PREC_FP16X3;
       probed16 = false;
       R->fallback = 3;
-      TRY(generate(ctx, X, m, t, true, false, R));
+      TRY(generate(ctx, X, m, t, true, false, R, true));
       continue;
     }
     // escalate to the FP64 factor (re-plans the workspace: pointers re-fetched above)
     prec = MAG_PREC_FP64;
     R->fallback = 2;
     TRY(ensure_workspace(ctx, n, true, true));
-    TRY(generate(ctx, X, m, t, false, true, R));
+    TRY(generate(ctx, X, m, t, false, true, R, true));
   }
   R->rel = overall;
   if (!(overall < INFINITY)) return fail(ctx, MAG_ENOTPD, "no factor succeeded");

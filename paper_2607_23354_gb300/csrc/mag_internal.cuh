@@ -74,17 +74,25 @@ struct DevStatus {
 // accumulates full row sums of Z into rowsum (n doubles, must be zeroed),
 // min off-diagonal d^2, and non-finite/duplicate flags.  kind selects the
 // matrix: MAT_EXP, Z_jk = exp(-t d_jk) (Eq. weighting); MAT_SHIFTED_DIST,
-// Z_jk = 1 - t d_jk (the scale-zero system with t = 1/c).
+// Z_jk = 1 - t d_jk (the scale-zero system with t = 1/c).  With tiny_arg
+// finite, MAT_EXP entries with t d_jk > tiny_arg are evaluated in FP32
+// (exp_neg_tiny); +inf keeps every entry FP64-exact.
 enum MatKind : int { MAT_EXP = 0, MAT_SHIFTED_DIST = 1 };
+// Entries exp(-t d) with t d above this (below e^-46 < 2^-66) are evaluated in
+// FP32 on the solve path: their error cannot reach one FP64 rounding of a row
+// sum that holds the unit diagonal (exp_neg_tiny in mag_math.cuh).
+constexpr double kTinyArg = 46.0;
 cudaError_t launch_generate(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
-                            double* Zd, double* rowsum, DevStatus* st, cudaStream_t s, int kind = MAT_EXP);
+                            double* Zd, double* rowsum, DevStatus* st, cudaStream_t s, int kind = MAT_EXP,
+                            double tiny_arg = INFINITY);
 // The same, also writing the FP64 distances d_jk into Dd (packed tiles like Z).
 cudaError_t launch_generate_dist(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
                                  double* Zd, double* Dd, double* rowsum, DevStatus* st, cudaStream_t s,
-                                 int kind = MAT_EXP);
+                                 int kind = MAT_EXP, double tiny_arg = INFINITY);
 // Z from stored FP64 distance tiles: Zf (may be null) and Zd (may be null), row sums.
 cudaError_t launch_generate_from_dist(const double* Dd, int64_t n, double t, int64_t N, float* Zf, double* Zd,
-                                     double* rowsum, cudaStream_t s, int kind = MAT_EXP);
+                                     double* rowsum, cudaStream_t s, int kind = MAT_EXP,
+                                     double tiny_arg = INFINITY);
 // max_j ||x_j - x_0||^2 into st->far_d2_bits (st->far_d2_bits must start at 0).
 cudaError_t launch_far_from_first(const double* X, int64_t n, int m, DevStatus* st, cudaStream_t s);
 // min_{j != k} d^2 over all pairs (FP64) into st->min_d2_bits.

@@ -47,6 +47,17 @@ __device__ __forceinline__ double exp_neg(double x, const double* tab) {
   return __hiloint2double(__double2hiint(s) + k * (1 << 20), __double2loint(s));
 }
 
+// exp(-a) for a > kTinyArg = 46 (mag_internal.cuh; results below
+// e^-46 < 2^-66) in FP32: the
+// CUDA expf of the rounded argument, relative error below 6e-6 (argument
+// rounding a 2^-24 <= 5.2e-6 for a <= 87, plus the expf error), and 0 for
+// a > 87 (below FP32's normal range).  In a row of Z that holds the unit
+// diagonal these entries change the FP64 row sum by at most
+// n (6e-6 e^-46 + 2^-126) < n 2^-83: for n <= 2^20 far below the 2^-53 of
+// one FP64 rounding of that sum, so residuals and refinement see the same
+// matrix as with FP64 exponentials everywhere.
+__device__ __forceinline__ float exp_neg_tiny(double a) { return a > 87.0 ? 0.0f : expf(-(float)a); }
+
 // x in [0, 2^128) to FP32, round to nearest even, on the integer pipe; values
 // below 2^-126 (FP32 subnormals) become 0.  Used for the FP32 copy of a Z
 // entry, whose role is the factor's input.

@@ -578,3 +578,25 @@ def test_auto_probe_misprediction_falls_back_to_the_split_factor(ctx):
     assert info["fallback"] == 3
     assert info["precision_used"] == M.PREC_FP16X3
     check_solution(X, 0.3, w.cpu().numpy(), mag)
+
+
+@pytest.mark.parametrize("resid", ["stored", "matrix_free"])
+def test_solve_where_most_entries_are_below_exp_minus_46(ctx, resid):
+    # t = 120 on [0,1]^3: t d > 46 (Z below e^-46, evaluated in FP32 by the
+    # solve path) for all pairs farther apart than 0.38, i.e. most of them;
+    # weights and magnitude still match the FP64 oracle, and the oracle's own
+    # FP64 residual of the GPU weighting meets the tolerance
+    X = _cloud(2000, 3, 4245)
+    t = 120.0
+    ctx.set_options(M.Options(residual_mode=resid))
+    try:
+        w, mag, info = ctx.solve(_dev(X), t)
+    finally:
+        ctx.set_options(M.Options())
+    w_ref, mag_ref, _ = oracle.weighting(X, t)
+    check_solution(X, t, w.cpu().numpy(), mag, w_ref, mag_ref)
+    # the similarity matrix entry point keeps every entry FP64-exact
+    Zg = ctx.similarity_matrix(_dev(X[:300]), t, "fp64").cpu().numpy()
+    Zo = oracle.similarity_matrix(X[:300], t)
+    td = t * oracle.distance_matrix(X[:300])
+    assert np.all(np.abs(Zg - Zo) <= 2e-15 * (1 + td) * Zo + 1e-300)
