@@ -182,9 +182,12 @@ __global__ void __launch_bounds__(512) k_potrf_diag(T* __restrict__ Z, T* __rest
 // loads):
 //   for kb = 0..3 (o = 32 kb):
 //     warp 0 factors the diagonal block A[o:o+32, o:o+32] with lane l owning
-//       row l (pivots and column entries exchanged by shuffles, no barrier;
-//       1/sqrt of the pivot from rsqrtf), then inverts it (lane l forward-
-//       substitutes column l of the identity) into the diagonal block of Y;
+//       column l: lane c scales column c (1/sqrt of the pivot from rsqrtf)
+//       and publishes it in shared memory, the lanes to its right update
+//       their columns from it (broadcast float4 reads, no barrier beyond
+//       __syncwarp); then it inverts the block into the diagonal block of Y,
+//       lane l solving for column l of the identity right-looking in
+//       registers from the published columns;
 //     all warps: blocks below it, A_ib,kb <- A_ib,kb Yd_kb^T (panel solve);
 //     all warps: trailing blocks A_ib,jb -= A_ib,kb A_jb,kb^T (kb < jb <= ib).
 //   Off-diagonal blocks of Y by block diagonals d = ib - jb = 1, 2, 3:
@@ -208,7 +211,7 @@ __global__ void __launch_bounds__(512, 1) k_potrf_blk(float* __restrict__ Z, flo
   extern __shared__ __align__(16) float psm[];
   float* A = psm;                // [TILE][LDB]
   float* Y = psm + TILE * LDB;   // [TILE][LDB]
-  __shared__ float rdiag[TILE];  // 1 / L[i][i]
+  __shared__ __align__(16) float colL[PB][PB];  // finished columns of the current diagonal block
   __shared__ int skip;
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
   if (tid == 0) skip = (st->flags & (ST_NOTPD | ST_NONFINITE | ST_DUPLICATE)) != 0;  // set by earlier kernels
@@ -224,50 +227,70 @@ __global__ void __launch_bounds__(512, 1) k_potrf_blk(float* __restrict__ Z, flo
   for (int kb = 0; kb < TILE / PB; ++kb) {
     const int o = kb * PB;
     if (w == 0) {
-      float d[PB];
+      // lane l owns column l of the diagonal block: a[i] = A[o+i][o+l] (i >= l
+      // matter; entries above the diagonal are never read and stored as 0)
+      float a[PB];
 #pragma unroll
-      for (int j = 0; j < PB; j += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(A + (o + l) * LDB + o + j);
-        d[j] = v.x, d[j + 1] = v.y, d[j + 2] = v.z, d[j + 3] = v.w;
-      }
+      for (int i = 0; i < PB; ++i) a[i] = A[(o + i) * LDB + o + l];
 #pragma unroll
       for (int c = 0; c < PB; ++c) {
-        const float piv = __shfl_sync(0xffffffffu, d[c], c);
-        const bool bad = !(piv > 0.f);
-        if (bad && l == 0) {
-          atomicOr(&st->flags, ST_NOTPD);
-          atomicMin(&st->notpd_index, (int)(K * TILE + o + c + 1));
-        }
-        const float rs = bad ? 1.f : rsqrtf(piv);
-        const float lc = l > c ? d[c] * rs : (l == c ? (bad ? 1.f : piv * rs) : 0.f);
-        d[c] = lc;
-        if (l == c) rdiag[o + c] = 1.f / lc;
+        // lane c: column c is final; scale it and publish it in colL[c]
+        if (l == c) {
+          const float piv = a[c];
+          const bool bad = !(piv > 0.f);
+          if (bad) {
+            atomicOr(&st->flags, ST_NOTPD);
+            atomicMin(&st->notpd_index, (int)(K * TILE + o + c + 1));
+          }
+          const float rs = bad ? 1.f : rsqrtf(piv);
+          a[c] = bad ? 1.f : piv * rs;
 #pragma unroll
-        for (int j = c + 1; j < PB; ++j) d[j] -= lc * __shfl_sync(0xffffffffu, lc, j);
+          for (int i = c + 1; i < PB; ++i) a[i] *= rs;
+#pragma unroll
+          for (int i = 0; i < PB; i += 4)
+            *reinterpret_cast<float4*>(&colL[c][i]) =
+                make_float4(i >= c ? a[i] : 0.f, i + 1 >= c ? a[i + 1] : 0.f, i + 2 >= c ? a[i + 2] : 0.f,
+                            i + 3 >= c ? a[i + 3] : 0.f);
+        }
+        __syncwarp();
+        // lanes l > c: A[i][l] -= L[i][c] L[l][c] (broadcast reads of column c)
+        if (l > c) {
+          const float llc = colL[c][l];
+#pragma unroll
+          for (int i4 = (c + 1) & ~3; i4 < PB; i4 += 4) {  // aligned float4 groups from row c+1
+            const float4 v = *reinterpret_cast<const float4*>(&colL[c][i4]);
+            const float lv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (i4 + q > c) a[i4 + q] -= lv[q] * llc;
+          }
+        }
       }
 #pragma unroll
-      for (int j = 0; j < PB; j += 4)
-        *reinterpret_cast<float4*>(A + (o + l) * LDB + o + j) =
-            make_float4(j <= l ? d[j] : 0.f, j + 1 <= l ? d[j + 1] : 0.f, j + 2 <= l ? d[j + 2] : 0.f,
-                        j + 3 <= l ? d[j + 3] : 0.f);
-      __syncwarp();
-      // column l of inv(L_D): y_i = (e_l[i] - sum_{k<i} L[i][k] y_k) / L[i][i]
-      // (two partial sums per row for a shorter dependence chain)
+      for (int i = 0; i < PB; ++i) A[(o + i) * LDB + o + l] = i >= l ? a[i] : 0.f;
+      const float myinv = 1.f / colL[l][l];  // every lane its own pivot: one division per lane
+      // column l of inv(L_D), right-looking: once y_k is final (scaled by
+      // 1/L[k][k]), y_i -= L[i][k] y_k for i > k; L's column k is read from
+      // colL by broadcast, so the dependence chain is one multiply and one
+      // FMA per k
       float y[PB];
 #pragma unroll
-      for (int i = 0; i < PB; ++i) {
-        float a0 = (i == l) ? 1.f : 0.f, a1 = 0.f;
+      for (int i = 0; i < PB; ++i) y[i] = i == l ? 1.f : 0.f;
 #pragma unroll
-        for (int k = 0; k + 1 < i; k += 2) {
-          const float2 lk = *reinterpret_cast<const float2*>(A + (o + i) * LDB + o + k);
-          a0 -= lk.x * y[k];
-          a1 -= lk.y * y[k + 1];
+      for (int k = 0; k < PB; ++k) {
+        y[k] *= __shfl_sync(0xffffffffu, myinv, k);
+#pragma unroll
+        for (int i4 = (k + 1) & ~3; i4 < PB; i4 += 4) {
+          const float4 v = *reinterpret_cast<const float4*>(&colL[k][i4]);
+          const float lv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (i4 + q > k) y[i4 + q] -= lv[q] * y[k];
         }
-        if (i & 1) a0 -= A[(o + i) * LDB + o + i - 1] * y[i - 1];
-        y[i] = (a0 + a1) * rdiag[o + i];
       }
 #pragma unroll
       for (int i = 0; i < PB; ++i) Y[(o + i) * LDB + o + l] = y[i];
+      __syncwarp();  // colL is rewritten by the next block's factor
     }
     __syncthreads();
     // panel solve of the blocks below: X[r][c] = sum_k A[r][o+k] Yd[c][k]
