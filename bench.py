@@ -52,7 +52,7 @@ def parse_args():
     p.add_argument("--cpu-sample-n", type=int, default=12288)
     p.add_argument("--panel-tiles", type=int, default=0, help="factor panel width in 128-wide tiles (0 = library default)")
     p.add_argument("--lookahead", type=int, default=1, help="1: factor the next panel on a second stream")
-    p.add_argument("--lookahead-sms", type=int, default=0, help="SMs kept for the panel stream (0 = library default)")
+    p.add_argument("--lookahead-sms", type=int, default=0, help="> 0: SMs kept for the panel stream; 0: library default (stream priority); < 0: priority with that many trailing blocks per CTA")
     p.add_argument("--paper-sweep", action="store_true",
                    help="instead of the headline step: the paper's runtime workload (t_+ and w(t_+) for "
                         "n in 1e3..3e4, m in 3..100, two covariances, 3 runs) with bisection and Ridders")

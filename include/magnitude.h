@@ -100,11 +100,16 @@ typedef struct mag_options {
                              and copy) on a second stream alongside the
                              trailing update of the current panel; 0: one
                              stream, step after step (same arithmetic)        */
-  int32_t lookahead_sms;  /* SMs kept free of the trailing update for the
-                             panel stream (0: 24 for the split precisions,
-                             32 for one-product factors); the panel factor's
-                             launches beside the trailing update use that
-                             many CTAs                                         */
+  int32_t lookahead_sms;  /* how the look-ahead streams share the GPU.  > 0:
+                             that many SMs kept free of the (persistent)
+                             trailing update for the panel stream, whose
+                             launches beside it use that many CTAs.  0
+                             (default): the panel stream has the higher
+                             stream priority and every trailing CTA (pair)
+                             leaves after 4 output blocks of 256 x 256,
+                             so the panel stream's CTAs take
+                             SMs as they come free; < 0: the same with
+                             -lookahead_sms blocks per CTA                   */
   int32_t cta_pairs;      /* tensor-core updates on clusters of two CTAs
                              sharing each 256 x 256 MMA (cta_group::2):
                              1 (default) always, 0 never, 2 for the split

@@ -351,10 +351,14 @@ __global__ void __launch_bounds__(UPD_THREADS, 1)
       for (int s = 0; s < S; ++s) issued[s] = false, issued_parity[s] = 0;
       bool ok = true;
       uint32_t ts = 0, tph = 0;
+      int claimed = 0;
       while (ok) {
-        // claim the next task and hand it to the MMA and epilogue roles
+        // claim the next task and hand it to the MMA and epilogue roles (at
+        // most p.max_tasks per CTA when that is set)
         if (!mbar_wait(&tq_empty[ts], tph ^ 1u, &abort_flag, deadline)) break;
-        const int64_t q = (int64_t)atomicAdd(p.counter, 1u);
+        const bool capped = p.max_tasks > 0 && claimed >= p.max_tasks;
+        const int64_t q = capped ? p.ntasks : (int64_t)atomicAdd(p.counter, 1u);
+        ++claimed;
         const bool end = q >= p.ntasks;
         tq_val[ts] = end ? -1 : q;
         mbar_arrive(&tq_full[ts]);
@@ -686,11 +690,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
       bool issued[S];
       for (int s = 0; s < S; ++s) issued[s] = false, issued_parity[s] = 0;
       bool ok = true;
+      int claimed = 0;
       while (ok) {
         int64_t q;
         if (rank == 0) {
           if (!mbar_wait_cluster(&tq_empty[ts], tph ^ 1u, &abort_flag, deadline)) break;
-          q = (int64_t)atomicAdd(p.counter, 1u);
+          // at most p.max_tasks per CTA pair when that is set
+          const bool capped = p.max_tasks > 0 && claimed >= p.max_tasks;
+          q = capped ? -1 : (int64_t)atomicAdd(p.counter, 1u);
+          ++claimed;
           if (q >= p.ntasks) q = -1;
           tq_val[ts] = q;
           st_remote_s64(r1_tq_val + ts * 8u, q);

@@ -462,7 +462,7 @@ struct TcFactor {
 // C_IJ -= sum_{k in [kc_lo, kc_hi)} P_Ik P_Jk^T for J in [j0, j1) with the
 // panel of tile column k0 in buffer b, on stream st with at most `grid` CTAs.
 int tc_update(TcFactor& F, int b, int64_t k0, int kc_lo, int kc_hi, int64_t j0, int64_t j1, int grid,
-              cudaStream_t st, int cat) {
+              cudaStream_t st, int cat, int max_tasks = 0) {
   mag_ctx* ctx = F.ctx;
   const Layout& L = ctx->lay;
   auto it = ctx->tasks->rng.find(std::make_pair(j0, j1));
@@ -481,6 +481,12 @@ int tc_update(TcFactor& F, int b, int64_t k0, int kc_lo, int kc_hi, int64_t j0, 
   up.counter = ctx->counters() + F.next_ctr++;
   up.st = ctx->st();
   up.timeout_ns = 20000000000ull;
+  up.max_tasks = max_tasks;
+  if (max_tasks > 0) {
+    // enough CTAs (pairs) for every task at max_tasks each; they start as SMs come free
+    const int64_t units = (up.ntasks + max_tasks - 1) / max_tasks;
+    grid = (int)std::min<int64_t>(units * (F.pairs ? 2 : 1), 1 << 30);
+  }
   TRY(prof_begin(ctx, cat, st));
   CU(launch_update_tc(ctx->maps[b], *F.cmap, up, F.mode, grid, F.pairs, st));
   TRY(prof_end(ctx, st));
@@ -571,20 +577,32 @@ int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
     return MAG_OK;
   }
   if (!ctx->side) {
-    CU(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+    // the panel stream outranks the solver's stream: CTAs of its launches
+    // are placed on SMs before pending CTAs of the trailing update
+    int least = 0, greatest = 0;
+    CU(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CU(cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, greatest));
     for (int i = 0; i < 3; ++i) CU(cudaEventCreateWithFlags(&ctx->ev_la[i], cudaEventDisableTiming));
   }
   cudaStream_t side = ctx->side;
   cudaEvent_t ev_start = ctx->ev_la[0], ev_panel = ctx->ev_la[1], ev_trail = ctx->ev_la[2];
-  // SMs for the panel stream, measured at n = 1e5 with the tensor-core panel
-  // solve: 24 for the split products, 32 for one-product factors
-  const int reserve = ctx->opt.lookahead_sms > 0 ? ctx->opt.lookahead_sms : (split ? 24 : 32);
-  const int trail_grid = std::max(1, ctx->sm_count - reserve);
+  // Two ways to share the GPU between the streams.  lookahead_sms > 0: the
+  // trailing update is a persistent launch on all but that many SMs, and
+  // the panel factor's launches beside it are capped at the rest.  Else
+  // (default): every trailing CTA (pair) leaves after `tpc` 256 x 256 output
+  // blocks (4: measured at n = 1e5 against 5 to 20, and 16 to 32 reserved
+  // SMs; -lookahead_sms sets it), so SMs come free all the time and the
+  // panel stream's launches, on the higher-priority stream, take them first.
+  const bool reserved = ctx->opt.lookahead_sms > 0;
+  const int reserve = reserved ? ctx->opt.lookahead_sms : 0;
+  const int tpc = ctx->opt.lookahead_sms < 0 ? -ctx->opt.lookahead_sms : 4;
+  const int trail_grid = reserved ? std::max(1, ctx->sm_count - reserve) : ctx->sm_count;
+  const int trail_tasks = reserved ? 0 : tpc;
   CU(cudaEventRecord(ev_start, s));
   CU(cudaStreamWaitEvent(side, ev_start, 0));
   TRY(tc_panel(F, 0, 0, side));  // nothing runs beside the first panel: all SMs
   CU(cudaEventRecord(ev_panel, side));
-  const int beside = std::max(1, std::min(ctx->sm_count, reserve));
+  const int beside = reserved ? std::max(1, std::min(ctx->sm_count, reserve)) : ctx->sm_count;
   int64_t p = 0;
   for (int64_t k0 = 0;; k0 += nb, ++p) {
     const int64_t k1 = std::min<int64_t>(L.N, k0 + nb);
@@ -598,7 +616,7 @@ int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
     TRY(tc_panel(F, k1, b ^ 1, side));
     CU(cudaEventRecord(ev_panel, side));
     // solver stream: the rest of the trailing matrix
-    if (k2 < L.N) TRY(tc_update(F, b, k0, 0, (int)(k1 - k0), k2, L.N, trail_grid, s, PC_UPDATE));
+    if (k2 < L.N) TRY(tc_update(F, b, k0, 0, (int)(k1 - k0), k2, L.N, trail_grid, s, PC_UPDATE, trail_tasks));
     CU(cudaEventRecord(ev_trail, s));
     CU(cudaStreamWaitEvent(side, ev_trail, 0));  // columns of panel p+2 and buffer b are free
   }

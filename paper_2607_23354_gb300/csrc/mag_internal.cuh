@@ -135,6 +135,8 @@ struct UpdParams {
   unsigned* counter;      // zero before the launch; CTAs claim tasks from it
   DevStatus* st;
   uint64_t timeout_ns; // bound on every barrier wait inside the kernel
+  int max_tasks;       // > 0: a CTA (pair) leaves after that many tasks, so that
+                       // SMs come free during the launch; 0: until the queue is empty
 };
 
 // Four TMA descriptors (A/B boxes of the hi and lo panel copies), 128 B each.

@@ -120,10 +120,13 @@ def test_cholesky_tensor_core_normwise(ctx, prec, tol, n):
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "fp16x3", "fp16"])
-@pytest.mark.parametrize("n,panel,sms", [(3300, 8, 16), (3300, 2, 1), (5000, 4, 40), (2500, 3, 150)])
+@pytest.mark.parametrize("n,panel,sms", [(3300, 8, 16), (3300, 2, 1), (5000, 4, 40), (2500, 3, 150),
+                                         (5000, 4, 0), (3300, 8, -1), (6000, 16, -3)])
 def test_lookahead_and_cta_pairs_give_bitwise_the_serial_factor(prec, n, panel, sms):
     # the look-ahead schedule applies the same products to every tile in the
-    # same order as the one-stream schedule, so the factors agree exactly
+    # same order as the one-stream schedule, so the factors agree exactly;
+    # sms > 0 reserves SMs for the panel stream, sms <= 0 shares them through
+    # stream priority with trailing CTAs that leave after -sms (default) tasks
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     X = _dev(_cloud(n, 4, seed=n + panel))
