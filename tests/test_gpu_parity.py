@@ -603,3 +603,28 @@ def test_solve_where_most_entries_are_below_exp_minus_46(ctx, resid):
     Zo = oracle.similarity_matrix(X[:300], t)
     td = t * oracle.distance_matrix(X[:300])
     assert np.all(np.abs(Zg - Zo) <= 2e-15 * (1 + td) * Zo + 1e-300)
+
+
+def test_stored_residual_on_separated_clusters(ctx):
+    # six clusters of 256 points (two tiles each), centres 3 apart, radius
+    # 0.3, t = 25: every tile between two clusters holds only entries near
+    # e^-60 (evaluated in FP32 by the solve path's generator) next to
+    # well-coupled diagonal blocks; weights, magnitude and the oracle's FP64
+    # residual match
+    rng = np.random.default_rng(4246)
+    centres = np.array([[3.0 * i, 0.0, 0.0] for i in range(6)])
+    pts = []
+    for c in centres:
+        v = rng.standard_normal((256, 3))
+        v *= 0.3 * rng.random((256, 1)) ** (1 / 3) / np.linalg.norm(v, axis=1, keepdims=True)
+        pts.append(c + v)
+    X = np.vstack(pts)
+    t = 25.0
+    ctx.set_options(M.Options(residual_mode="stored"))
+    try:
+        w, mag, info = ctx.solve(_dev(X), t)
+    finally:
+        ctx.set_options(M.Options())
+    assert info["residual_mode"] == M.RESID_STORED
+    w_ref, mag_ref, _ = oracle.weighting(X, t)
+    check_solution(X, t, w.cpu().numpy(), mag, w_ref, mag_ref)
