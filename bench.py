@@ -322,7 +322,7 @@ def run_ours(a):
                                       f"t in {{{', '.join(s.strip() for s in a.ts.split(','))}}}; one step = "
                                       f"{len(ts)} solves to rel. residual <= 1e-14",
                           "n": a.n, "m": a.m, "t": ts, "precision": a.precision, "residual_mode": a.resid,
-                          "panel_tiles": a.panel_tiles or "auto (16 split, 24 one-product)",
+                          "panel_tiles": a.panel_tiles or "auto (16 split, 32 one-product)",
                           "parallelism": f"replicas x{world}",
                           "l2": "inputs larger than L2 (packed factor tiles of several GB per solve)",
                           "api": "mag_solve_multi (one call per step for all t; distances computed once per call)"},

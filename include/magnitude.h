@@ -54,7 +54,7 @@ enum mag_status {
 /* Precision of the Cholesky factor (Zw = 1 is always refined in FP64). */
 enum mag_precision {
   MAG_PREC_AUTO = 0,     /* FP16 if the Gershgorin bound gives lambda_min(Z) >= 1/2;
-                            else (n >= 384 K, K = panel width in tiles) FP16
+                            else (n >= 384 K, K = min(24, panel width)) FP16
                             when a probe (FP16 factor + two refinement steps
                             on the leading 128 K points) predicts that its
                             extra refinement steps cost less than the factor
@@ -88,7 +88,7 @@ typedef struct mag_options {
   int32_t gmres_max_iters;/* inner GMRES iterations of GMRES-IR, default 30     */
   int32_t allow_fallback; /* 1: escalate to GMRES-IR then FP64 factor (default)  */
   int32_t panel_tiles;    /* outer panel width in 128-wide tiles (0: 16 for the
-                             split precisions, 24 for one-product factors)     */
+                             split precisions, 32 for one-product factors)     */
   double workspace_limit_bytes; /* 0 = no limit; larger requests give ENOMEM     */
   int32_t profile;        /* 1: time the trailing-update kernel with CUDA events */
   int32_t reuse_distances;/* 1 (default): inside one mag_solve_multi or

@@ -193,7 +193,7 @@ Layout plan(const mag_ctx* ctx, int64_t n, bool f32, bool f64, bool dist = false
   if (dist) off = align_up(off + (size_t)L.tiles * TILE_ELEMS * sizeof(double));
   // panel buffers sized for the widest default panel, so that factors of
   // different precisions in one call share the workspace
-  L.nb = ctx->opt.panel_tiles > 0 ? ctx->opt.panel_tiles : 24;
+  L.nb = ctx->opt.panel_tiles > 0 ? ctx->opt.panel_tiles : 32;
   L.W = (int64_t)L.nb * TILE;
   L.off_panel = off;
   // two panel buffers (hi + lo copies each): the next panel is written while
@@ -552,7 +552,7 @@ int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
   const bool split = mode == UPD_FP16X3 || mode == UPD_TF32X3;
   // panel width and panel-stream SMs by product count (measured at n = 1e5):
   // one-product updates are short, so wider panels and a larger panel share
-  const int nb = std::max(1, std::min(L.nb, ctx->opt.panel_tiles > 0 ? ctx->opt.panel_tiles : (split ? 16 : 24)));
+  const int nb = std::max(1, std::min(L.nb, ctx->opt.panel_tiles > 0 ? ctx->opt.panel_tiles : (split ? 16 : 32)));
   const int64_t npanels = (L.N + nb - 1) / nb;
   const bool la = ctx->opt.lookahead != 0 && npanels > 2;
   const bool pairs = ctx->opt.cta_pairs == 1 || (ctx->opt.cta_pairs == 2 && split);
@@ -966,6 +966,9 @@ int residual(mag_ctx* ctx, const double* X, int32_t m, double t, const double* w
   return MAG_OK;
 }
 
+// Tile rows of the precision probe's leading block (3072 points).
+constexpr int64_t kProbeTiles = 24;
+
 // Refinement steps after the first solve until a relative residual that
 // starts near rho and shrinks by rho per step is below tol.
 double ir_steps(double rho, double tol) {
@@ -975,8 +978,8 @@ double ir_steps(double rho, double tol) {
 }
 
 // Precision probe of the AUTO policy: the contraction of refinement with the
-// one-product FP16 factor, measured on the leading K x K tile block (K = the
-// panel buffer width).  The packed index of a tile does not depend on N, so
+// one-product FP16 factor, measured on the leading K x K tile block (K = 24,
+// or the panel width when that is smaller).  The packed index of a tile does not depend on N, so
 // the first K(K+1)/2 tiles are the packed matrix of the first 128 K points:
 // a copy of their FP32 tiles is factored with FP16 updates (one panel of K
 // tiles), then x_0 = F^{-1} 1, r_0 = 1 - Z_K x_0, x_1 = x_0 + F^{-1} r_0,
@@ -991,7 +994,7 @@ double ir_steps(double rho, double tol) {
 int probe_fp16(mag_ctx* ctx, const double* X, int32_t m, double t, bool stored, SolveResult* R, double* rho) {
   const Layout& L = ctx->lay;
   cudaStream_t s = ctx->stream;
-  const int64_t K = L.nb, ns = K * TILE, tiles = K * (K + 1) / 2;
+  const int64_t K = std::min<int64_t>(L.nb, kProbeTiles), ns = K * TILE, tiles = K * (K + 1) / 2;
   const size_t bytes = (size_t)tiles * TILE_ELEMS * sizeof(float);
   if (bytes > ctx->probe_bytes) {
     if (ctx->probe_z) {
@@ -1242,7 +1245,7 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
     prec = MAG_PREC_FP16X3;
     if (R->gersh >= 0.5) {
       prec = MAG_PREC_FP16;
-    } else if (ctx->lay.N >= 3 * (int64_t)ctx->lay.nb) {
+    } else if (ctx->lay.N >= 3 * std::min<int64_t>(ctx->lay.nb, kProbeTiles)) {
       double rho = INFINITY;
       TRY(probe_fp16(ctx, X, m, t, stored, R, &rho));
       const double tol = kStopMargin * o.ir_tol;
