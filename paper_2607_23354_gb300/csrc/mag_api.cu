@@ -366,10 +366,10 @@ int upd_mode(int prec) {
 }
 
 // Two-level blocked Cholesky with the trailing update on tensor cores.  For
-// each panel of nb tile columns [k0, k1): potrf + panel solve per column,
-// the column's split copy into the panel buffer, a rank-128 tensor-core update
-// of the remaining panel columns; then one tensor-core update of the whole
-// trailing matrix with K = (k1 - k0) * 128.
+// each panel of nb tile columns [k0, k1): potrf + panel solve per column
+// with the column's copy into the panel buffer (one tensor-core pass for the
+// FP16 kinds), recursive tensor-core updates inside the panel; then one
+// tensor-core update of the whole trailing matrix with K = (k1 - k0) * 128.
 // Task tables of every tensor-core update launch of one factor with the
 // current N, panel width nb and schedule (built on the host once and kept).
 int ensure_tasks(mag_ctx* ctx, int64_t N, int nb, bool la, bool pairs) {
@@ -550,8 +550,9 @@ int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
   const Layout& L = ctx->lay;
   cudaStream_t s = ctx->stream;
   const bool split = mode == UPD_FP16X3 || mode == UPD_TF32X3;
-  // panel width and panel-stream SMs by product count (measured at n = 1e5):
-  // one-product updates are short, so wider panels and a larger panel share
+  // panel width by product count (measured at n = 1e5): one-product updates
+  // are short and gain from K = 4096 per launch (32 tiles); the split
+  // products refine in fewer steps with 16-tile panels
   const int nb = std::max(1, std::min(L.nb, ctx->opt.panel_tiles > 0 ? ctx->opt.panel_tiles : (split ? 16 : 32)));
   const int64_t npanels = (L.N + nb - 1) / nb;
   const bool la = ctx->opt.lookahead != 0 && npanels > 2;
