@@ -58,6 +58,12 @@ def parse_args():
                         "n in 1e3..3e4, m in 3..100, two covariances, 3 runs) with bisection and Ridders")
     p.add_argument("--batch-only", action="store_true",
                    help="instead of the headline step: time the batched solver (512 clouds in R^32 x 8 t)")
+    p.add_argument("--no-comparators", action="store_true",
+                   help="skip the FP64-dense comparison and the batch throughput after the timed steps")
+    p.add_argument("--fp64-dense-n", type=int, default=0,
+                   help="instead of the headline step: the FP64 dense paths against AUTO at this n "
+                        "(points uniform in [0,1]^8, t=1; --no-cusolver to skip cuSOLVER)")
+    p.add_argument("--no-cusolver", action="store_true")
     p.add_argument("--cta-pairs", type=int, default=1,
                    help="CTA-pair (cta_group::2) tensor-core updates: 1 always, 0 never, 2 split precisions only")
     return p.parse_args()
@@ -187,8 +193,9 @@ def run_ours(a):
     opts = M.Options(precision=a.precision, residual_mode=a.resid, profile=True, panel_tiles=a.panel_tiles,
                      lookahead=bool(a.lookahead), lookahead_sms=a.lookahead_sms, cta_pairs=a.cta_pairs)
     ctx = M.Context(opts)
-    dmin, bound = ctx.min_distance(Xd)
-    ts = [bound if s.strip() == "bound" else float(s) for s in a.ts.split(",")]
+    # 'bound' = the Sec. 1 bound log(n-1)/min d, found inside the call (t <= 0
+    # asks mag_solve_multi for it: min d comes from the first t's generator)
+    ts = [0.0 if s.strip() == "bound" else float(s) for s in a.ts.split(",")]
     Wbuf = torch.empty(len(ts), a.n, dtype=torch.float64, device=dev)
 
     def step(acc=None):
@@ -258,7 +265,8 @@ def run_ours(a):
     if rank == 0:
         peaks, peak_kind = measured_peaks()
         last = infos[-len(ts):]
-        per_t = [{"t": t, "solve_s": i["ms_total"] / 1e3, "mag": mag, "rel_residual": i["rel_residual"],
+        dmin = last[0][2]["min_distance"]
+        per_t = [{"t": i["t"], "solve_s": i["ms_total"] / 1e3, "mag": mag, "rel_residual": i["rel_residual"],
                   "ir_iters": i["ir_iters"], "precision_used": i["precision_used"], "fallback": i["fallback"],
                   "ms_generate": i["ms_generate"], "ms_factor": i["ms_factor"], "ms_solve": i["ms_solve"],
                   "ms_residual": i["ms_residual"], "residual_evals": i["residual_evals"],
@@ -320,8 +328,10 @@ def run_ours(a):
                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                "config": {"workload": f"n={a.n} points uniform in [0,1]^{a.m} (seed {workloads.SEEDS['cube']}+rank), "
                                       f"t in {{{', '.join(s.strip() for s in a.ts.split(','))}}}; one step = "
-                                      f"{len(ts)} solves to rel. residual <= 1e-14",
-                          "n": a.n, "m": a.m, "t": ts, "precision": a.precision, "residual_mode": a.resid,
+                                      f"{len(ts)} solves to rel. residual <= 1e-14 (the bound log(n-1)/min d "
+                                      f"found inside the step)",
+                          "n": a.n, "m": a.m, "t": [i["t"] for _, _, i in last], "precision": a.precision,
+                          "residual_mode": a.resid,
                           "panel_tiles": a.panel_tiles or "auto (16 split, 32 one-product)",
                           "parallelism": f"replicas x{world}",
                           "l2": "inputs larger than L2 (packed factor tiles of several GB per solve)",
@@ -330,6 +340,104 @@ def run_ours(a):
                "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
                "min_distance": dmin}
     return out, (ctx, Xd, X, ts)
+
+
+def _gpu_id(dev):
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    gid = str(getattr(props, "uuid", dev.index))
+    if gid and not gid.startswith("GPU-") and len(gid) > 8:
+        gid = "GPU-" + gid
+    return gid
+
+
+def _event_time(fn, dev):
+    """Device time (s) of fn() on the current stream, host-synchronised on both sides."""
+    import torch
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    r = fn()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / 1e3, r
+
+
+def fp64_dense_comparison(dev, n=16384, t=0.5, repeats=3):
+    """The metric's comparison: mixed precision + FP64 refinement (AUTO) against
+    the plain FP64 dense path on the same GPU -- this library's FP64 blocked
+    Cholesky (precision = fp64, CUDA-core FP64) and cuSOLVER's FP64 Cholesky
+    (torch.linalg.cholesky + cholesky_solve on the full square matrix) -- on
+    the precision workload (Gaussian mixture, n = 16384 in R^3, t = 0.5).
+    Device-timed, `repeats` runs each after one warm-up, clocks sampled."""
+    import torch
+
+    import paper_2607_23354_gb300 as M
+    import workloads
+    X = torch.from_numpy(workloads.gaussian_mixture_cloud(n=n)).to(dev)
+    sampler = ClockSampler(_gpu_id(dev))
+    res = {"workload": f"Gaussian mixture n={n} in R^3 (seed {workloads.SEEDS['mixture']}), t={t}",
+           "n": n, "t": t, "repeats": repeats}
+    sampler.start()
+    for prec in ("auto", "fp64"):
+        c = M.Context(M.Options(precision=prec))
+        c.solve(X, t)
+        times, info = [], None
+        for _ in range(repeats):
+            el, (_, _, info) = _event_time(lambda: c.solve(X, t), dev)
+            times.append(el)
+        res[f"{prec}_s"] = times
+        res[f"{prec}_rel_residual"] = info["rel_residual"]
+        res[f"{prec}_ir_iters"] = info["ir_iters"]
+        c.close()
+    try:
+        def cusolver():
+            d = torch.cdist(X, X)
+            Z = torch.exp(d.mul_(-t))
+            del d
+            L = torch.linalg.cholesky(Z)
+            w = torch.cholesky_solve(torch.ones(n, 1, dtype=torch.float64, device=dev), L)
+            return w
+        cusolver()
+        times = []
+        for _ in range(repeats):
+            el, w = _event_time(cusolver, dev)
+            times.append(el)
+        res["cusolver_fp64_s"] = times
+        del w
+        torch.cuda.empty_cache()
+    except Exception as e:  # noqa: BLE001
+        res["cusolver_fp64_error"] = str(e)[:160]
+    res["clocks"] = sampler.stop()
+    best = {k: min(v) for k, v in res.items() if k.endswith("_s") and isinstance(v, list)}
+    res["best_s"] = best
+    res["speedup_vs_own_fp64"] = best["fp64_s"] / best["auto_s"]
+    if "cusolver_fp64_s" in best:
+        res["speedup_vs_cusolver_fp64"] = best["cusolver_fp64_s"] / best["auto_s"]
+    return res
+
+
+def batch_throughput(dev, repeats=3):
+    """Batch solves/s: 512 clouds in R^32 (sizes log-uniform in [64, 2048]) x 8
+    values of t in [0.1, 10], one persistent solve launch per call
+    (mag_solve_batch), device-timed after one warm-up; best of `repeats`."""
+    import torch
+
+    import paper_2607_23354_gb300 as M
+    import workloads
+    c = M.Context(M.Options())
+    clouds, tvals = workloads.batch_clouds()
+    cl = [torch.from_numpy(x).to(dev) for x in clouds]
+    c.solve_batch(cl, list(tvals))
+    times, failed = [], 0
+    for _ in range(repeats):
+        el, (_, _, sts) = _event_time(lambda: c.solve_batch(cl, list(tvals)), dev)
+        times.append(el)
+        failed = int((sts != 0).sum())
+    c.close()
+    nsolves = len(cl) * len(tvals)
+    return {"workload": "512 clouds in R^32, n log-uniform in [64, 2048], x 8 t log-spaced in [0.1, 10]",
+            "solves": nsolves, "seconds": times, "solves_per_s": nsolves / min(times), "failed": failed}
 
 
 def run_extras(ctx, a, out, Xd):
@@ -427,9 +535,18 @@ def run_reference(a):
     if rank != 0:
         return None
     X = workloads.unit_cube_cloud(n=a.n, m=a.m)
-    n_s = min(a.cpu_sample_n, a.n)
-    Xs = workloads.subsample(X, n_s, seed=11)
     oracle.build()
+    # size the sample so that all warm-up and timed steps take about 150 s:
+    # time one 4096-point solve and scale by n^3 (between 2048 and the
+    # --cpu-sample-n cap)
+    Xc = workloads.subsample(X, min(4096, a.n), seed=12)
+    t0 = time.perf_counter()
+    oracle.weighting(Xc, 1.0, ir_steps=2)
+    calib = time.perf_counter() - t0
+    per_step = 150.0 / max(1, a.steps + a.warmup)
+    n_s = int(Xc.shape[0] * (per_step / calib) ** (1.0 / 3.0)) // 256 * 256
+    n_s = max(min(2048, a.n), min(n_s, a.cpu_sample_n, a.n))
+    Xs = workloads.subsample(X, n_s, seed=11)
     times = []
     for k in range(a.warmup + a.steps):
         t0 = time.perf_counter()
@@ -521,8 +638,55 @@ def run_paper_sweep(a):
             "n_gpus": world, "rank": rank, "data": "synthetic", "rows": rows}
 
 
+def run_fp64_dense_headline(a):
+    """One solve of the headline workload's first t (points uniform in
+    [0,1]^m, t = 1) by this library's plain FP64 path (precision = fp64) and
+    by AUTO, device-timed, and optionally cuSOLVER's FP64 Cholesky on the full
+    square matrix.  Minutes per FP64 solve at n = 1e5 (1.2 TFLOP/s FP64)."""
+    import torch
+
+    import paper_2607_23354_gb300 as M
+    import workloads
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n = a.fp64_dense_n
+    X = torch.from_numpy(workloads.unit_cube_cloud(n=n, m=a.m)).to(dev)
+    sampler = ClockSampler(_gpu_id(dev))
+    out = {"metric": "FP64 dense vs mixed+IR solve time", "n": n, "m": a.m, "t": 1.0, "data": "synthetic",
+           "workload": f"n={n} points uniform in [0,1]^{a.m} (seed {workloads.SEEDS['cube']}), t=1"}
+    sampler.start()
+    for prec in ("auto", "fp64"):
+        c = M.Context(M.Options(precision=prec, profile=True))
+        if prec == "auto":
+            c.solve(X, 1.0)  # warm-up (task tables, workspace)
+        el, (_, mag, info) = _event_time(lambda: c.solve(X, 1.0), dev)
+        out[prec] = {"seconds": el, "ms_generate": info["ms_generate"], "ms_factor": info["ms_factor"],
+                     "ms_solve": info["ms_solve"], "ms_residual": info["ms_residual"],
+                     "ir_iters": info["ir_iters"], "rel_residual": info["rel_residual"], "mag": mag,
+                     "precision_used": info["precision_used"], "useful_flops": info["useful_flops"],
+                     "tflops": info["useful_flops"] / el / 1e12}
+        c.close()
+        torch.cuda.empty_cache()
+    if not a.no_cusolver:
+        try:
+            def cusolver():
+                Z = torch.cdist(X, X).mul_(-1.0).exp_()
+                torch.linalg.cholesky(Z, out=Z)  # in place: 8 n^2 bytes in all
+                return torch.cholesky_solve(torch.ones(n, 1, dtype=torch.float64, device=dev), Z)
+            el, _ = _event_time(cusolver, dev)
+            out["cusolver_fp64"] = {"seconds": el, "tflops": (n ** 3 / 3) / el / 1e12}
+        except Exception as e:  # noqa: BLE001
+            out["cusolver_fp64"] = {"error": str(e)[:200]}
+    out["clocks"] = sampler.stop()
+    out["speedup_vs_own_fp64"] = out["fp64"]["seconds"] / out["auto"]["seconds"]
+    return out
+
+
 def main():
     a = parse_args()
+    if a.fp64_dense_n:
+        print(json.dumps(run_fp64_dense_headline(a)), flush=True)
+        return
     if a.paper_sweep:
         print(json.dumps(run_paper_sweep(a)), flush=True)
         return
@@ -538,6 +702,11 @@ def main():
     rank, world, _ = dist_env()
     if rank == 0:
         ctx, Xd, X, ts = state
+        if not a.no_comparators:
+            # the metric's other two parts, outside the timed region
+            out["fp64_dense"] = fp64_dense_comparison(Xd.device)
+            out["batch"] = batch_throughput(Xd.device)
+            out["batch_solves_per_s"] = out["batch"]["solves_per_s"]
         if a.extras:
             run_extras(ctx, a, out, Xd)
         if not a.no_cpu:

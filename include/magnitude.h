@@ -23,10 +23,11 @@
  *   - The library owns only the workspace inside a context (device memory it
  *     allocates and grows on demand, freed by mag_ctx_destroy).  A context is
  *     used by one host thread at a time; use one context per thread/stream.
- *   - Invalid arguments (n < 2, m < 1, t <= 0 or not finite, NULL pointers)
- *     give MAG_EINVAL before any device work.  Non-finite coordinates give
- *     MAG_EINVAL and coincident points MAG_EDUPLICATE (Z is then singular),
- *     both detected on the device while Z is generated.
+ *   - Invalid arguments (n < 2, m < 1 or m > MAG_MAX_DIM, t <= 0 or not
+ *     finite, NULL pointers) give MAG_EINVAL before any device work.
+ *     Non-finite coordinates give MAG_EINVAL and coincident points
+ *     MAG_EDUPLICATE (Z is then singular), both detected on the device while
+ *     Z is generated.
  */
 #ifndef MAGNITUDE_H
 #define MAGNITUDE_H
@@ -36,6 +37,11 @@
 #ifdef __cplusplus
 extern "C" {
 #endif
+
+/* Largest dimension m of the points accepted by every entry point (the
+ * matrix-free residual stages at least eight points of m + 1 doubles in
+ * shared memory).  mag_grad accepts m <= 64. */
+#define MAG_MAX_DIM 2048
 
 /* Status codes. */
 enum mag_status {
@@ -116,6 +122,13 @@ typedef struct mag_options {
                              precisions (FP16X3, TF32X3) only                 */
   int32_t tplus_method;   /* mag_sweep_tplus root-finder on min_j w_j(t):
                              0 (default) bisection, 1 Ridders' method        */
+  int64_t wait_timeout_ns;/* the persistent triangular sweeps wait for
+                             tiles that other CTAs solve; each wait gives up
+                             this long after the sweep started and the solve
+                             returns MAG_ETIMEOUT (default 1e10 = 10 s; must be
+                             > 0).  The context stays usable.  The
+                             tensor-core update keeps a fixed 20 s bound on
+                             its barrier waits.                               */
 } mag_options;
 
 /* Diagnostics of one call (all fields written when info != NULL). */
@@ -151,6 +164,8 @@ typedef struct mag_info {
                               refinement step of the one-product FP16 factor
                               (0 = no probe, +inf = its block factor broke down) */
   double ms_probe;         /* device time of the probe                          */
+  double t;                /* the t of this solve (the Sec. 1 bound where the
+                              call asked for it with t <= 0)                   */
 } mag_info;
 
 typedef struct mag_ctx mag_ctx;
@@ -208,9 +223,13 @@ int mag_solve(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t
 /* a2-a7 for several values of t on the same points (Sec. 2: Z = exp[-t d]
  * shares d across t): ts (host, nt values), W (device, nt x n row-major: the
  * weighting of ts[i] in row i), mags (host, nt), infos (host, nt, nullable).
- * The FP64 distances are computed once and kept for the call (see
- * reuse_distances).  Returns the first non-OK status; later t values are still
- * solved. */
+ * A value ts[i] <= 0 stands for the Sec. 1 bound t = log(n-1) / min d, with
+ * min d taken from the first solve of the call (the generator finds it while
+ * it forms Z): the positive values are solved first, in their order, then the
+ * bound entries (a call with only bound entries makes one min-distance pass
+ * first); infos[i].t reports the t solved.  The FP64 distances are computed
+ * once and kept for the call (see reuse_distances).  Returns the first non-OK
+ * status; later t values are still solved. */
 int mag_solve_multi(mag_ctx* ctx, const double* points, int64_t n, int32_t m, const double* ts, int32_t nt,
                     double* W, double* mags, mag_info* infos);
 
@@ -251,9 +270,11 @@ int mag_residual(mag_ctx* ctx, const double* points, int64_t n, int32_t m, doubl
  *
  * points: device n x m; w: device n; b: device n or NULL (all ones);
  * r_out: device n (required); norms: host, 4 doubles as in mag_residual;
- * stream: cudaStream_t (NULL = legacy default stream).  The call returns after
- * the stream has completed the work.  MAG_EINVAL for bad arguments,
- * MAG_ENOMEM when n > MAG_NOALLOC_MAX_N, MAG_ECUDA if a CUDA call fails. */
+ * stream: cudaStream_t (NULL = legacy default stream) of the current device,
+ * which must also be the device that holds the arrays.  The call returns
+ * after the stream has completed the work.  MAG_EINVAL for bad arguments
+ * (including m > MAG_MAX_DIM), MAG_ENOMEM when n > MAG_NOALLOC_MAX_N,
+ * MAG_ECUDA if a CUDA call fails. */
 int mag_residual_noalloc(const double* points, int64_t n, int32_t m, double t, const double* w,
                          const double* b, double* r_out, double* norms, void* stream);
 

@@ -31,8 +31,9 @@ MAG_OK, MAG_EINVAL, MAG_EDUPLICATE, MAG_ENOTPD, MAG_ENOCONV, MAG_ENOBRACKET, MAG
 PREC_AUTO, PREC_BF16, PREC_TF32, PREC_TF32X3, PREC_FP32, PREC_FP64, PREC_FP16X3, PREC_FP16 = range(8)
 PRECISIONS = {"auto": PREC_AUTO, "bf16": PREC_BF16, "tf32": PREC_TF32, "tf32x3": PREC_TF32X3,
               "fp32": PREC_FP32, "fp64": PREC_FP64, "fp16x3": PREC_FP16X3, "fp16": PREC_FP16}
-# #define MAG_NOALLOC_MAX_N
+# #define MAG_NOALLOC_MAX_N, MAG_MAX_DIM
 NOALLOC_MAX_N = 262144
+MAX_DIM = 2048
 # enum mag_residual_mode
 RESID_MATRIX_FREE, RESID_STORED, RESID_AUTO = 0, 1, 2
 
@@ -44,7 +45,8 @@ class mag_options(ctypes.Structure):
                 ("panel_tiles", ctypes.c_int32), ("workspace_limit_bytes", ctypes.c_double),
                 ("profile", ctypes.c_int32), ("reuse_distances", ctypes.c_int32),
                 ("lookahead", ctypes.c_int32), ("lookahead_sms", ctypes.c_int32),
-                ("cta_pairs", ctypes.c_int32), ("tplus_method", ctypes.c_int32)]
+                ("cta_pairs", ctypes.c_int32), ("tplus_method", ctypes.c_int32),
+                ("wait_timeout_ns", ctypes.c_int64)]
 
 
 class mag_info(ctypes.Structure):
@@ -62,7 +64,7 @@ class mag_info(ctypes.Structure):
                 ("update_launches", ctypes.c_int32), ("ms_update", ctypes.c_double),
                 ("update_flops", ctypes.c_double), ("ms_update_panel", ctypes.c_double),
                 ("ms_potrf", ctypes.c_double), ("ms_trsm", ctypes.c_double), ("ms_split", ctypes.c_double),
-                ("probe_rho", ctypes.c_double), ("ms_probe", ctypes.c_double)]
+                ("probe_rho", ctypes.c_double), ("ms_probe", ctypes.c_double), ("t", ctypes.c_double)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -150,6 +152,7 @@ class Options:
     lookahead_sms: int = 0
     cta_pairs: int = 1
     tplus_method: str = "bisection"
+    wait_timeout_ns: int = 10_000_000_000
 
     def to_c(self) -> mag_options:
         o = mag_options()
@@ -169,6 +172,7 @@ class Options:
         o.lookahead_sms = int(self.lookahead_sms)
         o.cta_pairs = int(self.cta_pairs)
         o.tplus_method = {"bisection": 0, "ridders": 1}[self.tplus_method]
+        o.wait_timeout_ns = int(self.wait_timeout_ns)
         return o
 
 
@@ -267,7 +271,10 @@ class Context:
 
     def solve_multi(self, X: torch.Tensor, ts, W: torch.Tensor | None = None):
         """Weightings for several t on the same points (distances computed once).
-        Returns (W [len(ts), n], mags list, infos list)."""
+        A t of "bound" (or <= 0) is the Sec. 1 bound log(n-1)/min d, found by
+        the call itself; infos[i]["t"] is the t solved.  Returns
+        (W [len(ts), n], mags list, infos list)."""
+        ts = [0.0 if (isinstance(t, str) and t == "bound") else t for t in ts]
         X = self._points(X)
         n, m = X.shape
         nt = len(ts)
@@ -398,16 +405,25 @@ def residual_noalloc(X: torch.Tensor, t: float, w: torch.Tensor, b: torch.Tensor
     library (static scratch; n <= NOALLOC_MAX_N).  Returns (r, norms dict);
     r is allocated here by PyTorch, not by the library."""
     lib = load_library()
-    X = X.to(torch.float64).contiguous()
+    if not isinstance(X, torch.Tensor) or X.dim() != 2 or not X.is_cuda:
+        raise TypeError("points must be a 2-D CUDA tensor (n x m)")
     n, m = X.shape
-    w = w.to(device=X.device, dtype=torch.float64).contiguous()
-    bb = None if b is None else b.to(device=X.device, dtype=torch.float64).contiguous()
-    r = torch.empty(n, dtype=torch.float64, device=X.device)
-    nr = (ctypes.c_double * 4)()
-    s = stream if stream is not None else torch.cuda.current_stream(X.device)
-    st = lib.mag_residual_noalloc(_P(X.data_ptr()), n, m, float(t), _P(w.data_ptr()),
-                                  _P(0) if bb is None else _P(bb.data_ptr()), _P(r.data_ptr()),
-                                  ctypes.cast(nr, _DP), _P(s.cuda_stream))
+    for name, v in (("w", w), ("b", b)):
+        if v is not None and (not isinstance(v, torch.Tensor) or v.numel() != n):
+            raise ValueError(f"{name} must be a tensor of n = {n} entries")
+    # the library picks its static scratch on the current device: make it X's
+    with torch.cuda.device(X.device):
+        X = X.to(torch.float64).contiguous()
+        w = w.to(device=X.device, dtype=torch.float64).contiguous().reshape(n)
+        bb = None if b is None else b.to(device=X.device, dtype=torch.float64).contiguous().reshape(n)
+        r = torch.empty(n, dtype=torch.float64, device=X.device)
+        nr = (ctypes.c_double * 4)()
+        s = stream if stream is not None else torch.cuda.current_stream(X.device)
+        if s.device != X.device:
+            raise ValueError(f"stream on {s.device}, points on {X.device}")
+        st = lib.mag_residual_noalloc(_P(X.data_ptr()), n, m, float(t), _P(w.data_ptr()),
+                                      _P(0) if bb is None else _P(bb.data_ptr()), _P(r.data_ptr()),
+                                      ctypes.cast(nr, _DP), _P(s.cuda_stream))
     if st != MAG_OK:
         raise MagnitudeError(st, "mag_residual_noalloc failed" +
                              (f" (n = {n} > {NOALLOC_MAX_N})" if st == MAG_ENOMEM else ""))
@@ -449,8 +465,9 @@ class MagnitudeFn(torch.autograd.Function):
     """(X, t) -> (w, Mag) with the adjoint gradients of mag_grad.
 
     Backward: for upstream grads gw (of w) and gM (of Mag), the loss gradient
-    with respect to w is g = gw + gM 1; the library solves lambda = Z^{-1} g
-    with the same solver and forms dL/dt and dL/dX in one fused pass."""
+    with respect to w is g = gw + gM 1, handed to mag_grad as is; the library
+    solves lambda = Z^{-1} g with the same solver (lambda = gM w without a
+    solve when g is constant) and forms dL/dt and dL/dX in one fused pass."""
 
     @staticmethod
     def forward(ctx, X, t):
@@ -464,15 +481,10 @@ class MagnitudeFn(torch.autograd.Function):
     def backward(ctx, gw, gM):
         X, w = ctx.saved_tensors
         c = default_context()
-        if gw is None or not bool(torch.any(gw != 0)):
-            scale = 0.0 if gM is None else float(gM)
-            dt, dx = c.grad(X.detach(), ctx.t, w=w)
-            dt, dx = dt * scale, dx * scale
-        else:
-            g = gw.to(torch.float64)
-            if gM is not None:
-                g = g + gM.to(torch.float64)
-            dt, dx = c.grad(X.detach(), ctx.t, w=w, dL_dw=g)
+        g = torch.zeros_like(w) if gw is None else gw.to(torch.float64).reshape(w.shape)
+        if gM is not None:
+            g = g + gM.to(torch.float64)
+        dt, dx = c.grad(X.detach(), ctx.t, w=w, dL_dw=g.contiguous())
         dX = dx.to(X.dtype)
         dT = torch.tensor(dt, dtype=torch.float64, device=X.device)
         return dX, dT

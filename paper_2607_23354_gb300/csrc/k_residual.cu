@@ -435,6 +435,28 @@ __global__ void __launch_bounds__(1024) k_sum_f64(const double* __restrict__ v, 
   if (threadIdx.x == 0) *out = ss[0] + sc[0];
 }
 
+// out[0] = min_i v_i, out[1] = max_i v_i (one CTA).
+__global__ void __launch_bounds__(1024) k_minmax_f64(const double* __restrict__ v, int64_t n, double* out) {
+  __shared__ double smin[32], smax[32];
+  double lo = INFINITY, hi = -INFINITY;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    lo = fmin(lo, v[i]);
+    hi = fmax(hi, v[i]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if ((threadIdx.x & 31) == 0) smin[threadIdx.x >> 5] = lo, smax[threadIdx.x >> 5] = hi;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) lo = fmin(lo, smin[w]), hi = fmax(hi, smax[w]);
+    out[0] = lo;
+    out[1] = hi;
+  }
+}
+
 // GMRES helpers (FP64): out[i] = <V_i, w> for i < k (V: k rows of length ld),
 // one CTA per i; and w -= sum_i h[i] V_i; and x = s * w.
 __global__ void __launch_bounds__(256) k_mdot(const double* __restrict__ V, int64_t ld, int k,
@@ -484,10 +506,18 @@ inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + thre
 cudaError_t launch_residual_mf(const double* X, int64_t n, int m, double t, const double* w,
                                const double* b, double* r, double* part, int chunks, int64_t np,
                                DevStatus* st, cudaStream_t s, int kind) {
+  if (m < 1 || m > MAG_MAX_DIM) return cudaErrorInvalidValue;
   int ct = 128;
-  while (ct > 8 && (size_t)ct * (m + 1) * sizeof(double) > 48 * 1024) ct /= 2;
+  while (ct > 8 && (size_t)ct * (m + 1) * sizeof(double) > 44 * 1024) ct /= 2;
   const size_t smem = (size_t)ct * (m + 1) * sizeof(double);
   const dim3 grid(blocks_for(n, RES_THREADS), (unsigned)chunks);
+  if (smem > 44 * 1024) {
+    // large m: eight column points per stage need more than the default
+    // 48 KB of static (4 KB exp table) plus dynamic shared memory; at most
+    // 8 x 2049 doubles = 131 KB
+    cudaError_t e = cudaFuncSetAttribute(k_resid_mf<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   if (m <= 8)
     k_resid_mf<8><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct, kind);
   else if (m <= 16)
@@ -591,7 +621,7 @@ cudaError_t launch_grad(const double* X, int64_t n, int m, double t, const doubl
                         cudaStream_t s) {
   (void)np;
   int ct = 128;
-  while (ct > 8 && (size_t)ct * (m + 2) * sizeof(double) > 48 * 1024) ct /= 2;
+  while (ct > 8 && (size_t)ct * (m + 2) * sizeof(double) > 44 * 1024) ct /= 2;  // + 4 KB exp table
   const size_t smem = (size_t)ct * (m + 2) * sizeof(double);
   const unsigned grid = blocks_for(n, RES_THREADS);
   if (m <= 8)
@@ -610,6 +640,12 @@ cudaError_t launch_grad(const double* X, int64_t n, int m, double t, const doubl
 
 cudaError_t launch_sum_f64(const double* v, int64_t n, double* out, cudaStream_t s) {
   k_sum_f64<<<1, 1024, 0, s>>>(v, n, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_minmax(const double* v, int64_t n, double* out2, cudaStream_t s) {
+  k_minmax_f64<<<1, 1024, 0, s>>>(v, n, out2);
   note_launch();
   return cudaGetLastError();
 }
@@ -654,7 +690,8 @@ cudaError_t noalloc_scratch(double** out) {
 extern "C" int mag_residual_noalloc(const double* points, int64_t n, int32_t m, double t, const double* w,
                                     const double* b, double* r_out, double* norms, void* stream) {
   using namespace mag;
-  if (!points || !w || !r_out || !norms || n < 2 || m < 1 || !(t > 0.0) || !isfinite(t)) return MAG_EINVAL;
+  if (!points || !w || !r_out || !norms || n < 2 || m < 1 || m > MAG_MAX_DIM || !(t > 0.0) || !isfinite(t))
+    return MAG_EINVAL;
   if (n > MAG_NOALLOC_MAX_N) return MAG_ENOMEM;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* scratch = nullptr;

@@ -249,14 +249,13 @@ int coop_grid(K kern, int64_t N, size_t smem) {
 
 template <typename T, typename K>
 cudaError_t launch_sweep(K kern, const T* Z, const T* D, int64_t N, const T* in, T* out, unsigned* progress,
-                         DevStatus* st, cudaStream_t s) {
+                         DevStatus* st, uint64_t timeout, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(progress, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   const size_t smem = (size_t)TILE_ELEMS * sizeof(T);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = coop_grid(kern, N, smem);
-  uint64_t timeout = 10000000000ull;
   void* args[] = {(void*)&Z, (void*)&D, (void*)&N, (void*)&in, (void*)&out, (void*)&progress, (void*)&st,
                   (void*)&timeout};
   e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(TS_THREADS), args, smem, s);
@@ -268,23 +267,23 @@ cudaError_t launch_sweep(K kern, const T* Z, const T* D, int64_t N, const T* in,
 
 template <typename T>
 cudaError_t launch_forward_persistent(const T* Z, const T* Dinv, int64_t N, const T* v, T* y, unsigned* flags,
-                                      DevStatus* st, cudaStream_t s) {
-  return launch_sweep<T>(k_forward_persistent<T>, Z, Dinv + N * TILE_ELEMS, N, v, y, flags, st, s);
+                                      DevStatus* st, uint64_t timeout_ns, cudaStream_t s) {
+  return launch_sweep<T>(k_forward_persistent<T>, Z, Dinv + N * TILE_ELEMS, N, v, y, flags, st, timeout_ns, s);
 }
 
 template <typename T>
 cudaError_t launch_backward_persistent(const T* Z, const T* Dinv, int64_t N, const T* yv, T* x, unsigned* flags,
-                                       DevStatus* st, cudaStream_t s) {
-  return launch_sweep<T>(k_backward_persistent<T>, Z, Dinv, N, yv, x, flags, st, s);
+                                       DevStatus* st, uint64_t timeout_ns, cudaStream_t s) {
+  return launch_sweep<T>(k_backward_persistent<T>, Z, Dinv, N, yv, x, flags, st, timeout_ns, s);
 }
 
 template cudaError_t launch_forward_persistent<float>(const float*, const float*, int64_t, const float*, float*,
-                                                      unsigned*, DevStatus*, cudaStream_t);
+                                                      unsigned*, DevStatus*, uint64_t, cudaStream_t);
 template cudaError_t launch_forward_persistent<double>(const double*, const double*, int64_t, const double*,
-                                                       double*, unsigned*, DevStatus*, cudaStream_t);
+                                                       double*, unsigned*, DevStatus*, uint64_t, cudaStream_t);
 template cudaError_t launch_backward_persistent<float>(const float*, const float*, int64_t, const float*, float*,
-                                                       unsigned*, DevStatus*, cudaStream_t);
+                                                       unsigned*, DevStatus*, uint64_t, cudaStream_t);
 template cudaError_t launch_backward_persistent<double>(const double*, const double*, int64_t, const double*,
-                                                        double*, unsigned*, DevStatus*, cudaStream_t);
+                                                        double*, unsigned*, DevStatus*, uint64_t, cudaStream_t);
 
 }  // namespace mag

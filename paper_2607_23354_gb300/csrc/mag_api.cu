@@ -287,7 +287,7 @@ int check_args(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double 
   if (!ctx) return MAG_EINVAL;
   if (!points) return fail(ctx, MAG_EINVAL, "points is NULL");
   if (n < 2) return fail(ctx, MAG_EINVAL, "n = %lld < 2", (long long)n);
-  if (m < 1) return fail(ctx, MAG_EINVAL, "m = %d < 1", (int)m);
+  if (m < 1 || m > MAG_MAX_DIM) return fail(ctx, MAG_EINVAL, "m = %d outside [1, %d]", (int)m, MAG_MAX_DIM);
   if (n > (int64_t)1 << 31) return fail(ctx, MAG_EINVAL, "n = %lld too large", (long long)n);
   if (!(t > 0.0) || !std::isfinite(t)) return fail(ctx, MAG_EINVAL, "t = %g must be finite and > 0", t);
   return MAG_OK;
@@ -662,6 +662,7 @@ int mag_options_default(mag_options* opt) {
   opt->lookahead_sms = 0;
   opt->cta_pairs = 1;
   opt->tplus_method = 0;
+  opt->wait_timeout_ns = 10000000000ll;
   return MAG_OK;
 }
 
@@ -671,6 +672,10 @@ int mag_ctx_create(mag_ctx** out, void* stream, const mag_options* opt) {
   mag_ctx* ctx = new (std::nothrow) mag_ctx();
   if (!ctx) return MAG_ENOMEM;
   ctx->stream = (cudaStream_t)stream;
+  if (opt && opt->wait_timeout_ns <= 0) {
+    delete ctx;
+    return MAG_EINVAL;
+  }
   if (opt)
     ctx->opt = *opt;
   else
@@ -693,6 +698,7 @@ int mag_ctx_create(mag_ctx** out, void* stream, const mag_options* opt) {
 
 int mag_ctx_set_options(mag_ctx* ctx, const mag_options* opt) {
   if (!ctx || !opt) return MAG_EINVAL;
+  if (opt->wait_timeout_ns <= 0) return fail(ctx, MAG_EINVAL, "wait_timeout_ns must be > 0");
   ctx->opt = *opt;
   return MAG_OK;
 }
@@ -919,8 +925,9 @@ int correction_t(mag_ctx* ctx, T* Z, T* Dinv, T* v, T* y, const double* r, doubl
                  int64_t np, int64_t N) {
   cudaStream_t s = ctx->stream;
   CU(launch_scale_rhs<T>(r, n, np, v, ctx->st(), s));
-  CU(launch_forward_persistent<T>(Z, Dinv, N, v, y, ctx->flags(), ctx->st(), s));
-  CU(launch_backward_persistent<T>(Z, Dinv, N, y, v, ctx->flags(), ctx->st(), s));
+  const uint64_t tmo = (uint64_t)ctx->opt.wait_timeout_ns;
+  CU(launch_forward_persistent<T>(Z, Dinv, N, v, y, ctx->flags(), ctx->st(), tmo, s));
+  CU(launch_backward_persistent<T>(Z, Dinv, N, y, v, ctx->flags(), ctx->st(), tmo, s));
   CU(launch_accumulate<T>(x, v, n, ctx->st(), init, s));
   return MAG_OK;
 }
@@ -955,6 +962,9 @@ int residual(mag_ctx* ctx, const double* X, int32_t m, double t, const double* w
     CU(launch_residual_mf(X, L.n, m, t, w, b, r, ctx->part(), L.chunks, L.np, ctx->st(), s, ctx->kind));
   CU(cudaEventRecord(ctx->ev[1], s));
   TRY(read_status(ctx));
+  if (ctx->h_st->flags & ST_TIMEOUT)
+    return fail(ctx, MAG_ETIMEOUT, "a bounded wait of a triangular sweep expired (wait_timeout_ns = %lld)",
+                (long long)ctx->opt.wait_timeout_ns);
   R->ms_res += elapsed(ctx, 0, 1);
   R->residual_evals++;
   const double rn = bits_to_double(ctx->h_st->r_max_bits);
@@ -1446,6 +1456,7 @@ int mag_solve(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t
   }
   fill_info(ctx, R, n, info);
   if (info) {
+    info->t = t;
     float ms = 0;
     if (!timed || cudaEventElapsedTime(&ms, t0, t1) != cudaSuccess) {
       cudaGetLastError();  // the end event was not recorded (failed solve): no total time
@@ -1464,13 +1475,36 @@ int mag_solve_multi(mag_ctx* ctx, const double* points, int64_t n, int32_t m, co
   TRY(check_args(ctx, points, n, m, 1.0));
   if (!ts || nt < 1 || !W || !mags) return fail(ctx, MAG_EINVAL, "bad multi-t arguments");
   for (int32_t i = 0; i < nt; ++i)
-    if (!(ts[i] > 0.0) || !std::isfinite(ts[i])) return fail(ctx, MAG_EINVAL, "t[%d] = %g", (int)i, ts[i]);
+    if (!std::isfinite(ts[i])) return fail(ctx, MAG_EINVAL, "t[%d] = %g", (int)i, ts[i]);
+  // explicit t first (their solves find min d), then the Sec. 1 bound entries
+  std::vector<int32_t> order;
+  for (int32_t i = 0; i < nt; ++i)
+    if (ts[i] > 0.0) order.push_back(i);
+  for (int32_t i = 0; i < nt; ++i)
+    if (!(ts[i] > 0.0)) order.push_back(i);
   begin_dist_reuse(ctx, n);
   int first = MAG_OK;
   std::string first_err;
-  for (int32_t i = 0; i < nt; ++i) {
+  double dmin = -1.0;  // min d from a solve of this call (-1: none yet)
+  for (int32_t i : order) {
     mag_info inf;
-    const int st = mag_solve(ctx, points, n, m, ts[i], W + (size_t)i * n, &mags[i], &inf);
+    std::memset(&inf, 0, sizeof inf);
+    double t = ts[i];
+    int st = MAG_OK;
+    if (!(t > 0.0)) {
+      if (dmin < 0.0) {
+        double bound = 0.0;
+        st = mag_min_distance(ctx, points, n, m, &dmin, &bound);
+        if (st != MAG_OK) dmin = -1.0;
+      }
+      if (st == MAG_OK && !(dmin > 0.0)) st = fail(ctx, MAG_EDUPLICATE, "two points coincide (min d = 0)");
+      if (st == MAG_OK) t = std::log((double)(n - 1)) / dmin;
+    }
+    if (st == MAG_OK) {
+      st = mag_solve(ctx, points, n, m, t, W + (size_t)i * n, &mags[i], &inf);
+      if (dmin < 0.0 && (st == MAG_OK || st == MAG_ENOCONV || st == MAG_ENOTPD)) dmin = inf.min_distance;
+    }
+    inf.t = t;
     if (infos) infos[i] = inf;
     if (st != MAG_OK && first == MAG_OK) {
       first = st;
@@ -1669,7 +1703,19 @@ int mag_grad(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t,
     double mg = 0;
     TRY(mag_solve(ctx, points, n, m, t, wv, &mg, &si));
   }
+  bool constant_g = false;
+  double gc = 0.0;
   if (dL_dw) {
+    // a constant g = c 1 (the loss c Mag) needs no adjoint solve: lambda = c w
+    if (!ctx->ws) TRY(ensure_workspace(ctx, n, false, false));
+    CU(launch_minmax(dL_dw, n, &ctx->st()->aux[1], s));
+    TRY(read_status(ctx));
+    constant_g = ctx->h_st->aux[1] == ctx->h_st->aux[2];
+    gc = ctx->h_st->aux[1];
+  }
+  if (dL_dw && constant_g) {
+    CU(launch_scale(wv, gc, lam, n, s));
+  } else if (dL_dw) {
     // adjoint solve lambda = Z^{-1} g
     CU(cudaMemcpyAsync(g, dL_dw, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     mag_info ai;
@@ -1698,7 +1744,7 @@ int mag_solve_batch(mag_ctx* ctx, const mag_batch_desc* desc, int32_t count, con
   if (count == 0) return MAG_OK;
   for (int32_t i = 0; i < count; ++i) {
     const mag_batch_desc& d = desc[i];
-    if (d.n < 2 || d.m < 1 || !(d.t > 0.0) || !std::isfinite(d.t) || d.point_offset < 0 || d.w_offset < 0)
+    if (d.n < 2 || d.m < 1 || d.m > MAG_MAX_DIM || !(d.t > 0.0) || !std::isfinite(d.t) || d.point_offset < 0 || d.w_offset < 0)
       return fail(ctx, MAG_EINVAL, "bad descriptor %d (n=%d m=%d t=%g)", (int)i, (int)d.n, (int)d.m, d.t);
   }
   cudaStream_t s = ctx->stream;

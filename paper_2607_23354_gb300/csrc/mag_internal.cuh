@@ -188,14 +188,16 @@ cudaError_t launch_forward(const T* Z, const T* Dinv, int64_t N, T* v, T* tmp, c
 template <typename T>
 cudaError_t launch_backward(const T* Z, const T* Dinv, int64_t N, T* v, T* tmp, cudaStream_t s);
 
-// K3, persistent single-launch versions (cooperative; per-tile ready flags,
-// N unsigned of scratch).  Same arguments as above; y/x must not alias v/yv.
+// K3, persistent single-launch versions (cooperative; one progress counter,
+// flags[0]).  Same arguments as above; y/x must not alias v/yv.  Every wait
+// for another CTA's tile gives up timeout_ns after the launch started and
+// raises ST_TIMEOUT (the results are then invalid).
 template <typename T>
 cudaError_t launch_forward_persistent(const T* Z, const T* Dinv, int64_t N, const T* v, T* y, unsigned* flags,
-                                      DevStatus* st, cudaStream_t s);
+                                      DevStatus* st, uint64_t timeout_ns, cudaStream_t s);
 template <typename T>
 cudaError_t launch_backward_persistent(const T* Z, const T* Dinv, int64_t N, const T* yv, T* x, unsigned* flags,
-                                       DevStatus* st, cudaStream_t s);
+                                       DevStatus* st, uint64_t timeout_ns, cudaStream_t s);
 
 // K4: FP64 residual r = b - Z w (b == null means all ones), Z regenerated
 // from the points (matrix free) or read from FP64 packed tiles (stored).
@@ -261,5 +263,7 @@ cudaError_t launch_grad(const double* X, int64_t n, int m, double t, const doubl
                         const double* lam, double* dL_dx, double* part_t, int64_t np,
                         cudaStream_t s);
 cudaError_t launch_sum_f64(const double* v, int64_t n, double* out, cudaStream_t s);
+// out2[0] = min_i v_i, out2[1] = max_i v_i (device).
+cudaError_t launch_minmax(const double* v, int64_t n, double* out2, cudaStream_t s);
 
 }  // namespace mag

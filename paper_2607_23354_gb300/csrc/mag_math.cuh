@@ -28,7 +28,11 @@ __device__ __forceinline__ void load_exp_table(double* tab) {
 }
 
 __device__ __forceinline__ double exp_neg(double x, const double* tab) {
-  if ((__double2hiint(x) & 0x7ff00000) == 0x7ff00000) return x != x ? x : 0.0;  // NaN, -inf
+  // |x| >= 1024 (high word at least that of 1024.0), -inf and NaN leave on
+  // the integer pipe: every such result is 0 (NaN propagates).  The test also
+  // keeps N = round(256 x / ln 2) far inside the int32 low word read below,
+  // which would wrap for x below about -5.8e6.
+  if ((__double2hiint(x) & 0x7fffffff) >= 0x40900000) return x != x ? x : 0.0;
   const double shift = 0x1.8p52;
   double kd = fma(x, EXPT_INV_L, shift);
   const int N = __double2loint(kd);        // round(x 256 / ln 2)

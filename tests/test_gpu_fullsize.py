@@ -121,3 +121,108 @@ def test_grid_support_sweep_full(ctx):
     assert np.array_equal(_signs(r["w"].cpu().numpy()), _signs(w_ref))
     dmin, tb = ctx.min_distance(_dev(G))
     assert tb == pytest.approx(math.log(len(G) - 1), rel=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# The headline distribution ([0, 1]^8; the leading points of the seeded
+# n = 1e5 cloud) at multi-panel sizes, default AUTO options: every weighting
+# against the oracle's, elementwise, with the AUTO branch each t takes.  The
+# oracle here factors with LAPACK (oracle.weighting_lapack: same definition,
+# library Cholesky as the factor step), so n = 32768 runs in about a minute.
+
+def _report(name, rows):
+    """Write a table of measured errors to $MAG_REPORT_DIR/<name>.json (when set)."""
+    import json
+    import os
+    d = os.environ.get("MAG_REPORT_DIR")
+    if d:
+        os.makedirs(d, exist_ok=True)
+        with open(os.path.join(d, name + ".json"), "w") as f:
+            json.dump(rows, f, indent=1)
+
+
+def _compare(X, t, wg, mag, ref):
+    w_ref, mag_ref, oinfo = ref
+    return {"t": t, "rel_residual_by_oracle": oracle.relative_residual(X, t, wg),
+            "w_err": float(np.abs(wg - w_ref).max() / np.abs(w_ref).max()),
+            "mag_err": abs(mag - mag_ref) / abs(mag_ref),
+            "signs_equal": bool(np.array_equal(_signs(wg), _signs(w_ref))),
+            "kappa1_est": oinfo["kappa1_est"], "oracle_rel_residual": oinfo["rel_residual"]}
+
+
+@pytest.mark.parametrize("n", [16384, 32768])
+def test_cube_auto_branches_against_oracle_weighting(ctx, n):
+    X = workloads.unit_cube_cloud(n=n)
+    Xd = _dev(X)
+    W, mags, infos = ctx.solve_multi(Xd, [1.0, 10.0, "bound"])
+    rows = []
+    for i, which in enumerate(["t=1", "t=10", "bound"]):
+        info = infos[i]
+        t = info["t"]
+        wg = W[i].cpu().numpy()
+        c = _compare(X, t, wg, mags[i], oracle.weighting_lapack(X, t))
+        c.update(n=n, which=which, precision_used=info["precision_used"], probe_rho=info["probe_rho"],
+                 gershgorin_lmin=info["gershgorin_lmin"], fallback=info["fallback"], ir_iters=info["ir_iters"])
+        rows.append(c)
+        assert c["rel_residual_by_oracle"] <= 1e-14, c
+        assert c["w_err"] <= 1e-9, c
+        assert c["mag_err"] <= 1e-10, c
+        assert c["signs_equal"], c
+        assert info["fallback"] == 0
+        if which == "t=1":      # probe: FP16 would refine too slowly -> split factor
+            assert info["precision_used"] == M.PREC_FP16X3 and info["probe_rho"] > 1e-2
+        elif which == "t=10":   # probe: FP16 refines fast -> one product
+            assert 0.0 < info["probe_rho"] < 1e-2
+            # at n = 16384 its extra refinement steps may outweigh the factor
+            # time saved (the rule weighs them against n / 9500 steps)
+            if n >= 32768:
+                assert info["precision_used"] == M.PREC_FP16
+            else:
+                assert info["precision_used"] in (M.PREC_FP16, M.PREC_FP16X3)
+        else:                   # Gershgorin bound lambda_min >= 1/2: FP16 without a probe
+            assert info["precision_used"] == M.PREC_FP16 and info["gershgorin_lmin"] >= 0.5
+            assert info["probe_rho"] == 0.0
+            assert t == pytest.approx(oracle.tplus_bound(X), rel=1e-15)
+    _report(f"cube_auto_n{n}", rows)
+
+
+# Per-precision error table: each factor precision forced, refined to the same
+# tolerance, against the oracle, on the headline distribution (n = 16384) and
+# on the precision workload (Gaussian mixture, n = 16384, t in {0.05, 0.5, 5,
+# bound}).  Where kappa_1(Z) is large (the mixture at t = 0.05) the weighting
+# is fixed only to kappa times the residuals ("parity bounded by kappa"):
+# ||dw||inf / ||w||inf <= kappa (res_gpu + res_oracle), checked with LAPACK's
+# kappa_1 estimate and a margin of 10 for the estimate.
+TABLE_PRECISIONS = ["auto", "fp16x3", "fp16", "tf32x3", "fp64"]
+
+
+@pytest.mark.parametrize("workload", ["cube", "mixture"])
+def test_per_precision_error_table(workload):
+    if workload == "cube":
+        X = workloads.unit_cube_cloud(n=16384)
+        ts = [1.0, 10.0, oracle.tplus_bound(X)]
+    else:
+        X = workloads.gaussian_mixture_cloud()
+        ts = [0.05, 0.5, 5.0, oracle.tplus_bound(X)]
+    Xd = _dev(X)
+    rows = []
+    refs = {t: oracle.weighting_lapack(X, t) for t in ts}
+    for prec in TABLE_PRECISIONS:
+        c = M.Context(M.Options(precision=prec))
+        for t in ts:
+            w, mag, info = c.solve(Xd, t, allow_noconv=True)
+            wg = w.cpu().numpy()
+            row = _compare(X, t, wg, mag, refs[t])
+            row.update(workload=workload, precision=prec, precision_used=info["precision_used"],
+                       fallback=info["fallback"], ir_iters=info["ir_iters"], gmres_iters=info["gmres_iters"],
+                       status=info["status"], solve_ms=info["ms_total"])
+            rows.append(row)
+            assert info["status"] == M.MAG_OK, row
+            assert row["rel_residual_by_oracle"] <= 1e-14, row
+            bound = 10.0 * row["kappa1_est"] * (row["rel_residual_by_oracle"] + row["oracle_rel_residual"])
+            assert row["w_err"] <= max(1e-9, bound), row
+            if bound <= 1e-9:
+                assert row["mag_err"] <= 1e-10, row
+                assert row["signs_equal"], row
+        c.close()
+    _report(f"precision_table_{workload}", rows)

@@ -262,6 +262,104 @@ def test_residual_of_exact_two_point_solution():
     np.testing.assert_array_equal(r2, [1.0, 1.0])
 
 
+def _exact_residual_norms(Z, w, b=None):
+    """||b - Zw||inf, max row sum of Z and ||w||inf in exact rational
+    arithmetic on the given FP64 entries (each rounded once at the end)."""
+    from fractions import Fraction
+    n = len(w)
+    wf = [Fraction(float(v)) for v in w]
+    rmax, zmax = Fraction(0), Fraction(0)
+    for j in range(n):
+        row = [Fraction(float(z)) for z in Z[j]]
+        bj = Fraction(1) if b is None else Fraction(float(b[j]))
+        rmax = max(rmax, abs(bj - sum(z * v for z, v in zip(row, wf))))
+        zmax = max(zmax, sum(row))
+    return float(rmax), float(zmax), float(max(abs(v) for v in wf))
+
+
+@pytest.mark.parametrize("a,b", [(0.3, -0.7), (2.5, 1e-3), (-1e-8, 4.0)])
+def test_relative_residual_two_point_closed_form(a, b):
+    # two points at distance 5, w = (a, b) far from the solution: r and the
+    # norms are closed forms, ||Z||inf = 1 + e^{-5t} (diagonal included)
+    X = np.array([[0.0, 0.0, 0.0], [3.0, 4.0, 0.0]])
+    t = 0.3
+    z = math.exp(-5 * t)
+    r1 = abs(1 - a - z * b)
+    r2 = abs(1 - z * a - b)
+    expect = max(r1, r2) / ((1 + z) * max(abs(a), abs(b)))
+    got = oracle.relative_residual(X, t, np.array([a, b]))
+    assert got == pytest.approx(expect, rel=1e-14)
+    # a general right-hand side enters r, not the normalisation
+    bb = np.array([2.0, -3.0])
+    expect_b = max(abs(2 - a - z * b), abs(-3 - z * a - b)) / ((1 + z) * max(abs(a), abs(b)))
+    assert oracle.relative_residual(X, t, np.array([a, b]), b=bb) == pytest.approx(expect_b, rel=1e-14)
+
+
+@pytest.mark.parametrize("seed,t,perturb", [(41, 0.7, 1.0), (42, 3.0, 1e-7)])
+def test_relative_residual_against_exact_rational_sums(seed, t, perturb):
+    # n = 200 in R^3: the norm step against exact sums of the (pinned) FP64
+    # entries of Z; w is the solution plus a perturbation, so the residual is
+    # large compared with the rounding of any single row sum
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((200, 3))
+    Z = np.exp(-t * squareform(pdist(X)))
+    w = scipy.linalg.solve(Z, np.ones(200), assume_a="pos") + perturb * rng.standard_normal(200)
+    Zo = oracle.similarity_matrix(X, t)
+    rmax, zmax, wmax = _exact_residual_norms(Zo, w)
+    got = oracle.relative_residual(X, t, w)
+    assert got == pytest.approx(rmax / (zmax * wmax), rel=1e-12)
+    r, rs = oracle.residual_rows(X, t, w)
+    assert np.abs(r).max() == pytest.approx(rmax, rel=1e-12)
+    assert rs.max() == pytest.approx(zmax, rel=1e-15)
+
+
+def test_solve_info_norms_are_the_relative_residual():
+    # orc_solve's info: ||Z||inf and ||x||inf exactly, and its relative
+    # residual the one of orc_relative_residual (pinned above) for the same x
+    X = np.random.default_rng(43).standard_normal((150, 4))
+    b = np.random.default_rng(44).standard_normal(150)
+    t = 0.6
+    for bb in (None, b):
+        x, info = oracle.solve(X, t, b=bb, ir_steps=1)
+        _, zmax, wmax = _exact_residual_norms(oracle.similarity_matrix(X, t), x, bb)
+        assert info["z_norm_inf"] == pytest.approx(zmax, rel=1e-15)
+        assert info["x_norm_inf"] == wmax
+        assert info["rel_residual"] == pytest.approx(oracle.relative_residual(X, t, x, b=bb), rel=1e-12)
+        assert 0 < info["rel_residual"] <= 1e-15
+        w, mag, winfo = oracle.weighting(X, t, ir_steps=1) if bb is None else (None, None, None)
+        if bb is None:
+            assert winfo["rel_residual"] == pytest.approx(oracle.relative_residual(X, t, w), rel=1e-12)
+
+
+@pytest.mark.parametrize("t", [0.05, 1.0, 7.0])
+def test_weighting_lapack_closed_forms_and_agreement(t):
+    # the library-factor weighting: two points, points on a line, the centred
+    # 12-gon (closed forms), and the plain-loop weighting on a random cloud
+    X2 = np.array([[0.0, 0.0], [3.0, 4.0]])
+    w2, mag2, _ = oracle.weighting_lapack(X2, t)
+    assert mag2 == pytest.approx(2 / (1 + math.exp(-5 * t)), rel=1e-14)
+    Xl, gaps, _ = _collinear(40, 3, seed=31)
+    wl, _, info = oracle.weighting_lapack(Xl, t)
+    np.testing.assert_allclose(wl, _collinear_w(gaps, t), rtol=1e-12, atol=1e-14)
+    assert info["rel_residual"] < 1e-15
+    k = 12
+    S = _kgon_S(t, k)
+    wk, _, _ = oracle.weighting_lapack(_kgon(k), t)
+    den = S - k * math.exp(-2 * t)
+    assert wk[0] == pytest.approx((S - k * math.exp(-t)) / den, rel=1e-11, abs=1e-13)
+    np.testing.assert_allclose(wk[1:], (1 - math.exp(-t)) / den, rtol=1e-11, atol=1e-13)
+    X = np.random.default_rng(32).random((400, 5))
+    wa, ma, ia = oracle.weighting_lapack(X, t)
+    wb, mb, ib = oracle.weighting(X, t)
+    assert np.abs(wa - wb).max() <= 1e-10 * np.abs(wb).max()
+    assert ma == pytest.approx(mb, rel=1e-12)
+    assert ia["min_w"] == wa.min() and ia["rel_residual"] <= 1e-15
+    # the condition estimate against the exact 1-norm condition number
+    Z = oracle.similarity_matrix(X, t)
+    k1 = np.linalg.norm(Z, 1) * np.linalg.norm(np.linalg.inv(Z), 1)
+    assert k1 / 3 <= ia["kappa1_est"] <= k1 * 1.0000001
+
+
 def test_general_rhs_solve_matches_dense_library_solve():
     X = np.random.default_rng(17).standard_normal((120, 3))
     b = np.random.default_rng(18).standard_normal(120)
