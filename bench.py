@@ -64,6 +64,9 @@ def parse_args():
                    help="instead of the headline step: the FP64 dense paths against AUTO at this n "
                         "(points uniform in [0,1]^8, t=1; --no-cusolver to skip cuSOLVER)")
     p.add_argument("--no-cusolver", action="store_true")
+    p.add_argument("--ooc-n", type=int, default=0,
+                   help="instead of the headline step: one solve of n points in [0,1]^8 at --ts' first t with the "
+                        "default options (out of core when the FP32 tiles do not fit in device memory)")
     p.add_argument("--cta-pairs", type=int, default=1,
                    help="CTA-pair (cta_group::2) tensor-core updates: 1 always, 0 never, 2 split precisions only")
     return p.parse_args()
@@ -682,8 +685,46 @@ def run_fp64_dense_headline(a):
     return out
 
 
+def run_out_of_core(a):
+    """One solve of a workload past the GPU's memory (the packed FP32 tiles
+    alone exceed it): the slabs, the bytes kept in host memory, the rate of
+    the reads from host memory over the CPU-GPU link, and the solve's time."""
+    import torch
+
+    import paper_2607_23354_gb300 as M
+    import workloads
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n = a.ooc_n
+    t = float(a.ts.split(",")[0])
+    X = torch.from_numpy(workloads.unit_cube_cloud(n=n, m=a.m)).to(dev)
+    c = M.Context(M.Options(profile=True))
+    sampler = ClockSampler(_gpu_id(dev))
+    sampler.start()
+    el, (_, mag, info) = _event_time(lambda: c.solve(X, t), dev)
+    clocks = sampler.stop()
+    keys = ("precision_used", "probe_rho", "ir_iters", "gmres_iters", "fallback", "rel_residual", "slabs",
+            "host_slabs", "host_bytes", "host_read_bytes", "ms_host_read", "ms_generate", "ms_factor", "ms_solve",
+            "ms_residual", "residual_evals", "update_launches", "ms_update", "update_flops", "useful_flops")
+    out = {"metric": "solve beyond one GPU's memory (out-of-core factor)", "n": n, "m": a.m, "t": t,
+           "data": "synthetic", "workload": f"n={n} points uniform in [0,1]^{a.m} (seed {workloads.SEEDS['cube']})",
+           "fp32_tile_bytes": ((n + 127) // 128) * ((n + 127) // 128 + 1) // 2 * 128 * 128 * 4,
+           "device_bytes": torch.cuda.get_device_properties(dev).total_memory,
+           "seconds": el, "mag": mag, "tflops": info["useful_flops"] / el / 1e12,
+           "info": {k: info[k] for k in keys}, "clocks": clocks}
+    if info["ms_host_read"] > 0:
+        out["host_read_gbs"] = info["host_read_bytes"] / (info["ms_host_read"] / 1e3) / 1e9
+    if info["update_launches"]:
+        out["update_tflops"] = info["update_flops"] / (info["ms_update"] / 1e3) / 1e12 if info["ms_update"] else None
+    c.close()
+    return out
+
+
 def main():
     a = parse_args()
+    if a.ooc_n:
+        print(json.dumps(run_out_of_core(a)), flush=True)
+        return
     if a.fp64_dense_n:
         print(json.dumps(run_fp64_dense_headline(a)), flush=True)
         return

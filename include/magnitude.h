@@ -129,6 +129,21 @@ typedef struct mag_options {
                              > 0).  The context stays usable.  The
                              tensor-core update keeps a fixed 20 s bound on
                              its barrier waits.                               */
+  int32_t out_of_core;    /* 0 (default): when the packed FP32 tiles of Z do
+                             not fit in device memory (or in
+                             workspace_limit_bytes), factor slab by slab:
+                             slabs of tile columns generated, updated by the
+                             earlier slabs and factored on the device, then
+                             kept in device memory while it has room, else in
+                             pinned host memory; the triangular solves read
+                             each slab where it lives.  1: always (slabs
+                             sized by workspace_limit_bytes or the free device
+                             memory); -1: never.  FP16, FP16X3 and AUTO only;
+                             the residual is then matrix free.             */
+  int32_t reserved1;
+  double host_limit_bytes;/* pinned host memory the out-of-core factor may
+                             take (0: half of the host's physical memory);
+                             more gives MAG_ENOMEM                          */
 } mag_options;
 
 /* Diagnostics of one call (all fields written when info != NULL). */
@@ -144,7 +159,9 @@ typedef struct mag_info {
   double z_norm_inf;       /* ||Z||inf = max row sum                           */
   double w_norm_inf;       /* max |w_j|                                       */
   double min_w;            /* min w_j                                         */
-  double gershgorin_lmin;  /* 1 - max_j sum_{k != j} Z_jk (lower bound on lambda_min) */
+  double gershgorin_lmin;  /* 1 - max_j sum_{k != j} Z_jk (lower bound on
+                              lambda_min); NaN for out-of-core solves, which
+                              do not form the row sums before the factor     */
   double min_distance;     /* min_{j != k} d_jk                                */
   int32_t below_bracket;   /* sweep: feasible already at t_lo                  */
   int32_t probes;          /* sweep: number of solves                           */
@@ -166,6 +183,12 @@ typedef struct mag_info {
   double ms_probe;         /* device time of the probe                          */
   double t;                /* the t of this solve (the Sec. 1 bound where the
                               call asked for it with t <= 0)                   */
+  int32_t slabs;           /* slabs of the out-of-core factor (0: in core)     */
+  int32_t host_slabs;      /* of which held in host memory                      */
+  double host_bytes;       /* bytes of the factor in host memory               */
+  double host_read_bytes;  /* bytes the factor's slab updates read from host
+                              memory (over the CPU-GPU link)                   */
+  double ms_host_read;     /* device time of those reads (profile = 1)          */
 } mag_info;
 
 typedef struct mag_ctx mag_ctx;

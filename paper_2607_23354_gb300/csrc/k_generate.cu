@@ -28,11 +28,14 @@ __device__ inline void atomic_max_nonneg(unsigned long long* a, double v) {
   atomicMax(a, (unsigned long long)__double_as_longlong(v));
 }
 
+// Tiles of a slab layout (mag_internal.cuh: tile_index with column cap W)
+// whose tile (0, 0) is the global tile (t0, t0); W >= the tile rows and
+// t0 = 0 give the whole packed matrix.
 template <bool WF, bool WD, bool ROWSUM, bool WDIST>
 __global__ void __launch_bounds__(GEN_THREADS, 1)
     k_generate(const double* __restrict__ X, int64_t n, int m, double t, float* __restrict__ Zf,
                double* __restrict__ Zd, double* __restrict__ Dd, double* __restrict__ rowsum, DevStatus* st,
-               int kind, double tiny_arg) {
+               int kind, double tiny_arg, int64_t t0, int64_t W) {
   extern __shared__ double smem[];
   double* xr = smem;                   // [TILE][GEN_MC] row points (broadcast reads)
   double* xc = smem + TILE * GEN_MC;   // [GEN_MC][TILE] column points (conflict free)
@@ -42,9 +45,9 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
   if (WD) load_exp_table(exptab);
 
   int64_t I, J;
-  tri_coords((int64_t)blockIdx.x, &I, &J);
+  tile_coords((int64_t)blockIdx.x, W, &I, &J);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t row0 = I * TILE, col0 = J * TILE;
+  const int64_t row0 = (t0 + I) * TILE, col0 = (t0 + J) * TILE;
 
   double d2[8][4];
 #pragma unroll
@@ -78,7 +81,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
     __syncthreads();
   }
 
-  const int64_t tile_off = tri_index(I, J) * TILE_ELEMS;
+  const int64_t tile_off = tile_index(I, J, W) * TILE_ELEMS;
   // row/column partial sums of a thread cover 4 and 8 entries: FP32 is ample
   // for a norm, and keeps the FP64 pipe for the distances and the exponential
   float rs[8], cs[4];
@@ -264,13 +267,16 @@ __global__ void k_rowsum_max(const double* __restrict__ rowsum, int64_t n, DevSt
 template <bool WF, bool WD, bool ROWSUM, bool WDIST = false>
 cudaError_t launch_gen_t(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
                          double* Zd, double* rowsum, DevStatus* st, cudaStream_t s, double* Dd = nullptr,
-                         int kind = 0, double tiny_arg = INFINITY) {
+                         int kind = 0, double tiny_arg = INFINITY, int64_t t0 = 0, int64_t W = -1) {
   const size_t smem = 2 * (size_t)TILE * GEN_MC * sizeof(double);
   auto kern = k_generate<WF, WD, ROWSUM, WDIST>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t tiles = num_lower_tiles(N);
-  kern<<<(unsigned)tiles, GEN_THREADS, smem, s>>>(X, n, m, t, Zf, Zd, Dd, rowsum, st, kind, tiny_arg);
+  // N: tile rows of the (slab) matrix from global tile t0; W < 0: all columns
+  if (W < 0) W = N;
+  const int64_t tiles = num_slab_tiles(N, W);
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  kern<<<(unsigned)tiles, GEN_THREADS, smem, s>>>(X, n, m, t, Zf, Zd, Dd, rowsum, st, kind, tiny_arg, t0, W);
   note_launch();
   return cudaGetLastError();
 }
@@ -311,6 +317,14 @@ cudaError_t launch_generate_from_dist(const double* Dd, int64_t n, double t, int
     return cudaErrorInvalidValue;
   note_launch();
   return cudaGetLastError();
+}
+
+cudaError_t launch_generate_slab(const double* X, int64_t n, int m, double t, int64_t t0, int64_t W, float* Zf,
+                                 DevStatus* st, cudaStream_t s, double tiny_arg) {
+  const int64_t N = (n + TILE - 1) / TILE;
+  if (t0 < 0 || t0 >= N || W < 1) return cudaErrorInvalidValue;
+  return launch_gen_t<true, false, false>(X, n, m, t, N - t0, Zf, nullptr, nullptr, st, s, nullptr, MAT_EXP,
+                                          tiny_arg, t0, W);
 }
 
 cudaError_t launch_min_distance(const double* X, int64_t n, int m, DevStatus* st, cudaStream_t s) {

@@ -54,14 +54,16 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 
 // Warp-level wait for *progress >= target (lane 0 spins, every lane then
 // acquires once so its own later loads are ordered after the publication).
-// Returns the value seen, or 0 if the wait gave up (deadline or abort).
+// Returns the value seen, or 0 if the wait gave up (deadline or abort).  The
+// deadline and the CTA's abort flag are checked when a wait starts and then
+// every 64 reads, so a wait that begins after the deadline gives up at once.
 __device__ __forceinline__ unsigned warp_wait_progress(const unsigned* progress, unsigned target,
                                                        uint64_t deadline, int* abort_flag) {
   unsigned seen = 0;
   if ((threadIdx.x & 31) == 0) {
     uint32_t it = 0;
     while ((seen = ld_acquire(progress)) < target) {
-      if ((++it & 63u) == 0 && (*(volatile int*)abort_flag || gtimer() > deadline)) {
+      if ((it++ & 63u) == 0 && (*(volatile int*)abort_flag || gtimer() > deadline)) {
         seen = 0;
         *(volatile int*)abort_flag = 1;
         break;
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_forward_persistent(const T* _
                                                                       const T* __restrict__ DinvT, int64_t N,
                                                                       const T* __restrict__ v, T* __restrict__ y,
                                                                       unsigned* progress, DevStatus* st,
-                                                                      uint64_t timeout_ns) {
+                                                                      uint64_t timeout_ns, int prefetch) {
   extern __shared__ __align__(16) unsigned char ts_smem[];
   T* Ds = reinterpret_cast<T*>(ts_smem);  // inv(L_II)^T
   __shared__ T accs[TILE];
@@ -135,8 +137,10 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_forward_persistent(const T* _
     for (int64_t J = 0; J < I; ++J) {
       const T* tile = Z + tri_index(I, J) * TILE_ELEMS + (int64_t)(w * 32) * TILE + 4 * l;
       if ((unsigned)J >= known) {
+        if (prefetch) {
 #pragma unroll 4
-        for (int i = 0; i < 32; ++i) prefetch_l2(tile + (int64_t)i * TILE);
+          for (int i = 0; i < 32; ++i) prefetch_l2(tile + (int64_t)i * TILE);
+        }
         known = warp_wait_progress(progress, (unsigned)J + 1u, deadline, &abort_flag);
         if (!known) break;
       }
@@ -179,7 +183,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_backward_persistent(const T* 
                                                                        const T* __restrict__ Dinv, int64_t N,
                                                                        const T* __restrict__ yv, T* __restrict__ x,
                                                                        unsigned* progress, DevStatus* st,
-                                                                       uint64_t timeout_ns) {
+                                                                       uint64_t timeout_ns, int prefetch) {
   extern __shared__ __align__(16) unsigned char ts_smem[];
   T* Ds = reinterpret_cast<T*>(ts_smem);  // inv(L_II)
   __shared__ T accw[4][TILE];
@@ -198,8 +202,10 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_backward_persistent(const T* 
       const T* tile = Z + tri_index(J, I) * TILE_ELEMS + (int64_t)(w * 32) * TILE + 4 * l;
       const unsigned need = (unsigned)(N - J);
       if (need > known) {
+        if (prefetch) {
 #pragma unroll 4
-        for (int i = 0; i < 32; ++i) prefetch_l2(tile + (int64_t)i * TILE);
+          for (int i = 0; i < 32; ++i) prefetch_l2(tile + (int64_t)i * TILE);
+        }
         known = warp_wait_progress(progress, need, deadline, &abort_flag);
         if (!known) break;
       }
@@ -249,7 +255,7 @@ int coop_grid(K kern, int64_t N, size_t smem) {
 
 template <typename T, typename K>
 cudaError_t launch_sweep(K kern, const T* Z, const T* D, int64_t N, const T* in, T* out, unsigned* progress,
-                         DevStatus* st, uint64_t timeout, cudaStream_t s) {
+                         DevStatus* st, uint64_t timeout, cudaStream_t s, int prefetch = 1) {
   cudaError_t e = cudaMemsetAsync(progress, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   const size_t smem = (size_t)TILE_ELEMS * sizeof(T);
@@ -257,7 +263,7 @@ cudaError_t launch_sweep(K kern, const T* Z, const T* D, int64_t N, const T* in,
   if (e != cudaSuccess) return e;
   const int grid = coop_grid(kern, N, smem);
   void* args[] = {(void*)&Z, (void*)&D, (void*)&N, (void*)&in, (void*)&out, (void*)&progress, (void*)&st,
-                  (void*)&timeout};
+                  (void*)&timeout, (void*)&prefetch};
   e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(TS_THREADS), args, smem, s);
   note_launch();
   return e;
@@ -276,6 +282,23 @@ cudaError_t launch_backward_persistent(const T* Z, const T* Dinv, int64_t N, con
                                        DevStatus* st, uint64_t timeout_ns, cudaStream_t s) {
   return launch_sweep<T>(k_backward_persistent<T>, Z, Dinv, N, yv, x, flags, st, timeout_ns, s);
 }
+
+template <typename T>
+cudaError_t launch_forward_sweep(const T* Z, const T* DinvT, int64_t N, const T* v, T* y, unsigned* progress,
+                                 DevStatus* st, uint64_t timeout_ns, bool z_on_host, cudaStream_t s) {
+  return launch_sweep<T>(k_forward_persistent<T>, Z, DinvT, N, v, y, progress, st, timeout_ns, s, z_on_host ? 0 : 1);
+}
+
+template <typename T>
+cudaError_t launch_backward_sweep(const T* Z, const T* Dinv, int64_t N, const T* yv, T* x, unsigned* progress,
+                                  DevStatus* st, uint64_t timeout_ns, bool z_on_host, cudaStream_t s) {
+  return launch_sweep<T>(k_backward_persistent<T>, Z, Dinv, N, yv, x, progress, st, timeout_ns, s, z_on_host ? 0 : 1);
+}
+
+template cudaError_t launch_forward_sweep<float>(const float*, const float*, int64_t, const float*, float*,
+                                                 unsigned*, DevStatus*, uint64_t, bool, cudaStream_t);
+template cudaError_t launch_backward_sweep<float>(const float*, const float*, int64_t, const float*, float*,
+                                                  unsigned*, DevStatus*, uint64_t, bool, cudaStream_t);
 
 template cudaError_t launch_forward_persistent<float>(const float*, const float*, int64_t, const float*, float*,
                                                       unsigned*, DevStatus*, uint64_t, cudaStream_t);

@@ -254,7 +254,8 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 // conflicts) and added to C_{Ir, J+cc/4} by the TMA; two boxes alternate.
 // Returns once the TMEM reads are done and the boxes may be reused.
 __device__ __forceinline__ void epilogue_reduce(const CUtensorMap* cmap, uint32_t tmem_addr, int64_t Ir, int64_t J,
-                                                int nchunks, int quad, int lane, float* stg, float scale) {
+                                                int64_t wcap, int nchunks, int quad, int lane, float* stg,
+                                                float scale) {
   for (int cc = 0; cc < nchunks; ++cc) {
     float* sb = stg + (cc & 1) * 1024;
     if (cc >= 2) {
@@ -271,7 +272,7 @@ __device__ __forceinline__ void epilogue_reduce(const CUtensorMap* cmap, uint32_
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncwarp();
     if (lane == 0) {
-      tma_reduce_add_3d(cmap, smem_u32(sb), (cc & 3) * 32, quad * 32, (int)tri_index(Ir, J + (cc >> 2)));
+      tma_reduce_add_3d(cmap, smem_u32(sb), (cc & 3) * 32, quad * 32, (int)tile_index(Ir, J + (cc >> 2), wcap));
       bulk_commit();
     }
   }
@@ -458,8 +459,8 @@ __global__ void __launch_bounds__(UPD_THREADS, 1)
       // FP16 panels are stored scaled by 2^s, so products carry 2^(2s)
       constexpr float acc_scale =
           (MODE == UPD_FP16X3 || MODE == UPD_FP16) ? 1.0f / (float)(1u << (2 * FP16_SCALE_LOG2)) : 1.0f;
-      epilogue_reduce(&mC, tmem_base + ((uint32_t)(quad * 32) << 16) + acc * (uint32_t)B_ROWS, I, J, second ? 8 : 4,
-                      quad, lane, stg, acc_scale);
+      epilogue_reduce(&mC, tmem_base + ((uint32_t)(quad * 32) << 16) + acc * (uint32_t)B_ROWS, I, J, p.wcap,
+                      second ? 8 : 4, quad, lane, stg, acc_scale);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty_bar[acc]);
@@ -839,8 +840,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(UPD_THREADS, 1)
       if (Ir < p.N) {
         // tile (Ir, J) is always in the trapezoid; (Ir, J+1) only below j1 and the diagonal
         const int nchunks = (J + 1 < p.j1 && J + 1 <= Ir) ? 8 : 4;
-        epilogue_reduce(&mC, tmem_base + ((uint32_t)(quad * 32) << 16) + acc * 256u, Ir, J, nchunks, quad, lane,
-                        stg, acc_scale);
+        epilogue_reduce(&mC, tmem_base + ((uint32_t)(quad * 32) << 16) + acc * 256u, Ir, J, p.wcap, nchunks, quad,
+                        lane, stg, acc_scale);
       }
       tc_fence_before();
       __syncwarp();
@@ -957,7 +958,7 @@ __device__ __forceinline__ void mma_f16_128x128(uint32_t d_tmem, uint64_t a, uin
 __global__ void __launch_bounds__(TRSM_THREADS, 1)
     k_trsm_tc(float* __restrict__ Z, const float* __restrict__ Dinv, int64_t K, int64_t N, int64_t k0,
               int64_t width, int split, __half* __restrict__ phi, __half* __restrict__ plo,
-              unsigned* __restrict__ counter, DevStatus* st, uint64_t timeout_ns) {
+              unsigned* __restrict__ counter, DevStatus* st, uint64_t timeout_ns, int64_t wcap) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* b_hi = smem;
@@ -990,7 +991,7 @@ __global__ void __launch_bounds__(TRSM_THREADS, 1)
   trsm_load(Dinv + K * TILE_ELEMS, x);
   trsm_split(x, b_hi, b_lo, bexp);
   int64_t tile = s_next;
-  trsm_load(Z + tri_index(K + 1 + tile, K) * TILE_ELEMS, x);
+  trsm_load(Z + tile_index(K + 1 + tile, K, wcap) * TILE_ELEMS, x);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -1021,7 +1022,7 @@ __global__ void __launch_bounds__(TRSM_THREADS, 1)
       mma_commit(&done_bar);
     }
     const int64_t next = s_next;
-    if (next < ntiles) trsm_load(Z + tri_index(K + 1 + next, K) * TILE_ELEMS, x);
+    if (next < ntiles) trsm_load(Z + tile_index(K + 1 + next, K, wcap) * TILE_ELEMS, x);
     const bool waited = mbar_wait(&done_bar, phase, &abort_flag, deadline);
     phase ^= 1u;
     const bool ok = __syncthreads_and(waited ? 1 : 0) != 0;  // one decision for the whole CTA
@@ -1048,7 +1049,7 @@ __global__ void __launch_bounds__(TRSM_THREADS, 1)
     __syncthreads();
     if (!ok) break;
     // row-major write-out: warp w, rows w + 8 i; lane l, columns 4 l .. 4 l + 3
-    float* out = Z + tri_index(I, K) * TILE_ELEMS;
+    float* out = Z + tile_index(I, K, wcap) * TILE_ELEMS;
     const int64_t prow = (I - k0) * TILE, pcol = (K - k0) * TILE + 4 * lane;
     for (int i = 0; i < 16; ++i) {
       const int r = warp + 8 * i;
@@ -1205,6 +1206,7 @@ int64_t update_tasks(int64_t N, int64_t j0, int64_t j1, bool pairs, std::vector<
 cudaError_t launch_update_tc(const UpdMaps& maps, const CMap& cmap, UpdParams p, int mode, int grid, bool pairs,
                              cudaStream_t s) {
   if (p.ntasks <= 0 || p.kc_hi <= p.kc_lo) return cudaSuccess;
+  if (p.wcap <= 0) p.wcap = p.N;
   if (pairs) {
     if ((int64_t)grid > 2 * p.ntasks) grid = (int)(2 * p.ntasks);
     switch (mode) {
@@ -1228,7 +1230,10 @@ cudaError_t launch_update_tc(const UpdMaps& maps, const CMap& cmap, UpdParams p,
 }
 
 cudaError_t launch_trsm_tc(float* Z, const float* Dinv, int64_t K, int64_t N, int64_t k0, int64_t width, int mode,
-                           void* hi, void* lo, unsigned* counter, DevStatus* st, int grid, cudaStream_t s) {
+                           void* hi, void* lo, unsigned* counter, DevStatus* st, int grid, cudaStream_t s,
+                           int64_t wcap) {
+  if (wcap < 0) wcap = N;
+  if (K >= wcap) return cudaErrorInvalidValue;
   const int64_t ntiles = N - K - 1;
   if (ntiles <= 0) return cudaSuccess;
   if (mode != UPD_FP16 && mode != UPD_FP16X3) return cudaErrorInvalidValue;
@@ -1239,7 +1244,7 @@ cudaError_t launch_trsm_tc(float* Z, const float* Dinv, int64_t K, int64_t N, in
   if (grid < 1) grid = 1;
   k_trsm_tc<<<grid, TRSM_THREADS, smem, s>>>(Z, Dinv, K, N, k0, width, mode == UPD_FP16X3 ? 1 : 0,
                                               static_cast<__half*>(hi), static_cast<__half*>(lo), counter, st,
-                                              10000000000ull);
+                                              10000000000ull, wcap);
   note_launch();
   return cudaGetLastError();
 }

@@ -10,6 +10,8 @@
 // 1/||r||inf.  When the residual stagnates the solve escalates to GMRES-IR
 // (FGMRES preconditioned by the same factor, all vectors FP64) and then to an
 // FP64 factor.
+#include <unistd.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -41,6 +43,17 @@ struct Layout {
   int64_t W = 0;       // panel buffer row length in columns (nb * TILE)
   int64_t nctr = 0;    // task counters of one factor: update launches, then one per panel solve
   int64_t nctr_upd = 0;  // the update launches' share (at the front)
+  int64_t zf_tiles = 0;  // FP32 tiles of the zf region: all lower tiles, or the slab pool
+};
+
+// One slab of the out-of-core factor: tile columns [c0, c0 + S) of every row
+// below, in the slab layout (tile_index with cap S); generated and factored
+// at dev (device pool), then kept there or copied to host (pinned, mapped).
+struct Slab {
+  int64_t c0 = 0, S = 0, tiles = 0;
+  int64_t pool_off = 0;    // tile offset of its device location in the pool
+  bool host = false;       // finished slab lives in host memory
+  int64_t host_off = 0;    // tile offset in the host buffer
 };
 
 constexpr int NVEC_D = 6;   // FP64 vectors of np entries
@@ -90,11 +103,19 @@ struct mag_ctx {
     uint32_t* d = nullptr;
     std::map<std::pair<int64_t, int64_t>, std::pair<int64_t, int64_t>> rng;
   };
-  std::map<std::tuple<int64_t, int, int, int>, TaskTable> task_tables;
+  std::map<std::tuple<int64_t, int, int, int, int64_t>, TaskTable> task_tables;
   TaskTable* tasks = nullptr;        // the table of the factor in progress
   cudaStream_t side = nullptr;       // panel stream of the look-ahead factor
   int kind = MAT_EXP;                // matrix the solve path generates (MatKind)
   cudaEvent_t ev_la[3] = {nullptr, nullptr, nullptr};  // start, panel done, trailing done
+  // out-of-core factor (slabs); empty when the solve runs in core
+  std::vector<Slab> slabs;
+  bool ooc = false;                  // the current solve factors out of core
+  float* host_L = nullptr;           // pinned host memory of the host slabs (mapped)
+  size_t host_L_bytes = 0;
+  CMap slab_cmap;                    // TMA descriptor of the slab being updated
+  const void* slab_cmap_base = nullptr;
+  int64_t slab_cmap_tiles = 0;
   float* probe_z = nullptr;          // FP32 tiles of the leading block the precision probe factors
   size_t probe_bytes = 0;
   CMap probe_cmap;                   // TMA descriptor of those tiles (update epilogue)
@@ -103,6 +124,11 @@ struct mag_ctx {
 
   // typed views of the workspace
   float* zf() { return (float*)((char*)ws + lay.off_zf); }
+  float* slab_dev(const Slab& sl) { return zf() + sl.pool_off * TILE_ELEMS; }
+  // where a finished slab is read: its device location, or its host copy
+  const float* slab_data(const Slab& sl) {
+    return sl.host ? host_L + sl.host_off * TILE_ELEMS : slab_dev(sl);
+  }
   double* zd() { return (double*)((char*)ws + lay.off_zd); }
   float* dinvf() { return (float*)((char*)ws + lay.off_dinvf); }
   double* dinvd() { return (double*)((char*)ws + lay.off_dinvd); }
@@ -163,7 +189,7 @@ double bits_to_double(unsigned long long b) {
   return d;
 }
 
-Layout plan(const mag_ctx* ctx, int64_t n, bool f32, bool f64, bool dist = false) {
+Layout plan(const mag_ctx* ctx, int64_t n, bool f32, bool f64, bool dist = false, int64_t zf_tiles = -1) {
   Layout L;
   L.n = n;
   L.N = (n + TILE - 1) / TILE;
@@ -204,7 +230,8 @@ Layout plan(const mag_ctx* ctx, int64_t n, bool f32, bool f64, bool dist = false
   L.off_dinvd = off;
   if (f64) off = align_up(off + (size_t)2 * L.N * TILE_ELEMS * sizeof(double));
   L.off_zf = off;
-  if (f32) off = align_up(off + (size_t)L.tiles * TILE_ELEMS * sizeof(float));
+  L.zf_tiles = zf_tiles >= 0 ? zf_tiles : L.tiles;
+  if (f32) off = align_up(off + (size_t)L.zf_tiles * TILE_ELEMS * sizeof(float));
   L.off_zd = off;
   if (f64) off = align_up(off + (size_t)L.tiles * TILE_ELEMS * sizeof(double));
   L.off_spart = off;  // partials of the stored residual: N * N * 128 doubles
@@ -213,8 +240,8 @@ Layout plan(const mag_ctx* ctx, int64_t n, bool f32, bool f64, bool dist = false
   return L;
 }
 
-int ensure_workspace(mag_ctx* ctx, int64_t n, bool f32, bool f64) {
-  Layout L = plan(ctx, n, f32, f64, ctx->dist_active);
+int ensure_workspace(mag_ctx* ctx, int64_t n, bool f32, bool f64, int64_t zf_tiles = -1) {
+  Layout L = plan(ctx, n, f32, f64, ctx->dist_active && zf_tiles < 0, zf_tiles);
   if (ctx->opt.workspace_limit_bytes > 0 && (double)L.total > ctx->opt.workspace_limit_bytes)
     return fail(ctx, MAG_ENOMEM, "workspace of %.3g bytes exceeds the limit %.3g", (double)L.total,
                 ctx->opt.workspace_limit_bytes);
@@ -295,7 +322,7 @@ int check_args(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double 
 
 // ---------------------------------------------------------------- factor
 // Optional CUDA-event timing of factor launches by category (profile = 1).
-enum { PC_UPDATE = 0, PC_UPDATE_PANEL = 1, PC_POTRF = 2, PC_TRSM = 3, PC_SPLIT = 4, PC_COUNT = 5 };
+enum { PC_UPDATE = 0, PC_UPDATE_PANEL = 1, PC_POTRF = 2, PC_TRSM = 3, PC_SPLIT = 4, PC_HOST_READ = 5, PC_COUNT = 6 };
 int prof_begin(mag_ctx* ctx, int cat = PC_UPDATE, cudaStream_t st = nullptr) {
   if (!ctx->opt.profile) return MAG_OK;
   const size_t need = 2 * (size_t)(ctx->prof_used + 1);
@@ -372,8 +399,11 @@ int upd_mode(int prec) {
 // tensor-core update of the whole trailing matrix with K = (k1 - k0) * 128.
 // Task tables of every tensor-core update launch of one factor with the
 // current N, panel width nb and schedule (built on the host once and kept).
-int ensure_tasks(mag_ctx* ctx, int64_t N, int nb, bool la, bool pairs) {
-  const auto key = std::make_tuple(N, nb, (int)la, (int)pairs);
+int ensure_tasks(mag_ctx* ctx, int64_t N, int nb, bool la, bool pairs, int64_t ncol = -1, bool slab = false) {
+  // ncol: tile columns factored (a slab of the out-of-core factor); -1 = N.
+  // slab: also the range [0, ncol) (the update of a slab by earlier slabs)
+  if (ncol < 0) ncol = N;
+  const auto key = std::make_tuple(N, nb, (int)la + 2 * (int)slab, (int)pairs, ncol);
   auto found = ctx->task_tables.find(key);
   if (found != ctx->task_tables.end()) {
     ctx->tasks = &found->second;
@@ -397,16 +427,17 @@ int ensure_tasks(mag_ctx* ctx, int64_t N, int nb, bool la, bool pairs) {
     add(mid, b);
     panel(mid, b);
   };
-  for (int64_t k0 = 0; k0 < N; k0 += nb) {
-    const int64_t k1 = std::min<int64_t>(N, k0 + nb), k2 = std::min<int64_t>(N, k1 + nb);
+  for (int64_t k0 = 0; k0 < ncol; k0 += nb) {
+    const int64_t k1 = std::min<int64_t>(ncol, k0 + nb), k2 = std::min<int64_t>(ncol, k1 + nb);
     panel(k0, k1);
     if (la) {
       add(k1, k2);
-      add(k2, N);
+      add(k2, ncol);
     } else {
-      add(k1, N);
+      add(k1, ncol);
     }
   }
+  if (slab) add(0, ncol);  // a whole slab: the updates from earlier slabs
   cudaError_t e = cudaMalloc((void**)&tab.d, std::max<size_t>(1, t.size()) * sizeof(uint32_t));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -457,6 +488,9 @@ struct TcFactor {
   // update leaves free while it runs beside them (a launch whose CTAs cannot
   // all be resident ends only when the trailing update does)
   int panel_grid;
+  // tile columns of Z's layout (tile_index column cap): N for the whole
+  // matrix, the slab width for a slab of the out-of-core factor
+  int64_t W = 0;
 };
 
 // C_IJ -= sum_{k in [kc_lo, kc_hi)} P_Ik P_Jk^T for J in [j0, j1) with the
@@ -482,6 +516,7 @@ int tc_update(TcFactor& F, int b, int64_t k0, int kc_lo, int kc_hi, int64_t j0, 
   up.st = ctx->st();
   up.timeout_ns = 20000000000ull;
   up.max_tasks = max_tasks;
+  up.wcap = F.W > 0 ? F.W : F.N;
   if (max_tasks > 0) {
     // enough CTAs (pairs) for every task at max_tasks each; they start as SMs come free
     const int64_t units = (up.ntasks + max_tasks - 1) / max_tasks;
@@ -514,7 +549,7 @@ int tc_panel_range(TcFactor& F, int64_t k0, int64_t a, int64_t b, int buf, cudaS
       // solve and panel copy in one tensor-core pass
       TRY(prof_begin(ctx, PC_TRSM, st));
       CU(launch_trsm_tc(Z, Dinv, a, F.N, k0, L.W, F.mode, ctx->panel_hi(buf), ctx->panel_lo(buf),
-                        ctx->counters() + L.nctr_upd + a, ctx->st(), F.panel_grid, st));
+                        ctx->counters() + L.nctr_upd + a, ctx->st(), F.panel_grid, st, F.W > 0 ? F.W : F.N));
       TRY(prof_end(ctx, st));
       return MAG_OK;
     }
@@ -546,34 +581,35 @@ int tc_panel(TcFactor& F, int64_t k0, int b, cudaStream_t st) {
 // factors it (into the other panel buffer) while the solver's stream applies
 // the current panel to the remaining columns; CTAs of the trailing update are
 // capped so that some SMs stay free for the panel stream.
-int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
+// Two-level right-looking Cholesky of the packed FP32 tiles at Z (N tile
+// rows; the first W tile columns are factored, the slab layout tile_index
+// with cap W -- W = N is the whole matrix) with the tensor-core updates.
+// Dinv receives inv(L_KK) of its diagonal tiles (and the transposes N_global
+// tiles further, see launch_potrf_diag).
+int factor_tc_on(mag_ctx* ctx, int mode, float* Z, float* Dinv, const CMap* cmap, int64_t N, int64_t W,
+                 int* launches, double* flops, bool slab = false) {
   const Layout& L = ctx->lay;
   cudaStream_t s = ctx->stream;
   const bool split = mode == UPD_FP16X3 || mode == UPD_TF32X3;
   // panel width by product count (measured at n = 1e5): one-product updates
   // are short and gain from K = 4096 per launch (32 tiles); the split
   // products refine in fewer steps with 16-tile panels
-  const int nb = std::max(1, std::min(L.nb, ctx->opt.panel_tiles > 0 ? ctx->opt.panel_tiles : (split ? 16 : 32)));
-  const int64_t npanels = (L.N + nb - 1) / nb;
+  int nb = std::max(1, std::min(L.nb, ctx->opt.panel_tiles > 0 ? ctx->opt.panel_tiles : (split ? 16 : 32)));
+  nb = (int)std::min<int64_t>(nb, W);
+  const int64_t npanels = (W + nb - 1) / nb;
   const bool la = ctx->opt.lookahead != 0 && npanels > 2;
   const bool pairs = ctx->opt.cta_pairs == 1 || (ctx->opt.cta_pairs == 2 && split);
-  TRY(ensure_tasks(ctx, L.N, nb, la, pairs));
+  TRY(ensure_tasks(ctx, N, nb, la, pairs, W, slab));
   TRY(ensure_maps(ctx, mode, 0));
   TRY(ensure_maps(ctx, mode, 1));
-  if (ctx->cmap_base != ctx->zf() || ctx->cmap_tiles != L.tiles) {
-    if (!make_c_map(&ctx->cmap, ctx->zf(), L.tiles))
-      return fail(ctx, MAG_ECUDA, "cuTensorMapEncodeTiled failed for the factor tiles");
-    ctx->cmap_base = ctx->zf();
-    ctx->cmap_tiles = L.tiles;
-  }
   CU(cudaMemsetAsync(ctx->counters(), 0, (size_t)L.nctr * sizeof(unsigned), s));
-  TcFactor F{ctx, mode, pairs, nb, launches, flops, 0, ctx->zf(), ctx->dinvf(), &ctx->cmap, L.n, L.N,
-             ctx->sm_count};
+  TcFactor F{ctx, mode, pairs, nb, launches, flops, 0, Z, Dinv, cmap, L.n, N, ctx->sm_count};
+  F.W = W;
   if (!la) {
-    for (int64_t k0 = 0; k0 < L.N; k0 += nb) {
-      const int64_t k1 = std::min<int64_t>(L.N, k0 + nb);
+    for (int64_t k0 = 0; k0 < W; k0 += nb) {
+      const int64_t k1 = std::min<int64_t>(W, k0 + nb);
       TRY(tc_panel(F, k0, 0, s));
-      if (k1 < L.N) TRY(tc_update(F, 0, k0, 0, (int)(k1 - k0), k1, L.N, ctx->sm_count, s, PC_UPDATE));
+      if (k1 < W) TRY(tc_update(F, 0, k0, 0, (int)(k1 - k0), k1, W, ctx->sm_count, s, PC_UPDATE));
     }
     return MAG_OK;
   }
@@ -606,22 +642,224 @@ int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
   const int beside = reserved ? std::max(1, std::min(ctx->sm_count, reserve)) : ctx->sm_count;
   int64_t p = 0;
   for (int64_t k0 = 0;; k0 += nb, ++p) {
-    const int64_t k1 = std::min<int64_t>(L.N, k0 + nb);
-    if (k1 >= L.N) break;
-    const int64_t k2 = std::min<int64_t>(L.N, k1 + nb);
+    const int64_t k1 = std::min<int64_t>(W, k0 + nb);
+    if (k1 >= W) break;
+    const int64_t k2 = std::min<int64_t>(W, k1 + nb);
     const int b = (int)(p & 1);
     CU(cudaStreamWaitEvent(s, ev_panel, 0));  // panel p factored and copied
     // panel stream: next panel's columns, then the next panel itself
     TRY(tc_update(F, b, k0, 0, (int)(k1 - k0), k1, k2, ctx->sm_count, side, PC_UPDATE));
-    F.panel_grid = k2 < L.N ? beside : ctx->sm_count;  // the last panel runs alone
+    F.panel_grid = k2 < W ? beside : ctx->sm_count;  // the last panel runs alone
     TRY(tc_panel(F, k1, b ^ 1, side));
     CU(cudaEventRecord(ev_panel, side));
     // solver stream: the rest of the trailing matrix
-    if (k2 < L.N) TRY(tc_update(F, b, k0, 0, (int)(k1 - k0), k2, L.N, trail_grid, s, PC_UPDATE, trail_tasks));
+    if (k2 < W) TRY(tc_update(F, b, k0, 0, (int)(k1 - k0), k2, W, trail_grid, s, PC_UPDATE, trail_tasks));
     CU(cudaEventRecord(ev_trail, s));
     CU(cudaStreamWaitEvent(side, ev_trail, 0));  // columns of panel p+2 and buffer b are free
   }
   CU(cudaStreamWaitEvent(s, ev_panel, 0));
+  return MAG_OK;
+}
+
+// The in-core factor: the whole packed matrix of the workspace.
+int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
+  const Layout& L = ctx->lay;
+  if (ctx->cmap_base != ctx->zf() || ctx->cmap_tiles != L.tiles) {
+    if (!make_c_map(&ctx->cmap, ctx->zf(), L.tiles))
+      return fail(ctx, MAG_ECUDA, "cuTensorMapEncodeTiled failed for the factor tiles");
+    ctx->cmap_base = ctx->zf();
+    ctx->cmap_tiles = L.tiles;
+  }
+  return factor_tc_on(ctx, mode, ctx->zf(), ctx->dinvf(), &ctx->cmap, L.N, L.N, launches, flops);
+}
+
+// ------------------------------------------------------------ out of core
+// When the packed FP32 tiles of Z do not fit in device memory (or the
+// workspace limit), the factor runs slab by slab (mag_internal.cuh: slab
+// layout).  The device keeps a pool of tiles: the first slab, as wide as
+// two thirds of the pool allows, is generated, factored and kept there; the
+// remaining columns go through a working buffer (the last third) one slab
+// at a time, each copied to pinned host memory once factored, except the
+// last, which stays.  Slab s is first updated with every earlier slab q
+// (C -= L_q L_q^T restricted to its rows and columns): the FP16 panel copies
+// of q's columns are gathered K chunk by K chunk (from device or host memory)
+// into the panel buffers and applied by the tensor-core update kernel; then
+// its columns are factored by the right-looking two-level factor.
+
+// Widest slab (tile columns) of `rows` tile rows in `cap` tiles (0 if none).
+int64_t slab_width(int64_t rows, int64_t cap) {
+  int64_t lo = 0, hi = rows;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (num_slab_tiles(rows, mid) <= cap) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Host memory the host slabs may take: options.host_limit_bytes, else half
+// of the machine's physical memory.
+double host_limit(const mag_ctx* ctx) {
+  if (ctx->opt.host_limit_bytes > 0) return ctx->opt.host_limit_bytes;
+  const long pages = sysconf(_SC_PHYS_PAGES), psz = sysconf(_SC_PAGE_SIZE);
+  return pages > 0 && psz > 0 ? 0.5 * (double)pages * (double)psz : 0.0;
+}
+
+// Decide whether the solve of size n factors out of core and, if so, plan
+// the slabs and the device pool (pool_tiles > 0 on return).  In core: 0.
+int plan_out_of_core(mag_ctx* ctx, int64_t n, int prec, int64_t* pool_tiles) {
+  *pool_tiles = 0;
+  ctx->slabs.clear();
+  const mag_options& o = ctx->opt;
+  if (o.out_of_core < 0) return MAG_OK;
+  const bool fp16_kind = prec == MAG_PREC_AUTO || prec == MAG_PREC_FP16 || prec == MAG_PREC_FP16X3;
+  if (!fp16_kind) {
+    if (o.out_of_core > 0)
+      return fail(ctx, MAG_EINVAL, "the out-of-core factor runs the FP16 and FP16X3 (or AUTO) precisions");
+    return MAG_OK;
+  }
+  size_t fre = 0, tot = 0;
+  if (cudaMemGetInfo(&fre, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    fre = 0;
+  }
+  double avail = 0.95 * ((double)fre + (double)ctx->ws_bytes);
+  if (o.workspace_limit_bytes > 0) avail = std::min(avail, o.workspace_limit_bytes);
+  const Layout incore = plan(ctx, n, true, false);
+  if (o.out_of_core == 0 && (double)incore.total <= avail) return MAG_OK;
+  const Layout base = plan(ctx, n, true, false, false, 0);
+  const double tile_bytes = (double)TILE_ELEMS * sizeof(float);
+  const int64_t pool = (int64_t)std::floor((avail - (double)base.total - 4096.0) / tile_bytes);
+  const int64_t N = incore.N;
+  if (pool < 1) return fail(ctx, MAG_ENOMEM, "no device memory left for the out-of-core factor's tiles");
+  std::vector<Slab> sl;
+  int64_t host_tiles = 0;
+  if (num_lower_tiles(N) <= pool) {
+    Slab a;
+    a.c0 = 0;
+    a.S = N;
+    a.tiles = num_lower_tiles(N);
+    sl.push_back(a);
+  } else {
+    const int64_t work = pool / 3, resident = pool - work;
+    int64_t c0 = slab_width(N, resident), used = 0;
+    if (c0 > 0) {
+      Slab a;
+      a.c0 = 0;
+      a.S = c0;
+      a.tiles = num_slab_tiles(N, c0);
+      sl.push_back(a);
+      used = a.tiles;
+    }
+    while (c0 < N) {
+      Slab b;
+      b.c0 = c0;
+      b.S = slab_width(N - c0, work);
+      if (b.S < 1) return fail(ctx, MAG_ENOMEM, "device pool of %lld tiles too small for a slab", (long long)pool);
+      b.tiles = num_slab_tiles(N - c0, b.S);
+      b.pool_off = used;
+      c0 += b.S;
+      b.host = c0 < N;  // the last slab stays on the device
+      if (b.host) {
+        b.host_off = host_tiles;
+        host_tiles += b.tiles;
+      }
+      sl.push_back(b);
+    }
+  }
+  const double host_bytes = (double)host_tiles * tile_bytes;
+  if (host_bytes > host_limit(ctx))
+    return fail(ctx, MAG_ENOMEM, "out-of-core factor needs %.3g GB of host memory (limit %.3g GB)", host_bytes / 1e9,
+                host_limit(ctx) / 1e9);
+  if (host_tiles > 0 && (size_t)host_bytes > ctx->host_L_bytes) {
+    if (ctx->host_L) {
+      cudaStreamSynchronize(ctx->stream);
+      cudaFreeHost(ctx->host_L);
+      ctx->host_L = nullptr;
+      ctx->host_L_bytes = 0;
+    }
+    void* h = nullptr;
+    cudaError_t e = cudaHostAlloc(&h, (size_t)host_bytes, cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, MAG_ENOMEM, "pinned host memory of %.3g GB: %s", host_bytes / 1e9, cudaGetErrorString(e));
+    }
+    void* d = nullptr;
+    e = cudaHostGetDevicePointer(&d, h, 0);
+    if (e != cudaSuccess || d != h) {
+      cudaGetLastError();
+      cudaFreeHost(h);
+      return fail(ctx, MAG_ECUDA, "host memory is not addressed alike on the device");
+    }
+    ctx->host_L = static_cast<float*>(h);
+    ctx->host_L_bytes = (size_t)host_bytes;
+  }
+  int64_t need = 0;
+  for (const Slab& x : sl) need = std::max(need, x.pool_off + x.tiles);
+  ctx->slabs = sl;
+  *pool_tiles = need;
+  return MAG_OK;
+}
+
+// The out-of-core factor of Z = exp[-t d] in an FP16 kind (UPD_FP16X3 or
+// UPD_FP16).  slab0_ready: slab 0 is already generated (the precision probe
+// read its leading block).
+int factor_ooc(mag_ctx* ctx, const double* X, int32_t m, double t, int mode, bool slab0_ready, int* launches,
+               double* flops, double* host_read_bytes) {
+  const Layout& L = ctx->lay;
+  cudaStream_t s = ctx->stream;
+  const bool split = mode == UPD_FP16X3;
+  const bool pairs = ctx->opt.cta_pairs != 0;
+  for (size_t si = 0; si < ctx->slabs.size(); ++si) {
+    const Slab& sl = ctx->slabs[si];
+    float* Zs = ctx->slab_dev(sl);
+    const int64_t rows = L.N - sl.c0;
+    if (!(si == 0 && slab0_ready)) CU(launch_generate_slab(X, L.n, m, t, sl.c0, sl.S, Zs, ctx->st(), s));
+    if (ctx->slab_cmap_base != Zs || ctx->slab_cmap_tiles != sl.tiles) {
+      if (!make_c_map(&ctx->slab_cmap, Zs, sl.tiles))
+        return fail(ctx, MAG_ECUDA, "cuTensorMapEncodeTiled failed for a slab");
+      ctx->slab_cmap_base = Zs;
+      ctx->slab_cmap_tiles = sl.tiles;
+    }
+    if (si > 0) {
+      // C -= L_q L_q^T from every earlier slab, K chunks of at most L.nb
+      // tiles gathered into the two panel buffers in turn
+      const int nb = (int)std::min<int64_t>(L.nb, 32);
+      TRY(ensure_tasks(ctx, rows, nb, false, pairs, sl.S, true));
+      TRY(ensure_maps(ctx, mode, 0));
+      TRY(ensure_maps(ctx, mode, 1));
+      CU(cudaMemsetAsync(ctx->counters(), 0, (size_t)L.nctr_upd * sizeof(unsigned), s));
+      TcFactor F{ctx, mode, pairs, nb, launches, flops, 0, Zs, ctx->dinvf(), &ctx->slab_cmap, L.n, rows,
+                 ctx->sm_count};
+      F.W = sl.S;
+      int buf = 0;
+      for (size_t qi = 0; qi < si; ++qi) {
+        const Slab& q = ctx->slabs[qi];
+        for (int64_t k = q.c0; k < q.c0 + q.S; k += nb) {
+          const int kw = (int)std::min<int64_t>(nb, q.c0 + q.S - k);
+          if (F.next_ctr >= L.nctr_upd) {
+            CU(cudaMemsetAsync(ctx->counters(), 0, (size_t)L.nctr_upd * sizeof(unsigned), s));
+            F.next_ctr = 0;
+          }
+          // gathers from host slabs are timed (profile = 1): the reads over
+          // the CPU-GPU link
+          if (q.host) TRY(prof_begin(ctx, PC_HOST_READ, s));
+          CU(launch_gather_split(ctx->slab_data(q), q.c0, q.S, sl.c0, rows, k, kw, ctx->panel_hi(buf),
+                                 ctx->panel_lo(buf), L.W, split, s));
+          if (q.host) {
+            TRY(prof_end(ctx, s));
+            *host_read_bytes += (double)rows * kw * TILE_ELEMS * sizeof(float);
+          }
+          TRY(tc_update(F, buf, 0, 0, kw, 0, sl.S, ctx->sm_count, s, PC_UPDATE));
+          buf ^= 1;
+        }
+      }
+    }
+    TRY(factor_tc_on(ctx, mode, Zs, ctx->dinvf() + sl.c0 * TILE_ELEMS, &ctx->slab_cmap, rows, sl.S, launches,
+                     flops, true));
+    if (sl.host)
+      CU(cudaMemcpyAsync(ctx->host_L + sl.host_off * TILE_ELEMS, Zs, (size_t)sl.tiles * TILE_ELEMS * sizeof(float),
+                         cudaMemcpyDeviceToHost, s));
+  }
   return MAG_OK;
 }
 
@@ -663,6 +901,8 @@ int mag_options_default(mag_options* opt) {
   opt->cta_pairs = 1;
   opt->tplus_method = 0;
   opt->wait_timeout_ns = 10000000000ll;
+  opt->out_of_core = 0;
+  opt->host_limit_bytes = 0.0;
   return MAG_OK;
 }
 
@@ -711,6 +951,7 @@ int mag_ctx_destroy(mag_ctx* ctx) {
   if (ctx->bws) cudaFree(ctx->bws);
   if (ctx->gm) cudaFree(ctx->gm);
   if (ctx->probe_z) cudaFree(ctx->probe_z);
+  if (ctx->host_L) cudaFreeHost(ctx->host_L);
   for (auto& kv : ctx->task_tables)
     if (kv.second.d) cudaFree(kv.second.d);
   if (ctx->side) {
@@ -812,6 +1053,8 @@ struct SolveResult {
   bool stored = false;
   double ms_update = 0, update_flops = 0, ms_update_panel = 0, ms_potrf = 0, ms_trsm = 0, ms_split = 0;
   double probe_rho = 0, ms_probe = 0;
+  int slabs = 0, host_slabs = 0;
+  double host_bytes = 0, host_read_bytes = 0, ms_host_read = 0;
 };
 
 float elapsed(mag_ctx* ctx, int a, int b) {
@@ -932,11 +1175,45 @@ int correction_t(mag_ctx* ctx, T* Z, T* Dinv, T* v, T* y, const double* r, doubl
   return MAG_OK;
 }
 
+// The same correction with the out-of-core factor: forward and backward
+// substitution slab by slab (each slab's triangle by the persistent sweeps,
+// its rectangle below by a product with the rows that follow), reading every
+// slab where it lives.
+int correction_ooc(mag_ctx* ctx, const double* r, double* x, bool init) {
+  const Layout& L = ctx->lay;
+  cudaStream_t s = ctx->stream;
+  const uint64_t tmo = (uint64_t)ctx->opt.wait_timeout_ns;
+  float* v = ctx->vf(F_V);
+  float* y = ctx->vf(F_Y);
+  float* Dinv = ctx->dinvf();
+  float* DinvT = Dinv + L.N * TILE_ELEMS;
+  CU(launch_scale_rhs<float>(r, L.n, L.np, v, ctx->st(), s));
+  for (const Slab& sl : ctx->slabs) {  // L y = v
+    const float* Ls = ctx->slab_data(sl);
+    const int64_t o = sl.c0 * TILE, below = L.N - sl.c0 - sl.S;
+    CU(launch_forward_sweep<float>(Ls, DinvT + sl.c0 * TILE_ELEMS, sl.S, v + o, y + o, ctx->flags(), ctx->st(), tmo,
+                                   sl.host, s));
+    CU(launch_rect_gemv(Ls + num_lower_tiles(sl.S) * TILE_ELEMS, below, sl.S, y + o, v + o + sl.S * TILE, s));
+  }
+  for (size_t i = ctx->slabs.size(); i-- > 0;) {  // L^T x = y, x into v
+    const Slab& sl = ctx->slabs[i];
+    const float* Ls = ctx->slab_data(sl);
+    const int64_t o = sl.c0 * TILE, below = L.N - sl.c0 - sl.S;
+    CU(launch_rect_gemv_t(Ls + num_lower_tiles(sl.S) * TILE_ELEMS, below, sl.S, v + o + sl.S * TILE, y + o, s));
+    CU(launch_backward_sweep<float>(Ls, Dinv + sl.c0 * TILE_ELEMS, sl.S, y + o, v + o, ctx->flags(), ctx->st(), tmo,
+                                    sl.host, s));
+  }
+  CU(launch_accumulate<float>(x, v, L.n, ctx->st(), init, s));
+  return MAG_OK;
+}
+
 int correction(mag_ctx* ctx, int prec, const double* r, double* x, bool init, SolveResult* R) {
   cudaStream_t s = ctx->stream;
   CU(cudaEventRecord(ctx->ev[2], s));
   const Layout& L = ctx->lay;
-  if (prec == MAG_PREC_FP64)
+  if (ctx->ooc)
+    TRY(correction_ooc(ctx, r, x, init));
+  else if (prec == MAG_PREC_FP64)
     TRY(correction_t<double>(ctx, ctx->zd(), ctx->dinvd(), ctx->vd(V_T2), ctx->vd(V_E), r, x, init, L.n, L.np,
                              L.N));
   else
@@ -1218,10 +1495,170 @@ int gmres_ir(mag_ctx* ctx, int prec, const double* X, int32_t m, double t, const
 // Full solve of Z x = b (b == null: ones) into x (device, n).  The iterate
 // lives in the workspace; x receives the best iterate (lowest relative
 // residual) over all precisions tried.
+// FP16 factor chosen on the probe's prediction rho: its extra refinement
+// steps over the split factor cost less than the factor time saved (n / 9500
+// steps with stored FP64 tiles, a quarter of that matrix free).
+bool probe_takes_fp16(double rho, double tol, int64_t n, bool stored) {
+  const double saved = (double)n / 9500.0 * (stored ? 1.0 : 0.25);
+  return rho < 1.0 && ir_steps(rho, tol) - ir_steps(rho * 0x1p-12, tol) <= saved;
+}
+
+// The solve with the out-of-core factor (plan_out_of_core set the slabs; the
+// device pool holds pool_tiles tiles).  The residual is matrix free, the
+// generation happens inside the factor slab by slab, the AUTO policy has no
+// Gershgorin shortcut (no full row sums before the factor) and runs the probe
+// on the first slab's leading block; refinement and GMRES-IR as in core, but
+// no FP64 factor (it would not fit either).
+int solve_ooc(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, const double* b, double* x,
+              int64_t pool_tiles, SolveResult* R) {
+  const mag_options& o = ctx->opt;
+  cudaStream_t s = ctx->stream;
+  R->stored = false;
+  R->gersh = NAN;
+  TRY(ensure_workspace(ctx, n, true, false, pool_tiles));
+  ctx->ooc = true;
+  struct OocOff {
+    mag_ctx* c;
+    ~OocOff() { c->ooc = false; }
+  } ooc_off{ctx};
+  R->slabs = (int)ctx->slabs.size();
+  for (const Slab& sl : ctx->slabs)
+    if (sl.host) {
+      R->host_slabs++;
+      R->host_bytes += (double)sl.tiles * TILE_ELEMS * sizeof(float);
+    }
+  const Layout& L = ctx->lay;
+  const double tol = kStopMargin * o.ir_tol;
+  int prec = o.precision;
+  bool slab0_ready = false, probed16 = false;
+  TRY(reset_status(ctx));
+  if (prec == MAG_PREC_AUTO) {
+    prec = MAG_PREC_FP16X3;
+    const int64_t K = std::min<int64_t>(L.nb, kProbeTiles);
+    if (ctx->slabs[0].S >= K && L.N >= 3 * K) {
+      CU(cudaEventRecord(ctx->ev[0], s));
+      CU(launch_generate_slab(X, n, m, t, 0, ctx->slabs[0].S, ctx->slab_dev(ctx->slabs[0]), ctx->st(), s));
+      CU(cudaEventRecord(ctx->ev[1], s));
+      TRY(read_status(ctx));
+      R->ms_gen += elapsed(ctx, 0, 1);
+      if (ctx->h_st->flags & ST_NONFINITE) return fail(ctx, MAG_EINVAL, "non-finite coordinate in points");
+      if (ctx->h_st->flags & ST_DUPLICATE) return fail(ctx, MAG_EDUPLICATE, "two points coincide (min d = 0)");
+      slab0_ready = true;
+      double rho = INFINITY;
+      TRY(probe_fp16(ctx, X, m, t, false, R, &rho));
+      if (probe_takes_fp16(rho, tol, n, false)) {
+        prec = MAG_PREC_FP16;
+        probed16 = true;
+      }
+    }
+  }
+  if (prec != MAG_PREC_FP16 && prec != MAG_PREC_FP16X3)
+    return fail(ctx, MAG_EINVAL, "the out-of-core factor runs the FP16 and FP16X3 (or AUTO) precisions");
+  double overall = INFINITY;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    double* r = ctx->vd(V_R);
+    double* xw = ctx->vd(V_X);
+    double* best = ctx->vd(V_BEST);
+    double best_rel = INFINITY;
+    bool escalate = false;
+    if (!slab0_ready) TRY(reset_status(ctx));
+    CU(cudaEventRecord(ctx->ev[0], s));
+    ctx->prof_used = 0;
+    TRY(factor_ooc(ctx, X, m, t, upd_mode(prec), slab0_ready, &R->update_launches, &R->update_flops,
+                   &R->host_read_bytes));
+    slab0_ready = false;
+    CU(cudaEventRecord(ctx->ev[1], s));
+    TRY(read_status(ctx));
+    R->ms_fac += elapsed(ctx, 0, 1);
+    double pc[PC_COUNT];
+    R->ms_update += prof_collect(ctx, pc);
+    R->ms_update_panel += pc[PC_UPDATE_PANEL];
+    R->ms_potrf += pc[PC_POTRF];
+    R->ms_trsm += pc[PC_TRSM];
+    R->ms_host_read += pc[PC_HOST_READ];
+    const int fl = ctx->h_st->flags;
+    if (fl & ST_NONFINITE) return fail(ctx, MAG_EINVAL, "non-finite coordinate in points");
+    if (fl & ST_DUPLICATE) return fail(ctx, MAG_EDUPLICATE, "two points coincide (min d = 0)");
+    R->dmin = std::sqrt(bits_to_double(ctx->h_st->min_d2_bits));
+    if (fl & ST_TIMEOUT) return fail(ctx, MAG_ETIMEOUT, "a bounded device wait in the tensor-core update expired");
+    if (fl & ST_NOTPD) {
+      if (probed16 && o.allow_fallback) {
+        prec = MAG_PREC_FP16X3;
+        probed16 = false;
+        R->fallback = 3;
+        continue;
+      }
+      return fail(ctx, MAG_ENOTPD, "non-positive pivot at row %d of a slab (precision %d)",
+                  ctx->h_st->notpd_index - 1, prec);
+    }
+    R->prec_used = prec;
+    if (b)
+      CU(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    else
+      CU(launch_fill(r, n, 1.0, s));
+    CU(launch_fill(r + n, L.np - n, 0.0, s));
+    TRY(reset_norms(ctx));
+    CU(launch_absmax(r, n, ctx->st(), s));
+    TRY(correction(ctx, prec, r, xw, /*init=*/true, R));
+    double rel = INFINITY, prev = INFINITY;
+    int slow = 0;
+    for (int it = 0;; ++it) {
+      TRY(residual(ctx, X, m, t, xw, b, r, &rel, false, R));
+      if (rel < best_rel) {
+        best_rel = rel;
+        CU(cudaMemcpyAsync(best, xw, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      }
+      if (rel <= tol) break;
+      if (it >= o.ir_max_iters || (rel > 0.5 * prev && ++slow >= 2)) {
+        escalate = true;
+        break;
+      }
+      if (!(rel > 0.5 * prev)) slow = 0;
+      prev = rel;
+      TRY(correction(ctx, prec, r, xw, /*init=*/false, R));
+      R->ir_iters++;
+    }
+    if (best_rel < overall) {
+      overall = best_rel;
+      CU(cudaMemcpyAsync(x, best, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CU(cudaStreamSynchronize(s));
+    }
+    if (!escalate || !o.allow_fallback) break;
+    if (probed16 && prec == MAG_PREC_FP16) {
+      prec = MAG_PREC_FP16X3;
+      probed16 = false;
+      R->fallback = 3;
+      continue;
+    }
+    if (o.gmres_max_iters > 0) {
+      CU(cudaMemcpyAsync(xw, best, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      double grel = INFINITY;
+      R->fallback = 1;
+      TRY(gmres_ir(ctx, prec, X, m, t, b, xw, false, R, &grel));
+      if (grel < overall) {
+        overall = grel;
+        CU(cudaMemcpyAsync(x, xw, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CU(cudaStreamSynchronize(s));
+      }
+    }
+    break;
+  }
+  R->rel = overall;
+  if (!(overall < INFINITY)) return fail(ctx, MAG_ENOTPD, "no factor succeeded");
+  if (!(overall <= o.ir_tol))
+    return fail(ctx, MAG_ENOCONV, "refinement stopped at relative residual %.3e > %.3e", overall, o.ir_tol);
+  return MAG_OK;
+}
+
 int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, const double* b,
                double* x, SolveResult* R) {
   const mag_options& o = ctx->opt;
   int prec = o.precision;
+  {
+    int64_t pool_tiles = 0;
+    TRY(plan_out_of_core(ctx, n, prec, &pool_tiles));
+    if (pool_tiles > 0) return solve_ooc(ctx, X, n, m, t, b, x, pool_tiles, R);
+  }
   bool stored = o.residual_mode == MAG_RESID_STORED;
   if (o.residual_mode == MAG_RESID_AUTO && prec != MAG_PREC_FP64) {
     // Stored FP64 tiles cost one FP64 exp per pair once instead of once per
@@ -1259,9 +1696,7 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
     } else if (ctx->lay.N >= 3 * std::min<int64_t>(ctx->lay.nb, kProbeTiles)) {
       double rho = INFINITY;
       TRY(probe_fp16(ctx, X, m, t, stored, R, &rho));
-      const double tol = kStopMargin * o.ir_tol;
-      const double saved = (double)n / 9500.0 * (stored ? 1.0 : 0.25);
-      if (rho < 1.0 && ir_steps(rho, tol) - ir_steps(rho * 0x1p-12, tol) <= saved) {
+      if (probe_takes_fp16(rho, kStopMargin * o.ir_tol, n, stored)) {
         prec = MAG_PREC_FP16;
         probed16 = true;
       }
@@ -1383,6 +1818,11 @@ void fill_info(mag_ctx* ctx, const SolveResult& R, int64_t n, mag_info* info) {
   info->ms_split = R.ms_split;
   info->probe_rho = R.probe_rho;
   info->ms_probe = R.ms_probe;
+  info->slabs = R.slabs;
+  info->host_slabs = R.host_slabs;
+  info->host_bytes = R.host_bytes;
+  info->host_read_bytes = R.host_read_bytes;
+  info->ms_host_read = R.ms_host_read;
 }
 
 }  // namespace

@@ -42,6 +42,27 @@ __host__ __device__ inline void tri_coords(int64_t q, int64_t* I, int64_t* J) {
   *J = q - i * (i + 1) / 2;
 }
 
+// Packed lower tiles with at most W tile columns (a "slab": the first W
+// columns of a lower-triangular tile matrix).  Rows I < W are packed like
+// tri_index; rows I >= W hold W tiles each, row-major after them.  W >= the
+// number of rows gives tri_index exactly, so the full matrix is the case
+// W = N.  Tile (I, J) needs J <= min(I, W - 1).
+__host__ __device__ inline int64_t tile_index(int64_t I, int64_t J, int64_t W) {
+  return I < W ? I * (I + 1) / 2 + J : W * (W + 1) / 2 + (I - W) * W + J;
+}
+__host__ __device__ inline int64_t num_slab_tiles(int64_t rows, int64_t W) {
+  return rows <= W ? rows * (rows + 1) / 2 : W * (W + 1) / 2 + (rows - W) * W;
+}
+__host__ __device__ inline void tile_coords(int64_t q, int64_t W, int64_t* I, int64_t* J) {
+  const int64_t tri = W * (W + 1) / 2;
+  if (q < tri) {
+    tri_coords(q, I, J);
+  } else {
+    *I = W + (q - tri) / W;
+    *J = (q - tri) % W;
+  }
+}
+
 // Device-side status and scalar results of the kernels of one solve.  Reset
 // (memset 0 plus the min fields) before each solve, read back by the host.
 enum StatusFlags : int {
@@ -89,6 +110,12 @@ cudaError_t launch_generate(const double* X, int64_t n, int m, double t, int64_t
 cudaError_t launch_generate_dist(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
                                  double* Zd, double* Dd, double* rowsum, DevStatus* st, cudaStream_t s,
                                  int kind = MAT_EXP, double tiny_arg = INFINITY);
+// FP32 tiles of one slab for the out-of-core factor: global tile columns
+// [t0, t0 + W) of rows [t0, N), in the slab layout (tile_index with column
+// cap W, tile (0, 0) = global (t0, t0)); no row sums; min d^2 and flags as
+// above (the slabs of a factor partition the lower triangle's pairs).
+cudaError_t launch_generate_slab(const double* X, int64_t n, int m, double t, int64_t t0, int64_t W, float* Zf,
+                                 DevStatus* st, cudaStream_t s, double tiny_arg = INFINITY);
 // Z from stored FP64 distance tiles: Zf (may be null) and Zd (may be null), row sums.
 cudaError_t launch_generate_from_dist(const double* Dd, int64_t n, double t, int64_t N, float* Zf, double* Zd,
                                      double* rowsum, cudaStream_t s, int kind = MAT_EXP,
@@ -137,6 +164,7 @@ struct UpdParams {
   uint64_t timeout_ns; // bound on every barrier wait inside the kernel
   int max_tasks;       // > 0: a CTA (pair) leaves after that many tasks, so that
                        // SMs come free during the launch; 0: until the queue is empty
+  int64_t wcap;        // column cap of Z's tile layout (tile_index); <= 0: N (the whole matrix)
 };
 
 // Four TMA descriptors (A/B boxes of the hi and lo panel copies), 128 B each.
@@ -178,8 +206,10 @@ cudaError_t launch_split_col(const float* Z, int64_t K, int64_t N, int64_t k0, i
 // the panel buffer as launch_split_col does (lo only for FP16X3).  At most
 // `grid` persistent CTAs (129 KB of shared memory each) claim the N - K - 1
 // tiles from *counter, which must be zero before the launch.
+// wcap: column cap of Z's tile layout (tile_index), -1 for the whole matrix.
 cudaError_t launch_trsm_tc(float* Z, const float* Dinv, int64_t K, int64_t N, int64_t k0, int64_t width, int mode,
-                           void* hi, void* lo, unsigned* counter, DevStatus* st, int grid, cudaStream_t s);
+                           void* hi, void* lo, unsigned* counter, DevStatus* st, int grid, cudaStream_t s,
+                           int64_t wcap = -1);
 
 // K3: triangular solves with the packed factor, in place on v (np = N*TILE
 // entries of type T).  tmp: np entries of scratch.
@@ -198,6 +228,32 @@ cudaError_t launch_forward_persistent(const T* Z, const T* Dinv, int64_t N, cons
 template <typename T>
 cudaError_t launch_backward_persistent(const T* Z, const T* Dinv, int64_t N, const T* yv, T* x, unsigned* flags,
                                        DevStatus* st, uint64_t timeout_ns, cudaStream_t s);
+// The same sweeps with the transposed inverses given directly (DinvT: N tiles
+// of inv(L_II)^T), for the triangle of one slab of the out-of-core factor;
+// z_on_host: Z is host memory read in place (no L2 prefetch hints).
+template <typename T>
+cudaError_t launch_forward_sweep(const T* Z, const T* DinvT, int64_t N, const T* v, T* y, unsigned* progress,
+                                 DevStatus* st, uint64_t timeout_ns, bool z_on_host, cudaStream_t s);
+template <typename T>
+cudaError_t launch_backward_sweep(const T* Z, const T* Dinv, int64_t N, const T* yv, T* x, unsigned* progress,
+                                  DevStatus* st, uint64_t timeout_ns, bool z_on_host, cudaStream_t s);
+
+// Out-of-core factor (k_ooc.cu).  A slab of tile columns [q0, q0 + Sq) is
+// stored in the slab layout (tile_index with cap Sq, tile (0, 0) = global
+// (q0, q0)), in device or (mapped) host memory.
+// Panel copy for the updates of a later slab: for local tile rows I' in
+// [0, rows) (global c0 + I') and the global tile columns [k0, k0 + kw) of
+// slab (Lq, q0, Sq), writes 2^12 x rounded to FP16 (hi) and the rounded
+// remainder (lo, when split) at row I' * TILE + r, column (K - k0) * TILE + c
+// of the row-major panel buffers with `width` columns -- the values the
+// panel solve writes for the same entries of L.
+cudaError_t launch_gather_split(const float* Lq, int64_t q0, int64_t Sq, int64_t c0, int64_t rows, int64_t k0,
+                                int kw, void* hi, void* lo, int64_t width, bool split, cudaStream_t s);
+// v[r] -= sum_c A[r][c] y[c] for the rectangle part of a slab (R tile rows x
+// S tile columns, tile (i, j) at A + (i S + j) TILE^2): r < R TILE, c < S TILE.
+cudaError_t launch_rect_gemv(const float* A, int64_t R, int64_t S, const float* y, float* v, cudaStream_t s);
+// y[c] -= sum_r A[r][c] x[r] (the transposed product) for the same rectangle.
+cudaError_t launch_rect_gemv_t(const float* A, int64_t R, int64_t S, const float* x, float* y, cudaStream_t s);
 
 // K4: FP64 residual r = b - Z w (b == null means all ones), Z regenerated
 // from the points (matrix free) or read from FP64 packed tiles (stored).
