@@ -571,7 +571,8 @@ int tc_panel_range(TcFactor& F, int64_t k0, int64_t a, int64_t b, int buf, cudaS
 
 // The panel of tile columns [k0, min(N, k0 + nb)) into panel buffer b.
 int tc_panel(TcFactor& F, int64_t k0, int b, cudaStream_t st) {
-  const int64_t k1 = std::min<int64_t>(F.N, k0 + F.nb);
+  // a slab's last panel ends at its column cap
+  const int64_t k1 = std::min<int64_t>(F.W > 0 ? F.W : F.N, k0 + F.nb);
   return tc_panel_range(F, k0, k0, k1, b, st);
 }
 

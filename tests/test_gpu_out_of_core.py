@@ -71,13 +71,14 @@ def test_slabs_on_host_match_oracle(ref_cube, prec, t):
     assert abs(mag2 - mag) <= 1e-12 * abs(mag)
 
 
-@pytest.mark.parametrize("n,pool", [(5000, 300), (3000, 10 ** 6)])
-def test_ragged_sizes_and_a_single_slab(n, pool):
-    # n = 5000: a ragged last tile row inside host slabs; n = 3000 with room
-    # for everything: the forced out-of-core path as one device slab
+@pytest.mark.parametrize("n,pool,panel", [(5000, 300, 0), (5000, 400, 3), (3000, 10 ** 6, 0)])
+def test_ragged_sizes_and_a_single_slab(n, pool, panel):
+    # n = 5000: a ragged last tile row inside host slabs, and slab widths that
+    # are no multiple of a 3-tile panel; n = 3000 with room for everything:
+    # the forced out-of-core path as one device slab
     X = np.random.default_rng(n).random((n, 5))
     t = 3.0
-    c = M.Context(M.Options(precision="fp16x3", out_of_core=1,
+    c = M.Context(M.Options(precision="fp16x3", out_of_core=1, panel_tiles=panel,
                             workspace_limit_bytes=_limit_for_pool(n, pool)))
     w, mag, info = c.solve(_dev(X), t)
     c.close()
