@@ -31,10 +31,10 @@ def _signs(w):
     return np.sign(w) * keep
 
 
-def _limit_for_pool(n, pool_tiles):
+def _limit_for_pool(n, pool_tiles, panel_tiles=0):
     """A workspace limit that leaves `pool_tiles` FP32 tiles for the slabs
     next to the rest of the workspace (vectors, panel buffers, inverses)."""
-    c = M.Context(M.Options(residual_mode="matrix_free"))
+    c = M.Context(M.Options(residual_mode="matrix_free", panel_tiles=panel_tiles))
     total = c.workspace_bytes(n, 8)
     c.close()
     N = (n + 127) // 128
@@ -79,7 +79,7 @@ def test_ragged_sizes_and_a_single_slab(n, pool, panel):
     X = np.random.default_rng(n).random((n, 5))
     t = 3.0
     c = M.Context(M.Options(precision="fp16x3", out_of_core=1, panel_tiles=panel,
-                            workspace_limit_bytes=_limit_for_pool(n, pool)))
+                            workspace_limit_bytes=_limit_for_pool(n, pool, panel)))
     w, mag, info = c.solve(_dev(X), t)
     c.close()
     if pool < 10 ** 6:
