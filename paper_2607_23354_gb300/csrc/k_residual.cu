@@ -175,6 +175,173 @@ __global__ void __launch_bounds__(256) k_resid_stored(const double* __restrict__
   }
 }
 
+// Matrix-free FP64 residual over the lower triangle of tiles only (Z is
+// symmetric): one CTA per lower tile (I, J) computes its 128 x 128 entries
+// Z_jk = exp(-t d_jk) once -- the FP64 differences, square root and
+// exponential of the generator -- and uses each twice: the row contributions
+// Z_IJ w_J (rows of block I) go to partial P[I][J], and for I != J the
+// column contributions Z_IJ^T w_I (rows of block J) to P[J][I], so every row
+// block X has exactly N partials P[X][0..N-1] (J <= X: its tiles' rows;
+// J > X: the tiles below it, transposed).  Within a tile each thread adds its
+// 4 (row) or 8 (column) products with FMAs and the partial is a shuffle /
+// shared-memory tree; across tiles k_resid_sym_finish adds the N partials of
+// a row with Neumaier compensation (the accuracy class of the stored-tile
+// residual).  Row sums of Z for ||Z||inf go to rowsum (FP32 within a tile,
+// FP64 atomics across tiles: a norm).  Thread layout as in the generator:
+// warp w has tile rows w + 16 i (i < 8), lane l columns l + 32 q (q < 4).
+constexpr int SYM_THREADS = 512;
+constexpr int SYM_MC = 32;
+
+__global__ void __launch_bounds__(SYM_THREADS, 1)
+    k_resid_sym(const double* __restrict__ X, int64_t n, int m, double t, const double* __restrict__ w,
+                double* __restrict__ P, double* __restrict__ rowsum, int64_t N, int kind) {
+  extern __shared__ double smem[];
+  double* xr = smem;                   // [TILE][SYM_MC] row points
+  double* xc = smem + TILE * SYM_MC;   // [SYM_MC][TILE] column points
+  __shared__ double colpart[SYM_THREADS / 32][TILE];
+  __shared__ float zcol[SYM_THREADS / 32][TILE];
+  __shared__ double exptab[2 * EXPT_SIZE];
+  load_exp_table(exptab);
+  int64_t I, J;
+  tri_coords((int64_t)blockIdx.x, &I, &J);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row0 = I * TILE, col0 = J * TILE;
+  double d2[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) d2[i][q] = 0.0;
+  for (int l0 = 0; l0 < m; l0 += SYM_MC) {
+    const int mc = min(SYM_MC, m - l0);
+    for (int e = threadIdx.x; e < TILE * mc; e += SYM_THREADS) {
+      const int r = e / mc, l = e - r * mc;
+      const int64_t gr = row0 + r, gc = col0 + r;
+      xr[r * SYM_MC + l] = gr < n ? X[gr * m + l0 + l] : 0.0;
+      xc[l * TILE + r] = gc < n ? X[gc * m + l0 + l] : 0.0;
+    }
+    __syncthreads();
+    for (int l = 0; l < mc; ++l) {
+      double a[8], b[4];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = xr[(warp + 16 * i) * SYM_MC + l];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) b[q] = xc[l * TILE + lane + 32 * q];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const double diff = a[i] - b[q];
+          d2[i][q] = fma(diff, diff, d2[i][q]);
+        }
+    }
+    __syncthreads();
+  }
+  __shared__ double s_wr[TILE], s_wc[TILE];
+  if (threadIdx.x < TILE) {
+    const int64_t gr = row0 + threadIdx.x, gc = col0 + threadIdx.x;
+    s_wr[threadIdx.x] = gr < n ? w[gr] : 0.0;
+    s_wc[threadIdx.x] = gc < n ? w[gc] : 0.0;
+  }
+  __syncthreads();
+  double cs[4] = {0.0, 0.0, 0.0, 0.0};
+  float zc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  // rows of block I: each row's 4 products per lane, then a lane tree -> P[I][J]
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = warp + 16 * i;
+    const int64_t gr = row0 + r;
+    const double wri = s_wr[r];
+    double v = 0.0;
+    float zv = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t gc = col0 + lane + 32 * q;
+      double z = 0.0;
+      if (gr < n && gc < n) {
+        if (gr == gc) {
+          z = 1.0;
+        } else {
+          const double dd = sqrt_pos(d2[i][q]);
+          z = kind ? fma(-t, dd, 1.0) : exp_neg(-t * dd, exptab);
+        }
+      }
+      v = fma(z, s_wc[lane + 32 * q], v);
+      cs[q] = fma(z, wri, cs[q]);
+      const float zf = kind ? (float)z : f64_to_f32_nonneg(z);
+      zv += zf;
+      zc[q] += zf;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v += __shfl_xor_sync(0xffffffffu, v, o);
+      zv += __shfl_xor_sync(0xffffffffu, zv, o);
+    }
+    if (lane == 0) {
+      P[(I * N + J) * TILE + r] = v;
+      if (gr < n) atomicAdd(rowsum + gr, (double)zv);
+    }
+  }
+  if (I == J) return;  // uniform: a diagonal tile's rows cover both triangles
+  // rows of block J (the transposed tile): P[J][I]
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    colpart[warp][lane + 32 * q] = cs[q];
+    zcol[warp][lane + 32 * q] = zc[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < TILE) {
+    double v = 0.0;
+    float zv = 0.0f;
+#pragma unroll
+    for (int k = 0; k < SYM_THREADS / 32; ++k) {
+      v += colpart[k][threadIdx.x];
+      zv += zcol[k][threadIdx.x];
+    }
+    P[(J * N + I) * TILE + threadIdx.x] = v;
+    if (col0 + threadIdx.x < n) atomicAdd(rowsum + col0 + threadIdx.x, (double)zv);
+  }
+}
+
+// r_j = b_j - (the N partials of row j, Neumaier), and the three norms.
+__global__ void k_resid_sym_finish(const double* __restrict__ P, int64_t n, int64_t N, int64_t np,
+                                   const double* __restrict__ w, const double* __restrict__ b,
+                                   const double* __restrict__ rowsum, double* __restrict__ r, DevStatus* st) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double ra = 0.0, za = 0.0, wa = 0.0;
+  if (j < n) {
+    const int64_t I = j / TILE, rr = j % TILE;
+    double s = 0.0, c = 0.0;
+    for (int64_t J = 0; J < N; ++J) {
+      const double v = P[(I * N + J) * TILE + rr];
+      const double tt = s + v;
+      if (fabs(s) >= fabs(v))
+        c += (s - tt) + v;
+      else
+        c += (v - tt) + s;
+      s = tt;
+    }
+    const double bj = b ? b[j] : 1.0;
+    const double rj = (bj - s) - c;
+    r[j] = rj;
+    ra = fabs(rj);
+    za = rowsum[j];
+    wa = fabs(w[j]);
+  } else if (j < np) {
+    r[j] = 0.0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ra = fmax(ra, __shfl_xor_sync(0xffffffffu, ra, o));
+    za = fmax(za, __shfl_xor_sync(0xffffffffu, za, o));
+    wa = fmax(wa, __shfl_xor_sync(0xffffffffu, wa, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg(&st->r_max_bits, ra);
+    atomic_max_nonneg(&st->z_max_bits, za);
+    atomic_max_nonneg(&st->w_max_bits, wa);
+  }
+}
+
 // r_j = b_j - (sum of the partials of row j) with Neumaier compensation: row
 // block X holds P[X][J] for J <= X (its tiles' row sums) followed by
 // P[X][X+t], t = 1..ceil((N-1-X)/S) (the strips' column sums); with ||r||,
@@ -530,6 +697,27 @@ cudaError_t launch_residual_mf(const double* X, int64_t n, int m, double t, cons
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_resid_finish<<<blocks_for(np, 256), 256, 0, s>>>(part, chunks, n, np, w, b, r, st);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_sym(const double* X, int64_t n, int m, double t, const double* w, const double* b,
+                                double* r, double* P, double* rowsum, int64_t np, DevStatus* st, cudaStream_t s,
+                                int kind) {
+  if (m < 1 || m > MAG_MAX_DIM) return cudaErrorInvalidValue;
+  const int64_t N = (n + TILE - 1) / TILE;
+  const int64_t tiles = num_lower_tiles(N);
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const size_t smem = 2 * (size_t)TILE * SYM_MC * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_resid_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(rowsum, 0, (size_t)n * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  k_resid_sym<<<(unsigned)tiles, SYM_THREADS, smem, s>>>(X, n, m, t, w, P, rowsum, N, kind);
+  note_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_resid_sym_finish<<<blocks_for(np, 256), 256, 0, s>>>(P, n, N, np, w, b, rowsum, r, st);
   note_launch();
   return cudaGetLastError();
 }

@@ -234,8 +234,8 @@ Layout plan(const mag_ctx* ctx, int64_t n, bool f32, bool f64, bool dist = false
   if (f32) off = align_up(off + (size_t)L.zf_tiles * TILE_ELEMS * sizeof(float));
   L.off_zd = off;
   if (f64) off = align_up(off + (size_t)L.tiles * TILE_ELEMS * sizeof(double));
-  L.off_spart = off;  // partials of the stored residual: N * N * 128 doubles
-  if (f64) off = align_up(off + (size_t)L.N * L.N * TILE * sizeof(double));
+  L.off_spart = off;  // partials of the stored and the symmetric matrix-free residual: N * N * 128 doubles
+  if (f32 || f64) off = align_up(off + (size_t)L.N * L.N * TILE * sizeof(double));
   L.total = off;
   return L;
 }
@@ -1237,7 +1237,7 @@ int residual(mag_ctx* ctx, const double* X, int32_t m, double t, const double* w
     CU(launch_residual_stored(ctx->zd(), L.n, L.N, w, b, ctx->vd(V_ROWSUM), r, ctx->spart(), L.np,
                               ctx->st(), s));
   else
-    CU(launch_residual_mf(X, L.n, m, t, w, b, r, ctx->part(), L.chunks, L.np, ctx->st(), s, ctx->kind));
+    CU(launch_residual_sym(X, L.n, m, t, w, b, r, ctx->spart(), ctx->vd(V_ROWSUM), L.np, ctx->st(), s, ctx->kind));
   CU(cudaEventRecord(ctx->ev[1], s));
   TRY(read_status(ctx));
   if (ctx->h_st->flags & ST_TIMEOUT)
@@ -1415,7 +1415,8 @@ int gmres_ir(mag_ctx* ctx, int prec, const double* X, int32_t m, double t, const
     if (stored)
       CU(launch_residual_stored(ctx->zd(), n, L.N, v, zeros, ctx->vd(V_ROWSUM), tmp, ctx->spart(), np, ctx->st(), s));
     else
-      CU(launch_residual_mf(X, n, m, t, v, zeros, tmp, ctx->part(), L.chunks, np, ctx->st(), s, ctx->kind));
+      CU(launch_residual_sym(X, n, m, t, v, zeros, tmp, ctx->spart(), ctx->vd(V_ROWSUM), np, ctx->st(), s,
+                             ctx->kind));
     TRY(correction(ctx, prec, tmp, out, /*init=*/true, R));
     CU(launch_scale(out, -1.0, out, n, s));
     return MAG_OK;

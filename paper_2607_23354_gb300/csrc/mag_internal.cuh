@@ -261,6 +261,12 @@ cudaError_t launch_rect_gemv_t(const float* A, int64_t R, int64_t S, const float
 cudaError_t launch_residual_mf(const double* X, int64_t n, int m, double t, const double* w,
                                const double* b, double* r, double* part, int chunks, int64_t np,
                                DevStatus* st, cudaStream_t s, int kind = MAT_EXP);
+// Matrix free over the lower triangle (each Z entry computed once, used for
+// its row and its column): P is scratch of N * N * 128 doubles, rowsum of n
+// doubles (overwritten with the row sums of Z).  Same outputs as above.
+cudaError_t launch_residual_sym(const double* X, int64_t n, int m, double t, const double* w, const double* b,
+                                double* r, double* P, double* rowsum, int64_t np, DevStatus* st, cudaStream_t s,
+                                int kind = MAT_EXP);
 // Stored: P is scratch of N * N * 128 doubles (one partial per row block,
 // tile and row); rowsum holds the row sums of Z from the generator.
 cudaError_t launch_residual_stored(const double* Zd, int64_t n, int64_t N, const double* w,

@@ -628,3 +628,21 @@ def test_stored_residual_on_separated_clusters(ctx):
     assert info["residual_mode"] == M.RESID_STORED
     w_ref, mag_ref, _ = oracle.weighting(X, t)
     check_solution(X, t, w.cpu().numpy(), mag, w_ref, mag_ref)
+
+
+@pytest.mark.parametrize("n,m,t", [(9000, 8, 1.0), (4500, 3, 0.3), (130, 16, 5.0)])
+def test_matrix_free_refinement_over_the_lower_triangle(ctx, n, m, t):
+    # the solver's matrix-free residual visits each lower tile once and uses
+    # its entries for two row blocks; several row blocks and a ragged tail
+    X = _cloud(n, m, seed=n + m)
+    ctx.set_options(M.Options(residual_mode="matrix_free"))
+    try:
+        w, mag, info = ctx.solve(_dev(X), t)
+    finally:
+        ctx.set_options(M.Options())
+    assert info["residual_mode"] == M.RESID_MATRIX_FREE
+    w_ref, mag_ref, _ = oracle.weighting(X, t)
+    check_solution(X, t, w.cpu().numpy(), mag, w_ref, mag_ref)
+    # its ||Z||inf is the oracle's
+    _, rs = oracle.residual_rows(X, t, w_ref)
+    assert info["z_norm_inf"] == pytest.approx(rs.max(), rel=1e-6)
