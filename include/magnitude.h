@@ -140,7 +140,15 @@ typedef struct mag_options {
                              sized by workspace_limit_bytes or the free device
                              memory); -1: never.  FP16, FP16X3 and AUTO only;
                              the residual is then matrix free.             */
-  int32_t reserved1;
+  int32_t deflate;        /* mag_solve at the small-t end, where Z nears the
+                             all-ones matrix: 0 (default) when t max d <= 1/4
+                             (judged from max_j ||x_j - x_0||), solve instead
+                             A u = 1 with A = (Z - (1 - c t) 1 1^T) / t
+                             (entries c + expm1(-t d_jk) / t, diagonal c),
+                             positive definite and well conditioned for c
+                             large enough, and return w = u / (t + (1 - c t)
+                             1^T u) = Z^{-1} 1 (Sherman-Morrison); 1: always;
+                             -1: never.  Reported in mag_info.deflation_c.  */
   double host_limit_bytes;/* pinned host memory the out-of-core factor may
                              take (0: half of the host's physical memory);
                              more gives MAG_ENOMEM                          */
@@ -189,6 +197,10 @@ typedef struct mag_info {
   double host_read_bytes;  /* bytes the factor's slab updates read from host
                               memory (over the CPU-GPU link)                   */
   double ms_host_read;     /* device time of those reads (profile = 1)          */
+  double deflation_c;      /* c of the deflated small-t solve (0: not used);
+                              rel_residual, z_norm_inf and w_norm_inf are then
+                              those of Z w = 1, the refinement's counts those
+                              of A u = 1                                       */
 } mag_info;
 
 typedef struct mag_ctx mag_ctx;

@@ -47,7 +47,7 @@ class mag_options(ctypes.Structure):
                 ("lookahead", ctypes.c_int32), ("lookahead_sms", ctypes.c_int32),
                 ("cta_pairs", ctypes.c_int32), ("tplus_method", ctypes.c_int32),
                 ("wait_timeout_ns", ctypes.c_int64), ("out_of_core", ctypes.c_int32),
-                ("reserved1", ctypes.c_int32), ("host_limit_bytes", ctypes.c_double)]
+                ("deflate", ctypes.c_int32), ("host_limit_bytes", ctypes.c_double)]
 
 
 class mag_info(ctypes.Structure):
@@ -67,7 +67,8 @@ class mag_info(ctypes.Structure):
                 ("ms_potrf", ctypes.c_double), ("ms_trsm", ctypes.c_double), ("ms_split", ctypes.c_double),
                 ("probe_rho", ctypes.c_double), ("ms_probe", ctypes.c_double), ("t", ctypes.c_double),
                 ("slabs", ctypes.c_int32), ("host_slabs", ctypes.c_int32), ("host_bytes", ctypes.c_double),
-                ("host_read_bytes", ctypes.c_double), ("ms_host_read", ctypes.c_double)]
+                ("host_read_bytes", ctypes.c_double), ("ms_host_read", ctypes.c_double),
+                ("deflation_c", ctypes.c_double)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -157,6 +158,7 @@ class Options:
     tplus_method: str = "bisection"
     wait_timeout_ns: int = 10_000_000_000
     out_of_core: int = 0
+    deflate: int = 0
     host_limit_bytes: float = 0.0
 
     def to_c(self) -> mag_options:
@@ -179,6 +181,7 @@ class Options:
         o.tplus_method = {"bisection": 0, "ridders": 1}[self.tplus_method]
         o.wait_timeout_ns = int(self.wait_timeout_ns)
         o.out_of_core = int(self.out_of_core)
+        o.deflate = int(self.deflate)
         o.host_limit_bytes = float(self.host_limit_bytes)
         return o
 

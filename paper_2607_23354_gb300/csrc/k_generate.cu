@@ -35,7 +35,7 @@ template <bool WF, bool WD, bool ROWSUM, bool WDIST>
 __global__ void __launch_bounds__(GEN_THREADS, 1)
     k_generate(const double* __restrict__ X, int64_t n, int m, double t, float* __restrict__ Zf,
                double* __restrict__ Zd, double* __restrict__ Dd, double* __restrict__ rowsum, DevStatus* st,
-               int kind, double tiny_arg, int64_t t0, int64_t W) {
+               int kind, double tiny_arg, int64_t t0, int64_t W, double kc) {
   extern __shared__ double smem[];
   double* xr = smem;                   // [TILE][GEN_MC] row points (broadcast reads)
   double* xc = smem + TILE * GEN_MC;   // [GEN_MC][TILE] column points (conflict free)
@@ -92,6 +92,8 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
   unsigned long long mind2b = 0x7ff0000000000000ull;  // +inf
   int flags = 0;
   const float tf = (float)t;
+  const double tinv = 1.0 / t;
+  const double diag = kind == MAT_DEFLATED ? kc : 1.0;
   // d > tiny_arg / t on the bit patterns (d >= 0): the FP64 pipe stays on
   // the distances and the exponential
   const unsigned long long tiny_bits = (unsigned long long)__double_as_longlong(tiny_arg / t);
@@ -108,7 +110,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
       double zd = 0.0, dd = 0.0;
       float zf = 0.0f;
       if (gr >= n || gc >= n || gr == gc) {
-        zd = (gr == gc) ? 1.0 : 0.0;
+        zd = (gr == gc) ? (gr < n ? diag : 1.0) : 0.0;
         zf = (float)zd;
       } else {
         // v >= 0 or NaN: the checks and the minimum on the bit pattern (integer
@@ -122,8 +124,12 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
           zf = exp_neg_tiny(t * dd);
           zd = (double)zf;
         } else {
-          if (WD) zd = kind ? fma(-t, dd, 1.0) : exp_neg(-t * dd, exptab);
-          if (WF) zf = WD ? f64_to_f32_nonneg(zd) : (kind ? 1.0f - tf * sqrtf((float)v) : expf(-tf * sqrtf((float)v)));
+          if (WD) zd = mat_entry(kind, t, tinv, kc, dd, exptab);
+          if (WF)
+            zf = WD ? (kind == MAT_DEFLATED ? __double2float_rn(zd) : f64_to_f32_nonneg(zd))
+                    : (kind == MAT_EXP ? expf(-tf * sqrtf((float)v))
+                                       : (kind == MAT_SHIFTED_DIST ? 1.0f - tf * sqrtf((float)v)
+                                                                   : (float)kc + expm1f(-tf * sqrtf((float)v)) / tf));
         }
       }
       if (WF) Zf[tile_off + (int64_t)r * TILE + c] = zf;
@@ -178,7 +184,8 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
 template <bool WF, bool WD>
 __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __restrict__ Dd, int64_t n, double t,
                                                             float* __restrict__ Zf, double* __restrict__ Zd,
-                                                            double* __restrict__ rowsum, int kind, double tiny_arg) {
+                                                            double* __restrict__ rowsum, int kind, double tiny_arg,
+                                                            double kc) {
   __shared__ double exptab[2 * EXPT_SIZE];
   __shared__ float colpart[8][TILE];
   load_exp_table(exptab);
@@ -188,6 +195,8 @@ __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __rest
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t off = tri_index(I, J) * TILE_ELEMS;
   const float tf = (float)t;
+  const double tinv = 1.0 / t;
+  const double diag = kind == MAT_DEFLATED ? kc : 1.0;
   const unsigned long long tiny_bits = (unsigned long long)__double_as_longlong(tiny_arg / t);
   // row/column partial sums in FP32 (a norm; the FP64 pipe is the limit)
   float cs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -203,17 +212,20 @@ __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __rest
       double zd;
       float zf;
       if (gr >= n || gc >= n || gr == gc) {
-        zd = (gr == gc) ? 1.0 : 0.0;
+        zd = (gr == gc) ? (gr < n ? diag : 1.0) : 0.0;
         zf = (float)zd;
-        if (gr == gc && gr < n) rs += 1.0f;  // the diagonal counts in its row sum
+        if (gr == gc && gr < n) rs += zf;  // the diagonal counts in its row sum
       } else {
         const double d = Dd[e];
         if (WD && !kind && (unsigned long long)__double_as_longlong(d) > tiny_bits) {
           zf = exp_neg_tiny(t * d);
           zd = (double)zf;
         } else {
-          zd = WD ? (kind ? fma(-t, d, 1.0) : exp_neg(-t * d, exptab)) : 0.0;
-          zf = WD ? f64_to_f32_nonneg(zd) : (kind ? 1.0f - tf * (float)d : expf(-tf * (float)d));
+          zd = WD ? mat_entry(kind, t, tinv, kc, d, exptab) : 0.0;
+          zf = WD ? (kind == MAT_DEFLATED ? __double2float_rn(zd) : f64_to_f32_nonneg(zd))
+                  : (kind == MAT_EXP ? expf(-tf * (float)d)
+                                     : (kind == MAT_SHIFTED_DIST ? 1.0f - tf * (float)d
+                                                                 : (float)kc + expm1f(-tf * (float)d) / tf));
         }
         rs += zf;
         cs[q] += zf;
@@ -267,7 +279,7 @@ __global__ void k_rowsum_max(const double* __restrict__ rowsum, int64_t n, DevSt
 template <bool WF, bool WD, bool ROWSUM, bool WDIST = false>
 cudaError_t launch_gen_t(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
                          double* Zd, double* rowsum, DevStatus* st, cudaStream_t s, double* Dd = nullptr,
-                         int kind = 0, double tiny_arg = INFINITY, int64_t t0 = 0, int64_t W = -1) {
+                         int kind = 0, double tiny_arg = INFINITY, int64_t t0 = 0, int64_t W = -1, double kc = 0.0) {
   const size_t smem = 2 * (size_t)TILE * GEN_MC * sizeof(double);
   auto kern = k_generate<WF, WD, ROWSUM, WDIST>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -276,7 +288,7 @@ cudaError_t launch_gen_t(const double* X, int64_t n, int m, double t, int64_t N,
   if (W < 0) W = N;
   const int64_t tiles = num_slab_tiles(N, W);
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-  kern<<<(unsigned)tiles, GEN_THREADS, smem, s>>>(X, n, m, t, Zf, Zd, Dd, rowsum, st, kind, tiny_arg, t0, W);
+  kern<<<(unsigned)tiles, GEN_THREADS, smem, s>>>(X, n, m, t, Zf, Zd, Dd, rowsum, st, kind, tiny_arg, t0, W, kc);
   note_launch();
   return cudaGetLastError();
 }
@@ -284,35 +296,36 @@ cudaError_t launch_gen_t(const double* X, int64_t n, int m, double t, int64_t N,
 }  // namespace
 
 cudaError_t launch_generate(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
-                            double* Zd, double* rowsum, DevStatus* st, cudaStream_t s, int kind, double tiny_arg) {
+                            double* Zd, double* rowsum, DevStatus* st, cudaStream_t s, int kind, double tiny_arg,
+                            double kc) {
   if (Zf && Zd)
-    return launch_gen_t<true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, nullptr, kind, tiny_arg);
-  if (Zf) return launch_gen_t<true, false, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, nullptr, kind);
+    return launch_gen_t<true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, nullptr, kind, tiny_arg, 0, -1, kc);
+  if (Zf) return launch_gen_t<true, false, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, nullptr, kind, INFINITY, 0, -1, kc);
   if (Zd)
-    return launch_gen_t<false, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, nullptr, kind, tiny_arg);
+    return launch_gen_t<false, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, nullptr, kind, tiny_arg, 0, -1, kc);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_generate_dist(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
                                  double* Zd, double* Dd, double* rowsum, DevStatus* st, cudaStream_t s,
-                                 int kind, double tiny_arg) {
+                                 int kind, double tiny_arg, double kc) {
   if (Zf && Zd)
-    return launch_gen_t<true, true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd, kind, tiny_arg);
-  if (Zf) return launch_gen_t<true, false, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd, kind);
+    return launch_gen_t<true, true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd, kind, tiny_arg, 0, -1, kc);
+  if (Zf) return launch_gen_t<true, false, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd, kind, INFINITY, 0, -1, kc);
   if (Zd)
-    return launch_gen_t<false, true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd, kind, tiny_arg);
+    return launch_gen_t<false, true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd, kind, tiny_arg, 0, -1, kc);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_generate_from_dist(const double* Dd, int64_t n, double t, int64_t N, float* Zf, double* Zd,
-                                     double* rowsum, cudaStream_t s, int kind, double tiny_arg) {
+                                     double* rowsum, cudaStream_t s, int kind, double tiny_arg, double kc) {
   const unsigned tiles = (unsigned)num_lower_tiles(N);
   if (Zf && Zd)
-    k_generate_from_dist<true, true><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum, kind, tiny_arg);
+    k_generate_from_dist<true, true><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum, kind, tiny_arg, kc);
   else if (Zf)
-    k_generate_from_dist<true, false><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum, kind, INFINITY);
+    k_generate_from_dist<true, false><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum, kind, INFINITY, kc);
   else if (Zd)
-    k_generate_from_dist<false, true><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum, kind, tiny_arg);
+    k_generate_from_dist<false, true><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum, kind, tiny_arg, kc);
   else
     return cudaErrorInvalidValue;
   note_launch();

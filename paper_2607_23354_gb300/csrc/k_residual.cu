@@ -34,13 +34,14 @@ __global__ void __launch_bounds__(RES_THREADS) k_resid_mf(const double* __restri
                                                           int m, double t,
                                                           const double* __restrict__ w,
                                                           double* __restrict__ part, int chunks,
-                                                          int64_t np, int ct, int kind) {
+                                                          int64_t np, int ct, int kind, double kc) {
   extern __shared__ double sm[];
   double* xc = sm;            // [ct][m]
   double* wc = sm + ct * m;   // [ct]
   __shared__ double exptab[2 * EXPT_SIZE];
   load_exp_table(exptab);
   const int64_t j = (int64_t)blockIdx.x * RES_THREADS + threadIdx.x;
+  const double tinv = 1.0 / t;
   const int64_t ntiles = (n + ct - 1) / ct;
   const int64_t per = (ntiles + chunks - 1) / chunks;
   const int64_t c0 = blockIdx.y * per * ct;
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_resid_mf(const double* __restri
         }
       }
       const double dd = sqrt_pos(d2);
-      const double z = kind ? fma(-t, dd, 1.0) : exp_neg(-t * dd, exptab);
+      const double z = mat_entry(kind, t, tinv, kc, dd, exptab);  // dd = 0 (k = j): the diagonal
       zs += z;
       // Kahan step for s += z * w_k
       const double y = fma(z, wc[q], -c);
@@ -194,7 +195,7 @@ constexpr int SYM_MC = 32;
 
 __global__ void __launch_bounds__(SYM_THREADS, 1)
     k_resid_sym(const double* __restrict__ X, int64_t n, int m, double t, const double* __restrict__ w,
-                double* __restrict__ P, double* __restrict__ rowsum, int64_t N, int kind) {
+                double* __restrict__ P, double* __restrict__ rowsum, int64_t N, int kind, double kc) {
   extern __shared__ double smem[];
   double* xr = smem;                   // [TILE][SYM_MC] row points
   double* xc = smem + TILE * SYM_MC;   // [SYM_MC][TILE] column points
@@ -245,6 +246,7 @@ __global__ void __launch_bounds__(SYM_THREADS, 1)
   __syncthreads();
   double cs[4] = {0.0, 0.0, 0.0, 0.0};
   float zc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  const double tinv = 1.0 / t, diag = kind == MAT_DEFLATED ? kc : 1.0;
   // rows of block I: each row's 4 products per lane, then a lane tree -> P[I][J]
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -259,15 +261,15 @@ __global__ void __launch_bounds__(SYM_THREADS, 1)
       double z = 0.0;
       if (gr < n && gc < n) {
         if (gr == gc) {
-          z = 1.0;
+          z = diag;
         } else {
           const double dd = sqrt_pos(d2[i][q]);
-          z = kind ? fma(-t, dd, 1.0) : exp_neg(-t * dd, exptab);
+          z = mat_entry(kind, t, tinv, kc, dd, exptab);
         }
       }
       v = fma(z, s_wc[lane + 32 * q], v);
       cs[q] = fma(z, wri, cs[q]);
-      const float zf = kind ? (float)z : f64_to_f32_nonneg(z);
+      const float zf = kind ? __double2float_rn(z) : f64_to_f32_nonneg(z);
       zv += zf;
       zc[q] += zf;
     }
@@ -672,7 +674,7 @@ inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + thre
 
 cudaError_t launch_residual_mf(const double* X, int64_t n, int m, double t, const double* w,
                                const double* b, double* r, double* part, int chunks, int64_t np,
-                               DevStatus* st, cudaStream_t s, int kind) {
+                               DevStatus* st, cudaStream_t s, int kind, double kc) {
   if (m < 1 || m > MAG_MAX_DIM) return cudaErrorInvalidValue;
   int ct = 128;
   while (ct > 8 && (size_t)ct * (m + 1) * sizeof(double) > 44 * 1024) ct /= 2;
@@ -686,13 +688,13 @@ cudaError_t launch_residual_mf(const double* X, int64_t n, int m, double t, cons
     if (e != cudaSuccess) return e;
   }
   if (m <= 8)
-    k_resid_mf<8><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct, kind);
+    k_resid_mf<8><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct, kind, kc);
   else if (m <= 16)
-    k_resid_mf<16><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct, kind);
+    k_resid_mf<16><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct, kind, kc);
   else if (m <= 32)
-    k_resid_mf<32><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct, kind);
+    k_resid_mf<32><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct, kind, kc);
   else
-    k_resid_mf<0><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct, kind);
+    k_resid_mf<0><<<grid, RES_THREADS, smem, s>>>(X, n, m, t, w, part, chunks, np, ct, kind, kc);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -703,7 +705,7 @@ cudaError_t launch_residual_mf(const double* X, int64_t n, int m, double t, cons
 
 cudaError_t launch_residual_sym(const double* X, int64_t n, int m, double t, const double* w, const double* b,
                                 double* r, double* P, double* rowsum, int64_t np, DevStatus* st, cudaStream_t s,
-                                int kind) {
+                                int kind, double kc) {
   if (m < 1 || m > MAG_MAX_DIM) return cudaErrorInvalidValue;
   const int64_t N = (n + TILE - 1) / TILE;
   const int64_t tiles = num_lower_tiles(N);
@@ -713,7 +715,7 @@ cudaError_t launch_residual_sym(const double* X, int64_t n, int m, double t, con
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(rowsum, 0, (size_t)n * sizeof(double), s);
   if (e != cudaSuccess) return e;
-  k_resid_sym<<<(unsigned)tiles, SYM_THREADS, smem, s>>>(X, n, m, t, w, P, rowsum, N, kind);
+  k_resid_sym<<<(unsigned)tiles, SYM_THREADS, smem, s>>>(X, n, m, t, w, P, rowsum, N, kind, kc);
   note_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -896,7 +898,7 @@ extern "C" int mag_residual_noalloc(const double* points, int64_t n, int32_t m, 
   // as many column chunks as the scratch holds (at most 8): 3 * chunks * n <= 3 * MAX_N
   int chunks = (int)std::min<int64_t>(8, MAG_NOALLOC_MAX_N / n);
   if (chunks < 1) chunks = 1;
-  if (launch_residual_mf(points, n, m, t, w, b, r_out, scratch, chunks, n, st, s) != cudaSuccess) {
+  if (launch_residual_mf(points, n, m, t, w, b, r_out, scratch, chunks, n, st, s, MAT_EXP, 0.0) != cudaSuccess) {
     cudaGetLastError();
     return MAG_ECUDA;
   }

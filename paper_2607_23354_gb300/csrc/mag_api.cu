@@ -107,6 +107,7 @@ struct mag_ctx {
   TaskTable* tasks = nullptr;        // the table of the factor in progress
   cudaStream_t side = nullptr;       // panel stream of the look-ahead factor
   int kind = MAT_EXP;                // matrix the solve path generates (MatKind)
+  double kind_c = 0.0;               // its parameter c (MAT_DEFLATED)
   cudaEvent_t ev_la[3] = {nullptr, nullptr, nullptr};  // start, panel done, trailing done
   // out-of-core factor (slabs); empty when the solve runs in core
   std::vector<Slab> slabs;
@@ -712,6 +713,9 @@ int plan_out_of_core(mag_ctx* ctx, int64_t n, int prec, int64_t* pool_tiles) {
   ctx->slabs.clear();
   const mag_options& o = ctx->opt;
   if (o.out_of_core < 0) return MAG_OK;
+  // the slab generator forms Z = exp[-t d]; the scale-zero and the deflated
+  // systems are solved in core
+  if (ctx->kind != MAT_EXP) return MAG_OK;
   const bool fp16_kind = prec == MAG_PREC_AUTO || prec == MAG_PREC_FP16 || prec == MAG_PREC_FP16X3;
   if (!fp16_kind) {
     if (o.out_of_core > 0)
@@ -903,6 +907,7 @@ int mag_options_default(mag_options* opt) {
   opt->tplus_method = 0;
   opt->wait_timeout_ns = 10000000000ll;
   opt->out_of_core = 0;
+  opt->deflate = 0;
   opt->host_limit_bytes = 0.0;
   return MAG_OK;
 }
@@ -1056,6 +1061,7 @@ struct SolveResult {
   double probe_rho = 0, ms_probe = 0;
   int slabs = 0, host_slabs = 0;
   double host_bytes = 0, host_read_bytes = 0, ms_host_read = 0;
+  double deflation_c = 0;
 };
 
 float elapsed(mag_ctx* ctx, int a, int b) {
@@ -1082,21 +1088,24 @@ int generate(mag_ctx* ctx, const double* X, int32_t m, double t, bool f32, bool 
                      ctx->dist_m == m;
   if (reuse) {
     CU(launch_generate_from_dist(ctx->dist(), L.n, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr,
-                                 ctx->vd(V_ROWSUM), s, ctx->kind, tiny_arg));
+                                 ctx->vd(V_ROWSUM), s, ctx->kind, tiny_arg, ctx->kind_c));
   } else if (ctx->dist_active && L.dist) {
     CU(launch_generate_dist(X, L.n, m, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr, ctx->dist(),
-                            ctx->vd(V_ROWSUM), ctx->st(), s, ctx->kind, tiny_arg));
+                            ctx->vd(V_ROWSUM), ctx->st(), s, ctx->kind, tiny_arg, ctx->kind_c));
   } else {
     CU(launch_generate(X, L.n, m, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr,
-                       ctx->vd(V_ROWSUM), ctx->st(), s, ctx->kind, tiny_arg));
+                       ctx->vd(V_ROWSUM), ctx->st(), s, ctx->kind, tiny_arg, ctx->kind_c));
   }
   CU(launch_rowsum_max(ctx->vd(V_ROWSUM), L.n, ctx->st(), s));
   CU(cudaEventRecord(ctx->ev[1], s));
   TRY(read_status(ctx));
   R->ms_gen += elapsed(ctx, 0, 1);
+  // the Gershgorin bound 1 - max off-diagonal row sum holds for the kinds
+  // with a unit diagonal
+  const bool unit_diag = ctx->kind != MAT_DEFLATED;
   if (reuse) {
     R->dmin = ctx->dist_dmin;
-    R->gersh = 1.0 - bits_to_double(ctx->h_st->off_max_bits);
+    R->gersh = unit_diag ? 1.0 - bits_to_double(ctx->h_st->off_max_bits) : -INFINITY;
     return MAG_OK;
   }
   const int fl = ctx->h_st->flags;
@@ -1104,7 +1113,7 @@ int generate(mag_ctx* ctx, const double* X, int32_t m, double t, bool f32, bool 
   const double d2 = bits_to_double(ctx->h_st->min_d2_bits);
   R->dmin = std::sqrt(d2);
   if ((fl & ST_DUPLICATE) || !(d2 > 0.0)) return fail(ctx, MAG_EDUPLICATE, "two points coincide (min d = 0)");
-  R->gersh = 1.0 - bits_to_double(ctx->h_st->off_max_bits);
+  R->gersh = unit_diag ? 1.0 - bits_to_double(ctx->h_st->off_max_bits) : -INFINITY;
   if (ctx->dist_active && L.dist) {
     ctx->dist_valid = true;
     ctx->dist_pts = X;
@@ -1237,7 +1246,8 @@ int residual(mag_ctx* ctx, const double* X, int32_t m, double t, const double* w
     CU(launch_residual_stored(ctx->zd(), L.n, L.N, w, b, ctx->vd(V_ROWSUM), r, ctx->spart(), L.np,
                               ctx->st(), s));
   else
-    CU(launch_residual_sym(X, L.n, m, t, w, b, r, ctx->spart(), ctx->vd(V_ROWSUM), L.np, ctx->st(), s, ctx->kind));
+    CU(launch_residual_sym(X, L.n, m, t, w, b, r, ctx->spart(), ctx->vd(V_ROWSUM), L.np, ctx->st(), s, ctx->kind,
+                           ctx->kind_c));
   CU(cudaEventRecord(ctx->ev[1], s));
   TRY(read_status(ctx));
   if (ctx->h_st->flags & ST_TIMEOUT)
@@ -1349,7 +1359,8 @@ int probe_fp16(mag_ctx* ctx, const double* X, int32_t m, double t, bool stored, 
       CU(launch_residual_stored(ctx->zd(), ns, K, x, nullptr, ctx->vd(V_ROWSUM), r, ctx->spart(), ns, ctx->st(),
                                 s));
     else
-      CU(launch_residual_mf(X, ns, m, t, x, nullptr, r, ctx->part(), chunks, ns, ctx->st(), s, ctx->kind));
+      CU(launch_residual_mf(X, ns, m, t, x, nullptr, r, ctx->part(), chunks, ns, ctx->st(), s, ctx->kind,
+                            ctx->kind_c));
     TRY(read_status(ctx));
     *rn = bits_to_double(ctx->h_st->r_max_bits);
     *floor = 32.0 * 0x1p-52 * bits_to_double(ctx->h_st->z_max_bits) * bits_to_double(ctx->h_st->w_max_bits);
@@ -1416,7 +1427,7 @@ int gmres_ir(mag_ctx* ctx, int prec, const double* X, int32_t m, double t, const
       CU(launch_residual_stored(ctx->zd(), n, L.N, v, zeros, ctx->vd(V_ROWSUM), tmp, ctx->spart(), np, ctx->st(), s));
     else
       CU(launch_residual_sym(X, n, m, t, v, zeros, tmp, ctx->spart(), ctx->vd(V_ROWSUM), np, ctx->st(), s,
-                             ctx->kind));
+                             ctx->kind, ctx->kind_c));
     TRY(correction(ctx, prec, tmp, out, /*init=*/true, R));
     CU(launch_scale(out, -1.0, out, n, s));
     return MAG_OK;
@@ -1825,6 +1836,50 @@ void fill_info(mag_ctx* ctx, const SolveResult& R, int64_t n, mag_info* info) {
   info->host_bytes = R.host_bytes;
   info->host_read_bytes = R.host_read_bytes;
   info->ms_host_read = R.ms_host_read;
+  info->deflation_c = R.deflation_c;
+}
+
+// The small-t end (Z close to 1 1^T, kappa(Z) growing like 1/t): with
+// alpha = 1 - c t, Z = t A + alpha 1 1^T where A = (Z - alpha 1 1^T) / t has
+// entries c + expm1(-t d_jk) / t and diagonal c (no cancellation: expm1).  A
+// is c 1 1^T - D_t with D_t = (1 1^T - Z) / t conditionally negative definite
+// (Z is positive definite), so A is positive definite for c large enough --
+// the t > 0 form of the scale-zero system (App. C) -- and its condition
+// number stays bounded as t -> 0, where that of Z grows like 1/t.  The solver
+// refines u = A^{-1} 1 to the tolerance on A's system, and by Sherman-Morrison
+// w = Z^{-1} 1 = u / (t + alpha 1^T u).  Then 1 - Z w = t (1 - A u) / (t +
+// alpha 1^T u) exactly, so Z's relative residual is A's times t ||A|| / ||Z||
+// (||Z||inf = t ||A||inf + alpha n): below the tolerance as well.  c starts at
+// 4 max_j ||x_j - x_0|| >= 2 max d and doubles on a non-positive pivot while
+// c t <= 1 (alpha >= 0: no cancellation in t + alpha 1^T u).
+// Returns MAG_ENOTPD when no c up to 1/t gave a positive definite A (the
+// caller then solves Z directly).
+int solve_deflated(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, double* w, double c,
+                   SolveResult* R) {
+  cudaStream_t s = ctx->stream;
+  int st = MAG_ENOTPD;
+  for (; c * t <= 1.0 && st == MAG_ENOTPD; c *= 2.0) {
+    SolveResult Ra;
+    ctx->kind = MAT_DEFLATED;
+    ctx->kind_c = c;
+    st = solve_impl(ctx, X, n, m, t, nullptr, w, &Ra);
+    ctx->kind = MAT_EXP;
+    ctx->kind_c = 0.0;
+    *R = Ra;
+    if (st != MAG_OK && st != MAG_ENOCONV) continue;
+    CU(launch_reduce_w(w, n, ctx->st(), s));  // 1^T u (compensated)
+    TRY(read_status(ctx));
+    const double alpha = 1.0 - c * t, su = ctx->h_st->mag, den = t + alpha * su;
+    if (!(den > 0.0) || !std::isfinite(den)) return fail(ctx, MAG_ENOCONV, "deflated solve: t + alpha 1^T u = %g", den);
+    CU(launch_scale(w, 1.0 / den, w, n, s));
+    const double za = R->znorm;
+    R->znorm = t * za + alpha * (double)n;
+    R->rel = R->rel * t * za / R->znorm;
+    R->wnorm = R->wnorm / den;
+    R->deflation_c = c;
+    return st;
+  }
+  return st;
 }
 
 }  // namespace
@@ -1881,7 +1936,29 @@ int mag_solve(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
   cudaEventRecord(t0, ctx->stream);
-  int st = solve_impl(ctx, points, n, m, t, nullptr, w, &R);
+  int st = MAG_ENOTPD;
+  bool deflated = false;
+  if (ctx->kind == MAT_EXP && ctx->opt.deflate >= 0) {
+    // the deflated form when t max d <= 1/4: every entry of Z at least
+    // e^-1/4, kappa(Z) dominated by the rank-one 1 1^T part
+    if (!ctx->ws || ctx->lay.np < ((n + TILE - 1) / TILE) * TILE) st = ensure_workspace(ctx, n, false, false);
+    if (st == MAG_ENOTPD || st == MAG_OK) st = reset_status(ctx);
+    if (st == MAG_OK) {
+      cudaError_t e = launch_far_from_first(points, n, m, ctx->st(), ctx->stream);
+      st = e == cudaSuccess ? read_status(ctx) : fail(ctx, MAG_ECUDA, "far: %s", cudaGetErrorString(e));
+    }
+    if (st != MAG_OK) {
+      cudaEventDestroy(t0);
+      cudaEventDestroy(t1);
+      return st;
+    }
+    const double far = std::sqrt(bits_to_double(ctx->h_st->far_d2_bits));
+    if (std::isfinite(far) && far > 0.0 && (ctx->opt.deflate > 0 || t * far <= 0.125)) {
+      st = solve_deflated(ctx, points, n, m, t, w, 4.0 * far, &R);
+      deflated = st != MAG_ENOTPD;
+    }
+  }
+  if (!deflated) st = solve_impl(ctx, points, n, m, t, nullptr, w, &R);
   bool timed = false;
   if (st == MAG_OK || st == MAG_ENOCONV) {
     cudaStream_t s = ctx->stream;

@@ -98,18 +98,20 @@ struct DevStatus {
 // Z_jk = 1 - t d_jk (the scale-zero system with t = 1/c).  With tiny_arg
 // finite, MAT_EXP entries with t d_jk > tiny_arg are evaluated in FP32
 // (exp_neg_tiny); +inf keeps every entry FP64-exact.
-enum MatKind : int { MAT_EXP = 0, MAT_SHIFTED_DIST = 1 };
+// MAT_DEFLATED: Z_jk = c + expm1(-t d_jk) / t, diagonal c (the small-t
+// system (Z - (1 - c t) 1 1^T) / t with its rank-one part deflated; kc = c).
+enum MatKind : int { MAT_EXP = 0, MAT_SHIFTED_DIST = 1, MAT_DEFLATED = 2 };
 // Entries exp(-t d) with t d above this (below e^-46 < 2^-66) are evaluated in
 // FP32 on the solve path: their error cannot reach one FP64 rounding of a row
 // sum that holds the unit diagonal (exp_neg_tiny in mag_math.cuh).
 constexpr double kTinyArg = 46.0;
 cudaError_t launch_generate(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
                             double* Zd, double* rowsum, DevStatus* st, cudaStream_t s, int kind = MAT_EXP,
-                            double tiny_arg = INFINITY);
+                            double tiny_arg = INFINITY, double kc = 0.0);
 // The same, also writing the FP64 distances d_jk into Dd (packed tiles like Z).
 cudaError_t launch_generate_dist(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
                                  double* Zd, double* Dd, double* rowsum, DevStatus* st, cudaStream_t s,
-                                 int kind = MAT_EXP, double tiny_arg = INFINITY);
+                                 int kind = MAT_EXP, double tiny_arg = INFINITY, double kc = 0.0);
 // FP32 tiles of one slab for the out-of-core factor: global tile columns
 // [t0, t0 + W) of rows [t0, N), in the slab layout (tile_index with column
 // cap W, tile (0, 0) = global (t0, t0)); no row sums; min d^2 and flags as
@@ -119,7 +121,7 @@ cudaError_t launch_generate_slab(const double* X, int64_t n, int m, double t, in
 // Z from stored FP64 distance tiles: Zf (may be null) and Zd (may be null), row sums.
 cudaError_t launch_generate_from_dist(const double* Dd, int64_t n, double t, int64_t N, float* Zf, double* Zd,
                                      double* rowsum, cudaStream_t s, int kind = MAT_EXP,
-                                     double tiny_arg = INFINITY);
+                                     double tiny_arg = INFINITY, double kc = 0.0);
 // max_j ||x_j - x_0||^2 into st->far_d2_bits (st->far_d2_bits must start at 0).
 cudaError_t launch_far_from_first(const double* X, int64_t n, int m, DevStatus* st, cudaStream_t s);
 // min_{j != k} d^2 over all pairs (FP64) into st->min_d2_bits.
@@ -260,13 +262,13 @@ cudaError_t launch_rect_gemv_t(const float* A, int64_t R, int64_t S, const float
 // part: scratch of 3 * chunks * np doubles.  Norms go to st (r_max, z_max, w_max).
 cudaError_t launch_residual_mf(const double* X, int64_t n, int m, double t, const double* w,
                                const double* b, double* r, double* part, int chunks, int64_t np,
-                               DevStatus* st, cudaStream_t s, int kind = MAT_EXP);
+                               DevStatus* st, cudaStream_t s, int kind = MAT_EXP, double kc = 0.0);
 // Matrix free over the lower triangle (each Z entry computed once, used for
 // its row and its column): P is scratch of N * N * 128 doubles, rowsum of n
 // doubles (overwritten with the row sums of Z).  Same outputs as above.
 cudaError_t launch_residual_sym(const double* X, int64_t n, int m, double t, const double* w, const double* b,
                                 double* r, double* P, double* rowsum, int64_t np, DevStatus* st, cudaStream_t s,
-                                int kind = MAT_EXP);
+                                int kind = MAT_EXP, double kc = 0.0);
 // Stored: P is scratch of N * N * 128 doubles (one partial per row block,
 // tile and row); rowsum holds the row sums of Z from the generator.
 cudaError_t launch_residual_stored(const double* Zd, int64_t n, int64_t N, const double* w,

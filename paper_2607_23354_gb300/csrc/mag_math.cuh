@@ -51,6 +51,39 @@ __device__ __forceinline__ double exp_neg(double x, const double* tab) {
   return __hiloint2double(__double2hiint(s) + k * (1 << 20), __double2loint(s));
 }
 
+// exp(x) - 1 for x <= 0 without the cancellation of exp(x) - 1 near 0: for
+// x >= -1/4 the Taylor series x + x^2/2! + ... + x^14/14! in Horner form
+// (the first omitted term is below 2^-63 |x|), else exp_neg(x) - 1, whose
+// result lies in [-1, -0.22] so the subtraction costs at most two units in
+// the last place.
+__device__ __forceinline__ double expm1_neg(double x, const double* tab) {
+  if (x < -0.25) return exp_neg(x, tab) - 1.0;
+  double p = 1.0 / 87178291200.0;  // 1/14!
+  p = fma(p, x, 1.0 / 6227020800.0);
+  p = fma(p, x, 1.0 / 479001600.0);
+  p = fma(p, x, 1.0 / 39916800.0);
+  p = fma(p, x, 1.0 / 3628800.0);
+  p = fma(p, x, 1.0 / 362880.0);
+  p = fma(p, x, 1.0 / 40320.0);
+  p = fma(p, x, 1.0 / 5040.0);
+  p = fma(p, x, 1.0 / 720.0);
+  p = fma(p, x, 1.0 / 120.0);
+  p = fma(p, x, 1.0 / 24.0);
+  p = fma(p, x, 1.0 / 6.0);
+  p = fma(p, x, 0.5);
+  return fma(p * x, x, x);
+}
+
+// Off-diagonal entry of the matrix a solve factors, from the FP64 distance
+// dd (kind: MatKind of mag_internal.cuh): exp(-t d) (Eq. weighting);
+// 1 - t d (the scale-zero system, t = 1/c); c + expm1(-t d) / t (the
+// deflated small-t system, tinv = 1/t, kc = c).  The diagonal is 1, 1 and c.
+__device__ __forceinline__ double mat_entry(int kind, double t, double tinv, double kc, double dd, const double* tab) {
+  if (kind == 1) return fma(-t, dd, 1.0);
+  if (kind == 2) return fma(expm1_neg(-t * dd, tab), tinv, kc);
+  return exp_neg(-t * dd, tab);
+}
+
 // exp(-a) for a > kTinyArg = 46 (mag_internal.cuh; results below
 // e^-46 < 2^-66) in FP32: the
 // CUDA expf of the rounded argument, relative error below 6e-6 (argument

@@ -646,3 +646,90 @@ def test_matrix_free_refinement_over_the_lower_triangle(ctx, n, m, t):
     # its ||Z||inf is the oracle's
     _, rs = oracle.residual_rows(X, t, w_ref)
     assert info["z_norm_inf"] == pytest.approx(rs.max(), rel=1e-6)
+
+
+# ------------------------------------------------- small t: the deflated system
+# Near t = 0, Z approaches 1 1^T and kappa(Z) grows like 1/t; mag_solve then
+# solves the deflated system A u = 1 (A = (Z - (1 - c t) 1 1^T) / t) and maps u
+# back to w = Z^{-1} 1 by Sherman-Morrison.  Closed forms fix w exactly.
+
+def _line(n, seed):
+    rng = np.random.default_rng(seed)
+    gaps = rng.uniform(0.05, 2.0, size=n - 1)
+    s = np.concatenate([[0.0], np.cumsum(gaps)])
+    u = rng.standard_normal(3)
+    u /= np.linalg.norm(u)
+    return s[:, None] * u[None, :], gaps
+
+
+@pytest.mark.parametrize("t", [1e-2, 1e-3, 1e-5])
+@pytest.mark.parametrize("deflate", [0, 1])
+def test_deflated_small_t_closed_forms(ctx, t, deflate):
+    ctx.set_options(M.Options(deflate=deflate))
+    try:
+        # two points: w = 1 / (1 + e^{-t d})
+        X2 = np.array([[0.0, 0.0, 0.0], [3.0, 4.0, 0.0]])
+        w, mag, info = ctx.solve(_dev(X2), t)
+        assert info["deflation_c"] > 0
+        np.testing.assert_allclose(w.cpu().numpy(), 1 / (1 + math.exp(-5 * t)), rtol=1e-13)
+        # points on a line: the tanh formula (w_1 = (1 + tanh(t g_1/2))/2, ...)
+        X, gaps = _line(300, 7)
+        w, mag, info = ctx.solve(_dev(X), t)
+        far = gaps.sum()  # max_j ||x_j - x_0||
+        # deflated when t max d is small: t far <= 1/8 (AUTO), 4 far t <= 1 (forced)
+        assert (info["deflation_c"] > 0) == (t * far <= (0.125 if deflate == 0 else 0.25))
+        th = np.tanh(t * gaps / 2)
+        exact = np.concatenate([[(1 + th[0]) / 2], (th[:-1] + th[1:]) / 2, [(1 + th[-1]) / 2]])
+        np.testing.assert_allclose(w.cpu().numpy(), exact, rtol=1e-11, atol=1e-13 * np.abs(exact).max())
+        assert mag == pytest.approx(1 + np.sum(th), rel=1e-12)
+        assert info["rel_residual"] <= 1e-14
+        assert oracle.relative_residual(X, t, w.cpu().numpy()) <= 1e-14
+        # centred regular 12-gon (radius 1): w = (a, b, ..., b)
+        k = 12
+        ang = 2 * np.pi * np.arange(k) / k
+        Xk = np.vstack([[0.0, 0.0], np.stack([np.cos(ang), np.sin(ang)], axis=1)])
+        w, mag, info = ctx.solve(_dev(Xk), t)
+        S = np.sum(np.exp(-2 * t * np.sin(np.pi * np.arange(k) / k)))
+        den = S - k * math.exp(-2 * t)
+        wk = w.cpu().numpy()
+        assert wk[0] == pytest.approx((S - k * math.exp(-t)) / den, rel=1e-9)
+        np.testing.assert_allclose(wk[1:], (1 - math.exp(-t)) / den, rtol=1e-9)
+    finally:
+        ctx.set_options(M.Options())
+
+
+@pytest.mark.parametrize("n,m,cov", [(1000, 3, "identity"), (3000, 3, "halving"), (2000, 10, "identity")])
+def test_deflated_small_t_against_oracle(ctx, n, m, cov):
+    # the paper's runtime workload at the bracket's lower end t = 1e-3: the
+    # deflated solve needs no FP64 factor; the oracle's FP64 residual of the
+    # GPU weighting and the weighting within kappa times the residuals
+    X = workloads.paper_runtime_cloud(n, m, cov, 0)
+    t = 1e-3
+    w, mag, info = ctx.solve(_dev(X), t)
+    assert info["deflation_c"] > 0 and info["fallback"] != 2
+    wg = w.cpu().numpy()
+    assert oracle.relative_residual(X, t, wg) <= 1e-14
+    w_ref, mag_ref, oi = oracle.weighting_lapack(X, t)
+    bound = max(1e-9, 10 * oi["kappa1_est"] * (1e-14 + oi["rel_residual"]))
+    assert np.abs(wg - w_ref).max() <= bound * np.abs(w_ref).max()
+    # the plain solve of Z (FP64 factor fallback) agrees within the same bound
+    ctx.set_options(M.Options(deflate=-1))
+    try:
+        w2, mag2, info2 = ctx.solve(_dev(X), t)
+    finally:
+        ctx.set_options(M.Options())
+    assert info2["deflation_c"] == 0
+    assert np.abs(w2.cpu().numpy() - wg).max() <= bound * np.abs(wg).max()
+
+
+def test_deflated_solve_tends_to_scale_zero(ctx):
+    # w(t) -> d^{-1} 1 / 1^T d^{-1} 1 with O(t) error (App. C)
+    X = np.random.default_rng(91).standard_normal((500, 3))
+    w0, _, _ = ctx.scale_zero(_dev(X))
+    w0 = w0.cpu().numpy()
+    errs = []
+    for t in (1e-3, 1e-4):
+        w, _, info = ctx.solve(_dev(X), t)
+        assert info["deflation_c"] > 0
+        errs.append(np.abs(w.cpu().numpy() - w0).max() / np.abs(w0).max())
+    assert errs[1] < errs[0] / 5
