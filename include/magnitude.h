@@ -143,12 +143,14 @@ typedef struct mag_options {
   int32_t deflate;        /* mag_solve at the small-t end, where Z nears the
                              all-ones matrix: 0 (default) when t max d <= 1/4
                              (judged from max_j ||x_j - x_0||), solve instead
-                             A u = 1 with A = (Z - (1 - c t) 1 1^T) / t
-                             (entries c + expm1(-t d_jk) / t, diagonal c),
-                             positive definite and well conditioned for c
-                             large enough, and return w = u / (t + (1 - c t)
-                             1^T u) = Z^{-1} 1 (Sherman-Morrison); 1: always;
-                             -1: never.  Reported in mag_info.deflation_c.  */
+                             A u = 1 with A = (Z - (1 - c t) 1 1^T) / (c t)
+                             (entries 1 + expm1(-t d_jk) / (c t), unit
+                             diagonal), positive definite and well
+                             conditioned for c large enough, and return
+                             w = u / (c t + (1 - c t) 1^T u) = Z^{-1} 1
+                             (Sherman-Morrison); 1: whenever c t <= 1 allows
+                             it; -1: never.  Reported in
+                             mag_info.deflation_c.                          */
   double host_limit_bytes;/* pinned host memory the out-of-core factor may
                              take (0: half of the host's physical memory);
                              more gives MAG_ENOMEM                          */

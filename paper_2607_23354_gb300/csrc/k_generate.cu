@@ -92,8 +92,6 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
   unsigned long long mind2b = 0x7ff0000000000000ull;  // +inf
   int flags = 0;
   const float tf = (float)t;
-  const double tinv = 1.0 / t;
-  const double diag = kind == MAT_DEFLATED ? kc : 1.0;
   // d > tiny_arg / t on the bit patterns (d >= 0): the FP64 pipe stays on
   // the distances and the exponential
   const unsigned long long tiny_bits = (unsigned long long)__double_as_longlong(tiny_arg / t);
@@ -110,7 +108,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
       double zd = 0.0, dd = 0.0;
       float zf = 0.0f;
       if (gr >= n || gc >= n || gr == gc) {
-        zd = (gr == gc) ? (gr < n ? diag : 1.0) : 0.0;
+        zd = (gr == gc) ? 1.0 : 0.0;
         zf = (float)zd;
       } else {
         // v >= 0 or NaN: the checks and the minimum on the bit pattern (integer
@@ -124,12 +122,12 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
           zf = exp_neg_tiny(t * dd);
           zd = (double)zf;
         } else {
-          if (WD) zd = mat_entry(kind, t, tinv, kc, dd, exptab);
+          if (WD) zd = mat_entry(kind, t, kc, dd, exptab);
           if (WF)
             zf = WD ? (kind == MAT_DEFLATED ? __double2float_rn(zd) : f64_to_f32_nonneg(zd))
                     : (kind == MAT_EXP ? expf(-tf * sqrtf((float)v))
                                        : (kind == MAT_SHIFTED_DIST ? 1.0f - tf * sqrtf((float)v)
-                                                                   : (float)kc + expm1f(-tf * sqrtf((float)v)) / tf));
+                                                                   : fmaf((float)kc, expm1f(-tf * sqrtf((float)v)), 1.0f)));
         }
       }
       if (WF) Zf[tile_off + (int64_t)r * TILE + c] = zf;
@@ -195,8 +193,6 @@ __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __rest
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t off = tri_index(I, J) * TILE_ELEMS;
   const float tf = (float)t;
-  const double tinv = 1.0 / t;
-  const double diag = kind == MAT_DEFLATED ? kc : 1.0;
   const unsigned long long tiny_bits = (unsigned long long)__double_as_longlong(tiny_arg / t);
   // row/column partial sums in FP32 (a norm; the FP64 pipe is the limit)
   float cs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -212,20 +208,20 @@ __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __rest
       double zd;
       float zf;
       if (gr >= n || gc >= n || gr == gc) {
-        zd = (gr == gc) ? (gr < n ? diag : 1.0) : 0.0;
+        zd = (gr == gc) ? 1.0 : 0.0;
         zf = (float)zd;
-        if (gr == gc && gr < n) rs += zf;  // the diagonal counts in its row sum
+        if (gr == gc && gr < n) rs += 1.0f;  // the diagonal counts in its row sum
       } else {
         const double d = Dd[e];
         if (WD && !kind && (unsigned long long)__double_as_longlong(d) > tiny_bits) {
           zf = exp_neg_tiny(t * d);
           zd = (double)zf;
         } else {
-          zd = WD ? mat_entry(kind, t, tinv, kc, d, exptab) : 0.0;
+          zd = WD ? mat_entry(kind, t, kc, d, exptab) : 0.0;
           zf = WD ? (kind == MAT_DEFLATED ? __double2float_rn(zd) : f64_to_f32_nonneg(zd))
                   : (kind == MAT_EXP ? expf(-tf * (float)d)
                                      : (kind == MAT_SHIFTED_DIST ? 1.0f - tf * (float)d
-                                                                 : (float)kc + expm1f(-tf * (float)d) / tf));
+                                                                 : fmaf((float)kc, expm1f(-tf * (float)d), 1.0f)));
         }
         rs += zf;
         cs[q] += zf;

@@ -41,7 +41,6 @@ __global__ void __launch_bounds__(RES_THREADS) k_resid_mf(const double* __restri
   __shared__ double exptab[2 * EXPT_SIZE];
   load_exp_table(exptab);
   const int64_t j = (int64_t)blockIdx.x * RES_THREADS + threadIdx.x;
-  const double tinv = 1.0 / t;
   const int64_t ntiles = (n + ct - 1) / ct;
   const int64_t per = (ntiles + chunks - 1) / chunks;
   const int64_t c0 = blockIdx.y * per * ct;
@@ -78,7 +77,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_resid_mf(const double* __restri
         }
       }
       const double dd = sqrt_pos(d2);
-      const double z = mat_entry(kind, t, tinv, kc, dd, exptab);  // dd = 0 (k = j): the diagonal
+      const double z = mat_entry(kind, t, kc, dd, exptab);  // dd = 0 (k = j): the unit diagonal
       zs += z;
       // Kahan step for s += z * w_k
       const double y = fma(z, wc[q], -c);
@@ -246,7 +245,6 @@ __global__ void __launch_bounds__(SYM_THREADS, 1)
   __syncthreads();
   double cs[4] = {0.0, 0.0, 0.0, 0.0};
   float zc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  const double tinv = 1.0 / t, diag = kind == MAT_DEFLATED ? kc : 1.0;
   // rows of block I: each row's 4 products per lane, then a lane tree -> P[I][J]
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -261,10 +259,10 @@ __global__ void __launch_bounds__(SYM_THREADS, 1)
       double z = 0.0;
       if (gr < n && gc < n) {
         if (gr == gc) {
-          z = diag;
+          z = 1.0;
         } else {
           const double dd = sqrt_pos(d2[i][q]);
-          z = mat_entry(kind, t, tinv, kc, dd, exptab);
+          z = mat_entry(kind, t, kc, dd, exptab);
         }
       }
       v = fma(z, s_wc[lane + 32 * q], v);

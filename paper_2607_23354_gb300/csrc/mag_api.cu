@@ -1100,12 +1100,9 @@ int generate(mag_ctx* ctx, const double* X, int32_t m, double t, bool f32, bool 
   CU(cudaEventRecord(ctx->ev[1], s));
   TRY(read_status(ctx));
   R->ms_gen += elapsed(ctx, 0, 1);
-  // the Gershgorin bound 1 - max off-diagonal row sum holds for the kinds
-  // with a unit diagonal
-  const bool unit_diag = ctx->kind != MAT_DEFLATED;
   if (reuse) {
     R->dmin = ctx->dist_dmin;
-    R->gersh = unit_diag ? 1.0 - bits_to_double(ctx->h_st->off_max_bits) : -INFINITY;
+    R->gersh = 1.0 - bits_to_double(ctx->h_st->off_max_bits);
     return MAG_OK;
   }
   const int fl = ctx->h_st->flags;
@@ -1113,7 +1110,7 @@ int generate(mag_ctx* ctx, const double* X, int32_t m, double t, bool f32, bool 
   const double d2 = bits_to_double(ctx->h_st->min_d2_bits);
   R->dmin = std::sqrt(d2);
   if ((fl & ST_DUPLICATE) || !(d2 > 0.0)) return fail(ctx, MAG_EDUPLICATE, "two points coincide (min d = 0)");
-  R->gersh = unit_diag ? 1.0 - bits_to_double(ctx->h_st->off_max_bits) : -INFINITY;
+  R->gersh = 1.0 - bits_to_double(ctx->h_st->off_max_bits);
   if (ctx->dist_active && L.dist) {
     ctx->dist_valid = true;
     ctx->dist_pts = X;
@@ -1840,28 +1837,31 @@ void fill_info(mag_ctx* ctx, const SolveResult& R, int64_t n, mag_info* info) {
 }
 
 // The small-t end (Z close to 1 1^T, kappa(Z) growing like 1/t): with
-// alpha = 1 - c t, Z = t A + alpha 1 1^T where A = (Z - alpha 1 1^T) / t has
-// entries c + expm1(-t d_jk) / t and diagonal c (no cancellation: expm1).  A
-// is c 1 1^T - D_t with D_t = (1 1^T - Z) / t conditionally negative definite
-// (Z is positive definite), so A is positive definite for c large enough --
-// the t > 0 form of the scale-zero system (App. C) -- and its condition
-// number stays bounded as t -> 0, where that of Z grows like 1/t.  The solver
-// refines u = A^{-1} 1 to the tolerance on A's system, and by Sherman-Morrison
-// w = Z^{-1} 1 = u / (t + alpha 1^T u).  Then 1 - Z w = t (1 - A u) / (t +
-// alpha 1^T u) exactly, so Z's relative residual is A's times t ||A|| / ||Z||
-// (||Z||inf = t ||A||inf + alpha n): below the tolerance as well.  c starts at
+// alpha = 1 - c t, Z = c t A + alpha 1 1^T where A = (Z - alpha 1 1^T) / (c t)
+// has entries 1 + expm1(-t d_jk) / (c t) and a unit diagonal (no
+// cancellation: expm1).  A = 1 1^T - D_t / c with D_t = (1 1^T - Z) / t
+// conditionally negative definite (Z is positive definite), so A is positive
+// definite for c large enough -- the t > 0 form of the scale-zero system M of
+// App. C -- and has Z's structure (unit diagonal, entries in [1/2, 1] for
+// c >= 2 max d), with a condition number that stays bounded as t -> 0, where
+// that of Z grows like 1/t.  The solver refines u = A^{-1} 1 to the tolerance
+// on A's system, and by Sherman-Morrison w = Z^{-1} 1 = u / (c t + alpha
+// 1^T u).  Then 1 - Z w = c t (1 - A u) / (c t + alpha 1^T u) exactly, so
+// Z's relative residual is A's times c t ||A|| / ||Z|| (||Z||inf = c t
+// ||A||inf + alpha n): below the tolerance as well.  c starts at
 // 4 max_j ||x_j - x_0|| >= 2 max d and doubles on a non-positive pivot while
-// c t <= 1 (alpha >= 0: no cancellation in t + alpha 1^T u).
-// Returns MAG_ENOTPD when no c up to 1/t gave a positive definite A (the
-// caller then solves Z directly).
+// c t <= 1 (alpha >= 0: no cancellation in c t + alpha 1^T u).  Returns
+// MAG_ENOTPD when no such c gave a positive definite A (the caller then
+// solves Z directly).
 int solve_deflated(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, double* w, double c,
                    SolveResult* R) {
   cudaStream_t s = ctx->stream;
   int st = MAG_ENOTPD;
   for (; c * t <= 1.0 && st == MAG_ENOTPD; c *= 2.0) {
     SolveResult Ra;
+    const double ct = c * t;
     ctx->kind = MAT_DEFLATED;
-    ctx->kind_c = c;
+    ctx->kind_c = 1.0 / ct;
     st = solve_impl(ctx, X, n, m, t, nullptr, w, &Ra);
     ctx->kind = MAT_EXP;
     ctx->kind_c = 0.0;
@@ -1869,12 +1869,12 @@ int solve_deflated(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t
     if (st != MAG_OK && st != MAG_ENOCONV) continue;
     CU(launch_reduce_w(w, n, ctx->st(), s));  // 1^T u (compensated)
     TRY(read_status(ctx));
-    const double alpha = 1.0 - c * t, su = ctx->h_st->mag, den = t + alpha * su;
-    if (!(den > 0.0) || !std::isfinite(den)) return fail(ctx, MAG_ENOCONV, "deflated solve: t + alpha 1^T u = %g", den);
+    const double alpha = 1.0 - ct, su = ctx->h_st->mag, den = ct + alpha * su;
+    if (!(den > 0.0) || !std::isfinite(den)) return fail(ctx, MAG_ENOCONV, "deflated solve: c t + alpha 1^T u = %g", den);
     CU(launch_scale(w, 1.0 / den, w, n, s));
     const double za = R->znorm;
-    R->znorm = t * za + alpha * (double)n;
-    R->rel = R->rel * t * za / R->znorm;
+    R->znorm = ct * za + alpha * (double)n;
+    R->rel = R->rel * ct * za / R->znorm;
     R->wnorm = R->wnorm / den;
     R->deflation_c = c;
     return st;

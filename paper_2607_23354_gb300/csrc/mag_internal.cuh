@@ -98,8 +98,9 @@ struct DevStatus {
 // Z_jk = 1 - t d_jk (the scale-zero system with t = 1/c).  With tiny_arg
 // finite, MAT_EXP entries with t d_jk > tiny_arg are evaluated in FP32
 // (exp_neg_tiny); +inf keeps every entry FP64-exact.
-// MAT_DEFLATED: Z_jk = c + expm1(-t d_jk) / t, diagonal c (the small-t
-// system (Z - (1 - c t) 1 1^T) / t with its rank-one part deflated; kc = c).
+// MAT_DEFLATED: Z_jk = 1 + expm1(-t d_jk) / (c t), unit diagonal (the
+// small-t system (Z - (1 - c t) 1 1^T) / (c t) with its rank-one part
+// deflated; kc = 1 / (c t)).
 enum MatKind : int { MAT_EXP = 0, MAT_SHIFTED_DIST = 1, MAT_DEFLATED = 2 };
 // Entries exp(-t d) with t d above this (below e^-46 < 2^-66) are evaluated in
 // FP32 on the solve path: their error cannot reach one FP64 rounding of a row

@@ -76,11 +76,11 @@ __device__ __forceinline__ double expm1_neg(double x, const double* tab) {
 
 // Off-diagonal entry of the matrix a solve factors, from the FP64 distance
 // dd (kind: MatKind of mag_internal.cuh): exp(-t d) (Eq. weighting);
-// 1 - t d (the scale-zero system, t = 1/c); c + expm1(-t d) / t (the
-// deflated small-t system, tinv = 1/t, kc = c).  The diagonal is 1, 1 and c.
-__device__ __forceinline__ double mat_entry(int kind, double t, double tinv, double kc, double dd, const double* tab) {
+// 1 - t d (the scale-zero system, t = 1/c); 1 + kc expm1(-t d) with
+// kc = 1/(c t) (the deflated small-t system).  The diagonal is 1 for all.
+__device__ __forceinline__ double mat_entry(int kind, double t, double kc, double dd, const double* tab) {
   if (kind == 1) return fma(-t, dd, 1.0);
-  if (kind == 2) return fma(expm1_neg(-t * dd, tab), tinv, kc);
+  if (kind == 2) return fma(expm1_neg(-t * dd, tab), kc, 1.0);
   return exp_neg(-t * dd, tab);
 }
 
