@@ -203,6 +203,11 @@ typedef struct mag_info {
                               rel_residual, z_norm_inf and w_norm_inf are then
                               those of Z w = 1, the refinement's counts those
                               of A u = 1                                       */
+  int32_t factor_reused;   /* mag_solve_rhs (mag_grad's adjoint solve) refined
+                              with the factor the last solve of the same points
+                              (pointer, size and contents) and t left in the
+                              context, without generating or factoring again */
+  int32_t reserved2;
 } mag_info;
 
 typedef struct mag_ctx mag_ctx;
@@ -271,7 +276,12 @@ int mag_solve_multi(mag_ctx* ctx, const double* points, int64_t n, int32_t m, co
                     double* W, double* mags, mag_info* infos);
 
 /* The same solve for a general right-hand side: Z x = b (b: device, n).  Used
- * for the adjoint solve lambda = Z^{-1} dL/dw of mag_grad. */
+ * for the adjoint solve lambda = Z^{-1} dL/dw of mag_grad.  When the last
+ * solve on this context (mag_solve, mag_solve_multi's last t, mag_solve_rhs)
+ * had the same points -- pointer, n, m and a checksum of the contents -- and
+ * the same t, its factor is still in the workspace and the call only refines
+ * with it (info.factor_reused = 1); it factors again if that refinement does
+ * not reach the tolerance. */
 int mag_solve_rhs(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t,
                   const double* b, double* x, mag_info* info);
 

@@ -68,7 +68,8 @@ class mag_info(ctypes.Structure):
                 ("probe_rho", ctypes.c_double), ("ms_probe", ctypes.c_double), ("t", ctypes.c_double),
                 ("slabs", ctypes.c_int32), ("host_slabs", ctypes.c_int32), ("host_bytes", ctypes.c_double),
                 ("host_read_bytes", ctypes.c_double), ("ms_host_read", ctypes.c_double),
-                ("deflation_c", ctypes.c_double)]
+                ("deflation_c", ctypes.c_double), ("factor_reused", ctypes.c_int32),
+                ("reserved2", ctypes.c_int32)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}

@@ -624,6 +624,21 @@ __global__ void __launch_bounds__(1024) k_minmax_f64(const double* __restrict__ 
   }
 }
 
+// Checksum: sum over i of a 64-bit mix (splitmix64 finaliser) of the bits of
+// v[i] and i, wrapping; one atomic per warp.
+__global__ void k_hash_f64(const double* __restrict__ v, int64_t count, unsigned long long* out) {
+  unsigned long long acc = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long z = (unsigned long long)__double_as_longlong(v[i]) + 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    acc += z ^ (z >> 31);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
 // GMRES helpers (FP64): out[i] = <V_i, w> for i < k (V: k rows of length ld),
 // one CTA per i; and w -= sum_i h[i] V_i; and x = s * w.
 __global__ void __launch_bounds__(256) k_mdot(const double* __restrict__ V, int64_t ld, int k,
@@ -828,6 +843,14 @@ cudaError_t launch_grad(const double* X, int64_t n, int m, double t, const doubl
 
 cudaError_t launch_sum_f64(const double* v, int64_t n, double* out, cudaStream_t s) {
   k_sum_f64<<<1, 1024, 0, s>>>(v, n, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hash(const double* v, int64_t count, unsigned long long* out, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  int blocks = (int)std::min<int64_t>((count + 255) / 256, 1024);
+  k_hash_f64<<<blocks, 256, 0, s>>>(v, count, out);
   note_launch();
   return cudaGetLastError();
 }

@@ -109,6 +109,17 @@ struct mag_ctx {
   int kind = MAT_EXP;                // matrix the solve path generates (MatKind)
   double kind_c = 0.0;               // its parameter c (MAT_DEFLATED)
   cudaEvent_t ev_la[3] = {nullptr, nullptr, nullptr};  // start, panel done, trailing done
+  // the factor left in the workspace by the last in-core solve of Z =
+  // exp[-t d], reusable by a later solve with the same points and t (the
+  // adjoint solve of mag_grad): key and how to refine with it
+  bool fac_valid = false;
+  const double* fac_pts = nullptr;
+  int64_t fac_n = 0;
+  int32_t fac_m = 0;
+  double fac_t = 0.0;
+  unsigned long long fac_hash = 0;
+  int fac_prec = 0;
+  bool fac_stored = false;
   // out-of-core factor (slabs); empty when the solve runs in core
   std::vector<Slab> slabs;
   bool ooc = false;                  // the current solve factors out of core
@@ -254,6 +265,7 @@ int ensure_workspace(mag_ctx* ctx, int64_t n, bool f32, bool f64, int64_t zf_til
       ctx->ws_bytes = 0;
     }
     ctx->dist_valid = false;  // any stored distances are gone with the old buffer
+    ctx->fac_valid = false;   // and the factor
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, L.total);
     if (e != cudaSuccess) {
@@ -1062,6 +1074,7 @@ struct SolveResult {
   int slabs = 0, host_slabs = 0;
   double host_bytes = 0, host_read_bytes = 0, ms_host_read = 0;
   double deflation_c = 0;
+  int factor_reused = 0;
 };
 
 float elapsed(mag_ctx* ctx, int a, int b) {
@@ -1505,12 +1518,108 @@ int gmres_ir(mag_ctx* ctx, int prec, const double* X, int32_t m, double t, const
 // Full solve of Z x = b (b == null: ones) into x (device, n).  The iterate
 // lives in the workspace; x receives the best iterate (lowest relative
 // residual) over all precisions tried.
+// Checksum of the points (order-independent mix of their bits), the part of
+// the factor's key that sees changes made in place.
+int points_hash(mag_ctx* ctx, const double* X, int64_t n, int32_t m, unsigned long long* h) {
+  CU(cudaMemsetAsync(&ctx->st()->hash_bits, 0, sizeof(unsigned long long), ctx->stream));
+  CU(launch_hash(X, n * m, &ctx->st()->hash_bits, ctx->stream));
+  unsigned long long v = 0;
+  CU(cudaMemcpyAsync(&v, &ctx->st()->hash_bits, sizeof v, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  *h = v;
+  return MAG_OK;
+}
+
+int keep_factor(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, int prec, bool stored) {
+  unsigned long long h = 0;
+  TRY(points_hash(ctx, X, n, m, &h));
+  ctx->fac_valid = true;
+  ctx->fac_pts = X;
+  ctx->fac_n = n;
+  ctx->fac_m = m;
+  ctx->fac_t = t;
+  ctx->fac_hash = h;
+  ctx->fac_prec = prec;
+  ctx->fac_stored = stored && prec != MAG_PREC_FP64;
+  return MAG_OK;
+}
+
 // FP16 factor chosen on the probe's prediction rho: its extra refinement
 // steps over the split factor cost less than the factor time saved (n / 9500
 // steps with stored FP64 tiles, a quarter of that matrix free).
 bool probe_takes_fp16(double rho, double tol, int64_t n, bool stored) {
   const double saved = (double)n / 9500.0 * (stored ? 1.0 : 0.25);
   return rho < 1.0 && ir_steps(rho, tol) - ir_steps(rho * 0x1p-12, tol) <= saved;
+}
+
+// Refinement of Z x = b (b == null: ones) with the factor in the workspace
+// (precision prec): x0 = factor^{-1} b, then r = b - Z x in FP64 and
+// x += factor^{-1} r until the relative residual is below kStopMargin times
+// the tolerance; on stagnation (two steps each reducing it by less than 2x)
+// or after ir_max_iters steps, GMRES-IR with the same factor from the best
+// iterate, unless the probe chose FP16 (probed16: the caller replaces the
+// factor instead).  *overall keeps the lowest relative residual over calls,
+// with its iterate in x; *escalate reports a factor that did not get there.
+int refine(mag_ctx* ctx, int prec, const double* X, int64_t n, int32_t m, double t, const double* b, double* x,
+           bool stored, bool probed16, SolveResult* R, double* overall, bool* escalate) {
+  const mag_options& o = ctx->opt;
+  const Layout& L = ctx->lay;
+  cudaStream_t s = ctx->stream;
+  double* r = ctx->vd(V_R);
+  double* xw = ctx->vd(V_X);
+  double* best = ctx->vd(V_BEST);
+  double best_rel = INFINITY;
+  *escalate = false;
+  R->prec_used = prec;
+  // initial solve x0 = factor^{-1} b: the correction from x = 0 with r = b.
+  if (b)
+    CU(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  else
+    CU(launch_fill(r, n, 1.0, s));
+  CU(launch_fill(r + n, L.np - n, 0.0, s));
+  TRY(reset_norms(ctx));
+  CU(launch_absmax(r, n, ctx->st(), s));
+  TRY(correction(ctx, prec, r, xw, /*init=*/true, R));
+  double rel = INFINITY, prev = INFINITY;
+  int slow = 0;
+  for (int it = 0;; ++it) {
+    // The FP64 factor overwrites the FP64 tiles, so it refines matrix free.
+    TRY(residual(ctx, X, m, t, xw, b, r, &rel, stored && prec != MAG_PREC_FP64, R));
+    if (rel < best_rel) {
+      best_rel = rel;
+      CU(cudaMemcpyAsync(best, xw, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    if (rel <= kStopMargin * o.ir_tol) break;
+    if (it >= o.ir_max_iters || (rel > 0.5 * prev && ++slow >= 2)) {
+      *escalate = true;
+      break;
+    }
+    if (!(rel > 0.5 * prev)) slow = 0;
+    prev = rel;
+    TRY(correction(ctx, prec, r, xw, /*init=*/false, R));
+    R->ir_iters++;
+  }
+  if (best_rel < *overall) {
+    *overall = best_rel;
+    CU(cudaMemcpyAsync(x, best, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CU(cudaStreamSynchronize(s));
+  }
+  // a mispredicted FP16 choice goes to the split factor instead of GMRES-IR
+  const bool to_split = *escalate && probed16 && prec == MAG_PREC_FP16 && o.allow_fallback;
+  if (*escalate && !to_split && prec != MAG_PREC_FP64 && o.allow_fallback && o.gmres_max_iters > 0) {
+    // GMRES-IR with the same factor, from the best iterate so far
+    CU(cudaMemcpyAsync(xw, best, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    double grel = INFINITY;
+    R->fallback = 1;
+    TRY(gmres_ir(ctx, prec, X, m, t, b, xw, stored, R, &grel));
+    if (grel < *overall) {
+      *overall = grel;
+      CU(cudaMemcpyAsync(x, xw, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CU(cudaStreamSynchronize(s));
+    }
+    if (grel <= kStopMargin * o.ir_tol) *escalate = false;
+  }
+  return MAG_OK;
 }
 
 // The solve with the out-of-core factor (plan_out_of_core set the slabs; the
@@ -1664,6 +1773,7 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
                double* x, SolveResult* R) {
   const mag_options& o = ctx->opt;
   int prec = o.precision;
+  ctx->fac_valid = false;  // the workspace's tiles are about to be rewritten
   {
     int64_t pool_tiles = 0;
     TRY(plan_out_of_core(ctx, n, prec, &pool_tiles));
@@ -1713,69 +1823,15 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
     }
   }
 
-  cudaStream_t s = ctx->stream;
   double overall = INFINITY;
   for (int attempt = 0; attempt < 3; ++attempt) {
-    const Layout& L = ctx->lay;
-    double* r = ctx->vd(V_R);
-    double* xw = ctx->vd(V_X);
-    double* best = ctx->vd(V_BEST);
-    double best_rel = INFINITY;
     bool escalate = false;
     int st = run_factor(ctx, prec, R);
     if (st == MAG_ENOTPD && prec != MAG_PREC_FP64 && o.allow_fallback) {
       escalate = true;
     } else {
       TRY(st);
-      R->prec_used = prec;
-      // initial solve x0 = factor^{-1} b: the correction from x = 0 with r = b.
-      if (b)
-        CU(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      else
-        CU(launch_fill(r, n, 1.0, s));
-      CU(launch_fill(r + n, L.np - n, 0.0, s));
-      TRY(reset_norms(ctx));
-      CU(launch_absmax(r, n, ctx->st(), s));
-      TRY(correction(ctx, prec, r, xw, /*init=*/true, R));
-      double rel = INFINITY, prev = INFINITY;
-      int slow = 0;
-      for (int it = 0;; ++it) {
-        // The FP64 factor overwrites the FP64 tiles, so it refines matrix free.
-        TRY(residual(ctx, X, m, t, xw, b, r, &rel, stored && prec != MAG_PREC_FP64, R));
-        if (rel < best_rel) {
-          best_rel = rel;
-          CU(cudaMemcpyAsync(best, xw, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        }
-        if (rel <= kStopMargin * o.ir_tol) break;
-        if (it >= o.ir_max_iters || (rel > 0.5 * prev && ++slow >= 2)) {
-          escalate = true;
-          break;
-        }
-        if (!(rel > 0.5 * prev)) slow = 0;
-        prev = rel;
-        TRY(correction(ctx, prec, r, xw, /*init=*/false, R));
-        R->ir_iters++;
-      }
-      if (best_rel < overall) {
-        overall = best_rel;
-        CU(cudaMemcpyAsync(x, best, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        CU(cudaStreamSynchronize(s));
-      }
-      // a mispredicted FP16 choice goes to the split factor instead of GMRES-IR
-      const bool to_split = escalate && probed16 && prec == MAG_PREC_FP16 && o.allow_fallback;
-      if (escalate && !to_split && prec != MAG_PREC_FP64 && o.allow_fallback && o.gmres_max_iters > 0) {
-        // GMRES-IR with the same factor, from the best iterate so far
-        CU(cudaMemcpyAsync(xw, best, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        double grel = INFINITY;
-        R->fallback = 1;
-        TRY(gmres_ir(ctx, prec, X, m, t, b, xw, stored, R, &grel));
-        if (grel < overall) {
-          overall = grel;
-          CU(cudaMemcpyAsync(x, xw, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-          CU(cudaStreamSynchronize(s));
-        }
-        if (grel <= kStopMargin * o.ir_tol) escalate = false;
-      }
+      TRY(refine(ctx, prec, X, n, m, t, b, x, stored, probed16, R, &overall, &escalate));
     }
     if (!escalate || prec == MAG_PREC_FP64 || !o.allow_fallback) break;
     if (probed16 && prec == MAG_PREC_FP16) {
@@ -1793,6 +1849,7 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
     TRY(generate(ctx, X, m, t, false, true, R, true));
   }
   R->rel = overall;
+  if (overall < INFINITY && ctx->kind == MAT_EXP) TRY(keep_factor(ctx, X, n, m, t, R->prec_used, stored));
   if (!(overall < INFINITY)) return fail(ctx, MAG_ENOTPD, "no factor succeeded");
   if (!(overall <= o.ir_tol))
     return fail(ctx, MAG_ENOCONV, "refinement stopped at relative residual %.3e > %.3e", overall, o.ir_tol);
@@ -1834,6 +1891,7 @@ void fill_info(mag_ctx* ctx, const SolveResult& R, int64_t n, mag_info* info) {
   info->host_read_bytes = R.host_read_bytes;
   info->ms_host_read = R.ms_host_read;
   info->deflation_c = R.deflation_c;
+  info->factor_reused = R.factor_reused;
 }
 
 // The small-t end (Z close to 1 1^T, kappa(Z) growing like 1/t): with
@@ -1893,6 +1951,7 @@ int mag_similarity_matrix(mag_ctx* ctx, const double* points, int64_t n, int32_t
   ctx->err.clear();
   const bool f64 = precision == MAG_PREC_FP64;
   SolveResult R;
+  ctx->fac_valid = false;
   TRY(ensure_workspace(ctx, n, !f64, f64));
   TRY(generate(ctx, points, m, t, !f64, f64, &R));
   const Layout& L = ctx->lay;
@@ -1912,6 +1971,7 @@ int mag_cholesky_factor(mag_ctx* ctx, const double* points, int64_t n, int32_t m
   const bool f64 = precision == MAG_PREC_FP64;
   int prec = f64 ? MAG_PREC_FP64 : (precision == MAG_PREC_AUTO ? MAG_PREC_FP16X3 : precision);
   SolveResult R;
+  ctx->fac_valid = false;
   TRY(ensure_workspace(ctx, n, !f64, f64));
   TRY(generate(ctx, points, m, t, !f64, f64, &R));
   TRY(run_factor(ctx, prec, &R));
@@ -2042,7 +2102,29 @@ int mag_solve_rhs(mag_ctx* ctx, const double* points, int64_t n, int32_t m, doub
   ctx->err.clear();
   if (info) std::memset(info, 0, sizeof *info);
   SolveResult R;
-  int st = solve_impl(ctx, points, n, m, t, b, x, &R);
+  int st = MAG_ENOCONV;
+  if (ctx->fac_valid && ctx->fac_pts == points && ctx->fac_n == n && ctx->fac_m == m && ctx->fac_t == t &&
+      ctx->kind == MAT_EXP) {
+    // the factor of the last solve with these points and t is still in the
+    // workspace: refine with it (the adjoint solve of mag_grad after the
+    // forward solve); a new factor only if that does not converge
+    unsigned long long h = 0;
+    TRY(points_hash(ctx, points, n, m, &h));
+    if (h == ctx->fac_hash) {
+      TRY(reset_status(ctx));
+      double overall = INFINITY;
+      bool escalate = false;
+      R.stored = ctx->fac_stored;
+      R.factor_reused = 1;
+      TRY(refine(ctx, ctx->fac_prec, points, n, m, t, b, x, ctx->fac_stored, false, &R, &overall, &escalate));
+      R.rel = overall;
+      st = overall <= ctx->opt.ir_tol ? MAG_OK : MAG_ENOCONV;
+    }
+  }
+  if (st != MAG_OK) {
+    R = SolveResult();
+    st = solve_impl(ctx, points, n, m, t, b, x, &R);
+  }
   fill_info(ctx, R, n, info);
   return st;
 }
@@ -2241,6 +2323,7 @@ int mag_grad(mag_ctx* ctx, const double* points, int64_t n, int32_t m, double t,
     TRY(mag_solve_rhs(ctx, points, n, m, t, g, lam, &ai));
     si.ir_iters += ai.ir_iters;
     si.rel_residual = std::max(si.rel_residual, ai.rel_residual);
+    si.factor_reused = ai.factor_reused;
   } else {
     CU(cudaMemcpyAsync(lam, wv, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }

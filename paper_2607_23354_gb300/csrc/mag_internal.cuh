@@ -85,6 +85,7 @@ struct DevStatus {
   double mag;                      // 1^T w (compensated)
   double min_w;                    // min_j w_j
   double aux[6];                   // scratch scalars (GMRES dot products, grad sums)
+  unsigned long long hash_bits;    // checksum of the points (launch_hash)
 };
 
 // ---------------------------------------------------------------- launchers
@@ -328,6 +329,9 @@ cudaError_t launch_grad(const double* X, int64_t n, int m, double t, const doubl
                         const double* lam, double* dL_dx, double* part_t, int64_t np,
                         cudaStream_t s);
 cudaError_t launch_sum_f64(const double* v, int64_t n, double* out, cudaStream_t s);
+// *out += an order-independent 64-bit mix of the bits of v[0..count) and
+// their positions (a checksum: *out must be zeroed first).
+cudaError_t launch_hash(const double* v, int64_t count, unsigned long long* out, cudaStream_t s);
 // out2[0] = min_i v_i, out2[1] = max_i v_i (device).
 cudaError_t launch_minmax(const double* v, int64_t n, double* out2, cudaStream_t s);
 

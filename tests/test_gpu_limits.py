@@ -190,3 +190,38 @@ def test_constant_loss_gradient_is_scaled_magnitude_gradient(ctx):
     assert float((dx2 - c * dx1).abs().max()) <= 1e-14 * float(dx1.abs().max()) * abs(c)
     dto, dxo = oracle.grad(X, t, oracle.weighting(X, t)[0])
     assert dt1 == pytest.approx(dto, rel=1e-9)
+
+
+# ------------------------------------------- the adjoint solve reuses the factor
+
+def test_adjoint_solve_reuses_the_forward_factor(ctx):
+    # after a solve, a solve with another right-hand side for the same points
+    # and t refines with the factor still in the context (no new factor); a
+    # change of the points in place (same pointer) is seen by the checksum
+    X = np.random.default_rng(809).random((3000, 6))
+    Xd = _dev(X)
+    t = 1.5
+    w, mag, info = ctx.solve(Xd, t)
+    g = np.random.default_rng(810).standard_normal(3000)
+    lam, ai = ctx.solve_rhs(Xd, t, torch.from_numpy(g).cuda())
+    assert ai["factor_reused"] == 1 and ai["ms_factor"] == 0.0
+    lam_ref, oi = oracle.solve(X, t, b=g)
+    assert oracle.relative_residual(X, t, lam.cpu().numpy(), b=g) <= 1e-14
+    assert np.abs(lam.cpu().numpy() - lam_ref).max() <= 1e-9 * np.abs(lam_ref).max()
+    # another t: no reuse
+    _, ai2 = ctx.solve_rhs(Xd, 1.6, torch.from_numpy(g).cuda())
+    assert ai2["factor_reused"] == 0
+    # the same t again after the points changed in place: no reuse, and the
+    # result is the new points' solution
+    ctx.solve(Xd, t)
+    Xd[17, 3] += 1e-3
+    X2 = Xd.cpu().numpy()
+    lam3, ai3 = ctx.solve_rhs(Xd, t, torch.from_numpy(g).cuda())
+    assert ai3["factor_reused"] == 0
+    assert oracle.relative_residual(X2, t, lam3.cpu().numpy(), b=g) <= 1e-14
+    # mag_grad with a general loss right after the forward solve
+    w, _, _ = ctx.solve(Xd, t)
+    dt, dx = ctx.grad(Xd, t, w=w, dL_dw=2 * w)
+    dto, dxo = oracle.grad_loss(X2, t, 2 * w.cpu().numpy(), w=w.cpu().numpy())
+    assert dt == pytest.approx(dto, rel=1e-8)
+    assert np.abs(dx.cpu().numpy() - dxo).max() <= 1e-7 * np.abs(dxo).max()
