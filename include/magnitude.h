@@ -208,6 +208,11 @@ typedef struct mag_info {
                               (pointer, size and contents) and t left in the
                               context, without generating or factoring again */
   int32_t reserved2;
+  double ms_update_busy;   /* length of the union of the update launches'
+                              intervals (profile = 1): the time during which
+                              at least one update launch was in flight; the
+                              look-ahead streams overlap, so ms_update, a sum
+                              of intervals, counts shared stretches twice    */
 } mag_info;
 
 typedef struct mag_ctx mag_ctx;

@@ -69,7 +69,7 @@ class mag_info(ctypes.Structure):
                 ("slabs", ctypes.c_int32), ("host_slabs", ctypes.c_int32), ("host_bytes", ctypes.c_double),
                 ("host_read_bytes", ctypes.c_double), ("ms_host_read", ctypes.c_double),
                 ("deflation_c", ctypes.c_double), ("factor_reused", ctypes.c_int32),
-                ("reserved2", ctypes.c_int32)]
+                ("reserved2", ctypes.c_int32), ("ms_update_busy", ctypes.c_double)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}

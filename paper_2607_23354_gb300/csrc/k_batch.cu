@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(BT, 1)
     for (int i = warp; i < n; i += BT / 32) {
       const double* Di = Dc + (int64_t)i * (i - 1) / 2;
       for (int j = lane; j < i; j += 32) {
-        const double z = exp_neg(-P.t * Di[j], exptab);
+        const double z = exp_neg_of(P.t * Di[j], exptab);
         S.Zd[(int64_t)i * n + j] = z;
         S.Zd[(int64_t)j * n + i] = z;
         S.Lf[(int64_t)i * n + j] = f64_to_f32_nonneg(z);

@@ -35,7 +35,7 @@ template <bool WF, bool WD, bool ROWSUM, bool WDIST>
 __global__ void __launch_bounds__(GEN_THREADS, 1)
     k_generate(const double* __restrict__ X, int64_t n, int m, double t, float* __restrict__ Zf,
                double* __restrict__ Zd, double* __restrict__ Dd, double* __restrict__ rowsum, DevStatus* st,
-               int kind, double tiny_arg, int64_t t0, int64_t W, double kc) {
+               int kind, double dcut, int64_t t0, int64_t W, double kc) {
   extern __shared__ double smem[];
   double* xr = smem;                   // [TILE][GEN_MC] row points (broadcast reads)
   double* xc = smem + TILE * GEN_MC;   // [GEN_MC][TILE] column points (conflict free)
@@ -92,9 +92,9 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
   unsigned long long mind2b = 0x7ff0000000000000ull;  // +inf
   int flags = 0;
   const float tf = (float)t;
-  // d > tiny_arg / t on the bit patterns (d >= 0): the FP64 pipe stays on
-  // the distances and the exponential
-  const unsigned long long tiny_bits = (unsigned long long)__double_as_longlong(tiny_arg / t);
+  // d > dcut = tiny_arg / t (from the host) on the bit patterns (d >= 0):
+  // the FP64 pipe stays on the distances and the exponential
+  const unsigned long long tiny_bits = (unsigned long long)__double_as_longlong(dcut);
 
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -151,14 +151,15 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
   if (lane == 0) warpmin[warp] = mind2b;
 
   if (ROWSUM) {
-    // row sums: reduce over lanes, one atomic per row
+    // row sums: an FP32 lane tree (a norm: depth 5 adds at most 5 roundings
+    // to the 4-entry partials), one FP64 atomic per row
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      double v = (double)rs[i];
+      float v = rs[i];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       const int64_t gr = row0 + warp + 16 * i;
-      if (lane == 0 && gr < n) atomicAdd(rowsum + gr, v);
+      if (lane == 0 && gr < n) atomicAdd(rowsum + gr, (double)v);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) colpart[warp][lane + 32 * q] = (double)cs[q];
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
 template <bool WF, bool WD>
 __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __restrict__ Dd, int64_t n, double t,
                                                             float* __restrict__ Zf, double* __restrict__ Zd,
-                                                            double* __restrict__ rowsum, int kind, double tiny_arg,
+                                                            double* __restrict__ rowsum, int kind, double dcut,
                                                             double kc) {
   __shared__ double exptab[2 * EXPT_SIZE];
   __shared__ float colpart[8][TILE];
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __rest
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t off = tri_index(I, J) * TILE_ELEMS;
   const float tf = (float)t;
-  const unsigned long long tiny_bits = (unsigned long long)__double_as_longlong(tiny_arg / t);
+  const unsigned long long tiny_bits = (unsigned long long)__double_as_longlong(dcut);
   // row/column partial sums in FP32 (a norm; the FP64 pipe is the limit)
   float cs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   for (int i = 0; i < 16; ++i) {
@@ -284,7 +285,9 @@ cudaError_t launch_gen_t(const double* X, int64_t n, int m, double t, int64_t N,
   if (W < 0) W = N;
   const int64_t tiles = num_slab_tiles(N, W);
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-  kern<<<(unsigned)tiles, GEN_THREADS, smem, s>>>(X, n, m, t, Zf, Zd, Dd, rowsum, st, kind, tiny_arg, t0, W, kc);
+  // entries with d > tiny_arg / t leave the FP64 exponential
+  const double dcut = tiny_arg / t;
+  kern<<<(unsigned)tiles, GEN_THREADS, smem, s>>>(X, n, m, t, Zf, Zd, Dd, rowsum, st, kind, dcut, t0, W, kc);
   note_launch();
   return cudaGetLastError();
 }
@@ -316,12 +319,13 @@ cudaError_t launch_generate_dist(const double* X, int64_t n, int m, double t, in
 cudaError_t launch_generate_from_dist(const double* Dd, int64_t n, double t, int64_t N, float* Zf, double* Zd,
                                      double* rowsum, cudaStream_t s, int kind, double tiny_arg, double kc) {
   const unsigned tiles = (unsigned)num_lower_tiles(N);
+  const double dcut = tiny_arg / t;
   if (Zf && Zd)
-    k_generate_from_dist<true, true><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum, kind, tiny_arg, kc);
+    k_generate_from_dist<true, true><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum, kind, dcut, kc);
   else if (Zf)
     k_generate_from_dist<true, false><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum, kind, INFINITY, kc);
   else if (Zd)
-    k_generate_from_dist<false, true><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum, kind, tiny_arg, kc);
+    k_generate_from_dist<false, true><<<tiles, 256, 0, s>>>(Dd, n, t, Zf, Zd, rowsum, kind, dcut, kc);
   else
     return cudaErrorInvalidValue;
   note_launch();

@@ -178,7 +178,8 @@ __global__ void __launch_bounds__(256) k_resid_stored(const double* __restrict__
 // Matrix-free FP64 residual over the lower triangle of tiles only (Z is
 // symmetric): one CTA per lower tile (I, J) computes its 128 x 128 entries
 // Z_jk = exp(-t d_jk) once -- the FP64 differences, square root and
-// exponential of the generator -- and uses each twice: the row contributions
+// exponential of the generator, entries below e^-46 in FP32 as the generator
+// writes them for a solve -- and uses each twice: the row contributions
 // Z_IJ w_J (rows of block I) go to partial P[I][J], and for I != J the
 // column contributions Z_IJ^T w_I (rows of block J) to P[J][I], so every row
 // block X has exactly N partials P[X][0..N-1] (J <= X: its tiles' rows;
@@ -245,6 +246,7 @@ __global__ void __launch_bounds__(SYM_THREADS, 1)
   __syncthreads();
   double cs[4] = {0.0, 0.0, 0.0, 0.0};
   float zc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  const unsigned long long tiny_bits = (unsigned long long)__double_as_longlong(kTinyArg);
   // rows of block I: each row's 4 products per lane, then a lane tree -> P[I][J]
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -260,9 +262,14 @@ __global__ void __launch_bounds__(SYM_THREADS, 1)
       if (gr < n && gc < n) {
         if (gr == gc) {
           z = 1.0;
+        } else if (kind == MAT_EXP) {
+          // the solver's entries: FP32 below e^-46 (as the generator writes
+          // them for a solve), the FP32-reduced FP64 exponential above
+          const double a = t * sqrt_pos(d2[i][q]);
+          z = (unsigned long long)__double_as_longlong(a) > tiny_bits ? (double)exp_neg_tiny(a)
+                                                                       : exp_neg_small(a, exptab);
         } else {
-          const double dd = sqrt_pos(d2[i][q]);
-          z = mat_entry(kind, t, kc, dd, exptab);
+          z = mat_entry(kind, t, kc, sqrt_pos(d2[i][q]), exptab);
         }
       }
       v = fma(z, s_wc[lane + 32 * q], v);
@@ -557,7 +564,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_grad(const double* __restrict__
           d2 = fma(diff, diff, d2);
         }
       const double d = sqrt_pos(d2);
-      const double z = exp_neg(-t * d, exptab);
+      const double z = exp_neg_of(t * d, exptab);
       // dL/dt contribution with Kahan compensation
       const double y = fma(li * d * z, wc[q], -st_c);
       const double tt = st_s + y;

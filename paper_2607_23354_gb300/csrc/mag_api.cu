@@ -357,14 +357,40 @@ int prof_end(mag_ctx* ctx, cudaStream_t st = nullptr) {
 }
 // Per-category sums of the recorded intervals (after the stream has been
 // synchronized); returns the update total (trailing + panel updates).
-double prof_collect(mag_ctx* ctx, double* per_cat) {
+// *busy (if given) receives the length of the union of the update
+// intervals: launches on the two look-ahead streams overlap in time, so the
+// sum counts the shared stretches twice while the union is the time during
+// which at least one update launch was in flight.
+double prof_collect(mag_ctx* ctx, double* per_cat, double* busy = nullptr) {
   for (int c = 0; c < PC_COUNT; ++c) per_cat[c] = 0;
+  std::vector<std::pair<float, float>> upd;
   for (int i = 0; i < ctx->prof_used; ++i) {
-    float v = 0;
-    if (cudaEventElapsedTime(&v, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]) == cudaSuccess)
+    float v = 0, a = 0, b = 0;
+    if (cudaEventElapsedTime(&v, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]) == cudaSuccess) {
       per_cat[ctx->prof_cat[i]] += v;
-    else
+      if (busy && (ctx->prof_cat[i] == PC_UPDATE || ctx->prof_cat[i] == PC_UPDATE_PANEL) &&
+          cudaEventElapsedTime(&a, ctx->prof_ev[0], ctx->prof_ev[2 * i]) == cudaSuccess &&
+          cudaEventElapsedTime(&b, ctx->prof_ev[0], ctx->prof_ev[2 * i + 1]) == cudaSuccess)
+        upd.emplace_back(a, b);
+      cudaGetLastError();
+    } else {
       cudaGetLastError();  // an interval cut short by an error: drop it, leave no pending error
+    }
+  }
+  if (busy) {
+    std::sort(upd.begin(), upd.end());
+    double total = 0, lo = 0, hi = -INFINITY;
+    for (const auto& iv : upd) {
+      if (iv.first > hi) {
+        if (hi > lo) total += hi - lo;
+        lo = iv.first;
+        hi = iv.second;
+      } else if (iv.second > hi) {
+        hi = iv.second;
+      }
+    }
+    if (hi > lo) total += hi - lo;
+    *busy = total;
   }
   ctx->prof_used = 0;
   return per_cat[PC_UPDATE] + per_cat[PC_UPDATE_PANEL];
@@ -1070,6 +1096,7 @@ struct SolveResult {
   int residual_evals = 0, update_launches = 0;
   bool stored = false;
   double ms_update = 0, update_flops = 0, ms_update_panel = 0, ms_potrf = 0, ms_trsm = 0, ms_split = 0;
+  double ms_update_busy = 0;
   double probe_rho = 0, ms_probe = 0;
   int slabs = 0, host_slabs = 0;
   double host_bytes = 0, host_read_bytes = 0, ms_host_read = 0;
@@ -1166,8 +1193,9 @@ int run_factor(mag_ctx* ctx, int prec, SolveResult* R) {
   CU(cudaEventRecord(ctx->ev[1], s));
   TRY(read_status(ctx));
   R->ms_fac += elapsed(ctx, 0, 1);
-  double pc[PC_COUNT];
-  R->ms_update += prof_collect(ctx, pc);
+  double pc[PC_COUNT], busy = 0;
+  R->ms_update += prof_collect(ctx, pc, &busy);
+  R->ms_update_busy += busy;
   R->ms_update_panel += pc[PC_UPDATE_PANEL];
   R->ms_potrf += pc[PC_POTRF];
   R->ms_trsm += pc[PC_TRSM];
@@ -1689,8 +1717,9 @@ int solve_ooc(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, con
     CU(cudaEventRecord(ctx->ev[1], s));
     TRY(read_status(ctx));
     R->ms_fac += elapsed(ctx, 0, 1);
-    double pc[PC_COUNT];
-    R->ms_update += prof_collect(ctx, pc);
+    double pc[PC_COUNT], busy = 0;
+    R->ms_update += prof_collect(ctx, pc, &busy);
+    R->ms_update_busy += busy;
     R->ms_update_panel += pc[PC_UPDATE_PANEL];
     R->ms_potrf += pc[PC_POTRF];
     R->ms_trsm += pc[PC_TRSM];
@@ -1892,6 +1921,7 @@ void fill_info(mag_ctx* ctx, const SolveResult& R, int64_t n, mag_info* info) {
   info->ms_host_read = R.ms_host_read;
   info->deflation_c = R.deflation_c;
   info->factor_reused = R.factor_reused;
+  info->ms_update_busy = R.ms_update_busy;
 }
 
 // The small-t end (Z close to 1 1^T, kappa(Z) growing like 1/t): with
