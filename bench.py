@@ -270,7 +270,8 @@ def run_ours(a):
         last = infos[-len(ts):]
         dmin = last[0][2]["min_distance"]
         per_t = [{"t": i["t"], "solve_s": i["ms_total"] / 1e3, "mag": mag, "rel_residual": i["rel_residual"],
-                  "ir_iters": i["ir_iters"], "precision_used": i["precision_used"], "fallback": i["fallback"],
+                  "ir_iters": i["ir_iters"], "gmres_iters": i["gmres_iters"], "precision_used": i["precision_used"],
+                  "fallback": i["fallback"],
                   "ms_generate": i["ms_generate"], "ms_factor": i["ms_factor"], "ms_solve": i["ms_solve"],
                   "ms_residual": i["ms_residual"], "residual_evals": i["residual_evals"],
                   "probe_rho": i["probe_rho"], "ms_probe": i["ms_probe"],
