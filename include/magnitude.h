@@ -154,6 +154,20 @@ typedef struct mag_options {
   double host_limit_bytes;/* pinned host memory the out-of-core factor may
                              take (0: half of the host's physical memory);
                              more gives MAG_ENOMEM                          */
+  int32_t gmres_matvec;   /* products Z v of GMRES-IR's inner iterations:
+                             0 (default) float-float on the FP32 pipe from
+                             the stored FP64 tiles of exp(-t d) (a few units
+                             of 2^-46 of sum |Z||v|; the outer residuals
+                             stay FP64), else FP64 as the residual          */
+  int32_t fp16_gmres;     /* AUTO: 0 (default) the one-product FP16 factor
+                             with GMRES-IR straight after the first solve
+                             when the probe predicts plain refinement to
+                             diverge or crawl (contraction <= 16) and the
+                             factor saved outweighs the inner iterations
+                             (n >= 133,000 with stored tiles); a GMRES-IR that
+                             stalls is replaced by the split factor
+                             (mag_info.fallback = 3); -1 never; 1 whenever
+                             the contraction is <= 16 (any n)              */
 } mag_options;
 
 /* Diagnostics of one call (all fields written when info != NULL). */
@@ -162,7 +176,9 @@ typedef struct mag_info {
   int32_t ir_iters;        /* refinement steps taken (all precisions)          */
   int32_t gmres_iters;     /* total inner GMRES iterations (0 if not used)     */
   int32_t fallback;        /* 0 none, 1 GMRES-IR, 2 FP64 factor, 3 the probe's
-                              FP16 choice refined slowly: split factor       */
+                              FP16 choice refined slowly: split factor,
+                              4 the probe chose the FP16 factor with
+                              GMRES-IR (options.fp16_gmres)                  */
   int32_t residual_mode;   /* enum mag_residual_mode actually used (0 or 1)    */
   int32_t reserved0;
   double rel_residual;     /* final ||1-Zw||inf / (||Z||inf ||w||inf)          */

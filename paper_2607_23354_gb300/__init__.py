@@ -47,7 +47,8 @@ class mag_options(ctypes.Structure):
                 ("lookahead", ctypes.c_int32), ("lookahead_sms", ctypes.c_int32),
                 ("cta_pairs", ctypes.c_int32), ("tplus_method", ctypes.c_int32),
                 ("wait_timeout_ns", ctypes.c_int64), ("out_of_core", ctypes.c_int32),
-                ("deflate", ctypes.c_int32), ("host_limit_bytes", ctypes.c_double)]
+                ("deflate", ctypes.c_int32), ("host_limit_bytes", ctypes.c_double),
+                ("gmres_matvec", ctypes.c_int32), ("fp16_gmres", ctypes.c_int32)]
 
 
 class mag_info(ctypes.Structure):
@@ -161,6 +162,8 @@ class Options:
     out_of_core: int = 0
     deflate: int = 0
     host_limit_bytes: float = 0.0
+    gmres_matvec: str = "float_float"  # or "fp64"
+    fp16_gmres: int = 0
 
     def to_c(self) -> mag_options:
         o = mag_options()
@@ -184,6 +187,10 @@ class Options:
         o.out_of_core = int(self.out_of_core)
         o.deflate = int(self.deflate)
         o.host_limit_bytes = float(self.host_limit_bytes)
+        if self.gmres_matvec not in ("float_float", "fp64"):
+            raise ValueError(f"gmres_matvec must be 'float_float' or 'fp64', not {self.gmres_matvec!r}")
+        o.gmres_matvec = 0 if self.gmres_matvec == "float_float" else 1
+        o.fp16_gmres = int(self.fp16_gmres)
         return o
 
 

@@ -175,6 +175,135 @@ __global__ void __launch_bounds__(256) k_resid_stored(const double* __restrict__
   }
 }
 
+// The same product Z w from the same FP64 tiles in float-float arithmetic on
+// the FP32 pipe, for the inner iterations of GMRES-IR (GB300 runs FP64 at
+// 1/64 of FP32, and k_resid_stored is bound by its FP64 FMAs).  Each entry
+// z in [0, 1] (Z = exp(-t D)) is split on the integer pipe into z_h (its
+// leading 24 bits) and z_l (the next 23 of the 29 remaining), w into
+// w_h + w_l (k_split_ff); a product is z_h w_h exactly (FMA) plus
+// z_h w_l + z_l w_h, and the sums are float-float (Knuth's TwoSum on the
+// leading parts, the trailing parts added plainly).  Dropping z_l w_l, the
+// last 6 bits of z and the rounding of the trailing parts leave a relative
+// error of a few units of 2^-46 of sum_k |z_jk| |w_k| -- far below what a
+// preconditioned inner iteration resolves, not the FP64 residual (the outer
+// steps of GMRES-IR keep k_resid_stored).  Layout, partials and the finish
+// (k_resid_stored_finish) as in k_resid_stored.
+struct ffp {
+  float h, l;
+};
+
+__device__ __forceinline__ void ff_split_unit(double z, float* zh, float* zl) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(z);
+  const unsigned e = (unsigned)(b >> 52);  // z >= 0: the biased exponent
+  const float h = __uint_as_float((unsigned)(b >> 29) - ((1023u - 127u) << 23));
+  // the 29 bits below z_h: (m >> 6) 2^-23 exactly, times 2^(e - 1046)
+  const unsigned m = (unsigned)b & 0x1FFFFFFFu;
+  const float f = __uint_as_float((m >> 6) | 0x3F800000u) - 1.0f;
+  const int se = (int)e - (1046 - 127);
+  *zh = e >= 1023u - 126u ? h : 0.0f;  // below 2^-126: 0
+  *zl = se > 0 ? f * __uint_as_float((unsigned)se << 23) : 0.0f;
+}
+
+// s += z w in float-float
+__device__ __forceinline__ void ff_fma(ffp& s, float zh, float zl, float wh, float wl) {
+  const float ph = zh * wh;
+  float pl = fmaf(zh, wh, -ph);
+  pl = fmaf(zh, wl, pl);
+  pl = fmaf(zl, wh, pl);
+  const float t = s.h + ph;
+  const float bp = t - s.h;
+  const float e = (s.h - (t - bp)) + (ph - bp);
+  s.l += pl + e;
+  s.h = t;
+}
+
+__device__ __forceinline__ void ff_add(ffp& s, const ffp& o) {
+  const float t = s.h + o.h;
+  const float bp = t - s.h;
+  const float e = (s.h - (t - bp)) + (o.h - bp);
+  s.l += o.l + e;
+  s.h = t;
+}
+
+__device__ __forceinline__ ffp ff_shfl_xor(const ffp& v, int o) {
+  return ffp{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+}
+
+__global__ void k_split_ff(const double* __restrict__ w, int64_t n, int64_t np, float2* __restrict__ out) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= np) return;
+  const double v = j < n ? w[j] : 0.0;
+  const float h = __double2float_rn(v);
+  out[j] = make_float2(h, __double2float_rn(v - (double)h));
+}
+
+__global__ void __launch_bounds__(256) k_resid_stored_ff(const double* __restrict__ Zd, int64_t n, int64_t N,
+                                                         const float2* __restrict__ wf, double* __restrict__ P) {
+  __shared__ ffp colp[8][TILE];
+  const int64_t J = blockIdx.y;
+  const int64_t t = blockIdx.x;
+  const int64_t nstrips = (N - 1 - J + RS_STRIP - 1) / RS_STRIP;
+  if (t > nstrips) return;  // uniform
+  const int tid = threadIdx.x, wp = tid >> 5, l = tid & 31, cg = l & 7, rs = l >> 3;
+  float2 wc[16];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int64_t col = J * TILE + 16 * k + 2 * cg;
+    wc[2 * k] = wf[col];  // wf is zero-padded to a whole tile row
+    wc[2 * k + 1] = wf[col + 1];
+  }
+  const int64_t I0 = t == 0 ? J : J + 1 + (t - 1) * RS_STRIP;
+  const int64_t I1 = t == 0 ? J + 1 : (I0 + RS_STRIP < N ? I0 + RS_STRIP : N);
+  ffp cs[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) cs[k] = ffp{0.0f, 0.0f};
+  for (int64_t I = I0; I < I1; ++I) {
+    const double* tile = Zd + tri_index(I, J) * TILE_ELEMS;
+#pragma unroll 1
+    for (int i = 0; i < 4; ++i) {
+      const int r = wp * 16 + 4 * i + rs;
+      const float2 wr = wf[I * TILE + r];
+      const double* rp = tile + r * TILE + 2 * cg;
+      ffp sr{0.0f, 0.0f};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const double2 z = *reinterpret_cast<const double2*>(rp + 16 * k);
+        float zh0, zl0, zh1, zl1;
+        ff_split_unit(z.x, &zh0, &zl0);
+        ff_split_unit(z.y, &zh1, &zl1);
+        ff_fma(sr, zh0, zl0, wc[2 * k].x, wc[2 * k].y);
+        ff_fma(sr, zh1, zl1, wc[2 * k + 1].x, wc[2 * k + 1].y);
+        ff_fma(cs[2 * k], zh0, zl0, wr.x, wr.y);
+        ff_fma(cs[2 * k + 1], zh1, zl1, wr.x, wr.y);
+      }
+      ff_add(sr, ff_shfl_xor(sr, 1));
+      ff_add(sr, ff_shfl_xor(sr, 2));
+      ff_add(sr, ff_shfl_xor(sr, 4));
+      if (cg == 0) P[(I * N + J) * TILE + r] = (double)sr.h + (double)sr.l;
+    }
+  }
+  if (t == 0) return;  // uniform: the diagonal tile's rows already cover both triangles
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    ff_add(cs[k], ff_shfl_xor(cs[k], 8));
+    ff_add(cs[k], ff_shfl_xor(cs[k], 16));
+  }
+  if (rs == 0) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      colp[wp][16 * k + 2 * cg] = cs[2 * k];
+      colp[wp][16 * k + 2 * cg + 1] = cs[2 * k + 1];
+    }
+  }
+  __syncthreads();
+  if (tid < TILE) {
+    ffp sc = colp[0][tid];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) ff_add(sc, colp[k][tid]);
+    P[(J * N + J + t) * TILE + tid] = (double)sc.h + (double)sc.l;
+  }
+}
+
 // Matrix-free FP64 residual over the lower triangle of tiles only (Z is
 // symmetric): one CTA per lower tile (I, J) computes its 128 x 128 entries
 // Z_jk = exp(-t d_jk) once -- the FP64 differences, square root and
@@ -752,6 +881,25 @@ cudaError_t launch_residual_stored(const double* Zd, int64_t n, int64_t N, const
   k_resid_stored<<<grid, 256, 0, s>>>(Zd, n, N, w, P);
   note_launch();
   cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_resid_stored_finish<<<blocks_for(np, 256), 256, 0, s>>>(P, n, N, np, w, b, rowsum, r, st);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_stored_ff(const double* Zd, int64_t n, int64_t N, const double* w, void* wsplit,
+                                      const double* b, const double* rowsum, double* r, double* P, int64_t np,
+                                      DevStatus* st, cudaStream_t s) {
+  if (N > 65535 || np < N * TILE) return cudaErrorInvalidValue;
+  float2* wf = static_cast<float2*>(wsplit);
+  k_split_ff<<<blocks_for(np, 256), 256, 0, s>>>(w, n, np, wf);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const dim3 grid((unsigned)((N - 1 + RS_STRIP - 1) / RS_STRIP + 1), (unsigned)N);
+  k_resid_stored_ff<<<grid, 256, 0, s>>>(Zd, n, N, wf, P);
+  note_launch();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_resid_stored_finish<<<blocks_for(np, 256), 256, 0, s>>>(P, n, N, np, w, b, rowsum, r, st);
   note_launch();

@@ -120,6 +120,7 @@ struct mag_ctx {
   unsigned long long fac_hash = 0;
   int fac_prec = 0;
   bool fac_stored = false;
+  bool fac_gmres = false;  // the solve that made it needed GMRES-IR
   // out-of-core factor (slabs); empty when the solve runs in core
   std::vector<Slab> slabs;
   bool ooc = false;                  // the current solve factors out of core
@@ -947,6 +948,8 @@ int mag_options_default(mag_options* opt) {
   opt->out_of_core = 0;
   opt->deflate = 0;
   opt->host_limit_bytes = 0.0;
+  opt->gmres_matvec = 0;
+  opt->fp16_gmres = 0;
   return MAG_OK;
 }
 
@@ -1429,12 +1432,12 @@ int probe_fp16(mag_ctx* ctx, const double* X, int32_t m, double t, bool stored, 
 // kappa(Z) u_factor is not small), with classical Gram-Schmidt applied twice.
 // x is the FP64 iterate (updated in place); returns the best relative residual.
 int gmres_ir(mag_ctx* ctx, int prec, const double* X, int32_t m, double t, const double* b, double* x,
-             bool stored, SolveResult* R, double* rel_out) {
+             bool stored, SolveResult* R, double* rel_out, bool planned = false) {
   const Layout& L = ctx->lay;
   const int64_t n = L.n, np = L.np;
   cudaStream_t s = ctx->stream;
   const int k = std::max(2, std::min(ctx->opt.gmres_max_iters, 200));
-  const size_t need = ((size_t)(k + 1) * np + 2 * np + 2 * (size_t)(k + 2)) * sizeof(double);
+  const size_t need = ((size_t)(k + 1) * np + 3 * np + 2 * (size_t)(k + 2)) * sizeof(double);
   if (need > ctx->gm_bytes) {
     if (ctx->gm) {
       cudaStreamSynchronize(s);
@@ -1455,13 +1458,19 @@ int gmres_ir(mag_ctx* ctx, int prec, const double* X, int32_t m, double t, const
   double* wv = zeros + np;                     // np
   double* dh = wv + np;                        // k+2
   double* dh2 = dh + (k + 2);                  // k+2
+  double* vsplit = dh2 + (k + 2);              // np float2 (the float-float product's split of v)
   double* r = ctx->vd(V_R);
   double* tmp = ctx->vd(V_E);
   CU(cudaMemsetAsync(zeros, 0, np * sizeof(double), s));
+  // the inner products Z v in float-float from the stored tiles of exp(-t d)
+  const bool ff = stored && ctx->kind == MAT_EXP && ctx->opt.gmres_matvec == 0;
   auto precond_matvec = [&](const double* v, double* out) -> int {
     // out = M^{-1} (Z v):  the residual kernel with b = 0 gives -Z v
     TRY(reset_norms(ctx));
-    if (stored)
+    if (ff)
+      CU(launch_residual_stored_ff(ctx->zd(), n, L.N, v, vsplit, zeros, ctx->vd(V_ROWSUM), tmp, ctx->spart(), np,
+                                   ctx->st(), s));
+    else if (stored)
       CU(launch_residual_stored(ctx->zd(), n, L.N, v, zeros, ctx->vd(V_ROWSUM), tmp, ctx->spart(), np, ctx->st(), s));
     else
       CU(launch_residual_sym(X, n, m, t, v, zeros, tmp, ctx->spart(), ctx->vd(V_ROWSUM), np, ctx->st(), s,
@@ -1470,13 +1479,18 @@ int gmres_ir(mag_ctx* ctx, int prec, const double* X, int32_t m, double t, const
     CU(launch_scale(out, -1.0, out, n, s));
     return MAG_OK;
   };
-  double best = INFINITY;
+  double best = INFINITY, prev_rel = INFINITY, rel = INFINITY;
+  bool fresh = false;  // rel is the residual of the current x
   std::vector<double> H((size_t)(k + 1) * k), cs(k), sn(k), g(k + 1), y(k), h(k + 1), h2(k + 1);
   for (int outer = 0; outer < 8; ++outer) {
-    double rel;
     TRY(residual(ctx, X, m, t, x, b, r, &rel, stored, R));
+    fresh = true;
     best = std::min(best, rel);
     if (rel <= kStopMargin * ctx->opt.ir_tol) break;
+    // planned (the probe's FP16 choice): an outer step that gains less than
+    // two digits leaves the rest to the split factor
+    if (planned && !(rel <= 1e-2 * prev_rel)) break;
+    prev_rel = rel;
     // V_0 = M^{-1} r / beta
     TRY(correction(ctx, prec, r, wv, /*init=*/true, R));
     CU(launch_mdot(wv, np, 1, wv, n, dh, s));
@@ -1534,11 +1548,10 @@ int gmres_ir(mag_ctx* ctx, int prec, const double* X, int32_t m, double t, const
     for (int i = 0; i < j; ++i) y[i] = -y[i];
     CU(cudaMemcpyAsync(dh, y.data(), j * sizeof(double), cudaMemcpyHostToDevice, s));
     CU(launch_maxpy(V, np, j, dh, x, n, s));
+    fresh = false;
     R->ir_iters++;
   }
-  double rel;
-  TRY(residual(ctx, X, m, t, x, b, r, &rel, stored, R));
-  best = std::min(best, rel);
+  if (!fresh) TRY(residual(ctx, X, m, t, x, b, r, &rel, stored, R));
   *rel_out = rel;
   return MAG_OK;
 }
@@ -1558,7 +1571,8 @@ int points_hash(mag_ctx* ctx, const double* X, int64_t n, int32_t m, unsigned lo
   return MAG_OK;
 }
 
-int keep_factor(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, int prec, bool stored) {
+int keep_factor(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, int prec, bool stored,
+                bool gmres) {
   unsigned long long h = 0;
   TRY(points_hash(ctx, X, n, m, &h));
   ctx->fac_valid = true;
@@ -1569,6 +1583,7 @@ int keep_factor(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, i
   ctx->fac_hash = h;
   ctx->fac_prec = prec;
   ctx->fac_stored = stored && prec != MAG_PREC_FP64;
+  ctx->fac_gmres = gmres;
   return MAG_OK;
 }
 
@@ -1580,6 +1595,23 @@ bool probe_takes_fp16(double rho, double tol, int64_t n, bool stored) {
   return rho < 1.0 && ir_steps(rho, tol) - ir_steps(rho * 0x1p-12, tol) <= saved;
 }
 
+// The FP16 factor with GMRES-IR where plain refinement with it would not
+// do (probe_takes_fp16 false): preconditioned by an FP16 factor whose
+// refinement contraction is predicted at most 16, GMRES-IR took 10-11 inner
+// iterations at n = 16384 and 32768 and 19 at n = 1e5 (t = 1 on [0,1]^8,
+// rho 0.87, 1.74 and 5.3).  An inner iteration (a float-float product with
+// the stored tiles, two triangular sweeps) costs about 0.7 refinement steps
+// (20 of 29 ms at n = 1e5), so 19 of them come to about 13 steps beyond the
+// split factor's refinement, while the half of the factor saved is worth
+// n / 9500 steps (at n = 1e5 the two solves took 1.045 and 1.037 s): taken
+// from n = 133,000 (options.fp16_gmres = 1: at any n).
+bool probe_takes_fp16_gmres(const mag_ctx* ctx, double rho, int64_t n, bool stored) {
+  const int mode = ctx->opt.fp16_gmres;
+  if (mode < 0 || !stored || ctx->kind != MAT_EXP || ctx->opt.gmres_max_iters < 2 || !ctx->opt.allow_fallback)
+    return false;
+  return rho <= 16.0 && (mode > 0 || (double)n / 9500.0 >= 14.0);
+}
+
 // Refinement of Z x = b (b == null: ones) with the factor in the workspace
 // (precision prec): x0 = factor^{-1} b, then r = b - Z x in FP64 and
 // x += factor^{-1} r until the relative residual is below kStopMargin times
@@ -1589,7 +1621,7 @@ bool probe_takes_fp16(double rho, double tol, int64_t n, bool stored) {
 // factor instead).  *overall keeps the lowest relative residual over calls,
 // with its iterate in x; *escalate reports a factor that did not get there.
 int refine(mag_ctx* ctx, int prec, const double* X, int64_t n, int32_t m, double t, const double* b, double* x,
-           bool stored, bool probed16, SolveResult* R, double* overall, bool* escalate) {
+           bool stored, bool probed16, SolveResult* R, double* overall, bool* escalate, bool gm_direct = false) {
   const mag_options& o = ctx->opt;
   const Layout& L = ctx->lay;
   cudaStream_t s = ctx->stream;
@@ -1608,6 +1640,20 @@ int refine(mag_ctx* ctx, int prec, const double* X, int64_t n, int32_t m, double
   TRY(reset_norms(ctx));
   CU(launch_absmax(r, n, ctx->st(), s));
   TRY(correction(ctx, prec, r, xw, /*init=*/true, R));
+  if (gm_direct) {
+    // the probe's FP16 factor with GMRES-IR from x0 at once: plain
+    // refinement was predicted to diverge or crawl
+    double grel = INFINITY;
+    R->fallback = 4;
+    TRY(gmres_ir(ctx, prec, X, m, t, b, xw, stored, R, &grel, /*planned=*/true));
+    if (grel < *overall) {
+      *overall = grel;
+      CU(cudaMemcpyAsync(x, xw, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CU(cudaStreamSynchronize(s));
+    }
+    *escalate = !(grel <= kStopMargin * o.ir_tol);
+    return MAG_OK;
+  }
   double rel = INFINITY, prev = INFINITY;
   int slow = 0;
   for (int it = 0;; ++it) {
@@ -1838,6 +1884,7 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
   // times more.  Else the scaled-FP16 split (FP32-like factor accuracy at the
   // FP16 tensor rate).
   bool probed16 = false;  // FP16 chosen on the probe's prediction
+  bool gm_direct = false;  // ... with GMRES-IR from the first solve on
   if (prec == MAG_PREC_AUTO) {
     prec = MAG_PREC_FP16X3;
     if (R->gersh >= 0.5) {
@@ -1848,6 +1895,10 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
       if (probe_takes_fp16(rho, kStopMargin * o.ir_tol, n, stored)) {
         prec = MAG_PREC_FP16;
         probed16 = true;
+      } else if (probe_takes_fp16_gmres(ctx, rho, n, stored)) {
+        prec = MAG_PREC_FP16;
+        probed16 = true;
+        gm_direct = true;
       }
     }
   }
@@ -1860,7 +1911,8 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
       escalate = true;
     } else {
       TRY(st);
-      TRY(refine(ctx, prec, X, n, m, t, b, x, stored, probed16, R, &overall, &escalate));
+      TRY(refine(ctx, prec, X, n, m, t, b, x, stored, probed16, R, &overall, &escalate,
+                 gm_direct && prec == MAG_PREC_FP16));
     }
     if (!escalate || prec == MAG_PREC_FP64 || !o.allow_fallback) break;
     if (probed16 && prec == MAG_PREC_FP16) {
@@ -1878,7 +1930,8 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
     TRY(generate(ctx, X, m, t, false, true, R, true));
   }
   R->rel = overall;
-  if (overall < INFINITY && ctx->kind == MAT_EXP) TRY(keep_factor(ctx, X, n, m, t, R->prec_used, stored));
+  if (overall < INFINITY && ctx->kind == MAT_EXP)
+    TRY(keep_factor(ctx, X, n, m, t, R->prec_used, stored, R->fallback == 1 || R->fallback == 4));
   if (!(overall < INFINITY)) return fail(ctx, MAG_ENOTPD, "no factor succeeded");
   if (!(overall <= o.ir_tol))
     return fail(ctx, MAG_ENOCONV, "refinement stopped at relative residual %.3e > %.3e", overall, o.ir_tol);
@@ -2146,7 +2199,8 @@ int mag_solve_rhs(mag_ctx* ctx, const double* points, int64_t n, int32_t m, doub
       bool escalate = false;
       R.stored = ctx->fac_stored;
       R.factor_reused = 1;
-      TRY(refine(ctx, ctx->fac_prec, points, n, m, t, b, x, ctx->fac_stored, false, &R, &overall, &escalate));
+      TRY(refine(ctx, ctx->fac_prec, points, n, m, t, b, x, ctx->fac_stored, false, &R, &overall, &escalate,
+                 ctx->fac_gmres));
       R.rel = overall;
       st = overall <= ctx->opt.ir_tol ? MAG_OK : MAG_ENOCONV;
     }

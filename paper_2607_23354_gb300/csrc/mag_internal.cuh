@@ -276,6 +276,13 @@ cudaError_t launch_residual_sym(const double* X, int64_t n, int m, double t, con
 cudaError_t launch_residual_stored(const double* Zd, int64_t n, int64_t N, const double* w,
                                    const double* b, const double* rowsum, double* r, double* P, int64_t np,
                                    DevStatus* st, cudaStream_t s);
+// The same product in float-float on the FP32 pipe (entries of exp(-t d) in
+// [0, 1] only): r = b - Z w to a few units of 2^-46 of sum |Z| |w|, for the
+// inner iterations of GMRES-IR.  wsplit: np float2 of scratch (w split into
+// FP32 leading and trailing parts); np >= N * TILE.
+cudaError_t launch_residual_stored_ff(const double* Zd, int64_t n, int64_t N, const double* w, void* wsplit,
+                                      const double* b, const double* rowsum, double* r, double* P, int64_t np,
+                                      DevStatus* st, cudaStream_t s);
 
 // K5/K6 helpers.  r_max below is max_j |r_j| as kept in st->r_max_bits.
 // v[i] = r[i] / r_max for i < n, 0 for n <= i < np (right-hand side of a correction).
