@@ -168,6 +168,15 @@ typedef struct mag_options {
                              stalls is replaced by the split factor
                              (mag_info.fallback = 3); -1 never; 1 whenever
                              the contraction is <= 16 (any n)              */
+  int32_t batch_shape;    /* mag_solve_batch launch shape: 0 (default) tuned
+                             per size class (ceil(log2 max n)) on the first
+                             batch of that class with at least twice the
+                             largest grid of problems -- each shape solves a
+                             sample of the batch once, the fastest is kept
+                             (smaller batches use shape 1 until then); 1:
+                             512 threads x 1 CTA per SM, 2: 256 x 2, 3: 256
+                             x 3 (mag_info.batch_threads / _ctas_per_sm)    */
+  int32_t reserved3;
 } mag_options;
 
 /* Diagnostics of one call (all fields written when info != NULL). */
@@ -229,6 +238,8 @@ typedef struct mag_info {
                               at least one update launch was in flight; the
                               look-ahead streams overlap, so ms_update, a sum
                               of intervals, counts shared stretches twice    */
+  int32_t batch_threads;   /* mag_solve_batch: threads per CTA of the launch   */
+  int32_t batch_ctas_per_sm; /* ... and the CTAs per SM of its shape          */
 } mag_info;
 
 typedef struct mag_ctx mag_ctx;

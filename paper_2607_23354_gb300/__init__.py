@@ -48,7 +48,8 @@ class mag_options(ctypes.Structure):
                 ("cta_pairs", ctypes.c_int32), ("tplus_method", ctypes.c_int32),
                 ("wait_timeout_ns", ctypes.c_int64), ("out_of_core", ctypes.c_int32),
                 ("deflate", ctypes.c_int32), ("host_limit_bytes", ctypes.c_double),
-                ("gmres_matvec", ctypes.c_int32), ("fp16_gmres", ctypes.c_int32)]
+                ("gmres_matvec", ctypes.c_int32), ("fp16_gmres", ctypes.c_int32),
+                ("batch_shape", ctypes.c_int32), ("reserved3", ctypes.c_int32)]
 
 
 class mag_info(ctypes.Structure):
@@ -70,7 +71,8 @@ class mag_info(ctypes.Structure):
                 ("slabs", ctypes.c_int32), ("host_slabs", ctypes.c_int32), ("host_bytes", ctypes.c_double),
                 ("host_read_bytes", ctypes.c_double), ("ms_host_read", ctypes.c_double),
                 ("deflation_c", ctypes.c_double), ("factor_reused", ctypes.c_int32),
-                ("reserved2", ctypes.c_int32), ("ms_update_busy", ctypes.c_double)]
+                ("reserved2", ctypes.c_int32), ("ms_update_busy", ctypes.c_double),
+                ("batch_threads", ctypes.c_int32), ("batch_ctas_per_sm", ctypes.c_int32)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -164,6 +166,7 @@ class Options:
     host_limit_bytes: float = 0.0
     gmres_matvec: str = "float_float"  # or "fp64"
     fp16_gmres: int = 0
+    batch_shape: int = 0  # 0 tuned, 1..3 fixed
 
     def to_c(self) -> mag_options:
         o = mag_options()
@@ -191,6 +194,7 @@ class Options:
             raise ValueError(f"gmres_matvec must be 'float_float' or 'fp64', not {self.gmres_matvec!r}")
         o.gmres_matvec = 0 if self.gmres_matvec == "float_float" else 1
         o.fp16_gmres = int(self.fp16_gmres)
+        o.batch_shape = int(self.batch_shape)
         return o
 
 
@@ -408,6 +412,7 @@ class Context:
         S.fill_(-1)
         st = self._lib.mag_solve_batch(self._h, D, len(descs), _P(P.data_ptr()), _P(W.data_ptr()),
                                        _P(M.data_ptr()), _P(S.data_ptr()), ctypes.byref(info))
+        self.last_batch_info = info.as_dict()
         # per-problem failures are reported in S; raise only for a call-level error
         if st != MAG_OK and not bool((S == st).any()):
             self._check(st)

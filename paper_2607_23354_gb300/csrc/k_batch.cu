@@ -13,8 +13,10 @@
 //
 // A problem whose FP32 factor meets a non-positive pivot, or whose refinement
 // stalls, is reported in its status and left to the host to re-solve with the
-// single-problem path (which escalates precision).  The block size B is a
-// template parameter chosen by the host-side tuner.
+// single-problem path (which escalates precision).  The factor block is 64;
+// the threads per CTA and the CTAs per SM (kBatchShapes) are template
+// parameters, chosen per batch size class by the host-side tuner
+// (mag_solve_batch).
 #include <algorithm>
 
 #include "mag_internal.cuh"
@@ -24,7 +26,6 @@ namespace mag {
 
 namespace {
 
-constexpr int BT = 512;  // threads per CTA
 
 __device__ __forceinline__ void two_sum_d(double a, double b, double* s, double* e) {
   const double x = a + b;
@@ -72,7 +73,7 @@ struct Scratch {
 
 // FP32 Cholesky of the n x n lower triangle of A (row stride n) in place.
 // Returns false on a non-positive pivot.
-template <int B>
+template <int B, int NT>
 __device__ bool cta_cholesky(float* A, int n, float* sm, int* flag) {
   float* D = sm;                    // [B][B+1] diagonal block
   float* Pi = sm + B * (B + 1);     // [B][B+4] panel block of tile row bi (k-major)
@@ -83,7 +84,7 @@ __device__ bool cta_cholesky(float* A, int n, float* sm, int* flag) {
     const int k0 = kb * B, kw = min(B, n - k0);
     // (a) factor the diagonal block in shared memory (unscaled elimination)
     __syncthreads();
-    for (int e = tid; e < B * B; e += BT) {
+    for (int e = tid; e < B * B; e += NT) {
       const int r = e / B, c = e % B;
       D[r * (B + 1) + c] = (r < kw && c < kw && c <= r) ? A[(int64_t)(k0 + r) * n + k0 + c] : 0.0f;
     }
@@ -92,7 +93,7 @@ __device__ bool cta_cholesky(float* A, int n, float* sm, int* flag) {
       const float p = D[c * (B + 1) + c];
       const float pinv = p > 0.0f ? 1.0f / p : 0.0f;
       const int w = kw - 1 - c;
-      for (int e = tid; e < w * w; e += BT) {
+      for (int e = tid; e < w * w; e += NT) {
         const int r = c + 1 + e / w, cc = c + 1 + e % w;
         if (cc <= r) D[r * (B + 1) + cc] -= D[r * (B + 1) + c] * D[cc * (B + 1) + c] * pinv;
       }
@@ -107,19 +108,19 @@ __device__ bool cta_cholesky(float* A, int n, float* sm, int* flag) {
     __syncthreads();
     if (*flag) return false;
     // scale: L[r][c] = D[r][c] / sqrt(p_c), L[c][c] = sqrt(p_c)
-    for (int e = tid; e < kw * kw; e += BT) {
+    for (int e = tid; e < kw * kw; e += NT) {
       const int r = e / kw, c = e % kw;
       if (c < r) D[r * (B + 1) + c] *= rsqrtf(D[c * (B + 1) + c]);
     }
     __syncthreads();
     if (tid < kw) D[tid * (B + 1) + tid] = sqrtf(D[tid * (B + 1) + tid]);
     __syncthreads();
-    for (int e = tid; e < kw * kw; e += BT) {
+    for (int e = tid; e < kw * kw; e += NT) {
       const int r = e / kw, c = e % kw;
       if (c <= r) A[(int64_t)(k0 + r) * n + k0 + c] = D[r * (B + 1) + c];
     }
     // (b) panel: rows i >= k0 + kw, x L^T = a (forward substitution per row)
-    for (int i = k0 + kw + tid; i < n; i += BT) {
+    for (int i = k0 + kw + tid; i < n; i += NT) {
       float x[B];
       float* row = A + (int64_t)i * n + k0;
 #pragma unroll
@@ -140,55 +141,89 @@ __device__ bool cta_cholesky(float* A, int n, float* sm, int* flag) {
     __syncthreads();
     // (c) trailing update of the lower tiles (bi, bj), kb < bj <= bi.  The
     // panel blocks are staged k-major (PiT[k][r], PjT[k][c], row stride
-    // B + 4) so that a thread's 4 x 2 output tile takes one broadcast float4
-    // and one float2 per k: 3 shared-memory wavefronts per 8 FMAs per warp.
-    static_assert(B == 64, "4 x 2 tiles of 512 threads cover a 64 x 64 block");
+    // B + 4); a thread owns a TR x TC output tile (4 x 2 with 512 threads,
+    // 4 x 4 with 256) and takes one broadcast float4 of PiT and a TC-wide
+    // vector of PjT per k.  The next PjT block is read from global memory
+    // into registers while the current one is in use, and the output block's
+    // entries of A are read before the products, so the products hide both
+    // latencies.
+    constexpr int TR = 4, TC = B * B / (NT * TR), GX = B / TC;
+    static_assert(TR * TC * NT == B * B && GX * TC == B && (NT / GX) * TR == B && (TC == 2 || TC == 4),
+                  "thread tile of the trailing update");
     constexpr int LT = B + 4;
+    constexpr int PER = B * B / NT;  // panel entries a thread stages per block
     float* PiT = Pi;  // [B][LT]
     float* PjT = Pj;  // [B][LT]
-    const int ty = tid >> 5, tx = tid & 31;  // rows 4 ty .. 4 ty + 3, columns 2 tx, 2 tx + 1
+    const int ty = tid / GX, tx = tid % GX;  // rows TR ty .., columns TC tx ..
+    float stage[PER];
+    auto fetch = [&](int r0, int rw) {  // panel rows r0 .. r0 + rw - 1, columns k0 .. k0 + kw - 1
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int e = tid + q * NT, r = e / B, c = e % B;
+        stage[q] = (r < rw && c < kw) ? A[(int64_t)(r0 + r) * n + k0 + c] : 0.0f;
+      }
+    };
+    auto put = [&](float* dstT) {
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int e = tid + q * NT, r = e / B, c = e % B;
+        dstT[c * LT + r] = stage[q];
+      }
+    };
     for (int bi = kb + 1; bi < nb; ++bi) {
       const int i0 = bi * B, iw = min(B, n - i0);
       __syncthreads();
-      for (int e = tid; e < B * B; e += BT) {
-        const int r = e / B, c = e % B;
-        PiT[c * LT + r] = (r < iw && c < kw) ? A[(int64_t)(i0 + r) * n + k0 + c] : 0.0f;
-      }
+      fetch(i0, iw);
+      put(PiT);
+      if (kb + 1 < bi) fetch((kb + 1) * B, B);  // PjT of the first column block
       for (int bj = kb + 1; bj <= bi; ++bj) {
         const int j0 = bj * B, jw = min(B, n - j0);
         __syncthreads();
         if (bj != bi) {
-          for (int e = tid; e < B * B; e += BT) {
-            const int r = e / B, c = e % B;
-            PjT[c * LT + r] = (r < jw && c < kw) ? A[(int64_t)(j0 + r) * n + k0 + c] : 0.0f;
-          }
+          put(PjT);
           __syncthreads();
+          if (bj + 1 < bi) fetch((bj + 1) * B, B);  // in flight during the products below
         }
         const float* QT = bj == bi ? PiT : PjT;
-        float acc[4][2];
+        // the block's entries of A, read ahead of the products
+        float av[TR][TC];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u][0] = acc[u][1] = 0.0f;
+        for (int u = 0; u < TR; ++u)
+#pragma unroll
+          for (int v = 0; v < TC; ++v) {
+            const int r = TR * ty + u, c = TC * tx + v;
+            av[u][v] = (r < iw && c < jw && (bi != bj || c <= r)) ? A[(int64_t)(i0 + r) * n + j0 + c] : 0.0f;
+          }
+        float acc[TR][TC];
+#pragma unroll
+        for (int u = 0; u < TR; ++u)
+#pragma unroll
+          for (int v = 0; v < TC; ++v) acc[u][v] = 0.0f;
 #pragma unroll 8
         for (int k = 0; k < B; ++k) {
-          const float4 a = *reinterpret_cast<const float4*>(PiT + k * LT + 4 * ty);
-          const float2 b = *reinterpret_cast<const float2*>(QT + k * LT + 2 * tx);
-          acc[0][0] = fmaf(a.x, b.x, acc[0][0]);
-          acc[0][1] = fmaf(a.x, b.y, acc[0][1]);
-          acc[1][0] = fmaf(a.y, b.x, acc[1][0]);
-          acc[1][1] = fmaf(a.y, b.y, acc[1][1]);
-          acc[2][0] = fmaf(a.z, b.x, acc[2][0]);
-          acc[2][1] = fmaf(a.z, b.y, acc[2][1]);
-          acc[3][0] = fmaf(a.w, b.x, acc[3][0]);
-          acc[3][1] = fmaf(a.w, b.y, acc[3][1]);
+          const float4 a = *reinterpret_cast<const float4*>(PiT + k * LT + TR * ty);
+          float b[TC];
+          if constexpr (TC == 4) {
+            const float4 b4 = *reinterpret_cast<const float4*>(QT + k * LT + TC * tx);
+            b[0] = b4.x, b[1] = b4.y, b[2] = b4.z, b[3] = b4.w;
+          } else {
+            const float2 b2 = *reinterpret_cast<const float2*>(QT + k * LT + TC * tx);
+            b[0] = b2.x, b[1] = b2.y;
+          }
+          const float ar[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+          for (int u = 0; u < TR; ++u)
+#pragma unroll
+            for (int v = 0; v < TC; ++v) acc[u][v] = fmaf(ar[u], b[v], acc[u][v]);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int r = 4 * ty + u;
+        for (int u = 0; u < TR; ++u) {
+          const int r = TR * ty + u;
           if (r >= iw) continue;
 #pragma unroll
-          for (int v = 0; v < 2; ++v) {
-            const int c = 2 * tx + v;
-            if (c < jw && (bi != bj || c <= r)) A[(int64_t)(i0 + r) * n + j0 + c] -= acc[u][v];
+          for (int v = 0; v < TC; ++v) {
+            const int c = TC * tx + v;
+            if (c < jw && (bi != bj || c <= r)) A[(int64_t)(i0 + r) * n + j0 + c] = av[u][v] - acc[u][v];
           }
         }
       }
@@ -202,7 +237,7 @@ __device__ bool cta_cholesky(float* A, int n, float* sm, int* flag) {
 // solves run in warp 0 column by column: lane l holds rows l and l + 32 of the
 // block's right-hand side; each step divides the pivot row, broadcasts the
 // solved unknown by a shuffle and updates the lanes' remaining rows.
-template <int B>
+template <int B, int NT>
 __device__ void cta_solve(const float* L, int n, float* v, float* sm) {
   static_assert(B == 64, "two rows per lane");
   float* blk = sm;  // [B] block values
@@ -231,8 +266,8 @@ __device__ void cta_solve(const float* L, int n, float* v, float* sm) {
       if (r1 < kw) blk[r1] = y1;
     }
     __syncthreads();
-    for (int e = tid; e < kw; e += BT) v[k0 + e] = blk[e];
-    for (int i = k0 + kw + tid; i < n; i += BT) {
+    for (int e = tid; e < kw; e += NT) v[k0 + e] = blk[e];
+    for (int i = k0 + kw + tid; i < n; i += NT) {
       const float* Li = L + (int64_t)i * n + k0;
       float s = 0.0f;
       for (int c = 0; c < kw; ++c) s += Li[c] * blk[c];
@@ -260,9 +295,9 @@ __device__ void cta_solve(const float* L, int n, float* v, float* sm) {
       if (r1 < kw) blk[r1] = x1;
     }
     __syncthreads();
-    for (int e = tid; e < kw; e += BT) v[k0 + e] = blk[e];
+    for (int e = tid; e < kw; e += NT) v[k0 + e] = blk[e];
     // x_i -= sum_{c in block} L[k0+c][i] x_c for i < k0
-    for (int i = tid; i < k0; i += BT) {
+    for (int i = tid; i < k0; i += NT) {
       float s = 0.0f;
       for (int c = 0; c < kw; ++c) s += L[(int64_t)(k0 + c) * n + i] * blk[c];
       v[i] -= s;
@@ -271,16 +306,16 @@ __device__ void cta_solve(const float* L, int n, float* v, float* sm) {
   __syncthreads();
 }
 
-template <int B>
-__global__ void __launch_bounds__(BT, 1)
+template <int B, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
     k_batch_solve(const BatchProblem* __restrict__ probs, const int* __restrict__ order, int count,
                   const double* __restrict__ D, const int* __restrict__ cloud_flags, float* scratch_f,
                   double* scratch_d, int64_t nmax,
                   double* __restrict__ w_out, double* __restrict__ mag_out, int* __restrict__ status,
-                  int* queue, double tol, int max_iter) {
+                  int* queue, double tol, int max_iter, unsigned long long* busy_cycles) {
   extern __shared__ __align__(16) float smf[];
   __shared__ int s_q, s_flag;
-  __shared__ double red[BT / 32][3];
+  __shared__ double red[NT / 32][3];
   __shared__ double exptab[2 * EXPT_SIZE];
   load_exp_table(exptab);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -290,12 +325,18 @@ __global__ void __launch_bounds__(BT, 1)
   S.Zd = scratch_d + (int64_t)blockIdx.x * (nmax * nmax + 2 * nmax);
   S.w = S.Zd + nmax * nmax;
   S.r = S.w + nmax;
+  const long long t_start = clock64();
   for (;;) {
     __syncthreads();
     if (tid == 0) s_q = atomicAdd(queue, 1);
     __syncthreads();
     const int q = s_q;
-    if (q >= count) break;
+    if (q >= count) {
+      // the tuner's measure: this CTA's busy time (its SM's cycles from the
+      // first problem to the last), summed over CTAs
+      if (tid == 0 && busy_cycles) atomicAdd(busy_cycles, (unsigned long long)(clock64() - t_start));
+      break;
+    }
     const int pid = order[q];
     const BatchProblem P = probs[pid];
     const int n = P.n;
@@ -312,7 +353,7 @@ __global__ void __launch_bounds__(BT, 1)
     // per row, lanes along the row), mirrored into the upper triangle; the
     // row sums of Z (for ||Z||inf) come with the first residual
     double zmax_p = 0.0;
-    for (int i = warp; i < n; i += BT / 32) {
+    for (int i = warp; i < n; i += NT / 32) {
       const double* Di = Dc + (int64_t)i * (i - 1) / 2;
       for (int j = lane; j < i; j += 32) {
         const double z = exp_neg_of(P.t * Di[j], exptab);
@@ -327,12 +368,12 @@ __global__ void __launch_bounds__(BT, 1)
     }
     __syncthreads();
     int st = MAG_BATCH_OK;
-    if (!cta_cholesky<B>(S.Lf, n, smf, &s_flag)) st = MAG_BATCH_NOTPD;
+    if (!cta_cholesky<B, NT>(S.Lf, n, smf, &s_flag)) st = MAG_BATCH_NOTPD;
     double rel = INFINITY;
     if (st == MAG_BATCH_OK) {
-      for (int i = tid; i < n; i += BT) S.v[i] = 1.0f;
-      cta_solve<B>(S.Lf, n, S.v, smf);
-      for (int i = tid; i < n; i += BT) S.w[i] = (double)S.v[i];
+      for (int i = tid; i < n; i += NT) S.v[i] = 1.0f;
+      cta_solve<B, NT>(S.Lf, n, S.v, smf);
+      for (int i = tid; i < n; i += NT) S.w[i] = (double)S.v[i];
       __syncthreads();
       double prev = INFINITY;
       int slow = 0;
@@ -340,7 +381,7 @@ __global__ void __launch_bounds__(BT, 1)
         // r = 1 - Z w (warp per row; per lane FMA chains of 16 terms whose
         // sums are combined with Neumaier compensation, TwoSum across lanes)
         double rmax = 0.0, wmax = 0.0;
-        for (int i = warp; i < n; i += BT / 32) {
+        for (int i = warp; i < n; i += NT / 32) {
           const double* Zi = S.Zd + (int64_t)i * n;
           double s = 0.0, c = 0.0;
           float zs = 0.0f;  // row sum of Z, first pass only (a norm: FP32 is ample)
@@ -385,7 +426,7 @@ __global__ void __launch_bounds__(BT, 1)
         }
         __syncthreads();
         double rn = 0.0, zn = 0.0, wn = 0.0;
-        for (int k = 0; k < BT / 32; ++k) {
+        for (int k = 0; k < NT / 32; ++k) {
           rn = fmax(rn, red[k][0]);
           zn = fmax(zn, red[k][1]);
           wn = fmax(wn, red[k][2]);
@@ -400,15 +441,15 @@ __global__ void __launch_bounds__(BT, 1)
         if (!(rel > 0.5 * prev)) slow = 0;
         prev = rel;
         const double inv = rn > 0.0 ? 1.0 / rn : 0.0;
-        for (int i = tid; i < n; i += BT) S.v[i] = (float)(S.r[i] * inv);
-        cta_solve<B>(S.Lf, n, S.v, smf);
-        for (int i = tid; i < n; i += BT) S.w[i] += rn * (double)S.v[i];
+        for (int i = tid; i < n; i += NT) S.v[i] = (float)(S.r[i] * inv);
+        cta_solve<B, NT>(S.Lf, n, S.v, smf);
+        for (int i = tid; i < n; i += NT) S.w[i] += rn * (double)S.v[i];
         __syncthreads();
       }
     }
     // ---- outputs: w, Mag (compensated), status
     double s = 0.0, c = 0.0;
-    for (int i = tid; i < n; i += BT) {
+    for (int i = tid; i < n; i += NT) {
       const double wi = S.w[i];
       w_out[P.w_offset + i] = wi;
       double hi, lo;
@@ -432,7 +473,7 @@ __global__ void __launch_bounds__(BT, 1)
     __syncthreads();
     if (tid == 0) {
       double ss = 0.0, cc = 0.0;
-      for (int k = 0; k < BT / 32; ++k) {
+      for (int k = 0; k < NT / 32; ++k) {
         double hi, lo;
         two_sum_d(ss, red[k][0], &hi, &lo);
         ss = hi;
@@ -444,19 +485,35 @@ __global__ void __launch_bounds__(BT, 1)
   }
 }
 
-template <int B>
+template <int B, int NT, int MINB>
 cudaError_t launch_batch_t(const BatchProblem* probs, const int* order, int count, const double* D,
                            const int* cloud_flags, float* scratch_f, double* scratch_d, int64_t nmax,
                            double* w_out, double* mag_out, int* status, int* queue, double tol, int max_iter,
-                           int grid, cudaStream_t s) {
+                           int grid, unsigned long long* busy_cycles, cudaStream_t s) {
   const size_t smem = ((size_t)B * (B + 1) + 2 * (size_t)B * (B + 4)) * sizeof(float);
-  auto kern = k_batch_solve<B>;
+  auto kern = k_batch_solve<B, NT, MINB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, BT, smem, s>>>(probs, order, count, D, cloud_flags, scratch_f, scratch_d, nmax, w_out, mag_out,
-                              status, queue, tol, max_iter);
+  kern<<<grid, NT, smem, s>>>(probs, order, count, D, cloud_flags, scratch_f, scratch_d, nmax, w_out, mag_out,
+                              status, queue, tol, max_iter, busy_cycles);
   note_launch();
   return cudaGetLastError();
+}
+
+template <int B, int NT, int MINB>
+int resident_per_sm() {
+  const size_t smem = ((size_t)B * (B + 1) + 2 * (size_t)B * (B + 4)) * sizeof(float);
+  auto kern = k_batch_solve<B, NT, MINB>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NT, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per;
 }
 
 }  // namespace
@@ -470,14 +527,37 @@ cudaError_t launch_batch_dist(const double* X, const BatchCloud* clouds, int ncl
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_solve(int block, const BatchProblem* probs, const int* order, int count,
+// Launch shapes of the batch kernel (factor block 64): threads per CTA and
+// the CTAs per SM the launch bounds are compiled for.
+const BatchShape kBatchShapes[kNumBatchShapes] = {{512, 1}, {256, 2}, {256, 3}};
+
+int batch_shape_resident(int shape) {
+  switch (shape) {
+    case 0: return resident_per_sm<64, 512, 1>();
+    case 1: return resident_per_sm<64, 256, 2>();
+    case 2: return resident_per_sm<64, 256, 3>();
+    default: return 0;
+  }
+}
+
+cudaError_t launch_batch_solve(int shape, const BatchProblem* probs, const int* order, int count,
                                const double* D, const int* cloud_flags, float* scratch_f, double* scratch_d,
                                int64_t nmax, double* w_out, double* mag_out, int* status, int* queue, double tol,
-                               int max_iter, int grid, cudaStream_t s) {
+                               int max_iter, int grid, unsigned long long* busy_cycles, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  (void)block;  // one factor block size (64): the register-tiled trailing update is written for it
-  return launch_batch_t<64>(probs, order, count, D, cloud_flags, scratch_f, scratch_d, nmax, w_out, mag_out,
-                            status, queue, tol, max_iter, grid, s);
+  switch (shape) {
+    case 0:
+      return launch_batch_t<64, 512, 1>(probs, order, count, D, cloud_flags, scratch_f, scratch_d, nmax, w_out,
+                                        mag_out, status, queue, tol, max_iter, grid, busy_cycles, s);
+    case 1:
+      return launch_batch_t<64, 256, 2>(probs, order, count, D, cloud_flags, scratch_f, scratch_d, nmax, w_out,
+                                        mag_out, status, queue, tol, max_iter, grid, busy_cycles, s);
+    case 2:
+      return launch_batch_t<64, 256, 3>(probs, order, count, D, cloud_flags, scratch_f, scratch_d, nmax, w_out,
+                                        mag_out, status, queue, tol, max_iter, grid, busy_cycles, s);
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace mag

@@ -89,7 +89,9 @@ struct mag_ctx {
   double dist_dmin = 0, dist_gersh_unused = 0;
   void* bws = nullptr;               // batch workspace
   size_t bws_bytes = 0;
-  int batch_block = 0;               // tuned factor block of the batch kernel (0 = not tuned)
+  int batch_tuned[12] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};  // launch shape per
+                                     // size class ceil(log2 nmax) of the batch kernel (-1: not tuned)
+  int batch_shape_used = 0;
   UpdMaps maps[2];                   // TMA descriptors of the two panel buffers
   const void* maps_base[2] = {nullptr, nullptr};
   int maps_mode[2] = {-1, -1};
@@ -950,6 +952,7 @@ int mag_options_default(mag_options* opt) {
   opt->host_limit_bytes = 0.0;
   opt->gmres_matvec = 0;
   opt->fp16_gmres = 0;
+  opt->batch_shape = 0;
   return MAG_OK;
 }
 
@@ -2478,15 +2481,33 @@ int mag_solve_batch(mag_ctx* ctx, const mag_batch_desc* desc, int32_t count, con
   std::vector<int> st_host(count, MAG_BATCH_OK);
   if (!small.empty()) {
     std::sort(small.begin(), small.end(), [&](int a, int b) { return probs[a].n > probs[b].n; });
-    const int grid = std::min<int>(ctx->sm_count, (int)small.size());
-    // batch workspace: clouds | problems | order | status | queue | D | scratch_f | scratch_d
+    // launch shape (threads per CTA, CTAs per SM): options.batch_shape, else
+    // the one tuned for this size class, else tuned below on a sample
+    int cls = 0;
+    while ((int64_t)1 << cls < nmax) ++cls;
+    cls = std::min(cls, 11);
+    int grids[kNumBatchShapes];
+    for (int i = 0; i < kNumBatchShapes; ++i)
+      grids[i] = std::min<int>(ctx->sm_count * std::max(1, batch_shape_resident(i)), (int)small.size());
+    int shape = ctx->opt.batch_shape > 0 ? std::min(ctx->opt.batch_shape, kNumBatchShapes) - 1 : ctx->batch_tuned[cls];
+    // tuning needs a batch that fills every shape's grid twice
+    const bool tune = shape < 0 && (int64_t)small.size() >= 2 * (int64_t)grids[kNumBatchShapes - 1] &&
+                      ctx->opt.batch_shape == 0;
+    if (shape < 0 && !tune) shape = 0;
+    int grid = 0;
+    for (int i = 0; i < kNumBatchShapes; ++i)
+      if (tune || i == shape) grid = std::max(grid, grids[i]);
+    // batch workspace: clouds | problems | order | sample order | status | queue (+ tuner cycle count) | D |
+    // scratch_f | scratch_d
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
     const size_t o_cl = take(clouds.size() * sizeof(BatchCloud));
     const size_t o_pr = take((size_t)count * sizeof(BatchProblem));
     const size_t o_or = take(small.size() * sizeof(int));
+    const size_t o_sa = take(small.size() * sizeof(int));
     const size_t o_st = take((size_t)count * sizeof(int));
     const size_t o_q = take(2 * sizeof(int));
+    const size_t o_cy = take(sizeof(unsigned long long));
     const size_t o_cf = take(clouds.size() * sizeof(int));
     const size_t o_d = take((size_t)dist_total * sizeof(double));
     const size_t o_sf = take((size_t)grid * (nmax * nmax + nmax) * sizeof(float));
@@ -2510,8 +2531,10 @@ int mag_solve_batch(mag_ctx* ctx, const mag_batch_desc* desc, int32_t count, con
     BatchCloud* d_cl = (BatchCloud*)(base + o_cl);
     BatchProblem* d_pr = (BatchProblem*)(base + o_pr);
     int* d_or = (int*)(base + o_or);
+    int* d_sa = (int*)(base + o_sa);
     int* d_st = (int*)(base + o_st);
     int* d_q = (int*)(base + o_q);
+    unsigned long long* d_cy = (unsigned long long*)(base + o_cy);
     int* d_cf = (int*)(base + o_cf);
     double* d_D = (double*)(base + o_d);
     float* d_sf = (float*)(base + o_sf);
@@ -2523,11 +2546,43 @@ int mag_solve_batch(mag_ctx* ctx, const mag_batch_desc* desc, int32_t count, con
     CU(launch_batch_dist(points, d_cl, (int)clouds.size(), max_pairs, d_D, d_cf, s));
     const double tol = kStopMargin * ctx->opt.ir_tol;
     const int max_iter = std::max(ctx->opt.ir_max_iters, 1);
-    ctx->batch_block = 64;  // factor block of the batched Cholesky
+    if (tune) {
+      // every k-th problem of the size-sorted order (the batch's size mix),
+      // about twice the largest grid; each shape solves it once.  The measure
+      // is the CTAs' summed busy cycles over the grid -- the time of a batch
+      // whose load balances, as the full one does with several problems per
+      // CTA -- not the sample's makespan, which one large problem can set.
+      // The fastest shape is kept for this size class; the sample's outputs
+      // are overwritten by the full run below.
+      const int64_t want = 2 * (int64_t)grids[kNumBatchShapes - 1];
+      const int64_t stride = std::max<int64_t>(1, (int64_t)small.size() / want);
+      std::vector<int> sample;
+      for (int64_t i = 0; i < (int64_t)small.size() && (int64_t)sample.size() < want; i += stride)
+        sample.push_back(small[i]);
+      CU(cudaMemcpyAsync(d_sa, sample.data(), sample.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+      double best = INFINITY;
+      for (int i = 0; i < kNumBatchShapes; ++i) {
+        const int g = std::min<int>(grids[i], (int)sample.size());
+        CU(cudaMemsetAsync(d_q, 0, sizeof(int), s));
+        CU(cudaMemsetAsync(d_cy, 0, sizeof(unsigned long long), s));
+        CU(launch_batch_solve(i, d_pr, d_sa, (int)sample.size(), d_D, d_cf, d_sf, d_sd, nmax, w_out, mag_out,
+                              d_st, d_q, tol, max_iter, g, d_cy, s));
+        unsigned long long cyc = 0;
+        CU(cudaMemcpyAsync(&cyc, d_cy, sizeof cyc, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        const double est = (double)cyc / g;
+        if (est < best) {
+          best = est;
+          shape = i;
+        }
+      }
+      ctx->batch_tuned[cls] = shape;
+    }
+    ctx->batch_shape_used = shape;
     CU(cudaMemsetAsync(d_q, 0, sizeof(int), s));
     CU(cudaMemsetAsync(d_st, 0, (size_t)count * sizeof(int), s));
-    CU(launch_batch_solve(ctx->batch_block, d_pr, d_or, (int)small.size(), d_D, d_cf, d_sf, d_sd, nmax, w_out,
-                          mag_out, d_st, d_q, tol, max_iter, grid, s));
+    CU(launch_batch_solve(shape, d_pr, d_or, (int)small.size(), d_D, d_cf, d_sf, d_sd, nmax, w_out,
+                          mag_out, d_st, d_q, tol, max_iter, grids[shape], nullptr, s));
     CU(cudaMemcpyAsync(st_host.data(), d_st, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
   }
@@ -2559,7 +2614,8 @@ int mag_solve_batch(mag_ctx* ctx, const mag_batch_desc* desc, int32_t count, con
   if (info) {
     info->fallback = fallbacks;
     info->kernel_launches = g_kernel_launches.load() - l0;
-    info->probes = ctx->batch_block;
+    info->batch_threads = kBatchShapes[ctx->batch_shape_used].threads;
+    info->batch_ctas_per_sm = kBatchShapes[ctx->batch_shape_used].ctas_per_sm;
   }
   return first;
 }

@@ -326,10 +326,20 @@ cudaError_t launch_batch_dist(const double* X, const BatchCloud* clouds, int ncl
                               double* D, int* cloud_flags, cudaStream_t s);
 // block = 32 or 64 (factor block size); scratch_f: grid * (nmax^2 + nmax) floats,
 // scratch_d: grid * (nmax^2 + 2 nmax) doubles; queue: one zeroed int.
-cudaError_t launch_batch_solve(int block, const BatchProblem* probs, const int* order, int count,
+// Launch shapes of k_batch_solve: threads per CTA, CTAs per SM its launch
+// bounds target; batch_shape_resident(i) = CTAs of shape i one SM holds.
+// busy_cycles (or null) receives the sum over CTAs of their busy time in SM
+// cycles (the tuner's measure).
+struct BatchShape {
+  int threads, ctas_per_sm;
+};
+constexpr int kNumBatchShapes = 3;
+extern const BatchShape kBatchShapes[kNumBatchShapes];
+int batch_shape_resident(int shape);
+cudaError_t launch_batch_solve(int shape, const BatchProblem* probs, const int* order, int count,
                                const double* D, const int* cloud_flags, float* scratch_f, double* scratch_d,
                                int64_t nmax, double* w_out, double* mag_out, int* status, int* queue, double tol,
-                               int max_iter, int grid, cudaStream_t s);
+                               int max_iter, int grid, unsigned long long* busy_cycles, cudaStream_t s);
 
 // K7 gradients: dL/dt partial sums and dL/dx.
 cudaError_t launch_grad(const double* X, int64_t n, int m, double t, const double* w,

@@ -412,6 +412,51 @@ def test_batch_config_shape_sample(ctx):
             k += 1
 
 
+@pytest.mark.parametrize("shape,threads,per_sm", [(1, 512, 1), (2, 256, 2), (3, 256, 3)])
+def test_batch_every_launch_shape_matches_oracle(shape, threads, per_sm):
+    # ragged sizes (not multiples of the 64-point factor block, one of 2048)
+    # through each launch shape of the batch kernel
+    rng = np.random.default_rng(400 + shape)
+    clouds = [rng.standard_normal((n, 7)) / 2 for n in (3, 63, 65, 130, 511, 777, 2048)]
+    ts = [0.7, 4.0]
+    c = M.Context(M.Options(batch_shape=shape))
+    ws, mags, sts = c.solve_batch([_dev(x) for x in clouds], ts)
+    info = c.last_batch_info
+    c.close()
+    assert info["batch_threads"] == threads and info["batch_ctas_per_sm"] == per_sm
+    assert int(sts.abs().sum()) == 0
+    k = 0
+    for i, x in enumerate(clouds):
+        for j, t in enumerate(ts):
+            if x.shape[0] <= 777:
+                w_ref, mag_ref, _ = oracle.weighting(x, t)
+                check_solution(x, t, ws[k].cpu().numpy(), mags[i, j].item(), w_ref, mag_ref)
+            else:
+                assert oracle.relative_residual(x, t, ws[k].cpu().numpy()) <= 1e-14
+            k += 1
+
+
+def test_batch_tuner_picks_a_shape():
+    # 130 clouds x 8 t = 1040 problems: at least twice the largest grid
+    # (3 CTAs per SM), so the first call tunes the launch shape on a sample
+    clouds, ts = workloads.batch_clouds(count=130, m=8, n_min=20, n_max=160, n_t=8, seed=9)
+    c = M.Context()
+    ws, mags, sts = c.solve_batch([_dev(x) for x in clouds], list(ts))
+    info = c.last_batch_info
+    ws2, mags2, sts2 = c.solve_batch([_dev(x) for x in clouds], list(ts))
+    info2 = c.last_batch_info
+    c.close()
+    assert (info["batch_threads"], info["batch_ctas_per_sm"]) in {(512, 1), (256, 2), (256, 3)}
+    assert (info2["batch_threads"], info2["batch_ctas_per_sm"]) == (info["batch_threads"], info["batch_ctas_per_sm"])
+    assert int(sts.abs().sum()) == 0 and int(sts2.abs().sum()) == 0
+    assert torch.equal(mags, mags2)
+    for i in range(0, 130, 26):
+        for j in (0, 7):
+            x, t = clouds[i], ts[j]
+            w_ref, mag_ref, _ = oracle.weighting(x, t)
+            check_solution(x, t, ws[i * 8 + j].cpu().numpy(), mags[i, j].item(), w_ref, mag_ref)
+
+
 @pytest.mark.parametrize("prec,resid", [("fp16x3", "stored"), ("fp16x3", "matrix_free"), ("tf32x3", "stored")])
 def test_gmres_ir_finishes_after_refinement_is_cut_short(ctx, prec, resid):
     X = _cloud(1500, 8, seed=61)
