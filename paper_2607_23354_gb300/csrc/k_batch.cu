@@ -240,23 +240,34 @@ __device__ bool cta_cholesky(float* A, int n, float* sm, int* flag) {
 template <int B, int NT>
 __device__ void cta_solve(const float* L, int n, float* v, float* sm) {
   static_assert(B == 64, "two rows per lane");
-  float* blk = sm;  // [B] block values
+  float* blk = sm;                  // [B] block values
+  float* Db = sm + B;               // [B][B+1] the diagonal block of L, staged
   const int tid = threadIdx.x;
   const int nb = (n + B - 1) / B;
+  // the diagonal block of block row kb into shared memory (all threads), so
+  // that warp 0's column-serial solve reads it at shared-memory latency
+  auto stage_diag = [&](int k0, int kw) {
+    for (int e = tid; e < B * B; e += NT) {
+      const int r = e / B, c = e % B;
+      if (r < kw && c <= r) Db[r * (B + 1) + c] = L[(int64_t)(k0 + r) * n + k0 + c];
+    }
+  };
   // forward: L y = v
   for (int kb = 0; kb < nb; ++kb) {
     const int k0 = kb * B, kw = min(B, n - k0);
     __syncthreads();
+    stage_diag(k0, kw);
+    __syncthreads();
     if (tid < 32) {
       const int r0 = tid, r1 = tid + 32;
       float y0 = r0 < kw ? v[k0 + r0] : 0.0f, y1 = r1 < kw ? v[k0 + r1] : 0.0f;
-      const float* L0 = L + (int64_t)(k0 + r0) * n + k0;
-      const float* L1 = L + (int64_t)(k0 + r1) * n + k0;
+      const float* L0 = Db + r0 * (B + 1);
+      const float* L1 = Db + r1 * (B + 1);
       for (int c = 0; c < kw; ++c) {
         // the owner of row c finishes it, then every lane eliminates it
         const float own = c < 32 ? y0 : y1;
         float xc = __shfl_sync(0xffffffffu, own, c & 31);
-        xc /= L[(int64_t)(k0 + c) * n + k0 + c];
+        xc /= Db[c * (B + 1) + c];
         if (r0 == c) y0 = xc;
         if (r1 == c) y1 = xc;
         if (r0 > c && r0 < kw) y0 -= L0[c] * xc;
@@ -278,13 +289,15 @@ __device__ void cta_solve(const float* L, int n, float* v, float* sm) {
   for (int kb = nb - 1; kb >= 0; --kb) {
     const int k0 = kb * B, kw = min(B, n - k0);
     __syncthreads();
+    stage_diag(k0, kw);
+    __syncthreads();
     if (tid < 32) {
       const int r0 = tid, r1 = tid + 32;
       float x0 = r0 < kw ? v[k0 + r0] : 0.0f, x1 = r1 < kw ? v[k0 + r1] : 0.0f;
       for (int c = kw - 1; c >= 0; --c) {
         const float own = c < 32 ? x0 : x1;
         float xc = __shfl_sync(0xffffffffu, own, c & 31);
-        const float* Lc = L + (int64_t)(k0 + c) * n + k0;  // row c: L[c][r] for r < c
+        const float* Lc = Db + c * (B + 1);  // row c: L[c][r] for r < c
         xc /= Lc[c];
         if (r0 == c) x0 = xc;
         if (r1 == c) x1 = xc;
@@ -351,12 +364,16 @@ __global__ void __launch_bounds__(NT, MINB)
     const double* Dc = D + P.dist_offset;
     // ---- Z: FP64 full square and FP32 lower, one exp per pair j < i (warp
     // per row, lanes along the row), mirrored into the upper triangle; the
-    // row sums of Z (for ||Z||inf) come with the first residual
+    // row sums of Z (for ||Z||inf) come with the first residual.  Entries
+    // below e^-46 in FP32 (exp_neg_tiny), as the single-problem solver does.
+    const unsigned long long tiny_bits = (unsigned long long)__double_as_longlong(kTinyArg);
     double zmax_p = 0.0;
     for (int i = warp; i < n; i += NT / 32) {
       const double* Di = Dc + (int64_t)i * (i - 1) / 2;
       for (int j = lane; j < i; j += 32) {
-        const double z = exp_neg_of(P.t * Di[j], exptab);
+        const double a = P.t * Di[j];
+        const double z = (unsigned long long)__double_as_longlong(a) > tiny_bits ? (double)exp_neg_tiny(a)
+                                                                                  : exp_neg_small(a, exptab);
         S.Zd[(int64_t)i * n + j] = z;
         S.Zd[(int64_t)j * n + i] = z;
         S.Lf[(int64_t)i * n + j] = f64_to_f32_nonneg(z);
@@ -379,7 +396,11 @@ __global__ void __launch_bounds__(NT, MINB)
       int slow = 0;
       for (int it = 0;; ++it) {
         // r = 1 - Z w (warp per row; per lane FMA chains of 16 terms whose
-        // sums are combined with Neumaier compensation, TwoSum across lanes)
+        // sums are combined with Neumaier compensation, then a plain lane
+        // tree: each lane total is within the chains' 16 u of its part of
+        // sum |z w|, the tree adds at most 5 u -- both far below the
+        // tolerance -- and GB300's FP64 pipe makes a compensated tree (8
+        // FP64 operations per level) the bulk of a small row's cost)
         double rmax = 0.0, wmax = 0.0;
         for (int i = warp; i < n; i += NT / 32) {
           const double* Zi = S.Zd + (int64_t)i * n;
@@ -393,23 +414,17 @@ __global__ void __launch_bounds__(NT, MINB)
               if (j < n) {
                 const double z = Zi[j];
                 part = fma(z, S.w[j], part);
-                if (it == 0) zs += (float)z;
+                if (it == 0) zs += f64_to_f32_nonneg(z);  // integer pipe
               }
             }
             const double tt = s + part;
             c += fabs(s) >= fabs(part) ? (s - tt) + part : (part - tt) + s;
             s = tt;
           }
+          double tot = s + c;
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            double hi, lo;
-            const double other = __shfl_xor_sync(0xffffffffu, s, o);
-            const double oc = __shfl_xor_sync(0xffffffffu, c, o);
-            two_sum_d(s, other, &hi, &lo);
-            s = hi;
-            c += oc + lo;
-          }
-          const double ri = (1.0 - s) - c;
+          for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+          const double ri = 1.0 - tot;
           if (lane == 0) S.r[i] = ri;
           rmax = fmax(rmax, fabs(ri));
           wmax = fmax(wmax, fabs(S.w[i]));
