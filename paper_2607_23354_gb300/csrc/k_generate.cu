@@ -8,8 +8,11 @@
 // FP64 d^2; the FP64 tile (FP64 factor or stored residual) takes them in FP64.
 //
 // Thread layout (512 threads): warp w handles tile rows w + 16 i (i < 8),
-// lane l handles tile columns l + 32 q (q < 4), so each store instruction of
-// a warp writes 32 consecutive elements of one tile row (128 B for FP32).
+// lane l handles tile columns 4 l + q (q < 4), so each thread stores its four
+// entries of a row with one 16-byte store (FP32: a float4; FP64: two
+// double2) and a warp's stores cover one whole tile row.  The column points
+// are staged in shared memory with column 4 l + q at position 32 q + l, so
+// the distance loop's reads stay conflict free.
 //
 // Side outputs, all fused: full row sums of Z (for ||Z||inf and the Gershgorin
 // bound used to choose the factor precision), min off-diagonal d^2 (the Sec. 1
@@ -61,7 +64,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
       const int r = e / mc, l = e - r * mc;
       const int64_t gr = row0 + r, gc = col0 + r;
       xr[r * GEN_MC + l] = gr < n ? X[gr * m + l0 + l] : 0.0;
-      xc[l * TILE + r] = gc < n ? X[gc * m + l0 + l] : 0.0;
+      xc[l * TILE + 32 * (r & 3) + (r >> 2)] = gc < n ? X[gc * m + l0 + l] : 0.0;
     }
     __syncthreads();
     for (int l = 0; l < mc; ++l) {
@@ -69,7 +72,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
 #pragma unroll
       for (int i = 0; i < 8; ++i) a[i] = xr[(warp + 16 * i) * GEN_MC + l];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) b[q] = xc[l * TILE + lane + 32 * q];
+      for (int q = 0; q < 4; ++q) b[q] = xc[l * TILE + 32 * q + lane];  // column 4 lane + q
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -100,9 +103,11 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
   for (int i = 0; i < 8; ++i) {
     const int r = warp + 16 * i;
     const int64_t gr = row0 + r;
+    float zfv[4];
+    double zdv[4], ddv[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int c = lane + 32 * q;
+      const int c = 4 * lane + q;
       const int64_t gc = col0 + c;
       const double v = d2[i][q];
       double zd = 0.0, dd = 0.0;
@@ -130,14 +135,25 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
                                                                    : fmaf((float)kc, expm1f(-tf * sqrtf((float)v)), 1.0f)));
         }
       }
-      if (WF) Zf[tile_off + (int64_t)r * TILE + c] = zf;
-      if (WD) Zd[tile_off + (int64_t)r * TILE + c] = zd;
-      if (WDIST) Dd[tile_off + (int64_t)r * TILE + c] = dd;
+      zfv[q] = zf;
+      zdv[q] = zd;
+      ddv[q] = dd;
       if (ROWSUM && gr < n && gc < n) {
         const float zs = WF ? zf : (float)zd;
         rs[i] += zs;
         cs[q] += zs;
       }
+    }
+    // the four entries of row r, columns 4 lane .. 4 lane + 3: 16-byte stores
+    const int64_t e = tile_off + (int64_t)r * TILE + 4 * lane;
+    if (WF) *reinterpret_cast<float4*>(Zf + e) = make_float4(zfv[0], zfv[1], zfv[2], zfv[3]);
+    if (WD) {
+      *reinterpret_cast<double2*>(Zd + e) = make_double2(zdv[0], zdv[1]);
+      *reinterpret_cast<double2*>(Zd + e + 2) = make_double2(zdv[2], zdv[3]);
+    }
+    if (WDIST) {
+      *reinterpret_cast<double2*>(Dd + e) = make_double2(ddv[0], ddv[1]);
+      *reinterpret_cast<double2*>(Dd + e + 2) = make_double2(ddv[2], ddv[3]);
     }
   }
 
@@ -162,7 +178,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
       if (lane == 0 && gr < n) atomicAdd(rowsum + gr, (double)v);
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) colpart[warp][lane + 32 * q] = (double)cs[q];
+    for (int q = 0; q < 4; ++q) colpart[warp][4 * lane + q] = (double)cs[q];
   }
   __syncthreads();
   if (ROWSUM && I != J && threadIdx.x < TILE) {
@@ -179,7 +195,8 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
 }
 
 // Z from stored FP64 distances (same layout): one CTA per lower tile, FP64
-// exp only.  Tiles of the padding get the identity, as in k_generate.
+// exp only, 16-byte reads and stores (lane l: columns 4 l .. 4 l + 3).
+// Tiles of the padding get the identity, as in k_generate.
 template <bool WF, bool WD>
 __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __restrict__ Dd, int64_t n, double t,
                                                             float* __restrict__ Zf, double* __restrict__ Zd,
@@ -201,11 +218,18 @@ __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __rest
     const int r = warp * 16 + i;
     const int64_t gr = I * TILE + r;
     float rs = 0.0f;
+    // lane: columns 4 lane .. 4 lane + 3 of row r, read and written with
+    // 16-byte accesses
+    const int64_t e0 = off + (int64_t)r * TILE + 4 * lane;
+    const double2 d01 = *reinterpret_cast<const double2*>(Dd + e0);
+    const double2 d23 = *reinterpret_cast<const double2*>(Dd + e0 + 2);
+    const double dv[4] = {d01.x, d01.y, d23.x, d23.y};
+    float zfv[4];
+    double zdv[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int c = lane + 32 * q;
+      const int c = 4 * lane + q;
       const int64_t gc = J * TILE + c;
-      const int64_t e = off + (int64_t)r * TILE + c;
       double zd;
       float zf;
       if (gr >= n || gc >= n || gr == gc) {
@@ -213,7 +237,7 @@ __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __rest
         zf = (float)zd;
         if (gr == gc && gr < n) rs += 1.0f;  // the diagonal counts in its row sum
       } else {
-        const double d = Dd[e];
+        const double d = dv[q];
         if (WD && !kind && (unsigned long long)__double_as_longlong(d) > tiny_bits) {
           zf = exp_neg_tiny(t * d);
           zd = (double)zf;
@@ -227,15 +251,20 @@ __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __rest
         rs += zf;
         cs[q] += zf;
       }
-      if (WF) Zf[e] = zf;
-      if (WD) Zd[e] = zd;
+      zfv[q] = zf;
+      zdv[q] = zd;
+    }
+    if (WF) *reinterpret_cast<float4*>(Zf + e0) = make_float4(zfv[0], zfv[1], zfv[2], zfv[3]);
+    if (WD) {
+      *reinterpret_cast<double2*>(Zd + e0) = make_double2(zdv[0], zdv[1]);
+      *reinterpret_cast<double2*>(Zd + e0 + 2) = make_double2(zdv[2], zdv[3]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
     if (lane == 0 && gr < n) atomicAdd(rowsum + gr, (double)rs);
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) colpart[warp][lane + 32 * q] = cs[q];
+  for (int q = 0; q < 4; ++q) colpart[warp][4 * lane + q] = cs[q];
   __syncthreads();
   if (I != J && threadIdx.x < TILE) {
     double v = 0.0;
