@@ -175,7 +175,11 @@ typedef struct mag_options {
                              sample of the batch once, the fastest is kept
                              (smaller batches use shape 1 until then); 1:
                              512 threads x 1 CTA per SM, 2: 256 x 2, 3: 256
-                             x 3 (mag_info.batch_threads / _ctas_per_sm)    */
+                             x 3, all with the factor's trailing update on
+                             the CUDA cores in FP32; 4: 256 x 2, 5: 256 x 3
+                             with it on the tensor cores in split TF32
+                             (mag_info.batch_threads / _ctas_per_sm /
+                             _tensor_cores)                                  */
   int32_t reserved3;
 } mag_options;
 
@@ -239,7 +243,10 @@ typedef struct mag_info {
                               look-ahead streams overlap, so ms_update, a sum
                               of intervals, counts shared stretches twice    */
   int32_t batch_threads;   /* mag_solve_batch: threads per CTA of the launch   */
-  int32_t batch_ctas_per_sm; /* ... and the CTAs per SM of its shape          */
+  int32_t batch_ctas_per_sm; /* ... the CTAs per SM of its shape              */
+  int32_t batch_tensor_cores; /* ... 1: the factor's trailing update on the
+                              tensor cores (split TF32), 0: CUDA cores      */
+  int32_t reserved4;
 } mag_info;
 
 typedef struct mag_ctx mag_ctx;

@@ -72,7 +72,8 @@ class mag_info(ctypes.Structure):
                 ("host_read_bytes", ctypes.c_double), ("ms_host_read", ctypes.c_double),
                 ("deflation_c", ctypes.c_double), ("factor_reused", ctypes.c_int32),
                 ("reserved2", ctypes.c_int32), ("ms_update_busy", ctypes.c_double),
-                ("batch_threads", ctypes.c_int32), ("batch_ctas_per_sm", ctypes.c_int32)]
+                ("batch_threads", ctypes.c_int32), ("batch_ctas_per_sm", ctypes.c_int32),
+                ("batch_tensor_cores", ctypes.c_int32), ("reserved4", ctypes.c_int32)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -166,7 +167,7 @@ class Options:
     host_limit_bytes: float = 0.0
     gmres_matvec: str = "float_float"  # or "fp64"
     fp16_gmres: int = 0
-    batch_shape: int = 0  # 0 tuned, 1..3 fixed
+    batch_shape: int = 0  # 0 tuned, 1..5 fixed
 
     def to_c(self) -> mag_options:
         o = mag_options()

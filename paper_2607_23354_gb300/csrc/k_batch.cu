@@ -73,7 +73,29 @@ struct Scratch {
 
 // FP32 Cholesky of the n x n lower triangle of A (row stride n) in place.
 // Returns false on a non-positive pivot.
-template <int B, int NT>
+// TF32 split: hi = a rounded to TF32 (10 mantissa bits), lo = the rest
+// rounded to TF32; hi*hi + hi*lo + lo*hi recovers the product to about
+// 2^-22 relative.
+__device__ __forceinline__ void split_tf32(float a, uint32_t* hi, uint32_t* lo) {
+  uint32_t h, l;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(a));
+  const float rest = a - __uint_as_float(h);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(rest));
+  *hi = h;
+  *lo = l;
+}
+
+// d += a b for one m16n8k8 TF32 tile (A row-major 16 x 8, B 8 x 8 column
+// fragments, FP32 accumulators; the PTX fragment layout).
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int B, int NT, bool MMA>
 __device__ bool cta_cholesky(float* A, int n, float* sm, int* flag) {
   float* D = sm;                    // [B][B+1] diagonal block
   float* Pi = sm + B * (B + 1);     // [B][B+4] panel block of tile row bi (k-major)
@@ -139,22 +161,23 @@ __device__ bool cta_cholesky(float* A, int n, float* sm, int* flag) {
         if (c < kw) row[c] = x[c];
     }
     __syncthreads();
-    // (c) trailing update of the lower tiles (bi, bj), kb < bj <= bi.  The
-    // panel blocks are staged k-major (PiT[k][r], PjT[k][c], row stride
-    // B + 4); a thread owns a TR x TC output tile (4 x 2 with 512 threads,
-    // 4 x 4 with 256) and takes one broadcast float4 of PiT and a TC-wide
-    // vector of PjT per k.  The next PjT block is read from global memory
-    // into registers while the current one is in use, and the output block's
-    // entries of A are read before the products, so the products hide both
-    // latencies.
-    constexpr int TR = 4, TC = B * B / (NT * TR), GX = B / TC;
-    static_assert(TR * TC * NT == B * B && GX * TC == B && (NT / GX) * TR == B && (TC == 2 || TC == 4),
-                  "thread tile of the trailing update");
+    // (c) trailing update of the lower tiles (bi, bj), kb < bj <= bi.  CUDA
+    // cores (MMA false): the panel blocks are staged k-major (PiT[k][r],
+    // PjT[k][c], row stride B + 4); a thread owns a TR x TC output tile (4 x 2
+    // with 512 threads, 4 x 4 with 256) and takes one broadcast float4 of PiT
+    // and a TC-wide vector of PjT per k.  Tensor cores (MMA true): the blocks
+    // are staged row-major (row stride B + 4, so that the fragment reads
+    // below are free of bank conflicts), each warp owns 16 rows x (8 NTW)
+    // columns of the output and runs mma.sync m16n8k8 TF32 on split
+    // operands (a = a_hi + a_lo, hi*hi + hi*lo + lo*hi: the FP32-class
+    // product, error about 2^-22 of |a||b|).  Both: the next panel block is
+    // read from global memory into registers while the current one is in
+    // use, and the output block's entries of A are read before the products,
+    // so the products hide both latencies.
     constexpr int LT = B + 4;
     constexpr int PER = B * B / NT;  // panel entries a thread stages per block
     float* PiT = Pi;  // [B][LT]
     float* PjT = Pj;  // [B][LT]
-    const int ty = tid / GX, tx = tid % GX;  // rows TR ty .., columns TC tx ..
     float stage[PER];
     auto fetch = [&](int r0, int rw) {  // panel rows r0 .. r0 + rw - 1, columns k0 .. k0 + kw - 1
 #pragma unroll
@@ -163,11 +186,14 @@ __device__ bool cta_cholesky(float* A, int n, float* sm, int* flag) {
         stage[q] = (r < rw && c < kw) ? A[(int64_t)(r0 + r) * n + k0 + c] : 0.0f;
       }
     };
-    auto put = [&](float* dstT) {
+    auto put = [&](float* dst) {
 #pragma unroll
       for (int q = 0; q < PER; ++q) {
         const int e = tid + q * NT, r = e / B, c = e % B;
-        dstT[c * LT + r] = stage[q];
+        if constexpr (MMA)
+          dst[r * LT + c] = stage[q];
+        else
+          dst[c * LT + r] = stage[q];
       }
     };
     for (int bi = kb + 1; bi < nb; ++bi) {
@@ -185,45 +211,94 @@ __device__ bool cta_cholesky(float* A, int n, float* sm, int* flag) {
           if (bj + 1 < bi) fetch((bj + 1) * B, B);  // in flight during the products below
         }
         const float* QT = bj == bi ? PiT : PjT;
-        // the block's entries of A, read ahead of the products
-        float av[TR][TC];
+        if constexpr (MMA) {
+          static_assert(B == 64 && NT % 128 == 0 && NT <= 512, "warp tiles of the tensor-core update");
+          constexpr int W = NT / 32, NTW = 32 / W;  // n8 tiles per warp
+          const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
+          const int rw0 = 16 * (warp & 3), cw0 = (warp >> 2) * 8 * NTW;
+          // the block's entries of A at the accumulator positions, read ahead
+          float av[NTW][4];
 #pragma unroll
-        for (int u = 0; u < TR; ++u)
+          for (int j = 0; j < NTW; ++j)
 #pragma unroll
-          for (int v = 0; v < TC; ++v) {
-            const int r = TR * ty + u, c = TC * tx + v;
-            av[u][v] = (r < iw && c < jw && (bi != bj || c <= r)) ? A[(int64_t)(i0 + r) * n + j0 + c] : 0.0f;
+            for (int h = 0; h < 4; ++h) {
+              const int r = rw0 + g + 8 * (h >> 1), c = cw0 + 8 * j + 2 * tq + (h & 1);
+              av[j][h] = (r < iw && c < jw && (bi != bj || c <= r)) ? A[(int64_t)(i0 + r) * n + j0 + c] : 0.0f;
+            }
+          float acc[NTW][4];
+#pragma unroll
+          for (int j = 0; j < NTW; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+#pragma unroll 2
+          for (int kk = 0; kk < B / 8; ++kk) {
+            const int kc = 8 * kk + tq;
+            const float ar[4] = {PiT[(rw0 + g) * LT + kc], PiT[(rw0 + g + 8) * LT + kc], PiT[(rw0 + g) * LT + kc + 4],
+                                 PiT[(rw0 + g + 8) * LT + kc + 4]};
+            uint32_t ahi[4], alo[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) split_tf32(ar[h], &ahi[h], &alo[h]);
+#pragma unroll
+            for (int j = 0; j < NTW; ++j) {
+              const int nn = cw0 + 8 * j + g;
+              uint32_t bhi[2], blo[2];
+              split_tf32(QT[nn * LT + kc], &bhi[0], &blo[0]);
+              split_tf32(QT[nn * LT + kc + 4], &bhi[1], &blo[1]);
+              mma_tf32(acc[j], ahi, bhi);
+              mma_tf32(acc[j], ahi, blo);
+              mma_tf32(acc[j], alo, bhi);
+            }
           }
-        float acc[TR][TC];
 #pragma unroll
-        for (int u = 0; u < TR; ++u)
+          for (int j = 0; j < NTW; ++j)
 #pragma unroll
-          for (int v = 0; v < TC; ++v) acc[u][v] = 0.0f;
-#pragma unroll 8
-        for (int k = 0; k < B; ++k) {
-          const float4 a = *reinterpret_cast<const float4*>(PiT + k * LT + TR * ty);
-          float b[TC];
-          if constexpr (TC == 4) {
-            const float4 b4 = *reinterpret_cast<const float4*>(QT + k * LT + TC * tx);
-            b[0] = b4.x, b[1] = b4.y, b[2] = b4.z, b[3] = b4.w;
-          } else {
-            const float2 b2 = *reinterpret_cast<const float2*>(QT + k * LT + TC * tx);
-            b[0] = b2.x, b[1] = b2.y;
-          }
-          const float ar[4] = {a.x, a.y, a.z, a.w};
+            for (int h = 0; h < 4; ++h) {
+              const int r = rw0 + g + 8 * (h >> 1), c = cw0 + 8 * j + 2 * tq + (h & 1);
+              if (r < iw && c < jw && (bi != bj || c <= r)) A[(int64_t)(i0 + r) * n + j0 + c] = av[j][h] - acc[j][h];
+            }
+        } else {
+          constexpr int TR = 4, TC = B * B / (NT * TR), GX = B / TC;
+          static_assert(TR * TC * NT == B * B && GX * TC == B && (NT / GX) * TR == B && (TC == 2 || TC == 4),
+                        "thread tile of the trailing update");
+          const int ty = tid / GX, tx = tid % GX;  // rows TR ty .., columns TC tx ..
+          // the block's entries of A, read ahead of the products
+          float av[TR][TC];
 #pragma unroll
           for (int u = 0; u < TR; ++u)
 #pragma unroll
-            for (int v = 0; v < TC; ++v) acc[u][v] = fmaf(ar[u], b[v], acc[u][v]);
-        }
+            for (int v = 0; v < TC; ++v) {
+              const int r = TR * ty + u, c = TC * tx + v;
+              av[u][v] = (r < iw && c < jw && (bi != bj || c <= r)) ? A[(int64_t)(i0 + r) * n + j0 + c] : 0.0f;
+            }
+          float acc[TR][TC];
 #pragma unroll
-        for (int u = 0; u < TR; ++u) {
-          const int r = TR * ty + u;
-          if (r >= iw) continue;
+          for (int u = 0; u < TR; ++u)
 #pragma unroll
-          for (int v = 0; v < TC; ++v) {
-            const int c = TC * tx + v;
-            if (c < jw && (bi != bj || c <= r)) A[(int64_t)(i0 + r) * n + j0 + c] = av[u][v] - acc[u][v];
+            for (int v = 0; v < TC; ++v) acc[u][v] = 0.0f;
+#pragma unroll 8
+          for (int k = 0; k < B; ++k) {
+            const float4 a = *reinterpret_cast<const float4*>(PiT + k * LT + TR * ty);
+            float b[TC];
+            if constexpr (TC == 4) {
+              const float4 b4 = *reinterpret_cast<const float4*>(QT + k * LT + TC * tx);
+              b[0] = b4.x, b[1] = b4.y, b[2] = b4.z, b[3] = b4.w;
+            } else {
+              const float2 b2 = *reinterpret_cast<const float2*>(QT + k * LT + TC * tx);
+              b[0] = b2.x, b[1] = b2.y;
+            }
+            const float ar[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+            for (int u = 0; u < TR; ++u)
+#pragma unroll
+              for (int v = 0; v < TC; ++v) acc[u][v] = fmaf(ar[u], b[v], acc[u][v]);
+          }
+#pragma unroll
+          for (int u = 0; u < TR; ++u) {
+            const int r = TR * ty + u;
+            if (r >= iw) continue;
+#pragma unroll
+            for (int v = 0; v < TC; ++v) {
+              const int c = TC * tx + v;
+              if (c < jw && (bi != bj || c <= r)) A[(int64_t)(i0 + r) * n + j0 + c] = av[u][v] - acc[u][v];
+            }
           }
         }
       }
@@ -319,7 +394,7 @@ __device__ void cta_solve(const float* L, int n, float* v, float* sm) {
   __syncthreads();
 }
 
-template <int B, int NT, int MINB>
+template <int B, int NT, int MINB, bool MMA>
 __global__ void __launch_bounds__(NT, MINB)
     k_batch_solve(const BatchProblem* __restrict__ probs, const int* __restrict__ order, int count,
                   const double* __restrict__ D, const int* __restrict__ cloud_flags, float* scratch_f,
@@ -385,7 +460,7 @@ __global__ void __launch_bounds__(NT, MINB)
     }
     __syncthreads();
     int st = MAG_BATCH_OK;
-    if (!cta_cholesky<B, NT>(S.Lf, n, smf, &s_flag)) st = MAG_BATCH_NOTPD;
+    if (!cta_cholesky<B, NT, MMA>(S.Lf, n, smf, &s_flag)) st = MAG_BATCH_NOTPD;
     double rel = INFINITY;
     if (st == MAG_BATCH_OK) {
       for (int i = tid; i < n; i += NT) S.v[i] = 1.0f;
@@ -500,13 +575,13 @@ __global__ void __launch_bounds__(NT, MINB)
   }
 }
 
-template <int B, int NT, int MINB>
+template <int B, int NT, int MINB, bool MMA>
 cudaError_t launch_batch_t(const BatchProblem* probs, const int* order, int count, const double* D,
                            const int* cloud_flags, float* scratch_f, double* scratch_d, int64_t nmax,
                            double* w_out, double* mag_out, int* status, int* queue, double tol, int max_iter,
                            int grid, unsigned long long* busy_cycles, cudaStream_t s) {
   const size_t smem = ((size_t)B * (B + 1) + 2 * (size_t)B * (B + 4)) * sizeof(float);
-  auto kern = k_batch_solve<B, NT, MINB>;
+  auto kern = k_batch_solve<B, NT, MINB, MMA>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, NT, smem, s>>>(probs, order, count, D, cloud_flags, scratch_f, scratch_d, nmax, w_out, mag_out,
@@ -515,10 +590,10 @@ cudaError_t launch_batch_t(const BatchProblem* probs, const int* order, int coun
   return cudaGetLastError();
 }
 
-template <int B, int NT, int MINB>
+template <int B, int NT, int MINB, bool MMA>
 int resident_per_sm() {
   const size_t smem = ((size_t)B * (B + 1) + 2 * (size_t)B * (B + 4)) * sizeof(float);
-  auto kern = k_batch_solve<B, NT, MINB>;
+  auto kern = k_batch_solve<B, NT, MINB, MMA>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -542,15 +617,18 @@ cudaError_t launch_batch_dist(const double* X, const BatchCloud* clouds, int ncl
   return cudaGetLastError();
 }
 
-// Launch shapes of the batch kernel (factor block 64): threads per CTA and
-// the CTAs per SM the launch bounds are compiled for.
-const BatchShape kBatchShapes[kNumBatchShapes] = {{512, 1}, {256, 2}, {256, 3}};
+// Launch shapes of the batch kernel (factor block 64): threads per CTA, the
+// CTAs per SM the launch bounds are compiled for, and the trailing update on
+// CUDA cores (FP32) or on the tensor cores (split TF32, mma.sync).
+const BatchShape kBatchShapes[kNumBatchShapes] = {{512, 1, 0}, {256, 2, 0}, {256, 3, 0}, {256, 2, 1}, {256, 3, 1}};
 
 int batch_shape_resident(int shape) {
   switch (shape) {
-    case 0: return resident_per_sm<64, 512, 1>();
-    case 1: return resident_per_sm<64, 256, 2>();
-    case 2: return resident_per_sm<64, 256, 3>();
+    case 0: return resident_per_sm<64, 512, 1, false>();
+    case 1: return resident_per_sm<64, 256, 2, false>();
+    case 2: return resident_per_sm<64, 256, 3, false>();
+    case 3: return resident_per_sm<64, 256, 2, true>();
+    case 4: return resident_per_sm<64, 256, 3, true>();
     default: return 0;
   }
 }
@@ -560,19 +638,18 @@ cudaError_t launch_batch_solve(int shape, const BatchProblem* probs, const int* 
                                int64_t nmax, double* w_out, double* mag_out, int* status, int* queue, double tol,
                                int max_iter, int grid, unsigned long long* busy_cycles, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
+#define MAG_BATCH_LAUNCH(NT_, MINB_, MMA_)                                                                  \
+  return launch_batch_t<64, NT_, MINB_, MMA_>(probs, order, count, D, cloud_flags, scratch_f, scratch_d, nmax, \
+                                               w_out, mag_out, status, queue, tol, max_iter, grid, busy_cycles, s)
   switch (shape) {
-    case 0:
-      return launch_batch_t<64, 512, 1>(probs, order, count, D, cloud_flags, scratch_f, scratch_d, nmax, w_out,
-                                        mag_out, status, queue, tol, max_iter, grid, busy_cycles, s);
-    case 1:
-      return launch_batch_t<64, 256, 2>(probs, order, count, D, cloud_flags, scratch_f, scratch_d, nmax, w_out,
-                                        mag_out, status, queue, tol, max_iter, grid, busy_cycles, s);
-    case 2:
-      return launch_batch_t<64, 256, 3>(probs, order, count, D, cloud_flags, scratch_f, scratch_d, nmax, w_out,
-                                        mag_out, status, queue, tol, max_iter, grid, busy_cycles, s);
-    default:
-      return cudaErrorInvalidValue;
+    case 0: MAG_BATCH_LAUNCH(512, 1, false);
+    case 1: MAG_BATCH_LAUNCH(256, 2, false);
+    case 2: MAG_BATCH_LAUNCH(256, 3, false);
+    case 3: MAG_BATCH_LAUNCH(256, 2, true);
+    case 4: MAG_BATCH_LAUNCH(256, 3, true);
+    default: return cudaErrorInvalidValue;
   }
+#undef MAG_BATCH_LAUNCH
 }
 
 }  // namespace mag

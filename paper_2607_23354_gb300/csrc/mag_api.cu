@@ -2490,9 +2490,9 @@ int mag_solve_batch(mag_ctx* ctx, const mag_batch_desc* desc, int32_t count, con
     for (int i = 0; i < kNumBatchShapes; ++i)
       grids[i] = std::min<int>(ctx->sm_count * std::max(1, batch_shape_resident(i)), (int)small.size());
     int shape = ctx->opt.batch_shape > 0 ? std::min(ctx->opt.batch_shape, kNumBatchShapes) - 1 : ctx->batch_tuned[cls];
+    const int maxgrid = *std::max_element(grids, grids + kNumBatchShapes);
     // tuning needs a batch that fills every shape's grid twice
-    const bool tune = shape < 0 && (int64_t)small.size() >= 2 * (int64_t)grids[kNumBatchShapes - 1] &&
-                      ctx->opt.batch_shape == 0;
+    const bool tune = shape < 0 && (int64_t)small.size() >= 2 * (int64_t)maxgrid && ctx->opt.batch_shape == 0;
     if (shape < 0 && !tune) shape = 0;
     int grid = 0;
     for (int i = 0; i < kNumBatchShapes; ++i)
@@ -2554,7 +2554,7 @@ int mag_solve_batch(mag_ctx* ctx, const mag_batch_desc* desc, int32_t count, con
       // CTA -- not the sample's makespan, which one large problem can set.
       // The fastest shape is kept for this size class; the sample's outputs
       // are overwritten by the full run below.
-      const int64_t want = 2 * (int64_t)grids[kNumBatchShapes - 1];
+      const int64_t want = 2 * (int64_t)maxgrid;
       const int64_t stride = std::max<int64_t>(1, (int64_t)small.size() / want);
       std::vector<int> sample;
       for (int64_t i = 0; i < (int64_t)small.size() && (int64_t)sample.size() < want; i += stride)
@@ -2616,6 +2616,7 @@ int mag_solve_batch(mag_ctx* ctx, const mag_batch_desc* desc, int32_t count, con
     info->kernel_launches = g_kernel_launches.load() - l0;
     info->batch_threads = kBatchShapes[ctx->batch_shape_used].threads;
     info->batch_ctas_per_sm = kBatchShapes[ctx->batch_shape_used].ctas_per_sm;
+    info->batch_tensor_cores = kBatchShapes[ctx->batch_shape_used].tensor_cores;
   }
   return first;
 }

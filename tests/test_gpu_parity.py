@@ -412,8 +412,9 @@ def test_batch_config_shape_sample(ctx):
             k += 1
 
 
-@pytest.mark.parametrize("shape,threads,per_sm", [(1, 512, 1), (2, 256, 2), (3, 256, 3)])
-def test_batch_every_launch_shape_matches_oracle(shape, threads, per_sm):
+@pytest.mark.parametrize("shape,threads,per_sm,tc", [(1, 512, 1, 0), (2, 256, 2, 0), (3, 256, 3, 0), (4, 256, 2, 1),
+                                                     (5, 256, 3, 1)])
+def test_batch_every_launch_shape_matches_oracle(shape, threads, per_sm, tc):
     # ragged sizes (not multiples of the 64-point factor block, one of 2048)
     # through each launch shape of the batch kernel
     rng = np.random.default_rng(400 + shape)
@@ -424,6 +425,7 @@ def test_batch_every_launch_shape_matches_oracle(shape, threads, per_sm):
     info = c.last_batch_info
     c.close()
     assert info["batch_threads"] == threads and info["batch_ctas_per_sm"] == per_sm
+    assert info["batch_tensor_cores"] == tc
     assert int(sts.abs().sum()) == 0
     k = 0
     for i, x in enumerate(clouds):
@@ -446,8 +448,9 @@ def test_batch_tuner_picks_a_shape():
     ws2, mags2, sts2 = c.solve_batch([_dev(x) for x in clouds], list(ts))
     info2 = c.last_batch_info
     c.close()
-    assert (info["batch_threads"], info["batch_ctas_per_sm"]) in {(512, 1), (256, 2), (256, 3)}
-    assert (info2["batch_threads"], info2["batch_ctas_per_sm"]) == (info["batch_threads"], info["batch_ctas_per_sm"])
+    shape = (info["batch_threads"], info["batch_ctas_per_sm"], info["batch_tensor_cores"])
+    assert shape in {(512, 1, 0), (256, 2, 0), (256, 3, 0), (256, 2, 1), (256, 3, 1)}
+    assert (info2["batch_threads"], info2["batch_ctas_per_sm"], info2["batch_tensor_cores"]) == shape
     assert int(sts.abs().sum()) == 0 and int(sts2.abs().sum()) == 0
     assert torch.equal(mags, mags2)
     for i in range(0, 130, 26):
