@@ -274,6 +274,7 @@ def run_ours(a):
                   "fallback": i["fallback"],
                   "ms_generate": i["ms_generate"], "ms_factor": i["ms_factor"], "ms_solve": i["ms_solve"],
                   "ms_residual": i["ms_residual"], "residual_evals": i["residual_evals"],
+                  "residual_evals_ff": i["residual_evals_ff"],
                   "probe_rho": i["probe_rho"], "ms_probe": i["ms_probe"],
                   "ms_factor_parts": {"update_trailing": i["ms_update"] - i["ms_update_panel"],
                                       "update_panel": i["ms_update_panel"], "potrf": i["ms_potrf"],

@@ -154,11 +154,13 @@ typedef struct mag_options {
   double host_limit_bytes;/* pinned host memory the out-of-core factor may
                              take (0: half of the host's physical memory);
                              more gives MAG_ENOMEM                          */
-  int32_t gmres_matvec;   /* products Z v of GMRES-IR's inner iterations:
-                             0 (default) float-float on the FP32 pipe from
-                             the stored FP64 tiles of exp(-t d) (a few units
-                             of 2^-46 of sum |Z||v|; the outer residuals
-                             stay FP64), else FP64 as the residual          */
+  int32_t gmres_matvec;   /* products Z v of GMRES-IR's inner iterations
+                             and the residuals of refinement steps far
+                             above the tolerance: 0 (default) float-float on
+                             the FP32 pipe from the stored FP64 tiles of
+                             exp(-t d) (a few units of 2^-46 of sum |Z||v|;
+                             the outer and deciding residuals stay FP64),
+                             else FP64 as the residual                      */
   int32_t fp16_gmres;     /* AUTO: 0 (default) the one-product FP16 factor
                              with GMRES-IR straight after the first solve
                              when the probe predicts plain refinement to
@@ -246,7 +248,9 @@ typedef struct mag_info {
   int32_t batch_ctas_per_sm; /* ... the CTAs per SM of its shape              */
   int32_t batch_tensor_cores; /* ... 1: the factor's trailing update on the
                               tensor cores (split TF32), 0: CUDA cores      */
-  int32_t reserved4;
+  int32_t residual_evals_ff; /* refinement residuals taken in float-float from
+                              the stored tiles (far above the tolerance; the
+                              deciding ones are FP64, in residual_evals)     */
 } mag_info;
 
 typedef struct mag_ctx mag_ctx;

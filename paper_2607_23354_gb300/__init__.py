@@ -73,7 +73,7 @@ class mag_info(ctypes.Structure):
                 ("deflation_c", ctypes.c_double), ("factor_reused", ctypes.c_int32),
                 ("reserved2", ctypes.c_int32), ("ms_update_busy", ctypes.c_double),
                 ("batch_threads", ctypes.c_int32), ("batch_ctas_per_sm", ctypes.c_int32),
-                ("batch_tensor_cores", ctypes.c_int32), ("reserved4", ctypes.c_int32)]
+                ("batch_tensor_cores", ctypes.c_int32), ("residual_evals_ff", ctypes.c_int32)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}

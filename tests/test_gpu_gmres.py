@@ -1,6 +1,7 @@
 """GMRES-IR with the one-product FP16 factor: the inner products Z v in
 float-float from the stored FP64 tiles (options.gmres_matvec) against the
-FP64 products, and the AUTO branch that takes the FP16 factor with GMRES-IR
+FP64 products, the float-float residuals of the early refinement steps,
+and the AUTO branch that takes the FP16 factor with GMRES-IR
 straight after the first solve (options.fp16_gmres, mag_info.fallback = 4).
 The weighting is compared with the oracle's (LAPACK factor step, FP64
 refinement), elementwise.
@@ -114,3 +115,23 @@ def test_short_gmres_outer_steps(cube):
     else:
         assert info["fallback"] == 4 and info["precision_used"] == M.PREC_FP16
     _check(X, 1.0, w, mag, ref)
+
+
+def test_early_refinement_residuals_in_float_float(cube):
+    # the split factor at t = 1 refines in three steps: the first residuals
+    # (far above the tolerance) come from the float-float product, the last
+    # ones from FP64; switching the float-float products off gives the same
+    # weighting
+    X, ref = cube
+    Xd = _dev(X)
+    c = M.Context(M.Options(precision="fp16x3", residual_mode="stored"))
+    w, mag, info = c.solve(Xd, 1.0)
+    c.close()
+    assert info["residual_evals_ff"] >= 1 and info["residual_evals"] >= 1, info
+    _check(X, 1.0, w, mag, ref)
+    c = M.Context(M.Options(precision="fp16x3", residual_mode="stored", gmres_matvec="fp64"))
+    w2, mag2, info2 = c.solve(Xd, 1.0)
+    c.close()
+    assert info2["residual_evals_ff"] == 0
+    assert info2["ir_iters"] == info["ir_iters"]
+    assert np.abs(w2.cpu().numpy() - w.cpu().numpy()).max() <= 1e-12 * np.abs(w.cpu().numpy()).max()
