@@ -179,9 +179,11 @@ typedef struct mag_options {
                              512 threads x 1 CTA per SM, 2: 256 x 2, 3: 256
                              x 3, all with the factor's trailing update on
                              the CUDA cores in FP32; 4: 256 x 2, 5: 256 x 3
-                             with it on the tensor cores in split TF32
-                             (mag_info.batch_threads / _ctas_per_sm /
-                             _tensor_cores)                                  */
+                             with it on the tensor cores in split TF32; 6:
+                             256 x 2, 7: 256 x 3 with a left-looking factor
+                             (each block of A updated once, with all earlier
+                             columns; CUDA cores) (mag_info.batch_threads /
+                             _ctas_per_sm / _tensor_cores / _left_looking)  */
   int32_t reserved3;
 } mag_options;
 
@@ -251,6 +253,8 @@ typedef struct mag_info {
   int32_t residual_evals_ff; /* refinement residuals taken in float-float from
                               the stored tiles (far above the tolerance; the
                               deciding ones are FP64, in residual_evals)     */
+  int32_t batch_left_looking; /* mag_solve_batch: 1 left-looking factor      */
+  int32_t reserved5;
 } mag_info;
 
 typedef struct mag_ctx mag_ctx;

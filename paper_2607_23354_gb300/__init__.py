@@ -73,7 +73,8 @@ class mag_info(ctypes.Structure):
                 ("deflation_c", ctypes.c_double), ("factor_reused", ctypes.c_int32),
                 ("reserved2", ctypes.c_int32), ("ms_update_busy", ctypes.c_double),
                 ("batch_threads", ctypes.c_int32), ("batch_ctas_per_sm", ctypes.c_int32),
-                ("batch_tensor_cores", ctypes.c_int32), ("residual_evals_ff", ctypes.c_int32)]
+                ("batch_tensor_cores", ctypes.c_int32), ("residual_evals_ff", ctypes.c_int32),
+                ("batch_left_looking", ctypes.c_int32), ("reserved5", ctypes.c_int32)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -167,7 +168,7 @@ class Options:
     host_limit_bytes: float = 0.0
     gmres_matvec: str = "float_float"  # or "fp64"
     fp16_gmres: int = 0
-    batch_shape: int = 0  # 0 tuned, 1..5 fixed
+    batch_shape: int = 0  # 0 tuned, 1..7 fixed
 
     def to_c(self) -> mag_options:
         o = mag_options()

@@ -95,8 +95,16 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-template <int B, int NT, bool MMA>
+// LEFT: left-looking -- before block column kb is factored, all its blocks
+// (bi, kb), bi >= kb, take their whole update sum_{k < kb} L_bi,k L_kb,k^T
+// in registers (block pairs of L streamed through shared memory, the next
+// pair read into registers during the products), and each block of A is
+// read and written once instead of once per earlier column: about two
+// thirds of the block traffic of the right-looking update (CUDA cores
+// only).
+template <int B, int NT, bool MMA, bool LEFT>
 __device__ bool cta_cholesky(float* A, int n, float* sm, int* flag) {
+  static_assert(!(MMA && LEFT), "the left-looking factor runs on the CUDA cores");
   float* D = sm;                    // [B][B+1] diagonal block
   float* Pi = sm + B * (B + 1);     // [B][B+4] panel block of tile row bi (k-major)
   float* Pj = Pi + B * (B + 4);     // [B][B+4] panel block of tile row bj (k-major)
@@ -104,6 +112,81 @@ __device__ bool cta_cholesky(float* A, int n, float* sm, int* flag) {
   const int nb = (n + B - 1) / B;
   for (int kb = 0; kb < nb; ++kb) {
     const int k0 = kb * B, kw = min(B, n - k0);
+    if constexpr (LEFT) {
+      if (kb > 0) {
+        constexpr int TR = 4, TC = B * B / (NT * TR), GX = B / TC;
+        static_assert(TR * TC * NT == B * B && GX * TC == B && (NT / GX) * TR == B && (TC == 2 || TC == 4),
+                      "thread tile of the left-looking update");
+        constexpr int LT = B + 4;
+        constexpr int PER = B * B / NT;
+        const int ty = tid / GX, tx = tid % GX;
+        float si[PER], sj[PER];
+        // rows r0 .. r0 + rw - 1 of the full column block starting at column c0
+        auto fetch_blk = [&](float (&stg)[PER], int r0, int rw, int c0) {
+#pragma unroll
+          for (int q = 0; q < PER; ++q) {
+            const int e = tid + q * NT, r = e / B, c = e % B;
+            stg[q] = r < rw ? A[(int64_t)(r0 + r) * n + c0 + c] : 0.0f;
+          }
+        };
+        auto put_blk = [&](const float (&stg)[PER], float* dstT) {
+#pragma unroll
+          for (int q = 0; q < PER; ++q) {
+            const int e = tid + q * NT, r = e / B, c = e % B;
+            dstT[c * LT + r] = stg[q];
+          }
+        };
+        for (int bi = kb; bi < nb; ++bi) {
+          const int i0 = bi * B, iw = min(B, n - i0);
+          const bool diag = bi == kb;
+          float acc[TR][TC];
+#pragma unroll
+          for (int u = 0; u < TR; ++u)
+#pragma unroll
+            for (int v = 0; v < TC; ++v) acc[u][v] = 0.0f;
+          fetch_blk(si, i0, iw, 0);
+          if (!diag) fetch_blk(sj, k0, kw, 0);
+          for (int k = 0; k < kb; ++k) {
+            __syncthreads();  // the previous products are done with PiT / PjT
+            put_blk(si, Pi);
+            if (!diag) put_blk(sj, Pj);
+            __syncthreads();
+            if (k + 1 < kb) {  // in flight during the products below
+              fetch_blk(si, i0, iw, (k + 1) * B);
+              if (!diag) fetch_blk(sj, k0, kw, (k + 1) * B);
+            }
+            const float* QT = diag ? Pi : Pj;
+#pragma unroll 8
+            for (int kk = 0; kk < B; ++kk) {
+              const float4 a = *reinterpret_cast<const float4*>(Pi + kk * LT + TR * ty);
+              float b[TC];
+              if constexpr (TC == 4) {
+                const float4 b4 = *reinterpret_cast<const float4*>(QT + kk * LT + TC * tx);
+                b[0] = b4.x, b[1] = b4.y, b[2] = b4.z, b[3] = b4.w;
+              } else {
+                const float2 b2 = *reinterpret_cast<const float2*>(QT + kk * LT + TC * tx);
+                b[0] = b2.x, b[1] = b2.y;
+              }
+              const float ar[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+              for (int u = 0; u < TR; ++u)
+#pragma unroll
+                for (int v = 0; v < TC; ++v) acc[u][v] = fmaf(ar[u], b[v], acc[u][v]);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < TR; ++u) {
+            const int r = TR * ty + u;
+            if (r >= iw) continue;
+#pragma unroll
+            for (int v = 0; v < TC; ++v) {
+              const int c = TC * tx + v;
+              if (c < kw && (!diag || c <= r)) A[(int64_t)(i0 + r) * n + k0 + c] -= acc[u][v];
+            }
+          }
+        }
+      }
+    }
     // (a) factor the diagonal block in shared memory (unscaled elimination)
     __syncthreads();
     for (int e = tid; e < B * B; e += NT) {
@@ -161,6 +244,7 @@ __device__ bool cta_cholesky(float* A, int n, float* sm, int* flag) {
         if (c < kw) row[c] = x[c];
     }
     __syncthreads();
+    if constexpr (LEFT) continue;  // the next column's blocks take their updates themselves
     // (c) trailing update of the lower tiles (bi, bj), kb < bj <= bi.  CUDA
     // cores (MMA false): the panel blocks are staged k-major (PiT[k][r],
     // PjT[k][c], row stride B + 4); a thread owns a TR x TC output tile (4 x 2
@@ -394,7 +478,7 @@ __device__ void cta_solve(const float* L, int n, float* v, float* sm) {
   __syncthreads();
 }
 
-template <int B, int NT, int MINB, bool MMA>
+template <int B, int NT, int MINB, bool MMA, bool LEFT>
 __global__ void __launch_bounds__(NT, MINB)
     k_batch_solve(const BatchProblem* __restrict__ probs, const int* __restrict__ order, int count,
                   const double* __restrict__ D, const int* __restrict__ cloud_flags, float* scratch_f,
@@ -460,7 +544,7 @@ __global__ void __launch_bounds__(NT, MINB)
     }
     __syncthreads();
     int st = MAG_BATCH_OK;
-    if (!cta_cholesky<B, NT, MMA>(S.Lf, n, smf, &s_flag)) st = MAG_BATCH_NOTPD;
+    if (!cta_cholesky<B, NT, MMA, LEFT>(S.Lf, n, smf, &s_flag)) st = MAG_BATCH_NOTPD;
     double rel = INFINITY;
     if (st == MAG_BATCH_OK) {
       for (int i = tid; i < n; i += NT) S.v[i] = 1.0f;
@@ -575,13 +659,13 @@ __global__ void __launch_bounds__(NT, MINB)
   }
 }
 
-template <int B, int NT, int MINB, bool MMA>
+template <int B, int NT, int MINB, bool MMA, bool LEFT>
 cudaError_t launch_batch_t(const BatchProblem* probs, const int* order, int count, const double* D,
                            const int* cloud_flags, float* scratch_f, double* scratch_d, int64_t nmax,
                            double* w_out, double* mag_out, int* status, int* queue, double tol, int max_iter,
                            int grid, unsigned long long* busy_cycles, cudaStream_t s) {
   const size_t smem = ((size_t)B * (B + 1) + 2 * (size_t)B * (B + 4)) * sizeof(float);
-  auto kern = k_batch_solve<B, NT, MINB, MMA>;
+  auto kern = k_batch_solve<B, NT, MINB, MMA, LEFT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, NT, smem, s>>>(probs, order, count, D, cloud_flags, scratch_f, scratch_d, nmax, w_out, mag_out,
@@ -590,10 +674,10 @@ cudaError_t launch_batch_t(const BatchProblem* probs, const int* order, int coun
   return cudaGetLastError();
 }
 
-template <int B, int NT, int MINB, bool MMA>
+template <int B, int NT, int MINB, bool MMA, bool LEFT>
 int resident_per_sm() {
   const size_t smem = ((size_t)B * (B + 1) + 2 * (size_t)B * (B + 4)) * sizeof(float);
-  auto kern = k_batch_solve<B, NT, MINB, MMA>;
+  auto kern = k_batch_solve<B, NT, MINB, MMA, LEFT>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -620,15 +704,18 @@ cudaError_t launch_batch_dist(const double* X, const BatchCloud* clouds, int ncl
 // Launch shapes of the batch kernel (factor block 64): threads per CTA, the
 // CTAs per SM the launch bounds are compiled for, and the trailing update on
 // CUDA cores (FP32) or on the tensor cores (split TF32, mma.sync).
-const BatchShape kBatchShapes[kNumBatchShapes] = {{512, 1, 0}, {256, 2, 0}, {256, 3, 0}, {256, 2, 1}, {256, 3, 1}};
+const BatchShape kBatchShapes[kNumBatchShapes] = {{512, 1, 0, 0}, {256, 2, 0, 0}, {256, 3, 0, 0}, {256, 2, 1, 0},
+                                                  {256, 3, 1, 0}, {256, 2, 0, 1}, {256, 3, 0, 1}};
 
 int batch_shape_resident(int shape) {
   switch (shape) {
-    case 0: return resident_per_sm<64, 512, 1, false>();
-    case 1: return resident_per_sm<64, 256, 2, false>();
-    case 2: return resident_per_sm<64, 256, 3, false>();
-    case 3: return resident_per_sm<64, 256, 2, true>();
-    case 4: return resident_per_sm<64, 256, 3, true>();
+    case 0: return resident_per_sm<64, 512, 1, false, false>();
+    case 1: return resident_per_sm<64, 256, 2, false, false>();
+    case 2: return resident_per_sm<64, 256, 3, false, false>();
+    case 3: return resident_per_sm<64, 256, 2, true, false>();
+    case 4: return resident_per_sm<64, 256, 3, true, false>();
+    case 5: return resident_per_sm<64, 256, 2, false, true>();
+    case 6: return resident_per_sm<64, 256, 3, false, true>();
     default: return 0;
   }
 }
@@ -638,15 +725,18 @@ cudaError_t launch_batch_solve(int shape, const BatchProblem* probs, const int* 
                                int64_t nmax, double* w_out, double* mag_out, int* status, int* queue, double tol,
                                int max_iter, int grid, unsigned long long* busy_cycles, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-#define MAG_BATCH_LAUNCH(NT_, MINB_, MMA_)                                                                  \
-  return launch_batch_t<64, NT_, MINB_, MMA_>(probs, order, count, D, cloud_flags, scratch_f, scratch_d, nmax, \
-                                               w_out, mag_out, status, queue, tol, max_iter, grid, busy_cycles, s)
+#define MAG_BATCH_LAUNCH(NT_, MINB_, MMA_, LEFT_)                                                              \
+  return launch_batch_t<64, NT_, MINB_, MMA_, LEFT_>(probs, order, count, D, cloud_flags, scratch_f, scratch_d, \
+                                                      nmax, w_out, mag_out, status, queue, tol, max_iter, grid,   \
+                                                      busy_cycles, s)
   switch (shape) {
-    case 0: MAG_BATCH_LAUNCH(512, 1, false);
-    case 1: MAG_BATCH_LAUNCH(256, 2, false);
-    case 2: MAG_BATCH_LAUNCH(256, 3, false);
-    case 3: MAG_BATCH_LAUNCH(256, 2, true);
-    case 4: MAG_BATCH_LAUNCH(256, 3, true);
+    case 0: MAG_BATCH_LAUNCH(512, 1, false, false);
+    case 1: MAG_BATCH_LAUNCH(256, 2, false, false);
+    case 2: MAG_BATCH_LAUNCH(256, 3, false, false);
+    case 3: MAG_BATCH_LAUNCH(256, 2, true, false);
+    case 4: MAG_BATCH_LAUNCH(256, 3, true, false);
+    case 5: MAG_BATCH_LAUNCH(256, 2, false, true);
+    case 6: MAG_BATCH_LAUNCH(256, 3, false, true);
     default: return cudaErrorInvalidValue;
   }
 #undef MAG_BATCH_LAUNCH

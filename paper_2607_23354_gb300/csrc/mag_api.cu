@@ -2643,6 +2643,7 @@ int mag_solve_batch(mag_ctx* ctx, const mag_batch_desc* desc, int32_t count, con
     info->batch_threads = kBatchShapes[ctx->batch_shape_used].threads;
     info->batch_ctas_per_sm = kBatchShapes[ctx->batch_shape_used].ctas_per_sm;
     info->batch_tensor_cores = kBatchShapes[ctx->batch_shape_used].tensor_cores;
+    info->batch_left_looking = kBatchShapes[ctx->batch_shape_used].left_looking;
   }
   return first;
 }

@@ -327,14 +327,15 @@ cudaError_t launch_batch_dist(const double* X, const BatchCloud* clouds, int ncl
 // block = 32 or 64 (factor block size); scratch_f: grid * (nmax^2 + nmax) floats,
 // scratch_d: grid * (nmax^2 + 2 nmax) doubles; queue: one zeroed int.
 // Launch shapes of k_batch_solve: threads per CTA, CTAs per SM its launch
-// bounds target, trailing update on the tensor cores (split TF32) or not;
+// bounds target, trailing update on the tensor cores (split TF32) or not,
+// right- or left-looking factor;
 // batch_shape_resident(i) = CTAs of shape i one SM holds.
 // busy_cycles (or null) receives the sum over CTAs of their busy time in SM
 // cycles (the tuner's measure).
 struct BatchShape {
-  int threads, ctas_per_sm, tensor_cores;
+  int threads, ctas_per_sm, tensor_cores, left_looking;
 };
-constexpr int kNumBatchShapes = 5;
+constexpr int kNumBatchShapes = 7;
 extern const BatchShape kBatchShapes[kNumBatchShapes];
 int batch_shape_resident(int shape);
 cudaError_t launch_batch_solve(int shape, const BatchProblem* probs, const int* order, int count,

@@ -412,9 +412,10 @@ def test_batch_config_shape_sample(ctx):
             k += 1
 
 
-@pytest.mark.parametrize("shape,threads,per_sm,tc", [(1, 512, 1, 0), (2, 256, 2, 0), (3, 256, 3, 0), (4, 256, 2, 1),
-                                                     (5, 256, 3, 1)])
-def test_batch_every_launch_shape_matches_oracle(shape, threads, per_sm, tc):
+@pytest.mark.parametrize("shape,threads,per_sm,tc,left", [(1, 512, 1, 0, 0), (2, 256, 2, 0, 0), (3, 256, 3, 0, 0),
+                                                          (4, 256, 2, 1, 0), (5, 256, 3, 1, 0), (6, 256, 2, 0, 1),
+                                                          (7, 256, 3, 0, 1)])
+def test_batch_every_launch_shape_matches_oracle(shape, threads, per_sm, tc, left):
     # ragged sizes (not multiples of the 64-point factor block, one of 2048)
     # through each launch shape of the batch kernel
     rng = np.random.default_rng(400 + shape)
@@ -425,7 +426,7 @@ def test_batch_every_launch_shape_matches_oracle(shape, threads, per_sm, tc):
     info = c.last_batch_info
     c.close()
     assert info["batch_threads"] == threads and info["batch_ctas_per_sm"] == per_sm
-    assert info["batch_tensor_cores"] == tc
+    assert info["batch_tensor_cores"] == tc and info["batch_left_looking"] == left
     assert int(sts.abs().sum()) == 0
     k = 0
     for i, x in enumerate(clouds):
@@ -448,9 +449,11 @@ def test_batch_tuner_picks_a_shape():
     ws2, mags2, sts2 = c.solve_batch([_dev(x) for x in clouds], list(ts))
     info2 = c.last_batch_info
     c.close()
-    shape = (info["batch_threads"], info["batch_ctas_per_sm"], info["batch_tensor_cores"])
-    assert shape in {(512, 1, 0), (256, 2, 0), (256, 3, 0), (256, 2, 1), (256, 3, 1)}
-    assert (info2["batch_threads"], info2["batch_ctas_per_sm"], info2["batch_tensor_cores"]) == shape
+    keys = ("batch_threads", "batch_ctas_per_sm", "batch_tensor_cores", "batch_left_looking")
+    shape = tuple(info[k] for k in keys)
+    assert shape in {(512, 1, 0, 0), (256, 2, 0, 0), (256, 3, 0, 0), (256, 2, 1, 0), (256, 3, 1, 0), (256, 2, 0, 1),
+                     (256, 3, 0, 1)}
+    assert tuple(info2[k] for k in keys) == shape
     assert int(sts.abs().sum()) == 0 and int(sts2.abs().sum()) == 0
     assert torch.equal(mags, mags2)
     for i in range(0, 130, 26):
