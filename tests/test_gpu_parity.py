@@ -731,10 +731,10 @@ def test_deflated_small_t_closed_forms(ctx, t, deflate):
         assert (info["deflation_c"] > 0) == (t * far <= (0.125 if deflate == 0 else 0.25))
         th = np.tanh(t * gaps / 2)
         exact = np.concatenate([[(1 + th[0]) / 2], (th[:-1] + th[1:]) / 2, [(1 + th[-1]) / 2]])
-        # the benchmark spec's weighting tolerance, or kappa times the residual
-        # of the system solved (reading 9): Z (kappa 2.5e5 at t = 1e-2, where
-        # the line is too long for the deflated form) or the deflated A
-        # (kappa 6e6 at t = 1e-5 against 5e8 for Z)
+        # the weighting tolerance (1e-9 of max |w|), or kappa times the
+        # residual of the system solved where that is larger: Z (kappa 2.5e5
+        # at t = 1e-2, where the line is too long for the deflated form) or
+        # the deflated A (kappa 6e6 at t = 1e-5 against 5e8 for Z)
         c = info["deflation_c"]
         D = np.linalg.norm(X[:, None, :] - X[None, :, :], axis=2)
         rel = info["rel_residual"]
