@@ -524,15 +524,18 @@ __global__ void __launch_bounds__(NT, MINB)
     // ---- Z: FP64 full square and FP32 lower, one exp per pair j < i (warp
     // per row, lanes along the row), mirrored into the upper triangle; the
     // row sums of Z (for ||Z||inf) come with the first residual.  Entries
-    // below e^-46 in FP32 (exp_neg_tiny), as the single-problem solver does.
-    const unsigned long long tiny_bits = (unsigned long long)__double_as_longlong(kTinyArg);
+    // below e^-46 in FP32 on the FP32 pipe (exp_neg_tiny_td), as the
+    // single-problem solver does.
+    const unsigned long long tiny_bits = (unsigned long long)__double_as_longlong(kTinyArg / P.t);
+    const float tf = (float)P.t;
     double zmax_p = 0.0;
     for (int i = warp; i < n; i += NT / 32) {
       const double* Di = Dc + (int64_t)i * (i - 1) / 2;
       for (int j = lane; j < i; j += 32) {
-        const double a = P.t * Di[j];
-        const double z = (unsigned long long)__double_as_longlong(a) > tiny_bits ? (double)exp_neg_tiny(a)
-                                                                                  : exp_neg_small(a, exptab);
+        const double d = Di[j];
+        const double z = (unsigned long long)__double_as_longlong(d) > tiny_bits
+                             ? f32_to_f64_nonneg(exp_neg_tiny_td(tf, P.t, d))
+                             : exp_neg_small(P.t * d, exptab);
         S.Zd[(int64_t)i * n + j] = z;
         S.Zd[(int64_t)j * n + i] = z;
         S.Lf[(int64_t)i * n + j] = f64_to_f32_nonneg(z);

@@ -124,8 +124,8 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
         else mind2b = vb < mind2b ? vb : mind2b;
         if (WD || WDIST) dd = sqrt_pos(v);
         if (WD && !kind && (unsigned long long)__double_as_longlong(dd) > tiny_bits) {
-          zf = exp_neg_tiny(t * dd);
-          zd = (double)zf;
+          zf = exp_neg_tiny_td(tf, t, dd);
+          zd = f32_to_f64_nonneg(zf);
         } else {
           if (WD) zd = mat_entry(kind, t, kc, dd, exptab);
           if (WF)
@@ -239,8 +239,8 @@ __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __rest
       } else {
         const double d = dv[q];
         if (WD && !kind && (unsigned long long)__double_as_longlong(d) > tiny_bits) {
-          zf = exp_neg_tiny(t * d);
-          zd = (double)zf;
+          zf = exp_neg_tiny_td(tf, t, d);
+          zd = f32_to_f64_nonneg(zf);
         } else {
           zd = WD ? mat_entry(kind, t, kc, d, exptab) : 0.0;
           zf = WD ? (kind == MAT_DEFLATED ? __double2float_rn(zd) : f64_to_f32_nonneg(zd))

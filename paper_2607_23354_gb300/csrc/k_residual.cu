@@ -375,7 +375,10 @@ __global__ void __launch_bounds__(SYM_THREADS, 1)
   __syncthreads();
   double cs[4] = {0.0, 0.0, 0.0, 0.0};
   float zc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  const unsigned long long tiny_bits = (unsigned long long)__double_as_longlong(kTinyArg);
+  // d^2 above (kTinyArg / t)^2: t d > kTinyArg, the entry below e^-46
+  const double dcut = kTinyArg / t;
+  const unsigned long long tiny_bits = (unsigned long long)__double_as_longlong(dcut * dcut);
+  const float tf = (float)t;
   // rows of block I: each row's 4 products per lane, then a lane tree -> P[I][J]
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -393,10 +396,13 @@ __global__ void __launch_bounds__(SYM_THREADS, 1)
           z = 1.0;
         } else if (kind == MAT_EXP) {
           // the solver's entries: FP32 below e^-46 (as the generator writes
-          // them for a solve), the FP32-reduced FP64 exponential above
-          const double a = t * sqrt_pos(d2[i][q]);
-          z = (unsigned long long)__double_as_longlong(a) > tiny_bits ? (double)exp_neg_tiny(a)
-                                                                       : exp_neg_small(a, exptab);
+          // them for a solve; decided on d^2, then sqrt and exp on the FP32
+          // pipe), the FP32-reduced FP64 exponential above
+          if ((unsigned long long)__double_as_longlong(d2[i][q]) > tiny_bits) {
+            z = f32_to_f64_nonneg(exp_neg_tiny_td2(tf, t, d2[i][q]));
+          } else {
+            z = exp_neg_small(t * sqrt_pos(d2[i][q]), exptab);
+          }
         } else {
           z = mat_entry(kind, t, kc, sqrt_pos(d2[i][q]), exptab);
         }

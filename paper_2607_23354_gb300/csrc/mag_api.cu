@@ -1121,7 +1121,7 @@ float elapsed(mag_ctx* ctx, int a, int b) {
 }
 
 // Generate the tiles for the given precision into the current layout.
-// tiny_fp32: entries below e^-46 in FP32 (exp_neg_tiny), for the solve path;
+// tiny_fp32: entries below e^-46 in FP32 (exp_neg_tiny_td), for the solve path;
 // the entry points that return Z or differentiate it keep FP64 everywhere.
 int generate(mag_ctx* ctx, const double* X, int32_t m, double t, bool f32, bool f64, SolveResult* R,
              bool tiny_fp32 = false) {

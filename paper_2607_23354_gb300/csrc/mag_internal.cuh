@@ -98,14 +98,14 @@ struct DevStatus {
 // matrix: MAT_EXP, Z_jk = exp(-t d_jk) (Eq. weighting); MAT_SHIFTED_DIST,
 // Z_jk = 1 - t d_jk (the scale-zero system with t = 1/c).  With tiny_arg
 // finite, MAT_EXP entries with t d_jk > tiny_arg are evaluated in FP32
-// (exp_neg_tiny); +inf keeps every entry FP64-exact.
+// (exp_neg_tiny_td); +inf keeps every entry FP64-exact.
 // MAT_DEFLATED: Z_jk = 1 + expm1(-t d_jk) / (c t), unit diagonal (the
 // small-t system (Z - (1 - c t) 1 1^T) / (c t) with its rank-one part
 // deflated; kc = 1 / (c t)).
 enum MatKind : int { MAT_EXP = 0, MAT_SHIFTED_DIST = 1, MAT_DEFLATED = 2 };
 // Entries exp(-t d) with t d above this (below e^-46 < 2^-66) are evaluated in
 // FP32 on the solve path: their error cannot reach one FP64 rounding of a row
-// sum that holds the unit diagonal (exp_neg_tiny in mag_math.cuh).
+// sum that holds the unit diagonal (exp_neg_tiny_td in mag_math.cuh).
 constexpr double kTinyArg = 46.0;
 cudaError_t launch_generate(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
                             double* Zd, double* rowsum, DevStatus* st, cudaStream_t s, int kind = MAT_EXP,

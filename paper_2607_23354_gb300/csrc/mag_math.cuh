@@ -123,15 +123,16 @@ __device__ __forceinline__ double mat_entry(int kind, double t, double kc, doubl
 }
 
 // exp(-a) for a > kTinyArg = 46 (mag_internal.cuh; results below
-// e^-46 < 2^-66) in FP32: the
-// CUDA expf of the rounded argument, relative error below 6e-6 (argument
-// rounding a 2^-24 <= 5.2e-6 for a <= 87, plus the expf error), and 0 for
-// a > 87 (below FP32's normal range).  In a row of Z that holds the unit
+// e^-46 < 2^-66) in FP32, a = t d formed from FP32 roundings of t and d
+// (exp_neg_tiny_td, no FP64 operation: GB300's FP64 pipe is the generator's
+// limit): the CUDA expf of the argument, relative error below 2e-5
+// (three roundings of 2^-24 in a <= 87, 1.6e-5, plus the expf error), and 0
+// for a > 87 (below FP32's normal range).  In a row of Z that holds the unit
 // diagonal these entries change the FP64 row sum by at most
-// n (6e-6 e^-46 + 2^-126) < n 2^-83: for n <= 2^20 far below the 2^-53 of
+// n (2e-5 e^-46 + 2^-126) < n 2^-81: for n <= 2^20 far below the 2^-53 of
 // one FP64 rounding of that sum, so residuals and refinement see the same
 // matrix as with FP64 exponentials everywhere.
-__device__ __forceinline__ float exp_neg_tiny(double a) { return a > 87.0 ? 0.0f : expf(-(float)a); }
+__device__ __forceinline__ float exp_neg_tiny_f(float a) { return a > 87.0f ? 0.0f : expf(-a); }
 
 // x in [0, 2^128) to FP32, round to nearest even, on the integer pipe; values
 // below 2^-126 (FP32 subnormals) become 0.  Used for the FP32 copy of a Z
@@ -142,6 +143,25 @@ __device__ __forceinline__ float f64_to_f32_nonneg(double x) {
   b += 0x0FFFFFFFull + ((b >> 29) & 1ull);  // round the 29 dropped bits, ties to even
   return __uint_as_float((unsigned)(b >> 29) - ((1023u - 127u) << 23));
 }
+
+// v >= 0 (an FP32 value, e.g. an FP32 entry of Z) to FP64 on the integer
+// pipe: exponent rebiased, significand shifted; 0 and FP32 subnormals give 0.
+__device__ __forceinline__ double f32_to_f64_nonneg(float v) {
+  const unsigned b = __float_as_uint(v);
+  const unsigned e = b >> 23;
+  if (e == 0u) return 0.0;
+  if (e == 255u) return (double)v;  // inf, NaN
+  return __longlong_as_double(
+      (long long)(((unsigned long long)(e + (1023u - 127u)) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
+// exp(-t d) below e^-46 (exp_neg_tiny_f) from FP64 d >= 0 and tf = t rounded
+// to FP32: d rounded on the integer pipe, the product and the exponential on
+// the FP32 pipe.  Returns the FP32 entry; its FP64 copy is
+// f32_to_f64_nonneg of it.  d of 2^126 or more (or NaN) takes t d in FP64.
+__device__ __forceinline__ float exp_neg_tiny_td(float tf, double t, double d);
+// The same from d^2 (the square root on the FP32 pipe as well).
+__device__ __forceinline__ float exp_neg_tiny_td2(float tf, double t, double d2);
 
 // sqrt(v) for v >= 0 by Markstein's method (P. Markstein, "Computation of
 // elementary functions on the IBM RISC System/6000 processor", IBM J. Res.
@@ -170,6 +190,17 @@ __device__ __forceinline__ double sqrt_pos(double v) {
   s = fma(h, r, s);
   r = fma(-s, s, v);
   return fma(h, r, s);
+}
+
+__device__ __forceinline__ float exp_neg_tiny_td(float tf, double t, double d) {
+  if ((unsigned long long)__double_as_longlong(d) >= 0x47D0000000000000ull)  // 2^126, inf, NaN
+    return d != d ? (float)d : exp_neg_tiny_f((float)fmin(t * d, 100.0));
+  return exp_neg_tiny_f(tf * f64_to_f32_nonneg(d));
+}
+__device__ __forceinline__ float exp_neg_tiny_td2(float tf, double t, double d2) {
+  if ((unsigned long long)__double_as_longlong(d2) >= 0x47D0000000000000ull)
+    return d2 != d2 ? (float)d2 : exp_neg_tiny_f((float)fmin(t * sqrt(d2), 100.0));
+  return exp_neg_tiny_f(tf * sqrtf(f64_to_f32_nonneg(d2)));
 }
 
 }  // namespace mag
