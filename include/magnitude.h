@@ -159,14 +159,14 @@ typedef struct mag_options {
                              above the tolerance: 0 (default) float-float on
                              the FP32 pipe from the stored FP64 tiles of
                              exp(-t d) (a few units of 2^-46 of sum |Z||v|;
-                             the outer and deciding residuals stay FP64),
-                             else FP64 as the residual                      */
+                             the residuals that decide convergence stay
+                             FP64), else FP64 as the residual               */
   int32_t fp16_gmres;     /* AUTO: 0 (default) the one-product FP16 factor
                              with GMRES-IR straight after the first solve
                              when the probe predicts plain refinement to
                              diverge or crawl (contraction <= 16) and the
                              factor saved outweighs the inner iterations
-                             (n >= 133,000 with stored tiles); a GMRES-IR that
+                             (n >= 72,000 with stored tiles); a GMRES-IR that
                              stalls is replaced by the split factor
                              (mag_info.fallback = 3); -1 never; 1 whenever
                              the contraction is <= 16 (any n)              */
@@ -184,7 +184,15 @@ typedef struct mag_options {
                              (each block of A updated once, with all earlier
                              columns; CUDA cores) (mag_info.batch_threads /
                              _ctas_per_sm / _tensor_cores / _left_looking)  */
-  int32_t reserved3;
+  int32_t sweep_kind;     /* triangular sweeps of the refinement corrections
+                             (in core): 0 (default) one product with a
+                             precomputed B_I = inv(L_II) L_{I,I-1} per tile on
+                             the sweep's critical path, the off-diagonal tiles
+                             read as FP16 for the one-product FP16 factor (the
+                             operands its updates used) and as FP32 otherwise;
+                             1 the same with FP32 tiles always; 2 the sweeps
+                             with one progress counter and the full tile
+                             product per step                               */
 } mag_options;
 
 /* Diagnostics of one call (all fields written when info != NULL). */
@@ -254,7 +262,10 @@ typedef struct mag_info {
                               the stored tiles (far above the tolerance; the
                               deciding ones are FP64, in residual_evals)     */
   int32_t batch_left_looking; /* mag_solve_batch: 1 left-looking factor      */
-  int32_t reserved5;
+  int32_t sweeps_used;     /* triangular sweeps of the last correction: 0 the
+                              chain sweeps with FP16 tiles, 1 with FP32 tiles,
+                              2 the progress-counter sweeps (FP64 factor, out
+                              of core, options.sweep_kind = 2); -1 none     */
 } mag_info;
 
 typedef struct mag_ctx mag_ctx;

@@ -49,7 +49,7 @@ class mag_options(ctypes.Structure):
                 ("wait_timeout_ns", ctypes.c_int64), ("out_of_core", ctypes.c_int32),
                 ("deflate", ctypes.c_int32), ("host_limit_bytes", ctypes.c_double),
                 ("gmres_matvec", ctypes.c_int32), ("fp16_gmres", ctypes.c_int32),
-                ("batch_shape", ctypes.c_int32), ("reserved3", ctypes.c_int32)]
+                ("batch_shape", ctypes.c_int32), ("sweep_kind", ctypes.c_int32)]
 
 
 class mag_info(ctypes.Structure):
@@ -74,7 +74,7 @@ class mag_info(ctypes.Structure):
                 ("reserved2", ctypes.c_int32), ("ms_update_busy", ctypes.c_double),
                 ("batch_threads", ctypes.c_int32), ("batch_ctas_per_sm", ctypes.c_int32),
                 ("batch_tensor_cores", ctypes.c_int32), ("residual_evals_ff", ctypes.c_int32),
-                ("batch_left_looking", ctypes.c_int32), ("reserved5", ctypes.c_int32)]
+                ("batch_left_looking", ctypes.c_int32), ("sweeps_used", ctypes.c_int32)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -169,6 +169,7 @@ class Options:
     gmres_matvec: str = "float_float"  # or "fp64"
     fp16_gmres: int = 0
     batch_shape: int = 0  # 0 tuned, 1..7 fixed
+    sweeps: str = "chain"  # "chain", "chain_fp32" (FP32 tiles always), "progress"
 
     def to_c(self) -> mag_options:
         o = mag_options()
@@ -197,6 +198,10 @@ class Options:
         o.gmres_matvec = 0 if self.gmres_matvec == "float_float" else 1
         o.fp16_gmres = int(self.fp16_gmres)
         o.batch_shape = int(self.batch_shape)
+        kinds = {"chain": 0, "chain_fp32": 1, "progress": 2}
+        if self.sweeps not in kinds:
+            raise ValueError(f"sweeps must be one of {sorted(kinds)}, not {self.sweeps!r}")
+        o.sweep_kind = kinds[self.sweeps]
         return o
 
 

@@ -958,7 +958,8 @@ __device__ __forceinline__ void mma_f16_128x128(uint32_t d_tmem, uint64_t a, uin
 __global__ void __launch_bounds__(TRSM_THREADS, 1)
     k_trsm_tc(float* __restrict__ Z, const float* __restrict__ Dinv, int64_t K, int64_t N, int64_t k0,
               int64_t width, int split, __half* __restrict__ phi, __half* __restrict__ plo,
-              unsigned* __restrict__ counter, DevStatus* st, uint64_t timeout_ns, int64_t wcap) {
+              unsigned* __restrict__ counter, DevStatus* st, uint64_t timeout_ns, int64_t wcap,
+              __half* __restrict__ lh) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* b_hi = smem;
@@ -1050,6 +1051,7 @@ __global__ void __launch_bounds__(TRSM_THREADS, 1)
     if (!ok) break;
     // row-major write-out: warp w, rows w + 8 i; lane l, columns 4 l .. 4 l + 3
     float* out = Z + tile_index(I, K, wcap) * TILE_ELEMS;
+    __half* lout = lh ? lh + tile_index(I, K, wcap) * TILE_ELEMS : nullptr;
     const int64_t prow = (I - k0) * TILE, pcol = (K - k0) * TILE + 4 * lane;
     for (int i = 0; i < 16; ++i) {
       const int r = warp + 8 * i;
@@ -1065,6 +1067,7 @@ __global__ void __launch_bounds__(TRSM_THREADS, 1)
       const int64_t off = (prow + r) * width + pcol;
       *reinterpret_cast<uint2*>(phi + off) = *reinterpret_cast<const uint2*>(h);
       if (split) *reinterpret_cast<uint2*>(plo + off) = *reinterpret_cast<const uint2*>(l);
+      if (lout) *reinterpret_cast<uint2*>(lout + r * TILE + 4 * lane) = *reinterpret_cast<const uint2*>(h);
     }
     __syncthreads();
     tile = next;
@@ -1231,7 +1234,7 @@ cudaError_t launch_update_tc(const UpdMaps& maps, const CMap& cmap, UpdParams p,
 
 cudaError_t launch_trsm_tc(float* Z, const float* Dinv, int64_t K, int64_t N, int64_t k0, int64_t width, int mode,
                            void* hi, void* lo, unsigned* counter, DevStatus* st, int grid, cudaStream_t s,
-                           int64_t wcap) {
+                           int64_t wcap, void* lh) {
   if (wcap < 0) wcap = N;
   if (K >= wcap) return cudaErrorInvalidValue;
   const int64_t ntiles = N - K - 1;
@@ -1244,7 +1247,8 @@ cudaError_t launch_trsm_tc(float* Z, const float* Dinv, int64_t K, int64_t N, in
   if (grid < 1) grid = 1;
   k_trsm_tc<<<grid, TRSM_THREADS, smem, s>>>(Z, Dinv, K, N, k0, width, mode == UPD_FP16X3 ? 1 : 0,
                                               static_cast<__half*>(hi), static_cast<__half*>(lo), counter, st,
-                                              10000000000ull, wcap);
+                                              10000000000ull, wcap,
+                                              mode == UPD_FP16 ? static_cast<__half*>(lh) : nullptr);
   note_launch();
   return cudaGetLastError();
 }

@@ -23,6 +23,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "../../include/magnitude.h"
 #include "mag_internal.cuh"
 
@@ -131,6 +133,16 @@ struct mag_ctx {
   CMap slab_cmap;                    // TMA descriptor of the slab being updated
   const void* slab_cmap_base = nullptr;
   int64_t slab_cmap_tiles = 0;
+  // in-core sweeps (k_chain.cu): the B tiles of the factor in the workspace
+  // (Sf: N tiles, then Sb: N tiles) and the FP16 copy of its off-diagonal
+  // tiles that the panel solve of the one-product factor writes
+  float* chain_s = nullptr;
+  size_t chain_s_bytes = 0;
+  void* lh = nullptr;
+  size_t lh_bytes = 0;
+  bool chain_ready = false;          // chain_s holds the B tiles of the current factor
+  bool lh_ready = false;             // lh holds its FP16 tiles
+  int64_t chain_N = 0;
   float* probe_z = nullptr;          // FP32 tiles of the leading block the precision probe factors
   size_t probe_bytes = 0;
   CMap probe_cmap;                   // TMA descriptor of those tiles (update epilogue)
@@ -269,6 +281,7 @@ int ensure_workspace(mag_ctx* ctx, int64_t n, bool f32, bool f64, int64_t zf_til
     }
     ctx->dist_valid = false;  // any stored distances are gone with the old buffer
     ctx->fac_valid = false;   // and the factor
+    ctx->chain_ready = ctx->lh_ready = false;
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, L.total);
     if (e != cudaSuccess) {
@@ -281,6 +294,33 @@ int ensure_workspace(mag_ctx* ctx, int64_t n, bool f32, bool f64, int64_t zf_til
   }
   ctx->lay = L;
   return MAG_OK;
+}
+
+// A device buffer of at least `need` bytes at *p (*have: its size), grown
+// only while at least `margin` bytes of device memory stay free beside it.
+// false (and no buffer change) when that does not hold or cudaMalloc fails:
+// the caller then takes a path without the buffer.
+bool grow_buffer(mag_ctx* ctx, void** p, size_t* have, size_t need, size_t margin) {
+  if (need <= *have) return true;
+  size_t fre = 0, tot = 0;
+  if (cudaMemGetInfo(&fre, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if ((double)fre + (double)*have < (double)need + (double)margin) return false;
+  if (*p) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(*p);
+    *p = nullptr;
+    *have = 0;
+  }
+  if (cudaMalloc(p, need) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return false;
+  }
+  *have = need;
+  return true;
 }
 
 int ensure_aux(mag_ctx* ctx, int64_t n) {
@@ -533,6 +573,9 @@ struct TcFactor {
   // tile columns of Z's layout (tile_index column cap): N for the whole
   // matrix, the slab width for a slab of the out-of-core factor
   int64_t W = 0;
+  // FP16 copy of the factor's off-diagonal tiles (one-product factor in
+  // core), written by the panel solves; null: none
+  void* lh = nullptr;
 };
 
 // C_IJ -= sum_{k in [kc_lo, kc_hi)} P_Ik P_Jk^T for J in [j0, j1) with the
@@ -591,7 +634,7 @@ int tc_panel_range(TcFactor& F, int64_t k0, int64_t a, int64_t b, int buf, cudaS
       // solve and panel copy in one tensor-core pass
       TRY(prof_begin(ctx, PC_TRSM, st));
       CU(launch_trsm_tc(Z, Dinv, a, F.N, k0, L.W, F.mode, ctx->panel_hi(buf), ctx->panel_lo(buf),
-                        ctx->counters() + L.nctr_upd + a, ctx->st(), F.panel_grid, st, F.W > 0 ? F.W : F.N));
+                        ctx->counters() + L.nctr_upd + a, ctx->st(), F.panel_grid, st, F.W > 0 ? F.W : F.N, F.lh));
       TRY(prof_end(ctx, st));
       return MAG_OK;
     }
@@ -630,7 +673,7 @@ int tc_panel(TcFactor& F, int64_t k0, int b, cudaStream_t st) {
 // Dinv receives inv(L_KK) of its diagonal tiles (and the transposes N_global
 // tiles further, see launch_potrf_diag).
 int factor_tc_on(mag_ctx* ctx, int mode, float* Z, float* Dinv, const CMap* cmap, int64_t N, int64_t W,
-                 int* launches, double* flops, bool slab = false) {
+                 int* launches, double* flops, bool slab = false, void* lh = nullptr) {
   const Layout& L = ctx->lay;
   cudaStream_t s = ctx->stream;
   const bool split = mode == UPD_FP16X3 || mode == UPD_TF32X3;
@@ -648,6 +691,7 @@ int factor_tc_on(mag_ctx* ctx, int mode, float* Z, float* Dinv, const CMap* cmap
   CU(cudaMemsetAsync(ctx->counters(), 0, (size_t)L.nctr * sizeof(unsigned), s));
   TcFactor F{ctx, mode, pairs, nb, launches, flops, 0, Z, Dinv, cmap, L.n, N, ctx->sm_count};
   F.W = W;
+  F.lh = lh;
   if (!la) {
     for (int64_t k0 = 0; k0 < W; k0 += nb) {
       const int64_t k1 = std::min<int64_t>(W, k0 + nb);
@@ -705,7 +749,7 @@ int factor_tc_on(mag_ctx* ctx, int mode, float* Z, float* Dinv, const CMap* cmap
 }
 
 // The in-core factor: the whole packed matrix of the workspace.
-int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
+int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops, void* lh = nullptr) {
   const Layout& L = ctx->lay;
   if (ctx->cmap_base != ctx->zf() || ctx->cmap_tiles != L.tiles) {
     if (!make_c_map(&ctx->cmap, ctx->zf(), L.tiles))
@@ -713,7 +757,7 @@ int factor_tc(mag_ctx* ctx, int mode, int* launches, double* flops) {
     ctx->cmap_base = ctx->zf();
     ctx->cmap_tiles = L.tiles;
   }
-  return factor_tc_on(ctx, mode, ctx->zf(), ctx->dinvf(), &ctx->cmap, L.N, L.N, launches, flops);
+  return factor_tc_on(ctx, mode, ctx->zf(), ctx->dinvf(), &ctx->cmap, L.N, L.N, launches, flops, false, lh);
 }
 
 // ------------------------------------------------------------ out of core
@@ -953,6 +997,7 @@ int mag_options_default(mag_options* opt) {
   opt->gmres_matvec = 0;
   opt->fp16_gmres = 0;
   opt->batch_shape = 0;
+  opt->sweep_kind = 0;
   return MAG_OK;
 }
 
@@ -1001,6 +1046,8 @@ int mag_ctx_destroy(mag_ctx* ctx) {
   if (ctx->bws) cudaFree(ctx->bws);
   if (ctx->gm) cudaFree(ctx->gm);
   if (ctx->probe_z) cudaFree(ctx->probe_z);
+  if (ctx->chain_s) cudaFree(ctx->chain_s);
+  if (ctx->lh) cudaFree(ctx->lh);
   if (ctx->host_L) cudaFreeHost(ctx->host_L);
   for (auto& kv : ctx->task_tables)
     if (kv.second.d) cudaFree(kv.second.d);
@@ -1104,6 +1151,7 @@ struct SolveResult {
   double ms_update = 0, update_flops = 0, ms_update_panel = 0, ms_potrf = 0, ms_trsm = 0, ms_split = 0;
   double ms_update_busy = 0;
   int residual_evals_ff = 0;
+  int sweeps_used = -1;
   double probe_rho = 0, ms_probe = 0;
   int slabs = 0, host_slabs = 0;
   double host_bytes = 0, host_read_bytes = 0, ms_host_read = 0;
@@ -1189,6 +1237,15 @@ void end_dist_reuse(mag_ctx* ctx) {
 
 int run_factor(mag_ctx* ctx, int prec, SolveResult* R) {
   cudaStream_t s = ctx->stream;
+  const Layout& L = ctx->lay;
+  ctx->chain_ready = ctx->lh_ready = false;
+  const bool chain = prec != MAG_PREC_FP64 && ctx->opt.sweep_kind != 2 &&
+                     grow_buffer(ctx, (void**)&ctx->chain_s, &ctx->chain_s_bytes,
+                                 (size_t)2 * L.N * TILE_ELEMS * sizeof(float), 0);
+  void* lh = nullptr;
+  if (chain && ctx->opt.sweep_kind == 0 && prec != MAG_PREC_FP32 && upd_mode(prec) == UPD_FP16 &&
+      grow_buffer(ctx, &ctx->lh, &ctx->lh_bytes, (size_t)L.tiles * TILE_ELEMS * 2, 1u << 30))
+    lh = ctx->lh;
   CU(cudaEventRecord(ctx->ev[0], s));
   ctx->prof_used = 0;
   if (prec == MAG_PREC_FP64)
@@ -1196,7 +1253,8 @@ int run_factor(mag_ctx* ctx, int prec, SolveResult* R) {
   else if (prec == MAG_PREC_FP32)
     TRY(factor_blocked<float>(ctx, ctx->zf(), ctx->dinvf(), &R->update_launches, &R->update_flops));
   else
-    TRY(factor_tc(ctx, upd_mode(prec), &R->update_launches, &R->update_flops));
+    TRY(factor_tc(ctx, upd_mode(prec), &R->update_launches, &R->update_flops, lh));
+  if (chain) CU(launch_chain_prep(ctx->zf(), ctx->dinvf(), L.N, ctx->chain_s, ctx->chain_s + L.N * TILE_ELEMS, s));
   CU(cudaEventRecord(ctx->ev[1], s));
   TRY(read_status(ctx));
   R->ms_fac += elapsed(ctx, 0, 1);
@@ -1212,6 +1270,9 @@ int run_factor(mag_ctx* ctx, int prec, SolveResult* R) {
   if (ctx->h_st->flags & ST_NOTPD)
     return fail(ctx, MAG_ENOTPD, "non-positive pivot at row %d (precision %d)", ctx->h_st->notpd_index - 1,
                 prec);
+  ctx->chain_ready = chain;
+  ctx->lh_ready = chain && lh != nullptr;
+  ctx->chain_N = L.N;
   return MAG_OK;
 }
 
@@ -1262,13 +1323,42 @@ int correction_ooc(mag_ctx* ctx, const double* r, double* x, bool init) {
   return MAG_OK;
 }
 
+// The same correction with the in-core sweeps of k_chain.cu (the B tiles
+// formed after the factor; FP16 off-diagonal tiles when the one-product
+// factor wrote them).
+int correction_chain(mag_ctx* ctx, const double* r, double* x, bool init) {
+  const Layout& L = ctx->lay;
+  cudaStream_t s = ctx->stream;
+  const uint64_t tmo = (uint64_t)ctx->opt.wait_timeout_ns;
+  float* v = ctx->vf(F_V);
+  float* y = ctx->vf(F_Y);
+  const float* Sf = ctx->chain_s;
+  const float* Sb = ctx->chain_s + L.N * TILE_ELEMS;
+  CU(launch_scale_rhs_unset(r, L.n, L.np, v, y, ctx->st(), s));
+  if (ctx->lh_ready) {
+    const __half* lh = (const __half*)ctx->lh;
+    const float sc = 1.0f / (float)(1 << FP16_SCALE_LOG2);
+    CU(launch_forward_chain<__half>(lh, sc, ctx->dinvf(), Sf, L.N, v, y, ctx->st(), tmo, s));
+    CU(launch_backward_chain<__half>(lh, sc, ctx->dinvf(), Sb, L.N, y, v, ctx->st(), tmo, s));
+  } else {
+    CU(launch_forward_chain<float>(ctx->zf(), 1.0f, ctx->dinvf(), Sf, L.N, v, y, ctx->st(), tmo, s));
+    CU(launch_backward_chain<float>(ctx->zf(), 1.0f, ctx->dinvf(), Sb, L.N, y, v, ctx->st(), tmo, s));
+  }
+  CU(launch_accumulate<float>(x, v, L.n, ctx->st(), init, s));
+  return MAG_OK;
+}
+
 int correction(mag_ctx* ctx, int prec, const double* r, double* x, bool init, SolveResult* R) {
   cudaStream_t s = ctx->stream;
   CU(cudaEventRecord(ctx->ev[2], s));
   const Layout& L = ctx->lay;
+  R->sweeps_used = 2;
   if (ctx->ooc)
     TRY(correction_ooc(ctx, r, x, init));
-  else if (prec == MAG_PREC_FP64)
+  else if (prec != MAG_PREC_FP64 && ctx->chain_ready && ctx->chain_N == L.N) {
+    TRY(correction_chain(ctx, r, x, init));
+    R->sweeps_used = ctx->lh_ready ? 0 : 1;
+  } else if (prec == MAG_PREC_FP64)
     TRY(correction_t<double>(ctx, ctx->zd(), ctx->dinvd(), ctx->vd(V_T2), ctx->vd(V_E), r, x, init, L.n, L.np,
                              L.N));
   else
@@ -1494,17 +1584,28 @@ int gmres_ir(mag_ctx* ctx, int prec, const double* X, int32_t m, double t, const
     CU(launch_scale(out, -1.0, out, n, s));
     return MAG_OK;
   };
-  double best = INFINITY, prev_rel = INFINITY, rel = INFINITY;
+  double best = INFINITY, prev_rel = INFINITY, prev2_rel = INFINITY, rel = INFINITY;
   bool fresh = false;  // rel is the residual of the current x
   std::vector<double> H((size_t)(k + 1) * k), cs(k), sn(k), g(k + 1), y(k), h(k + 1), h2(k + 1);
+  // outer residuals in float-float while they are predicted well above the
+  // tolerance (the rule of refine's loop); the deciding ones in FP64
+  const bool ff_ok = ff && prec != MAG_PREC_FP64;
   for (int outer = 0; outer < 8; ++outer) {
-    TRY(residual(ctx, X, m, t, x, b, r, &rel, stored, R));
+    bool ffr = false;
+    if (ff_ok) {
+      const double rho_est =
+          (std::isfinite(prev2_rel) && prev2_rel > 0.0) ? std::min(1.0, prev_rel / prev2_rel) : 1e-3;
+      ffr = outer == 0 || prev_rel * rho_est > 1e-10;
+    }
+    TRY(residual(ctx, X, m, t, x, b, r, &rel, stored, R, ffr));
+    if (ffr && !(rel > 1e-10)) TRY(residual(ctx, X, m, t, x, b, r, &rel, stored, R, false));
     fresh = true;
     best = std::min(best, rel);
     if (rel <= kStopMargin * ctx->opt.ir_tol) break;
     // planned (the probe's FP16 choice): an outer step that gains less than
     // two digits leaves the rest to the split factor
     if (planned && !(rel <= 1e-2 * prev_rel)) break;
+    prev2_rel = prev_rel;
     prev_rel = rel;
     // V_0 = M^{-1} r / beta
     TRY(correction(ctx, prec, r, wv, /*init=*/true, R));
@@ -1612,19 +1713,19 @@ bool probe_takes_fp16(double rho, double tol, int64_t n, bool stored) {
 
 // The FP16 factor with GMRES-IR where plain refinement with it would not
 // do (probe_takes_fp16 false): preconditioned by an FP16 factor whose
-// refinement contraction is predicted at most 16, GMRES-IR took 10-11 inner
-// iterations at n = 16384 and 32768 and 19 at n = 1e5 (t = 1 on [0,1]^8,
-// rho 0.87, 1.74 and 5.3).  An inner iteration (a float-float product with
-// the stored tiles, two triangular sweeps) costs about 0.7 refinement steps
-// (20 of 29 ms at n = 1e5), so 19 of them come to about 13 steps beyond the
-// split factor's refinement, while the half of the factor saved is worth
-// n / 9500 steps (at n = 1e5 the two solves took 1.045 and 1.037 s): taken
-// from n = 133,000 (options.fp16_gmres = 1: at any n).
+// refinement contraction is predicted at most 16, GMRES-IR took 10-15 inner
+// iterations from n = 16384 to 1e5 (t = 1 on [0,1]^8, rho 0.87 to 5.3).  An
+// inner iteration is a float-float product with the stored tiles (8 ms at
+// n = 1e5) and a correction through the chain sweeps with the FP16 tiles
+// (4.5 ms).  Measured against the split factor: 0.859 against 1.012 s at
+// n = 1e5 (factor 285 against 632 ms, 15 inner iterations), 0.356 against
+// 0.360 s at n = 65,536: taken from n = 72,000 (options.fp16_gmres = 1: at
+// any n).
 bool probe_takes_fp16_gmres(const mag_ctx* ctx, double rho, int64_t n, bool stored) {
   const int mode = ctx->opt.fp16_gmres;
   if (mode < 0 || !stored || ctx->kind != MAT_EXP || ctx->opt.gmres_max_iters < 2 || !ctx->opt.allow_fallback)
     return false;
-  return rho <= 16.0 && (mode > 0 || (double)n / 9500.0 >= 14.0);
+  return rho <= 16.0 && (mode > 0 || n >= 72000);
 }
 
 // Refinement of Z x = b (b == null: ones) with the factor in the workspace
@@ -1877,6 +1978,7 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
   const mag_options& o = ctx->opt;
   int prec = o.precision;
   ctx->fac_valid = false;  // the workspace's tiles are about to be rewritten
+  ctx->chain_ready = ctx->lh_ready = false;
   {
     int64_t pool_tiles = 0;
     TRY(plan_out_of_core(ctx, n, prec, &pool_tiles));
@@ -2004,6 +2106,7 @@ void fill_info(mag_ctx* ctx, const SolveResult& R, int64_t n, mag_info* info) {
   info->factor_reused = R.factor_reused;
   info->ms_update_busy = R.ms_update_busy;
   info->residual_evals_ff = R.residual_evals_ff;
+  info->sweeps_used = R.sweeps_used;
 }
 
 // The small-t end (Z close to 1 1^T, kappa(Z) growing like 1/t): with

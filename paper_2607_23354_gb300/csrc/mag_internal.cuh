@@ -211,9 +211,12 @@ cudaError_t launch_split_col(const float* Z, int64_t K, int64_t N, int64_t k0, i
 // `grid` persistent CTAs (129 KB of shared memory each) claim the N - K - 1
 // tiles from *counter, which must be zero before the launch.
 // wcap: column cap of Z's tile layout (tile_index), -1 for the whole matrix.
+// lh (FP16 mode only, may be null): also writes the panel copy's FP16
+// values (2^12 L_IK) to tile tile_index(I, K, wcap) of lh, row-major: the
+// FP16 copy of the factor that the in-core sweeps read.
 cudaError_t launch_trsm_tc(float* Z, const float* Dinv, int64_t K, int64_t N, int64_t k0, int64_t width, int mode,
                            void* hi, void* lo, unsigned* counter, DevStatus* st, int grid, cudaStream_t s,
-                           int64_t wcap = -1);
+                           int64_t wcap = -1, void* lh = nullptr);
 
 // K3: triangular solves with the packed factor, in place on v (np = N*TILE
 // entries of type T).  tmp: np entries of scratch.
@@ -232,6 +235,26 @@ cudaError_t launch_forward_persistent(const T* Z, const T* Dinv, int64_t N, cons
 template <typename T>
 cudaError_t launch_backward_persistent(const T* Z, const T* Dinv, int64_t N, const T* yv, T* x, unsigned* flags,
                                        DevStatus* st, uint64_t timeout_ns, cudaStream_t s);
+// K3, in-core sweeps with one 128 x 128 product per tile on the critical
+// path (k_chain.cu).  After a factor: launch_chain_prep forms Sf (N tiles,
+// tile I = (inv(L_II) L_{I,I-1})^T) and Sb (N tiles, tile I =
+// L_{I+1,I} inv(L_II)) from the FP32 factor Z and Dinv (2N tiles: inv(L_II),
+// then the transposes).  Per correction: launch_scale_rhs_unset (v = r /
+// r_max as launch_scale_rhs, y = the "not yet written" pattern), the forward
+// sweep v -> y (v is reset to the pattern), the backward sweep y -> x (x = v
+// of the forward sweep).  Lt: the off-diagonal tiles (packed, FP32 or FP16
+// scaled by 1/lscale).  Waits give up timeout_ns after the launch started
+// and raise ST_TIMEOUT (the results are then invalid).
+cudaError_t launch_chain_prep(const float* Z, const float* Dinv, int64_t N, float* Sf, float* Sb, cudaStream_t s);
+cudaError_t launch_scale_rhs_unset(const double* r, int64_t n, int64_t np, float* v, float* y, const DevStatus* st,
+                                   cudaStream_t s);
+template <typename TL>
+cudaError_t launch_forward_chain(const TL* Lt, float lscale, const float* Dinv, const float* Sf, int64_t N, float* v,
+                                 float* y, DevStatus* st, uint64_t timeout_ns, cudaStream_t s);
+template <typename TL>
+cudaError_t launch_backward_chain(const TL* Lt, float lscale, const float* Dinv, const float* Sb, int64_t N,
+                                  const float* y, float* x, DevStatus* st, uint64_t timeout_ns, cudaStream_t s);
+
 // The same sweeps with the transposed inverses given directly (DinvT: N tiles
 // of inv(L_II)^T), for the triangle of one slab of the out-of-core factor;
 // z_on_host: Z is host memory read in place (no L2 prefetch hints).

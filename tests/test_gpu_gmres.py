@@ -81,6 +81,8 @@ def test_auto_takes_fp16_with_gmres(cube):
     assert info["precision_used"] == M.PREC_FP16, info
     assert info["fallback"] == 4 and info["gmres_iters"] > 0, info
     assert 0.0 < info["probe_rho"] <= 16.0, info
+    # the first outer residual (far above the tolerance) in float-float
+    assert info["residual_evals_ff"] >= 1 and info["residual_evals"] >= 1, info
     _check(X, 1.0, w, mag, ref)
     # the adjoint solve reuses that factor and goes to GMRES-IR at once
     b = torch.linspace(0.5, 1.5, X.shape[0], dtype=torch.float64, device="cuda")
@@ -92,7 +94,7 @@ def test_auto_takes_fp16_with_gmres(cube):
 
 
 def test_auto_default_keeps_the_split_factor_below_the_size_rule(cube):
-    # fp16_gmres = 0 (default) at n = 9600 < 133,000: the split factor
+    # fp16_gmres = 0 (default) at n = 9600 < 72,000: the split factor
     X, ref = cube
     c = M.Context(M.Options(residual_mode="stored"))
     w, mag, info = c.solve(_dev(X), 1.0)
