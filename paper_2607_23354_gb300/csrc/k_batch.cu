@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(NT, MINB)
   __shared__ int s_q, s_flag;
   __shared__ double red[NT / 32][3];
   __shared__ double exptab[2 * EXPT_SIZE];
-  load_exp_table(exptab);
+  load_exp_table_d(exptab);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   Scratch S;
   S.Lf = scratch_f + (int64_t)blockIdx.x * (nmax * nmax + nmax);
@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(NT, MINB)
         const double d = Di[j];
         const double z = (unsigned long long)__double_as_longlong(d) > tiny_bits
                              ? f32_to_f64_nonneg(exp_neg_tiny_td(tf, P.t, d))
-                             : exp_neg_small(P.t * d, exptab);
+                             : exp_neg_small_d(P.t * d, exptab);
         S.Zd[(int64_t)i * n + j] = z;
         S.Zd[(int64_t)j * n + i] = z;
         S.Lf[(int64_t)i * n + j] = f64_to_f32_nonneg(z);

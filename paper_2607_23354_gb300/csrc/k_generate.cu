@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
   double* xc = smem + TILE * GEN_MC;   // [GEN_MC][TILE] column points (conflict free)
   __shared__ double colpart[GEN_THREADS / 32][TILE];
   __shared__ unsigned long long warpmin[GEN_THREADS / 32];
-  __shared__ double exptab[2 * EXPT_SIZE];
+  __shared__ __align__(16) double exptab[EXPT_SMEM];
   if (WD) load_exp_table(exptab);
 
   int64_t I, J;
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(256) k_generate_from_dist(const double* __rest
                                                             float* __restrict__ Zf, double* __restrict__ Zd,
                                                             double* __restrict__ rowsum, int kind, double dcut,
                                                             double kc) {
-  __shared__ double exptab[2 * EXPT_SIZE];
+  __shared__ __align__(16) double exptab[EXPT_SMEM];
   __shared__ float colpart[8][TILE];
   load_exp_table(exptab);
   __syncthreads();

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_resid_mf(const double* __restri
   extern __shared__ double sm[];
   double* xc = sm;            // [ct][m]
   double* wc = sm + ct * m;   // [ct]
-  __shared__ double exptab[2 * EXPT_SIZE];
+  __shared__ __align__(16) double exptab[EXPT_SMEM];
   load_exp_table(exptab);
   const int64_t j = (int64_t)blockIdx.x * RES_THREADS + threadIdx.x;
   const int64_t ntiles = (n + ct - 1) / ct;
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(SYM_THREADS, 1)
   double* xc = smem + TILE * SYM_MC;   // [SYM_MC][TILE] column points
   __shared__ double colpart[SYM_THREADS / 32][TILE];
   __shared__ float zcol[SYM_THREADS / 32][TILE];
-  __shared__ double exptab[2 * EXPT_SIZE];
+  __shared__ __align__(16) double exptab[EXPT_SMEM];
   load_exp_table(exptab);
   int64_t I, J;
   tri_coords((int64_t)blockIdx.x, &I, &J);
@@ -666,7 +666,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_grad(const double* __restrict__
   double* xc = sm;                 // [ct][m]
   double* wc = sm + ct * m;        // [ct]
   double* lc = sm + ct * (m + 1);  // [ct]
-  __shared__ double exptab[2 * EXPT_SIZE];
+  __shared__ __align__(16) double exptab[EXPT_SMEM];
   load_exp_table(exptab);
   const int64_t i = (int64_t)blockIdx.x * RES_THREADS + threadIdx.x;
   const bool live = i < n;

@@ -12,9 +12,11 @@
 // operations on the bit patterns (the FP64 pipe is the generator's limit).
 // At most about one unit in the last place from the exact value (the tests
 // compare it with the host libm exp).  Results below 2^-1021 (x below about
-// -707.7) are returned as 0, NaN propagates.  The 2 * EXPT_SIZE-double table
-// (T_hi, T_lo pairs) must be staged by the caller, usually in shared memory:
-// load_exp_table().
+// -707.7) are returned as 0, NaN propagates.  The table (T_hi, T_lo pairs,
+// then the FP32 pieces exp_neg_small uses) must be staged by the caller,
+// usually in shared memory: EXPT_SMEM doubles filled by load_exp_table()
+// (or the 2 * EXPT_SIZE doubles of load_exp_table_d() for exp_neg and
+// exp_neg_small_d alone).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -23,8 +25,16 @@ namespace mag {
 
 #include "exp_table.inc"
 
-__device__ __forceinline__ void load_exp_table(double* tab) {
+// Doubles of the shared-memory table of load_exp_table.
+constexpr int EXPT_SMEM = 4 * EXPT_SIZE;
+
+__device__ __forceinline__ void load_exp_table_d(double* tab) {
   for (int i = threadIdx.x; i < 2 * EXPT_SIZE; i += blockDim.x) tab[i] = kExpTable[i];
+}
+__device__ __forceinline__ void load_exp_table(double* tab) {
+  load_exp_table_d(tab);
+  float* f = reinterpret_cast<float*>(tab + 2 * EXPT_SIZE);
+  for (int i = threadIdx.x; i < 4 * EXPT_SIZE; i += blockDim.x) f[i] = kExpTableF[i];
 }
 
 __device__ __forceinline__ double exp_neg(double x, const double* tab) {
@@ -56,8 +66,9 @@ __device__ __forceinline__ double exp_neg(double x, const double* tab) {
 // bits (truncation and the FP32 constant move a N below 23,700 by less than
 // 0.005, so |r| <= 0.5042 ln2/256 and the first omitted series term stays
 // below 4.1e-17 relative) and N widened to FP64 on the integer pipe: eight
-// FP64 operations against exp_neg's ten, same accuracy.
-__device__ __forceinline__ double exp_neg_small(double a, const double* tab) {
+// FP64 operations against exp_neg's ten, same accuracy.  Table of
+// load_exp_table_d.
+__device__ __forceinline__ double exp_neg_small_d(double a, const double* tab) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(a);
   const float af = (b >> 52) < 1023 - 126 ? 0.0f : __uint_as_float((unsigned)(b >> 29) - ((1023u - 127u) << 23));
   // af 256/ln2 + 1.5 2^23, rounded once: the low bits hold N
@@ -80,6 +91,88 @@ __device__ __forceinline__ double exp_neg_small(double a, const double* tab) {
   const int j = M & (EXPT_SIZE - 1), k = M >> 8;
   const double th = tab[2 * j], tl = tab[2 * j + 1];
   const double s = th + fma(th, p, tl);
+  return __hiloint2double(__double2hiint(s) + k * (1 << 20), __double2loint(s));
+}
+
+__device__ __forceinline__ double f32_to_f64_nonneg(float v);
+
+// v (any FP32 value) to FP64 on the integer pipe; FP32 subnormals give 0.
+__device__ __forceinline__ double f32_to_f64(float v) {
+  const unsigned b = __float_as_uint(v);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e == 0u) return 0.0;
+  if (e == 255u) return (double)v;  // inf, NaN
+  return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) |
+                                          ((unsigned long long)(e + (1023u - 127u)) << 52) |
+                                          ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
+// exp(-a) for 0 <= a <= 64 with four FP64 operations.  N and its FP64 copy
+// as in exp_neg_small_d; r = N ln2/256 - a = r1 + rc with r1 = N L1 - a,
+// exact in one FP64 FMA (N L1 is exact and close to a), and rc = N L2 in
+// float-float.  exp(-a) = 2^(-N/256) exp(r) and
+//   T exp(r) = T_hi + T_hi r1 + (T_hi (u + rc) + T_lo) + O(2^-100),
+//   u = exp(r) - 1 - r = r^2/2 + r^3/6 + r^4/24 + r^5/120 + O(9e-21):
+// the last bracket, below 1e-6 T_hi, needs only a relative accuracy of
+// 2^-40 and is formed in float-float on the FP32 pipe from r split into
+// FP32 parts (rh + rl, |rl| <= ulp(rh)) -- r^2 and r^3 from exact products
+// (FMA), r^4 and r^5 in plain FP32 -- then widened to FP64 on the integer
+// pipe.  The FP64 work is r1, the sum of the two widened parts, one FMA and
+// the final sum, whose rounding dominates: within about 0.51 units in the
+// last place (compared with the host libm in the tests).
+__device__ __forceinline__ double exp_neg_small(double a, const double* tab) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+  const float af = (b >> 52) < 1023 - 126 ? 0.0f : __uint_as_float((unsigned)(b >> 29) - ((1023u - 127u) << 23));
+  const float shifted = fmaf(af, 0x1.715476p+8f, 12582912.0f);
+  const int N = __float_as_int(shifted) - 0x4B400000;
+  const float kf = shifted - 12582912.0f;  // N as an FP32, exact
+  const unsigned nb = __float_as_uint(kf);
+  const double kd =
+      nb == 0u ? 0.0
+               : __longlong_as_double((long long)(((unsigned long long)((nb >> 23) + (1023u - 127u)) << 52) |
+                                                  ((unsigned long long)(nb & 0x7fffffu) << 29)));
+  const double r1 = fma(kd, EXPT_L1, -a);
+  const float rch = kf * EXPT_L2H;
+  const float rcl = fmaf(kf, EXPT_L2L, fmaf(kf, EXPT_L2H, -rch));
+  // r1 = rh0 + rl0 on the integer pipe (leading 24 bits; the next 23 bits);
+  // |r1| below 2^-103 counts as 0 here (it still enters through T_hi r1)
+  const unsigned long long rb = (unsigned long long)__double_as_longlong(r1);
+  const unsigned re = (unsigned)(rb >> 52) & 0x7ffu;
+  const unsigned rs = (unsigned)(rb >> 32) & 0x80000000u;
+  float rh0 = 0.0f, rl0 = 0.0f;
+  if (re >= 920u) {
+    rh0 = __uint_as_float(rs | ((re - (1023u - 127u)) << 23) | ((unsigned)(rb >> 29) & 0x7fffffu));
+    const float f = __uint_as_float((((unsigned)rb & 0x1fffffffu) >> 6) | 0x3f800000u) - 1.0f;
+    rl0 = __uint_as_float(__float_as_uint(f * __uint_as_float((re - 919u) << 23)) | rs);
+  }
+  // r = rh + rl: rc folded in, renormalized (|rl0 + rch| < |rh0| or rh0 = 0)
+  const float t1 = rl0 + rch;
+  const float rh = rh0 + t1;
+  const float rl = (rh0 - rh) + t1;
+  // u = uh + ul
+  const float p = rh * rh;
+  const float pe = fmaf(2.0f * rh, rl, fmaf(rh, rh, -p));  // r^2 = p + pe
+  const float c = p * rh;
+  const float ce = fmaf(pe, rh, fmaf(p, rl, fmaf(p, rh, -c)));  // r^3 = c + ce
+  const float d = c * EXPT_S6H;
+  const float de = fmaf(c, EXPT_S6L, fmaf(ce, EXPT_S6H, fmaf(c, EXPT_S6H, -d)));  // r^3/6 = d + de
+  const float q = (p * p) * fmaf(rh, 1.0f / 120.0f, 1.0f / 24.0f);
+  const float hp = 0.5f * p;  // |r^3/6| < |r^2/2|: the sum's error is exact below
+  const float uh = hp + d;
+  const float ul = (((hp - uh) + d) + 0.5f * pe) + (de + q);
+  // g = u + rc (rc >= 0, either may be the larger)
+  const float gh = uh + rch;
+  const float bv = gh - uh;
+  const float gl = ((uh - (gh - bv)) + (rch - bv)) + (ul + rcl);
+  // exp(-a) = 2^(-N/256) exp(r): -N = 256 k + j
+  const int M = -N;
+  const int j = M & (EXPT_SIZE - 1), k = M >> 8;
+  const double th = tab[2 * j];
+  const float4 T = reinterpret_cast<const float4*>(tab + 2 * EXPT_SIZE)[j];  // TH, TL, T_lo, 0
+  const float vh = T.x * gh;  // >= 0
+  const float vl = fmaf(T.x, gl, fmaf(T.y, gh, fmaf(T.x, gh, -vh))) + T.z;
+  const double w = f32_to_f64_nonneg(vh) + f32_to_f64(vl);
+  const double s = th + fma(th, r1, w);
   return __hiloint2double(__double2hiint(s) + k * (1 << 20), __double2loint(s));
 }
 

@@ -491,6 +491,26 @@ def test_fp64_exponential_over_its_range(ctx):
     assert np.all(np.abs(Zg - ref) <= 2 * np.spacing(ref))
 
 
+def test_fp64_exponential_random_arguments(ctx):
+    # points at random multiples of 2^-30 in [0, 1) on a line and t = 64:
+    # every t d_ij is an exact FP64 value in [0, 64), the range of the
+    # four-FP64-operation exponential (float-float polynomial).  Against an
+    # extended-precision reference it is within about half a unit in the
+    # last place (the final rounding); a plain-double reference adds its
+    # own half unit.
+    n = 1500
+    rng = np.random.default_rng(61)
+    X = np.zeros((n, 1))
+    X[:, 0] = rng.integers(0, 2 ** 30, n) * 2.0 ** -30
+    Zg = ctx.similarity_matrix(_dev(X), 64.0, "fp64").cpu().numpy()
+    a = 64.0 * np.abs(X[:, 0][:, None] - X[:, 0][None, :])
+    ext = np.finfo(np.longdouble).nmant >= 63
+    ref = np.exp(-a.astype(np.longdouble)) if ext else np.exp(-a)
+    ulp = np.spacing(np.exp(-a))
+    err = np.abs(Zg.astype(np.longdouble) - ref) / ulp
+    assert float(err.max()) <= (0.6 if ext else 1.1), float(err.max())
+
+
 @pytest.mark.parametrize("resid", ["stored", "matrix_free"])
 def test_solve_multi_reuses_distances_and_matches(ctx, resid):
     X = _cloud(1500, 8, seed=71)
