@@ -193,6 +193,16 @@ typedef struct mag_options {
                              1 the same with FP32 tiles always; 2 the sweeps
                              with one progress counter and the full tile
                              product per step                               */
+  int32_t exact_distances;  /* distances of a multi-t call (mag_solve_multi,
+                             mag_sweep_tplus) from coordinates quantized to
+                             a common grid, as exact integer sums on the
+                             integer pipe (1, default; pairs closer than
+                             sqrt(m) 2^53 times the grid step take FP64
+                             differences), or FP64 differences for all
+                             pairs (0).  Either way within the FP64
+                             differences' rounding of d; m <= 32 and finite
+                             coordinates, else FP64                          */
+  int32_t reserved4;
 } mag_options;
 
 /* Diagnostics of one call (all fields written when info != NULL). */
@@ -266,6 +276,9 @@ typedef struct mag_info {
                               chain sweeps with FP16 tiles, 1 with FP32 tiles,
                               2 the progress-counter sweeps (FP64 factor, out
                               of core, options.sweep_kind = 2); -1 none     */
+  int32_t exact_distances; /* 1: the distances came from the exact integer
+                              pass (options.exact_distances)                */
+  int32_t reserved6;
 } mag_info;
 
 typedef struct mag_ctx mag_ctx;

@@ -49,7 +49,8 @@ class mag_options(ctypes.Structure):
                 ("wait_timeout_ns", ctypes.c_int64), ("out_of_core", ctypes.c_int32),
                 ("deflate", ctypes.c_int32), ("host_limit_bytes", ctypes.c_double),
                 ("gmres_matvec", ctypes.c_int32), ("fp16_gmres", ctypes.c_int32),
-                ("batch_shape", ctypes.c_int32), ("sweep_kind", ctypes.c_int32)]
+                ("batch_shape", ctypes.c_int32), ("sweep_kind", ctypes.c_int32),
+                ("exact_distances", ctypes.c_int32), ("reserved4", ctypes.c_int32)]
 
 
 class mag_info(ctypes.Structure):
@@ -74,7 +75,8 @@ class mag_info(ctypes.Structure):
                 ("reserved2", ctypes.c_int32), ("ms_update_busy", ctypes.c_double),
                 ("batch_threads", ctypes.c_int32), ("batch_ctas_per_sm", ctypes.c_int32),
                 ("batch_tensor_cores", ctypes.c_int32), ("residual_evals_ff", ctypes.c_int32),
-                ("batch_left_looking", ctypes.c_int32), ("sweeps_used", ctypes.c_int32)]
+                ("batch_left_looking", ctypes.c_int32), ("sweeps_used", ctypes.c_int32),
+                ("exact_distances", ctypes.c_int32), ("reserved6", ctypes.c_int32)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -170,6 +172,7 @@ class Options:
     fp16_gmres: int = 0
     batch_shape: int = 0  # 0 tuned, 1..7 fixed
     sweeps: str = "chain"  # "chain", "chain_fp32" (FP32 tiles always), "progress"
+    exact_distances: bool = True
 
     def to_c(self) -> mag_options:
         o = mag_options()
@@ -202,6 +205,7 @@ class Options:
         if self.sweeps not in kinds:
             raise ValueError(f"sweeps must be one of {sorted(kinds)}, not {self.sweeps!r}")
         o.sweep_kind = kinds[self.sweeps]
+        o.exact_distances = int(self.exact_distances)
         return o
 
 

@@ -302,6 +302,209 @@ __global__ void k_rowsum_max(const double* __restrict__ rowsum, int64_t n, DevSt
   if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&st->off_max_bits, fmax(v, 0.0));
 }
 
+// ---------------------------------------------------------------- exact d^2
+// Pair distances from quantized coordinates (quantize_points in the host
+// code): every coordinate is an integer multiple of 2^-e relative to its
+// dimension's minimum (x = lo_l + q 2^-e, |x - that| <= 2^-e), so a pair's
+// d^2 = 2^-2e sum_l (q_il - q_jl)^2 is an exact integer sum, here in 128
+// bits on the integer pipe: |D| < 2^(2L) in two L-bit limbs, three 64-bit
+// sums (lo lo, hi lo, hi hi) of 32 x 32 -> 64-bit multiply-adds, combined
+// and rounded to FP64 once.  The quantization moves d by at most
+// 2 sqrt(m) 2^-e, no more than the FP64 differences' rounding (2^-52 d)
+// once d >= sqrt(m) 2^(53-e); closer pairs (d^2 below tau2) take the FP64
+// differences from the points instead.  Replaces 2m FP64 operations per
+// pair; the square root stays FP64 (sqrt_pos).
+struct QuantParams {
+  int L;        // limb bits
+  int e;        // coordinate scale exponent
+  double tau2;  // d^2 below which a pair takes the FP64 differences
+};
+
+// 2^-2e (C 2^2L + Bx 2^(L+1) + A) rounded to nearest FP64 (A, Bx, C < 2^63)
+__device__ __forceinline__ double q128_to_f64(unsigned long long A, unsigned long long Bx, unsigned long long C,
+                                              int L, int e) {
+  unsigned long long ql = A, qh = 0;
+  const unsigned long long bl = Bx << (L + 1), bh = Bx >> (63 - L);
+  ql += bl;
+  qh += bh + (ql < bl ? 1ull : 0ull);
+  const unsigned long long cl = C << (2 * L), ch = C >> (64 - 2 * L);
+  ql += cl;
+  qh += ch + (ql < cl ? 1ull : 0ull);
+  if ((qh | ql) == 0ull) return 0.0;
+  const int lz = qh ? __clzll((long long)qh) : 64 + __clzll((long long)ql);
+  unsigned long long nh, nl;
+  if (lz == 0) {
+    nh = qh;
+    nl = ql;
+  } else if (lz < 64) {
+    nh = (qh << lz) | (ql >> (64 - lz));
+    nl = ql << lz;
+  } else {
+    nh = ql << (lz - 64);
+    nl = 0ull;
+  }
+  // the top 53 of the 128 bits, rounded to nearest even on the other 75
+  unsigned long long mant = nh >> 11;
+  const unsigned long long rest = nh & 0x7ffull;
+  const bool up = (rest >> 10) && ((rest & 0x3ffull) || nl || (mant & 1ull));
+  mant += up ? 1ull : 0ull;
+  // leading bit 127 - lz of the integer, times 2^-2e; mant carries the
+  // implicit bit (a rounding carry to 2^53 moves the exponent by one)
+  const long long ex = 127 - lz - 2 * e;
+  return __longlong_as_double((long long)(((unsigned long long)(ex + 1022) << 52) + mant));
+}
+
+// d^2 of rows (x) and columns (y) given as quantized coordinates, m terms
+__device__ __forceinline__ void q_accumulate(long long a, long long b, unsigned long long mask, int L,
+                                             unsigned long long& A, unsigned long long& Bx,
+                                             unsigned long long& C) {
+  const long long dv = a - b;
+  const unsigned long long ad = dv < 0 ? 0ull - (unsigned long long)dv : (unsigned long long)dv;
+  const unsigned lo = (unsigned)(ad & mask), hi = (unsigned)(ad >> L);
+  A += (unsigned long long)lo * lo;
+  Bx += (unsigned long long)hi * lo;
+  C += (unsigned long long)hi * hi;
+}
+
+// FP64 distances of the packed lower tiles from the quantized coordinates
+// (m <= GEN_MC; MQ8: m <= 8, a column's coordinates held in registers),
+// with min d^2 and the coincident-point flag as k_generate: one CTA per
+// tile, warp w on tile rows w + 16 i (i < 8), lane l on columns 32 q + l
+// (q < 4), each pair finished and stored on its own (a warp's store covers
+// 32 consecutive entries of a row).  Rows and columns of the padding get
+// d = 0 (the generator from distances gives them the identity by index).
+template <bool MQ8>
+__global__ void __launch_bounds__(GEN_THREADS, 1)
+    k_dist_q(const long long* __restrict__ Xq, const double* __restrict__ X, int64_t n, int m, QuantParams qp,
+             double* __restrict__ Dd, DevStatus* st) {
+  extern __shared__ double smem[];
+  long long* xr = reinterpret_cast<long long*>(smem);  // [TILE][GEN_MC] row points (broadcast reads)
+  long long* xc = xr + TILE * GEN_MC;                  // [GEN_MC][TILE] column points (conflict free)
+  __shared__ unsigned long long warpmin[GEN_THREADS / 32];
+  int64_t I, J;
+  tri_coords((int64_t)blockIdx.x, &I, &J);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row0 = I * TILE, col0 = J * TILE;
+  const int mc = MQ8 ? 8 : m;  // MQ8: dimensions m .. 7 staged as zeros
+  for (int e = threadIdx.x; e < TILE * mc; e += GEN_THREADS) {
+    const int r = e / mc, l = e - r * mc;
+    const int64_t gr = row0 + r, gc = col0 + r;
+    xr[r * GEN_MC + l] = gr < n && l < m ? Xq[gr * m + l] : 0ll;
+    xc[l * TILE + r] = gc < n && l < m ? Xq[gc * m + l] : 0ll;
+  }
+  __syncthreads();
+  const unsigned long long mask = (1ull << qp.L) - 1ull;
+  const unsigned long long tau2_bits = (unsigned long long)__double_as_longlong(qp.tau2);
+  const int64_t tile_off = tri_index(I, J) * TILE_ELEMS;
+  unsigned long long mind2b = 0x7ff0000000000000ull;  // +inf
+  int flags = 0;
+  for (int q = 0; q < 4; ++q) {
+    const int c = 32 * q + lane;
+    const int64_t gc = col0 + c;
+    long long cv[8];
+    if (MQ8) {
+#pragma unroll
+      for (int l = 0; l < 8; ++l) cv[l] = xc[l * TILE + c];
+    }
+#pragma unroll 2
+    for (int i = 0; i < 8; ++i) {
+      const int r = warp + 16 * i;
+      const int64_t gr = row0 + r;
+      const long long* xrow = xr + r * GEN_MC;
+      unsigned long long A = 0ull, Bx = 0ull, C = 0ull;
+      if (MQ8) {
+#pragma unroll
+        for (int l = 0; l < 8; ++l) q_accumulate(xrow[l], cv[l], mask, qp.L, A, Bx, C);
+      } else {
+        for (int l = 0; l < m; ++l) q_accumulate(xrow[l], xc[l * TILE + c], mask, qp.L, A, Bx, C);
+      }
+      double dd = 0.0;
+      if (gr < n && gc < n && gr != gc) {
+        double v = q128_to_f64(A, Bx, C, qp.L, qp.e);
+        unsigned long long vb = (unsigned long long)__double_as_longlong(v);
+        if (vb < tau2_bits) {
+          // close pair: the FP64 differences of the points, as k_generate
+          v = 0.0;
+          for (int l = 0; l < m; ++l) {
+            const double diff = X[gr * m + l] - X[gc * m + l];
+            v = fma(diff, diff, v);
+          }
+          vb = (unsigned long long)__double_as_longlong(v);
+        }
+        if (vb == 0ull) flags |= ST_DUPLICATE;
+        else mind2b = vb < mind2b ? vb : mind2b;
+        dd = sqrt_pos(v);
+      }
+      Dd[tile_off + (int64_t)r * TILE + c] = dd;
+    }
+  }
+  if (flags) atomicOr(&st->flags, flags);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_xor_sync(0xffffffffu, mind2b, o);
+    mind2b = other < mind2b ? other : mind2b;
+  }
+  if (lane == 0) warpmin[warp] = mind2b;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long v = warpmin[0];
+    for (int w = 1; w < GEN_THREADS / 32; ++w) v = warpmin[w] < v ? warpmin[w] : v;
+    if (v < 0x7ff0000000000000ull) atomicMin(&st->min_d2_bits, v);
+  }
+}
+
+// Per dimension l < m (one CTA each): min and max of X[:, l] into
+// out[2 l], out[2 l + 1]; out[2 m] = 1 if a coordinate is not finite.
+__global__ void k_coord_range(const double* __restrict__ X, int64_t n, int m, double* __restrict__ out) {
+  const int l = blockIdx.x;
+  double lo = INFINITY, hi = -INFINITY;
+  int bad = 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = X[i * m + l];
+    if (!isfinite(v)) bad = 1;
+    lo = fmin(lo, v);
+    hi = fmax(hi, v);
+  }
+  __shared__ double slo[32], shi[32];
+  __shared__ int sbad;
+  if (threadIdx.x == 0) sbad = 0;
+  __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if (bad) atomicOr(&sbad, 1);
+  if ((threadIdx.x & 31) == 0) {
+    slo[threadIdx.x >> 5] = lo;
+    shi[threadIdx.x >> 5] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      lo = fmin(lo, slo[w]);
+      hi = fmax(hi, shi[w]);
+    }
+    out[2 * l] = lo;
+    out[2 * l + 1] = hi;
+    if (sbad) out[2 * m] = 1.0;
+  }
+}
+
+// q = round(2^e (x - lo_l)) with x - lo_l taken exactly as s + err (TwoSum):
+// round(2^e s) + round(2^e err), within one unit of 2^e (x - lo_l).
+__global__ void k_quantize(const double* __restrict__ X, int64_t n, int m, const double* __restrict__ range,
+                           int e, long long* __restrict__ Xq) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n * m) return;
+  const int l = (int)(k % m);
+  const double x = X[k], b = -range[2 * l];
+  const double s = x + b;
+  const double bv = s - x;
+  const double err = (x - (s - bv)) + (b - bv);
+  Xq[k] = __double2ll_rn(ldexp(s, e)) + __double2ll_rn(ldexp(err, e));
+}
+
 template <bool WF, bool WD, bool ROWSUM, bool WDIST = false>
 cudaError_t launch_gen_t(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
                          double* Zd, double* rowsum, DevStatus* st, cudaStream_t s, double* Dd = nullptr,
@@ -343,6 +546,43 @@ cudaError_t launch_generate_dist(const double* X, int64_t n, int m, double t, in
   if (Zd)
     return launch_gen_t<false, true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd, kind, tiny_arg, 0, -1, kc);
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_coord_range(const double* X, int64_t n, int m, double* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out + 2 * m, 0, sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  k_coord_range<<<m, 1024, 0, s>>>(X, n, m, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quantize(const double* X, int64_t n, int m, const double* range, int e, long long* Xq,
+                            cudaStream_t s) {
+  const int64_t k = n * m;
+  k_quantize<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(X, n, m, range, e, Xq);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dist_q(const long long* Xq, const double* X, int64_t n, int m, int L, int e, double tau2,
+                          int64_t N, double* Dd, DevStatus* st, cudaStream_t s) {
+  if (m < 1 || m > GEN_MC) return cudaErrorInvalidValue;
+  const size_t smem = 2 * (size_t)TILE * GEN_MC * sizeof(long long);
+  const QuantParams qp{L, e, tau2};
+  const int64_t tiles = num_lower_tiles(N);
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  cudaError_t err;
+  if (m <= 8) {
+    err = cudaFuncSetAttribute(k_dist_q<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_dist_q<true><<<(unsigned)tiles, GEN_THREADS, smem, s>>>(Xq, X, n, m, qp, Dd, st);
+  } else {
+    err = cudaFuncSetAttribute(k_dist_q<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_dist_q<false><<<(unsigned)tiles, GEN_THREADS, smem, s>>>(Xq, X, n, m, qp, Dd, st);
+  }
+  note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_generate_from_dist(const double* Dd, int64_t n, double t, int64_t N, float* Zf, double* Zd,

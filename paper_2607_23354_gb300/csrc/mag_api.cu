@@ -89,6 +89,7 @@ struct mag_ctx {
   int64_t dist_n = 0;
   int32_t dist_m = 0;
   double dist_dmin = 0, dist_gersh_unused = 0;
+  bool dist_exact = false;           // the stored distances came from the exact integer pass
   void* bws = nullptr;               // batch workspace
   size_t bws_bytes = 0;
   int batch_tuned[12] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};  // launch shape per
@@ -138,6 +139,10 @@ struct mag_ctx {
   // tiles that the panel solve of the one-product factor writes
   float* chain_s = nullptr;
   size_t chain_s_bytes = 0;
+  // quantized coordinates of the exact distance pass: 2m + 1 doubles of
+  // ranges (and a flag), then n m int64
+  void* xq = nullptr;
+  size_t xq_bytes = 0;
   void* lh = nullptr;
   size_t lh_bytes = 0;
   bool chain_ready = false;          // chain_s holds the B tiles of the current factor
@@ -998,6 +1003,8 @@ int mag_options_default(mag_options* opt) {
   opt->fp16_gmres = 0;
   opt->batch_shape = 0;
   opt->sweep_kind = 0;
+  opt->exact_distances = 1;
+  opt->reserved4 = 0;
   return MAG_OK;
 }
 
@@ -1047,6 +1054,7 @@ int mag_ctx_destroy(mag_ctx* ctx) {
   if (ctx->gm) cudaFree(ctx->gm);
   if (ctx->probe_z) cudaFree(ctx->probe_z);
   if (ctx->chain_s) cudaFree(ctx->chain_s);
+  if (ctx->xq) cudaFree(ctx->xq);
   if (ctx->lh) cudaFree(ctx->lh);
   if (ctx->host_L) cudaFreeHost(ctx->host_L);
   for (auto& kv : ctx->task_tables)
@@ -1152,6 +1160,7 @@ struct SolveResult {
   double ms_update_busy = 0;
   int residual_evals_ff = 0;
   int sweeps_used = -1;
+  int exact_distances = 0;
   double probe_rho = 0, ms_probe = 0;
   int slabs = 0, host_slabs = 0;
   double host_bytes = 0, host_read_bytes = 0, ms_host_read = 0;
@@ -1171,6 +1180,48 @@ float elapsed(mag_ctx* ctx, int a, int b) {
 // Generate the tiles for the given precision into the current layout.
 // tiny_fp32: entries below e^-46 in FP32 (exp_neg_tiny_td), for the solve path;
 // the entry points that return Z or differentiate it keep FP64 everywhere.
+// Coordinates quantized for the exact distance pass (launch_dist_q): per
+// dimension the minimum lo_l, the largest span S < 2^E, limbs of L bits with
+// m 2^(2L) <= 2^63 (the kernel's 64-bit sums cannot wrap), B = 2L - 1 bits
+// per coordinate, scale 2^e with e = B - E (every coordinate offset below
+// 2^B), and tau2 = m 2^(106 - 2e): at d >= sqrt(tau2) the quantization
+// (at most 2 sqrt(m) 2^-e in d) is below 2^-52 d.  false: FP64 differences
+// instead (a non-finite coordinate, every dimension constant, m > 32, a
+// scale beyond 2^+-400, or no memory for the copy).
+bool quantize_points(mag_ctx* ctx, const double* X, int64_t n, int32_t m, int* L, int* e, double* tau2,
+                     const long long** Xq) {
+  if (!ctx->opt.exact_distances || m > 32 || m < 1) return false;
+  const size_t head = ((size_t)(2 * m + 1) * sizeof(double) + 255) & ~(size_t)255;
+  if (!grow_buffer(ctx, &ctx->xq, &ctx->xq_bytes, head + (size_t)n * m * sizeof(long long), 0)) return false;
+  double* range = (double*)ctx->xq;
+  long long* q = (long long*)((char*)ctx->xq + head);
+  cudaStream_t s = ctx->stream;
+  std::vector<double> h(2 * m + 1);
+  if (launch_coord_range(X, n, m, range, s) != cudaSuccess ||
+      cudaMemcpyAsync(h.data(), range, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (h[2 * m] != 0.0) return false;
+  double S = 0.0;
+  for (int l = 0; l < m; ++l) S = std::max(S, h[2 * l + 1] - h[2 * l]);
+  if (!(S > 0.0) || !std::isfinite(S)) return false;
+  const int E = std::ilogb(S) + 1;  // S < 2^E
+  int mb = 0;
+  while ((1 << mb) < m) ++mb;
+  *L = (63 - mb) / 2;
+  *e = (2 * *L - 1) - E;
+  if (*e < -400 || *e > 400) return false;
+  *tau2 = std::ldexp((double)m, 106 - 2 * *e);
+  if (launch_quantize(X, n, m, range, *e, q, s) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  *Xq = q;
+  return true;
+}
+
 int generate(mag_ctx* ctx, const double* X, int32_t m, double t, bool f32, bool f64, SolveResult* R,
              bool tiny_fp32 = false) {
   const double tiny_arg = tiny_fp32 ? kTinyArg : INFINITY;
@@ -1185,8 +1236,19 @@ int generate(mag_ctx* ctx, const double* X, int32_t m, double t, bool f32, bool 
     CU(launch_generate_from_dist(ctx->dist(), L.n, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr,
                                  ctx->vd(V_ROWSUM), s, ctx->kind, tiny_arg, ctx->kind_c));
   } else if (ctx->dist_active && L.dist) {
-    CU(launch_generate_dist(X, L.n, m, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr, ctx->dist(),
-                            ctx->vd(V_ROWSUM), ctx->st(), s, ctx->kind, tiny_arg, ctx->kind_c));
+    int qL = 0, qe = 0;
+    double qtau2 = 0.0;
+    const long long* Xq = nullptr;
+    if (quantize_points(ctx, X, L.n, m, &qL, &qe, &qtau2, &Xq)) {
+      // exact d^2 on the integer pipe, then Z from the distances
+      CU(launch_dist_q(Xq, X, L.n, m, qL, qe, qtau2, L.N, ctx->dist(), ctx->st(), s));
+      CU(launch_generate_from_dist(ctx->dist(), L.n, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr,
+                                   ctx->vd(V_ROWSUM), s, ctx->kind, tiny_arg, ctx->kind_c));
+      R->exact_distances = 1;
+    } else {
+      CU(launch_generate_dist(X, L.n, m, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr,
+                              ctx->dist(), ctx->vd(V_ROWSUM), ctx->st(), s, ctx->kind, tiny_arg, ctx->kind_c));
+    }
   } else {
     CU(launch_generate(X, L.n, m, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr,
                        ctx->vd(V_ROWSUM), ctx->st(), s, ctx->kind, tiny_arg, ctx->kind_c));
@@ -1197,6 +1259,7 @@ int generate(mag_ctx* ctx, const double* X, int32_t m, double t, bool f32, bool 
   R->ms_gen += elapsed(ctx, 0, 1);
   if (reuse) {
     R->dmin = ctx->dist_dmin;
+    R->exact_distances = ctx->dist_exact ? 1 : 0;
     R->gersh = 1.0 - bits_to_double(ctx->h_st->off_max_bits);
     return MAG_OK;
   }
@@ -1212,6 +1275,7 @@ int generate(mag_ctx* ctx, const double* X, int32_t m, double t, bool f32, bool 
     ctx->dist_n = L.n;
     ctx->dist_m = m;
     ctx->dist_dmin = R->dmin;
+    ctx->dist_exact = R->exact_distances != 0;
   }
   return MAG_OK;
 }
@@ -2107,6 +2171,7 @@ void fill_info(mag_ctx* ctx, const SolveResult& R, int64_t n, mag_info* info) {
   info->ms_update_busy = R.ms_update_busy;
   info->residual_evals_ff = R.residual_evals_ff;
   info->sweeps_used = R.sweeps_used;
+  info->exact_distances = R.exact_distances;
 }
 
 // The small-t end (Z close to 1 1^T, kappa(Z) growing like 1/t): with

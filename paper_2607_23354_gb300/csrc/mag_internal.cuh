@@ -114,6 +114,18 @@ cudaError_t launch_generate(const double* X, int64_t n, int m, double t, int64_t
 cudaError_t launch_generate_dist(const double* X, int64_t n, int m, double t, int64_t N, float* Zf,
                                  double* Zd, double* Dd, double* rowsum, DevStatus* st, cudaStream_t s,
                                  int kind = MAT_EXP, double tiny_arg = INFINITY, double kc = 0.0);
+// Exact pair distances from quantized coordinates (k_generate.cu).
+// launch_coord_range: per dimension min and max of X into out[2l], out[2l+1]
+// and out[2m] = 1 if a coordinate is not finite (2m + 1 doubles).
+// launch_quantize: Xq[i m + l] = round(2^e (X[i m + l] - out[2l])) (int64).
+// launch_dist_q: FP64 distances Dd of the packed lower tiles (m <= 32) from
+// Xq (limb bits L, scale 2^e; pairs with d^2 < tau2 from the FP64
+// differences of X), min d^2 and ST_DUPLICATE into st as the generator.
+cudaError_t launch_coord_range(const double* X, int64_t n, int m, double* out, cudaStream_t s);
+cudaError_t launch_quantize(const double* X, int64_t n, int m, const double* range, int e, long long* Xq,
+                            cudaStream_t s);
+cudaError_t launch_dist_q(const long long* Xq, const double* X, int64_t n, int m, int L, int e, double tau2,
+                          int64_t N, double* Dd, DevStatus* st, cudaStream_t s);
 // FP32 tiles of one slab for the out-of-core factor: global tile columns
 // [t0, t0 + W) of rows [t0, N), in the slab layout (tile_index with column
 // cap W, tile (0, 0) = global (t0, t0)); no row sums; min d^2 and flags as

@@ -47,9 +47,9 @@ def test_options_defaults_and_struct_sizes(lib):
     assert o.precision == M.PREC_AUTO and o.ir_tol == 1e-14 and o.allow_fallback == 1
     assert o.residual_mode == M.RESID_AUTO and o.ir_max_iters > 0
     # sizes follow the C layout (natural alignment on both x86-64 and aarch64)
-    assert ctypes.sizeof(M.mag_options) == 104
+    assert ctypes.sizeof(M.mag_options) == 112
     assert ctypes.sizeof(M.mag_batch_desc) == 32
-    assert ctypes.sizeof(M.mag_info) == 6 * 4 + 6 * 8 + 2 * 4 + 6 * 8 + 8 + 2 * 4 + 2 * 8 + 4 * 8 + 2 * 8 + 8 + 2 * 4 + 4 * 8 + 2 * 4 + 8 + 6 * 4
+    assert ctypes.sizeof(M.mag_info) == 6 * 4 + 6 * 8 + 2 * 4 + 6 * 8 + 8 + 2 * 4 + 2 * 8 + 4 * 8 + 2 * 8 + 8 + 2 * 4 + 4 * 8 + 2 * 4 + 8 + 8 * 4
     assert lib.mag_options_default(None) == M.MAG_EINVAL
 
 

@@ -491,6 +491,36 @@ def test_fp64_exponential_over_its_range(ctx):
     assert np.all(np.abs(Zg - ref) <= 2 * np.spacing(ref))
 
 
+@pytest.mark.parametrize("m,offset,kind", [(8, 0.0, "cube"), (20, 0.0, "normal"), (3, 1e6, "cube")])
+def test_exact_distances_match_the_oracle(ctx, m, offset, kind):
+    # a multi-t call's distances from the quantized coordinates (exact
+    # integer sums; m <= 8 with the column coordinates in registers, m = 20
+    # the general loop; a cloud far from the origin exercises the exact
+    # offset) against FP64 differences and the oracle; ragged n
+    X = _cloud(1500 - 37, m, seed=91 + m, kind=kind) + offset
+    Xd = _dev(X)
+    ts = [1.0, 10.0]
+    out = {}
+    for exact in (True, False):
+        ctx.set_options(M.Options(exact_distances=exact))
+        try:
+            W, mags, infos = ctx.solve_multi(Xd, ts)
+        finally:
+            ctx.set_options(M.Options())
+        assert all(i["exact_distances"] == int(exact) for i in infos), infos
+        out[exact] = (W.cpu().numpy(), mags, infos)
+    for k, t in enumerate(ts):
+        w_ref, mag_ref, _ = oracle.weighting(X, t)
+        for exact in (True, False):
+            check_solution(X, t, out[exact][0][k], out[exact][1][k], w_ref, mag_ref)
+        # both distance passes agree to the FP64 differences' rounding: the
+        # weightings to kappa(Z) times it
+        w1, w0 = out[True][0][k], out[False][0][k]
+        assert np.abs(w1 - w0).max() <= 1e-10 * np.abs(w0).max()
+    d1, d0 = out[True][2][0]["min_distance"], out[False][2][0]["min_distance"]
+    assert abs(d1 - d0) <= 4e-16 * d0
+
+
 def test_fp64_exponential_random_arguments(ctx):
     # points at random multiples of 2^-30 in [0, 1) on a line and t = 64:
     # every t d_ij is an exact FP64 value in [0, 64), the range of the
