@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
 #pragma unroll
       for (int l = 0; l < 8; ++l) cv[l] = xc[l * TILE + c];
     }
-#pragma unroll 2
+#pragma unroll 4
     for (int i = 0; i < 8; ++i) {
       const int r = warp + 16 * i;
       const int64_t gr = row0 + r;

@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(SYM_THREADS, 1)
           if ((unsigned long long)__double_as_longlong(d2[i][q]) > tiny_bits) {
             z = f32_to_f64_nonneg(exp_neg_tiny_td2(tf, t, d2[i][q]));
           } else {
-            z = exp_neg_small(t * sqrt_pos(d2[i][q]), exptab);
+            z = exp_neg_td(t, sqrt_pos(d2[i][q]), exptab);
           }
         } else {
           z = mat_entry(kind, t, kc, sqrt_pos(d2[i][q]), exptab);
@@ -699,7 +699,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_grad(const double* __restrict__
           d2 = fma(diff, diff, d2);
         }
       const double d = sqrt_pos(d2);
-      const double z = exp_neg_of(t * d, exptab);
+      const double z = exp_neg_td(t, d, exptab);
       // dL/dt contribution with Kahan compensation
       const double y = fma(li * d * z, wc[q], -st_c);
       const double tt = st_s + y;

@@ -33,8 +33,8 @@ __device__ __forceinline__ void load_exp_table_d(double* tab) {
 }
 __device__ __forceinline__ void load_exp_table(double* tab) {
   load_exp_table_d(tab);
-  float* f = reinterpret_cast<float*>(tab + 2 * EXPT_SIZE);
-  for (int i = threadIdx.x; i < 4 * EXPT_SIZE; i += blockDim.x) f[i] = kExpTableF[i];
+  unsigned* x = reinterpret_cast<unsigned*>(tab + 2 * EXPT_SIZE);
+  for (int i = threadIdx.x; i < 4 * EXPT_SIZE; i += blockDim.x) x[i] = kExpTableX[i];
 }
 
 __device__ __forceinline__ double exp_neg(double x, const double* tab) {
@@ -107,31 +107,22 @@ __device__ __forceinline__ double f32_to_f64(float v) {
                                           ((unsigned long long)(b & 0x7fffffu) << 29)));
 }
 
-// exp(-a) for 0 <= a <= 64 with four FP64 operations.  N and its FP64 copy
-// as in exp_neg_small_d; r = N ln2/256 - a = r1 + rc with r1 = N L1 - a,
-// exact in one FP64 FMA (N L1 is exact and close to a), and rc = N L2 in
-// float-float.  exp(-a) = 2^(-N/256) exp(r) and
+// exp(-a) for 0 <= a <= 64 in four FP64 operations (exp_neg_small) or
+// exp(-t d) in three (exp_neg_td).  N = round(256 a / ln 2) as in
+// exp_neg_small_d and r = N ln2/256 - a = r1 + rc, r1 = N L1 - a rounded
+// once (exact for exp_neg_small, whose a is a double; exp_neg_td forms N L1
+// exactly on the integer pipe and r1 = fma(-t, d, N L1), so t d is never
+// rounded), rc = N L2 in float-float.  exp(-a) = 2^(-N/256) exp(r) and
 //   T exp(r) = T_hi + T_hi r1 + (T_hi (u + rc) + T_lo) + O(2^-100),
 //   u = exp(r) - 1 - r = r^2/2 + r^3/6 + r^4/24 + r^5/120 + O(9e-21):
 // the last bracket, below 1e-6 T_hi, needs only a relative accuracy of
 // 2^-40 and is formed in float-float on the FP32 pipe from r split into
 // FP32 parts (rh + rl, |rl| <= ulp(rh)) -- r^2 and r^3 from exact products
 // (FMA), r^4 and r^5 in plain FP32 -- then widened to FP64 on the integer
-// pipe.  The FP64 work is r1, the sum of the two widened parts, one FMA and
-// the final sum, whose rounding dominates: within about 0.51 units in the
-// last place (compared with the host libm in the tests).
-__device__ __forceinline__ double exp_neg_small(double a, const double* tab) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(a);
-  const float af = (b >> 52) < 1023 - 126 ? 0.0f : __uint_as_float((unsigned)(b >> 29) - ((1023u - 127u) << 23));
-  const float shifted = fmaf(af, 0x1.715476p+8f, 12582912.0f);
-  const int N = __float_as_int(shifted) - 0x4B400000;
-  const float kf = shifted - 12582912.0f;  // N as an FP32, exact
-  const unsigned nb = __float_as_uint(kf);
-  const double kd =
-      nb == 0u ? 0.0
-               : __longlong_as_double((long long)(((unsigned long long)((nb >> 23) + (1023u - 127u)) << 52) |
-                                                  ((unsigned long long)(nb & 0x7fffffu) << 29)));
-  const double r1 = fma(kd, EXPT_L1, -a);
+// pipe.  The FP64 work after r1 is the sum of the two widened parts, one
+// FMA and the final sum, whose rounding dominates: within about 0.51 units
+// in the last place (compared with the host libm in the tests).
+__device__ __forceinline__ double exp_neg_core(int N, float kf, double r1, const double* tab) {
   const float rch = kf * EXPT_L2H;
   const float rcl = fmaf(kf, EXPT_L2L, fmaf(kf, EXPT_L2H, -rch));
   // r1 = rh0 + rl0 on the integer pipe (leading 24 bits; the next 23 bits);
@@ -167,13 +158,64 @@ __device__ __forceinline__ double exp_neg_small(double a, const double* tab) {
   // exp(-a) = 2^(-N/256) exp(r): -N = 256 k + j
   const int M = -N;
   const int j = M & (EXPT_SIZE - 1), k = M >> 8;
-  const double th = tab[2 * j];
-  const float4 T = reinterpret_cast<const float4*>(tab + 2 * EXPT_SIZE)[j];  // TH, TL, T_lo, 0
-  const float vh = T.x * gh;  // >= 0
-  const float vl = fmaf(T.x, gl, fmaf(T.y, gh, fmaf(T.x, gh, -vh))) + T.z;
+  // one 16-byte entry: T_hi, TL = T_hi - TH (TH: T_hi's leading 24 bits), T_lo
+  const uint4 T = reinterpret_cast<const uint4*>(tab + 2 * EXPT_SIZE)[j];
+  const double th = __hiloint2double((int)T.y, (int)T.x);
+  const float thh = __uint_as_float(((T.y << 3) | (T.x >> 29)) - ((1023u - 127u) << 23));
+  const float thl = __uint_as_float(T.z), tlf = __uint_as_float(T.w);
+  const float vh = thh * gh;  // >= 0
+  const float vl = fmaf(thh, gl, fmaf(thl, gh, fmaf(thh, gh, -vh))) + tlf;
   const double w = f32_to_f64_nonneg(vh) + f32_to_f64(vl);
   const double s = th + fma(th, r1, w);
   return __hiloint2double(__double2hiint(s) + k * (1 << 20), __double2loint(s));
+}
+
+// N = round(256 af / ln 2) for 0 <= af < 64 (FP32) and N as an FP32.
+__device__ __forceinline__ int exp_reduce_n(float af, float* kf) {
+  const float shifted = fmaf(af, 0x1.715476p+8f, 12582912.0f);
+  *kf = shifted - 12582912.0f;  // N as an FP32, exact
+  return __float_as_int(shifted) - 0x4B400000;
+}
+
+__device__ __forceinline__ double exp_neg_small(double a, const double* tab) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+  const float af = (b >> 52) < 1023 - 126 ? 0.0f : __uint_as_float((unsigned)(b >> 29) - ((1023u - 127u) << 23));
+  float kf;
+  const int N = exp_reduce_n(af, &kf);
+  const unsigned nb = __float_as_uint(kf);
+  const double kd =
+      nb == 0u ? 0.0
+               : __longlong_as_double((long long)(((unsigned long long)((nb >> 23) + (1023u - 127u)) << 52) |
+                                                  ((unsigned long long)(nb & 0x7fffffu) << 29)));
+  return exp_neg_core(N, kf, fma(kd, EXPT_L1, -a), tab);
+}
+
+__device__ __forceinline__ float f64_to_f32_nonneg(double x);
+
+// N L1 for 0 <= N < 2^15 exactly, on the integer pipe (L1 = L1M 2^L1E with
+// a 32-bit L1M: the product has at most 47 bits).
+__device__ __forceinline__ double nl1_exact(int N) {
+  if (N <= 0) return 0.0;
+  const unsigned long long pr = (unsigned long long)N * EXPT_L1M;
+  const int top = 63 - __clzll((long long)pr);  // leading bit
+  const unsigned long long mant = pr << (52 - top);
+  return __longlong_as_double((long long)(((unsigned long long)(top + EXPT_L1E + 1022) << 52) + mant));
+}
+
+// exp(-t d) for t > 0, d >= 0 (NaN propagates): N from the FP32 product of
+// t and d rounded on the integer pipe (within 2^-21 relative of t d, moving
+// N by less than 0.006), then the reduction without rounding t d; for t d
+// of about 63.5 or more the product is formed and exp_neg takes it.
+__device__ __forceinline__ double exp_neg_td(double t, double d, const double* tab) {
+  const float af = f64_to_f32_nonneg(t) * f64_to_f32_nonneg(d);
+  if (!(af < 63.5f)) {
+    const double a = t * d;
+    return (unsigned long long)__double_as_longlong(a) < 0x4050000000000000ull ? exp_neg_small(a, tab)
+                                                                               : exp_neg(-a, tab);
+  }
+  float kf;
+  const int N = exp_reduce_n(af, &kf);
+  return exp_neg_core(N, kf, fma(-t, d, nl1_exact(N)), tab);
 }
 
 // exp(-a) for a >= 0 (NaN propagates): exp_neg_small below 64, else exp_neg.
@@ -212,7 +254,7 @@ __device__ __forceinline__ double expm1_neg(double x, const double* tab) {
 __device__ __forceinline__ double mat_entry(int kind, double t, double kc, double dd, const double* tab) {
   if (kind == 1) return fma(-t, dd, 1.0);
   if (kind == 2) return fma(expm1_neg(-t * dd, tab), kc, 1.0);
-  return exp_neg_of(t * dd, tab);
+  return exp_neg_td(t, dd, tab);
 }
 
 // exp(-a) for a > kTinyArg = 46 (mag_internal.cuh; results below
