@@ -302,70 +302,6 @@ __global__ void k_rowsum_max(const double* __restrict__ rowsum, int64_t n, DevSt
   if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&st->off_max_bits, fmax(v, 0.0));
 }
 
-// ---------------------------------------------------------------- exact d^2
-// Pair distances from quantized coordinates (quantize_points in the host
-// code): every coordinate is an integer multiple of 2^-e relative to its
-// dimension's minimum (x = lo_l + q 2^-e, |x - that| <= 2^-e), so a pair's
-// d^2 = 2^-2e sum_l (q_il - q_jl)^2 is an exact integer sum, here in 128
-// bits on the integer pipe: |D| < 2^(2L) in two L-bit limbs, three 64-bit
-// sums (lo lo, hi lo, hi hi) of 32 x 32 -> 64-bit multiply-adds, combined
-// and rounded to FP64 once.  The quantization moves d by at most
-// 2 sqrt(m) 2^-e, no more than the FP64 differences' rounding (2^-52 d)
-// once d >= sqrt(m) 2^(53-e); closer pairs (d^2 below tau2) take the FP64
-// differences from the points instead.  Replaces 2m FP64 operations per
-// pair; the square root stays FP64 (sqrt_pos).
-struct QuantParams {
-  int L;        // limb bits
-  int e;        // coordinate scale exponent
-  double tau2;  // d^2 below which a pair takes the FP64 differences
-};
-
-// 2^-2e (C 2^2L + Bx 2^(L+1) + A) rounded to nearest FP64 (A, Bx, C < 2^63)
-__device__ __forceinline__ double q128_to_f64(unsigned long long A, unsigned long long Bx, unsigned long long C,
-                                              int L, int e) {
-  unsigned long long ql = A, qh = 0;
-  const unsigned long long bl = Bx << (L + 1), bh = Bx >> (63 - L);
-  ql += bl;
-  qh += bh + (ql < bl ? 1ull : 0ull);
-  const unsigned long long cl = C << (2 * L), ch = C >> (64 - 2 * L);
-  ql += cl;
-  qh += ch + (ql < cl ? 1ull : 0ull);
-  if ((qh | ql) == 0ull) return 0.0;
-  const int lz = qh ? __clzll((long long)qh) : 64 + __clzll((long long)ql);
-  unsigned long long nh, nl;
-  if (lz == 0) {
-    nh = qh;
-    nl = ql;
-  } else if (lz < 64) {
-    nh = (qh << lz) | (ql >> (64 - lz));
-    nl = ql << lz;
-  } else {
-    nh = ql << (lz - 64);
-    nl = 0ull;
-  }
-  // the top 53 of the 128 bits, rounded to nearest even on the other 75
-  unsigned long long mant = nh >> 11;
-  const unsigned long long rest = nh & 0x7ffull;
-  const bool up = (rest >> 10) && ((rest & 0x3ffull) || nl || (mant & 1ull));
-  mant += up ? 1ull : 0ull;
-  // leading bit 127 - lz of the integer, times 2^-2e; mant carries the
-  // implicit bit (a rounding carry to 2^53 moves the exponent by one)
-  const long long ex = 127 - lz - 2 * e;
-  return __longlong_as_double((long long)(((unsigned long long)(ex + 1022) << 52) + mant));
-}
-
-// d^2 of rows (x) and columns (y) given as quantized coordinates, m terms
-__device__ __forceinline__ void q_accumulate(long long a, long long b, unsigned long long mask, int L,
-                                             unsigned long long& A, unsigned long long& Bx,
-                                             unsigned long long& C) {
-  const long long dv = a - b;
-  const unsigned long long ad = dv < 0 ? 0ull - (unsigned long long)dv : (unsigned long long)dv;
-  const unsigned lo = (unsigned)(ad & mask), hi = (unsigned)(ad >> L);
-  A += (unsigned long long)lo * lo;
-  Bx += (unsigned long long)hi * lo;
-  C += (unsigned long long)hi * hi;
-}
-
 // FP64 distances of the packed lower tiles from the quantized coordinates
 // (m <= GEN_MC; MQ8: m <= 8, a column's coordinates held in registers),
 // with min d^2 and the coincident-point flag as k_generate: one CTA per

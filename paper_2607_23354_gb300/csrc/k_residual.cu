@@ -444,6 +444,125 @@ __global__ void __launch_bounds__(SYM_THREADS, 1)
   }
 }
 
+// k_resid_sym with the pair distances from quantized coordinates (Xq, the
+// exact integer d^2 of mag_math.cuh; pairs with d^2 < tau2 from the FP64
+// differences of X), Z = exp(-t d) only: the same entries, products, sums
+// and partials, with column q of a thread taken as the outer loop and each
+// pair finished on its own.
+__global__ void __launch_bounds__(SYM_THREADS, 1)
+    k_resid_sym_q(const long long* __restrict__ Xq, const double* __restrict__ X, int64_t n, int m, QuantParams qp,
+                  double t, const double* __restrict__ w, double* __restrict__ P, double* __restrict__ rowsum,
+                  int64_t N) {
+  extern __shared__ double smem[];
+  long long* xr = reinterpret_cast<long long*>(smem);  // [TILE][SYM_MC] row points
+  long long* xc = xr + TILE * SYM_MC;                  // [SYM_MC][TILE] column points
+  __shared__ double colpart[SYM_THREADS / 32][TILE];
+  __shared__ float zcol[SYM_THREADS / 32][TILE];
+  __shared__ __align__(16) double exptab[EXPT_SMEM];
+  __shared__ double s_wr[TILE], s_wc[TILE];
+  load_exp_table(exptab);
+  int64_t I, J;
+  tri_coords((int64_t)blockIdx.x, &I, &J);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row0 = I * TILE, col0 = J * TILE;
+  for (int e = threadIdx.x; e < TILE * m; e += SYM_THREADS) {
+    const int r = e / m, l = e - r * m;
+    const int64_t gr = row0 + r, gc = col0 + r;
+    xr[r * SYM_MC + l] = gr < n ? Xq[gr * m + l] : 0ll;
+    xc[l * TILE + r] = gc < n ? Xq[gc * m + l] : 0ll;
+  }
+  if (threadIdx.x < TILE) {
+    const int64_t gr = row0 + threadIdx.x, gc = col0 + threadIdx.x;
+    s_wr[threadIdx.x] = gr < n ? w[gr] : 0.0;
+    s_wc[threadIdx.x] = gc < n ? w[gc] : 0.0;
+  }
+  __syncthreads();
+  const unsigned long long mask = (1ull << qp.L) - 1ull;
+  const unsigned long long tau2_bits = (unsigned long long)__double_as_longlong(qp.tau2);
+  // d^2 above (kTinyArg / t)^2: t d > kTinyArg, the entry below e^-46
+  const double dcut = kTinyArg / t;
+  const unsigned long long tiny_bits = (unsigned long long)__double_as_longlong(dcut * dcut);
+  const float tf = (float)t;
+  double v[8];
+  float zv[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    v[i] = 0.0;
+    zv[i] = 0.0f;
+  }
+#pragma unroll 1
+  for (int q = 0; q < 4; ++q) {
+    const int c = lane + 32 * q;
+    const int64_t gc = col0 + c;
+    const double wcq = s_wc[c];
+    double csq = 0.0;
+    float zcq = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = warp + 16 * i;
+      const int64_t gr = row0 + r;
+      const long long* xrow = xr + r * SYM_MC;
+      unsigned long long A = 0ull, Bx = 0ull, C = 0ull;
+      for (int l = 0; l < m; ++l) q_accumulate(xrow[l], xc[l * TILE + c], mask, qp.L, A, Bx, C);
+      double z = 0.0;
+      if (gr < n && gc < n) {
+        if (gr == gc) {
+          z = 1.0;
+        } else {
+          double d2 = q128_to_f64(A, Bx, C, qp.L, qp.e);
+          if ((unsigned long long)__double_as_longlong(d2) < tau2_bits) {
+            d2 = 0.0;
+            for (int l = 0; l < m; ++l) {
+              const double diff = X[gr * m + l] - X[gc * m + l];
+              d2 = fma(diff, diff, d2);
+            }
+          }
+          if ((unsigned long long)__double_as_longlong(d2) > tiny_bits)
+            z = f32_to_f64_nonneg(exp_neg_tiny_td2(tf, t, d2));
+          else
+            z = exp_neg_td(t, sqrt_pos(d2), exptab);
+        }
+      }
+      v[i] = fma(z, wcq, v[i]);
+      csq = fma(z, s_wr[r], csq);
+      const float zf = f64_to_f32_nonneg(z);
+      zv[i] += zf;
+      zcq += zf;
+    }
+    colpart[warp][c] = csq;
+    zcol[warp][c] = zcq;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    double vi = v[i];
+    float zi = zv[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      vi += __shfl_xor_sync(0xffffffffu, vi, o);
+      zi += __shfl_xor_sync(0xffffffffu, zi, o);
+    }
+    const int r = warp + 16 * i;
+    const int64_t gr = row0 + r;
+    if (lane == 0) {
+      P[(I * N + J) * TILE + r] = vi;
+      if (gr < n) atomicAdd(rowsum + gr, (double)zi);
+    }
+  }
+  if (I == J) return;  // uniform: a diagonal tile's rows cover both triangles
+  __syncthreads();
+  if (threadIdx.x < TILE) {
+    double vc = 0.0;
+    float zc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < SYM_THREADS / 32; ++k) {
+      vc += colpart[k][threadIdx.x];
+      zc += zcol[k][threadIdx.x];
+    }
+    P[(J * N + I) * TILE + threadIdx.x] = vc;
+    if (col0 + threadIdx.x < n) atomicAdd(rowsum + col0 + threadIdx.x, (double)zc);
+  }
+}
+
 // r_j = b_j - (the N partials of row j, Neumaier), and the three norms.
 __global__ void k_resid_sym_finish(const double* __restrict__ P, int64_t n, int64_t N, int64_t np,
                                    const double* __restrict__ w, const double* __restrict__ b,
@@ -860,17 +979,26 @@ cudaError_t launch_residual_mf(const double* X, int64_t n, int m, double t, cons
 
 cudaError_t launch_residual_sym(const double* X, int64_t n, int m, double t, const double* w, const double* b,
                                 double* r, double* P, double* rowsum, int64_t np, DevStatus* st, cudaStream_t s,
-                                int kind, double kc) {
+                                int kind, double kc, const long long* Xq, int qL, int qe, double qtau2) {
   if (m < 1 || m > MAG_MAX_DIM) return cudaErrorInvalidValue;
   const int64_t N = (n + TILE - 1) / TILE;
   const int64_t tiles = num_lower_tiles(N);
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
   const size_t smem = 2 * (size_t)TILE * SYM_MC * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(k_resid_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaMemsetAsync(rowsum, 0, (size_t)n * sizeof(double), s);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(rowsum, 0, (size_t)n * sizeof(double), s);
-  if (e != cudaSuccess) return e;
-  k_resid_sym<<<(unsigned)tiles, SYM_THREADS, smem, s>>>(X, n, m, t, w, P, rowsum, N, kind, kc);
+  if (Xq && kind == MAT_EXP && m <= SYM_MC) {
+    const QuantParams qp{qL, qe, qtau2};
+    // the dimension loop stays a loop: unrolled over eight dimensions the
+    // kernel exceeds the 128 registers of its 512-thread launch bound
+    e = cudaFuncSetAttribute(k_resid_sym_q, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_resid_sym_q<<<(unsigned)tiles, SYM_THREADS, smem, s>>>(Xq, X, n, m, qp, t, w, P, rowsum, N);
+  } else {
+    e = cudaFuncSetAttribute(k_resid_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_resid_sym<<<(unsigned)tiles, SYM_THREADS, smem, s>>>(X, n, m, t, w, P, rowsum, N, kind, kc);
+  }
   note_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

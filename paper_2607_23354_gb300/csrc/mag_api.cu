@@ -143,6 +143,13 @@ struct mag_ctx {
   // ranges (and a flag), then n m int64
   void* xq = nullptr;
   size_t xq_bytes = 0;
+  bool xq_ok = false;                // xq holds the quantization of (xq_pts, xq_n, xq_m) for this solve
+  const double* xq_pts = nullptr;
+  int64_t xq_n = 0;
+  int32_t xq_m = 0;
+  int xq_L = 0, xq_e = 0;
+  double xq_tau2 = 0.0;
+  const long long* xq_q = nullptr;
   void* lh = nullptr;
   size_t lh_bytes = 0;
   bool chain_ready = false;          // chain_s holds the B tiles of the current factor
@@ -1190,6 +1197,7 @@ float elapsed(mag_ctx* ctx, int a, int b) {
 // scale beyond 2^+-400, or no memory for the copy).
 bool quantize_points(mag_ctx* ctx, const double* X, int64_t n, int32_t m, int* L, int* e, double* tau2,
                      const long long** Xq) {
+  ctx->xq_ok = false;
   if (!ctx->opt.exact_distances || m > 32 || m < 1) return false;
   const size_t head = ((size_t)(2 * m + 1) * sizeof(double) + 255) & ~(size_t)255;
   if (!grow_buffer(ctx, &ctx->xq, &ctx->xq_bytes, head + (size_t)n * m * sizeof(long long), 0)) return false;
@@ -1219,7 +1227,29 @@ bool quantize_points(mag_ctx* ctx, const double* X, int64_t n, int32_t m, int* L
     return false;
   }
   *Xq = q;
+  ctx->xq_ok = true;
+  ctx->xq_pts = X;
+  ctx->xq_n = n;
+  ctx->xq_m = m;
+  ctx->xq_L = *L;
+  ctx->xq_e = *e;
+  ctx->xq_tau2 = *tau2;
+  ctx->xq_q = q;
   return true;
+}
+
+// The quantized coordinates of this solve's points for the matrix-free
+// residual (quantize_points on first use; null: FP64 differences).
+const long long* quantized(mag_ctx* ctx, const double* X, int64_t n, int32_t m) {
+  if (ctx->xq_ok && ctx->xq_pts == X && ctx->xq_n == n && ctx->xq_m == m) return ctx->xq_q;
+  int L = 0, e = 0;
+  double tau2 = 0.0;
+  const long long* q = nullptr;
+  if (!quantize_points(ctx, X, n, m, &L, &e, &tau2, &q)) {
+    ctx->xq_ok = false;
+    return nullptr;
+  }
+  return q;
 }
 
 int generate(mag_ctx* ctx, const double* X, int32_t m, double t, bool f32, bool f64, SolveResult* R,
@@ -1452,9 +1482,11 @@ int residual(mag_ctx* ctx, const double* X, int32_t m, double t, const double* w
   else if (stored)
     CU(launch_residual_stored(ctx->zd(), L.n, L.N, w, b, ctx->vd(V_ROWSUM), r, ctx->spart(), L.np,
                               ctx->st(), s));
-  else
+  else {
+    const long long* q = ctx->kind == MAT_EXP ? quantized(ctx, X, L.n, m) : nullptr;
     CU(launch_residual_sym(X, L.n, m, t, w, b, r, ctx->spart(), ctx->vd(V_ROWSUM), L.np, ctx->st(), s, ctx->kind,
-                           ctx->kind_c));
+                           ctx->kind_c, q, ctx->xq_L, ctx->xq_e, ctx->xq_tau2));
+  }
   CU(cudaEventRecord(ctx->ev[1], s));
   TRY(read_status(ctx));
   if (ctx->h_st->flags & ST_TIMEOUT)
@@ -1641,9 +1673,11 @@ int gmres_ir(mag_ctx* ctx, int prec, const double* X, int32_t m, double t, const
                                    ctx->st(), s));
     else if (stored)
       CU(launch_residual_stored(ctx->zd(), n, L.N, v, zeros, ctx->vd(V_ROWSUM), tmp, ctx->spart(), np, ctx->st(), s));
-    else
+    else {
+      const long long* q = ctx->kind == MAT_EXP ? quantized(ctx, X, n, m) : nullptr;
       CU(launch_residual_sym(X, n, m, t, v, zeros, tmp, ctx->spart(), ctx->vd(V_ROWSUM), np, ctx->st(), s,
-                             ctx->kind, ctx->kind_c));
+                             ctx->kind, ctx->kind_c, q, ctx->xq_L, ctx->xq_e, ctx->xq_tau2));
+    }
     TRY(correction(ctx, prec, tmp, out, /*init=*/true, R));
     CU(launch_scale(out, -1.0, out, n, s));
     return MAG_OK;
@@ -2043,6 +2077,7 @@ int solve_impl(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, co
   int prec = o.precision;
   ctx->fac_valid = false;  // the workspace's tiles are about to be rewritten
   ctx->chain_ready = ctx->lh_ready = false;
+  ctx->xq_ok = false;      // the points may have changed in place since the last call
   {
     int64_t pool_tiles = 0;
     TRY(plan_out_of_core(ctx, n, prec, &pool_tiles));

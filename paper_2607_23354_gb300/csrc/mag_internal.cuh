@@ -303,9 +303,13 @@ cudaError_t launch_residual_mf(const double* X, int64_t n, int m, double t, cons
 // Matrix free over the lower triangle (each Z entry computed once, used for
 // its row and its column): P is scratch of N * N * 128 doubles, rowsum of n
 // doubles (overwritten with the row sums of Z).  Same outputs as above.
+// Xq (optional, Z = exp(-t d) with m <= 32): the quantized coordinates of
+// launch_quantize (limb bits qL, scale 2^qe, FP64 differences below qtau2),
+// the pair distances from their exact integer d^2.
 cudaError_t launch_residual_sym(const double* X, int64_t n, int m, double t, const double* w, const double* b,
                                 double* r, double* P, double* rowsum, int64_t np, DevStatus* st, cudaStream_t s,
-                                int kind = MAT_EXP, double kc = 0.0);
+                                int kind = MAT_EXP, double kc = 0.0, const long long* Xq = nullptr, int qL = 0,
+                                int qe = 0, double qtau2 = 0.0);
 // Stored: P is scratch of N * N * 128 doubles (one partial per row block,
 // tile and row); rowsum holds the row sums of Z from the generator.
 cudaError_t launch_residual_stored(const double* Zd, int64_t n, int64_t N, const double* w,
