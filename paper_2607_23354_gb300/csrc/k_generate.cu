@@ -389,6 +389,133 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
   }
 }
 
+// k_generate with the pair distances from the quantized coordinates (the
+// exact integer d^2 of mag_math.cuh; pairs with d^2 < tau2 from the FP64
+// differences of X), row sums always: the same entries, checks and outputs
+// in one pass, each pair finished on its own (row r = w + 16 i outer,
+// column 4 l + q inner, so a thread still stores its four entries of a row
+// with 16-byte stores).  Used where no distances are kept (a single t);
+// a multi-t call keeps them with k_dist_q, then k_generate_from_dist.
+template <bool WF, bool WD>
+__global__ void __launch_bounds__(GEN_THREADS, 1)
+    k_generate_q(const long long* __restrict__ Xq, const double* __restrict__ X, int64_t n, int m, QuantParams qp,
+                 double t, float* __restrict__ Zf, double* __restrict__ Zd, double* __restrict__ rowsum,
+                 DevStatus* st, int kind, double dcut, double kc) {
+  extern __shared__ double smem[];
+  long long* xr = reinterpret_cast<long long*>(smem);  // [TILE][GEN_MC] row points (broadcast reads)
+  long long* xc = xr + TILE * GEN_MC;                  // [GEN_MC][TILE] column points (conflict free)
+  __shared__ double colpart[GEN_THREADS / 32][TILE];
+  __shared__ unsigned long long warpmin[GEN_THREADS / 32];
+  __shared__ __align__(16) double exptab[EXPT_SMEM];
+  if (WD) load_exp_table(exptab);
+  int64_t I, J;
+  tri_coords((int64_t)blockIdx.x, &I, &J);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row0 = I * TILE, col0 = J * TILE;
+  for (int e = threadIdx.x; e < TILE * m; e += GEN_THREADS) {
+    const int r = e / m, l = e - r * m;
+    const int64_t gr = row0 + r, gc = col0 + r;
+    xr[r * GEN_MC + l] = gr < n ? Xq[gr * m + l] : 0ll;
+    xc[l * TILE + 32 * (r & 3) + (r >> 2)] = gc < n ? Xq[gc * m + l] : 0ll;
+  }
+  __syncthreads();
+  const unsigned long long mask = (1ull << qp.L) - 1ull;
+  const unsigned long long tau2_bits = (unsigned long long)__double_as_longlong(qp.tau2);
+  const int64_t tile_off = tri_index(I, J) * TILE_ELEMS;
+  float cs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  unsigned long long mind2b = 0x7ff0000000000000ull;  // +inf
+  int flags = 0;
+  const float tf = (float)t;
+  const unsigned long long tiny_bits = (unsigned long long)__double_as_longlong(dcut);
+#pragma unroll 1
+  for (int i = 0; i < 8; ++i) {
+    const int r = warp + 16 * i;
+    const int64_t gr = row0 + r;
+    const long long* xrow = xr + r * GEN_MC;
+    float rs = 0.0f;
+    float zfv[4];
+    double zdv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t gc = col0 + 4 * lane + q;
+      unsigned long long A = 0ull, Bx = 0ull, C = 0ull;
+      for (int l = 0; l < m; ++l) q_accumulate(xrow[l], xc[l * TILE + 32 * q + lane], mask, qp.L, A, Bx, C);
+      double zd = 0.0;
+      float zf = 0.0f;
+      if (gr >= n || gc >= n || gr == gc) {
+        zd = (gr == gc) ? 1.0 : 0.0;
+        zf = (float)zd;
+      } else {
+        double v = q128_to_f64(A, Bx, C, qp.L, qp.e);
+        unsigned long long vb = (unsigned long long)__double_as_longlong(v);
+        if (vb < tau2_bits) {
+          v = 0.0;
+          for (int l = 0; l < m; ++l) {
+            const double diff = X[gr * m + l] - X[gc * m + l];
+            v = fma(diff, diff, v);
+          }
+          vb = (unsigned long long)__double_as_longlong(v);
+        }
+        if (vb == 0ull) flags |= ST_DUPLICATE;
+        else mind2b = vb < mind2b ? vb : mind2b;
+        if (WD) {
+          const double dd = sqrt_pos(v);
+          if (!kind && (unsigned long long)__double_as_longlong(dd) > tiny_bits) {
+            zf = exp_neg_tiny_td(tf, t, dd);
+            zd = f32_to_f64_nonneg(zf);
+          } else {
+            zd = mat_entry(kind, t, kc, dd, exptab);
+            if (WF) zf = kind == MAT_DEFLATED ? __double2float_rn(zd) : f64_to_f32_nonneg(zd);
+          }
+        } else {
+          const float df = sqrtf(f64_to_f32_nonneg(v));
+          zf = kind == MAT_EXP ? expf(-tf * df)
+                               : (kind == MAT_SHIFTED_DIST ? 1.0f - tf * df
+                                                           : fmaf((float)kc, expm1f(-tf * df), 1.0f));
+        }
+      }
+      zfv[q] = zf;
+      zdv[q] = zd;
+      if (gr < n && gc < n) {
+        const float zs = WF ? zf : (float)zd;
+        rs += zs;
+        cs[q] += zs;
+      }
+    }
+    const int64_t e = tile_off + (int64_t)r * TILE + 4 * lane;
+    if (WF) *reinterpret_cast<float4*>(Zf + e) = make_float4(zfv[0], zfv[1], zfv[2], zfv[3]);
+    if (WD) {
+      *reinterpret_cast<double2*>(Zd + e) = make_double2(zdv[0], zdv[1]);
+      *reinterpret_cast<double2*>(Zd + e + 2) = make_double2(zdv[2], zdv[3]);
+    }
+    // the row's sum: an FP32 lane tree, one FP64 atomic per row
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+    if (lane == 0 && gr < n) atomicAdd(rowsum + gr, (double)rs);
+  }
+  if (flags) atomicOr(&st->flags, flags);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_xor_sync(0xffffffffu, mind2b, o);
+    mind2b = other < mind2b ? other : mind2b;
+  }
+  if (lane == 0) warpmin[warp] = mind2b;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) colpart[warp][4 * lane + q] = (double)cs[q];
+  __syncthreads();
+  if (I != J && threadIdx.x < TILE) {
+    double v = 0.0;
+    for (int w = 0; w < GEN_THREADS / 32; ++w) v += colpart[w][threadIdx.x];
+    const int64_t gc = col0 + threadIdx.x;
+    if (gc < n) atomicAdd(rowsum + gc, v);
+  }
+  if (threadIdx.x == 0) {
+    unsigned long long v = warpmin[0];
+    for (int w = 1; w < GEN_THREADS / 32; ++w) v = warpmin[w] < v ? warpmin[w] : v;
+    if (v < 0x7ff0000000000000ull) atomicMin(&st->min_d2_bits, v);
+  }
+}
+
 // Per dimension l < m (one CTA each): min and max of X[:, l] into
 // out[2 l], out[2 l + 1]; out[2 m] = 1 if a coordinate is not finite.
 __global__ void k_coord_range(const double* __restrict__ X, int64_t n, int m, double* __restrict__ out) {
@@ -482,6 +609,38 @@ cudaError_t launch_generate_dist(const double* X, int64_t n, int m, double t, in
   if (Zd)
     return launch_gen_t<false, true, true, true>(X, n, m, t, N, Zf, Zd, rowsum, st, s, Dd, kind, tiny_arg, 0, -1, kc);
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_generate_q(const long long* Xq, const double* X, int64_t n, int m, int L, int e, double tau2,
+                              double t, int64_t N, float* Zf, double* Zd, double* rowsum, DevStatus* st,
+                              cudaStream_t s, int kind, double tiny_arg, double kc) {
+  if (m < 1 || m > GEN_MC) return cudaErrorInvalidValue;
+  const size_t smem = 2 * (size_t)TILE * GEN_MC * sizeof(long long);
+  const QuantParams qp{L, e, tau2};
+  const int64_t tiles = num_lower_tiles(N);
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const double dcut = tiny_arg / t;
+  cudaError_t err;
+  if (Zf && Zd) {
+    err = cudaFuncSetAttribute(k_generate_q<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_generate_q<true, true><<<(unsigned)tiles, GEN_THREADS, smem, s>>>(Xq, X, n, m, qp, t, Zf, Zd, rowsum, st,
+                                                                         kind, dcut, kc);
+  } else if (Zf) {
+    err = cudaFuncSetAttribute(k_generate_q<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_generate_q<true, false><<<(unsigned)tiles, GEN_THREADS, smem, s>>>(Xq, X, n, m, qp, t, Zf, Zd, rowsum, st,
+                                                                          kind, INFINITY, kc);
+  } else if (Zd) {
+    err = cudaFuncSetAttribute(k_generate_q<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_generate_q<false, true><<<(unsigned)tiles, GEN_THREADS, smem, s>>>(Xq, X, n, m, qp, t, Zf, Zd, rowsum, st,
+                                                                          kind, dcut, kc);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_coord_range(const double* X, int64_t n, int m, double* out, cudaStream_t s) {

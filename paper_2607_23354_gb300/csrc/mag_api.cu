@@ -1280,8 +1280,18 @@ int generate(mag_ctx* ctx, const double* X, int32_t m, double t, bool f32, bool 
                               ctx->dist(), ctx->vd(V_ROWSUM), ctx->st(), s, ctx->kind, tiny_arg, ctx->kind_c));
     }
   } else {
-    CU(launch_generate(X, L.n, m, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr,
-                       ctx->vd(V_ROWSUM), ctx->st(), s, ctx->kind, tiny_arg, ctx->kind_c));
+    int qL = 0, qe = 0;
+    double qtau2 = 0.0;
+    const long long* Xq = nullptr;
+    if (quantize_points(ctx, X, L.n, m, &qL, &qe, &qtau2, &Xq)) {
+      CU(launch_generate_q(Xq, X, L.n, m, qL, qe, qtau2, t, L.N, f32 ? ctx->zf() : nullptr,
+                           f64 ? ctx->zd() : nullptr, ctx->vd(V_ROWSUM), ctx->st(), s, ctx->kind, tiny_arg,
+                           ctx->kind_c));
+      R->exact_distances = 1;
+    } else {
+      CU(launch_generate(X, L.n, m, t, L.N, f32 ? ctx->zf() : nullptr, f64 ? ctx->zd() : nullptr,
+                         ctx->vd(V_ROWSUM), ctx->st(), s, ctx->kind, tiny_arg, ctx->kind_c));
+    }
   }
   CU(launch_rowsum_max(ctx->vd(V_ROWSUM), L.n, ctx->st(), s));
   CU(cudaEventRecord(ctx->ev[1], s));

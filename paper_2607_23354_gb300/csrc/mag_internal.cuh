@@ -126,6 +126,11 @@ cudaError_t launch_quantize(const double* X, int64_t n, int m, const double* ran
                             cudaStream_t s);
 cudaError_t launch_dist_q(const long long* Xq, const double* X, int64_t n, int m, int L, int e, double tau2,
                           int64_t N, double* Dd, DevStatus* st, cudaStream_t s);
+// launch_generate (row sums, min d^2, flags) with the distances of
+// launch_dist_q, in one pass (no distances kept).
+cudaError_t launch_generate_q(const long long* Xq, const double* X, int64_t n, int m, int L, int e, double tau2,
+                              double t, int64_t N, float* Zf, double* Zd, double* rowsum, DevStatus* st,
+                              cudaStream_t s, int kind = MAT_EXP, double tiny_arg = INFINITY, double kc = 0.0);
 // FP32 tiles of one slab for the out-of-core factor: global tile columns
 // [t0, t0 + W) of rows [t0, N), in the slab layout (tile_index with column
 // cap W, tile (0, 0) = global (t0, t0)); no row sums; min d^2 and flags as

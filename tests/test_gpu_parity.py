@@ -519,6 +519,16 @@ def test_exact_distances_match_the_oracle(ctx, m, offset, kind):
         assert np.abs(w1 - w0).max() <= 1e-10 * np.abs(w0).max()
     d1, d0 = out[True][2][0]["min_distance"], out[False][2][0]["min_distance"]
     assert abs(d1 - d0) <= 4e-16 * d0
+    # a single-t solve: distances and Z in one pass from the quantized points
+    w_ref, mag_ref, _ = oracle.weighting(X, ts[0])
+    for exact in (True, False):
+        ctx.set_options(M.Options(exact_distances=exact))
+        try:
+            w, mag, info = ctx.solve(Xd, ts[0])
+        finally:
+            ctx.set_options(M.Options())
+        assert info["exact_distances"] == int(exact)
+        check_solution(X, ts[0], w.cpu().numpy(), mag, w_ref, mag_ref)
 
 
 def test_fp64_exponential_random_arguments(ctx):
