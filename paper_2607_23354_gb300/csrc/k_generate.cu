@@ -391,16 +391,18 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
 
 // k_generate with the pair distances from the quantized coordinates (the
 // exact integer d^2 of mag_math.cuh; pairs with d^2 < tau2 from the FP64
-// differences of X), row sums always: the same entries, checks and outputs
-// in one pass, each pair finished on its own (row r = w + 16 i outer,
-// column 4 l + q inner, so a thread still stores its four entries of a row
-// with 16-byte stores).  Used where no distances are kept (a single t);
-// a multi-t call keeps them with k_dist_q, then k_generate_from_dist.
+// differences of X), row sums when rowsum is given: the same entries,
+// checks and outputs in one pass, each pair finished on its own (row
+// r = w + 16 i outer, column 4 l + q inner, so a thread still stores its
+// four entries of a row with 16-byte stores), tiles in the slab layout of
+// k_generate.  Used where no distances are kept (a single t, the slabs of
+// the out-of-core factor); a multi-t call keeps them with k_dist_q, then
+// k_generate_from_dist.
 template <bool WF, bool WD>
 __global__ void __launch_bounds__(GEN_THREADS, 1)
     k_generate_q(const long long* __restrict__ Xq, const double* __restrict__ X, int64_t n, int m, QuantParams qp,
                  double t, float* __restrict__ Zf, double* __restrict__ Zd, double* __restrict__ rowsum,
-                 DevStatus* st, int kind, double dcut, double kc) {
+                 DevStatus* st, int kind, double dcut, double kc, int64_t t0, int64_t W) {
   extern __shared__ double smem[];
   long long* xr = reinterpret_cast<long long*>(smem);  // [TILE][GEN_MC] row points (broadcast reads)
   long long* xc = xr + TILE * GEN_MC;                  // [GEN_MC][TILE] column points (conflict free)
@@ -409,9 +411,9 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
   __shared__ __align__(16) double exptab[EXPT_SMEM];
   if (WD) load_exp_table(exptab);
   int64_t I, J;
-  tri_coords((int64_t)blockIdx.x, &I, &J);
+  tile_coords((int64_t)blockIdx.x, W, &I, &J);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t row0 = I * TILE, col0 = J * TILE;
+  const int64_t row0 = (t0 + I) * TILE, col0 = (t0 + J) * TILE;
   for (int e = threadIdx.x; e < TILE * m; e += GEN_THREADS) {
     const int r = e / m, l = e - r * m;
     const int64_t gr = row0 + r, gc = col0 + r;
@@ -421,7 +423,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
   __syncthreads();
   const unsigned long long mask = (1ull << qp.L) - 1ull;
   const unsigned long long tau2_bits = (unsigned long long)__double_as_longlong(qp.tau2);
-  const int64_t tile_off = tri_index(I, J) * TILE_ELEMS;
+  const int64_t tile_off = tile_index(I, J, W) * TILE_ELEMS;
   float cs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   unsigned long long mind2b = 0x7ff0000000000000ull;  // +inf
   int flags = 0;
@@ -491,7 +493,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
     // the row's sum: an FP32 lane tree, one FP64 atomic per row
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
-    if (lane == 0 && gr < n) atomicAdd(rowsum + gr, (double)rs);
+    if (rowsum && lane == 0 && gr < n) atomicAdd(rowsum + gr, (double)rs);
   }
   if (flags) atomicOr(&st->flags, flags);
 #pragma unroll
@@ -503,7 +505,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
 #pragma unroll
   for (int q = 0; q < 4; ++q) colpart[warp][4 * lane + q] = (double)cs[q];
   __syncthreads();
-  if (I != J && threadIdx.x < TILE) {
+  if (rowsum && I != J && threadIdx.x < TILE) {
     double v = 0.0;
     for (int w = 0; w < GEN_THREADS / 32; ++w) v += colpart[w][threadIdx.x];
     const int64_t gc = col0 + threadIdx.x;
@@ -613,11 +615,13 @@ cudaError_t launch_generate_dist(const double* X, int64_t n, int m, double t, in
 
 cudaError_t launch_generate_q(const long long* Xq, const double* X, int64_t n, int m, int L, int e, double tau2,
                               double t, int64_t N, float* Zf, double* Zd, double* rowsum, DevStatus* st,
-                              cudaStream_t s, int kind, double tiny_arg, double kc) {
+                              cudaStream_t s, int kind, double tiny_arg, double kc, int64_t t0, int64_t W) {
   if (m < 1 || m > GEN_MC) return cudaErrorInvalidValue;
   const size_t smem = 2 * (size_t)TILE * GEN_MC * sizeof(long long);
   const QuantParams qp{L, e, tau2};
-  const int64_t tiles = num_lower_tiles(N);
+  // N: tile rows of the (slab) matrix from global tile t0; W < 0: all columns
+  if (W < 0) W = N;
+  const int64_t tiles = num_slab_tiles(N, W);
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
   const double dcut = tiny_arg / t;
   cudaError_t err;
@@ -625,17 +629,17 @@ cudaError_t launch_generate_q(const long long* Xq, const double* X, int64_t n, i
     err = cudaFuncSetAttribute(k_generate_q<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     k_generate_q<true, true><<<(unsigned)tiles, GEN_THREADS, smem, s>>>(Xq, X, n, m, qp, t, Zf, Zd, rowsum, st,
-                                                                         kind, dcut, kc);
+                                                                         kind, dcut, kc, t0, W);
   } else if (Zf) {
     err = cudaFuncSetAttribute(k_generate_q<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     k_generate_q<true, false><<<(unsigned)tiles, GEN_THREADS, smem, s>>>(Xq, X, n, m, qp, t, Zf, Zd, rowsum, st,
-                                                                          kind, INFINITY, kc);
+                                                                          kind, INFINITY, kc, t0, W);
   } else if (Zd) {
     err = cudaFuncSetAttribute(k_generate_q<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     k_generate_q<false, true><<<(unsigned)tiles, GEN_THREADS, smem, s>>>(Xq, X, n, m, qp, t, Zf, Zd, rowsum, st,
-                                                                          kind, dcut, kc);
+                                                                          kind, dcut, kc, t0, W);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -697,9 +701,13 @@ cudaError_t launch_generate_from_dist(const double* Dd, int64_t n, double t, int
 }
 
 cudaError_t launch_generate_slab(const double* X, int64_t n, int m, double t, int64_t t0, int64_t W, float* Zf,
-                                 DevStatus* st, cudaStream_t s, double tiny_arg) {
+                                 DevStatus* st, cudaStream_t s, double tiny_arg, const long long* Xq, int qL, int qe,
+                                 double qtau2) {
   const int64_t N = (n + TILE - 1) / TILE;
   if (t0 < 0 || t0 >= N || W < 1) return cudaErrorInvalidValue;
+  if (Xq)
+    return launch_generate_q(Xq, X, n, m, qL, qe, qtau2, t, N - t0, Zf, nullptr, nullptr, st, s, MAT_EXP, tiny_arg,
+                             0.0, t0, W);
   return launch_gen_t<true, false, false>(X, n, m, t, N - t0, Zf, nullptr, nullptr, st, s, nullptr, MAT_EXP,
                                           tiny_arg, t0, W);
 }

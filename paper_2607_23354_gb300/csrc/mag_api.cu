@@ -902,6 +902,9 @@ int plan_out_of_core(mag_ctx* ctx, int64_t n, int prec, int64_t* pool_tiles) {
   return MAG_OK;
 }
 
+// The quantized coordinates of this solve's points (defined with generate).
+const long long* quantized(mag_ctx* ctx, const double* X, int64_t n, int32_t m);
+
 // The out-of-core factor of Z = exp[-t d] in an FP16 kind (UPD_FP16X3 or
 // UPD_FP16).  slab0_ready: slab 0 is already generated (the precision probe
 // read its leading block).
@@ -915,7 +918,11 @@ int factor_ooc(mag_ctx* ctx, const double* X, int32_t m, double t, int mode, boo
     const Slab& sl = ctx->slabs[si];
     float* Zs = ctx->slab_dev(sl);
     const int64_t rows = L.N - sl.c0;
-    if (!(si == 0 && slab0_ready)) CU(launch_generate_slab(X, L.n, m, t, sl.c0, sl.S, Zs, ctx->st(), s));
+    if (!(si == 0 && slab0_ready)) {
+      const long long* q = quantized(ctx, X, L.n, m);
+      CU(launch_generate_slab(X, L.n, m, t, sl.c0, sl.S, Zs, ctx->st(), s, INFINITY, q, ctx->xq_L, ctx->xq_e,
+                              ctx->xq_tau2));
+    }
     if (ctx->slab_cmap_base != Zs || ctx->slab_cmap_tiles != sl.tiles) {
       if (!make_c_map(&ctx->slab_cmap, Zs, sl.tiles))
         return fail(ctx, MAG_ECUDA, "cuTensorMapEncodeTiled failed for a slab");
@@ -1967,7 +1974,9 @@ int solve_ooc(mag_ctx* ctx, const double* X, int64_t n, int32_t m, double t, con
     const int64_t K = std::min<int64_t>(L.nb, kProbeTiles);
     if (ctx->slabs[0].S >= K && L.N >= 3 * K) {
       CU(cudaEventRecord(ctx->ev[0], s));
-      CU(launch_generate_slab(X, n, m, t, 0, ctx->slabs[0].S, ctx->slab_dev(ctx->slabs[0]), ctx->st(), s));
+      const long long* q = quantized(ctx, X, n, m);
+      CU(launch_generate_slab(X, n, m, t, 0, ctx->slabs[0].S, ctx->slab_dev(ctx->slabs[0]), ctx->st(), s, INFINITY,
+                              q, ctx->xq_L, ctx->xq_e, ctx->xq_tau2));
       CU(cudaEventRecord(ctx->ev[1], s));
       TRY(read_status(ctx));
       R->ms_gen += elapsed(ctx, 0, 1);

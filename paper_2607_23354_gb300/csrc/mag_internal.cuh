@@ -128,15 +128,20 @@ cudaError_t launch_dist_q(const long long* Xq, const double* X, int64_t n, int m
                           int64_t N, double* Dd, DevStatus* st, cudaStream_t s);
 // launch_generate (row sums, min d^2, flags) with the distances of
 // launch_dist_q, in one pass (no distances kept).
+// rowsum may be null (none); t0, W: the slab layout of launch_generate_slab.
 cudaError_t launch_generate_q(const long long* Xq, const double* X, int64_t n, int m, int L, int e, double tau2,
                               double t, int64_t N, float* Zf, double* Zd, double* rowsum, DevStatus* st,
-                              cudaStream_t s, int kind = MAT_EXP, double tiny_arg = INFINITY, double kc = 0.0);
+                              cudaStream_t s, int kind = MAT_EXP, double tiny_arg = INFINITY, double kc = 0.0,
+                              int64_t t0 = 0, int64_t W = -1);
 // FP32 tiles of one slab for the out-of-core factor: global tile columns
 // [t0, t0 + W) of rows [t0, N), in the slab layout (tile_index with column
 // cap W, tile (0, 0) = global (t0, t0)); no row sums; min d^2 and flags as
 // above (the slabs of a factor partition the lower triangle's pairs).
+// Xq (optional): the quantized coordinates (launch_quantize), the pairs'
+// distances from their exact integer d^2 (launch_generate_q).
 cudaError_t launch_generate_slab(const double* X, int64_t n, int m, double t, int64_t t0, int64_t W, float* Zf,
-                                 DevStatus* st, cudaStream_t s, double tiny_arg = INFINITY);
+                                 DevStatus* st, cudaStream_t s, double tiny_arg = INFINITY,
+                                 const long long* Xq = nullptr, int qL = 0, int qe = 0, double qtau2 = 0.0);
 // Z from stored FP64 distance tiles: Zf (may be null) and Zd (may be null), row sums.
 cudaError_t launch_generate_from_dist(const double* Dd, int64_t n, double t, int64_t N, float* Zf, double* Zd,
                                      double* rowsum, cudaStream_t s, int kind = MAT_EXP,
