@@ -65,6 +65,16 @@ def test_python_options_marshal(lib):
     o = M.Options(precision="fp64", residual_mode="stored", ir_tol=1e-13, ir_max_iters=7).to_c()
     assert o.precision == M.PREC_FP64 and o.residual_mode == M.RESID_STORED
     assert o.ir_tol == 1e-13 and o.ir_max_iters == 7
+    # the sweep kind and the exact distances: defaults as the C defaults
+    d = M.mag_options()
+    assert lib.mag_options_default(ctypes.byref(d)) == 0
+    o = M.Options().to_c()
+    assert o.sweep_kind == d.sweep_kind == 0 and o.exact_distances == d.exact_distances == 1
+    o = M.Options(sweeps="progress", exact_distances=False, fp16_gmres=1, gmres_matvec="fp64").to_c()
+    assert o.sweep_kind == 2 and o.exact_distances == 0 and o.fp16_gmres == 1 and o.gmres_matvec == 1
+    assert M.Options(sweeps="chain_fp32").to_c().sweep_kind == 1
+    with pytest.raises(ValueError):
+        M.Options(sweeps="fast").to_c()
 
 
 def test_product_path_has_no_oracle_import():
