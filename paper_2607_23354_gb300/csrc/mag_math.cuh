@@ -218,12 +218,6 @@ __device__ __forceinline__ double exp_neg_td(double t, double d, const double* t
   return exp_neg_core(N, kf, fma(-t, d, nl1_exact(N)), tab);
 }
 
-// exp(-a) for a >= 0 (NaN propagates): exp_neg_small below 64, else exp_neg.
-__device__ __forceinline__ double exp_neg_of(double a, const double* tab) {
-  return (unsigned long long)__double_as_longlong(a) < 0x4050000000000000ull ? exp_neg_small(a, tab)
-                                                                             : exp_neg(-a, tab);
-}
-
 // exp(x) - 1 for x <= 0 without the cancellation of exp(x) - 1 near 0: for
 // x >= -1/4 the Taylor series x + x^2/2! + ... + x^14/14! in Horner form
 // (the first omitted term is below 2^-63 |x|), else exp_neg(x) - 1, whose
