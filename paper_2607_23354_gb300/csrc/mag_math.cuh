@@ -107,8 +107,8 @@ __device__ __forceinline__ double f32_to_f64(float v) {
                                           ((unsigned long long)(b & 0x7fffffu) << 29)));
 }
 
-// exp(-a) for 0 <= a <= 64 in four FP64 operations (exp_neg_small) or
-// exp(-t d) in three (exp_neg_td).  N = round(256 a / ln 2) as in
+// exp(-a) for 0 <= a <= 64 in four FP64 operations (exp_neg_small), and
+// exp(-t d) in four as well, the product t d included (exp_neg_td).  N = round(256 a / ln 2) as in
 // exp_neg_small_d and r = N ln2/256 - a = r1 + rc, r1 = N L1 - a rounded
 // once (exact for exp_neg_small, whose a is a double; exp_neg_td forms N L1
 // exactly on the integer pipe and r1 = fma(-t, d, N L1), so t d is never
