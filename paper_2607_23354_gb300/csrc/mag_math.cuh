@@ -108,8 +108,9 @@ __device__ __forceinline__ double f32_to_f64(float v) {
 }
 
 // exp(-a) for 0 <= a <= 64 in four FP64 operations (exp_neg_small), and
-// exp(-t d) in four as well, the product t d included (exp_neg_td).  N = round(256 a / ln 2) as in
-// exp_neg_small_d and r = N ln2/256 - a = r1 + rc, r1 = N L1 - a rounded
+// exp(-t d) in four as well, the product t d included (exp_neg_td).
+// N = round(256 a / ln 2) as in exp_neg_small_d and r = N ln2/256 - a =
+// r1 + rc, r1 = N L1 - a rounded
 // once (exact for exp_neg_small, whose a is a double; exp_neg_td forms N L1
 // exactly on the integer pipe and r1 = fma(-t, d, N L1), so t d is never
 // rounded), rc = N L2 in float-float.  exp(-a) = 2^(-N/256) exp(r) and
